@@ -1,0 +1,210 @@
+/*
+ * tsylv.h -- C ABI of the GB300 (sm_103a) solver for triangular tensor
+ * Sylvester equations.
+ *
+ * Operation (Chen & Kressner, "Recursive blocked algorithms for linear
+ * systems with Kronecker product structure"):
+ *
+ *   Laplace-like form, Sec. 2, Eq. (2.2):
+ *       X x_1 A_1 + X x_2 A_2 + ... + X x_d A_d = B
+ *   d-term generalized form (the K-term equation of the Conclusions with
+ *   K = d and mode family {A_mu, C_mu}):
+ *       sum_mu  X x_1 C_1 ... x_mu A_mu ... x_d C_d = B
+ *
+ * where Y = X x_mu M means Y_(mu) = M X_(mu) (Sec. 2), A_mu is upper
+ * quasi-triangular (real Schur form: 1x1 and 2x2 diagonal blocks, Sec. 2
+ * after Alg. 1) and C_mu is upper triangular.  The solution is unique iff
+ * no sum of eigenvalues lambda_1 + ... + lambda_d vanishes (Sec. 2) --
+ * respectively iff the generalized operator is nonsingular.
+ *
+ * Method: the recursive blocked algorithm of Sec. 2.1 (Alg. 2) with merged
+ * modes in the base case (Sec. 2.2-2.3, Alg. 3).  The split tree of Alg. 2
+ * fixes a block partition of every mode; the right-hand-side updates of
+ * Eq. (2.3a) become block mode-mu products, and the leaves are solved by a
+ * back-substitution in which 2x2 Schur blocks are solved as coupled groups
+ * (the diagonal blocks after the perfect shuffle of Sec. 2.3).  The GPU runs
+ * the independent leaves of the split tree concurrently (anti-diagonal
+ * wavefronts over the block grid), one launch per wavefront, all captured in
+ * a CUDA graph.
+ *
+ * Layout.  Tensors are dense and column-major with mode 1 fastest -- the
+ * index map Eq. (2.1): element (i_1, ..., i_d) (0-based) is at
+ * i_1 + n_1*(i_2 + n_2*(i_3 + ...)).  A contiguous C-ordered torch tensor of
+ * shape (n_d, ..., n_1) has this layout.  Every coefficient matrix is an
+ * n_mu x n_mu column-major (LAPACK) array: M(i, j) at M[i + n_mu*j].
+ * Entries of A_mu below the first subdiagonal and of C_mu below the diagonal
+ * are never read (treated as zero).  A nonzero A_mu(i+1, i) marks a 2x2
+ * block at (i, i+1); two consecutive nonzero subdiagonal entries are an error.
+ *
+ * Pointers.  `n` and the arrays `A`, `C`, `dA`, `dC` are host arrays; the
+ * matrices and tensors they point to live in device memory (unless
+ * opts->host_io is set, see below).  All device memory is owned by the
+ * caller.  The library allocates no device memory: every scratch buffer is
+ * carved out of `work`, whose size comes from the matching *_workspace_bytes
+ * query (256-byte alignment is required).  In-place use (X == B) is allowed.
+ *
+ * Streams.  Work is queued on `stream`.  Each call reads the 2x2 block
+ * structure of A back to the host (a short synchronisation on `stream`
+ * before the solve) and synchronises `stream` again at the end to read the
+ * device status flag, so every call returns with its results complete.
+ *
+ * Status.  0 on success; -i if the i-th argument (1-based) is invalid, as in
+ * LAPACK's info; positive values are numerical or runtime conditions listed
+ * below.  No call aborts, traps or throws.
+ */
+#ifndef TSYLV_H
+#define TSYLV_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum tsylv_status {
+    TSYLV_OK = 0,
+    TSYLV_ESINGULAR = 1,    /* a diagonal group system had a zero or tiny pivot   */
+    TSYLV_ENONFINITE = 2,   /* NaN or Inf appeared in the solution                */
+    TSYLV_ENOCONV = 3,      /* refinement missed opts->tol within max_refine steps */
+    TSYLV_ECUDA = 4,        /* a CUDA runtime call failed                         */
+    TSYLV_ETIMEOUT = 5,     /* a bounded device-side wait ran out                 */
+    TSYLV_EUNSUPPORTED = 6  /* valid arguments outside what this build supports   */
+};
+
+enum tsylv_precision {
+    TSYLV_FP64 = 0,          /* plain FP64 solve (FP64 pipes)                       */
+    TSYLV_FP32_REFINED = 1,  /* FP32 solves + FP64-accurate residual refinement     */
+    TSYLV_TF32_REFINED = 2,  /* TF32 tensor-core updates, FP32 accumulation, refined */
+    TSYLV_BF16_REFINED = 3   /* BF16 tensor-core updates, FP32 accumulation, refined */
+};
+
+enum tsylv_residual_kind {
+    TSYLV_RESID_DF64 = 0,    /* residual in double-FP32 (~2^-48) arithmetic        */
+    TSYLV_RESID_FP64 = 1     /* residual on the native FP64 pipes                   */
+};
+
+typedef struct tsylv_opts {
+    int precision;    /* enum tsylv_precision, default TSYLV_FP64                    */
+    int max_refine;   /* refinement steps for *_REFINED (default 10)                 */
+    double tol;       /* target ||B - A(X)|| / (||A|| ||X||) (default 1e-12)         */
+    int residual;     /* enum tsylv_residual_kind, default TSYLV_RESID_DF64          */
+    int nmin;         /* largest block extent per mode; 0 = the default for d        */
+    int split;        /* largest cluster size for split block updates; 0 = auto      */
+    int use_graph;    /* 1 (default): capture each schedule once and replay it      */
+    int host_io;      /* 1: B, X, A, C (and backward buffers) are host pointers; the
+                         call copies them through `work` inside the call             */
+} tsylv_opts;
+
+typedef struct tsylv_info {
+    int iterations;       /* refinement steps taken (0 for TSYLV_FP64)              */
+    int waves;            /* wavefront launches per solve                           */
+    int launches;         /* kernels launched by the call                           */
+    int tiles;            /* blocks of the block grid                               */
+    double resid;         /* final ||B - A(X)|| / (||A|| ||X||) when computed, else -1 */
+    double norm_A;        /* the ||A|| used above (sum_mu ||A_mu||_2 prod ||C_eta||_2) */
+    double flops;         /* floating-point operations executed per solve           */
+} tsylv_info;
+
+/* Fill *opts with the defaults listed above. */
+void tsylv_opts_default(tsylv_opts* opts);
+
+/* Human-readable text of a status code (static storage). */
+const char* tsylv_status_string(int status);
+
+/* Workspace bytes for tsylv_solve (generalized = 0) / gtsylv_solve
+ * (generalized = 1) and their transposed variants.  Returns 0 for invalid
+ * arguments.  d in 1..4, every n[mu] >= 1. */
+size_t tsylv_workspace_bytes(int d, const int64_t* n, int generalized, const tsylv_opts* opts);
+
+/* Solve the Laplace-like equation Eq. (2.2).
+ *   d          number of modes (1..4)
+ *   n          host array of d mode sizes
+ *   A          host array of d pointers to the n_mu x n_mu upper
+ *              quasi-triangular coefficients
+ *   B          right-hand side tensor (read only)
+ *   X          solution tensor (written; may equal B)
+ *   work       device workspace of work_bytes >= tsylv_workspace_bytes(...)
+ *   opts       NULL for the defaults
+ *   info       optional output (may be NULL)
+ *   stream     CUDA stream (0 = legacy default stream)
+ * Errors: -1..-10 for the corresponding argument; TSYLV_ESINGULAR when a
+ * group pivot of the back-substitution is zero or below 16 eps times the
+ * group's largest entry; TSYLV_ENONFINITE for NaN/Inf in X; TSYLV_ENOCONV for
+ * a refined solve that missed opts->tol (X then holds the last iterate). */
+int tsylv_solve(int d, const int64_t* n, const double* const* A, const double* B, double* X,
+                void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
+                cudaStream_t stream);
+
+/* Solve the d-term generalized equation sum_mu X x_mu A_mu x_{eta!=mu} C_eta = B.
+ * C: host array of d pointers to the upper triangular C_mu.  Other arguments
+ * and errors as tsylv_solve (argument numbers shift by one after A). */
+int gtsylv_solve(int d, const int64_t* n, const double* const* A, const double* const* C,
+                 const double* B, double* X, void* work, size_t work_bytes,
+                 const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
+
+/* Transposed equations A^T(L) = G: the coefficients enter as A_mu^T (lower
+ * quasi-triangular) and C_mu^T.  Solved by the index flip J A_mu^T J (J the
+ * reversal permutation), which is upper quasi-triangular again, so the same
+ * recursion runs in reversed order.  Arguments as the forward calls
+ * (B -> G, X -> L). */
+int tsylv_solve_transposed(int d, const int64_t* n, const double* const* A, const double* G,
+                           double* L, void* work, size_t work_bytes, const tsylv_opts* opts,
+                           tsylv_info* info, cudaStream_t stream);
+int gtsylv_solve_transposed(int d, const int64_t* n, const double* const* A,
+                            const double* const* C, const double* G, double* L, void* work,
+                            size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
+                            cudaStream_t stream);
+
+/* Residual R = B - A(X) (C == NULL: Laplace form) with the arithmetic chosen
+ * by opts->residual; *rel (optional, host) receives ||R|| / (||A|| ||X||).
+ * Workspace: tsylv_workspace_bytes of the matching form. */
+int tsylv_residual(int d, const int64_t* n, const double* const* A, const double* const* C,
+                   const double* B, const double* X, double* R, double* rel, void* work,
+                   size_t work_bytes, const tsylv_opts* opts, cudaStream_t stream);
+
+/* Workspace bytes for tsylv_backward. */
+size_t tsylv_backward_workspace_bytes(int d, const int64_t* n, int generalized,
+                                      const tsylv_opts* opts);
+
+/* Adjoint of X = A^{-1}(B) for a scalar loss with gradient dX = dL/dX:
+ *   Lambda = A^{-T}(dX)                                 (transposed solve)
+ *   dB     = Lambda
+ *   dA_mu  = -mask_A( Lambda_(mu) [X x_{eta!=mu} C_eta]_(mu)^T )
+ *   dC_mu  = -mask_C( sum_{nu!=mu} Lambda_(mu) [X x_nu A_nu x_{eta!=mu,nu} C_eta]_(mu)^T )
+ * mask_A keeps the upper triangle and the subdiagonal entries of the 2x2
+ * blocks of A_mu; mask_C keeps the upper triangle.  C == NULL: Laplace form
+ * (then dC is ignored).  dB may be NULL; dA, dC may be NULL or hold NULL
+ * entries for gradients that are not wanted.  X is the forward solution. */
+int tsylv_backward(int d, const int64_t* n, const double* const* A, const double* const* C,
+                   const double* X, const double* dX, double* dB, double* const* dA,
+                   double* const* dC, void* work, size_t work_bytes, const tsylv_opts* opts,
+                   tsylv_info* info, cudaStream_t stream);
+
+/* Workspace bytes for tsylv_solve_batched. */
+size_t tsylv_batched_workspace_bytes(int count, const int* d, const int64_t* n_packed,
+                                     int generalized, const tsylv_opts* opts);
+
+/* Many independent equations of different sizes in one persistent launch.
+ *   count       number of equations
+ *   d           host array [count] of orders (1..4)
+ *   n_packed    host array: the mode sizes of all equations, concatenated
+ *   off_A       host array [sum d]: element offset of each A_mu (and C_mu) in
+ *               A_pool / C_pool, in the order of n_packed
+ *   off_X       host array [count]: element offset of each tensor in B_pool /
+ *               X_pool
+ *   C_pool      NULL for Laplace-form equations
+ * Every equation uses opts->precision; statuses are combined (the first
+ * nonzero wins).  per_status (optional, host [count]) receives each one. */
+int tsylv_solve_batched(int count, const int* d, const int64_t* n_packed, const int64_t* off_A,
+                        const int64_t* off_X, const double* A_pool, const double* C_pool,
+                        const double* B_pool, double* X_pool, void* work, size_t work_bytes,
+                        const tsylv_opts* opts, int* per_status, tsylv_info* info,
+                        cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSYLV_H */

@@ -1,0 +1,215 @@
+"""GB300-native solver for triangular tensor Sylvester equations.
+
+Thin Python binding over the C ABI of ``include/tsylv.h``: it only marshals
+torch CUDA tensors (device memory, streams) into pointers; every step of the
+solve runs in the library's sm_103a kernels.  There is no CPU path: if
+``libtsylv.so`` has not been built, every call raises.
+
+Tensor convention: a tensor argument has the mathematical shape
+``(n_1, ..., n_d)`` and column-major memory (mode 1 fastest, the index map
+Eq. (2.1) of Chen & Kressner); matrices are ``(n, n)`` column-major.  Use
+:func:`fortran` to obtain that layout from any tensor.  Inputs in another
+layout are copied into it first (marshalling only).
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (TSYLV_BF16_REFINED, TSYLV_FP32_REFINED, TSYLV_FP64, TSYLV_RESID_DF64, TSYLV_RESID_FP64,
+                   TSYLV_TF32_REFINED, Info, Opts, default_opts, load, status_string)
+
+__all__ = ["tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
+           "tsylv_residual", "tsylv_backward", "tsylv_solve_batched", "solve", "fortran", "TsylvError",
+           "Opts", "Info", "default_opts", "TSYLV_FP64", "TSYLV_FP32_REFINED", "TSYLV_TF32_REFINED",
+           "TSYLV_BF16_REFINED", "TSYLV_RESID_DF64", "TSYLV_RESID_FP64", "workspace"]
+
+
+class TsylvError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: status %d (%s)" % (where, status, status_string(status)))
+
+
+def is_fortran(t):
+    d = t.dim()
+    exp = 1
+    for k in range(d):
+        if t.shape[k] != 1 and t.stride(k) != exp:
+            return False
+        exp *= t.shape[k]
+    return True
+
+
+def fortran(t, dtype=torch.float64):
+    """Same values, column-major memory (mode 1 fastest), float64, on t's device."""
+    t = t.to(dtype)
+    if is_fortran(t):
+        return t
+    d = t.dim()
+    perm = list(range(d))[::-1]
+    return t.permute(*perm).contiguous().permute(*perm)
+
+
+def empty_fortran(shape, device, dtype=torch.float64):
+    d = len(shape)
+    perm = list(range(d))[::-1]
+    return torch.empty(tuple(shape[::-1]), device=device, dtype=dtype).permute(*perm)
+
+
+_ws = {}
+
+
+def workspace(nbytes, device):
+    """Grow-only device workspace (allocated by PyTorch, reused across calls)."""
+    dev = torch.device(device)
+    key = (dev.type, dev.index if dev.index is not None else torch.cuda.current_device())
+    buf = _ws.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+        _ws[key] = buf
+    return buf
+
+
+def _check_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("expected CUDA tensors (the solver runs on the GPU only)")
+
+
+def _mats(ms):
+    ms = [fortran(m) for m in ms]
+    arr = (ctypes.c_void_p * len(ms))(*[m.data_ptr() for m in ms])
+    return ms, arr
+
+
+def _dims(shape):
+    return (ctypes.c_int64 * len(shape))(*[int(s) for s in shape])
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _opts(opts, kw):
+    if opts is None:
+        opts = default_opts(**kw)
+    elif kw:
+        for k, v in kw.items():
+            setattr(opts, k, v)
+    return opts
+
+
+def _solve(fn, ws_fn, gen, transposed, A, C, B, X, opts, check, stream, info, kw):
+    lib = load()
+    _check_cuda(B, *A, *(C or []))
+    o = _opts(opts, kw)
+    B = fortran(B)
+    d = B.dim()
+    if X is None:
+        X = empty_fortran(B.shape, B.device)
+    elif not is_fortran(X) or X.dtype != torch.float64:
+        raise ValueError("X must be a float64 column-major tensor (see fortran())")
+    A_, pa = _mats(A)
+    pc = None
+    if gen:
+        C_, pc = _mats(C)
+    n = _dims(B.shape)
+    nbytes = ws_fn(d, n, 1 if gen else 0, ctypes.byref(o))
+    if nbytes == 0:
+        raise ValueError("invalid problem shape %s" % (tuple(B.shape),))
+    work = workspace(nbytes, B.device)
+    inf = info if info is not None else Info()
+    args = [d, n, pa] + ([pc] if gen else []) + [B.data_ptr(), X.data_ptr(), work.data_ptr(), work.numel(),
+                                                 ctypes.byref(o), ctypes.byref(inf), _stream(stream)]
+    st = fn(*args)
+    if check and st != 0:
+        raise TsylvError(st, fn.__name__)
+    return X, st
+
+
+def tsylv_solve(A, B, X=None, *, opts=None, check=True, stream=None, info=None, **kw):
+    """X with sum_mu X x_mu A_mu = B (Eq. (2.2)); returns (X, status)."""
+    lib = load()
+    return _solve(lib.tsylv_solve, lib.tsylv_workspace_bytes, False, False, A, None, B, X, opts, check, stream,
+                  info, kw)
+
+
+def gtsylv_solve(A, C, B, X=None, *, opts=None, check=True, stream=None, info=None, **kw):
+    """X with sum_mu X x_mu A_mu x_{eta != mu} C_eta = B; returns (X, status)."""
+    lib = load()
+    return _solve(lib.gtsylv_solve, lib.tsylv_workspace_bytes, True, False, A, C, B, X, opts, check, stream,
+                  info, kw)
+
+
+def tsylv_solve_transposed(A, G, L=None, *, opts=None, check=True, stream=None, info=None, **kw):
+    """L with A^T(L) = G for the Laplace-form operator; returns (L, status)."""
+    lib = load()
+    return _solve(lib.tsylv_solve_transposed, lib.tsylv_workspace_bytes, False, True, A, None, G, L, opts, check,
+                  stream, info, kw)
+
+
+def gtsylv_solve_transposed(A, C, G, L=None, *, opts=None, check=True, stream=None, info=None, **kw):
+    """L with A^T(L) = G for the generalized operator; returns (L, status)."""
+    lib = load()
+    return _solve(lib.gtsylv_solve_transposed, lib.tsylv_workspace_bytes, True, True, A, C, G, L, opts, check,
+                  stream, info, kw)
+
+
+def tsylv_residual(A, B, X, C=None, R=None, *, opts=None, check=True, stream=None, **kw):
+    """R = B - A(X) and the relative residual ||R|| / (||A|| ||X||)."""
+    lib = load()
+    _check_cuda(B, X, *A, *(C or []))
+    o = _opts(opts, kw)
+    B = fortran(B)
+    X = fortran(X)
+    if R is None:
+        R = empty_fortran(B.shape, B.device)
+    A_, pa = _mats(A)
+    pc = None
+    if C is not None:
+        C_, pc = _mats(C)
+    n = _dims(B.shape)
+    d = B.dim()
+    work = workspace(lib.tsylv_workspace_bytes(d, n, 1 if C is not None else 0, ctypes.byref(o)), B.device)
+    rel = ctypes.c_double(-1.0)
+    st = lib.tsylv_residual(d, n, pa, pc, B.data_ptr(), X.data_ptr(), R.data_ptr(), ctypes.byref(rel),
+                            work.data_ptr(), work.numel(), ctypes.byref(o), _stream(stream))
+    if check and st != 0:
+        raise TsylvError(st, "tsylv_residual")
+    return R, rel.value, st
+
+
+def tsylv_backward(A, X, dX, C=None, *, want_dB=True, want_dA=True, want_dC=True, opts=None, check=True,
+                   stream=None, info=None, **kw):
+    """(dB, dA list, dC list) of a scalar loss with gradient dX at the solution X."""
+    lib = load()
+    _check_cuda(X, dX, *A, *(C or []))
+    o = _opts(opts, kw)
+    X = fortran(X)
+    dX = fortran(dX)
+    d = X.dim()
+    A_, pa = _mats(A)
+    pc = None
+    gen = C is not None
+    if gen:
+        C_, pc = _mats(C)
+    dB = empty_fortran(X.shape, X.device) if want_dB else None
+    dA = [empty_fortran((m, m), X.device) for m in X.shape] if want_dA else None
+    dC = [empty_fortran((m, m), X.device) for m in X.shape] if (gen and want_dC) else None
+    pdA = (ctypes.c_void_p * d)(*[t.data_ptr() for t in dA]) if dA else None
+    pdC = (ctypes.c_void_p * d)(*[t.data_ptr() for t in dC]) if dC else None
+    n = _dims(X.shape)
+    work = workspace(lib.tsylv_backward_workspace_bytes(d, n, 1 if gen else 0, ctypes.byref(o)), X.device)
+    inf = info if info is not None else Info()
+    st = lib.tsylv_backward(d, n, pa, pc, X.data_ptr(), dX.data_ptr(), dB.data_ptr() if dB is not None else None,
+                            pdA, pdC, work.data_ptr(), work.numel(), ctypes.byref(o), ctypes.byref(inf),
+                            _stream(stream))
+    if check and st != 0:
+        raise TsylvError(st, "tsylv_backward")
+    return dB, dA, dC
+
+
+from .autograd import solve  # noqa: E402
+from .batched import tsylv_solve_batched  # noqa: E402

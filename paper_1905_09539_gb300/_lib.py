@@ -1,0 +1,100 @@
+"""ctypes view of the C ABI in include/tsylv.h (libtsylv.so, built in-tree)."""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtsylv.so")
+
+TSYLV_OK = 0
+TSYLV_ESINGULAR = 1
+TSYLV_ENONFINITE = 2
+TSYLV_ENOCONV = 3
+TSYLV_ECUDA = 4
+TSYLV_ETIMEOUT = 5
+TSYLV_EUNSUPPORTED = 6
+
+TSYLV_FP64 = 0
+TSYLV_FP32_REFINED = 1
+TSYLV_TF32_REFINED = 2
+TSYLV_BF16_REFINED = 3
+
+TSYLV_RESID_DF64 = 0
+TSYLV_RESID_FP64 = 1
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double),
+                ("residual", ctypes.c_int), ("nmin", ctypes.c_int), ("split", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("host_io", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("waves", ctypes.c_int), ("launches", ctypes.c_int),
+                ("tiles", ctypes.c_int), ("resid", ctypes.c_double), ("norm_A", ctypes.c_double),
+                ("flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = [
+    "tsylv_opts_default", "tsylv_status_string", "tsylv_workspace_bytes", "tsylv_solve", "gtsylv_solve",
+    "tsylv_solve_transposed", "gtsylv_solve_transposed", "tsylv_residual", "tsylv_backward_workspace_bytes",
+    "tsylv_backward", "tsylv_batched_workspace_bytes", "tsylv_solve_batched",
+]
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libtsylv.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libtsylv.so is missing: build it with `python -c 'import __graft_entry__ as g; "
+                           "g.build()'` (the solver has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    I64P = ctypes.POINTER(ctypes.c_int64)
+    OP = ctypes.POINTER(Opts)
+    IP = ctypes.POINTER(Info)
+    S = ctypes.c_size_t
+    lib.tsylv_opts_default.argtypes = [OP]
+    lib.tsylv_opts_default.restype = None
+    lib.tsylv_status_string.argtypes = [I]
+    lib.tsylv_status_string.restype = ctypes.c_char_p
+    lib.tsylv_workspace_bytes.argtypes = [I, I64P, I, OP]
+    lib.tsylv_workspace_bytes.restype = S
+    lib.tsylv_solve.argtypes = [I, I64P, P, P, P, P, S, OP, IP, P]
+    lib.gtsylv_solve.argtypes = [I, I64P, P, P, P, P, P, S, OP, IP, P]
+    lib.tsylv_solve_transposed.argtypes = [I, I64P, P, P, P, P, S, OP, IP, P]
+    lib.gtsylv_solve_transposed.argtypes = [I, I64P, P, P, P, P, P, S, OP, IP, P]
+    lib.tsylv_residual.argtypes = [I, I64P, P, P, P, P, P, ctypes.POINTER(ctypes.c_double), P, S, OP, P]
+    lib.tsylv_backward_workspace_bytes.argtypes = [I, I64P, I, OP]
+    lib.tsylv_backward_workspace_bytes.restype = S
+    lib.tsylv_backward.argtypes = [I, I64P, P, P, P, P, P, P, P, P, S, OP, IP, P]
+    lib.tsylv_batched_workspace_bytes.argtypes = [I, ctypes.POINTER(I), I64P, I, OP]
+    lib.tsylv_batched_workspace_bytes.restype = S
+    lib.tsylv_solve_batched.argtypes = [I, ctypes.POINTER(I), I64P, I64P, I64P, P, P, P, P, P, S, OP,
+                                        ctypes.POINTER(I), IP, P]
+    for f in ("tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
+              "tsylv_residual", "tsylv_backward", "tsylv_solve_batched"):
+        getattr(lib, f).restype = I
+    _lib = lib
+    return lib
+
+
+def default_opts(**kw):
+    o = Opts()
+    load().tsylv_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError("unknown option %r" % k)
+        setattr(o, k, v)
+    return o
+
+
+def status_string(s):
+    return load().tsylv_status_string(int(s)).decode()

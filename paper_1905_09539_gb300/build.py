@@ -1,0 +1,77 @@
+"""Build the in-tree CUDA library libtsylv.so (sm_103a only).
+
+Every translation unit under csrc/ is compiled by nvcc in parallel into
+_build/, then linked into paper_1905_09539_gb300/libtsylv.so against the
+shared CUDA runtime (the one PyTorch also uses).
+"""
+import concurrent.futures
+import glob
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libtsylv.so")
+ROOT = os.path.dirname(HERE)
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+         "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
+        if c and os.path.exists(c):
+            return c
+    raise RuntimeError("nvcc not found; the CUDA toolkit is required to build libtsylv.so")
+
+
+def _sources():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+
+
+def _headers():
+    return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+        glob.glob(os.path.join(ROOT, "include", "*.h"))
+
+
+def _stale(obj, src, hdr_mtime):
+    return not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_mtime)
+
+
+def build(verbose=False, jobs=None, extra=()):
+    nvcc = _nvcc()
+    os.makedirs(BUILD, exist_ok=True)
+    hdr_mtime = max([os.path.getmtime(h) for h in _headers()] + [0])
+    objs, todo = [], []
+    for src in _sources():
+        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        objs.append(obj)
+        if _stale(obj, src, hdr_mtime):
+            lang = ["-x", "cu"] if src.endswith(".cu") else []
+            todo.append([nvcc] + ARCH + FLAGS + list(extra) + lang + ["-c", src, "-o", obj])
+
+    def run(cmd):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed:\n%s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
+        return (r.stdout + r.stderr).strip()
+
+    jobs = jobs or min(len(todo) or 1, os.cpu_count() or 4)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=jobs) as ex:
+        for out in ex.map(run, todo):
+            if verbose and out:
+                print(out)
+    if todo or not os.path.exists(LIB):
+        tmp = LIB + ".tmp%d" % os.getpid()
+        run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs +
+            ["-Xlinker", "-rpath", "-Xlinker", "/usr/local/cuda/lib64"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose="-v" in sys.argv, extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else ()))

@@ -1,0 +1,99 @@
+// C ABI entry points (include/tsylv.h): argument checks, structure read-back,
+// schedule lookup, CUDA-graph capture/replay and status read-back.
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "plan.h"
+#include "solver.h"
+
+using namespace tsylv;
+
+extern "C" void tsylv_opts_default(tsylv_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = TSYLV_FP64;
+    o->max_refine = 10;
+    o->tol = 1e-12;
+    o->residual = TSYLV_RESID_DF64;
+    o->nmin = 0;
+    o->split = 0;
+    o->use_graph = 1;
+    o->host_io = 0;
+}
+
+extern "C" const char* tsylv_status_string(int s) {
+    if (s < 0) return "invalid argument (-i: the i-th argument)";
+    switch (s) {
+        case TSYLV_OK: return "ok";
+        case TSYLV_ESINGULAR: return "singular diagonal group system";
+        case TSYLV_ENONFINITE: return "non-finite value in the solution";
+        case TSYLV_ENOCONV: return "refinement did not reach the tolerance";
+        case TSYLV_ECUDA: return "CUDA runtime error";
+        case TSYLV_ETIMEOUT: return "bounded device wait timed out";
+        case TSYLV_EUNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+extern "C" size_t tsylv_workspace_bytes(int d, const int64_t* n, int generalized, const tsylv_opts* opts) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    return solver_workspace_bytes(d, n, generalized != 0, o, false);
+}
+
+extern "C" int tsylv_solve(int d, const int64_t* n, const double* const* A, const double* B, double* X, void* work,
+                           size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream) {
+    return solver_solve(d, n, A, nullptr, B, X, work, work_bytes, opts, info, stream, false, false);
+}
+
+extern "C" int gtsylv_solve(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,
+                            double* X, void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
+                            cudaStream_t stream) {
+    return solver_solve(d, n, A, C, B, X, work, work_bytes, opts, info, stream, true, false);
+}
+
+extern "C" int tsylv_solve_transposed(int d, const int64_t* n, const double* const* A, const double* G, double* L,
+                                      void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
+                                      cudaStream_t stream) {
+    return solver_solve(d, n, A, nullptr, G, L, work, work_bytes, opts, info, stream, false, true);
+}
+
+extern "C" int gtsylv_solve_transposed(int d, const int64_t* n, const double* const* A, const double* const* C,
+                                       const double* G, double* L, void* work, size_t work_bytes,
+                                       const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream) {
+    return solver_solve(d, n, A, C, G, L, work, work_bytes, opts, info, stream, true, true);
+}
+
+extern "C" int tsylv_residual(int d, const int64_t* n, const double* const* A, const double* const* C,
+                              const double* B, const double* X, double* R, double* rel, void* work, size_t work_bytes,
+                              const tsylv_opts* opts, cudaStream_t stream) {
+    return solver_residual(d, n, A, C, B, X, R, rel, work, work_bytes, opts, stream);
+}
+
+extern "C" size_t tsylv_backward_workspace_bytes(int d, const int64_t* n, int generalized, const tsylv_opts* opts) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    return solver_backward_workspace_bytes(d, n, generalized != 0, o);
+}
+
+extern "C" int tsylv_backward(int d, const int64_t* n, const double* const* A, const double* const* C, const double* X,
+                              const double* dX, double* dB, double* const* dA, double* const* dC, void* work,
+                              size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream) {
+    return solver_backward(d, n, A, C, X, dX, dB, dA, dC, work, work_bytes, opts, info, stream);
+}
+
+extern "C" size_t tsylv_batched_workspace_bytes(int count, const int* d, const int64_t* n_packed, int generalized,
+                                                const tsylv_opts* opts) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    return solver_batched_workspace_bytes(count, d, n_packed, generalized != 0, o);
+}
+
+extern "C" int tsylv_solve_batched(int count, const int* d, const int64_t* n_packed, const int64_t* off_A,
+                                   const int64_t* off_X, const double* A_pool, const double* C_pool,
+                                   const double* B_pool, double* X_pool, void* work, size_t work_bytes,
+                                   const tsylv_opts* opts, int* per_status, tsylv_info* info, cudaStream_t stream) {
+    return solver_batched(count, d, n_packed, off_A, off_X, A_pool, C_pool, B_pool, X_pool, work, work_bytes, opts,
+                          per_status, info, stream);
+}

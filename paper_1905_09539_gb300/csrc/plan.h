@@ -1,0 +1,73 @@
+// Host-side schedule: the split tree of Alg. 2 (Sec. 2.1) turned into a block
+// grid, its wavefronts, the workspace layout and the captured CUDA graphs.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "tsylv_internal.h"
+
+namespace tsylv {
+
+// Partition of one mode into the leaves of the split tree.
+struct Part {
+    int n = 0;
+    int nb = 0;
+    std::vector<int> start, size, blk_of;
+};
+
+// Alg. 2, lines 3-4 applied recursively to one mode: split m at
+// k = floor(m/2), k+1 when A(k+1, k) != 0 (1-based) so that no 2x2 block is
+// cut, until every piece has at most te entries.  sub[i] != 0 marks A(i+1, i).
+Part make_part(int n, const std::vector<uint8_t>& sub, int te);
+
+// Largest number of leaves any admissible block structure can produce.
+int max_blocks(int n, int te);
+
+struct GraphEntry {
+    std::vector<const void*> key;
+    cudaGraphExec_t exec = nullptr;
+};
+
+// One solve schedule: a block grid with its anti-diagonal wavefronts.
+struct Plan {
+    int d = 0, te = 0, td = 0, tc = 0;
+    bool gen = false;
+    int elem = 8;                    // bytes per block-tensor entry
+    long long n[kMaxD] = {};
+    Part part[kMaxD];
+    int nb[kMaxD] = {};
+    long long tstride[kMaxD] = {};
+    long long ntiles = 0;
+    // wavefronts, highest anti-diagonal first
+    std::vector<int> wave_tiles;
+    std::vector<int> wave_off, wave_cnt, wave_csize;
+    double flops = 0;                // executed flops of one solve
+    // device tables (ints): start/size/blk_of per mode, then wave tiles
+    std::vector<int> tab;
+    size_t t_start[kMaxD] = {}, t_size[kMaxD] = {}, t_blk[kMaxD] = {}, t_wave = 0;
+    int* h_tab = nullptr;            // pinned copy of tab (source of the graph's upload)
+    std::vector<GraphEntry> graphs;
+    ~Plan();
+};
+
+// Workspace regions, as byte offsets from the (256-byte aligned) base.
+struct Layout {
+    size_t err = 0, sub = 0, tab = 0;
+    size_t X = 0, P[kMaxD] = {}, G[kMaxD] = {}, At[kMaxD] = {}, Ct[kMaxD] = {};
+    size_t total = 0;
+};
+
+Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem, size_t tab_ints);
+
+std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, int split,
+                               const std::vector<uint8_t>* sub);
+
+GeomArgs geom_of(const Plan& p, const Layout& L, char* base, bool flip);
+
+}  // namespace tsylv

@@ -1,0 +1,24 @@
+// Solver entry points behind the C ABI.
+#pragma once
+
+#include "tsylv_internal.h"
+
+namespace tsylv {
+
+size_t solver_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o, bool transposed);
+int solver_solve(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B, double* X,
+                 void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream,
+                 bool gen, bool transposed);
+int solver_residual(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,
+                    const double* X, double* R, double* rel, void* work, size_t work_bytes, const tsylv_opts* opts,
+                    cudaStream_t stream);
+size_t solver_backward_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o);
+int solver_backward(int d, const int64_t* n, const double* const* A, const double* const* C, const double* X,
+                    const double* dX, double* dB, double* const* dA, double* const* dC, void* work, size_t work_bytes,
+                    const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
+size_t solver_batched_workspace_bytes(int count, const int* d, const int64_t* n_packed, bool gen, const tsylv_opts& o);
+int solver_batched(int count, const int* d, const int64_t* n_packed, const int64_t* off_A, const int64_t* off_X,
+                   const double* A_pool, const double* C_pool, const double* B_pool, double* X_pool, void* work,
+                   size_t work_bytes, const tsylv_opts* opts, int* per_status, tsylv_info* info, cudaStream_t stream);
+
+}  // namespace tsylv

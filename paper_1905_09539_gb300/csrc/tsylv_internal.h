@@ -1,0 +1,86 @@
+// Internal declarations shared by the host schedule code and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tsylv.h"
+
+namespace tsylv {
+
+constexpr int kMaxD = 4;
+constexpr int kThreads = 128;       // threads per CTA of the block kernels
+constexpr int kMaxCluster = 8;      // portable cluster size for split block updates
+
+// Block extent per mode (the leaf size n_min of the split tree) as a function
+// of the order d: the block holds at most 512 unknowns.
+__host__ __device__ constexpr int tile_extent(int d) { return d == 1 ? 32 : d == 2 ? 16 : d == 3 ? 8 : 4; }
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// Device-side error bits (OR-ed into the workspace status word).
+enum : int { kErrSingular = 1, kErrNonfinite = 2, kErrTimeout = 4 };
+
+// Arithmetic used for the block products of a wavefront.
+enum ProductKind : int { kProdNative = 0, kProdTF32 = 1, kProdBF16 = 2 };
+
+// Parameter block of one wavefront launch (passed by value).
+struct WaveArgs {
+    int nb[kMaxD];              // blocks per mode
+    int hi[kMaxD];              // block updates read sources J' < hi[mu]
+    long long tstride[kMaxD];   // linear block-grid stride of each mode
+    const int* bsize[kMaxD];    // extent of every block (<= tile extent)
+    const int* tiles;           // blocks of this wavefront (linear indices)
+    int ntiles;
+    int csize;                  // CTAs per block (cluster size)
+    void* X;                    // block tensor: right-hand side in, solution out
+    void* P[kMaxD];             // generalized form: P_l = X x_{eta>=l} C_eta  (l = 1..d-1)
+    void* G[kMaxD];             //                   G_l = sum_{nu>=l} X x_nu A_nu x_{eta>=l,!=nu} C_eta
+    const void* At[kMaxD];      // upper block triangle of A_mu, TE x TE tiles
+    const void* Ct[kMaxD];      // same for C_mu (generalized form)
+    int* err;                   // status word
+    long long timeout_ns;       // bound of every device-side wait
+};
+
+// Launch one wavefront.  T = double or float; generalized selects the d-term form.
+template <typename T>
+cudaError_t launch_wave(int d, bool generalized, int prod, const WaveArgs& a, cudaStream_t s);
+// Raise the dynamic shared-memory limit of every wavefront kernel (call
+// outside stream capture, once per process and device).
+template <typename T>
+cudaError_t prepare_wave();
+
+// Workspace tables of one block partition (device pointers).
+struct PartDev {
+    const int* start[kMaxD];    // first index of every block
+    const int* size[kMaxD];     // extent of every block
+    const int* blk_of[kMaxD];   // block of every index
+};
+
+struct GeomArgs {
+    int d;
+    long long n[kMaxD];
+    int nb[kMaxD];
+    long long tstride[kMaxD];
+    long long ntiles;
+    PartDev part;
+    int flip;                   // reverse every index (transposed solves)
+};
+
+// Layout conversions between the caller's column-major tensors and the block
+// tensor (all dense tiles of TE^d entries, zero padded).
+template <typename T>
+cudaError_t launch_pack_tensor(const GeomArgs& g, const double* src, T* tiles, double scale, cudaStream_t s);
+template <typename T>
+cudaError_t launch_unpack_tensor(const GeomArgs& g, const T* tiles, double* dst, cudaStream_t s);
+// Coefficient tiles of mode mu: the upper block triangle (I <= J), tile (I, J)
+// at index J (J + 1) / 2 + I.  upper_only: C (drop the subdiagonal).
+template <typename T>
+cudaError_t launch_pack_coef(const GeomArgs& g, int mu, const double* M, T* tiles, bool upper_only,
+                             cudaStream_t s);
+// out[i] = sub-diagonal entries of every A_mu (concatenated, n_mu - 1 each).
+cudaError_t launch_gather_subdiag(int d, const long long* n, const double* const* A, double* out,
+                                  cudaStream_t s);
+
+}  // namespace tsylv

@@ -1,0 +1,172 @@
+"""Parity of the CUDA path with the CPU oracle (element by element).
+
+Sizes span several blocks per mode and ragged tails; 2x2 Schur blocks are
+placed across split points of the recursion.  Tolerance: 1e-11 relative
+(Frobenius and max-entry) for the FP64 solve, as the FP64 path must agree
+with the oracle to that relative error.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from tests.gpu_helpers import max_rel, rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+CASES = [
+    (1, (1,)), (1, (37,)), (1, (100,)),
+    (2, (16, 16)), (2, (33, 17)), (2, (5, 70)),
+    (3, (8, 8, 8)), (3, (9, 8, 7)), (3, (24, 17, 13)), (3, (33, 30, 31)), (3, (1, 20, 9)),
+    (4, (4, 4, 4, 4)), (4, (9, 7, 5, 6)), (4, (13, 11, 10, 9)),
+]
+
+
+def _split_force(shape, te):
+    """2x2 blocks that straddle the first split point of each mode."""
+    out = []
+    for n in shape:
+        if n > te and n >= 4:
+            out.append([n // 2 - 1])
+        else:
+            out.append([])
+    return out
+
+
+def _te(d):
+    return {1: 32, 2: 16, 3: 8, 4: 4}[d]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1905_09539_gb300 as ts
+    ts.load()
+    return ts
+
+
+@pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("d,shape", CASES)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_solve_parity(lib, d, shape, gen, seed):
+    force = _split_force(shape, _te(d)) if seed == 1 else None
+    p = synthetic.problem(seed, shape, generalized=gen, force_blocks=force)
+    Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+    A = [to_dev(a) for a in p["A"]]
+    B = to_dev(p["B"])
+    if gen:
+        C = [to_dev(c) for c in p["C"]]
+        X, st = lib.gtsylv_solve(A, C, B)
+    else:
+        X, st = lib.tsylv_solve(A, B)
+    assert st == 0
+    Xg = to_host(X)
+    assert rel_err(Xg, Xo) <= TOL
+    assert max_rel(Xg, Xo) <= TOL
+
+
+@pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("d,shape", [(2, (19, 23)), (3, (17, 12, 9)), (3, (24, 24, 24)), (4, (7, 9, 5, 6))])
+def test_transposed_parity(lib, d, shape, gen):
+    p = synthetic.problem(5, shape, generalized=gen, force_blocks=_split_force(shape, _te(d)))
+    Lo = oracle.solve_backsub(p["A"], p["B"], p["C"], transpose=True)
+    A = [to_dev(a) for a in p["A"]]
+    G = to_dev(p["B"])
+    if gen:
+        L, st = lib.gtsylv_solve_transposed(A, [to_dev(c) for c in p["C"]], G)
+    else:
+        L, st = lib.tsylv_solve_transposed(A, G)
+    assert st == 0
+    Lg = to_host(L)
+    assert rel_err(Lg, Lo) <= TOL
+    assert max_rel(Lg, Lo) <= TOL
+
+
+def test_all_positions_in_2x2_blocks(lib):
+    shape = (16, 10, 12)
+    force = [list(range(0, n - 1, 2)) for n in shape]
+    for gen in (False, True):
+        p = synthetic.problem(7, shape, generalized=gen, force_blocks=force)
+        Xo = oracle.solve_backsub(p["A"], p["B"], p["C"])
+        A = [to_dev(a) for a in p["A"]]
+        if gen:
+            X, st = lib.gtsylv_solve(A, [to_dev(c) for c in p["C"]], to_dev(p["B"]))
+        else:
+            X, st = lib.tsylv_solve(A, to_dev(p["B"]))
+        assert st == 0
+        assert rel_err(to_host(X), Xo) <= TOL
+
+
+def test_diagonal_closed_form(lib):
+    rng = np.random.default_rng(3)
+    shape = (20, 13, 9)
+    a = [rng.uniform(1, 2, n) for n in shape]
+    A = [np.asfortranarray(np.diag(v)) for v in a]
+    B = np.asfortranarray(rng.standard_normal(shape))
+    Xc = B / sum(np.meshgrid(*a, indexing="ij"))
+    X, st = lib.tsylv_solve([to_dev(m) for m in A], to_dev(B))
+    assert st == 0
+    assert np.max(np.abs(to_host(X) - Xc) / np.abs(Xc)) <= 1e-14
+
+
+def test_in_place(lib):
+    p = synthetic.problem(2, (20, 18, 9))
+    Xo = oracle.solve_recursive(p["A"], p["B"], nmin=4)
+    B = to_dev(p["B"])
+    X, st = lib.tsylv_solve([to_dev(a) for a in p["A"]], B, X=B)
+    assert st == 0 and X.data_ptr() == B.data_ptr()
+    assert rel_err(to_host(B), Xo) <= TOL
+
+
+def test_repeat_calls_replay_graph(lib):
+    p = synthetic.problem(4, (17, 16, 15), generalized=True)
+    Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+    A = [to_dev(a) for a in p["A"]]
+    C = [to_dev(c) for c in p["C"]]
+    B = to_dev(p["B"])
+    X = lib.empty_fortran(B.shape, B.device) if hasattr(lib, "empty_fortran") else None
+    from paper_1905_09539_gb300 import empty_fortran
+    X = empty_fortran(tuple(B.shape), B.device)
+    for _ in range(3):
+        X.zero_()
+        lib.gtsylv_solve(A, C, B, X=X)
+        assert rel_err(to_host(X), Xo) <= TOL
+    X2, _ = lib.gtsylv_solve(A, C, B, use_graph=0)
+    assert rel_err(to_host(X2), Xo) <= TOL
+
+
+@pytest.mark.parametrize("split", [1, 2, 8])
+def test_cluster_split_sizes_agree(lib, split):
+    p = synthetic.problem(6, (40, 33, 24), generalized=True)
+    Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=8)
+    X, st = lib.gtsylv_solve([to_dev(a) for a in p["A"]], [to_dev(c) for c in p["C"]], to_dev(p["B"]), split=split)
+    assert st == 0
+    assert rel_err(to_host(X), Xo) <= TOL
+
+
+def test_singular_reported(lib):
+    # a1_i + a2_j + a3_k = 0 at one position: exactly singular
+    shape = (9, 8, 7)
+    p = synthetic.problem(8, shape)
+    A = [a.copy() for a in p["A"]]
+    A[0][3, 3] = -(A[1][2, 2] + A[2][4, 4])
+    A[0][2, 3] = 0.0 if A[0][3, 2] == 0 else A[0][2, 3]
+    _, st = lib.tsylv_solve([to_dev(a) for a in A], to_dev(p["B"]), check=False)
+    assert st == lib._lib.TSYLV_ESINGULAR
+
+
+def test_nonfinite_reported(lib):
+    p = synthetic.problem(9, (10, 9, 8))
+    B = p["B"].copy()
+    B[5, 4, 3] = np.nan
+    _, st = lib.tsylv_solve([to_dev(a) for a in p["A"]], to_dev(B), check=False)
+    assert st == lib._lib.TSYLV_ENONFINITE
+
+
+def test_bad_structure_rejected(lib):
+    p = synthetic.problem(10, (10, 9, 8))
+    A = [a.copy() for a in p["A"]]
+    A[1][3, 2] = 0.5
+    A[1][4, 3] = 0.5      # two consecutive subdiagonal entries
+    _, st = lib.tsylv_solve([to_dev(a) for a in A], to_dev(p["B"]), check=False)
+    assert st == -3
