@@ -95,6 +95,7 @@ typedef struct tsylv_opts {
     int use_graph;    /* 1 (default): capture each schedule once and replay it      */
     int host_io;      /* 1: B, X, A, C (and backward buffers) are host pointers; the
                          call copies them through `work` inside the call             */
+    int timing;       /* 1: time the phases with CUDA events (fields t_* of info)    */
 } tsylv_opts;
 
 typedef struct tsylv_info {
@@ -105,6 +106,9 @@ typedef struct tsylv_info {
     double resid;         /* final ||B - A(X)|| / (||A|| ||X||) when computed, else -1 */
     double norm_A;        /* the ||A|| used above (sum_mu ||A_mu||_2 prod ||C_eta||_2) */
     double flops;         /* floating-point operations executed per solve           */
+    double t_total_ms;    /* opts->timing: device time of the whole call             */
+    double t_waves_ms;    /* opts->timing: device time of the wavefront launches     */
+    double t_resid_ms;    /* opts->timing: device time of the residual launches      */
 } tsylv_info;
 
 /* Fill *opts with the defaults listed above. */
@@ -112,6 +116,11 @@ void tsylv_opts_default(tsylv_opts* opts);
 
 /* Human-readable text of a status code (static storage). */
 const char* tsylv_status_string(int status);
+
+/* Text of the last CUDA runtime failure seen by a call of this thread
+ * (TSYLV_ECUDA), naming the failing step; "" if none.  Valid until the next
+ * call on the same thread. */
+const char* tsylv_last_error(void);
 
 /* Workspace bytes for tsylv_solve (generalized = 0) / gtsylv_solve
  * (generalized = 1) and their transposed variants.  Returns 0 for invalid

@@ -28,7 +28,10 @@ __all__ = ["tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solv
 class TsylvError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        super().__init__("%s: status %d (%s)" % (where, status, status_string(status)))
+        msg = "%s: status %d (%s)" % (where, status, status_string(status))
+        if status == _lib.TSYLV_ECUDA:
+            msg += ": " + _lib.last_error()
+        super().__init__(msg)
 
 
 def is_fortran(t):

@@ -25,13 +25,14 @@ TSYLV_RESID_FP64 = 1
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double),
                 ("residual", ctypes.c_int), ("nmin", ctypes.c_int), ("split", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("host_io", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("waves", ctypes.c_int), ("launches", ctypes.c_int),
                 ("tiles", ctypes.c_int), ("resid", ctypes.c_double), ("norm_A", ctypes.c_double),
-                ("flops", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("t_total_ms", ctypes.c_double), ("t_waves_ms", ctypes.c_double),
+                ("t_resid_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -40,7 +41,7 @@ class Info(ctypes.Structure):
 EXPORTS = [
     "tsylv_opts_default", "tsylv_status_string", "tsylv_workspace_bytes", "tsylv_solve", "gtsylv_solve",
     "tsylv_solve_transposed", "gtsylv_solve_transposed", "tsylv_residual", "tsylv_backward_workspace_bytes",
-    "tsylv_backward", "tsylv_batched_workspace_bytes", "tsylv_solve_batched",
+    "tsylv_backward", "tsylv_batched_workspace_bytes", "tsylv_solve_batched", "tsylv_last_error",
 ]
 
 _lib = None
@@ -65,6 +66,8 @@ def load(path=LIB_PATH):
     lib.tsylv_opts_default.restype = None
     lib.tsylv_status_string.argtypes = [I]
     lib.tsylv_status_string.restype = ctypes.c_char_p
+    lib.tsylv_last_error.argtypes = []
+    lib.tsylv_last_error.restype = ctypes.c_char_p
     lib.tsylv_workspace_bytes.argtypes = [I, I64P, I, OP]
     lib.tsylv_workspace_bytes.restype = S
     lib.tsylv_solve.argtypes = [I, I64P, P, P, P, P, S, OP, IP, P]
@@ -98,3 +101,7 @@ def default_opts(**kw):
 
 def status_string(s):
     return load().tsylv_status_string(int(s)).decode()
+
+
+def last_error():
+    return load().tsylv_last_error().decode()

@@ -1,6 +1,7 @@
 // C ABI entry points (include/tsylv.h): argument checks, structure read-back,
 // schedule lookup, CUDA-graph capture/replay and status read-back.
 #include <cstring>
+#include <string>
 #include <mutex>
 #include <vector>
 
@@ -8,6 +9,23 @@
 #include "solver.h"
 
 using namespace tsylv;
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+namespace tsylv {
+int cuda_fail(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return TSYLV_ECUDA;
+}
+int cuda_fail_msg(const char* where) {
+    g_last_error = where;
+    return TSYLV_ECUDA;
+}
+}  // namespace tsylv
+
+extern "C" const char* tsylv_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" void tsylv_opts_default(tsylv_opts* o) {
     if (!o) return;

@@ -58,6 +58,8 @@ Plan::~Plan() {
     for (auto& g : graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (h_tab) cudaFreeHost(h_tab);
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
 }
 
 Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem, size_t tab_ints) {

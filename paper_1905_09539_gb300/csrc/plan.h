@@ -53,6 +53,7 @@ struct Plan {
     size_t t_start[kMaxD] = {}, t_size[kMaxD] = {}, t_blk[kMaxD] = {}, t_wave = 0;
     int* h_tab = nullptr;            // pinned copy of tab (source of the graph's upload)
     std::vector<GraphEntry> graphs;
+    cudaEvent_t ev[4] = {};          // opts->timing: call start, waves begin/end, call end
     ~Plan();
 };
 

@@ -47,6 +47,7 @@ bool shape_ok(int d, const int64_t* n) {
 }
 
 int map_err(int e) {
+    if (e & kErrBounds) return cuda_fail_msg("device self-check: index outside a block array");
     if (e & kErrTimeout) return TSYLV_ETIMEOUT;
     if (e & kErrSingular) return TSYLV_ESINGULAR;
     if (e & kErrNonfinite) return TSYLV_ENONFINITE;
@@ -91,7 +92,13 @@ struct Call {
     char* base = nullptr;
     std::shared_ptr<Plan> plan;
     Layout L;
+    bool timing = false;
 };
+
+inline cudaError_t mark(const Call& c, int i, cudaStream_t s) {
+    // External: inside stream capture this becomes an event-record node of the graph
+    return c.timing ? cudaEventRecordWithFlags(c.plan->ev[i], s, cudaEventRecordExternal) : cudaSuccess;
+}
 
 // Queue one FP64 solve of the planned block grid.
 cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
@@ -100,6 +107,7 @@ cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
     char* base = c.base;
     GeomArgs g = geom_of(p, L, base, c.flip);
     cudaError_t e;
+    if ((e = mark(c, 0, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(base + L.err, 0, 64, s)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(base + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s)) !=
         cudaSuccess)
@@ -130,18 +138,25 @@ cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
     wa.X = Xt;
     wa.err = reinterpret_cast<int*>(base + L.err);
     wa.timeout_ns = kTimeoutNs;
+    if ((e = mark(c, 1, s)) != cudaSuccess) return e;
     for (size_t w = 0; w < p.wave_off.size(); w++) {
         wa.tiles = tab + p.t_wave + p.wave_off[w];
         wa.ntiles = p.wave_cnt[w];
         wa.csize = p.wave_csize[w];
         if ((e = launch_wave<double>(p.d, p.gen, kProdNative, wa, s)) != cudaSuccess) return e;
     }
-    return launch_unpack_tensor<double>(g, Xt, c.X, s);
+    if ((e = mark(c, 2, s)) != cudaSuccess) return e;
+    if ((e = launch_unpack_tensor<double>(g, Xt, c.X, s)) != cudaSuccess) return e;
+    return mark(c, 3, s);
 }
 
 int run_enqueue(Plan& p, const std::vector<const void*>& key, bool use_graph, cudaStream_t stream,
                 cudaError_t (*fn)(const Call&, cudaStream_t), const Call& c) {
-    if (!use_graph) return fn(c, stream) == cudaSuccess ? 0 : TSYLV_ECUDA;
+    cudaError_t e;
+    if (!use_graph) {
+        if ((e = fn(c, stream)) != cudaSuccess) return cuda_fail(e, "enqueue");
+        return 0;
+    }
     static std::mutex gm;
     cudaGraphExec_t exec = nullptr;
     {
@@ -150,18 +165,19 @@ int run_enqueue(Plan& p, const std::vector<const void*>& key, bool use_graph, cu
             if (ge.key == key) exec = ge.exec;
         if (!exec) {
             cudaStream_t cs = capture_stream();
-            if (!cs) return TSYLV_ECUDA;
-            if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return TSYLV_ECUDA;
-            cudaError_t e = fn(c, cs);
+            if (!cs) return cuda_fail_msg("capture stream");
+            if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamBeginCapture");
+            e = fn(c, cs);
             cudaGraph_t graph = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
             if (e != cudaSuccess || e2 != cudaSuccess || !graph) {
                 if (graph) cudaGraphDestroy(graph);
-                return TSYLV_ECUDA;
+                return cuda_fail(e != cudaSuccess ? e : e2, e != cudaSuccess ? "capture: enqueue" : "cudaStreamEndCapture");
             }
             e = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
-            if (e != cudaSuccess) return TSYLV_ECUDA;
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
             if (p.graphs.size() >= 16) {
                 cudaGraphExecDestroy(p.graphs.front().exec);
                 p.graphs.erase(p.graphs.begin());
@@ -169,7 +185,8 @@ int run_enqueue(Plan& p, const std::vector<const void*>& key, bool use_graph, cu
             p.graphs.push_back(GraphEntry{key, exec});
         }
     }
-    return cudaGraphLaunch(exec, stream) == cudaSuccess ? 0 : TSYLV_ECUDA;
+    if ((e = cudaGraphLaunch(exec, stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return 0;
 }
 
 }  // namespace
@@ -213,6 +230,8 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     c.X = X;
     c.base = static_cast<char*>(work);
 
+    (void)cudaGetLastError();  // launch checks below must not see errors of earlier, unrelated calls
+
     // 2x2 block structure: sub-diagonal of every A_mu, read back once per call
     size_t nsub = 0;
     for (int mu = 0; mu < d; mu++) nsub += static_cast<size_t>(n[mu] - 1);
@@ -221,12 +240,15 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
         const size_t sub_off = 256;  // Layout::sub does not depend on the block counts
         double* dsub = reinterpret_cast<double*>(c.base + sub_off);
         if (nsub > 0) {
-            if (launch_gather_subdiag(d, c.n, c.A, dsub, stream) != cudaSuccess) return TSYLV_ECUDA;
-            if (cudaMemcpyAsync(hsub.data(), dsub, nsub * sizeof(double), cudaMemcpyDeviceToHost, stream) !=
+            cudaError_t e;
+            if ((e = launch_gather_subdiag(d, c.n, c.A, dsub, stream)) != cudaSuccess)
+                return cuda_fail(e, "gather sub-diagonal");
+            if ((e = cudaMemcpyAsync(hsub.data(), dsub, nsub * sizeof(double), cudaMemcpyDeviceToHost, stream)) !=
                 cudaSuccess)
-                return TSYLV_ECUDA;
+                return cuda_fail(e, "read sub-diagonal");
         }
-        if (cudaStreamSynchronize(stream) != cudaSuccess) return TSYLV_ECUDA;
+        cudaError_t e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e, "synchronize before planning");
     }
     std::vector<uint8_t> sub(nsub + 1, 0);
     {
@@ -243,9 +265,13 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
         }
     }
     c.plan = get_plan(d, c.n, c.gen, 8, o.split, &sub);
-    if (!c.plan) return TSYLV_ECUDA;
+    if (!c.plan) return cuda_fail_msg("plan: pinned host allocation");
     c.L = make_layout(d, c.n, c.plan->nb, c.gen, 8, c.plan->tab.size());
     if (c.L.total > work_bytes) return -(7 + sh);
+    c.timing = o.timing != 0;
+    if (c.timing && !c.plan->ev[0])
+        for (auto& ev : c.plan->ev)
+            if (cudaError_t e = cudaEventCreate(&ev); e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
 
     {
         static std::mutex pm;
@@ -254,7 +280,9 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
         cudaGetDevice(&dev);
         std::lock_guard<std::mutex> lk(pm);
         if (dev >= 0 && dev < 64 && !prepared[dev]) {
-            if (prepare_wave<double>() != cudaSuccess || prepare_wave<float>() != cudaSuccess) return TSYLV_ECUDA;
+            cudaError_t e = prepare_wave<double>();
+            if (e == cudaSuccess) e = prepare_wave<float>();
+            if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
             prepared[dev] = true;
         }
     }
@@ -266,13 +294,14 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     key.push_back(B);
     key.push_back(X);
     key.push_back(work);
-    key.push_back(reinterpret_cast<const void*>(static_cast<uintptr_t>(transposed ? 1 : 0)));
+    key.push_back(reinterpret_cast<const void*>(static_cast<uintptr_t>((transposed ? 1 : 0) | (c.timing ? 2 : 0))));
     int st = run_enqueue(*c.plan, key, o.use_graph != 0, stream, enqueue_fp64, c);
     if (st) return st;
     int herr = 0;
-    if (cudaMemcpyAsync(&herr, c.base + c.L.err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
-        return TSYLV_ECUDA;
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return TSYLV_ECUDA;
+    if (cudaError_t e = cudaMemcpyAsync(&herr, c.base + c.L.err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+        e != cudaSuccess)
+        return cuda_fail(e, "read status");
+    if (cudaError_t e = cudaStreamSynchronize(stream); e != cudaSuccess) return cuda_fail(e, "synchronize after solve");
     if (info) {
         std::memset(info, 0, sizeof(*info));
         info->iterations = 0;
@@ -282,6 +311,14 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
         info->resid = -1;
         info->norm_A = -1;
         info->flops = c.plan->flops;
+        if (c.timing) {
+            float a = -1, b = -1;
+            if (cudaEventElapsedTime(&a, c.plan->ev[0], c.plan->ev[3]) != cudaSuccess) a = -1;
+            if (cudaEventElapsedTime(&b, c.plan->ev[1], c.plan->ev[2]) != cudaSuccess) b = -1;
+            (void)cudaGetLastError();
+            info->t_total_ms = a;
+            info->t_waves_ms = b;
+        }
     }
     return map_err(herr);
 }

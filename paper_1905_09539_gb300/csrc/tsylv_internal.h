@@ -17,10 +17,19 @@ constexpr int kMaxCluster = 8;      // portable cluster size for split block upd
 // Block extent per mode (the leaf size n_min of the split tree) as a function
 // of the order d: the block holds at most 512 unknowns.
 __host__ __device__ constexpr int tile_extent(int d) { return d == 1 ? 32 : d == 2 ? 16 : d == 3 ? 8 : 4; }
-__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+__host__ __device__ constexpr int ipow(int b, int e) {
+    int r = 1;
+    for (int i = 0; i < e; i++) r *= b;
+    return r;
+}
+
+// Record a CUDA failure for tsylv_last_error(); returns TSYLV_ECUDA.
+int cuda_fail(cudaError_t e, const char* where);
+// Same for a failure with no CUDA error code of its own.
+int cuda_fail_msg(const char* where);
 
 // Device-side error bits (OR-ed into the workspace status word).
-enum : int { kErrSingular = 1, kErrNonfinite = 2, kErrTimeout = 4 };
+enum : int { kErrSingular = 1, kErrNonfinite = 2, kErrTimeout = 4, kErrBounds = 8 };
 
 // Arithmetic used for the block products of a wavefront.
 enum ProductKind : int { kProdNative = 0, kProdTF32 = 1, kProdBF16 = 2 };

@@ -30,18 +30,27 @@ struct WaveCfg {
     static constexpr int NACC = GEN ? 2 * (D - 1) + 1 : 1;
     static constexpr int NL = GEN ? D - 1 : 0;  // stored levels l = 1..d-1
     static constexpr int STAGE = 2 * TD + 2 * TC;
+    // the staging ring of the block updates and the base case's running
+    // line sums share one region
+    static constexpr int MINV = 1024;  // budget (entries) for precomputed coupled-group inverses
+    static constexpr int UNION = (2 * STAGE > NACC * TD + MINV) ? 2 * STAGE : NACC * TD + MINV;
     static constexpr int oStage = 0;
-    static constexpr int oRed = 2 * STAGE;
+    static constexpr int oLin = 0;
+    static constexpr int oMinv = NACC * TD;
+    static constexpr int oRed = UNION;
     static constexpr int oR = oRed + NACC * TD;
     static constexpr int oX = oR + TD;
-    static constexpr int oPin = oX + TD;
+    static constexpr int oRd = oX + TD;
+    static constexpr int oPin = oRd + TD;
     static constexpr int oGin = oPin + NL * TD;
     static constexpr int oD = oGin + NL * TD;
     static constexpr int oE = oD + D * TC;
     static constexpr int oEnd = oE + (GEN ? D * TC : 0);
     static constexpr size_t oBar = ((oEnd * sizeof(T)) + 15) / 16 * 16;
     static constexpr size_t oMeta = oBar + 16;
-    static constexpr size_t smem = oMeta + (2 * D * TE + 3 * D + 4) * sizeof(int);
+    // meta: gs, gl, gidx [D][TE]; ng, bs [D]; flag [4]; coupled-group lists
+    static constexpr int MAXSTEP = D * TE;
+    static constexpr size_t smem = oMeta + (3 * D * TE + 3 * D + 4 + 3 * MAXSTEP + 1 + 2 * (TD / 2 + 1)) * sizeof(int);
     static constexpr int slotP(int l) { return 2 * (D - 1 - l); }
     static constexpr int slotG(int l) { return 2 * (D - 1 - l) + 1; }
 };
@@ -132,296 +141,461 @@ __device__ __forceinline__ void dispatch_job(int level, T (&acc)[WaveCfg<T, D, G
     }
 }
 
-// Dense Gaussian elimination with partial pivoting for one coupled group
-// (s <= 2^d unknowns).  Returns false for a pivot below 16 eps max|M|.
-template <typename T, int SMAX>
-__device__ bool group_gepp(int s, T* M, T* r) {
-    T big = 0;
-    for (int i = 0; i < s * s; i++) big = fmax(big, fabs(M[i]));
-    const T tiny = T(16) * dev::Eps<T>::v * big;
-    for (int c = 0; c < s; c++) {
-        int p = c;
-        T best = fabs(M[c * SMAX + c]);
-        for (int q = c + 1; q < s; q++) {
-            T v = fabs(M[q * SMAX + c]);
-            if (v > best) { best = v; p = q; }
-        }
-        if (!(best > tiny)) return false;
-        if (p != c) {
-            for (int k = 0; k < s; k++) { T t = M[c * SMAX + k]; M[c * SMAX + k] = M[p * SMAX + k]; M[p * SMAX + k] = t; }
-            T t = r[c]; r[c] = r[p]; r[p] = t;
-        }
-        for (int q = c + 1; q < s; q++) {
-            T f = M[q * SMAX + c] / M[c * SMAX + c];
-            for (int k = c; k < s; k++) M[q * SMAX + k] -= f * M[c * SMAX + k];
-            r[q] -= f * r[c];
-        }
-    }
-    for (int c = s - 1; c >= 0; c--) {
-        T v = r[c];
-        for (int k = c + 1; k < s; k++) v -= M[c * SMAX + k] * r[k];
-        r[c] = v / M[c * SMAX + c];
-    }
-    return true;
-}
-
 template <typename T, int D, bool GEN>
 struct TileSmem {
     const T* Ds;   // [D][TC] diagonal tiles of A
     const T* Es;   // [D][TC] diagonal tiles of C (generalized)
     const T* Rs;   // right-hand side of the diagonal-block equation
+    const T* Rd;   // reciprocal of the diagonal entry of every 1x1 group
     T* Xs;         // solution (0 where not yet solved)
     T* Pin;        // [NL][TD] in-block intermediates (generalized)
     T* Gin;
+    T* Lin;        // [NACC][TD] running line sums from solved groups
     const int* gs; // [D][TE] group start
     const int* gl; // [D][TE] group length (1 or 2)
     const int* ng; // [D] groups per mode
     const int* bs; // [D] block extent
+    const int* gidx; // [D][TE] group of every in-block index
 };
 
-// Solve one coupled group g of the diagonal-block equation (element-level
-// version of the block recurrence: partial sums beyond the group along each
-// mode, the group system, then completion of the in-block intermediates).
+// One unknown whose group is 1x1 in every mode: all contributions of solved
+// groups are already in the running line sums Lin, so the solve is the
+// Horner chain over the diagonal entries (generalized form) and one product
+// with the reciprocal diagonal.
 template <typename T, int D, bool GEN>
-__device__ int solve_group(const TileSmem<T, D, GEN>& sm, const int (&g)[D]) {
+__device__ __forceinline__ int solve_single(const TileSmem<T, D, GEN>& sm, int o, const int (&u)[D],
+                                            const T (&L)[WaveCfg<T, D, GEN>::NACC]) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int TC = TE * TE;
-    constexpr int SMAX = 1 << D;
-    int a[D], s[D], smem_st[D], st[D];
-    int S = 1, o = 0;
+    using C = WaveCfg<T, D, GEN>;
+    T x;
+    if constexpr (!GEN) {
+        x = (sm.Rs[o] - L[0]) * sm.Rd[o];
+    } else {
+        T p0 = L[C::slotP(D - 1)];
+        T g0 = L[C::slotG(D - 1)];
+        T P0s[D], G0s[D];
+        P0s[D - 1] = p0;
+        G0s[D - 1] = g0;
+#pragma unroll
+        for (int l = D - 2; l >= 1; l--) {
+            const T ep = sm.Es[l * TC + u[l] * (TE + 1)], dp = sm.Ds[l * TC + u[l] * (TE + 1)];
+            const T np = ep * p0 + L[C::slotP(l)];
+            const T ng_ = ep * g0 + dp * p0 + L[C::slotG(l)];
+            p0 = np;
+            g0 = ng_;
+            P0s[l] = p0;
+            G0s[l] = g0;
+        }
+        const T off = sm.Es[u[0] * (TE + 1)] * g0 + sm.Ds[u[0] * (TE + 1)] * p0 + L[C::NACC - 1];
+        x = (sm.Rs[o] - off) * sm.Rd[o];
+        T pc = sm.Es[(D - 1) * TC + u[D - 1] * (TE + 1)] * x;
+        T gc = sm.Ds[(D - 1) * TC + u[D - 1] * (TE + 1)] * x;
+        sm.Pin[(D - 2) * TD + o] = P0s[D - 1] + pc;
+        sm.Gin[(D - 2) * TD + o] = G0s[D - 1] + gc;
+#pragma unroll
+        for (int l = D - 2; l >= 1; l--) {
+            const T ep = sm.Es[l * TC + u[l] * (TE + 1)], dp = sm.Ds[l * TC + u[l] * (TE + 1)];
+            gc = ep * gc + dp * pc;
+            pc = ep * pc;
+            sm.Pin[(l - 1) * TD + o] = P0s[l] + pc;
+            sm.Gin[(l - 1) * TD + o] = G0s[l] + gc;
+        }
+    }
+    sm.Xs[o] = x;
+    return isfinite(x) ? 0 : kErrNonfinite;
+}
+
+// Coupled group solved by one warp: lane m (< S) holds the equation row of
+// member m.  Members are ordered with the 2x2 modes of `mask` as binary
+// digits (member offset delta_mu(m) in {0, 1}).  Gaussian elimination with
+// partial pivoting runs across the lanes with warp shuffles; everything from
+// outside the group is already in the running line sums Lin.
+__device__ __forceinline__ int member_delta(int mask, int m, int mu) {
+    return ((mask >> mu) & 1) ? ((m >> __popc(mask & ((1 << mu) - 1))) & 1) : 0;
+}
+__device__ __forceinline__ int member_with(int mask, int m, int mu, int k) {
+    if (!((mask >> mu) & 1)) return m;
+    const int b = __popc(mask & ((1 << mu) - 1));
+    return (m & ~(1 << b)) | (k << b);
+}
+
+template <typename T, int D, bool GEN, int S>
+__device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D], int mask, const T* minv) {
+    constexpr int TE = tile_extent(D);
+    constexpr int TD = ipow(TE, D);
+    constexpr int TC = TE * TE;
+    using C = WaveCfg<T, D, GEN>;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < S;
+    const int m = act ? lane : 0;
+    int u[D], o = 0;
 #pragma unroll
     for (int mu = 0; mu < D; mu++) {
-        a[mu] = sm.gs[mu * TE + g[mu]];
-        s[mu] = sm.gl[mu * TE + g[mu]];
-        smem_st[mu] = S;
-        S *= s[mu];
-        st[mu] = ipow(TE, mu);
-        o += a[mu] * st[mu];
+        u[mu] = a[mu] + member_delta(mask, m, mu);
+        o += u[mu] * ipow(TE, mu);
     }
     auto Dm = [&](int mu, int i, int k) -> T { return sm.Ds[mu * TC + i + TE * k]; };
     auto Em = [&](int mu, int i, int k) -> T { return sm.Es[mu * TC + i + TE * k]; };
-    int status = 0;
-    if (S == 1) {
-        // ------------------------------------------------ single unknown
-        T x;
-        T mag = 0;
-        T diag = 0;
-        if constexpr (!GEN) {
-            T r = sm.Rs[o];
+    T r;
+    T row[S];
+    T P0[D], G0[D];
+    if constexpr (!GEN) {
+        r = sm.Rs[o] - sm.Lin[o];
+#pragma unroll
+        for (int k = 0; k < S; k++) {
+            T e = 0;
 #pragma unroll
             for (int mu = 0; mu < D; mu++) {
-                const T dd = Dm(mu, a[mu], a[mu]);
-                diag += dd;
-                mag += fabs(dd);
-                for (int k = a[mu] + 1; k < sm.bs[mu]; k++) r -= Dm(mu, a[mu], k) * sm.Xs[o + (k - a[mu]) * st[mu]];
-            }
-            x = r / diag;
-        } else {
-            T p0[D], g0[D];
-            {
-                constexpr int mu = D - 1;
-                T p = 0, q = 0;
-                for (int k = a[mu] + 1; k < sm.bs[mu]; k++) {
-                    const T xv = sm.Xs[o + (k - a[mu]) * st[mu]];
-                    p += Em(mu, a[mu], k) * xv;
-                    q += Dm(mu, a[mu], k) * xv;
-                }
-                p0[mu] = p;
-                g0[mu] = q;
-            }
-#pragma unroll
-            for (int l = D - 2; l >= 1; l--) {
-                const T ep = Em(l, a[l], a[l]), dp = Dm(l, a[l], a[l]);
-                T p = ep * p0[l + 1];
-                T q = ep * g0[l + 1] + dp * p0[l + 1];
-                const T* Pn = sm.Pin + (l + 1 - 1) * TD;
-                const T* Gn = sm.Gin + (l + 1 - 1) * TD;
-                for (int k = a[l] + 1; k < sm.bs[l]; k++) {
-                    const int oo = o + (k - a[l]) * st[l];
-                    p += Em(l, a[l], k) * Pn[oo];
-                    q += Em(l, a[l], k) * Gn[oo] + Dm(l, a[l], k) * Pn[oo];
-                }
-                p0[l] = p;
-                g0[l] = q;
-            }
-            T off = Em(0, a[0], a[0]) * g0[1] + Dm(0, a[0], a[0]) * p0[1];
-            {
-                const T* Pn = sm.Pin;
-                const T* Gn = sm.Gin;
-                for (int k = a[0] + 1; k < sm.bs[0]; k++) {
-                    const int oo = o + (k - a[0]);
-                    off += Em(0, a[0], k) * Gn[oo] + Dm(0, a[0], k) * Pn[oo];
-                }
-            }
-#pragma unroll
-            for (int mu = 0; mu < D; mu++) {
-                T t = Dm(mu, a[mu], a[mu]);
+                bool same = true;
 #pragma unroll
                 for (int eta = 0; eta < D; eta++)
-                    if (eta != mu) t *= Em(eta, a[eta], a[eta]);
-                diag += t;
-                mag += fabs(t);
+                    if (eta != mu && member_delta(mask, m, eta) != member_delta(mask, k, eta)) same = false;
+                if (same) e += Dm(mu, u[mu], a[mu] + member_delta(mask, k, mu));
             }
-            x = (sm.Rs[o] - off) / diag;
-            // completion of the in-block intermediates at this position
-            T pc = Em(D - 1, a[D - 1], a[D - 1]) * x;
-            T gc = Dm(D - 1, a[D - 1], a[D - 1]) * x;
-            sm.Pin[(D - 2) * TD + o] = p0[D - 1] + pc;
-            sm.Gin[(D - 2) * TD + o] = g0[D - 1] + gc;
-#pragma unroll
-            for (int l = D - 2; l >= 1; l--) {
-                const T ep = Em(l, a[l], a[l]), dp = Dm(l, a[l], a[l]);
-                gc = ep * gc + dp * pc;
-                pc = ep * pc;
-                sm.Pin[(l - 1) * TD + o] = p0[l] + pc;
-                sm.Gin[(l - 1) * TD + o] = g0[l] + gc;
-            }
-        }
-        if (!(fabs(diag) > T(16) * dev::Eps<T>::v * mag)) status |= kErrSingular;
-        if (!isfinite(x)) status |= kErrNonfinite;
-        sm.Xs[o] = x;
-        return status;
-    }
-    // ---------------------------------------------------- coupled group
-    int om[SMAX];
-    int um[SMAX][D];
-    for (int m = 0; m < S; m++) {
-        int oo = 0;
-#pragma unroll
-        for (int mu = 0; mu < D; mu++) {
-            um[m][mu] = a[mu] + (m / smem_st[mu]) % s[mu];
-            oo += um[m][mu] * st[mu];
-        }
-        om[m] = oo;
-    }
-    T r[SMAX];
-    T M[SMAX * SMAX];
-    T P0[D][SMAX], G0[D][SMAX];
-    if constexpr (!GEN) {
-        for (int m = 0; m < S; m++) {
-            T v = sm.Rs[om[m]];
-#pragma unroll
-            for (int mu = 0; mu < D; mu++) {
-                const int u = um[m][mu];
-                for (int k = a[mu] + s[mu]; k < sm.bs[mu]; k++) v -= Dm(mu, u, k) * sm.Xs[om[m] + (k - u) * st[mu]];
-            }
-            r[m] = v;
-            for (int m2 = 0; m2 < S; m2++) {
-                T e = 0;
-#pragma unroll
-                for (int mu = 0; mu < D; mu++) {
-                    bool same = true;
-#pragma unroll
-                    for (int eta = 0; eta < D; eta++)
-                        if (eta != mu && um[m][eta] != um[m2][eta]) same = false;
-                    if (same) e += Dm(mu, um[m][mu], um[m2][mu]);
-                }
-                M[m * SMAX + m2] = e;
-            }
+            row[k] = e;
         }
     } else {
-        for (int m = 0; m < S; m++) {
-            constexpr int mu = D - 1;
-            const int u = um[m][mu];
-            T p = 0, q = 0;
-            for (int k = a[mu] + s[mu]; k < sm.bs[mu]; k++) {
-                const T xv = sm.Xs[om[m] + (k - u) * st[mu]];
-                p += Em(mu, u, k) * xv;
-                q += Dm(mu, u, k) * xv;
-            }
-            P0[mu][m] = p;
-            G0[mu][m] = q;
-        }
+        P0[D - 1] = sm.Lin[C::slotP(D - 1) * TD + o];
+        G0[D - 1] = sm.Lin[C::slotG(D - 1) * TD + o];
 #pragma unroll
         for (int l = D - 2; l >= 1; l--) {
-            const T* Pn = sm.Pin + l * TD;  // level l + 1
-            const T* Gn = sm.Gin + l * TD;
-            for (int m = 0; m < S; m++) {
-                const int u = um[m][l];
-                T p = 0, q = 0;
-                for (int k = a[l]; k < a[l] + s[l]; k++) {
-                    const int m2 = m + (k - u) * smem_st[l];
-                    p += Em(l, u, k) * P0[l + 1][m2];
-                    q += Em(l, u, k) * G0[l + 1][m2] + Dm(l, u, k) * P0[l + 1][m2];
+            T p = sm.Lin[C::slotP(l) * TD + o], q = sm.Lin[C::slotG(l) * TD + o];
+            const bool two = (mask >> l) & 1;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int src = member_with(mask, m, l, k);
+                const T pp = __shfl_sync(full, P0[l + 1], src);
+                const T gg = __shfl_sync(full, G0[l + 1], src);
+                if (k == 0 || two) {
+                    const int kk = two ? a[l] + k : u[l];
+                    p += Em(l, u[l], kk) * pp;
+                    q += Em(l, u[l], kk) * gg + Dm(l, u[l], kk) * pp;
                 }
-                for (int k = a[l] + s[l]; k < sm.bs[l]; k++) {
-                    const int oo = om[m] + (k - u) * st[l];
-                    p += Em(l, u, k) * Pn[oo];
-                    q += Em(l, u, k) * Gn[oo] + Dm(l, u, k) * Pn[oo];
+            }
+            P0[l] = p;
+            G0[l] = q;
+        }
+        T of = sm.Lin[(C::NACC - 1) * TD + o];
+        {
+            const bool two = mask & 1;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int src = member_with(mask, m, 0, k);
+                const T pp = __shfl_sync(full, P0[1], src);
+                const T gg = __shfl_sync(full, G0[1], src);
+                if (k == 0 || two) {
+                    const int kk = two ? a[0] + k : u[0];
+                    of += Em(0, u[0], kk) * gg + Dm(0, u[0], kk) * pp;
                 }
-                P0[l][m] = p;
-                G0[l][m] = q;
             }
         }
-        for (int m = 0; m < S; m++) {
-            const int u = um[m][0];
-            T off = 0;
-            for (int k = a[0]; k < a[0] + s[0]; k++) {
-                const int m2 = m + (k - u) * smem_st[0];
-                off += Em(0, u, k) * G0[1][m2] + Dm(0, u, k) * P0[1][m2];
-            }
-            for (int k = a[0] + s[0]; k < sm.bs[0]; k++) {
-                const int oo = om[m] + (k - u);
-                off += Em(0, u, k) * sm.Gin[oo] + Dm(0, u, k) * sm.Pin[oo];
-            }
-            r[m] = sm.Rs[om[m]] - off;
-            for (int m2 = 0; m2 < S; m2++) {
-                T e = 0;
+        r = sm.Rs[o] - of;
 #pragma unroll
-                for (int mu = 0; mu < D; mu++) {
-                    T t = Dm(mu, um[m][mu], um[m2][mu]);
+        for (int k = 0; k < S; k++) {
+            T e = 0;
 #pragma unroll
-                    for (int eta = 0; eta < D; eta++)
-                        if (eta != mu) t *= Em(eta, um[m][eta], um[m2][eta]);
-                    e += t;
-                }
-                M[m * SMAX + m2] = e;
+            for (int mu = 0; mu < D; mu++) {
+                const int v = a[mu] + member_delta(mask, k, mu);
+                T t = Dm(mu, u[mu], v);
+#pragma unroll
+                for (int eta = 0; eta < D; eta++)
+                    if (eta != mu) t *= Em(eta, u[eta], a[eta] + member_delta(mask, k, eta));
+                e += t;
             }
+            row[k] = e;
         }
     }
-    if (!group_gepp<T, SMAX>(S, M, r)) status |= kErrSingular;
-    for (int m = 0; m < S; m++) {
-        if (!isfinite(r[m])) status |= kErrNonfinite;
-        sm.Xs[om[m]] = r[m];
+    if (!act) {
+        r = 0;
+#pragma unroll
+        for (int k = 0; k < S; k++) row[k] = 0;
+    }
+    int status = 0;
+    T x = 0;
+    if (minv != nullptr) {
+        // precomputed inverse: x_m = sum_k Minv(m, k) r_k
+#pragma unroll
+        for (int k = 0; k < S; k++) {
+            const T rk = __shfl_sync(full, r, k);
+            if (act) x += minv[m * S + k] * rk;
+        }
+    } else {
+    // scale for the pivot test: 16 eps max |M|
+    T big = 0;
+#pragma unroll
+    for (int k = 0; k < S; k++) big = fmax(big, fabs(row[k]));
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) big = fmax(big, __shfl_xor_sync(full, big, w));
+    const T tiny = T(16) * dev::Eps<T>::v * big;
+    // forward elimination
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+        T val = (lane >= c && act) ? fabs(row[c]) : T(-1);
+        int idx = lane;
+#pragma unroll
+        for (int w = 16; w >= 1; w >>= 1) {
+            const T ov = __shfl_xor_sync(full, val, w);
+            const int oi = __shfl_xor_sync(full, idx, w);
+            if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+        }
+        const int pv = idx;  // identical on every lane
+        if (pv != c) {
+            const int src = lane == c ? pv : (lane == pv ? c : lane);
+#pragma unroll
+            for (int k = 0; k < S; k++) row[k] = __shfl_sync(full, row[k], src);
+            r = __shfl_sync(full, r, src);
+        }
+        T prow[S];
+#pragma unroll
+        for (int k = 0; k < S; k++) prow[k] = __shfl_sync(full, row[k], c);
+        const T pr = __shfl_sync(full, r, c);
+        if (!(fabs(prow[c]) > tiny)) status |= kErrSingular;
+        if (act && lane > c) {
+            const T f = row[c] / prow[c];
+#pragma unroll
+            for (int k = c + 1; k < S; k++) row[k] -= f * prow[k];
+            r -= f * pr;
+        }
+    }
+    // back substitution; lane m ends with x_m
+#pragma unroll
+    for (int c = S - 1; c >= 0; c--) {
+        const T xc_local = r / row[c];
+        const T xc = __shfl_sync(full, xc_local, c);
+        if (lane == c) x = xc;
+        if (act && lane < c) r -= row[c] * xc;
+    }
+    }
+    if (act) {
+        if (!isfinite(x)) status |= kErrNonfinite;
+        sm.Xs[o] = x;
     }
     if constexpr (GEN) {
-        T pc[D][SMAX], gc[D][SMAX];
-        for (int m = 0; m < S; m++) {
+        // completion of the in-block intermediates at the group positions
+        T pc[D], gc[D];
+        {
             constexpr int mu = D - 1;
-            const int u = um[m][mu];
+            const bool two = (mask >> mu) & 1;
             T p = 0, q = 0;
-            for (int k = a[mu]; k < a[mu] + s[mu]; k++) {
-                const int m2 = m + (k - u) * smem_st[mu];
-                p += Em(mu, u, k) * r[m2];
-                q += Dm(mu, u, k) * r[m2];
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const T xv = __shfl_sync(full, x, member_with(mask, m, mu, k));
+                if (k == 0 || two) {
+                    const int kk = two ? a[mu] + k : u[mu];
+                    p += Em(mu, u[mu], kk) * xv;
+                    q += Dm(mu, u[mu], kk) * xv;
+                }
             }
-            pc[mu][m] = p;
-            gc[mu][m] = q;
+            pc[mu] = p;
+            gc[mu] = q;
         }
 #pragma unroll
         for (int l = D - 2; l >= 1; l--) {
-            for (int m = 0; m < S; m++) {
-                const int u = um[m][l];
-                T p = 0, q = 0;
-                for (int k = a[l]; k < a[l] + s[l]; k++) {
-                    const int m2 = m + (k - u) * smem_st[l];
-                    p += Em(l, u, k) * pc[l + 1][m2];
-                    q += Em(l, u, k) * gc[l + 1][m2] + Dm(l, u, k) * pc[l + 1][m2];
+            const bool two = (mask >> l) & 1;
+            T p = 0, q = 0;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int src = member_with(mask, m, l, k);
+                const T pp = __shfl_sync(full, pc[l + 1], src);
+                const T gg = __shfl_sync(full, gc[l + 1], src);
+                if (k == 0 || two) {
+                    const int kk = two ? a[l] + k : u[l];
+                    p += Em(l, u[l], kk) * pp;
+                    q += Em(l, u[l], kk) * gg + Dm(l, u[l], kk) * pp;
                 }
-                pc[l][m] = p;
-                gc[l][m] = q;
             }
+            pc[l] = p;
+            gc[l] = q;
         }
-        for (int m = 0; m < S; m++) {
+        if (act) {
 #pragma unroll
             for (int l = 1; l < D; l++) {
-                sm.Pin[(l - 1) * TD + om[m]] = P0[l][m] + pc[l][m];
-                sm.Gin[(l - 1) * TD + om[m]] = G0[l][m] + gc[l][m];
+                sm.Pin[(l - 1) * TD + o] = P0[l] + pc[l];
+                sm.Gin[(l - 1) * TD + o] = G0[l] + gc[l];
             }
         }
     }
     return status;
+}
+
+// Warp-uniform entry: the group whose first member is the in-block element e.
+template <typename T, int D, bool GEN>
+__device__ int warp_group(const TileSmem<T, D, GEN>& sm, int e, const T* minv) {
+    constexpr int TE = tile_extent(D);
+    int a[D], mask = 0, rem = e;
+#pragma unroll
+    for (int mu = 0; mu < D; mu++) {
+        a[mu] = rem % TE;
+        rem /= TE;
+        const int gi = sm.gidx[mu * TE + a[mu]];
+        if (sm.gl[mu * TE + gi] == 2) mask |= 1 << mu;
+    }
+    switch (__popc(mask)) {
+        case 1: return warp_group_solve<T, D, GEN, 2>(sm, a, mask, minv);
+        case 2: return warp_group_solve<T, D, GEN, 4>(sm, a, mask, minv);
+        case 3: if constexpr (D >= 3) return warp_group_solve<T, D, GEN, 8>(sm, a, mask, nullptr); else return 0;
+        case 4: if constexpr (D >= 4) return warp_group_solve<T, D, GEN, 16>(sm, a, mask, nullptr); else return 0;
+        default: return 0;
+    }
+}
+
+// After the groups of anti-diagonal t are solved: add their contributions to
+// the running line sums L (registers) of element e owned by this thread,
+// which lies on one of their mode lines (the group of e has index sum below t).
+// The products of the different modes are independent; each slot receives
+// one read-modify-write.
+template <typename T, int D, bool GEN>
+__device__ __forceinline__ void push_lines(const TileSmem<T, D, GEN>& sm, int t, int e, const int (&u)[D],
+                                           const int (&g)[D], int sg, T (&L)[WaveCfg<T, D, GEN>::NACC]) {
+    constexpr int TE = tile_extent(D);
+    constexpr int TD = ipow(TE, D);
+    constexpr int TC = TE * TE;
+    using C = WaveCfg<T, D, GEN>;
+    const T* __restrict__ Xs = sm.Xs;
+    T lap[D];
+#pragma unroll
+    for (int mu = 0; mu < D; mu++) {
+        lap[mu] = T(0);
+        const int src = t - (sg - g[mu]);
+        if (src >= sm.ng[mu]) continue;
+        const int k0 = sm.gs[mu * TE + src], kl = sm.gl[mu * TE + src];
+        const int st = ipow(TE, mu);
+        T s1 = T(0), s2 = T(0), s3 = T(0);
+        for (int k = k0; k < k0 + kl; k++) {
+            const int v = e + (k - u[mu]) * st;
+            const T dv = sm.Ds[mu * TC + u[mu] + TE * k];
+            if constexpr (!GEN) {
+                s1 += dv * Xs[v];
+            } else {
+                const T ev = sm.Es[mu * TC + u[mu] + TE * k];
+                if (mu == D - 1) {
+                    const T xv = Xs[v];
+                    s1 += ev * xv;
+                    s2 += dv * xv;
+                } else if (mu >= 1) {
+                    const T pv = sm.Pin[mu * TD + v], gv = sm.Gin[mu * TD + v];  // level mu + 1
+                    s1 += ev * pv;
+                    s2 += ev * gv;
+                    s3 += dv * pv;
+                } else {
+                    const T pv = sm.Pin[v], gv = sm.Gin[v];                       // level 1
+                    s1 += ev * gv;
+                    s2 += dv * pv;
+                }
+            }
+        }
+        if constexpr (!GEN) {
+            lap[mu] = s1;
+        } else {
+            if (mu == D - 1) {
+                L[C::slotP(D - 1)] += s1;
+                L[C::slotG(D - 1)] += s2;
+            } else if (mu >= 1) {
+                L[C::slotP(mu)] += s1;
+                L[C::slotG(mu)] += s2 + s3;
+            } else {
+                L[C::NACC - 1] += s1 + s2;
+            }
+        }
+    }
+    if constexpr (!GEN) {
+        T sum = lap[0];
+#pragma unroll
+        for (int mu = 1; mu < D; mu++) sum += lap[mu];
+        L[0] += sum;
+    }
+}
+
+// Entry (m, k) of the system of a coupled group with first element a and 2x2
+// modes `mask`: the operator restricted to the group (Laplace: the Kronecker
+// sum of the diagonal blocks; generalized: sum_mu A_mu x prod_{eta!=mu} C_eta).
+template <typename T, int D, bool GEN>
+__device__ __forceinline__ T group_entry(const TileSmem<T, D, GEN>& sm, const int (&a)[D], int mask, int m, int k) {
+    constexpr int TE = tile_extent(D);
+    constexpr int TC = TE * TE;
+    T e = 0;
+#pragma unroll
+    for (int mu = 0; mu < D; mu++) {
+        const int i = a[mu] + member_delta(mask, m, mu), j = a[mu] + member_delta(mask, k, mu);
+        T t = sm.Ds[mu * TC + i + TE * j];
+#pragma unroll
+        for (int eta = 0; eta < D; eta++) {
+            if (eta == mu) continue;
+            const int ii = a[eta] + member_delta(mask, m, eta), jj = a[eta] + member_delta(mask, k, eta);
+            if constexpr (GEN) t *= sm.Es[eta * TC + ii + TE * jj];
+            else if (ii != jj) t = T(0);
+        }
+        e += t;
+    }
+    return e;
+}
+
+// Inverse of a coupled group's system (S x S, row-major into out), by
+// Gauss-Jordan elimination with partial pivoting.  Returns kErrSingular for a
+// pivot below 16 eps max|M|.
+template <typename T, int D, bool GEN, int S>
+__device__ int group_inverse_s(const TileSmem<T, D, GEN>& sm, const int (&a)[D], int mask, T* out) {
+    T W[S][2 * S];
+    T big = 0;
+#pragma unroll
+    for (int m = 0; m < S; m++)
+#pragma unroll
+        for (int k = 0; k < S; k++) {
+            W[m][k] = group_entry<T, D, GEN>(sm, a, mask, m, k);
+            W[m][S + k] = m == k ? T(1) : T(0);
+            big = fmax(big, fabs(W[m][k]));
+        }
+    const T tiny = T(16) * dev::Eps<T>::v * big;
+    int status = 0;
+#pragma unroll
+    for (int c = 0; c < S; c++) {
+#pragma unroll
+        for (int q = c + 1; q < S; q++) {
+            const bool sw = fabs(W[q][c]) > fabs(W[c][c]);
+#pragma unroll
+            for (int k = 0; k < 2 * S; k++) {
+                const T x = W[c][k], y = W[q][k];
+                W[c][k] = sw ? y : x;
+                W[q][k] = sw ? x : y;
+            }
+        }
+        if (!(fabs(W[c][c]) > tiny)) status |= kErrSingular;
+        const T inv = T(1) / W[c][c];
+#pragma unroll
+        for (int k = 0; k < 2 * S; k++) W[c][k] *= inv;
+#pragma unroll
+        for (int q = 0; q < S; q++) {
+            if (q == c) continue;
+            const T f = W[q][c];
+#pragma unroll
+            for (int k = 0; k < 2 * S; k++) W[q][k] -= f * W[c][k];
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < S; m++)
+#pragma unroll
+        for (int k = 0; k < S; k++) out[m * S + k] = W[m][S + k];
+    return status;
+}
+
+template <typename T, int D, bool GEN>
+__device__ int group_inverse(const TileSmem<T, D, GEN>& sm, int e, T* out) {
+    constexpr int TE = tile_extent(D);
+    int a[D], mask = 0, rem = e;
+#pragma unroll
+    for (int mu = 0; mu < D; mu++) {
+        a[mu] = rem % TE;
+        rem /= TE;
+        if (sm.gl[mu * TE + sm.gidx[mu * TE + a[mu]]] == 2) mask |= 1 << mu;
+    }
+    switch (__popc(mask)) {
+        case 1: return group_inverse_s<T, D, GEN, 2>(sm, a, mask, out);
+        case 2: return group_inverse_s<T, D, GEN, 4>(sm, a, mask, out);
+        default: return 0;  // larger groups are eliminated in place by a warp
+    }
 }
 
 template <typename T, int D, bool GENF>
@@ -593,10 +767,13 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
     // ---- rank 0: base case of block T
     T* Rs = sbase + C::oR;
     T* Xs = sbase + C::oX;
+    T* Rd = sbase + C::oRd;
     T* Pin = sbase + C::oPin;
     T* Gin = sbase + C::oGin;
     T* Ds = sbase + C::oD;
     T* Es = sbase + C::oE;
+    T* Lin = sbase + C::oLin;
+    int* gidx = bs + D + 4;          // [D][TE] group of every in-block index
     T* Xg = static_cast<T*>(a.X) + t * TD;
     for (int idx = tid; idx < D * TC; idx += kThreads) {
         const int mu = idx / TC, e = idx % TC;
@@ -608,6 +785,14 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
         Rs[e] = Xg[e];
         Xs[e] = T(0);
     }
+    for (int e = tid; e < NACC * TD; e += kThreads) Lin[e] = T(0);
+    int* cg_cnt = gidx + D * TE;        // coupled groups per anti-diagonal
+    int* cg_off = cg_cnt + C::MAXSTEP;  // their offsets in cg_list
+    int* cg_fill = cg_off + C::MAXSTEP + 1;
+    int* cg_list = cg_fill + C::MAXSTEP;
+    int* cg_moff = cg_list + (TD / 2 + 1);  // offset of each group's inverse (-1: none)
+    T* Minv = sbase + C::oMinv;
+    for (int i = tid; i < C::MAXSTEP; i += kThreads) { cg_cnt[i] = 0; cg_fill[i] = 0; }
     if (GEN)
         for (int e = tid; e < C::NL * TD; e += kThreads) { Pin[e] = T(0); Gin[e] = T(0); }
     if (tid < D) bs[tid] = a.bsize[tid][I[tid]];
@@ -617,12 +802,17 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
         int n = 0, i = 0;
         while (i < b) {
             if (i + 1 < b && Ds[mu * TC + (i + 1) + TE * i] != T(0)) {
-                gs[mu * TE + n] = i; gl[mu * TE + n] = 2; i += 2;
+                gs[mu * TE + n] = i; gl[mu * TE + n] = 2;
+                gidx[mu * TE + i] = n; gidx[mu * TE + i + 1] = n;
+                i += 2;
             } else {
-                gs[mu * TE + n] = i; gl[mu * TE + n] = 1; i += 1;
+                gs[mu * TE + n] = i; gl[mu * TE + n] = 1;
+                gidx[mu * TE + i] = n;
+                i += 1;
             }
             n++;
         }
+        for (int k = b; k < TE; k++) gidx[mu * TE + k] = 0;
         ng[mu] = n;
     }
     if constexpr (GEN) {
@@ -631,8 +821,6 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
 #pragma unroll
         for (int l = D - 2; l >= 1; l--) {
             __syncthreads();
-            constexpr int dummy = 0;
-            (void)dummy;
             const int st = ipow(TE, l);
             const T* Pn = red + C::slotP(l + 1) * TD;
             const T* Gn = red + C::slotG(l + 1) * TD;
@@ -677,24 +865,132 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
     }
     __syncthreads();
 
-    // ---- back-substitution over coupled groups, anti-diagonal order
-    TileSmem<T, D, GEN> sm{Ds, Es, Rs, Xs, Pin, Gin, gs, gl, ng, bs};
-    int nsum = 0, nthr = 1;
+    // ---- back-substitution over coupled groups in anti-diagonal order.
+    // Every thread owns the elements e = tid + q*kThreads: it solves those
+    // that are 1x1 groups (or leads a coupled group) when their anti-diagonal
+    // comes, and keeps their running line sums current.
+    int status = 0;
+    int uq[EPT][D], gq[EPT][D], sq[EPT];
+    bool okq[EPT], lead[EPT], single[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; q++) {
+        const int e = tid + q * kThreads;
+        okq[q] = (TD % kThreads) == 0 || e < TD;
+        int rem = e, sgv = 0, S = 1;
+        bool ld = true;
+#pragma unroll
+        for (int mu = 0; mu < D; mu++) {
+            const int i = rem % TE;
+            rem /= TE;
+            uq[q][mu] = i;
+            if (i >= bs[mu]) okq[q] = false;
+            const int gg = okq[q] ? gidx[mu * TE + i] : 0;
+            gq[q][mu] = gg;
+            sgv += gg;
+            if (okq[q]) {
+                S *= gl[mu * TE + gg];
+                if (gs[mu * TE + gg] != i) ld = false;
+            }
+        }
+        sq[q] = sgv;
+        single[q] = okq[q] && S == 1;
+        lead[q] = okq[q] && S > 1 && ld;
+        if (single[q]) {
+            // reciprocal of the diagonal entry sum_mu a_mu,ii prod_{eta != mu} c_eta,jj
+            T diag = 0, mag = 0;
+#pragma unroll
+            for (int mu = 0; mu < D; mu++) {
+                T tt = Ds[mu * TC + uq[q][mu] * (TE + 1)];
+                if constexpr (GEN) {
+#pragma unroll
+                    for (int eta = 0; eta < D; eta++)
+                        if (eta != mu) tt *= Es[eta * TC + uq[q][eta] * (TE + 1)];
+                }
+                diag += tt;
+                mag += fabs(tt);
+            }
+            if (!(fabs(diag) > T(16) * dev::Eps<T>::v * mag)) status |= kErrSingular;
+            Rd[e] = T(1) / diag;
+        }
+    }
+    int nsum = 0;
 #pragma unroll
     for (int mu = 0; mu < D; mu++) nsum += ng[mu];
+    // coupled groups, bucketed by anti-diagonal (solved one warp per group)
 #pragma unroll
-    for (int mu = 1; mu < D; mu++) nthr *= ng[mu];
-    int status = 0;
+    for (int q = 0; q < EPT; q++)
+        if (lead[q]) atomicAdd(&cg_cnt[sq[q]], 1);
+    __syncthreads();
+    if (tid == 0) {
+        cg_off[0] = 0;
+        for (int i = 0; i < C::MAXSTEP; i++) cg_off[i + 1] = cg_off[i] + cg_cnt[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < EPT; q++)
+        if (lead[q]) cg_list[cg_off[sq[q]] + atomicAdd(&cg_fill[sq[q]], 1)] = tid + q * kThreads;
+    __syncthreads();
+    // inverses of the coupled groups with <= 4 members (the system depends only
+    // on the diagonal blocks), all groups in parallel
+    const int ncg = cg_off[C::MAXSTEP];
+    if (tid == 0) {
+        int run = 0;
+        for (int i = 0; i < ncg; i++) {
+            int rem = cg_list[i], mask = 0;
+            for (int mu = 0; mu < D; mu++) {
+                const int ai = rem % TE;
+                rem /= TE;
+                if (gl[mu * TE + gidx[mu * TE + ai]] == 2) mask |= 1 << mu;
+            }
+            const int S = 1 << __popc(mask);
+            if (S <= 4 && run + S * S <= C::MINV) {
+                cg_moff[i] = run;
+                run += S * S;
+            } else {
+                cg_moff[i] = -1;
+            }
+        }
+    }
+    __syncthreads();
+    TileSmem<T, D, GEN> sm{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
+    for (int i = tid; i < ncg; i += kThreads)
+        if (cg_moff[i] >= 0) status |= group_inverse<T, D, GEN>(sm, cg_list[i], Minv + cg_moff[i]);
+    T lsum[EPT][NACC];
+#pragma unroll
+    for (int q = 0; q < EPT; q++)
+#pragma unroll
+        for (int k = 0; k < NACC; k++) lsum[q][k] = T(0);
+    __syncthreads();
     for (int step = nsum - D; step >= 0; step--) {
-        for (int j = tid; j < nthr; j += kThreads) {
-            int g[D];
-            int rem = j, sum = 0;
+        // solve the 1x1 groups of this anti-diagonal from the register sums;
+        // members of coupled groups publish their sums for the solving warp
 #pragma unroll
-            for (int mu = 1; mu < D; mu++) { g[mu] = rem % ng[mu]; rem /= ng[mu]; sum += g[mu]; }
-            g[0] = step - sum;
-            if (g[0] >= 0 && g[0] < ng[0]) status |= solve_group<T, D, GEN>(sm, g);
+        for (int q = 0; q < EPT; q++) {
+            if (sq[q] != step || !okq[q]) continue;
+            const int e = tid + q * kThreads;
+            if (single[q]) {
+                status |= solve_single<T, D, GEN>(sm, e, uq[q], lsum[q]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < NACC; k++) Lin[k * TD + e] = lsum[q][k];
+            }
+        }
+        const int c0 = cg_off[step], cn = cg_cnt[step];
+        if (cn > 0) {
+            __syncthreads();
+            const int warp = tid >> 5, nw = kThreads >> 5;
+            for (int k = warp; k < cn; k += nw)
+                status |= warp_group<T, D, GEN>(sm, cg_list[c0 + k], cg_moff[c0 + k] >= 0 ? Minv + cg_moff[c0 + k] : nullptr);
         }
         __syncthreads();
+        if (step == 0) break;
+        // contributions of this anti-diagonal to the owned elements' sums
+        // (registers only; the next anti-diagonal's writes touch other positions)
+#pragma unroll
+        for (int q = 0; q < EPT; q++) {
+            if (!okq[q] || sq[q] >= step) continue;
+            push_lines<T, D, GEN>(sm, step, tid + q * kThreads, uq[q], gq[q], sq[q], lsum[q]);
+        }
     }
     if (status) atomicOr(a.err, status);
 
@@ -738,33 +1034,6 @@ cudaError_t launch_wave_t(const WaveArgs& a, cudaStream_t s) {
         cfg.numAttrs = 1;
     }
     return cudaLaunchKernelEx(&cfg, k_wave<T, D, GEN>, a);
-}
-
-template <typename T>
-cudaError_t prepare_wave_impl() {
-    cudaError_t e = cudaSuccess;
-    if ((e = prepare_wave_t<T, 1, false>()) != cudaSuccess) return e;
-    if ((e = prepare_wave_t<T, 2, false>()) != cudaSuccess) return e;
-    if ((e = prepare_wave_t<T, 2, true>()) != cudaSuccess) return e;
-    if ((e = prepare_wave_t<T, 3, false>()) != cudaSuccess) return e;
-    if ((e = prepare_wave_t<T, 3, true>()) != cudaSuccess) return e;
-    if ((e = prepare_wave_t<T, 4, false>()) != cudaSuccess) return e;
-    return prepare_wave_t<T, 4, true>();
-}
-
-template <typename T>
-cudaError_t launch_wave_impl(int d, bool gen, const WaveArgs& a, cudaStream_t s) {
-    switch (d * 2 + (gen ? 1 : 0)) {
-        case 2: return launch_wave_t<T, 1, false>(a, s);
-        case 3: return launch_wave_t<T, 1, false>(a, s);  // d = 1: both forms coincide
-        case 4: return launch_wave_t<T, 2, false>(a, s);
-        case 5: return launch_wave_t<T, 2, true>(a, s);
-        case 6: return launch_wave_t<T, 3, false>(a, s);
-        case 7: return launch_wave_t<T, 3, true>(a, s);
-        case 8: return launch_wave_t<T, 4, false>(a, s);
-        case 9: return launch_wave_t<T, 4, true>(a, s);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 }  // namespace tsylv
