@@ -70,7 +70,8 @@ enum tsylv_status {
     TSYLV_ENOCONV = 3,      /* refinement missed opts->tol within max_refine steps */
     TSYLV_ECUDA = 4,        /* a CUDA runtime call failed                         */
     TSYLV_ETIMEOUT = 5,     /* a bounded device-side wait ran out                 */
-    TSYLV_EUNSUPPORTED = 6  /* valid arguments outside what this build supports   */
+    TSYLV_EUNSUPPORTED = 6, /* valid arguments outside what this build supports   */
+    TSYLV_ESCRATCH = 7      /* problem too large for tsylv_solve_noalloc's array   */
 };
 
 enum tsylv_precision {
@@ -211,6 +212,25 @@ int tsylv_solve_batched(int count, const int* d, const int64_t* n_packed, const 
                         const double* B_pool, double* X_pool, void* work, size_t work_bytes,
                         const tsylv_opts* opts, int* per_status, tsylv_info* info,
                         cudaStream_t stream);
+
+/* Allocation-free variant of tsylv_solve (FP64 precision only).  The paper
+ * has no counterpart: this entry point serves callers that cannot allocate
+ * device memory when they solve -- a host application whose own allocator owns
+ * all device memory, a real-time loop that cannot afford cudaMalloc's latency
+ * and implicit synchronisation, a plug-in that may not grow the process's
+ * device footprint after start-up.  The caller passes A, B and X as for
+ * tsylv_solve; there is no workspace argument.  All scratch lives in one
+ * file-scope device array of 32 MiB, which every GPU that loads the library
+ * holds until the process exits; problems whose workspace (the
+ * tsylv_workspace_bytes bound) exceeds it are rejected with TSYLV_ESCRATCH and
+ * a tsylv_last_error() message, before any GPU work.  The first call on each
+ * device looks up the array's device address and sets kernel attributes; make
+ * that first call before any stream capture.  Calls share the array, so calls
+ * whose GPU work overlaps race on it: serialise them.  The status word is
+ * cleared by every call.  Arguments and the other status codes as
+ * tsylv_solve (opts->precision must be TSYLV_FP64, else -6). */
+int tsylv_solve_noalloc(int d, const int64_t* n, const double* const* A, const double* B, double* X,
+                        const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

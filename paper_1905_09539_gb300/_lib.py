@@ -12,6 +12,7 @@ TSYLV_ENOCONV = 3
 TSYLV_ECUDA = 4
 TSYLV_ETIMEOUT = 5
 TSYLV_EUNSUPPORTED = 6
+TSYLV_ESCRATCH = 7
 
 TSYLV_FP64 = 0
 TSYLV_FP32_REFINED = 1
@@ -42,6 +43,7 @@ EXPORTS = [
     "tsylv_opts_default", "tsylv_status_string", "tsylv_workspace_bytes", "tsylv_solve", "gtsylv_solve",
     "tsylv_solve_transposed", "gtsylv_solve_transposed", "tsylv_residual", "tsylv_backward_workspace_bytes",
     "tsylv_backward", "tsylv_batched_workspace_bytes", "tsylv_solve_batched", "tsylv_last_error",
+    "tsylv_solve_noalloc",
 ]
 
 _lib = None
@@ -82,6 +84,8 @@ def load(path=LIB_PATH):
     lib.tsylv_batched_workspace_bytes.restype = S
     lib.tsylv_solve_batched.argtypes = [I, ctypes.POINTER(I), I64P, I64P, I64P, P, P, P, P, P, S, OP,
                                         ctypes.POINTER(I), IP, P]
+    lib.tsylv_solve_noalloc.argtypes = [I, I64P, P, P, P, OP, IP, P]
+    lib.tsylv_solve_noalloc.restype = I
     for f in ("tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
               "tsylv_residual", "tsylv_backward", "tsylv_solve_batched"):
         getattr(lib, f).restype = I

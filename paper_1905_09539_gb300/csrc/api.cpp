@@ -50,6 +50,7 @@ extern "C" const char* tsylv_status_string(int s) {
         case TSYLV_ECUDA: return "CUDA runtime error";
         case TSYLV_ETIMEOUT: return "bounded device wait timed out";
         case TSYLV_EUNSUPPORTED: return "unsupported configuration";
+        case TSYLV_ESCRATCH: return "problem exceeds the static scratch of tsylv_solve_noalloc";
         default: return "unknown status";
     }
 }
