@@ -198,18 +198,23 @@ def run_reference(args, ws, rank):
         t_full, parts = oracle_sample((96, 96, 96), (64, 64, 64), full, seed=it % 3)
         if it >= args.warmup:
             times.append(t_full)
-    step = float(np.mean(times))
-    value = 2 * N / step
+    # the oracle solves each of the four parts of a step (FP64 and refined,
+    # Laplace and generalized) in FP64: two Laplace and two generalized solves
+    step = 2 * float(np.mean(times))
+    value = 4 * N / step
     line = {
-        "impl": "reference", "metric": "unknowns/s (FP64 solve, Laplace + generalized, d=3 256^3)",
+        "impl": "reference",
+        "metric": "unknowns/s (d=3 256^3, Laplace + generalized, FP64 and FP32-refined to rel. residual <= 1e-12); "
+                  "% of FP64 peak; mixed-precision vs FP64 speed-up",
         "value": value, "unit": "unknowns/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (synthetic.py, seed 0..2)",
-        "config": {"workload": "d=3 n=256^3 FP64 Laplace + generalized solve", "form": ["laplace", "generalized"],
+        "config": {"workload": "d=3 n=256^3: FP64 solve and FP32-refined solve, Laplace + generalized form",
+                   "form": ["laplace", "generalized"],
                    "sample": "oracle O-B on 96^3 (Laplace) + 64^3 (generalized), scaled by algorithmic flops"},
         "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                         "sample": "O-B recursion, 96^3 Laplace + 64^3 generalized per step, time scaled to "
-                                   "256^3 by the algorithmic-flop ratio"},
+                         "sample": "O-B recursion, 96^3 Laplace + 64^3 generalized per step (each solved twice: the "
+                                   "FP64 and the refined part), time scaled to 256^3 by the algorithmic-flop ratio"},
         "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -247,18 +252,23 @@ def run_ours(args, ws, rank, local):
             "flops": algorithmic_flops(p["A"], p["C"]),
         }
     stream = torch.cuda.current_stream(dev)
-    infos = {False: _lib.Info(), True: _lib.Info()}
+    PARTS = [("fp64_laplace", False, _lib.TSYLV_FP64), ("fp64_generalized", True, _lib.TSYLV_FP64),
+             ("fp32r_laplace", False, _lib.TSYLV_FP32_REFINED), ("fp32r_generalized", True, _lib.TSYLV_FP32_REFINED)]
+    infos = {name: _lib.Info() for name, _, _ in PARTS}
+    for gen in (False, True):
+        probs[gen]["Xr"] = ts.empty_fortran(shape, dev)
 
-    def solve(gen, timing=0):
+    def solve(name, gen, prec, timing=0):
         pr = probs[gen]
+        X = pr["X"] if prec == _lib.TSYLV_FP64 else pr["Xr"]
         if gen:
-            ts.gtsylv_solve(pr["A"], pr["C"], pr["B"], X=pr["X"], info=infos[gen], timing=timing)
+            ts.gtsylv_solve(pr["A"], pr["C"], pr["B"], X=X, info=infos[name], timing=timing, precision=prec)
         else:
-            ts.tsylv_solve(pr["A"], pr["B"], X=pr["X"], info=infos[gen], timing=timing)
+            ts.tsylv_solve(pr["A"], pr["B"], X=X, info=infos[name], timing=timing, precision=prec)
 
     def step(timing=0):
-        solve(False, timing)
-        solve(True, timing)
+        for name, gen, prec in PARTS:
+            solve(name, gen, prec, timing)
 
     for _ in range(args.warmup):
         step()
@@ -274,41 +284,49 @@ def run_ours(args, ws, rank, local):
         e0.record(stream)
         for _ in range(args.steps):
             step()
-            launches += infos[False].launches + infos[True].launches
+            launches += sum(infos[name].launches for name, _, _ in PARTS)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(ws)
     clocks = clk.summary()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, ws, dev)
-    units = sum_over_ranks(2 * N, ws, dev)
+    units = sum_over_ranks(len(PARTS) * N, ws, dev)
     value = units / (ms * 1e-3)
 
-    # ---- per-kernel timing of the wavefront launches (CUDA events recorded
-    # around them on the launching stream, inside the captured graph)
-    wave_ms = {False: [], True: []}
-    tot_ms = {False: [], True: []}
+    # ---- per-solve timing (CUDA events recorded on the launching stream inside
+    # the captured graphs: whole call, wavefront launches, residual launches)
+    tim = {name: {"tot": [], "wave": [], "res": []} for name, _, _ in PARTS}
     for _ in range(max(3, args.steps)):
-        for gen in (False, True):
-            solve(gen, timing=1)
-            wave_ms[gen].append(infos[gen].t_waves_ms)
-            tot_ms[gen].append(infos[gen].t_total_ms)
+        for name, gen, prec in PARTS:
+            solve(name, gen, prec, timing=1)
+            tim[name]["tot"].append(infos[name].t_total_ms)
+            tim[name]["wave"].append(infos[name].t_waves_ms)
+            tim[name]["res"].append(infos[name].t_resid_ms)
+    # residual of every result, measured independently of the solve with the
+    # library's FP64-pipe residual
     parts = {}
-    for gen in (False, True):
-        f = probs[gen]["flops"]
-        wm = float(np.median(wave_ms[gen]))
-        tm = float(np.median(tot_ms[gen]))
-        parts["fp64_generalized" if gen else "fp64_laplace"] = {
-            "ms": tm, "wave_ms": wm, "waves": infos[gen].waves, "tiles": infos[gen].tiles,
-            "algorithmic_gflop": f / 1e9, "executed_gflop": infos[gen].flops / 1e9,
-            "tflops_algorithmic": f / (tm * 1e-3) / 1e12,
-            "unknowns_per_s": N / (tm * 1e-3),
-            "frac_fp64_peak": f / (tm * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+    for name, gen, prec in PARTS:
+        pr = probs[gen]
+        X = pr["X"] if prec == _lib.TSYLV_FP64 else pr["Xr"]
+        _, rho, _ = ts.tsylv_residual(pr["A"], pr["B"], X, pr["C"], residual=_lib.TSYLV_RESID_FP64)
+        f = pr["flops"]
+        tm = float(np.median(tim[name]["tot"]))
+        parts[name] = {
+            "ms": tm, "wave_ms": float(np.median(tim[name]["wave"])), "resid_ms": float(np.median(tim[name]["res"])),
+            "iterations": infos[name].iterations, "rel_residual_fp64": rho, "waves": infos[name].waves,
+            "tiles": infos[name].tiles, "unknowns_per_s": N / (tm * 1e-3),
         }
-    dom = True  # the generalized wavefront kernel carries most of the step
-    f_dom = probs[dom]["flops"]
-    w_dom = float(np.median(wave_ms[dom]))
-    nwaves = infos[dom].waves
+        if prec == _lib.TSYLV_FP64:
+            parts[name].update({"algorithmic_gflop": f / 1e9, "executed_gflop": infos[name].flops / 1e9,
+                                "tflops_algorithmic": f / (tm * 1e-3) / 1e12,
+                                "frac_fp64_peak": f / (tm * 1e-3) / 1e12 / FP64_PEAK_TFLOPS})
+    mixed_vs_fp64 = {"laplace": parts["fp64_laplace"]["ms"] / parts["fp32r_laplace"]["ms"],
+                     "generalized": parts["fp64_generalized"]["ms"] / parts["fp32r_generalized"]["ms"]}
+    dom = "fp64_generalized"  # the generalized FP64 wavefront kernel carries most of the step
+    f_dom = probs[True]["flops"]
+    w_dom = parts[dom]["wave_ms"]
+    nwaves = parts[dom]["waves"]
     achieved = (f_dom / nwaves) / (w_dom * 1e-3 / nwaves) / 1e12
     roofline = {"bound": "alu", "kernel": "k_wave<double,3,generalized>", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
@@ -322,19 +340,21 @@ def run_ours(args, ws, rank, local):
     h2d = d2h = 0
     for gen in (False, True):
         pr = probs[gen]
-        hb = torch.empty_like(pr["B"], device="cpu").pin_memory()
+        hb = torch.empty(pr["B"].shape[::-1], dtype=torch.float64).pin_memory().permute(2, 1, 0)
         hb.copy_(pr["B"])
         hA = [a.cpu().pin_memory() for a in pr["A"]]
         hC = [c.cpu().pin_memory() for c in pr["C"]] if gen else None
-        hx = torch.empty_like(hb).pin_memory()
+        hx = torch.empty(pr["B"].shape[::-1], dtype=torch.float64).pin_memory().permute(2, 1, 0)
         host[gen] = (hb, hA, hC, hx)
+    for name, gen, prec in PARTS:
+        hb, hA, hC, hx = host[gen]
         h2d += hb.numel() * 8 + sum(a.numel() * 8 for a in hA) + (sum(c.numel() * 8 for c in hC) if gen else 0)
         d2h += hx.numel() * 8
     barrier(ws)
     torch.cuda.synchronize(dev)
     e0.record(stream)
     for _ in range(args.steps):
-        for gen in (False, True):
+        for name, gen, prec in PARTS:
             pr = probs[gen]
             hb, hA, hC, hx = host[gen]
             pr["B"].copy_(hb, non_blocking=True)
@@ -343,31 +363,33 @@ def run_ours(args, ws, rank, local):
             if gen:
                 for c, h in zip(pr["C"], hC):
                     c.copy_(h, non_blocking=True)
-            solve(gen)
-            hx.copy_(pr["X"], non_blocking=True)
+            solve(name, gen, prec)
+            hx.copy_(pr["X"] if prec == _lib.TSYLV_FP64 else pr["Xr"], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(ws)
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws, dev)
 
     line = {
-        "metric": "unknowns/s (FP64 solve, Laplace + generalized, d=3 256^3); % of FP64 peak",
+        "metric": "unknowns/s (d=3 256^3, Laplace + generalized, FP64 and FP32-refined to rel. residual <= 1e-12); "
+                  "% of FP64 peak; mixed-precision vs FP64 speed-up",
         "value": value, "unit": "unknowns/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (synthetic.py, seed %d)" % args.seed,
-        "config": {"workload": "d=3 n=%d^3 FP64 Laplace + generalized solve" % args.n,
+        "config": {"workload": "d=3 n=%d^3: FP64 solve and FP32-refined solve, Laplace + generalized form" % args.n,
                    "form": ["laplace", "generalized"], "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (%.0f MB per tensor)" % (N * 8 / 1e6)},
         "parts": parts,
+        "mixed_vs_fp64": mixed_vs_fp64,
         "roofline": roofline,
-        "e2e": {"value": sum_over_ranks(2 * N, ws, dev) / (e2e_ms * 1e-3), "unit": "unknowns/s",
+        "e2e": {"value": sum_over_ranks(len(PARTS) * N, ws, dev) / (e2e_ms * 1e-3), "unit": "unknowns/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:
         t_full, samp = oracle_sample((128, 128, 128), (96, 96, 96), shape, seed=args.seed)
-        line["cpu_baseline"] = {"value": 2 * N / t_full, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": 4 * N / (2 * t_full), "unit": "unknowns/s", "cores": 1, "kind": "oracle",
                                 "sample": "O-B recursion on 128^3 (Laplace, %.1f s) + 96^3 (generalized, %.1f s), "
                                           "time scaled to %d^3 by the algorithmic-flop ratio" %
                                           (samp["laplace"]["seconds"], samp["gen"]["seconds"], args.n)}

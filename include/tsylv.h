@@ -76,7 +76,11 @@ enum tsylv_status {
 
 enum tsylv_precision {
     TSYLV_FP64 = 0,          /* plain FP64 solve (FP64 pipes)                       */
-    TSYLV_FP32_REFINED = 1,  /* FP32 solves + FP64-accurate residual refinement     */
+    TSYLV_FP32_REFINED = 1,  /* FP32 solves + FP64-accurate residual refinement:
+                                X_0 = 0; D_k = solve_FP32(R_k / max|R_k|);
+                                X_{k+1} = X_k + max|R_k| D_k (FP64);
+                                R_{k+1} = B - A(X_{k+1}) (opts->residual)
+                                until ||R|| / (||A|| ||X||) <= opts->tol        */
     TSYLV_TF32_REFINED = 2,  /* TF32 tensor-core updates, FP32 accumulation, refined */
     TSYLV_BF16_REFINED = 3   /* BF16 tensor-core updates, FP32 accumulation, refined */
 };
@@ -167,9 +171,18 @@ int gtsylv_solve_transposed(int d, const int64_t* n, const double* const* A,
                             size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
                             cudaStream_t stream);
 
+/* Workspace bytes for tsylv_residual. */
+size_t tsylv_residual_workspace_bytes(int d, const int64_t* n, int generalized);
+
 /* Residual R = B - A(X) (C == NULL: Laplace form) with the arithmetic chosen
- * by opts->residual; *rel (optional, host) receives ||R|| / (||A|| ||X||).
- * Workspace: tsylv_workspace_bytes of the matching form. */
+ * by opts->residual: TSYLV_RESID_FP64 multiplies and adds on the FP64 pipes;
+ * TSYLV_RESID_DF64 carries every double as an unevaluated pair of floats
+ * (error <= 2^-48 relative per entry) and runs on the FP32 pipes.  *rel
+ * (optional, host) receives ||R||_F / (||A|| ||X||_F) with
+ * ||A|| = sum_mu ||A_mu||_2 prod_{eta!=mu} ||C_eta||_2 (power-iteration
+ * estimates of the 2-norms).  Arguments: 1 d, 2 n, 3 A, 4 C, 5 B, 6 X, 7 R,
+ * 8 rel, 9 work, 10 work_bytes (>= tsylv_residual_workspace_bytes), 11 opts,
+ * 12 stream. */
 int tsylv_residual(int d, const int64_t* n, const double* const* A, const double* const* C,
                    const double* B, const double* X, double* R, double* rel, void* work,
                    size_t work_bytes, const tsylv_opts* opts, cudaStream_t stream);

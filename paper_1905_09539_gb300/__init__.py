@@ -175,7 +175,7 @@ def tsylv_residual(A, B, X, C=None, R=None, *, opts=None, check=True, stream=Non
         C_, pc = _mats(C)
     n = _dims(B.shape)
     d = B.dim()
-    work = workspace(lib.tsylv_workspace_bytes(d, n, 1 if C is not None else 0, ctypes.byref(o)), B.device)
+    work = workspace(lib.tsylv_residual_workspace_bytes(d, n, 1 if C is not None else 0), B.device)
     rel = ctypes.c_double(-1.0)
     st = lib.tsylv_residual(d, n, pa, pc, B.data_ptr(), X.data_ptr(), R.data_ptr(), ctypes.byref(rel),
                             work.data_ptr(), work.numel(), ctypes.byref(o), _stream(stream))

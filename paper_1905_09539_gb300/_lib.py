@@ -43,7 +43,7 @@ EXPORTS = [
     "tsylv_opts_default", "tsylv_status_string", "tsylv_workspace_bytes", "tsylv_solve", "gtsylv_solve",
     "tsylv_solve_transposed", "gtsylv_solve_transposed", "tsylv_residual", "tsylv_backward_workspace_bytes",
     "tsylv_backward", "tsylv_batched_workspace_bytes", "tsylv_solve_batched", "tsylv_last_error",
-    "tsylv_solve_noalloc",
+    "tsylv_solve_noalloc", "tsylv_residual_workspace_bytes",
 ]
 
 _lib = None
@@ -77,6 +77,8 @@ def load(path=LIB_PATH):
     lib.tsylv_solve_transposed.argtypes = [I, I64P, P, P, P, P, S, OP, IP, P]
     lib.gtsylv_solve_transposed.argtypes = [I, I64P, P, P, P, P, P, S, OP, IP, P]
     lib.tsylv_residual.argtypes = [I, I64P, P, P, P, P, P, ctypes.POINTER(ctypes.c_double), P, S, OP, P]
+    lib.tsylv_residual_workspace_bytes.argtypes = [I, I64P, I]
+    lib.tsylv_residual_workspace_bytes.restype = S
     lib.tsylv_backward_workspace_bytes.argtypes = [I, I64P, I, OP]
     lib.tsylv_backward_workspace_bytes.restype = S
     lib.tsylv_backward.argtypes = [I, I64P, P, P, P, P, P, P, P, P, S, OP, IP, P]

@@ -38,6 +38,7 @@ extern "C" void tsylv_opts_default(tsylv_opts* o) {
     o->split = 0;
     o->use_graph = 1;
     o->host_io = 0;
+    o->timing = 0;
 }
 
 extern "C" const char* tsylv_status_string(int s) {
@@ -82,6 +83,10 @@ extern "C" int gtsylv_solve_transposed(int d, const int64_t* n, const double* co
                                        const double* G, double* L, void* work, size_t work_bytes,
                                        const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream) {
     return solver_solve(d, n, A, C, G, L, work, work_bytes, opts, info, stream, true, true);
+}
+
+extern "C" size_t tsylv_residual_workspace_bytes(int d, const int64_t* n, int generalized) {
+    return solver_residual_workspace_bytes(d, n, generalized != 0);
 }
 
 extern "C" int tsylv_residual(int d, const int64_t* n, const double* const* A, const double* const* C,

@@ -1,0 +1,65 @@
+// Operator application on the block tensor, for the residual B - A(X) of the
+// refinement (and of tsylv_residual).  One CTA per output block; the block
+// products along one mode (or, for the Laplace form, along every mode) are
+// staged through shared memory by bulk copies exactly as in the wavefront
+// kernel, but every source block J >= I_mu contributes (diagonal included)
+// and nothing depends on anything else of the same launch.
+//
+// Two arithmetics:
+//   FP64 : native double multiply-adds (FP64 pipes)
+//   DF64 : every double is carried as an unevaluated float pair (hi, lo),
+//          |x - hi - lo| <= 2^-48 |x|; products are formed exactly with
+//          an FMA (Dekker/Veltkamp product, Ogita-Rump-Oishi "Accurate sum
+//          and dot product", 2005) and accumulated with the two-sum of Knuth,
+//          so the whole contraction runs on the FP32 pipes.
+//
+// Generalized d-term form, Horner order over the modes (one launch per mode):
+//   level d-1:  P = X x C,  G = X x A
+//   level l  :  P = P' x C, G = G' x C + P' x A
+//   level 0  :  R = B - (G' x C + P' x A)
+// Laplace form: R = B - sum_mu X x_mu A_mu in one launch.
+#pragma once
+
+#include "tsylv_internal.h"
+
+namespace tsylv {
+
+enum ApplyKind : int { kApplyLaplace = 0, kApplyFirst = 1, kApplyMiddle = 2, kApplyFinal = 3 };
+
+struct ApplyArgs {
+    int nb[kMaxD];
+    long long tstride[kMaxD];
+    long long ntiles;
+    int kind;          // ApplyKind
+    int mode;          // mode of the generalized level
+    // sources (block tensors).  FP64: s1, s2 are double tiles.  DF64: s1h/s1l,
+    // s2h/s2l are float tiles.
+    const void* s1;
+    const void* s1l;
+    const void* s2;
+    const void* s2l;
+    // outputs of a generalized level (FP64: o1, o2 double; DF64: o1/o1l, o2/o2l float)
+    void* o1;
+    void* o1l;
+    void* o2;
+    void* o2l;
+    const double* B;   // right-hand side (double tiles) for kApplyLaplace / kApplyFinal
+    double* R;         // residual (double tiles)
+    double* part;      // [ntiles][2]: sum of R^2, max |R| of every block
+    // coefficient tiles (upper block triangle), per mode: FP64 A/C (double),
+    // DF64 Ah/Al, Ch/Cl (float)
+    const void* A[kMaxD];
+    const void* Al[kMaxD];
+    const void* C[kMaxD];
+    const void* Cl[kMaxD];
+    int* err;
+    long long timeout_ns;
+};
+
+template <bool DF>
+cudaError_t launch_apply(int d, const ApplyArgs& a, cudaStream_t s);
+template <bool DF>
+cudaError_t prepare_apply();
+
+
+}  // namespace tsylv

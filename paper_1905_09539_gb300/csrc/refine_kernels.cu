@@ -1,0 +1,214 @@
+// Elementwise and reduction kernels of the mixed-precision refinement:
+// scaling of the residual into the FP32 solve, the FP64 correction update of
+// X, double -> float-pair splitting for the DF64 residual, norm reductions and
+// spectral-norm estimates of the coefficients.
+#include "refine.h"
+
+namespace tsylv {
+
+namespace {
+
+inline int grid_for(long long total) {
+    long long b = (total + 255) / 256;
+    if (b > 152LL * 16) b = 152LL * 16;
+    if (b < 1) b = 1;
+    return static_cast<int>(b);
+}
+
+// x (double) -> (hi, lo) floats with hi + lo = x to 2^-48 relative
+__global__ void k_split(const double* __restrict__ x, float* __restrict__ h, float* __restrict__ l, long long n) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double v = x[i];
+        const float hv = static_cast<float>(v);
+        h[i] = hv;
+        l[i] = static_cast<float>(v - static_cast<double>(hv));
+    }
+}
+
+// r32 = r64 / max|r64|   (scale read from the device-side norm record)
+__global__ void k_scale_to_f32(const double* __restrict__ r, float* __restrict__ r32, const double* __restrict__ nrm,
+                               long long n) {
+    const double mx = nrm[1];
+    const double s = mx > 0 ? 1.0 / mx : 1.0;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        r32[i] = static_cast<float>(r[i] * s);
+}
+
+// x += max|r| * d32 (the correction of the scaled system), optional split of
+// the new x, and per-block partial sums of x^2 into part[2*blk + 0] (the
+// residual kernels own part[.. + 0, 1] of another array).
+__global__ void k_update_x(double* __restrict__ x, const float* __restrict__ d32, const double* __restrict__ nrm,
+                           float* __restrict__ xh, float* __restrict__ xl, double* __restrict__ xpart, long long n,
+                           int td) {
+    const double mx = nrm[1];
+    const double s = mx > 0 ? mx : 1.0;
+    for (long long blk = blockIdx.x; blk * td < n; blk += gridDim.x) {
+        double ss = 0;
+        for (int e = threadIdx.x; e < td; e += blockDim.x) {
+            const long long i = blk * td + e;
+            const double v = x[i] + s * static_cast<double>(d32[i]);
+            x[i] = v;
+            if (xh) {
+                const float hv = static_cast<float>(v);
+                xh[i] = hv;
+                xl[i] = static_cast<float>(v - static_cast<double>(hv));
+            }
+            ss += v * v;
+        }
+        for (int w = 16; w >= 1; w >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, w);
+        __shared__ double red[32];
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0;
+            for (int w = 0; w < static_cast<int>(blockDim.x >> 5); w++) t += red[w];
+            xpart[blk] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// nrm[0] = sum part[2i], nrm[1] = max part[2i+1], nrm[2] = sum xpart[i]
+__global__ void k_reduce(const double* __restrict__ part, const double* __restrict__ xpart, long long nt,
+                         double* __restrict__ nrm) {
+    double s = 0, m = 0, x = 0;
+    for (long long i = threadIdx.x; i < nt; i += blockDim.x) {
+        s += part[2 * i];
+        m = fmax(m, part[2 * i + 1]);
+        if (xpart) x += xpart[i];
+    }
+    for (int w = 16; w >= 1; w >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, w);
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, w));
+        x += __shfl_xor_sync(0xffffffffu, x, w);
+    }
+    __shared__ double red[3][32];
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s;
+        red[1][threadIdx.x >> 5] = m;
+        red[2][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); w++) {
+            a += red[0][w];
+            b = fmax(b, red[1][w]);
+            c += red[2][w];
+        }
+        nrm[0] = a;
+        nrm[1] = b;
+        nrm[2] = c;
+    }
+}
+
+// ||M||_2 estimate of an n x n column-major matrix (structural zeros below
+// the first subdiagonal ignored): power iteration on M^T M, 80 steps, one CTA
+// per matrix (the norm only scales the stopping test).
+__global__ void k_norm2(NormArgs a, double* __restrict__ out) {
+    const int mat = blockIdx.x;
+    const double* M = a.M[mat];
+    const int n = a.n[mat];
+    const int upper = a.upper[mat];
+    extern __shared__ double sh[];
+    double* v = sh;          // n
+    double* w = sh + n;      // n
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.0 + 0.01 * (i % 7);
+    __syncthreads();
+    double lam = 0;
+    for (int it = 0; it < 80; it++) {
+        // w = M v
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double s = 0;
+            const int j0 = upper ? i : (i > 0 ? i - 1 : 0);
+            for (int j = j0; j < n; j++) s += M[i + static_cast<long long>(n) * j] * v[j];
+            w[i] = s;
+        }
+        __syncthreads();
+        // v = M^T w, lam = ||v|| / ||previous v|| via normalisation
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            double s = 0;
+            const int iend = upper ? j : (j + 1 < n ? j + 1 : n - 1);
+            for (int i = 0; i <= iend; i++) s += M[i + static_cast<long long>(n) * j] * w[i];
+            v[j] = s;
+        }
+        __syncthreads();
+        double nv = 0;
+        for (int j = 0; j < n; j++) nv += v[j] * v[j];
+        nv = sqrt(nv);
+        lam = nv;
+        __syncthreads();
+        const double inv = nv > 0 ? 1.0 / nv : 0.0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) v[j] *= inv;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[mat] = sqrt(lam);
+}
+
+// part[2 t] = sum x^2, part[2 t + 1] = max |x| over block t
+__global__ void k_tile_stats(const double* __restrict__ x, double* __restrict__ part, long long nt, int td) {
+    for (long long t = blockIdx.x; t < nt; t += gridDim.x) {
+        double ss = 0, mx = 0;
+        for (int e = threadIdx.x; e < td; e += blockDim.x) {
+            const double v = x[t * td + e];
+            ss += v * v;
+            mx = fmax(mx, fabs(v));
+        }
+        for (int w = 16; w >= 1; w >>= 1) {
+            ss += __shfl_xor_sync(0xffffffffu, ss, w);
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, w));
+        }
+        __shared__ double red[2][32];
+        if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = ss; red[1][threadIdx.x >> 5] = mx; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0, b = 0;
+            for (int w = 0; w < static_cast<int>(blockDim.x >> 5); w++) { a += red[0][w]; b = fmax(b, red[1][w]); }
+            part[2 * t] = a;
+            part[2 * t + 1] = b;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_tile_stats(const double* x, double* part, long long nt, int td, cudaStream_t s) {
+    int g = static_cast<int>(nt < 152LL * 16 ? nt : 152LL * 16);
+    if (g < 1) g = 1;
+    k_tile_stats<<<g, 128, 0, s>>>(x, part, nt, td);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split(const double* x, float* h, float* l, long long n, cudaStream_t s) {
+    k_split<<<grid_for(n), 256, 0, s>>>(x, h, l, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_to_f32(const double* r, float* r32, const double* nrm, long long n, cudaStream_t s) {
+    k_scale_to_f32<<<grid_for(n), 256, 0, s>>>(r, r32, nrm, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_x(double* x, const float* d32, const double* nrm, float* xh, float* xl, double* xpart,
+                            long long n, int td, cudaStream_t s) {
+    long long nb = n / td;
+    int g = static_cast<int>(nb < 152LL * 16 ? nb : 152LL * 16);
+    if (g < 1) g = 1;
+    k_update_x<<<g, 128, 0, s>>>(x, d32, nrm, xh, xl, xpart, n, td);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double* part, const double* xpart, long long nt, double* nrm, cudaStream_t s) {
+    k_reduce<<<1, 1024, 0, s>>>(part, xpart, nt, nrm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(const NormArgs& a, int count, int nmax, double* out, cudaStream_t s) {
+    k_norm2<<<count, 128, 2 * nmax * sizeof(double), s>>>(a, out);
+    return cudaGetLastError();
+}
+
+}  // namespace tsylv

@@ -1,12 +1,15 @@
-// Solve orchestration: structure read-back, schedule, graph capture/replay.
+// Solve orchestration: structure read-back, schedule, graph capture/replay,
+// mixed-precision refinement and the residual entry point.
 #include "solver.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
 
 #include "plan.h"
+#include "refine.h"
 
 namespace tsylv {
 
@@ -54,44 +57,76 @@ int map_err(int e) {
     return TSYLV_OK;
 }
 
-}  // namespace
+size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
-size_t solver_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o, bool transposed) {
-    (void)transposed;
-    if (!shape_ok(d, n)) return 0;
-    long long nn[kMaxD];
-    int nb[kMaxD];
+// Workspace of a refined solve / residual: the FP32 solve's layout followed by
+// the FP64 block tensors (B, X, R), FP64 coefficient tiles, their float-pair
+// splits (DF64 residual), the generalized residual's two ping-pong sets of
+// intermediates, and the reduction records.
+struct RefLayout {
+    Layout L32;
+    size_t Bt = 0, Xt = 0, Rt = 0, Xh = 0, Xl = 0;
+    size_t A64[kMaxD] = {}, C64[kMaxD] = {}, Ah[kMaxD] = {}, Al[kMaxD] = {}, Ch[kMaxD] = {}, Cl[kMaxD] = {};
+    size_t set[2][4] = {};
+    size_t part = 0, xpart = 0, xstat = 0, nrm = 0, nA = 0;
+    size_t total = 0;
+};
+
+RefLayout make_ref_layout(int d, const long long* n, const int* nb, bool gen, size_t tab_ints) {
+    RefLayout R;
+    R.L32 = make_layout(d, n, nb, gen, 4, tab_ints);
     const int te = tile_extent(d);
+    const size_t td = static_cast<size_t>(ipow(te, d)), tc = static_cast<size_t>(te) * te;
+    size_t nt = 1;
+    for (int mu = 0; mu < d; mu++) nt *= static_cast<size_t>(nb[mu]);
+    size_t o = R.L32.total;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = al256(o + bytes);
+        return at;
+    };
+    R.Bt = take(nt * td * 8);
+    R.Xt = take(nt * td * 8);
+    R.Rt = take(nt * td * 8);
+    R.Xh = take(nt * td * 4);
+    R.Xl = take(nt * td * 4);
     for (int mu = 0; mu < d; mu++) {
-        nn[mu] = n[mu];
-        nb[mu] = max_blocks(static_cast<int>(n[mu]), te);
-    }
-    Layout L = make_layout(d, nn, nb, gen && d >= 2, 8, tab_ints_bound(d, nn, nb));
-    size_t total = L.total;
-    if (o.host_io) {
-        size_t N = 1, coef = 0;
-        for (int mu = 0; mu < d; mu++) {
-            N *= static_cast<size_t>(n[mu]);
-            coef += static_cast<size_t>(n[mu]) * static_cast<size_t>(n[mu]);
+        const size_t ntri = static_cast<size_t>(nb[mu]) * (nb[mu] + 1) / 2;
+        R.A64[mu] = take(ntri * tc * 8);
+        R.Ah[mu] = take(ntri * tc * 4);
+        R.Al[mu] = take(ntri * tc * 4);
+        if (gen) {
+            R.C64[mu] = take(ntri * tc * 8);
+            R.Ch[mu] = take(ntri * tc * 4);
+            R.Cl[mu] = take(ntri * tc * 4);
         }
-        total += ((gen ? 2 : 1) * coef + 2 * N) * sizeof(double) + 4 * 256;
     }
-    return total;
+    if (gen && d >= 2)
+        for (int k = 0; k < 2; k++)
+            for (int j = 0; j < 4; j++) R.set[k][j] = take(nt * td * 8);
+    R.part = take(nt * 2 * 8);
+    R.xpart = take(nt * 8);
+    R.xstat = take(nt * 2 * 8);
+    R.nrm = take(8 * 8);
+    R.nA = take(2 * kMaxD * 8);
+    R.total = o;
+    return R;
 }
-
-namespace {
 
 struct Call {
     int d = 0;
-    bool gen = false, flip = false;
+    bool gen = false, flip = false, df = true;
     long long n[kMaxD] = {};
     const double* A[kMaxD] = {};
     const double* C[kMaxD] = {};
     const double* B = nullptr;
     double* X = nullptr;
+    const double* Xin = nullptr;  // tsylv_residual: the X to evaluate
+    double* Rout = nullptr;       // tsylv_residual: output R
     char* base = nullptr;
     std::shared_ptr<Plan> plan;
     Layout L;
+    RefLayout R;
     bool timing = false;
 };
 
@@ -100,29 +135,13 @@ inline cudaError_t mark(const Call& c, int i, cudaStream_t s) {
     return c.timing ? cudaEventRecordWithFlags(c.plan->ev[i], s, cudaEventRecordExternal) : cudaSuccess;
 }
 
-// Queue one FP64 solve of the planned block grid.
-cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
-    const Plan& p = *c.plan;
-    const Layout& L = c.L;
-    char* base = c.base;
-    GeomArgs g = geom_of(p, L, base, c.flip);
-    cudaError_t e;
-    if ((e = mark(c, 0, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(base + L.err, 0, 64, s)) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(base + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s)) !=
-        cudaSuccess)
-        return e;
-    for (int mu = 0; mu < p.d; mu++) {
-        if ((e = launch_pack_coef<double>(g, mu, c.A[mu], reinterpret_cast<double*>(base + L.At[mu]), false, s)) !=
-            cudaSuccess)
-            return e;
-        if (p.gen &&
-            (e = launch_pack_coef<double>(g, mu, c.C[mu], reinterpret_cast<double*>(base + L.Ct[mu]), true, s)) !=
-                cudaSuccess)
-            return e;
-    }
-    double* Xt = reinterpret_cast<double*>(base + L.X);
-    if ((e = launch_pack_tensor<double>(g, c.B, Xt, 1.0, s)) != cudaSuccess) return e;
+#define TRY(x)                            \
+    do {                                  \
+        cudaError_t e_ = (x);             \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
+WaveArgs wave_args(const Plan& p, const Layout& L, char* base) {
     WaveArgs wa{};
     const int* tab = reinterpret_cast<const int*>(base + L.tab);
     for (int mu = 0; mu < p.d; mu++) {
@@ -135,20 +154,239 @@ cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
         wa.P[mu] = p.gen && mu >= 1 ? base + L.P[mu] : nullptr;
         wa.G[mu] = p.gen && mu >= 1 ? base + L.G[mu] : nullptr;
     }
-    wa.X = Xt;
+    wa.X = base + L.X;
     wa.err = reinterpret_cast<int*>(base + L.err);
     wa.timeout_ns = kTimeoutNs;
-    if ((e = mark(c, 1, s)) != cudaSuccess) return e;
+    return wa;
+}
+
+template <typename T>
+cudaError_t enqueue_waves(const Plan& p, const Layout& L, char* base, cudaStream_t s) {
+    WaveArgs wa = wave_args(p, L, base);
+    const int* tab = reinterpret_cast<const int*>(base + L.tab);
     for (size_t w = 0; w < p.wave_off.size(); w++) {
         wa.tiles = tab + p.t_wave + p.wave_off[w];
         wa.ntiles = p.wave_cnt[w];
         wa.csize = p.wave_csize[w];
-        if ((e = launch_wave<double>(p.d, p.gen, kProdNative, wa, s)) != cudaSuccess) return e;
+        TRY(launch_wave<T>(p.d, p.gen, kProdNative, wa, s));
     }
-    if ((e = mark(c, 2, s)) != cudaSuccess) return e;
-    if ((e = launch_unpack_tensor<double>(g, Xt, c.X, s)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- FP64 solve
+
+cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    const Layout& L = c.L;
+    char* base = c.base;
+    GeomArgs g = geom_of(p, L, base, c.flip);
+    TRY(mark(c, 0, s));
+    TRY(cudaMemsetAsync(base + L.err, 0, 64, s));
+    TRY(cudaMemcpyAsync(base + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int mu = 0; mu < p.d; mu++) {
+        TRY(launch_pack_coef<double>(g, mu, c.A[mu], reinterpret_cast<double*>(base + L.At[mu]), false, s));
+        if (p.gen) TRY(launch_pack_coef<double>(g, mu, c.C[mu], reinterpret_cast<double*>(base + L.Ct[mu]), true, s));
+    }
+    double* Xt = reinterpret_cast<double*>(base + L.X);
+    TRY(launch_pack_tensor<double>(g, c.B, Xt, 1.0, s));
+    TRY(mark(c, 1, s));
+    TRY(enqueue_waves<double>(p, L, base, s));
+    TRY(mark(c, 2, s));
+    TRY(launch_unpack_tensor<double>(g, Xt, c.X, s));
     return mark(c, 3, s);
 }
+
+// ------------------------------------------------- residual R = B - A(X) (tiles)
+
+cudaError_t enqueue_residual(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    const RefLayout& R = c.R;
+    char* b = c.base;
+    ApplyArgs a{};
+    for (int mu = 0; mu < p.d; mu++) {
+        a.nb[mu] = p.nb[mu];
+        a.tstride[mu] = p.tstride[mu];
+        if (c.df) {
+            a.A[mu] = b + R.Ah[mu];
+            a.Al[mu] = b + R.Al[mu];
+            a.C[mu] = p.gen ? b + R.Ch[mu] : nullptr;
+            a.Cl[mu] = p.gen ? b + R.Cl[mu] : nullptr;
+        } else {
+            a.A[mu] = b + R.A64[mu];
+            a.C[mu] = p.gen ? b + R.C64[mu] : nullptr;
+        }
+    }
+    a.ntiles = p.ntiles;
+    a.B = reinterpret_cast<const double*>(b + R.Bt);
+    a.R = reinterpret_cast<double*>(b + R.Rt);
+    a.part = reinterpret_cast<double*>(b + R.part);
+    a.err = reinterpret_cast<int*>(b + R.L32.err);
+    a.timeout_ns = kTimeoutNs;
+    const void* xs = c.df ? static_cast<const void*>(b + R.Xh) : static_cast<const void*>(b + R.Xt);
+    const void* xsl = c.df ? static_cast<const void*>(b + R.Xl) : nullptr;
+    if (!p.gen) {
+        a.kind = kApplyLaplace;
+        a.s1 = xs;
+        a.s1l = xsl;
+        return c.df ? launch_apply<true>(p.d, a, s) : launch_apply<false>(p.d, a, s);
+    }
+    // Horner levels d-1 .. 0, ping-pong between the two intermediate sets
+    int cur = 0;
+    auto setp = [&](int k, int j) -> void* { return b + R.set[k][j]; };
+    a.kind = kApplyFirst;
+    a.mode = p.d - 1;
+    a.s1 = xs;
+    a.s1l = xsl;
+    a.o1 = setp(0, 0);
+    a.o1l = setp(0, 1);
+    a.o2 = setp(0, 2);
+    a.o2l = setp(0, 3);
+    TRY(c.df ? launch_apply<true>(p.d, a, s) : launch_apply<false>(p.d, a, s));
+    for (int l = p.d - 2; l >= 0; l--) {
+        a.kind = l == 0 ? kApplyFinal : kApplyMiddle;
+        a.mode = l;
+        a.s1 = setp(cur, 0);
+        a.s1l = setp(cur, 1);
+        a.s2 = setp(cur, 2);
+        a.s2l = setp(cur, 3);
+        a.o1 = setp(1 - cur, 0);
+        a.o1l = setp(1 - cur, 1);
+        a.o2 = setp(1 - cur, 2);
+        a.o2l = setp(1 - cur, 3);
+        TRY(c.df ? launch_apply<true>(p.d, a, s) : launch_apply<false>(p.d, a, s));
+        cur = 1 - cur;
+    }
+    return cudaSuccess;
+}
+
+// coefficient tiles of the residual (FP64, and their float-pair split)
+cudaError_t enqueue_coef64(const Call& c, const GeomArgs& g, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    const RefLayout& R = c.R;
+    char* b = c.base;
+    const long long tc = static_cast<long long>(p.tc);
+    for (int mu = 0; mu < p.d; mu++) {
+        const long long ntri = static_cast<long long>(p.nb[mu]) * (p.nb[mu] + 1) / 2;
+        TRY(launch_pack_coef<double>(g, mu, c.A[mu], reinterpret_cast<double*>(b + R.A64[mu]), false, s));
+        if (c.df)
+            TRY(launch_split(reinterpret_cast<double*>(b + R.A64[mu]), reinterpret_cast<float*>(b + R.Ah[mu]),
+                             reinterpret_cast<float*>(b + R.Al[mu]), ntri * tc, s));
+        if (p.gen) {
+            TRY(launch_pack_coef<double>(g, mu, c.C[mu], reinterpret_cast<double*>(b + R.C64[mu]), true, s));
+            if (c.df)
+                TRY(launch_split(reinterpret_cast<double*>(b + R.C64[mu]), reinterpret_cast<float*>(b + R.Ch[mu]),
+                                 reinterpret_cast<float*>(b + R.Cl[mu]), ntri * tc, s));
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_norms(const Call& c, cudaStream_t s) {
+    NormArgs na{};
+    int cnt = 0, nmax = 1;
+    for (int mu = 0; mu < c.d; mu++) {
+        na.M[cnt] = c.A[mu];
+        na.n[cnt] = static_cast<int>(c.n[mu]);
+        na.upper[cnt++] = 0;
+        nmax = std::max(nmax, static_cast<int>(c.n[mu]));
+    }
+    if (c.gen)
+        for (int mu = 0; mu < c.d; mu++) {
+            na.M[cnt] = c.C[mu];
+            na.n[cnt] = static_cast<int>(c.n[mu]);
+            na.upper[cnt++] = 1;
+        }
+    return launch_norm2(na, cnt, nmax, reinterpret_cast<double*>(c.base + c.R.nA), s);
+}
+
+// ---------------------------------------------------------- refined solve
+
+cudaError_t enqueue_ref_setup(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    const RefLayout& R = c.R;
+    const Layout& L = R.L32;
+    char* b = c.base;
+    GeomArgs g = geom_of(p, L, b, c.flip);
+    const long long nel = p.ntiles * p.td;
+    TRY(cudaMemsetAsync(b + L.err, 0, 64, s));
+    TRY(cudaMemcpyAsync(b + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int mu = 0; mu < p.d; mu++) {
+        TRY(launch_pack_coef<float>(g, mu, c.A[mu], reinterpret_cast<float*>(b + L.At[mu]), false, s));
+        if (p.gen) TRY(launch_pack_coef<float>(g, mu, c.C[mu], reinterpret_cast<float*>(b + L.Ct[mu]), true, s));
+    }
+    TRY(enqueue_coef64(c, g, s));
+    TRY(launch_pack_tensor<double>(g, c.B, reinterpret_cast<double*>(b + R.Bt), 1.0, s));
+    TRY(cudaMemcpyAsync(b + R.Rt, b + R.Bt, nel * 8, cudaMemcpyDeviceToDevice, s));
+    TRY(cudaMemsetAsync(b + R.Xt, 0, nel * 8, s));
+    TRY(cudaMemsetAsync(b + R.Xh, 0, nel * 4, s));
+    TRY(cudaMemsetAsync(b + R.Xl, 0, nel * 4, s));
+    TRY(launch_tile_stats(reinterpret_cast<double*>(b + R.Rt), reinterpret_cast<double*>(b + R.part), p.ntiles, p.td,
+                          s));
+    TRY(launch_reduce(reinterpret_cast<double*>(b + R.part), nullptr, p.ntiles, reinterpret_cast<double*>(b + R.nrm),
+                      s));
+    return enqueue_norms(c, s);
+}
+
+cudaError_t enqueue_ref_iter(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    const RefLayout& R = c.R;
+    const Layout& L = R.L32;
+    char* b = c.base;
+    const long long nel = p.ntiles * p.td;
+    const double* nrm = reinterpret_cast<const double*>(b + R.nrm);
+    TRY(mark(c, 0, s));
+    // low-precision solve of A(D) = R / max|R|
+    TRY(launch_scale_to_f32(reinterpret_cast<double*>(b + R.Rt), reinterpret_cast<float*>(b + L.X), nrm, nel, s));
+    TRY(enqueue_waves<float>(p, L, b, s));
+    // X += max|R| D  (FP64), its float-pair split, block sums of X^2
+    TRY(launch_update_x(reinterpret_cast<double*>(b + R.Xt), reinterpret_cast<float*>(b + L.X), nrm,
+                        c.df ? reinterpret_cast<float*>(b + R.Xh) : nullptr,
+                        c.df ? reinterpret_cast<float*>(b + R.Xl) : nullptr, reinterpret_cast<double*>(b + R.xpart),
+                        nel, p.td, s));
+    TRY(mark(c, 1, s));
+    // R = B - A(X) in FP64-accurate arithmetic
+    TRY(enqueue_residual(c, s));
+    TRY(mark(c, 2, s));
+    TRY(launch_reduce(reinterpret_cast<double*>(b + R.part), reinterpret_cast<double*>(b + R.xpart), p.ntiles,
+                      reinterpret_cast<double*>(b + R.nrm), s));
+    return mark(c, 3, s);
+}
+
+cudaError_t enqueue_ref_final(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    GeomArgs g = geom_of(p, c.R.L32, c.base, c.flip);
+    return launch_unpack_tensor<double>(g, reinterpret_cast<double*>(c.base + c.R.Xt), c.X, s);
+}
+
+// ------------------------------------------------------------- residual API
+
+cudaError_t enqueue_resid_api(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    const RefLayout& R = c.R;
+    const Layout& L = R.L32;
+    char* b = c.base;
+    GeomArgs g = geom_of(p, L, b, false);
+    const long long nel = p.ntiles * p.td;
+    TRY(cudaMemsetAsync(b + L.err, 0, 64, s));
+    TRY(cudaMemcpyAsync(b + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(enqueue_coef64(c, g, s));
+    TRY(launch_pack_tensor<double>(g, c.B, reinterpret_cast<double*>(b + R.Bt), 1.0, s));
+    TRY(launch_pack_tensor<double>(g, c.Xin, reinterpret_cast<double*>(b + R.Xt), 1.0, s));
+    if (c.df)
+        TRY(launch_split(reinterpret_cast<double*>(b + R.Xt), reinterpret_cast<float*>(b + R.Xh),
+                         reinterpret_cast<float*>(b + R.Xl), nel, s));
+    TRY(launch_tile_stats(reinterpret_cast<double*>(b + R.Xt), reinterpret_cast<double*>(b + R.xstat), p.ntiles, p.td,
+                          s));
+    TRY(launch_reduce(reinterpret_cast<double*>(b + R.xstat), nullptr, p.ntiles,
+                      reinterpret_cast<double*>(b + R.nrm) + 4, s));
+    TRY(enqueue_residual(c, s));
+    TRY(launch_reduce(reinterpret_cast<double*>(b + R.part), nullptr, p.ntiles, reinterpret_cast<double*>(b + R.nrm),
+                      s));
+    TRY(enqueue_norms(c, s));
+    return launch_unpack_tensor<double>(g, reinterpret_cast<double*>(b + R.Rt), c.Rout, s);
+}
+
+// ---------------------------------------------------------- graph runner
 
 int run_enqueue(Plan& p, const std::vector<const void*>& key, bool use_graph, cudaStream_t stream,
                 cudaError_t (*fn)(const Call&, cudaStream_t), const Call& c) {
@@ -178,7 +416,7 @@ int run_enqueue(Plan& p, const std::vector<const void*>& key, bool use_graph, cu
             e = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-            if (p.graphs.size() >= 16) {
+            if (p.graphs.size() >= 32) {
                 cudaGraphExecDestroy(p.graphs.front().exec);
                 p.graphs.erase(p.graphs.begin());
             }
@@ -189,7 +427,126 @@ int run_enqueue(Plan& p, const std::vector<const void*>& key, bool use_graph, cu
     return 0;
 }
 
+int prepare_kernels() {
+    static std::mutex pm;
+    static bool prepared[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(pm);
+    if (dev >= 0 && dev < 64 && !prepared[dev]) {
+        cudaError_t e = prepare_wave<double>();
+        if (e == cudaSuccess) e = prepare_wave<float>();
+        if (e == cudaSuccess) e = prepare_apply<false>();
+        if (e == cudaSuccess) e = prepare_apply<true>();
+        if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+        prepared[dev] = true;
+    }
+    return 0;
+}
+
+// 2x2 block structure of every A_mu (sub-diagonal read back through the
+// workspace), validated; flipped for the transposed equation.
+int read_structure(int d, const long long* n, const double* const* A, char* base, bool flip, cudaStream_t stream,
+                   std::vector<uint8_t>& sub) {
+    size_t nsub = 0;
+    for (int mu = 0; mu < d; mu++) nsub += static_cast<size_t>(n[mu] - 1);
+    std::vector<double> hsub(nsub + 1, 0.0);
+    const size_t sub_off = 256;  // Layout::sub does not depend on the block counts
+    double* dsub = reinterpret_cast<double*>(base + sub_off);
+    cudaError_t e;
+    if (nsub > 0) {
+        if ((e = launch_gather_subdiag(d, n, A, dsub, stream)) != cudaSuccess) return cuda_fail(e, "gather sub-diagonal");
+        if ((e = cudaMemcpyAsync(hsub.data(), dsub, nsub * sizeof(double), cudaMemcpyDeviceToHost, stream)) !=
+            cudaSuccess)
+            return cuda_fail(e, "read sub-diagonal");
+    }
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize before planning");
+    sub.assign(nsub + 1, 0);
+    size_t off = 0;
+    for (int mu = 0; mu < d; mu++) {
+        const long long m = n[mu];
+        for (long long i = 0; i + 1 < m; i++) {
+            const size_t src = flip ? off + static_cast<size_t>(m - 2 - i) : off + static_cast<size_t>(i);
+            sub[off + i] = hsub[src] != 0.0 ? 1 : 0;
+        }
+        for (long long i = 0; i + 2 < m; i++)
+            if (sub[off + i] && sub[off + i + 1]) return -3;  // not quasi-triangular
+        off += static_cast<size_t>(m - 1);
+    }
+    return 0;
+}
+
+std::vector<const void*> make_key(const Call& c, int tag) {
+    std::vector<const void*> key;
+    for (int mu = 0; mu < c.d; mu++) {
+        key.push_back(c.A[mu]);
+        key.push_back(c.C[mu]);
+    }
+    key.push_back(c.B);
+    key.push_back(c.X);
+    key.push_back(c.Xin);
+    key.push_back(c.Rout);
+    key.push_back(c.base);
+    key.push_back(reinterpret_cast<const void*>(static_cast<uintptr_t>(tag)));
+    return key;
+}
+
+int ensure_events(Call& c) {
+    if (c.timing && !c.plan->ev[0])
+        for (auto& ev : c.plan->ev)
+            if (cudaError_t e = cudaEventCreate(&ev); e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    return 0;
+}
+
+double norm_op(const Call& c, const double* nA) {
+    double s = 0;
+    for (int mu = 0; mu < c.d; mu++) {
+        double t = nA[mu];
+        if (c.gen)
+            for (int eta = 0; eta < c.d; eta++)
+                if (eta != mu) t *= nA[c.d + eta];
+        s += t;
+    }
+    return s;
+}
+
 }  // namespace
+
+size_t solver_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o, bool transposed) {
+    (void)transposed;
+    if (!shape_ok(d, n)) return 0;
+    long long nn[kMaxD];
+    int nb[kMaxD];
+    const int te = tile_extent(d);
+    for (int mu = 0; mu < d; mu++) {
+        nn[mu] = n[mu];
+        nb[mu] = max_blocks(static_cast<int>(n[mu]), te);
+    }
+    const bool g = gen && d >= 2;
+    size_t total = o.precision == TSYLV_FP64 ? make_layout(d, nn, nb, g, 8, tab_ints_bound(d, nn, nb)).total
+                                             : make_ref_layout(d, nn, nb, g, tab_ints_bound(d, nn, nb)).total;
+    if (o.host_io) {
+        size_t N = 1, coef = 0;
+        for (int mu = 0; mu < d; mu++) {
+            N *= static_cast<size_t>(n[mu]);
+            coef += static_cast<size_t>(n[mu]) * static_cast<size_t>(n[mu]);
+        }
+        total += ((gen ? 2 : 1) * coef + 2 * N) * sizeof(double) + 4 * 256;
+    }
+    return total;
+}
+
+size_t solver_residual_workspace_bytes(int d, const int64_t* n, bool gen) {
+    if (!shape_ok(d, n)) return 0;
+    long long nn[kMaxD];
+    int nb[kMaxD];
+    const int te = tile_extent(d);
+    for (int mu = 0; mu < d; mu++) {
+        nn[mu] = n[mu];
+        nb[mu] = max_blocks(static_cast<int>(n[mu]), te);
+    }
+    return make_ref_layout(d, nn, nb, gen && d >= 2, tab_ints_bound(d, nn, nb)).total;
+}
 
 int solver_solve(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B, double* X,
                  void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream,
@@ -214,13 +571,15 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (o.precision < TSYLV_FP64 || o.precision > TSYLV_BF16_REFINED || o.max_refine < 0 || !(o.tol > 0) ||
         (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < 0)
         return -(8 + sh);
-    if (o.precision != TSYLV_FP64 || o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d)))
-        return TSYLV_EUNSUPPORTED;
+    if (o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d))) return TSYLV_EUNSUPPORTED;
+    if (o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) return TSYLV_EUNSUPPORTED;
+    const bool refined = o.precision != TSYLV_FP64;
 
     Call c;
     c.d = d;
     c.gen = gen && d >= 2;
     c.flip = transposed;
+    c.df = o.residual == TSYLV_RESID_DF64;
     for (int mu = 0; mu < d; mu++) {
         c.n[mu] = n[mu];
         c.A[mu] = A[mu];
@@ -229,103 +588,195 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     c.B = B;
     c.X = X;
     c.base = static_cast<char*>(work);
-
     (void)cudaGetLastError();  // launch checks below must not see errors of earlier, unrelated calls
 
-    // 2x2 block structure: sub-diagonal of every A_mu, read back once per call
-    size_t nsub = 0;
-    for (int mu = 0; mu < d; mu++) nsub += static_cast<size_t>(n[mu] - 1);
-    std::vector<double> hsub(nsub + 1, 0.0);
-    {
-        const size_t sub_off = 256;  // Layout::sub does not depend on the block counts
-        double* dsub = reinterpret_cast<double*>(c.base + sub_off);
-        if (nsub > 0) {
-            cudaError_t e;
-            if ((e = launch_gather_subdiag(d, c.n, c.A, dsub, stream)) != cudaSuccess)
-                return cuda_fail(e, "gather sub-diagonal");
-            if ((e = cudaMemcpyAsync(hsub.data(), dsub, nsub * sizeof(double), cudaMemcpyDeviceToHost, stream)) !=
-                cudaSuccess)
-                return cuda_fail(e, "read sub-diagonal");
-        }
-        cudaError_t e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) return cuda_fail(e, "synchronize before planning");
-    }
-    std::vector<uint8_t> sub(nsub + 1, 0);
-    {
-        size_t off = 0;
-        for (int mu = 0; mu < d; mu++) {
-            const long long m = n[mu];
-            for (long long i = 0; i + 1 < m; i++) {
-                const size_t src = transposed ? off + static_cast<size_t>(m - 2 - i) : off + static_cast<size_t>(i);
-                sub[off + i] = hsub[src] != 0.0 ? 1 : 0;
-            }
-            for (long long i = 0; i + 2 < m; i++)
-                if (sub[off + i] && sub[off + i + 1]) return -3;  // not quasi-triangular
-            off += static_cast<size_t>(m - 1);
-        }
-    }
-    c.plan = get_plan(d, c.n, c.gen, 8, o.split, &sub);
+    std::vector<uint8_t> sub;
+    if (int st = read_structure(d, c.n, c.A, c.base, transposed, stream, sub)) return st;
+    c.plan = get_plan(d, c.n, c.gen, refined ? 4 : 8, o.split, &sub);
     if (!c.plan) return cuda_fail_msg("plan: pinned host allocation");
-    c.L = make_layout(d, c.n, c.plan->nb, c.gen, 8, c.plan->tab.size());
-    if (c.L.total > work_bytes) return -(7 + sh);
+    if (int st = prepare_kernels()) return st;
     c.timing = o.timing != 0;
-    if (c.timing && !c.plan->ev[0])
-        for (auto& ev : c.plan->ev)
-            if (cudaError_t e = cudaEventCreate(&ev); e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if (int st = ensure_events(c)) return st;
+    const int tagbase = (transposed ? 1 : 0) | (c.timing ? 2 : 0) | (c.df ? 4 : 0);
 
-    {
-        static std::mutex pm;
-        static bool prepared[64] = {};
-        int dev = 0;
-        cudaGetDevice(&dev);
-        std::lock_guard<std::mutex> lk(pm);
-        if (dev >= 0 && dev < 64 && !prepared[dev]) {
-            cudaError_t e = prepare_wave<double>();
-            if (e == cudaSuccess) e = prepare_wave<float>();
-            if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
-            prepared[dev] = true;
+    if (!refined) {
+        c.L = make_layout(d, c.n, c.plan->nb, c.gen, 8, c.plan->tab.size());
+        if (c.L.total > work_bytes) return -(7 + sh);
+        int st = run_enqueue(*c.plan, make_key(c, tagbase), o.use_graph != 0, stream, enqueue_fp64, c);
+        if (st) return st;
+        int herr = 0;
+        if (cudaError_t e = cudaMemcpyAsync(&herr, c.base + c.L.err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+            e != cudaSuccess)
+            return cuda_fail(e, "read status");
+        if (cudaError_t e = cudaStreamSynchronize(stream); e != cudaSuccess)
+            return cuda_fail(e, "synchronize after solve");
+        if (info) {
+            std::memset(info, 0, sizeof(*info));
+            info->waves = static_cast<int>(c.plan->wave_off.size());
+            info->launches = info->waves + d * (c.gen ? 2 : 1) + 2;
+            info->tiles = static_cast<int>(c.plan->ntiles);
+            info->resid = -1;
+            info->norm_A = -1;
+            info->flops = c.plan->flops;
+            if (c.timing) {
+                float a = -1, b = -1;
+                if (cudaEventElapsedTime(&a, c.plan->ev[0], c.plan->ev[3]) != cudaSuccess) a = -1;
+                if (cudaEventElapsedTime(&b, c.plan->ev[1], c.plan->ev[2]) != cudaSuccess) b = -1;
+                (void)cudaGetLastError();
+                info->t_total_ms = a;
+                info->t_waves_ms = b;
+            }
+        }
+        return map_err(herr);
+    }
+
+    // ---- mixed-precision refinement
+    c.R = make_ref_layout(d, c.n, c.plan->nb, c.gen, c.plan->tab.size());
+    if (c.R.total > work_bytes) return -(7 + sh);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (c.timing) {
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        cudaEventRecord(t0, stream);
+    }
+    int st = run_enqueue(*c.plan, make_key(c, tagbase | 16), o.use_graph != 0, stream, enqueue_ref_setup, c);
+    if (st) return st;
+    double hA[2 * kMaxD] = {}, hn[3] = {};
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(hA, c.base + c.R.nA, 2 * kMaxD * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_fail(e, "read norms");
+    if ((e = cudaMemcpyAsync(hn, c.base + c.R.nrm, 3 * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_fail(e, "read norms");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize after set-up");
+    const double nA = norm_op(c, hA);
+    int iters = 0, status = TSYLV_ENOCONV;
+    double rho = -1, t_resid = 0, t_waves = 0;
+    if (!(hn[1] > 0)) {
+        status = TSYLV_OK;  // B = 0: X = 0
+        rho = 0;
+    } else {
+        double prev = HUGE_VAL;
+        int stall = 0;
+        for (int it = 0; it < std::max(1, o.max_refine); it++) {
+            st = run_enqueue(*c.plan, make_key(c, tagbase | 32), o.use_graph != 0, stream, enqueue_ref_iter, c);
+            if (st) return st;
+            if ((e = cudaMemcpyAsync(hn, c.base + c.R.nrm, 3 * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+                return cuda_fail(e, "read residual norm");
+            if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize in refinement");
+            iters = it + 1;
+            if (c.timing) {
+                float a = 0, b2 = 0;
+                if (cudaEventElapsedTime(&a, c.plan->ev[1], c.plan->ev[2]) == cudaSuccess) t_resid += a;
+                if (cudaEventElapsedTime(&b2, c.plan->ev[0], c.plan->ev[1]) == cudaSuccess) t_waves += b2;
+                (void)cudaGetLastError();
+            }
+            const double xn = std::sqrt(hn[2]);
+            rho = (xn > 0 && nA > 0) ? std::sqrt(hn[0]) / (nA * xn) : 0.0;
+            if (!std::isfinite(rho)) {
+                status = TSYLV_ENONFINITE;
+                break;
+            }
+            if (rho <= o.tol) {
+                status = TSYLV_OK;
+                break;
+            }
+            if (rho > 0.5 * prev) {
+                if (++stall >= 2) break;
+            } else {
+                stall = 0;
+            }
+            prev = rho;
         }
     }
-    std::vector<const void*> key;
-    for (int mu = 0; mu < d; mu++) {
-        key.push_back(c.A[mu]);
-        key.push_back(c.C[mu]);
-    }
-    key.push_back(B);
-    key.push_back(X);
-    key.push_back(work);
-    key.push_back(reinterpret_cast<const void*>(static_cast<uintptr_t>((transposed ? 1 : 0) | (c.timing ? 2 : 0))));
-    int st = run_enqueue(*c.plan, key, o.use_graph != 0, stream, enqueue_fp64, c);
+    st = run_enqueue(*c.plan, make_key(c, tagbase | 64), o.use_graph != 0, stream, enqueue_ref_final, c);
     if (st) return st;
     int herr = 0;
-    if (cudaError_t e = cudaMemcpyAsync(&herr, c.base + c.L.err, sizeof(int), cudaMemcpyDeviceToHost, stream);
-        e != cudaSuccess)
+    if ((e = cudaMemcpyAsync(&herr, c.base + c.R.L32.err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
         return cuda_fail(e, "read status");
-    if (cudaError_t e = cudaStreamSynchronize(stream); e != cudaSuccess) return cuda_fail(e, "synchronize after solve");
+    if (c.timing) cudaEventRecord(t1, stream);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize after refinement");
     if (info) {
         std::memset(info, 0, sizeof(*info));
-        info->iterations = 0;
+        info->iterations = iters;
         info->waves = static_cast<int>(c.plan->wave_off.size());
-        info->launches = info->waves + d * (c.gen ? 2 : 1) + 2;
+        info->launches = iters * (info->waves + (c.gen ? d : 1) + 4) + 4 * d + 8;
         info->tiles = static_cast<int>(c.plan->ntiles);
-        info->resid = -1;
-        info->norm_A = -1;
-        info->flops = c.plan->flops;
+        info->resid = rho;
+        info->norm_A = nA;
+        info->flops = c.plan->flops * iters;
         if (c.timing) {
-            float a = -1, b = -1;
-            if (cudaEventElapsedTime(&a, c.plan->ev[0], c.plan->ev[3]) != cudaSuccess) a = -1;
-            if (cudaEventElapsedTime(&b, c.plan->ev[1], c.plan->ev[2]) != cudaSuccess) b = -1;
+            float a = -1;
+            if (cudaEventElapsedTime(&a, t0, t1) != cudaSuccess) a = -1;
             (void)cudaGetLastError();
             info->t_total_ms = a;
-            info->t_waves_ms = b;
+            info->t_resid_ms = t_resid;
+            info->t_waves_ms = t_waves;
         }
     }
-    return map_err(herr);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    const int ms = map_err(herr);
+    if (ms == TSYLV_ETIMEOUT || ms == TSYLV_ECUDA) return ms;
+    if (status == TSYLV_OK && ms == TSYLV_ESINGULAR) return ms;
+    return status;
 }
 
-int solver_residual(int, const int64_t*, const double* const*, const double* const*, const double*, const double*,
-                    double*, double*, void*, size_t, const tsylv_opts*, cudaStream_t) {
-    return TSYLV_EUNSUPPORTED;
+int solver_residual(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,
+                    const double* X, double* R, double* rel, void* work, size_t work_bytes, const tsylv_opts* opts,
+                    cudaStream_t stream) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    if (d < 1 || d > kMaxD) return -1;
+    if (!shape_ok(d, n)) return -2;
+    if (!A) return -3;
+    for (int mu = 0; mu < d; mu++)
+        if (!A[mu]) return -3;
+    const bool gen = C != nullptr;
+    if (gen)
+        for (int mu = 0; mu < d; mu++)
+            if (!C[mu]) return -4;
+    if (!B) return -5;
+    if (!X) return -6;
+    if (!R) return -7;
+    if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -9;
+    if (work_bytes < solver_residual_workspace_bytes(d, n, gen)) return -10;
+    if (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) return -11;
+    Call c;
+    c.d = d;
+    c.gen = gen && d >= 2;
+    c.df = o.residual == TSYLV_RESID_DF64;
+    for (int mu = 0; mu < d; mu++) {
+        c.n[mu] = n[mu];
+        c.A[mu] = A[mu];
+        c.C[mu] = gen ? C[mu] : nullptr;
+    }
+    c.B = B;
+    c.Xin = X;
+    c.Rout = R;
+    c.base = static_cast<char*>(work);
+    (void)cudaGetLastError();
+    std::vector<uint8_t> sub;
+    if (int st = read_structure(d, c.n, c.A, c.base, false, stream, sub)) return st;
+    c.plan = get_plan(d, c.n, c.gen, 4, 0, &sub);
+    if (!c.plan) return cuda_fail_msg("plan: pinned host allocation");
+    if (int st = prepare_kernels()) return st;
+    c.R = make_ref_layout(d, c.n, c.plan->nb, c.gen, c.plan->tab.size());
+    if (c.R.total > work_bytes) return -10;
+    int st = run_enqueue(*c.plan, make_key(c, (c.df ? 4 : 0) | 128), o.use_graph != 0, stream, enqueue_resid_api, c);
+    if (st) return st;
+    double hn[8] = {}, hA[2 * kMaxD] = {};
+    int herr = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(hn, c.base + c.R.nrm, 8 * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hA, c.base + c.R.nA, 2 * kMaxD * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&herr, c.base + c.R.L32.err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_fail(e, "read residual norms");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize after residual");
+    if (rel) {
+        const double nA = norm_op(c, hA), xn = std::sqrt(hn[4]);
+        *rel = (nA > 0 && xn > 0) ? std::sqrt(hn[0]) / (nA * xn) : 0.0;
+    }
+    return map_err(herr);
 }
 
 size_t solver_backward_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o) {

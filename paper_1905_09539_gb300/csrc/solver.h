@@ -9,6 +9,7 @@ size_t solver_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opt
 int solver_solve(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B, double* X,
                  void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream,
                  bool gen, bool transposed);
+size_t solver_residual_workspace_bytes(int d, const int64_t* n, bool gen);
 int solver_residual(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,
                     const double* X, double* R, double* rel, void* work, size_t work_bytes, const tsylv_opts* opts,
                     cudaStream_t stream);

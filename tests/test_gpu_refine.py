@@ -1,0 +1,104 @@
+"""Residual and mixed-precision refinement on the GPU, against the oracle.
+
+Tolerances: the residual entries agree with the oracle's B - A(X) to
+1e-12 of max|A(X)| (FP64: rounding of two different summation orders;
+DF64: plus the 2^-48 representation error of its float pairs).  A refined
+solve must reach ||B - A(X)|| / (||A|| ||X||) <= 1e-12; its forward error
+against the FP64 oracle is then bounded by cond(A) * 1e-12 (cond <= ~20 for
+these coefficient distributions), tested at 1e-10.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from tests.gpu_helpers import norm_op, rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ts():
+    import paper_1905_09539_gb300 as m
+    m.load()
+    return m
+
+
+SHAPES = [(2, (23, 19)), (3, (17, 12, 9)), (3, (33, 30, 31)), (4, (9, 7, 5, 6))]
+
+
+@pytest.mark.parametrize("resid", [0, 1])
+@pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("d,shape", SHAPES)
+def test_residual_matches_oracle(ts, d, shape, gen, resid):
+    p = synthetic.problem(31, shape, generalized=gen, force_blocks=[[n // 2 - 1] if n > 4 else [] for n in shape])
+    rng = np.random.default_rng(5)
+    X = np.asfortranarray(rng.standard_normal(shape))
+    AX = oracle.apply(p["A"], X, p["C"])
+    Ro = p["B"] - AX
+    A = [to_dev(a) for a in p["A"]]
+    C = [to_dev(c) for c in p["C"]] if gen else None
+    R, rel, st = ts.tsylv_residual(A, to_dev(p["B"]), to_dev(X), C, residual=resid)
+    assert st == 0
+    Rg = to_host(R)
+    assert np.max(np.abs(Rg - Ro)) <= 1e-12 * np.max(np.abs(AX))
+    relo = np.linalg.norm(Ro) / (norm_op(p["A"], p["C"]) * np.linalg.norm(X))
+    assert abs(rel - relo) <= 1e-2 * relo  # power-iteration estimates of the 2-norms
+
+
+@pytest.mark.parametrize("resid", [0, 1])
+@pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("d,shape", SHAPES + [(3, (64, 64, 64))])
+def test_fp32_refined_solve(ts, d, shape, gen, resid):
+    p = synthetic.problem(32, shape, generalized=gen, force_blocks=[[n // 2 - 1] if n > 4 else [] for n in shape])
+    Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=8)
+    A = [to_dev(a) for a in p["A"]]
+    info = ts.Info()
+    if gen:
+        X, st = ts.gtsylv_solve(A, [to_dev(c) for c in p["C"]], to_dev(p["B"]), precision=ts.TSYLV_FP32_REFINED,
+                                residual=resid, info=info)
+    else:
+        X, st = ts.tsylv_solve(A, to_dev(p["B"]), precision=ts.TSYLV_FP32_REFINED, residual=resid, info=info)
+    assert st == 0
+    assert 0 < info.resid <= 1e-12
+    assert 1 <= info.iterations <= 4
+    Xg = to_host(X)
+    assert rel_err(Xg, Xo) <= 1e-10
+    # the residual the solver reports is the one the oracle sees
+    R = p["B"] - oracle.apply(p["A"], Xg, p["C"])
+    rho = np.linalg.norm(R) / (norm_op(p["A"], p["C"]) * np.linalg.norm(Xg))
+    assert rho <= 2e-12
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_refined_transposed(ts, gen):
+    shape = (19, 17, 13)
+    p = synthetic.problem(33, shape, generalized=gen, force_blocks=[[8], [7], [5]])
+    Lo = oracle.solve_backsub(p["A"], p["B"], p["C"], transpose=True)
+    A = [to_dev(a) for a in p["A"]]
+    info = ts.Info()
+    if gen:
+        L, st = ts.gtsylv_solve_transposed(A, [to_dev(c) for c in p["C"]], to_dev(p["B"]),
+                                           precision=ts.TSYLV_FP32_REFINED, info=info)
+    else:
+        L, st = ts.tsylv_solve_transposed(A, to_dev(p["B"]), precision=ts.TSYLV_FP32_REFINED, info=info)
+    assert st == 0 and info.resid <= 1e-12
+    assert rel_err(to_host(L), Lo) <= 1e-10
+
+
+def test_refined_zero_rhs(ts):
+    p = synthetic.problem(34, (12, 11, 10))
+    B = np.zeros((12, 11, 10), order="F")
+    X, st = ts.tsylv_solve([to_dev(a) for a in p["A"]], to_dev(B), precision=ts.TSYLV_FP32_REFINED)
+    assert st == 0
+    assert np.all(to_host(X) == 0)
+
+
+def test_refined_iteration_cap(ts):
+    # one step cannot reach 1e-12 from FP32 solves: ENOCONV, last iterate returned
+    p = synthetic.problem(35, (24, 20, 16))
+    info = ts.Info()
+    X, st = ts.tsylv_solve([to_dev(a) for a in p["A"]], to_dev(p["B"]), precision=ts.TSYLV_FP32_REFINED,
+                           max_refine=1, check=False, info=info)
+    assert st == ts._lib.TSYLV_ENOCONV
+    assert info.iterations == 1 and 1e-12 < info.resid < 1e-4
