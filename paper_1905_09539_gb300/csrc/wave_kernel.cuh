@@ -50,7 +50,8 @@ struct WaveCfg {
     static constexpr size_t oMeta = oBar + 16;
     // meta: gs, gl, gidx [D][TE]; ng, bs [D]; flag [4]; coupled-group lists
     static constexpr int MAXSTEP = D * TE;
-    static constexpr size_t smem = oMeta + (3 * D * TE + 3 * D + 4 + 3 * MAXSTEP + 1 + 2 * (TD / 2 + 1)) * sizeof(int);
+    static constexpr size_t smem =
+        oMeta + (3 * D * TE + 3 * D + 4 + 3 * MAXSTEP + 1 + 2 * (TD / 2 + 1) + 3 * MAXSTEP + 1 + TD) * sizeof(int);
     static constexpr int slotP(int l) { return 2 * (D - 1 - l); }
     static constexpr int slotG(int l) { return 2 * (D - 1 - l) + 1; }
 };
@@ -246,6 +247,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
         r = sm.Rs[o] - sm.Lin[o];
 #pragma unroll
         for (int k = 0; k < S; k++) {
+            if (minv != nullptr) { row[k] = 0; continue; }
             T e = 0;
 #pragma unroll
             for (int mu = 0; mu < D; mu++) {
@@ -295,6 +297,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
         r = sm.Rs[o] - of;
 #pragma unroll
         for (int k = 0; k < S; k++) {
+            if (minv != nullptr) { row[k] = 0; continue; }
             T e = 0;
 #pragma unroll
             for (int mu = 0; mu < D; mu++) {
@@ -442,14 +445,15 @@ __device__ int warp_group(const TileSmem<T, D, GEN>& sm, int e, const T* minv) {
     }
 }
 
-// After the groups of anti-diagonal t are solved: add their contributions to
-// the running line sums L (registers) of element e owned by this thread,
-// which lies on one of their mode lines (the group of e has index sum below t).
-// The products of the different modes are independent; each slot receives
-// one read-modify-write.
+// Running line sums of element e (owned by this thread) when its
+// anti-diagonal comes: along every mode, the products of the diagonal-block
+// coefficients with the solved positions beyond e's group (the solution X for
+// the Laplace form; X, P_{l+1}, G_{l+1} for the levels of the generalized
+// recurrence).  The modes are independent and each sum runs as two
+// interleaved chains, so the latency is that of a few multiply-adds.
 template <typename T, int D, bool GEN>
-__device__ __forceinline__ void push_lines(const TileSmem<T, D, GEN>& sm, int t, int e, const int (&u)[D],
-                                           const int (&g)[D], int sg, T (&L)[WaveCfg<T, D, GEN>::NACC]) {
+__device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e, const int (&u)[D], const int (&g)[D],
+                                           T (&L)[WaveCfg<T, D, GEN>::NACC]) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int TC = TE * TE;
@@ -458,46 +462,44 @@ __device__ __forceinline__ void push_lines(const TileSmem<T, D, GEN>& sm, int t,
     T lap[D];
 #pragma unroll
     for (int mu = 0; mu < D; mu++) {
-        lap[mu] = T(0);
-        const int src = t - (sg - g[mu]);
-        if (src >= sm.ng[mu]) continue;
-        const int k0 = sm.gs[mu * TE + src], kl = sm.gl[mu * TE + src];
         const int st = ipow(TE, mu);
-        T s1 = T(0), s2 = T(0), s3 = T(0);
-        for (int k = k0; k < k0 + kl; k++) {
+        const int k0 = sm.gs[mu * TE + g[mu]] + sm.gl[mu * TE + g[mu]];  // first index beyond the group
+        const int kb = sm.bs[mu];
+        T a0 = 0, a1 = 0, b0 = 0, b1 = 0, c0 = 0, c1 = 0;
+#pragma unroll 2
+        for (int k = k0; k < kb; k++) {
             const int v = e + (k - u[mu]) * st;
             const T dv = sm.Ds[mu * TC + u[mu] + TE * k];
+            const bool odd = k & 1;
             if constexpr (!GEN) {
-                s1 += dv * Xs[v];
+                const T t = dv * Xs[v];
+                if (odd) a1 += t; else a0 += t;
             } else {
                 const T ev = sm.Es[mu * TC + u[mu] + TE * k];
                 if (mu == D - 1) {
                     const T xv = Xs[v];
-                    s1 += ev * xv;
-                    s2 += dv * xv;
+                    if (odd) { a1 += ev * xv; b1 += dv * xv; } else { a0 += ev * xv; b0 += dv * xv; }
                 } else if (mu >= 1) {
                     const T pv = sm.Pin[mu * TD + v], gv = sm.Gin[mu * TD + v];  // level mu + 1
-                    s1 += ev * pv;
-                    s2 += ev * gv;
-                    s3 += dv * pv;
+                    if (odd) { a1 += ev * pv; b1 += ev * gv; c1 += dv * pv; }
+                    else { a0 += ev * pv; b0 += ev * gv; c0 += dv * pv; }
                 } else {
                     const T pv = sm.Pin[v], gv = sm.Gin[v];                       // level 1
-                    s1 += ev * gv;
-                    s2 += dv * pv;
+                    if (odd) { a1 += ev * gv; b1 += dv * pv; } else { a0 += ev * gv; b0 += dv * pv; }
                 }
             }
         }
         if constexpr (!GEN) {
-            lap[mu] = s1;
+            lap[mu] = a0 + a1;
         } else {
             if (mu == D - 1) {
-                L[C::slotP(D - 1)] += s1;
-                L[C::slotG(D - 1)] += s2;
+                L[C::slotP(D - 1)] = a0 + a1;
+                L[C::slotG(D - 1)] = b0 + b1;
             } else if (mu >= 1) {
-                L[C::slotP(mu)] += s1;
-                L[C::slotG(mu)] += s2 + s3;
+                L[C::slotP(mu)] = a0 + a1;
+                L[C::slotG(mu)] = (b0 + b1) + (c0 + c1);
             } else {
-                L[C::NACC - 1] += s1 + s2;
+                L[C::NACC - 1] = (a0 + a1) + (b0 + b1);
             }
         }
     }
@@ -505,7 +507,7 @@ __device__ __forceinline__ void push_lines(const TileSmem<T, D, GEN>& sm, int t,
         T sum = lap[0];
 #pragma unroll
         for (int mu = 1; mu < D; mu++) sum += lap[mu];
-        L[0] += sum;
+        L[0] = sum;
     }
 }
 
@@ -791,8 +793,12 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
     int* cg_fill = cg_off + C::MAXSTEP + 1;
     int* cg_list = cg_fill + C::MAXSTEP;
     int* cg_moff = cg_list + (TD / 2 + 1);  // offset of each group's inverse (-1: none)
+    int* act_cnt = cg_moff + (TD / 2 + 1);  // elements per anti-diagonal
+    int* act_off = act_cnt + C::MAXSTEP;
+    int* act_fill = act_off + C::MAXSTEP + 1;
+    int* act_list = act_fill + C::MAXSTEP;  // element | (member of a coupled group) << 16
     T* Minv = sbase + C::oMinv;
-    for (int i = tid; i < C::MAXSTEP; i += kThreads) { cg_cnt[i] = 0; cg_fill[i] = 0; }
+    for (int i = tid; i < C::MAXSTEP; i += kThreads) { cg_cnt[i] = 0; cg_fill[i] = 0; act_cnt[i] = 0; act_fill[i] = 0; }
     if (GEN)
         for (int e = tid; e < C::NL * TD; e += kThreads) { Pin[e] = T(0); Gin[e] = T(0); }
     if (tid < D) bs[tid] = a.bsize[tid][I[tid]];
@@ -917,18 +923,28 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
 #pragma unroll
     for (int mu = 0; mu < D; mu++) nsum += ng[mu];
     // coupled groups, bucketed by anti-diagonal (solved one warp per group)
+    // and all elements, bucketed the same way (each anti-diagonal's elements
+    // are handled by the first threads, so idle warps issue nothing)
 #pragma unroll
-    for (int q = 0; q < EPT; q++)
+    for (int q = 0; q < EPT; q++) {
         if (lead[q]) atomicAdd(&cg_cnt[sq[q]], 1);
+        if (okq[q]) atomicAdd(&act_cnt[sq[q]], 1);
+    }
     __syncthreads();
     if (tid == 0) {
         cg_off[0] = 0;
         for (int i = 0; i < C::MAXSTEP; i++) cg_off[i + 1] = cg_off[i] + cg_cnt[i];
+    } else if (tid == 32) {
+        act_off[0] = 0;
+        for (int i = 0; i < C::MAXSTEP; i++) act_off[i + 1] = act_off[i] + act_cnt[i];
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < EPT; q++)
+    for (int q = 0; q < EPT; q++) {
         if (lead[q]) cg_list[cg_off[sq[q]] + atomicAdd(&cg_fill[sq[q]], 1)] = tid + q * kThreads;
+        if (okq[q])
+            act_list[act_off[sq[q]] + atomicAdd(&act_fill[sq[q]], 1)] = (tid + q * kThreads) | (single[q] ? 0 : 1 << 16);
+    }
     __syncthreads();
     // inverses of the coupled groups with <= 4 members (the system depends only
     // on the diagonal blocks), all groups in parallel
@@ -955,24 +971,29 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
     TileSmem<T, D, GEN> sm{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
     for (int i = tid; i < ncg; i += kThreads)
         if (cg_moff[i] >= 0) status |= group_inverse<T, D, GEN>(sm, cg_list[i], Minv + cg_moff[i]);
-    T lsum[EPT][NACC];
-#pragma unroll
-    for (int q = 0; q < EPT; q++)
-#pragma unroll
-        for (int k = 0; k < NACC; k++) lsum[q][k] = T(0);
     __syncthreads();
     for (int step = nsum - D; step >= 0; step--) {
-        // solve the 1x1 groups of this anti-diagonal from the register sums;
-        // members of coupled groups publish their sums for the solving warp
+        // elements of this anti-diagonal: line sums from the solved positions,
+        // then the 1x1 groups are solved by their threads; members of coupled
+        // groups publish their sums for the solving warp
+        const int a0 = act_off[step], an = act_cnt[step];
+        for (int i = tid; i < an; i += kThreads) {
+            const int code = act_list[a0 + i];
+            const int e = code & 0xffff;
+            int u[D], g[D], rem = e;
 #pragma unroll
-        for (int q = 0; q < EPT; q++) {
-            if (sq[q] != step || !okq[q]) continue;
-            const int e = tid + q * kThreads;
-            if (single[q]) {
-                status |= solve_single<T, D, GEN>(sm, e, uq[q], lsum[q]);
+            for (int mu = 0; mu < D; mu++) {
+                u[mu] = rem % TE;
+                rem /= TE;
+                g[mu] = gidx[mu * TE + u[mu]];
+            }
+            T L[NACC];
+            pull_lines<T, D, GEN>(sm, e, u, g, L);
+            if (!(code >> 16)) {
+                status |= solve_single<T, D, GEN>(sm, e, u, L);
             } else {
 #pragma unroll
-                for (int k = 0; k < NACC; k++) Lin[k * TD + e] = lsum[q][k];
+                for (int k = 0; k < NACC; k++) Lin[k * TD + e] = L[k];
             }
         }
         const int c0 = cg_off[step], cn = cg_cnt[step];
@@ -983,14 +1004,6 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
                 status |= warp_group<T, D, GEN>(sm, cg_list[c0 + k], cg_moff[c0 + k] >= 0 ? Minv + cg_moff[c0 + k] : nullptr);
         }
         __syncthreads();
-        if (step == 0) break;
-        // contributions of this anti-diagonal to the owned elements' sums
-        // (registers only; the next anti-diagonal's writes touch other positions)
-#pragma unroll
-        for (int q = 0; q < EPT; q++) {
-            if (!okq[q] || sq[q] >= step) continue;
-            push_lines<T, D, GEN>(sm, step, tid + q * kThreads, uq[q], gq[q], sq[q], lsum[q]);
-        }
     }
     if (status) atomicOr(a.err, status);
 
