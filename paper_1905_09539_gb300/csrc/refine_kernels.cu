@@ -105,46 +105,52 @@ __global__ void k_reduce(const double* __restrict__ part, const double* __restri
 }
 
 // ||M||_2 estimate of an n x n column-major matrix (structural zeros below
-// the first subdiagonal ignored): power iteration on M^T M, 80 steps, one CTA
-// per matrix (the norm only scales the stopping test).
+// the first subdiagonal ignored): 30 steps of power iteration on M^T M in
+// FP32, one CTA per matrix.  The estimate only scales the stopping test.
 __global__ void k_norm2(NormArgs a, double* __restrict__ out) {
     const int mat = blockIdx.x;
     const double* M = a.M[mat];
     const int n = a.n[mat];
     const int upper = a.upper[mat];
-    extern __shared__ double sh[];
-    double* v = sh;          // n
-    double* w = sh + n;      // n
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.0 + 0.01 * (i % 7);
+    extern __shared__ float shf[];
+    float* v = shf;          // n
+    float* w = shf + n;      // n
+    __shared__ float red[32];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.0f + 0.01f * (i % 7);
     __syncthreads();
-    double lam = 0;
-    for (int it = 0; it < 80; it++) {
-        // w = M v
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            double s = 0;
+    float lam = 0.f;
+    for (int it = 0; it < 30; it++) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {  // w = M v
+            float s = 0.f;
             const int j0 = upper ? i : (i > 0 ? i - 1 : 0);
-            for (int j = j0; j < n; j++) s += M[i + static_cast<long long>(n) * j] * v[j];
+            for (int j = j0; j < n; j++) s = fmaf(static_cast<float>(M[i + static_cast<long long>(n) * j]), v[j], s);
             w[i] = s;
         }
         __syncthreads();
-        // v = M^T w, lam = ||v|| / ||previous v|| via normalisation
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            double s = 0;
+        float part = 0.f;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {  // v = M^T w
+            float s = 0.f;
             const int iend = upper ? j : (j + 1 < n ? j + 1 : n - 1);
-            for (int i = 0; i <= iend; i++) s += M[i + static_cast<long long>(n) * j] * w[i];
+            for (int i = 0; i <= iend; i++) s = fmaf(static_cast<float>(M[i + static_cast<long long>(n) * j]), w[i], s);
             v[j] = s;
+            part += s * s;
+        }
+        for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int q = 0; q < static_cast<int>(blockDim.x >> 5); q++) t += red[q];
+            red[31] = sqrtf(t);
         }
         __syncthreads();
-        double nv = 0;
-        for (int j = 0; j < n; j++) nv += v[j] * v[j];
-        nv = sqrt(nv);
+        const float nv = red[31];
         lam = nv;
-        __syncthreads();
-        const double inv = nv > 0 ? 1.0 / nv : 0.0;
+        const float inv = nv > 0.f ? 1.0f / nv : 0.f;
         for (int j = threadIdx.x; j < n; j += blockDim.x) v[j] *= inv;
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[mat] = sqrt(lam);
+    if (threadIdx.x == 0) out[mat] = sqrt(static_cast<double>(lam));
 }
 
 // part[2 t] = sum x^2, part[2 t + 1] = max |x| over block t
@@ -207,7 +213,7 @@ cudaError_t launch_reduce(const double* part, const double* xpart, long long nt,
 }
 
 cudaError_t launch_norm2(const NormArgs& a, int count, int nmax, double* out, cudaStream_t s) {
-    k_norm2<<<count, 128, 2 * nmax * sizeof(double), s>>>(a, out);
+    k_norm2<<<count, 256, 2 * nmax * sizeof(float), s>>>(a, out);
     return cudaGetLastError();
 }
 
