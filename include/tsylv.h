@@ -114,6 +114,9 @@ typedef struct tsylv_info {
     double t_total_ms;    /* opts->timing: device time of the whole call             */
     double t_waves_ms;    /* opts->timing: device time of the wavefront launches     */
     double t_resid_ms;    /* opts->timing: device time of the residual launches      */
+    int batch_order;      /* tsylv_solve_batched: job-queue order used (0 longest remaining
+                             path first, 1 wavefront-major, 2 equation-major)      */
+    int batch_ctas_per_sm;/* tsylv_solve_batched: resident CTAs per SM used          */
 } tsylv_info;
 
 /* Fill *opts with the defaults listed above. */
@@ -209,17 +212,36 @@ int tsylv_backward(int d, const int64_t* n, const double* const* A, const double
 size_t tsylv_batched_workspace_bytes(int count, const int* d, const int64_t* n_packed,
                                      int generalized, const tsylv_opts* opts);
 
-/* Many independent equations of different sizes in one persistent launch.
- *   count       number of equations
+/* Many independent equations of different sizes in one persistent launch
+ * (per order d present in the batch), captured with the packing and
+ * unpacking in one CUDA graph when opts->use_graph.  Each equation is solved
+ * exactly as tsylv_solve / gtsylv_solve would solve it (same block partition
+ * from the split rule of Alg. 2, same block updates and base case), so every
+ * result equals the corresponding single solve up to rounding.
+ *   count       number of equations (>= 1)
  *   d           host array [count] of orders (1..4)
  *   n_packed    host array: the mode sizes of all equations, concatenated
  *   off_A       host array [sum d]: element offset of each A_mu (and C_mu) in
- *               A_pool / C_pool, in the order of n_packed
+ *               A_pool / C_pool, in the order of n_packed; every matrix is
+ *               column-major n_mu x n_mu
  *   off_X       host array [count]: element offset of each tensor in B_pool /
- *               X_pool
- *   C_pool      NULL for Laplace-form equations
- * Every equation uses opts->precision; statuses are combined (the first
- * nonzero wins).  per_status (optional, host [count]) receives each one. */
+ *               X_pool (column-major, mode 1 fastest)
+ *   A_pool, C_pool, B_pool, X_pool   device pools; C_pool NULL for the
+ *               Laplace form (all equations share one form); X_pool may equal
+ *               B_pool
+ *   work        device workspace of tsylv_batched_workspace_bytes bytes,
+ *               256-byte aligned, caller-owned
+ * Precision: TSYLV_FP64 only (other values return TSYLV_EUNSUPPORTED).
+ * Launch parameters: on the first call for a given set of shapes and 2x2
+ * structures a built-in autotuner times the job-queue orders (longest
+ * remaining path first, wavefront-major, equation-major) and the resident
+ * CTAs per SM on this batch and keeps the fastest (info->batch_order,
+ * info->batch_ctas_per_sm); opts->split > 0 fixes the CTAs per SM instead.
+ * The block extent (the recursion cutoff) is that of a single solve.
+ * Errors: -i for a bad i-th argument (-6 when some A_mu is not quasi-
+ * triangular); numerical statuses as for tsylv_solve, combined (the first
+ * nonzero in equation order wins); per_status (optional, host [count])
+ * receives each equation's own.  Synchronises the stream before returning. */
 int tsylv_solve_batched(int count, const int* d, const int64_t* n_packed, const int64_t* off_A,
                         const int64_t* off_X, const double* A_pool, const double* C_pool,
                         const double* B_pool, double* X_pool, void* work, size_t work_bytes,

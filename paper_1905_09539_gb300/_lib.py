@@ -33,7 +33,9 @@ class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("waves", ctypes.c_int), ("launches", ctypes.c_int),
                 ("tiles", ctypes.c_int), ("resid", ctypes.c_double), ("norm_A", ctypes.c_double),
                 ("flops", ctypes.c_double), ("t_total_ms", ctypes.c_double), ("t_waves_ms", ctypes.c_double),
-                ("t_resid_ms", ctypes.c_double)]
+                ("t_resid_ms", ctypes.c_double),
+                ("batch_order", ctypes.c_int),
+                ("batch_ctas_per_sm", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1,0 +1,749 @@
+// Host driver of tsylv_solve_batched: per-equation block partitions (the
+// split rule of Alg. 2 applied to each mode, exactly as for one solve), the
+// job queue of the persistent launch, a small autotuner for the launch
+// (queue order and resident CTAs per SM), and the captured CUDA graph
+// (control reset, table upload, packing, the persistent launch per order d,
+// unpacking, status read-back).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "batched.h"
+#include "plan.h"
+#include "solver.h"
+
+namespace tsylv {
+
+namespace {
+
+constexpr long long kTimeoutNs = 2000000000LL;
+constexpr int kPolicies = 3;  // 0: longest remaining path first, 1: wavefront-major, 2: equation-major
+
+size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct EqPlan {
+    int d = 0;
+    long long n[kMaxD] = {};
+    Part part[kMaxD];
+    int nb[kMaxD] = {};
+    long long tstride[kMaxD] = {};
+    long long ntiles = 0;
+    int nwaves = 0;
+    // workspace offsets (bytes, from the data region)
+    size_t X = 0, P[kMaxD] = {}, G[kMaxD] = {}, At[kMaxD] = {}, Ct[kMaxD] = {};
+    size_t part_off[kMaxD] = {};  // ints in the table: start (nb), then size (nb)
+};
+
+struct BatchGraph {
+    std::vector<const void*> key;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct BatchPlan {
+    int count = 0;
+    bool gen = false;
+    std::vector<EqPlan> eq;
+    std::vector<int> dlist;                 // distinct orders, increasing
+    std::vector<BatchJob> jobs[kPolicies];  // per policy; segments by order d
+    std::vector<int> seg_off, seg_cnt;      // per entry of dlist (same for every policy)
+    std::vector<BatchCoefJob> cjobs;
+    size_t data_bytes = 0;
+    double flops = 0;
+    int tuned_policy = -1, tuned_grid = 0;
+    std::vector<BatchGraph> graphs;
+    ~BatchPlan() {
+        for (auto& g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+    }
+};
+
+// Regions of the batched workspace (byte offsets from its base).
+struct BatchLayout {
+    size_t ctl = 0;    // heads [4], done [count], errs [count]
+    size_t sub = 0;    // sub-diagonals of every A_mu, then the gather tables
+    size_t tab = 0;    // WaveArgs [count], BatchGeom [count], jobs, coefficient jobs, partition ints
+    size_t data = 0;   // block tensors and coefficient tiles
+    size_t total = 0;
+    size_t o_wave = 0, o_geom = 0, o_jobs = 0, o_cjobs = 0, o_part = 0, tab_bytes = 0;
+    size_t o_aoff = 0, o_nmat = 0, o_ooff = 0, nsub = 0;
+};
+
+// Upper bounds of one equation's block counts (any admissible structure).
+void eq_bounds(int d, const int64_t* n, long long& tiles, long long& ctiles, long long& pints) {
+    const int te = tile_extent(d);
+    tiles = 1;
+    ctiles = 0;
+    pints = 0;
+    for (int mu = 0; mu < d; mu++) {
+        const long long nb = max_blocks(static_cast<int>(n[mu]), te);
+        tiles *= nb;
+        ctiles += nb * (nb + 1) / 2;
+        pints += 2 * nb;
+    }
+}
+
+size_t eq_data_bytes(int d, long long tiles, long long ctiles, bool gen, int elem) {
+    const int te = tile_extent(d);
+    const size_t td = static_cast<size_t>(ipow(te, d)), tc = static_cast<size_t>(te) * te;
+    const bool g = gen && d >= 2;
+    size_t b = al256(tiles * td * elem);
+    if (g) b += 2 * (d - 1) * al256(tiles * td * elem);
+    b += (g ? 2 : 1) * al256(ctiles * tc * elem);
+    return b;
+}
+
+BatchLayout make_batch_layout(int count, const int* d, const int64_t* n_packed, bool gen, int elem,
+                              long long njobs, long long ncjobs, long long pints, size_t data_bytes) {
+    BatchLayout L;
+    size_t off = 0;
+    L.ctl = off;
+    off += al256((4 + 2 * static_cast<size_t>(count)) * sizeof(int));
+    size_t nsub = 0, nmats = 0, k = 0;
+    for (int e = 0; e < count; e++)
+        for (int mu = 0; mu < d[e]; mu++, k++) {
+            nsub += static_cast<size_t>(n_packed[k] > 0 ? n_packed[k] - 1 : 0);
+            nmats++;
+        }
+    L.nsub = nsub;
+    L.sub = off;
+    off += al256((nsub + 1) * sizeof(double));
+    L.o_aoff = off;
+    off += al256(nmats * sizeof(long long));
+    L.o_nmat = off;
+    off += al256(nmats * sizeof(long long));
+    L.o_ooff = off;
+    off += al256(nmats * sizeof(long long));
+    L.tab = off;
+    size_t t = 0;
+    L.o_wave = t;
+    t += al256(count * sizeof(WaveArgs));
+    L.o_geom = t;
+    t += al256(count * sizeof(BatchGeom));
+    L.o_jobs = t;
+    t += al256(njobs * sizeof(BatchJob));
+    L.o_cjobs = t;
+    t += al256(ncjobs * sizeof(BatchCoefJob));
+    L.o_part = t;
+    t += al256(pints * sizeof(int));
+    L.tab_bytes = t;
+    off += t;
+    L.data = off;
+    off += data_bytes;
+    L.total = off;
+    (void)gen;
+    (void)elem;
+    return L;
+}
+
+struct Bounds {
+    long long jobs = 0, cjobs = 0, pints = 0;
+    size_t data = 0;
+};
+
+Bounds batch_bounds(int count, const int* d, const int64_t* n_packed, bool gen, int elem) {
+    Bounds b;
+    size_t k = 0;
+    for (int e = 0; e < count; e++) {
+        long long t, c, p;
+        eq_bounds(d[e], n_packed + k, t, c, p);
+        b.jobs += t;
+        b.cjobs += c;
+        b.pints += p;
+        b.data += eq_data_bytes(d[e], t, c, gen, elem);
+        k += static_cast<size_t>(d[e]);
+    }
+    return b;
+}
+
+bool shapes_ok(int count, const int* d, const int64_t* n_packed) {
+    if (count < 1 || !d || !n_packed) return false;
+    size_t k = 0;
+    for (int e = 0; e < count; e++) {
+        if (d[e] < 1 || d[e] > kMaxD) return false;
+        long long N = 1;
+        for (int mu = 0; mu < d[e]; mu++, k++) {
+            if (n_packed[k] < 1 || n_packed[k] > (1LL << 30)) return false;
+            N *= n_packed[k];
+            if (N > (1LL << 40)) return false;
+        }
+    }
+    return true;
+}
+
+std::mutex g_bmu;
+std::map<std::vector<long long>, std::shared_ptr<BatchPlan>> g_bplans;
+
+// Queue order of the jobs of one order-d segment under a policy.  Every
+// order keeps each equation's wavefronts increasing, so a job's prerequisites
+// always sit earlier in the queue.
+void order_jobs(const BatchPlan& p, const std::vector<int>& eqs, int policy, std::vector<BatchJob>& out) {
+    struct Item {
+        int eq, tile, wave, need;
+    };
+    std::vector<Item> items;
+    for (int e : eqs) {
+        const EqPlan& q = p.eq[e];
+        std::vector<std::vector<int>> waves(static_cast<size_t>(q.nwaves));
+        for (long long t = 0; t < q.ntiles; t++) {
+            int w = 0;
+            for (int mu = 0; mu < q.d; mu++) w += q.nb[mu] - 1 - static_cast<int>((t / q.tstride[mu]) % q.nb[mu]);
+            waves[static_cast<size_t>(w)].push_back(static_cast<int>(t));
+        }
+        int before = 0;
+        for (int w = 0; w < q.nwaves; w++) {
+            for (int t : waves[static_cast<size_t>(w)]) items.push_back({e, t, w, before});
+            before += static_cast<int>(waves[static_cast<size_t>(w)].size());
+        }
+    }
+    auto rem = [&](const Item& it) { return p.eq[it.eq].nwaves - 1 - it.wave; };
+    if (policy == 0) {
+        std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
+            if (rem(a) != rem(b)) return rem(a) > rem(b);
+            return a.eq < b.eq;
+        });
+    } else if (policy == 1) {
+        std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
+            if (a.wave != b.wave) return a.wave < b.wave;
+            return a.eq < b.eq;
+        });
+    } else {
+        std::stable_sort(items.begin(), items.end(), [&](const Item& a, const Item& b) {
+            const long long wa = p.eq[a.eq].ntiles, wb = p.eq[b.eq].ntiles;
+            if (wa != wb) return wa > wb;
+            if (a.eq != b.eq) return a.eq < b.eq;
+            return a.wave < b.wave;
+        });
+    }
+    for (const Item& it : items) out.push_back({it.eq, it.tile, it.need, 0});
+}
+
+double eq_flops(const EqPlan& q, bool gen) {
+    // executed flops of the block updates (dense TE-tiles) and the base cases
+    const int te = tile_extent(q.d);
+    const double td = std::pow(te, q.d);
+    double f = 0;
+    for (long long t = 0; t < q.ntiles; t++) {
+        for (int mu = 0; mu < q.d; mu++) {
+            const int I = static_cast<int>((t / q.tstride[mu]) % q.nb[mu]);
+            const double srcs = q.nb[mu] - 1 - I;
+            f += srcs * 2.0 * td * te * (gen && q.d >= 2 ? 2.0 : 1.0);
+        }
+        f += td * (2.0 * q.d * te + 1);
+    }
+    return f;
+}
+
+std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t* n_packed, bool gen, int elem,
+                                          const std::vector<uint8_t>& sub) {
+    std::vector<long long> key = {count, gen ? 1 : 0, elem};
+    size_t k = 0;
+    for (int e = 0; e < count; e++) {
+        key.push_back(d[e]);
+        for (int mu = 0; mu < d[e]; mu++, k++) key.push_back(n_packed[k]);
+    }
+    // structure bits, packed 60 per word
+    long long word = 0;
+    int bits = 0;
+    for (uint8_t s : sub) {
+        word |= static_cast<long long>(s & 1) << bits;
+        if (++bits == 60) {
+            key.push_back(word);
+            word = 0;
+            bits = 0;
+        }
+    }
+    key.push_back(word);
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto it = g_bplans.find(key);
+    if (it != g_bplans.end()) return it->second;
+    if (g_bplans.size() > 16) g_bplans.clear();
+    auto p = std::make_shared<BatchPlan>();
+    p->count = count;
+    p->gen = gen;
+    p->eq.resize(count);
+    k = 0;
+    size_t soff = 0, data = 0, pints = 0;
+    for (int e = 0; e < count; e++) {
+        EqPlan& q = p->eq[e];
+        q.d = d[e];
+        const int te = tile_extent(q.d);
+        long long ts = 1;
+        int nw = 1;
+        for (int mu = 0; mu < q.d; mu++, k++) {
+            q.n[mu] = n_packed[k];
+            std::vector<uint8_t> s(sub.begin() + static_cast<long long>(soff),
+                                   sub.begin() + static_cast<long long>(soff + q.n[mu] - 1));
+            soff += static_cast<size_t>(q.n[mu] - 1);
+            q.part[mu] = make_part(static_cast<int>(q.n[mu]), s, te);
+            q.nb[mu] = q.part[mu].nb;
+            q.tstride[mu] = ts;
+            ts *= q.nb[mu];
+            nw += q.nb[mu] - 1;
+            q.part_off[mu] = pints;
+            pints += 2 * static_cast<size_t>(q.nb[mu]);
+        }
+        q.ntiles = ts;
+        q.nwaves = nw;
+        const size_t td = static_cast<size_t>(ipow(te, q.d)), tc = static_cast<size_t>(te) * te;
+        const bool g = gen && q.d >= 2;
+        q.X = data;
+        data += al256(q.ntiles * td * elem);
+        if (g)
+            for (int l = 1; l < q.d; l++) {
+                q.P[l] = data;
+                data += al256(q.ntiles * td * elem);
+                q.G[l] = data;
+                data += al256(q.ntiles * td * elem);
+            }
+        for (int mu = 0; mu < q.d; mu++) {
+            const size_t nct = static_cast<size_t>(q.nb[mu]) * (q.nb[mu] + 1) / 2;
+            q.At[mu] = data;
+            data += al256(nct * tc * elem);
+            if (g) {
+                q.Ct[mu] = data;
+                data += al256(nct * tc * elem);
+            }
+            for (int J = 0; J < q.nb[mu]; J++)
+                for (int I = 0; I <= J; I++) p->cjobs.push_back({e, mu, I, J});
+        }
+        p->flops += eq_flops(q, gen);
+    }
+    p->data_bytes = data;
+    for (int e = 0; e < count; e++)
+        if (std::find(p->dlist.begin(), p->dlist.end(), d[e]) == p->dlist.end()) p->dlist.push_back(d[e]);
+    std::sort(p->dlist.begin(), p->dlist.end());
+    for (int pol = 0; pol < kPolicies; pol++) {
+        for (int dd : p->dlist) {
+            std::vector<int> eqs;
+            for (int e = 0; e < count; e++)
+                if (d[e] == dd) eqs.push_back(e);
+            if (pol == 0) p->seg_off.push_back(static_cast<int>(p->jobs[pol].size()));
+            order_jobs(*p, eqs, pol, p->jobs[pol]);
+            if (pol == 0) p->seg_cnt.push_back(static_cast<int>(p->jobs[pol].size()) - p->seg_off.back());
+        }
+    }
+    g_bplans[key] = p;
+    return p;
+}
+
+// The uploaded table of one call: parameter blocks with device pointers into
+// this workspace, the job lists and the partitions.
+void fill_table(const BatchPlan& p, const BatchLayout& L, char* base, int policy, std::vector<unsigned char>& out,
+                const int64_t* off_A, const int64_t* off_X) {
+    out.assign(L.tab_bytes, 0);
+    char* dev_tab = base + L.tab;
+    char* dev_data = base + L.data;
+    int* errs = reinterpret_cast<int*>(base + L.ctl) + 4 + p.count;
+    const int* dev_part = reinterpret_cast<const int*>(dev_tab + L.o_part);
+    int* hpart = reinterpret_cast<int*>(out.data() + L.o_part);
+    WaveArgs* hw = reinterpret_cast<WaveArgs*>(out.data() + L.o_wave);
+    BatchGeom* hg = reinterpret_cast<BatchGeom*>(out.data() + L.o_geom);
+    size_t k = 0;
+    for (int e = 0; e < p.count; e++) {
+        const EqPlan& q = p.eq[e];
+        const bool g = p.gen && q.d >= 2;
+        WaveArgs wa{};
+        BatchGeom ge{};
+        ge.d = q.d;
+        ge.xoff = off_X[e];
+        for (int mu = 0; mu < q.d; mu++, k++) {
+            std::memcpy(hpart + q.part_off[mu], q.part[mu].start.data(), sizeof(int) * q.nb[mu]);
+            std::memcpy(hpart + q.part_off[mu] + q.nb[mu], q.part[mu].size.data(), sizeof(int) * q.nb[mu]);
+            wa.nb[mu] = q.nb[mu];
+            wa.hi[mu] = q.nb[mu];
+            wa.tstride[mu] = q.tstride[mu];
+            wa.bsize[mu] = dev_part + q.part_off[mu] + q.nb[mu];
+            wa.At[mu] = dev_data + q.At[mu];
+            wa.Ct[mu] = g ? dev_data + q.Ct[mu] : nullptr;
+            wa.P[mu] = g && mu >= 1 ? dev_data + q.P[mu] : nullptr;
+            wa.G[mu] = g && mu >= 1 ? dev_data + q.G[mu] : nullptr;
+            ge.nb[mu] = q.nb[mu];
+            ge.n[mu] = q.n[mu];
+            ge.tstride[mu] = q.tstride[mu];
+            ge.start[mu] = dev_part + q.part_off[mu];
+            ge.size[mu] = dev_part + q.part_off[mu] + q.nb[mu];
+            ge.aoff[mu] = off_A[k];
+            ge.At[mu] = dev_data + q.At[mu];
+            ge.Ct[mu] = g ? dev_data + q.Ct[mu] : nullptr;
+        }
+        wa.tiles = nullptr;
+        wa.ntiles = static_cast<int>(q.ntiles);
+        wa.csize = 1;
+        wa.X = dev_data + q.X;
+        wa.err = errs + e;
+        wa.timeout_ns = kTimeoutNs;
+        ge.X = dev_data + q.X;
+        hw[e] = wa;
+        hg[e] = ge;
+    }
+    std::memcpy(out.data() + L.o_jobs, p.jobs[policy].data(), p.jobs[policy].size() * sizeof(BatchJob));
+    std::memcpy(out.data() + L.o_cjobs, p.cjobs.data(), p.cjobs.size() * sizeof(BatchCoefJob));
+}
+
+struct Pinned {
+    unsigned char* ptr = nullptr;
+    size_t bytes = 0;
+    ~Pinned() {
+        if (ptr) cudaFreeHost(ptr);
+    }
+    bool reserve(size_t b) {
+        if (b <= bytes) return true;
+        if (ptr) cudaFreeHost(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        if (cudaMallocHost(&ptr, b) != cudaSuccess) return false;
+        bytes = b;
+        return true;
+    }
+};
+
+// Pinned staging of the host tables (per thread: calls on one thread are ordered
+// by their synchronisation at the end).
+thread_local Pinned t_pin_tab, t_pin_small;
+
+int occupancy_cached(int d, bool gen) {
+    static std::mutex m;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int key = dev * 16 + d * 2 + (gen ? 1 : 0);
+    std::lock_guard<std::mutex> lk(m);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const int o = batched_occupancy<double>(d, gen);
+    cache[key] = o;
+    return o;
+}
+
+int sm_count() {
+    static int sms[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!sms[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+        sms[dev] = v;
+    }
+    return sms[dev];
+}
+
+int prepare_batched_once() {
+    static std::mutex pm;
+    static bool prepared[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(pm);
+    if (dev >= 0 && dev < 64 && !prepared[dev]) {
+        if (cudaError_t e = prepare_batched<double>(); e != cudaSuccess) return cuda_fail(e, "batched kernel attributes");
+        prepared[dev] = true;
+    }
+    return 0;
+}
+
+struct BatchCall {
+    const BatchPlan* plan = nullptr;
+    BatchLayout L;
+    char* base = nullptr;
+    const unsigned char* htab = nullptr;
+    const double *A = nullptr, *C = nullptr, *B = nullptr;
+    double* X = nullptr;
+    int grid_per_sm[kMaxD + 1] = {};
+    int* herr = nullptr;   // pinned host copy of the per-equation status words
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the persistent launches (autotuner)
+};
+
+cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
+    const BatchPlan& p = *c.plan;
+    int* ctl = reinterpret_cast<int*>(c.base + c.L.ctl);
+    char* tab = c.base + c.L.tab;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ctl, 0, (4 + 2 * static_cast<size_t>(p.count)) * sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(tab, c.htab, c.L.tab_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    const BatchGeom* geo = reinterpret_cast<const BatchGeom*>(tab + c.L.o_geom);
+    const BatchJob* jobs = reinterpret_cast<const BatchJob*>(tab + c.L.o_jobs);
+    const BatchCoefJob* cjobs = reinterpret_cast<const BatchCoefJob*>(tab + c.L.o_cjobs);
+    const int njobs = static_cast<int>(p.jobs[0].size());
+    if ((e = launch_batch_pack<double>(geo, jobs, njobs, cjobs, static_cast<int>(p.cjobs.size()), c.B, c.A,
+                                       p.gen ? c.C : nullptr, s)) != cudaSuccess)
+        return e;
+    if (c.ev0 && (e = cudaEventRecord(c.ev0, s)) != cudaSuccess) return e;
+    for (size_t g = 0; g < p.dlist.size(); g++) {
+        BatchArgs a{};
+        a.eqs = reinterpret_cast<const WaveArgs*>(tab + c.L.o_wave);
+        a.jobs = jobs + p.seg_off[g];
+        a.njobs = p.seg_cnt[g];
+        a.head = ctl + g;
+        a.done = ctl + 4;
+        a.timeout_ns = kTimeoutNs;
+        const int dd = p.dlist[g];
+        int grid = c.grid_per_sm[dd] * sm_count();
+        if (grid > a.njobs) grid = a.njobs;
+        if (grid < 1) grid = 1;
+        if ((e = launch_batched<double>(dd, p.gen, a, grid, s)) != cudaSuccess) return e;
+    }
+    if (c.ev1 && (e = cudaEventRecord(c.ev1, s)) != cudaSuccess) return e;
+    if ((e = launch_batch_unpack<double>(geo, jobs, njobs, c.X, s)) != cudaSuccess) return e;
+    return cudaMemcpyAsync(c.herr, ctl + 4 + p.count, sizeof(int) * p.count, cudaMemcpyDeviceToHost, s);
+}
+
+// Same precedence as a single solve.
+int map_status(int e) {
+    if (e & kErrBounds) return cuda_fail_msg("device self-check: index outside a block array");
+    if (e & kErrTimeout) return TSYLV_ETIMEOUT;
+    if (e & kErrSingular) return TSYLV_ESINGULAR;
+    if (e & kErrNonfinite) return TSYLV_ENONFINITE;
+    return TSYLV_OK;
+}
+
+}  // namespace
+
+size_t solver_batched_workspace_bytes(int count, const int* d, const int64_t* n_packed, bool gen,
+                                      const tsylv_opts& o) {
+    if (!shapes_ok(count, d, n_packed)) return 0;
+    if (o.precision != TSYLV_FP64) return 0;
+    const Bounds b = batch_bounds(count, d, n_packed, gen, 8);
+    const BatchLayout L = make_batch_layout(count, d, n_packed, gen, 8, b.jobs, b.cjobs, b.pints, b.data);
+    return L.total;
+}
+
+int solver_batched(int count, const int* d, const int64_t* n_packed, const int64_t* off_A, const int64_t* off_X,
+                   const double* A_pool, const double* C_pool, const double* B_pool, double* X_pool, void* work,
+                   size_t work_bytes, const tsylv_opts* opts, int* per_status, tsylv_info* info,
+                   cudaStream_t stream) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    if (count < 1) return -1;
+    if (!d) return -2;
+    if (!n_packed || !shapes_ok(count, d, n_packed)) return -3;
+    if (!off_A) return -4;
+    if (!off_X) return -5;
+    if (!A_pool) return -6;
+    const bool gen = C_pool != nullptr;
+    if (!B_pool) return -8;
+    if (!X_pool) return -9;
+    if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -10;
+    if (o.precision != TSYLV_FP64) return TSYLV_EUNSUPPORTED;
+    const size_t need = solver_batched_workspace_bytes(count, d, n_packed, gen, o);
+    if (!need || work_bytes < need) return -11;
+    if (o.split < 0) return -12;
+    size_t nmats = 0;
+    for (int e = 0; e < count; e++) nmats += static_cast<size_t>(d[e]);
+    for (size_t k = 0; k < nmats; k++)
+        if (off_A[k] < 0) return -4;
+    for (int e = 0; e < count; e++)
+        if (off_X[e] < 0) return -5;
+    (void)cudaGetLastError();
+    char* base = static_cast<char*>(work);
+    const Bounds bd = batch_bounds(count, d, n_packed, gen, 8);
+    BatchLayout L = make_batch_layout(count, d, n_packed, gen, 8, bd.jobs, bd.cjobs, bd.pints, bd.data);
+
+    // ---- 2x2 structure of every A_mu (sub-diagonals gathered in one launch)
+    std::vector<long long> aoff(nmats), nmat(nmats), ooff(nmats);
+    long long maxn = 1;
+    {
+        size_t k = 0, so = 0;
+        for (int e = 0; e < count; e++)
+            for (int mu = 0; mu < d[e]; mu++, k++) {
+                aoff[k] = off_A[k];
+                nmat[k] = n_packed[k];
+                ooff[k] = static_cast<long long>(so);
+                so += static_cast<size_t>(n_packed[k] - 1);
+                maxn = std::max<long long>(maxn, n_packed[k]);
+            }
+    }
+    const size_t small_bytes = 3 * nmats * sizeof(long long) + (L.nsub + 1) * sizeof(double) + count * sizeof(int);
+    if (!t_pin_small.reserve(small_bytes)) return cuda_fail_msg("batched: pinned host allocation");
+    long long* hoffs = reinterpret_cast<long long*>(t_pin_small.ptr);
+    double* hsub = reinterpret_cast<double*>(t_pin_small.ptr + 3 * nmats * sizeof(long long));
+    int* herr = reinterpret_cast<int*>(t_pin_small.ptr + 3 * nmats * sizeof(long long) + (L.nsub + 1) * sizeof(double));
+    std::memcpy(hoffs, aoff.data(), nmats * sizeof(long long));
+    std::memcpy(hoffs + nmats, nmat.data(), nmats * sizeof(long long));
+    std::memcpy(hoffs + 2 * nmats, ooff.data(), nmats * sizeof(long long));
+    cudaError_t e;
+    // the three offset tables are contiguous in the workspace (o_aoff, o_nmat, o_ooff)
+    long long* daoff = reinterpret_cast<long long*>(base + L.o_aoff);
+    long long* dnmat = reinterpret_cast<long long*>(base + L.o_nmat);
+    long long* dooff = reinterpret_cast<long long*>(base + L.o_ooff);
+    double* dsub = reinterpret_cast<double*>(base + L.sub);
+    if ((e = cudaMemcpyAsync(daoff, hoffs, nmats * sizeof(long long), cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dnmat, hoffs + nmats, nmats * sizeof(long long), cudaMemcpyHostToDevice, stream)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(dooff, hoffs + 2 * nmats, nmats * sizeof(long long), cudaMemcpyHostToDevice, stream)) !=
+            cudaSuccess)
+        return cuda_fail(e, "batched: upload offsets");
+    if (L.nsub > 0) {
+        if ((e = launch_batch_subdiag(daoff, dnmat, dooff, static_cast<int>(nmats), maxn, A_pool, dsub, stream)) !=
+            cudaSuccess)
+            return cuda_fail(e, "batched: gather sub-diagonals");
+        if ((e = cudaMemcpyAsync(hsub, dsub, L.nsub * sizeof(double), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+            return cuda_fail(e, "batched: read sub-diagonals");
+    }
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "batched: synchronize before planning");
+    std::vector<uint8_t> sub(L.nsub + 1, 0);
+    {
+        size_t k = 0, so = 0;
+        for (int q = 0; q < count; q++)
+            for (int mu = 0; mu < d[q]; mu++, k++) {
+                const long long m = n_packed[k];
+                for (long long i = 0; i + 1 < m; i++) sub[so + i] = hsub[so + i] != 0.0 ? 1 : 0;
+                for (long long i = 0; i + 2 < m; i++)
+                    if (sub[so + i] && sub[so + i + 1]) {
+                        if (per_status)
+                            for (int r = 0; r < count; r++) per_status[r] = r == q ? -6 : 0;
+                        return -6;  // not quasi-triangular
+                    }
+                so += static_cast<size_t>(m - 1);
+            }
+    }
+
+    // ---- plan (cached per shapes and structure), tables, launch
+    std::shared_ptr<BatchPlan> plan = get_batch_plan(count, d, n_packed, gen, 8, sub);
+    if (!plan) return cuda_fail_msg("batched: plan");
+    if (plan->data_bytes > bd.data) return cuda_fail_msg("batched: workspace bound");
+    if (int st = prepare_batched_once()) return st;
+    BatchCall c;
+    c.plan = plan.get();
+    c.L = L;
+    c.base = base;
+    c.A = A_pool;
+    c.C = C_pool;
+    c.B = B_pool;
+    c.X = X_pool;
+    c.herr = herr;
+    if (!t_pin_tab.reserve(L.tab_bytes)) return cuda_fail_msg("batched: pinned host allocation");
+    std::vector<unsigned char> tabv;
+
+    auto set_grid = [&](int per_sm) {
+        for (int dd : plan->dlist) {
+            const int occ = occupancy_cached(dd, gen);
+            c.grid_per_sm[dd] = std::max(1, std::min(per_sm, occ));
+        }
+    };
+
+    // autotuner: queue order x resident CTAs per SM, timed on this batch once
+    int policy = plan->tuned_policy, per_sm = plan->tuned_grid;
+    if (o.split > 0) {
+        policy = policy >= 0 ? policy : 0;
+        per_sm = o.split;
+    } else if (policy < 0) {
+        int occ = 1;
+        for (int dd : plan->dlist) occ = std::max(occ, occupancy_cached(dd, gen));
+        std::vector<int> grids = {occ};
+        if (occ >= 2) grids.push_back((occ + 1) / 2);
+        if (occ >= 3) grids.push_back(1);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
+            return cuda_fail_msg("batched: autotuner events");
+        }
+        float best = 1e30f;
+        int bp = 0, bg = occ;
+        for (int pol = 0; pol < kPolicies; pol++) {
+            fill_table(*plan, L, base, pol, tabv, off_A, off_X);
+            std::memcpy(t_pin_tab.ptr, tabv.data(), tabv.size());
+            c.htab = t_pin_tab.ptr;
+            for (int gsz : grids) {
+                set_grid(gsz);
+                c.ev0 = e0;
+                c.ev1 = e1;
+                float ms = 0;
+                for (int rep = 0; rep < 2; rep++) {  // first run warms caches and code
+                    if ((e = enqueue_batch(c, stream)) != cudaSuccess) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return cuda_fail(e, "batched: autotuner launch");
+                    }
+                    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return cuda_fail(e, "batched: autotuner synchronize");
+                    }
+                    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = 1e30f;
+                }
+                int bad = 0;
+                for (int q = 0; q < count; q++) bad |= herr[q];
+                if (bad & kErrTimeout) ms = 1e30f;
+                if (ms < best) {
+                    best = ms;
+                    bp = pol;
+                    bg = gsz;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c.ev0 = c.ev1 = nullptr;
+        plan->tuned_policy = policy = bp;
+        plan->tuned_grid = per_sm = bg;
+    }
+    set_grid(per_sm);
+    fill_table(*plan, L, base, policy, tabv, off_A, off_X);
+    std::memcpy(t_pin_tab.ptr, tabv.data(), tabv.size());
+    c.htab = t_pin_tab.ptr;
+
+    const int launches = 3 + static_cast<int>(plan->dlist.size());
+    if (o.use_graph) {
+        std::vector<const void*> key = {base, A_pool, C_pool, B_pool, X_pool, t_pin_tab.ptr, herr,
+                                        reinterpret_cast<const void*>(static_cast<uintptr_t>(policy * 64 + per_sm))};
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : plan->graphs)
+            if (g.key == key) exec = g.exec;
+        if (!exec) {
+            cudaGraph_t graph = nullptr;
+            if ((e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return cuda_fail(e, "batched: begin capture");
+            const cudaError_t ee = enqueue_batch(c, stream);
+            e = cudaStreamEndCapture(stream, &graph);
+            if (ee != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_fail(ee, "batched: capture");
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "batched: end capture");
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "batched: instantiate");
+            if (plan->graphs.size() >= 8) {
+                cudaGraphExecDestroy(plan->graphs.front().exec);
+                plan->graphs.erase(plan->graphs.begin());
+            }
+            plan->graphs.push_back({key, exec});
+        }
+        if ((e = cudaGraphLaunch(exec, stream)) != cudaSuccess) return cuda_fail(e, "batched: graph launch");
+    } else {
+        if ((e = enqueue_batch(c, stream)) != cudaSuccess) return cuda_fail(e, "batched: launch");
+    }
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "batched: synchronize");
+    int status = TSYLV_OK;
+    for (int q = 0; q < count; q++) {
+        const int s = map_status(herr[q]);
+        if (per_status) per_status[q] = s;
+        if (status == TSYLV_OK && s != TSYLV_OK) status = s;
+    }
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        int waves = 0;
+        long long tiles = 0;
+        for (const EqPlan& q : plan->eq) {
+            waves = std::max(waves, q.nwaves);
+            tiles += q.ntiles;
+        }
+        info->waves = waves;
+        info->launches = launches;
+        info->tiles = static_cast<int>(tiles);
+        info->resid = -1;
+        info->norm_A = -1;
+        info->flops = plan->flops;
+        info->batch_order = policy;
+        info->batch_ctas_per_sm = per_sm;
+    }
+    return status;
+}
+
+}  // namespace tsylv

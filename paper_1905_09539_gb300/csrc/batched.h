@@ -1,0 +1,75 @@
+// Batched solve of many independent equations: declarations shared by the
+// host driver (batched.cpp) and its kernels.
+//
+// Every equation keeps the block grid of a single solve (block tensor,
+// coefficient tiles, partition tables).  One persistent launch works through
+// a job queue holding every block of every equation; a block of wavefront w
+// of equation e may start once equation e has finished all blocks of its
+// wavefronts before w.  Jobs are queued so that every job's prerequisites
+// sit earlier in the queue; a CTA that waits therefore only waits on jobs that
+// running CTAs already hold, and the launch needs no co-residency guarantee.
+#pragma once
+
+#include "tsylv_internal.h"
+
+namespace tsylv {
+
+struct BatchJob {
+    int eq;      // equation
+    int tile;    // linear block index in the equation's block grid
+    int need;    // blocks of equation `eq` that must be finished first
+    int pad;
+};
+
+// Per-equation geometry of the layout kernels (pools are kernel arguments).
+struct BatchGeom {
+    int d;
+    int nb[kMaxD];
+    long long n[kMaxD];
+    long long tstride[kMaxD];
+    const int* start[kMaxD];
+    const int* size[kMaxD];
+    long long xoff;            // element offset of B / X in the pools
+    long long aoff[kMaxD];     // element offset of A_mu / C_mu in the pools
+    void* X;                   // block tensor
+    void* At[kMaxD];           // coefficient tiles
+    void* Ct[kMaxD];
+};
+
+// Coefficient tile (I, J), I <= J, of mode mu of equation eq.
+struct BatchCoefJob {
+    int eq;
+    int mu;
+    int I;
+    int J;
+};
+
+struct BatchArgs {
+    const WaveArgs* eqs;       // one wavefront parameter block per equation (tiles unused)
+    const BatchJob* jobs;
+    int njobs;
+    int* head;                 // next job (zeroed before the launch)
+    int* done;                 // finished blocks per equation (zeroed before the launch)
+    long long timeout_ns;
+};
+
+// Persistent launch of `grid` CTAs (equations of order d, one form).
+template <typename T>
+cudaError_t launch_batched(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s);
+template <typename T>
+cudaError_t prepare_batched();
+// Resident CTAs per SM of the persistent kernel.
+template <typename T>
+int batched_occupancy(int d, bool gen);
+
+// Block tensors of B and coefficient tiles of every equation; back to X.
+template <typename T>
+cudaError_t launch_batch_pack(const BatchGeom* g, const BatchJob* jobs, int njobs, const BatchCoefJob* cjobs,
+                              int ncjobs, const double* B, const double* A, const double* C, cudaStream_t s);
+template <typename T>
+cudaError_t launch_batch_unpack(const BatchGeom* g, const BatchJob* jobs, int njobs, double* X, cudaStream_t s);
+// Sub-diagonals of every A_mu: out[ooff[k] + i] = A_k(i + 1, i), k over all matrices.
+cudaError_t launch_batch_subdiag(const long long* aoff, const long long* nmat, const long long* ooff, int nmats,
+                                 long long maxn, const double* A, double* out, cudaStream_t s);
+
+}  // namespace tsylv

@@ -1,0 +1,197 @@
+// Layout kernels of the batched solve (one launch for all equations) and the
+// dispatch of the persistent kernel over (element type, d, form).
+#include "batched.h"
+
+namespace tsylv {
+
+template <typename T, int D, bool GEN>
+cudaError_t launch_batched_t(const BatchArgs& a, int grid, cudaStream_t s);
+template <typename T, int D, bool GEN>
+cudaError_t prepare_batched_t();
+template <typename T, int D, bool GEN>
+int batched_occupancy_t();
+
+namespace {
+
+// CTA b < njobs: block tensor tile of job b (B -> tile, zero padding);
+// CTA njobs + c: coefficient tile c (A, and C for the generalized form;
+// entries that the structure makes zero are written as zero unread).
+template <typename T>
+__global__ void k_batch_pack(const BatchGeom* __restrict__ geo, const BatchJob* __restrict__ jobs, int njobs,
+                             const BatchCoefJob* __restrict__ cjobs, int ncjobs, const double* __restrict__ B,
+                             const double* __restrict__ A, const double* __restrict__ C) {
+    for (int b = blockIdx.x; b < njobs + ncjobs; b += gridDim.x) {
+        if (b < njobs) {
+            const BatchJob jb = jobs[b];
+            const BatchGeom& g = geo[jb.eq];
+            const int d = g.d, te = tile_extent(d), td = ipow(te, d);
+            int I[kMaxD], sz[kMaxD];
+            long long st[kMaxD];
+            for (int mu = 0; mu < d; mu++) {
+                I[mu] = static_cast<int>((jb.tile / g.tstride[mu]) % g.nb[mu]);
+                sz[mu] = g.size[mu][I[mu]];
+                st[mu] = g.start[mu][I[mu]];
+            }
+            T* dst = static_cast<T*>(g.X) + static_cast<long long>(jb.tile) * td;
+            for (int e = threadIdx.x; e < td; e += blockDim.x) {
+                int rem = e;
+                long long off = 0, gst = 1;
+                bool valid = true;
+                for (int mu = 0; mu < d; mu++) {
+                    const int i = rem % te;
+                    rem /= te;
+                    if (i >= sz[mu]) valid = false;
+                    off += (st[mu] + i) * gst;
+                    gst *= g.n[mu];
+                }
+                dst[e] = valid ? static_cast<T>(B[g.xoff + off]) : T(0);
+            }
+        } else {
+            const BatchCoefJob cj = cjobs[b - njobs];
+            const BatchGeom& g = geo[cj.eq];
+            const int te = tile_extent(g.d), tc = te * te, mu = cj.mu;
+            const long long n = g.n[mu];
+            const int si = g.size[mu][cj.I], sj = g.size[mu][cj.J];
+            const long long gi0 = g.start[mu][cj.I], gj0 = g.start[mu][cj.J];
+            const long long tri = static_cast<long long>(cj.J) * (cj.J + 1) / 2 + cj.I;
+            T* ta = static_cast<T*>(g.At[mu]) + tri * tc;
+            T* tcp = C ? static_cast<T*>(g.Ct[mu]) + tri * tc : nullptr;
+            const double* Am = A + g.aoff[mu];
+            const double* Cm = C ? C + g.aoff[mu] : nullptr;
+            for (int e = threadIdx.x; e < tc; e += blockDim.x) {
+                const int i = e % te, j = e / te;
+                T va = T(0), vc = T(0);
+                if (i < si && j < sj) {
+                    const long long gi = gi0 + i, gj = gj0 + j;
+                    if (gi <= gj + 1) va = static_cast<T>(Am[gi + n * gj]);
+                    if (Cm && gi <= gj) vc = static_cast<T>(Cm[gi + n * gj]);
+                }
+                ta[e] = va;
+                if (tcp) tcp[e] = vc;
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_batch_unpack(const BatchGeom* __restrict__ geo, const BatchJob* __restrict__ jobs, int njobs,
+                               double* __restrict__ X) {
+    for (int b = blockIdx.x; b < njobs; b += gridDim.x) {
+        const BatchJob jb = jobs[b];
+        const BatchGeom& g = geo[jb.eq];
+        const int d = g.d, te = tile_extent(d), td = ipow(te, d);
+        int sz[kMaxD];
+        long long st[kMaxD];
+        for (int mu = 0; mu < d; mu++) {
+            const int I = static_cast<int>((jb.tile / g.tstride[mu]) % g.nb[mu]);
+            sz[mu] = g.size[mu][I];
+            st[mu] = g.start[mu][I];
+        }
+        const T* src = static_cast<const T*>(g.X) + static_cast<long long>(jb.tile) * td;
+        for (int e = threadIdx.x; e < td; e += blockDim.x) {
+            int rem = e;
+            long long off = 0, gst = 1;
+            bool valid = true;
+            for (int mu = 0; mu < d; mu++) {
+                const int i = rem % te;
+                rem /= te;
+                if (i >= sz[mu]) valid = false;
+                off += (st[mu] + i) * gst;
+                gst *= g.n[mu];
+            }
+            if (valid) X[g.xoff + off] = static_cast<double>(src[e]);
+        }
+    }
+}
+
+__global__ void k_batch_subdiag(const long long* __restrict__ aoff, const long long* __restrict__ nmat,
+                                const long long* __restrict__ ooff, int nmats, const double* __restrict__ A,
+                                double* __restrict__ out) {
+    for (int k = blockIdx.y; k < nmats; k += gridDim.y) {
+        const long long m = nmat[k];
+        for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i + 1 < m;
+             i += static_cast<long long>(gridDim.x) * blockDim.x)
+            out[ooff[k] + i] = A[aoff[k] + (i + 1) + m * i];
+    }
+}
+
+inline int blocks_for(long long n) {
+    long long b = n < 1 ? 1 : n;
+    if (b > 152LL * 16) b = 152LL * 16;
+    return static_cast<int>(b);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_batch_pack(const BatchGeom* g, const BatchJob* jobs, int njobs, const BatchCoefJob* cjobs,
+                              int ncjobs, const double* B, const double* A, const double* C, cudaStream_t s) {
+    k_batch_pack<T><<<blocks_for(static_cast<long long>(njobs) + ncjobs), 128, 0, s>>>(g, jobs, njobs, cjobs, ncjobs,
+                                                                                      B, A, C);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch_unpack(const BatchGeom* g, const BatchJob* jobs, int njobs, double* X, cudaStream_t s) {
+    k_batch_unpack<T><<<blocks_for(njobs), 128, 0, s>>>(g, jobs, njobs, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_subdiag(const long long* aoff, const long long* nmat, const long long* ooff, int nmats,
+                                 long long maxn, const double* A, double* out, cudaStream_t s) {
+    const unsigned gx = static_cast<unsigned>((maxn + 127) / 128 > 0 ? (maxn + 127) / 128 : 1);
+    const unsigned gy = static_cast<unsigned>(nmats < 65535 ? (nmats > 0 ? nmats : 1) : 65535);
+    k_batch_subdiag<<<dim3(gx, gy), 128, 0, s>>>(aoff, nmat, ooff, nmats, A, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batched(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s) {
+    switch (d * 2 + (gen ? 1 : 0)) {
+        case 2:
+        case 3: return launch_batched_t<T, 1, false>(a, grid, s);
+        case 4: return launch_batched_t<T, 2, false>(a, grid, s);
+        case 5: return launch_batched_t<T, 2, true>(a, grid, s);
+        case 6: return launch_batched_t<T, 3, false>(a, grid, s);
+        case 7: return launch_batched_t<T, 3, true>(a, grid, s);
+        case 8: return launch_batched_t<T, 4, false>(a, grid, s);
+        case 9: return launch_batched_t<T, 4, true>(a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+int batched_occupancy(int d, bool gen) {
+    switch (d * 2 + (gen ? 1 : 0)) {
+        case 2:
+        case 3: return batched_occupancy_t<T, 1, false>();
+        case 4: return batched_occupancy_t<T, 2, false>();
+        case 5: return batched_occupancy_t<T, 2, true>();
+        case 6: return batched_occupancy_t<T, 3, false>();
+        case 7: return batched_occupancy_t<T, 3, true>();
+        case 8: return batched_occupancy_t<T, 4, false>();
+        case 9: return batched_occupancy_t<T, 4, true>();
+        default: return 1;
+    }
+}
+
+template <typename T>
+cudaError_t prepare_batched() {
+    cudaError_t e = cudaSuccess;
+    if ((e = prepare_batched_t<T, 1, false>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<T, 2, false>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<T, 2, true>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<T, 3, false>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<T, 3, true>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<T, 4, false>()) != cudaSuccess) return e;
+    return prepare_batched_t<T, 4, true>();
+}
+
+template cudaError_t launch_batched<double>(int, bool, const BatchArgs&, int, cudaStream_t);
+template int batched_occupancy<double>(int, bool);
+template cudaError_t prepare_batched<double>();
+template cudaError_t launch_batch_pack<double>(const BatchGeom*, const BatchJob*, int, const BatchCoefJob*, int,
+                                               const double*, const double*, const double*, cudaStream_t);
+template cudaError_t launch_batch_unpack<double>(const BatchGeom*, const BatchJob*, int, double*, cudaStream_t);
+
+}  // namespace tsylv

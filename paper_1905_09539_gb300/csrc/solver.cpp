@@ -1,6 +1,7 @@
 // Solve orchestration: structure read-back, schedule, graph capture/replay,
 // mixed-precision refinement and the residual entry point.
 #include "solver.h"
+#include "grad.h"
 
 #include <algorithm>
 #include <cmath>
@@ -779,21 +780,114 @@ int solver_residual(int d, const int64_t* n, const double* const* A, const doubl
     return map_err(herr);
 }
 
+// Workspace of tsylv_backward: the transposed solve's workspace, then Lambda
+// (N doubles, only when dB is not given -- sized unconditionally) and, for the
+// generalized form, two N-double temporaries of the mode-product chains.
 size_t solver_backward_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o) {
-    return solver_workspace_bytes(d, n, gen, o, true);
+    const size_t ws = solver_workspace_bytes(d, n, gen, o, true);
+    if (!ws) return 0;
+    long long N = 1;
+    for (int mu = 0; mu < d; mu++) N *= n[mu];
+    return al256(ws) + al256(N * 8) * (gen ? 3 : 1);
 }
 
-int solver_backward(int, const int64_t*, const double* const*, const double* const*, const double*, const double*,
-                    double*, double* const*, double* const*, void*, size_t, const tsylv_opts*, tsylv_info*,
-                    cudaStream_t) {
-    return TSYLV_EUNSUPPORTED;
-}
+int solver_backward(int d, const int64_t* n, const double* const* A, const double* const* C, const double* X,
+                    const double* dX, double* dB, double* const* dA, double* const* dC, void* work, size_t work_bytes,
+                    const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    if (d < 1 || d > kMaxD) return -1;
+    if (!shape_ok(d, n)) return -2;
+    if (!A) return -3;
+    for (int mu = 0; mu < d; mu++)
+        if (!A[mu]) return -3;
+    const bool gen = C != nullptr;
+    if (gen)
+        for (int mu = 0; mu < d; mu++)
+            if (!C[mu]) return -4;
+    if (!X) return -5;
+    if (!dX) return -6;
+    if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -10;
+    const size_t need = solver_backward_workspace_bytes(d, n, gen, o);
+    if (!need || work_bytes < need) return -11;
+    long long N = 1;
+    for (int mu = 0; mu < d; mu++) N *= n[mu];
+    const size_t ws = al256(solver_workspace_bytes(d, n, gen, o, true));
+    char* base = static_cast<char*>(work);
+    double* lam = dB ? dB : reinterpret_cast<double*>(base + ws);
+    double* t0 = reinterpret_cast<double*>(base + ws + al256(N * 8));
+    double* t1 = reinterpret_cast<double*>(base + ws + 2 * al256(N * 8));
 
-size_t solver_batched_workspace_bytes(int, const int*, const int64_t*, bool, const tsylv_opts&) { return 0; }
+    // Lambda = A^{-T}(dX): the transposed solve (index-flipped coefficients)
+    tsylv_info si{};
+    const int st = solver_solve(d, n, A, C, dX, lam, work, ws, &o, &si, stream, gen, true);
+    if (st < 0) return st == -1 || st == -2 || st == -3 || st == -4 ? st : -11;
+    if (st != TSYLV_OK && st != TSYLV_ENOCONV) return st;
 
-int solver_batched(int, const int*, const int64_t*, const int64_t*, const int64_t*, const double*, const double*,
-                   const double*, double*, void*, size_t, const tsylv_opts*, int*, tsylv_info*, cudaStream_t) {
-    return TSYLV_EUNSUPPORTED;
+    // X x_{eta in S} M_eta for the modes of S in increasing order; M_eta = A
+    // for eta == special, else C.  Returns the pointer holding the result.
+    int launches = 0;
+    auto chain = [&](int skip, int special, const double** out) -> cudaError_t {
+        const double* src = X;
+        double* bufs[2] = {t0, t1};
+        int which = 0;
+        for (int eta = 0; eta < d; eta++) {
+            if (eta == skip) continue;
+            long long L = 1, R = 1;
+            for (int q = 0; q < eta; q++) L *= n[q];
+            for (int q = eta + 1; q < d; q++) R *= n[q];
+            const bool isA = eta == special;
+            const double* M = isA ? A[eta] : C[eta];
+            cudaError_t e = launch_modeprod(src, M, bufs[which], L, static_cast<int>(n[eta]), R, isA, stream);
+            if (e != cudaSuccess) return e;
+            launches++;
+            src = bufs[which];
+            which ^= 1;
+        }
+        *out = src;
+        return cudaSuccess;
+    };
+
+    for (int mu = 0; mu < d; mu++) {
+        long long L = 1, R = 1;
+        for (int q = 0; q < mu; q++) L *= n[q];
+        for (int q = mu + 1; q < d; q++) R *= n[q];
+        const int m = static_cast<int>(n[mu]);
+        cudaError_t e;
+        if (dA && dA[mu]) {
+            const double* W = X;
+            if (gen && d > 1 && (e = chain(mu, -1, &W)) != cudaSuccess) return cuda_fail(e, "backward: mode products");
+            if ((e = cudaMemsetAsync(dA[mu], 0, sizeof(double) * m * m, stream)) != cudaSuccess)
+                return cuda_fail(e, "backward: clear dA");
+            if ((e = launch_gram(lam, W, dA[mu], L, m, R, stream)) != cudaSuccess)
+                return cuda_fail(e, "backward: dA contraction");
+            if ((e = launch_finalize_grad(dA[mu], A[mu], dA[mu], m, false, stream)) != cudaSuccess)
+                return cuda_fail(e, "backward: dA mask");
+            launches += 2;
+        }
+        if (gen && dC && dC[mu]) {
+            if ((e = cudaMemsetAsync(dC[mu], 0, sizeof(double) * m * m, stream)) != cudaSuccess)
+                return cuda_fail(e, "backward: clear dC");
+            for (int nu = 0; nu < d; nu++) {
+                if (nu == mu) continue;
+                const double* W = nullptr;
+                if ((e = chain(mu, nu, &W)) != cudaSuccess) return cuda_fail(e, "backward: mode products");
+                if ((e = launch_gram(lam, W, dC[mu], L, m, R, stream)) != cudaSuccess)
+                    return cuda_fail(e, "backward: dC contraction");
+                launches++;
+            }
+            if ((e = launch_finalize_grad(dC[mu], C[mu], dC[mu], m, true, stream)) != cudaSuccess)
+                return cuda_fail(e, "backward: dC mask");
+            launches++;
+        }
+    }
+    if (cudaError_t e = cudaStreamSynchronize(stream); e != cudaSuccess)
+        return cuda_fail(e, "synchronize after backward");
+    if (info) {
+        *info = si;
+        info->launches = si.launches + launches;
+    }
+    return st;
 }
 
 }  // namespace tsylv

@@ -600,8 +600,16 @@ __device__ int group_inverse(const TileSmem<T, D, GEN>& sm, int e, T* out) {
     }
 }
 
+// One block T of the block grid: its right-hand-side update (split over the
+// `csize` CTAs of a cluster, this CTA being `rank`) and, on rank 0, its base
+// case.  The CTA's two staging barriers are initialised by the caller;
+// uses[s] counts the phases barrier s has completed so far (a persistent
+// caller runs many blocks on the same barriers).  Returns false when a wait
+// ran out of time (the error word is set; no copy of this call is left in
+// flight).
 template <typename T, int D, bool GENF>
-__global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
+__device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, const int rank, const int csize,
+                                          uint32_t (&uses)[2]) {
     using C = WaveCfg<T, D, GENF>;
     constexpr int TE = C::TE, TD = C::TD, TC = C::TC, EPT = C::EPT, NACC = C::NACC;
     constexpr bool GEN = C::GEN;
@@ -615,13 +623,8 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
     int* gl = gs + D * TE;           // [D][TE]
     int* ng = gl + D * TE;           // [D]
     int* bs = ng + D;                // [D]
-    int* flag = bs + D;              // [4]
 
     const int tid = threadIdx.x;
-    const int csize = a.csize;
-    const int rank = csize > 1 ? static_cast<int>(dev::cluster_rank()) : 0;
-    const int tix = blockIdx.x / csize;
-    const long long t = a.tiles[tix];
     int I[D];
 #pragma unroll
     for (int mu = 0; mu < D; mu++) I[mu] = static_cast<int>((t / a.tstride[mu]) % a.nb[mu]);
@@ -701,20 +704,14 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
         for (int q = 0; q < EPT; q++) acc[s][q] = T(0);
 
     if (tid == 0) {
-        dev::mbar_init(&bar[0], 1);
-        dev::mbar_init(&bar[1], 1);
-        dev::fence_mbar_init();
-        flag[0] = 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
+        dev::fence_proxy_async();
         if (njob > 0) issue(j0, 0);
         if (njob > 1) issue(j0 + 1, 1);
     }
     bool dead = false;
     for (int jj = 0; jj < njob && !dead; jj++) {
         const int stg = jj & 1;
-        const bool ok = dev::mbar_wait(&bar[stg], static_cast<uint32_t>((jj >> 1) & 1), a.timeout_ns);
+        const bool ok = dev::mbar_wait(&bar[stg], (uses[stg] + static_cast<uint32_t>(jj >> 1)) & 1u, a.timeout_ns);
         if (__syncthreads_or(!ok)) {
             dead = true;
             if (tid == 0) atomicOr(a.err, kErrTimeout);
@@ -730,9 +727,12 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
         }
     }
     if (dead && tid == 0) {
-        // let copies still in flight land before the buffers go away (bounded)
-        for (int jj = 0; jj < 2 && jj < njob; jj++) (void)dev::mbar_wait(&bar[jj], 0, a.timeout_ns / 8);
+        // let copies still in flight land before the buffers go away (bounded);
+        // the block is finished with whatever it holds (the error word is set)
+        for (int jj = 0; jj < 2 && jj < njob; jj++) (void)dev::mbar_wait(&bar[jj], uses[jj] & 1u, a.timeout_ns / 8);
     }
+    uses[0] += static_cast<uint32_t>((njob + 1) / 2);
+    uses[1] += static_cast<uint32_t>(njob / 2);
 
     // ---- partial sums -> shared memory, cluster reduction into rank 0
 #pragma unroll
@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
                 }
         }
         dev::cluster_sync();
-        if (rank != 0) return;
+        if (rank != 0) return !dead;
     }
 
     // ---- rank 0: base case of block T
@@ -1020,6 +1020,24 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
             }
         }
     }
+    return !dead;
+}
+
+template <typename T, int D, bool GENF>
+__global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
+    using C = WaveCfg<T, D, GENF>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::oBar);
+    const int csize = a.csize;
+    const int rank = csize > 1 ? static_cast<int>(dev::cluster_rank()) : 0;
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&bar[0], 1);
+        dev::mbar_init(&bar[1], 1);
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t uses[2] = {0u, 0u};
+    (void)wave_tile<T, D, GENF>(a, a.tiles[blockIdx.x / csize], rank, csize, uses);
 }
 
 template <typename T, int D, bool GEN>

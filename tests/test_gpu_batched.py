@@ -1,0 +1,134 @@
+"""Batched persistent solve (tsylv_solve_batched) on the GPU.
+
+Every equation of a batch must equal its own single solve (1e-12 relative,
+the batch runs the same block partition, updates and base case) and the
+oracle (1e-11).  Batches follow the batching workload: independent d = 3
+equations with every n_mu drawn uniformly from {8, ..., 48}.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+from tests.gpu_helpers import rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1905_09539_gb300 as ts
+    ts.load()
+    return ts
+
+
+def _problems(ps, gen):
+    out = []
+    for p in ps:
+        A = [to_dev(a) for a in p["A"]]
+        B = to_dev(p["B"])
+        out.append((A, B, [to_dev(c) for c in p["C"]]) if gen else (A, B))
+    return out
+
+
+def _single(lib, pr, gen):
+    if gen:
+        return lib.gtsylv_solve(pr[0], pr[2], pr[1])[0]
+    return lib.tsylv_solve(pr[0], pr[1])[0]
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_batch_small_vs_single_and_oracle(lib, gen):
+    ps = synthetic.batch(5, count=24, lo=8, hi=20)
+    ps = [synthetic.problem([5, 100 + i], p["shape"], generalized=gen,
+                            force_blocks=[[n // 2 - 1] for n in p["shape"]] if i % 3 == 0 else None)
+          for i, p in enumerate(ps)]
+    prs = _problems(ps, gen)
+    info = lib.Info()
+    Xs, st = lib.tsylv_solve_batched(prs, generalized=gen, info=info)
+    assert all(s == 0 for s in st)
+    assert info.launches >= 4
+    for p, pr, X in zip(ps, prs, Xs):
+        Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+        Xs1 = to_host(_single(lib, pr, gen))
+        Xb = to_host(X)
+        assert rel_err(Xb, Xs1) <= 1e-12
+        assert rel_err(Xb, Xo) <= 1e-11
+
+
+def test_batch_mixed_orders(lib):
+    shapes = [(37,), (5, 70), (16, 16), (9, 8, 7), (24, 17, 13), (4, 4, 4, 4), (9, 7, 5, 6), (1,), (1, 20, 9)]
+    ps = [synthetic.problem([6, i], s, force_blocks=[[n // 2 - 1] if n >= 4 else [] for n in s])
+          for i, s in enumerate(shapes)]
+    prs = _problems(ps, False)
+    Xs, st = lib.tsylv_solve_batched(prs)
+    assert all(s == 0 for s in st)
+    for p, X in zip(ps, Xs):
+        Xo = oracle.solve_backsub(p["A"], p["B"])
+        assert rel_err(to_host(X), Xo) <= 1e-11
+
+
+def test_batch_count_one_and_fixed_grid(lib):
+    p = synthetic.problem(7, (33, 30, 31), force_blocks=[[15], [14], [15]])
+    prs = _problems([p], False)
+    Xo = oracle.solve_backsub(p["A"], p["B"])
+    for split in (0, 1, 2):
+        Xs, st = lib.tsylv_solve_batched(prs, split=split)
+        assert st == [0]
+        assert rel_err(to_host(Xs[0]), Xo) <= 1e-11
+
+
+def test_batch_graph_replay_and_eager(lib):
+    ps = synthetic.batch(8, count=16, lo=8, hi=30)
+    prs = _problems(ps, False)
+    X1, _ = lib.tsylv_solve_batched(prs)
+    X2, _ = lib.tsylv_solve_batched(prs)
+    X3, _ = lib.tsylv_solve_batched(prs, use_graph=0)
+    for a, b, c in zip(X1, X2, X3):
+        assert torch.equal(a, b)
+        assert torch.equal(a, c)
+
+
+def test_batch_bad_structure(lib):
+    ps = synthetic.batch(9, count=4, lo=8, hi=12)
+    prs = _problems(ps, False)
+    A = prs[2][0][1].clone()
+    A[2, 1] = 0.5
+    A[3, 2] = 0.5  # two adjacent sub-diagonal entries
+    prs[2] = ([prs[2][0][0], A, prs[2][0][2]], prs[2][1])
+    with pytest.raises(lib.TsylvError) as ei:
+        lib.tsylv_solve_batched(prs)
+    assert ei.value.status == -6
+
+
+def test_batch_singular_status(lib):
+    ps = synthetic.batch(10, count=6, lo=8, hi=12)
+    # equation 4: a1_i + a2_j + a3_k = 0 at one position (no 2x2 blocks)
+    q = synthetic.problem([10, 4], (9, 8, 7), block_prob=0.0)
+    A = [a.copy() for a in q["A"]]
+    A[0][3, 3] = -(A[1][2, 2] + A[2][4, 4])
+    ps[4] = {"A": A, "B": q["B"], "C": None}
+    prs = _problems(ps, False)
+    Xs, st = lib.tsylv_solve_batched(prs, check=False)
+    assert st[4] == lib._lib.TSYLV_ESINGULAR
+    assert all(s == 0 for i, s in enumerate(st) if i != 4)
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_batch_workload_512(lib, gen):
+    """512 equations, n_mu ~ U{8..48}: each equals its single solve; a sample
+    of 12 equations against the oracle."""
+    ps = synthetic.batch(0, count=512, generalized=gen)
+    prs = _problems(ps, gen)
+    Xs, st = lib.tsylv_solve_batched(prs, generalized=gen)
+    assert all(s == 0 for s in st)
+    worst = 0.0
+    for pr, X in zip(prs, Xs):
+        worst = max(worst, rel_err(to_host(X), to_host(_single(lib, pr, gen))))
+    assert worst <= 1e-12, worst
+    rng = np.random.default_rng(11)
+    for i in rng.choice(512, size=12, replace=False):
+        p = ps[int(i)]
+        Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+        assert rel_err(to_host(Xs[int(i)]), Xo) <= 1e-11

@@ -73,3 +73,63 @@ def test_argument_validation_without_gpu(lib):
     assert lib.gtsylv_solve(2, n, fake, None, None, None, None, 0, ctypes.byref(o), None, None) == -4
     assert lib.tsylv_solve(2, n, fake, P(16), P(16), P(17), 1 << 30, ctypes.byref(o), None, None) == -6
     assert lib.tsylv_solve(2, n, fake, P(16), P(16), P(256), 16, ctypes.byref(o), None, None) == -7
+
+
+def test_backward_workspace_and_validation(lib):
+    from paper_1905_09539_gb300 import _lib
+    o = _lib.default_opts()
+    n = (ctypes.c_int64 * 3)(20, 16, 12)
+    N = 20 * 16 * 12
+    ws = lib.tsylv_workspace_bytes(3, n, 0, ctypes.byref(o))
+    wb = lib.tsylv_backward_workspace_bytes(3, n, 0, ctypes.byref(o))
+    wbg = lib.tsylv_backward_workspace_bytes(3, n, 1, ctypes.byref(o))
+    assert wb >= ws + N * 8           # transposed solve + Lambda
+    assert wbg >= wb + 2 * N * 8      # + two mode-product temporaries
+    P = ctypes.c_void_p
+    fake = (P * 3)(16, 16, 16)
+    assert lib.tsylv_backward(0, n, fake, None, P(16), P(16), None, None, None, P(256), 1 << 30,
+                              ctypes.byref(o), None, None) == -1
+    assert lib.tsylv_backward(3, n, None, None, P(16), P(16), None, None, None, P(256), 1 << 30,
+                              ctypes.byref(o), None, None) == -3
+    assert lib.tsylv_backward(3, n, fake, None, None, P(16), None, None, None, P(256), 1 << 30,
+                              ctypes.byref(o), None, None) == -5
+    assert lib.tsylv_backward(3, n, fake, None, P(16), None, None, None, None, P(256), 1 << 30,
+                              ctypes.byref(o), None, None) == -6
+    assert lib.tsylv_backward(3, n, fake, None, P(16), P(16), None, None, None, P(257), 1 << 30,
+                              ctypes.byref(o), None, None) == -10
+    assert lib.tsylv_backward(3, n, fake, None, P(16), P(16), None, None, None, P(256), 16,
+                              ctypes.byref(o), None, None) == -11
+
+
+def test_batched_workspace_and_validation(lib):
+    from paper_1905_09539_gb300 import _lib
+    o = _lib.default_opts()
+    count = 3
+    d = (ctypes.c_int * count)(3, 3, 2)
+    n = (ctypes.c_int64 * 8)(8, 48, 20, 33, 9, 17, 40, 40)
+    w = lib.tsylv_batched_workspace_bytes(count, d, n, 0, ctypes.byref(o))
+    wg = lib.tsylv_batched_workspace_bytes(count, d, n, 1, ctypes.byref(o))
+    N = 8 * 48 * 20 + 33 * 9 * 17 + 40 * 40
+    assert w >= N * 8 and wg > w
+    bad = (ctypes.c_int64 * 8)(8, 48, 0, 33, 9, 17, 40, 40)
+    assert lib.tsylv_batched_workspace_bytes(count, d, bad, 0, ctypes.byref(o)) == 0
+    o32 = _lib.default_opts(precision=_lib.TSYLV_FP32_REFINED)
+    assert lib.tsylv_batched_workspace_bytes(count, d, n, 0, ctypes.byref(o32)) == 0
+    P = ctypes.c_void_p
+    offA = (ctypes.c_int64 * 8)(*range(8))
+    offX = (ctypes.c_int64 * 3)(0, 1, 2)
+    per = (ctypes.c_int * count)()
+    args = lambda **kw: [kw.get("count", count), kw.get("d", d), kw.get("n", n), kw.get("offA", offA),
+                         kw.get("offX", offX), kw.get("A", P(256)), None, kw.get("B", P(256)),
+                         kw.get("X", P(256)), kw.get("work", P(256)), kw.get("wb", 1 << 40), ctypes.byref(o), per,
+                         None, None]
+    assert lib.tsylv_solve_batched(*args(count=0)) == -1
+    assert lib.tsylv_solve_batched(*args(d=None)) == -2
+    assert lib.tsylv_solve_batched(*args(n=bad)) == -3
+    assert lib.tsylv_solve_batched(*args(offA=None)) == -4
+    assert lib.tsylv_solve_batched(*args(offX=None)) == -5
+    assert lib.tsylv_solve_batched(*args(A=None)) == -6
+    assert lib.tsylv_solve_batched(*args(B=None)) == -8
+    assert lib.tsylv_solve_batched(*args(X=None)) == -9
+    assert lib.tsylv_solve_batched(*args(work=P(300))) == -10
+    assert lib.tsylv_solve_batched(*args(wb=16)) == -11
