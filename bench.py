@@ -1,15 +1,18 @@
 """Benchmark of the triangular tensor Sylvester solver on one GB300 (or N replicas).
 
-Workload (default): d = 3, n = 256^3, FP64, coefficients and right-hand side
-drawn by synthetic.py (seed 0): one step = one FP64 solve of the Laplace form
-(Eq. (2.2)) and one FP64 solve of the d-term generalized form, both through the
-C ABI on device-resident inputs; plus, when the library provides them, the
-mixed-precision refined solves of the same two problems to
-||B - A(X)|| / (||A|| ||X||) <= 1e-12.
-
+One step is one pass of the whole hot path on synthetic inputs (synthetic.py,
+seed 0), every call through the C ABI on device-resident inputs:
+  * d = 3, n = 256^3: FP64 solve and FP32-refined solve (to
+    ||B - A(X)|| / (||A|| ||X||) <= 1e-12) of the Laplace form (Eq. (2.2)) and
+    of the d-term generalized form;
+  * d = 3, n = (200, 160, 120), Laplace form: forward solve + adjoint (transposed
+    solve, masked dA) of L = 0.5 ||X - X*||^2, FP64 and FP32-refined;
+  * 512 independent d = 3 Laplace equations, n_mu ~ U{8..48}: one batched
+    persistent solve (FP64).
 Prints one JSON line (rank 0).  `value` = unknowns solved per second over the
-whole step (all ranks).  `--impl reference` times the CPU oracle on a bounded
-sample of the same workload instead.
+whole step (all ranks; a forward + adjoint pass counts two solves).
+`--impl reference` times the CPU oracle on bounded samples of the same step;
+`--fp64-peak` builds and runs the FP64 throughput probe (bench_fp64_peak.cu).
 
 Under torchrun (N > 1) every rank solves its own replica (the solve of one
 equation does not shard; there is no collective on the data path).
@@ -30,9 +33,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 peak measured on this machine's GB300 (DMMA m8n8k4 loop, 152 SMs; DFMA
-# 1.06, cuBLAS DGEMM 1.10): see profiles/fp64_peak_probe.txt
+# FP64 peak measured on this GB300 model (DMMA m8n8k4 loop over 152 SMs;
+# DFMA 1.06, cuBLAS DGEMM 1.10): `python bench.py --fp64-peak`
 FP64_PEAK_TFLOPS = 1.10
+# DRAM bytes (read + write) per launch of the dominant kernel from an ncu
+# capture of the same kernel; None until a capture of the current kernel exists
+TRAFFIC_PER_LAUNCH_BYTES = None
 
 
 def algorithmic_flops(A, C=None):
@@ -161,63 +167,156 @@ def barrier(ws):
         dist.barrier()
 
 
+# ----------------------------------------------------------------- workload
+
+SOLVE_PARTS = [("fp64_laplace", False, 0), ("fp64_generalized", True, 0),
+               ("fp32r_laplace", False, 1), ("fp32r_generalized", True, 1)]
+ADJ_SHAPE = (200, 160, 120)
+BATCH = dict(count=512, lo=8, hi=48)
+
+
+def laplace_flops_dense(shape):
+    """Leading-term algorithmic flops of one Laplace solve (no 2x2 blocks)."""
+    N = float(np.prod(shape))
+    return sum(2 * N / n * n * (n - 1) / 2 for n in shape) + N
+
+
+def gen_flops_dense(shape):
+    N = float(np.prod(shape))
+    d = len(shape)
+    return sum(2 * N / n * ((1 if mu in (0, d - 1) else 2) * n * (n - 1) / 2 + n * (n - 1) / 2)
+               for mu, n in enumerate(shape)) + N
+
+
+def grad_flops(shape):
+    """Flops of the masked contractions dA_mu (Laplace form): 2 n_mu N each (upper half used)."""
+    N = float(np.prod(shape))
+    return sum(N * n for n in shape)
+
+
 # ----------------------------------------------------------------- CPU oracle
 
-def oracle_sample(shape_lap, shape_gen, full_shape, seed=0):
-    """Time the oracle (O-B recursion, single thread) on bounded samples and
-    scale to the full workload by the algorithmic-flop ratio."""
+def oracle_step_seconds(sizes, seed=0):
+    """Single-thread oracle time of one step, from bounded samples scaled to
+    the full workload by the algorithmic-flop ratio of each part.
+
+    sizes: (laplace sample shape, generalized sample shape, adjoint sample
+    shape, number of batch equations sampled)."""
     import oracle
     import synthetic
-    out = {}
-    t_full = 0.0
-    for gen, shape in ((False, shape_lap), (True, shape_gen)):
+    sl, sg, sa, nb = sizes
+    full = (256, 256, 256)
+    detail = {}
+    t_step = 0.0
+    for gen, shape in ((False, sl), (True, sg)):
         p = synthetic.problem(seed, shape, generalized=gen)
         t0 = time.perf_counter()
         oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=8)
         dt = time.perf_counter() - t0
-        # flop ratio with the full-size counts (structure-independent leading terms)
-        fs = algorithmic_flops(p["A"], p["C"])
-        Nf = float(np.prod(full_shape))
-        if gen:
-            ff = sum(2 * Nf / n * (((1 if mu in (0, len(full_shape) - 1) else 2) * n * (n - 1) / 2) +
-                                   n * (n - 1) / 2) for mu, n in enumerate(full_shape)) + Nf
-        else:
-            ff = sum(2 * Nf / n * n * (n - 1) / 2 for n in full_shape) + Nf
-        t_full += dt * ff / fs
-        out["gen" if gen else "laplace"] = {"shape": list(shape), "seconds": dt}
-    return t_full, out
+        ff = gen_flops_dense(full) if gen else laplace_flops_dense(full)
+        scaled = dt * ff / algorithmic_flops(p["A"], p["C"])
+        t_step += 2 * scaled  # the FP64 and the refined part: one oracle solve each
+        detail["generalized" if gen else "laplace"] = {"shape": list(shape), "seconds": dt}
+    # adjoint: forward solve, transposed solve, masked contractions
+    p = synthetic.problem(seed, sa)
+    t0 = time.perf_counter()
+    X = oracle.solve_recursive(p["A"], p["B"], None, nmin=8)
+    Lam = oracle.solve_recursive(p["A"], X - p["Xstar"], None, nmin=8, transpose=True)
+    oracle.grad(p["A"], X, Lam)
+    dt = time.perf_counter() - t0
+    fs = 2 * algorithmic_flops(p["A"]) + grad_flops(sa)
+    ff = 2 * laplace_flops_dense(ADJ_SHAPE) + grad_flops(ADJ_SHAPE)
+    t_step += 2 * dt * ff / fs  # FP64 and refined adjoint parts
+    detail["adjoint"] = {"shape": list(sa), "seconds": dt}
+    # batch: the first nb equations, scaled by the flops of all of them
+    shapes = synthetic.batch_shapes(seed, BATCH["count"], BATCH["lo"], BATCH["hi"])
+    t0 = time.perf_counter()
+    fs = 0.0
+    for e in range(nb):
+        q = synthetic.problem([seed, 1 + e], shapes[e])
+        oracle.solve_recursive(q["A"], q["B"], None, nmin=8)
+        fs += algorithmic_flops(q["A"])
+    dt = time.perf_counter() - t0
+    ff = sum(laplace_flops_dense(s) for s in shapes)
+    t_step += dt * ff / fs
+    detail["batched"] = {"equations": nb, "seconds": dt}
+    return t_step, detail
+
+
+def step_units():
+    """Unknowns solved per step (a forward + adjoint pass counts two solves)."""
+    import synthetic
+    N = 256.0 ** 3
+    Na = float(np.prod(ADJ_SHAPE))
+    Nb = float(sum(np.prod(s) for s in synthetic.batch_shapes(0, BATCH["count"], BATCH["lo"], BATCH["hi"])))
+    return {"solves_256": 4 * N, "adjoint": 2 * 2 * Na, "batched": Nb}
+
+
+METRIC = ("unknowns/s (one step: d=3 256^3 Laplace + generalized, FP64 and FP32-refined to rel. residual <= 1e-12; "
+          "(200,160,120) forward + adjoint, FP64 and FP32-refined; 512-equation batch FP64); % of FP64 peak; "
+          "mixed-precision vs FP64 speed-up")
+WORKLOAD = ("d=3: 256^3 FP64 and FP32-refined solves (Laplace + generalized); (200,160,120) Laplace forward + "
+            "adjoint (FP64, FP32-refined); 512 Laplace equations n_mu~U{8..48} batched (FP64)")
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    full = (256, 256, 256)
-    N = float(np.prod(full))
+    units = sum(step_units().values())
     times = []
     for it in range(args.warmup + args.steps):
-        t_full, parts = oracle_sample((96, 96, 96), (64, 64, 64), full, seed=it % 3)
+        t, _ = oracle_step_seconds(((96, 96, 96), (64, 64, 64), (100, 80, 60), 32), seed=it % 3)
         if it >= args.warmup:
-            times.append(t_full)
-    # the oracle solves each of the four parts of a step (FP64 and refined,
-    # Laplace and generalized) in FP64: two Laplace and two generalized solves
-    step = 2 * float(np.mean(times))
-    value = 4 * N / step
+            times.append(t)
+    step = float(np.mean(times))
+    value = units / step
+    sample = ("oracle O-B (single thread) per step: 96^3 Laplace + 64^3 generalized (each counted for the FP64 and "
+              "the refined part), (100,80,60) forward + reversed-order transposed solve + gradient, 32 of the 512 "
+              "batch equations; "
+              "each part's time scaled to the full workload by its algorithmic-flop ratio")
     line = {
-        "impl": "reference",
-        "metric": "unknowns/s (d=3 256^3, Laplace + generalized, FP64 and FP32-refined to rel. residual <= 1e-12); "
-                  "% of FP64 peak; mixed-precision vs FP64 speed-up",
+        "impl": "reference", "metric": METRIC,
         "value": value, "unit": "unknowns/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (synthetic.py, seed 0..2)",
-        "config": {"workload": "d=3 n=256^3: FP64 solve and FP32-refined solve, Laplace + generalized form",
-                   "form": ["laplace", "generalized"],
-                   "sample": "oracle O-B on 96^3 (Laplace) + 64^3 (generalized), scaled by algorithmic flops"},
-        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                         "sample": "O-B recursion, 96^3 Laplace + 64^3 generalized per step (each solved twice: the "
-                                   "FP64 and the refined part), time scaled to 256^3 by the algorithmic-flop ratio"},
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_fp64_peak():
+    """Build and run the FP64 throughput probe; print its JSON lines."""
+    import shutil
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    out_dir = os.path.join(ROOT, "paper_1905_09539_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    exe = os.path.join(out_dir, "fp64_peak")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
+                    os.path.join(ROOT, "bench_fp64_peak.cu")], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    sys.stdout.write(r.stdout)
+    try:
+        import torch
+        a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+        b = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            a @ b
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(3):
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        print(json.dumps({"kernel": "cublas_dgemm_4096", "tflops": 2 * 4096 ** 3 / (best * 1e-3) / 1e12}))
+    except Exception as ex:  # the probe above is the measurement; the DGEMM line is context
+        print(json.dumps({"kernel": "cublas_dgemm_4096", "error": str(ex)}))
+    sys.exit(r.returncode)
 
 
 # ------------------------------------------------------------------ GPU path
@@ -232,6 +331,7 @@ def run_ours(args, ws, rank, local):
     ts.load()
     shape = (args.n, args.n, args.n)
     N = float(np.prod(shape))
+    PREC = {0: _lib.TSYLV_FP64, 1: _lib.TSYLV_FP32_REFINED}
 
     def to_dev(a):
         a = np.asfortranarray(a)
@@ -240,35 +340,56 @@ def run_ours(args, ws, rank, local):
         out.copy_(t)
         return out
 
+    # ---- inputs (device resident)
     probs = {}
     for gen in (False, True):
         p = synthetic.problem(args.seed + rank, shape, generalized=gen)
         probs[gen] = {
-            "np": p,
             "A": [to_dev(a) for a in p["A"]],
             "C": [to_dev(c) for c in p["C"]] if gen else None,
             "B": to_dev(p["B"]),
-            "X": ts.empty_fortran(shape, dev),
+            "X": {0: ts.empty_fortran(shape, dev), 1: ts.empty_fortran(shape, dev)},
             "flops": algorithmic_flops(p["A"], p["C"]),
         }
+    pa = synthetic.problem(args.seed + rank, ADJ_SHAPE)
+    adj = {"A": [to_dev(a) for a in pa["A"]], "B": to_dev(pa["B"]), "Xs": to_dev(pa["Xstar"]),
+           "X": {0: ts.empty_fortran(ADJ_SHAPE, dev), 1: ts.empty_fortran(ADJ_SHAPE, dev)}, "out": {}}
+    bps = synthetic.batch(args.seed + rank, **BATCH)
+    pools = ts.BatchPools([([to_dev(a) for a in q["A"]], to_dev(q["B"])) for q in bps])
     stream = torch.cuda.current_stream(dev)
-    PARTS = [("fp64_laplace", False, _lib.TSYLV_FP64), ("fp64_generalized", True, _lib.TSYLV_FP64),
-             ("fp32r_laplace", False, _lib.TSYLV_FP32_REFINED), ("fp32r_generalized", True, _lib.TSYLV_FP32_REFINED)]
-    infos = {name: _lib.Info() for name, _, _ in PARTS}
-    for gen in (False, True):
-        probs[gen]["Xr"] = ts.empty_fortran(shape, dev)
+    infos = {name: _lib.Info() for name, _, _ in SOLVE_PARTS}
+    infos.update({"adjoint_fp64_fwd": _lib.Info(), "adjoint_fp64_bwd": _lib.Info(),
+                  "adjoint_fp32r_fwd": _lib.Info(), "adjoint_fp32r_bwd": _lib.Info(), "batched_fp64": _lib.Info()})
 
     def solve(name, gen, prec, timing=0):
         pr = probs[gen]
-        X = pr["X"] if prec == _lib.TSYLV_FP64 else pr["Xr"]
         if gen:
-            ts.gtsylv_solve(pr["A"], pr["C"], pr["B"], X=X, info=infos[name], timing=timing, precision=prec)
+            ts.gtsylv_solve(pr["A"], pr["C"], pr["B"], X=pr["X"][prec], info=infos[name], timing=timing,
+                            precision=PREC[prec])
         else:
-            ts.tsylv_solve(pr["A"], pr["B"], X=X, info=infos[name], timing=timing, precision=prec)
+            ts.tsylv_solve(pr["A"], pr["B"], X=pr["X"][prec], info=infos[name], timing=timing, precision=PREC[prec])
 
-    def step(timing=0):
-        for name, gen, prec in PARTS:
-            solve(name, gen, prec, timing)
+    def adjoint(prec):
+        tag = "adjoint_fp64" if prec == 0 else "adjoint_fp32r"
+        X = adj["X"][prec]
+        ts.tsylv_solve(adj["A"], adj["B"], X=X, info=infos[tag + "_fwd"], precision=PREC[prec])
+        # dL/dX of L = 0.5 ||X - X*||^2 (one elementwise torch op: marshalling of the loss, not the path)
+        dX = X - adj["Xs"]
+        adj["out"][prec] = ts.tsylv_backward(adj["A"], X, dX, want_dB=True, want_dA=True,
+                                             info=infos[tag + "_bwd"], precision=PREC[prec])
+
+    def batched():
+        pools.solve(info=infos["batched_fp64"])
+
+    def step():
+        for name, gen, prec in SOLVE_PARTS:
+            solve(name, gen, prec)
+        adjoint(0)
+        adjoint(1)
+        batched()
+
+    def launches_of_step():
+        return sum(i.launches for i in infos.values())
 
     for _ in range(args.warmup):
         step()
@@ -284,32 +405,43 @@ def run_ours(args, ws, rank, local):
         e0.record(stream)
         for _ in range(args.steps):
             step()
-            launches += sum(infos[name].launches for name, _, _ in PARTS)
+            launches += launches_of_step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(ws)
     clocks = clk.summary()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, ws, dev)
-    units = sum_over_ranks(len(PARTS) * N, ws, dev)
+    units_rank = step_units()
+    units = sum_over_ranks(sum(units_rank.values()), ws, dev)
     value = units / (ms * 1e-3)
 
-    # ---- per-solve timing (CUDA events recorded on the launching stream inside
-    # the captured graphs: whole call, wavefront launches, residual launches)
-    tim = {name: {"tot": [], "wave": [], "res": []} for name, _, _ in PARTS}
+    # ---- per-part timing: solves with the calls' own CUDA events (recorded on
+    # the launching stream inside the captured graphs); adjoint and batch with
+    # events around the calls
+    tim = {name: {"tot": [], "wave": [], "res": []} for name, _, _ in SOLVE_PARTS}
     for _ in range(max(3, args.steps)):
-        for name, gen, prec in PARTS:
+        for name, gen, prec in SOLVE_PARTS:
             solve(name, gen, prec, timing=1)
             tim[name]["tot"].append(infos[name].t_total_ms)
             tim[name]["wave"].append(infos[name].t_waves_ms)
             tim[name]["res"].append(infos[name].t_resid_ms)
-    # residual of every result, measured independently of the solve with the
-    # library's FP64-pipe residual
+
+    def event_ms(fn, reps):
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            out.append(e0.elapsed_time(e1))
+        return float(np.median(out))
+
     parts = {}
-    for name, gen, prec in PARTS:
+    for name, gen, prec in SOLVE_PARTS:
         pr = probs[gen]
-        X = pr["X"] if prec == _lib.TSYLV_FP64 else pr["Xr"]
-        _, rho, _ = ts.tsylv_residual(pr["A"], pr["B"], X, pr["C"], residual=_lib.TSYLV_RESID_FP64)
+        _, rho, _ = ts.tsylv_residual(pr["A"], pr["B"], pr["X"][prec], pr["C"], residual=_lib.TSYLV_RESID_FP64)
         f = pr["flops"]
         tm = float(np.median(tim[name]["tot"]))
         parts[name] = {
@@ -317,10 +449,29 @@ def run_ours(args, ws, rank, local):
             "iterations": infos[name].iterations, "rel_residual_fp64": rho, "waves": infos[name].waves,
             "tiles": infos[name].tiles, "unknowns_per_s": N / (tm * 1e-3),
         }
-        if prec == _lib.TSYLV_FP64:
+        if prec == 0:
             parts[name].update({"algorithmic_gflop": f / 1e9, "executed_gflop": infos[name].flops / 1e9,
                                 "tflops_algorithmic": f / (tm * 1e-3) / 1e12,
                                 "frac_fp64_peak": f / (tm * 1e-3) / 1e12 / FP64_PEAK_TFLOPS})
+    Na = float(np.prod(ADJ_SHAPE))
+    fa = 2 * algorithmic_flops([a.cpu().numpy() for a in adj["A"]]) + grad_flops(ADJ_SHAPE)
+    for prec in (0, 1):
+        tag = "adjoint_fp64" if prec == 0 else "adjoint_fp32r"
+        tm = event_ms(lambda: adjoint(prec), max(3, args.steps))
+        dB, dA, _ = adj["out"][prec]
+        dB0, dA0, _ = adj["out"][0]
+        parts[tag] = {"ms": tm, "unknowns_per_s": 2 * Na / (tm * 1e-3), "algorithmic_gflop": fa / 1e9,
+                      "tflops_algorithmic": fa / (tm * 1e-3) / 1e12,
+                      "iterations_fwd_bwd": [infos[tag + "_fwd"].iterations, infos[tag + "_bwd"].iterations]}
+        if prec == 1:
+            parts[tag]["rel_diff_vs_fp64"] = {
+                "dB": float(torch.linalg.vector_norm(dB - dB0) / torch.linalg.vector_norm(dB0)),
+                "dA": max(float(torch.linalg.matrix_norm(a - b) / torch.linalg.matrix_norm(b)) for a, b in zip(dA, dA0))}
+    tb = event_ms(batched, max(3, args.steps))
+    ib = infos["batched_fp64"]
+    parts["batched_fp64"] = {"ms": tb, "unknowns_per_s": units_rank["batched"] / (tb * 1e-3), "equations": pools.count,
+                             "unknowns": pools.unknowns, "tiles": ib.tiles, "max_waves": ib.waves,
+                             "queue_order": ib.batch_order, "ctas_per_sm": ib.batch_ctas_per_sm}
     mixed_vs_fp64 = {"laplace": parts["fp64_laplace"]["ms"] / parts["fp32r_laplace"]["ms"],
                      "generalized": parts["fp64_generalized"]["ms"] / parts["fp32r_generalized"]["ms"]}
     dom = "fp64_generalized"  # the generalized FP64 wavefront kernel carries most of the step
@@ -330,31 +481,47 @@ def run_ours(args, ws, rank, local):
     achieved = (f_dom / nwaves) / (w_dom * 1e-3 / nwaves) / 1e12
     roofline = {"bound": "alu", "kernel": "k_wave<double,3,generalized>", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None,
-                "peak_source": "measured FP64 DMMA/DFMA probe on this GB300 (MEASURED_PEAKS.json has no FP64 "
-                               "entry; bf16 1956.8 x 1.25/2250 nominal ratio gives 1.09)",
+                "traffic": TRAFFIC_PER_LAUNCH_BYTES,
+                "peak_source": "of measured: FP64 DMMA/DFMA probe on this GB300 (bench_fp64_peak.cu); "
+                               "MEASURED_PEAKS.json has no FP64 entry (its bf16 1956.8 x 1.25/2250 gives 1.09)",
                 "per_launch_gflop": f_dom / nwaves / 1e9, "per_launch_ms": w_dom / nwaves}
 
-    # ---- end to end: pinned host buffers, H2D + solve + D2H inside the timed region
+    # ---- end to end through the public API: pinned host buffers, H2D of every
+    # input and D2H of every result inside the timed region
     host = {}
     h2d = d2h = 0
+    rev = lambda t: t.permute(*range(t.dim() - 1, -1, -1))
     for gen in (False, True):
         pr = probs[gen]
-        hb = torch.empty(pr["B"].shape[::-1], dtype=torch.float64).pin_memory().permute(2, 1, 0)
+        hb = rev(torch.empty(pr["B"].shape[::-1], dtype=torch.float64).pin_memory())
         hb.copy_(pr["B"])
         hA = [a.cpu().pin_memory() for a in pr["A"]]
-        hC = [c.cpu().pin_memory() for c in pr["C"]] if gen else None
-        hx = torch.empty(pr["B"].shape[::-1], dtype=torch.float64).pin_memory().permute(2, 1, 0)
+        hC = [c.cpu().pin_memory() for c in pr["C"]] if gen else []
+        hx = rev(torch.empty(pr["B"].shape[::-1], dtype=torch.float64).pin_memory())
         host[gen] = (hb, hA, hC, hx)
-    for name, gen, prec in PARTS:
+    for name, gen, prec in SOLVE_PARTS:
         hb, hA, hC, hx = host[gen]
-        h2d += hb.numel() * 8 + sum(a.numel() * 8 for a in hA) + (sum(c.numel() * 8 for c in hC) if gen else 0)
+        h2d += hb.numel() * 8 + sum(a.numel() * 8 for a in hA) + sum(c.numel() * 8 for c in hC)
         d2h += hx.numel() * 8
+    hadj_B = rev(torch.empty(ADJ_SHAPE[::-1], dtype=torch.float64).pin_memory())
+    hadj_B.copy_(adj["B"])
+    hadj_Xs = rev(torch.empty(ADJ_SHAPE[::-1], dtype=torch.float64).pin_memory())
+    hadj_Xs.copy_(adj["Xs"])
+    hadj_A = [a.cpu().pin_memory() for a in adj["A"]]
+    hadj_dB = rev(torch.empty(ADJ_SHAPE[::-1], dtype=torch.float64).pin_memory())
+    hadj_dA = [torch.empty(a.shape, dtype=torch.float64).pin_memory() for a in adj["A"]]
+    h2d += 2 * (hadj_B.numel() * 8 + hadj_Xs.numel() * 8 + sum(a.numel() * 8 for a in hadj_A))
+    d2h += 2 * (hadj_dB.numel() * 8 + sum(a.numel() * 8 for a in hadj_dA))
+    hpB = pools.B.cpu().pin_memory()
+    hpA = pools.A.cpu().pin_memory()
+    hpX = torch.empty_like(hpB).pin_memory()
+    h2d += hpB.numel() * 8 + hpA.numel() * 8
+    d2h += hpX.numel() * 8
     barrier(ws)
     torch.cuda.synchronize(dev)
     e0.record(stream)
     for _ in range(args.steps):
-        for name, gen, prec in PARTS:
+        for name, gen, prec in SOLVE_PARTS:
             pr = probs[gen]
             hb, hA, hC, hx = host[gen]
             pr["B"].copy_(hb, non_blocking=True)
@@ -364,35 +531,54 @@ def run_ours(args, ws, rank, local):
                 for c, h in zip(pr["C"], hC):
                     c.copy_(h, non_blocking=True)
             solve(name, gen, prec)
-            hx.copy_(pr["X"] if prec == _lib.TSYLV_FP64 else pr["Xr"], non_blocking=True)
+            hx.copy_(pr["X"][prec], non_blocking=True)
+        for prec in (0, 1):
+            adj["B"].copy_(hadj_B, non_blocking=True)
+            adj["Xs"].copy_(hadj_Xs, non_blocking=True)
+            for a, h in zip(adj["A"], hadj_A):
+                a.copy_(h, non_blocking=True)
+            adjoint(prec)
+            dB, dA, _ = adj["out"][prec]
+            hadj_dB.copy_(dB, non_blocking=True)
+            for h, g in zip(hadj_dA, dA):
+                h.copy_(g, non_blocking=True)
+        pools.B.copy_(hpB, non_blocking=True)
+        pools.A.copy_(hpA, non_blocking=True)
+        batched()
+        hpX.copy_(pools.X, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(ws)
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws, dev)
 
     line = {
-        "metric": "unknowns/s (d=3 256^3, Laplace + generalized, FP64 and FP32-refined to rel. residual <= 1e-12); "
-                  "% of FP64 peak; mixed-precision vs FP64 speed-up",
+        "metric": METRIC,
         "value": value, "unit": "unknowns/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (synthetic.py, seed %d)" % args.seed,
-        "config": {"workload": "d=3 n=%d^3: FP64 solve and FP32-refined solve, Laplace + generalized form" % args.n,
-                   "form": ["laplace", "generalized"], "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "inputs larger than L2 (%.0f MB per tensor)" % (N * 8 / 1e6)},
+        "config": {"workload": WORKLOAD.replace("256^3", "%d^3" % args.n),
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (%.0f MB per 256^3 tensor); no flush" % (N * 8 / 1e6),
+                   "units_per_step": units_rank},
         "parts": parts,
         "mixed_vs_fp64": mixed_vs_fp64,
         "roofline": roofline,
-        "e2e": {"value": sum_over_ranks(len(PARTS) * N, ws, dev) / (e2e_ms * 1e-3), "unit": "unknowns/s",
+        "e2e": {"value": units / (e2e_ms * 1e-3), "unit": "unknowns/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:
-        t_full, samp = oracle_sample((128, 128, 128), (96, 96, 96), shape, seed=args.seed)
-        line["cpu_baseline"] = {"value": 4 * N / (2 * t_full), "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                                "sample": "O-B recursion on 128^3 (Laplace, %.1f s) + 96^3 (generalized, %.1f s), "
-                                          "time scaled to %d^3 by the algorithmic-flop ratio" %
-                                          (samp["laplace"]["seconds"], samp["gen"]["seconds"], args.n)}
+        t_step, samp = oracle_step_seconds(((160, 160, 160), (112, 112, 112), (160, 128, 96), 512),
+                                           seed=args.seed)
+        line["cpu_baseline"] = {
+            "value": sum(units_rank.values()) / t_step, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle O-B, single thread: 160^3 Laplace (%.1f s) + 112^3 generalized (%.1f s), each counted "
+                      "for the FP64 and the refined part; (160,128,96) forward + transposed solve + gradient "
+                      "(%.1f s, counted for both adjoint parts); all 512 batch equations (%.1f s); each part's time "
+                      "scaled to the step's workload by its algorithmic-flop ratio" %
+                      (samp["laplace"]["seconds"], samp["generalized"]["seconds"], samp["adjoint"]["seconds"],
+                       samp["batched"]["seconds"])}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -406,7 +592,11 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--fp64-peak", action="store_true", help="build and run the FP64 throughput probe")
     args = ap.parse_args()
+    if args.fp64_peak:
+        run_fp64_peak()
+        return
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -40,7 +40,7 @@ def _load():
         i64p = ctypes.POINTER(ctypes.c_int64)
         lib.orc_apply.argtypes = [ctypes.c_int, i64p, P, P, P, P, ctypes.c_int]
         lib.orc_backsub.argtypes = [ctypes.c_int, i64p, P, P, P, ctypes.c_int]
-        lib.orc_recursive.argtypes = [ctypes.c_int, i64p, P, P, P, ctypes.c_int64]
+        lib.orc_recursive.argtypes = [ctypes.c_int, i64p, P, P, P, ctypes.c_int64, ctypes.c_int]
         lib.orc_grad.argtypes = [ctypes.c_int, i64p, P, P, P, P, P, P]
         lib.orc_check_structure.argtypes = [ctypes.c_int, i64p, P]
         for f in (lib.orc_apply, lib.orc_backsub, lib.orc_recursive, lib.orc_grad, lib.orc_check_structure):
@@ -93,13 +93,14 @@ def solve_backsub(A, B, C=None, transpose=False):
     return X
 
 
-def solve_recursive(A, B, C=None, nmin=4):
-    """O-B: Alg. 2 recursion (Laplace form) / its d-term generalized analogue."""
+def solve_recursive(A, B, C=None, nmin=4, transpose=False):
+    """O-B: Alg. 2 recursion (Laplace form) / its d-term generalized analogue;
+    transpose=True solves A^T(X) = B with the reversed recursion order."""
     X = np.array(B, dtype=np.float64, order="F", copy=True)
     A_, pa = _mats(A)
     C_, pc = _mats(C)
     d, n = _dims(X)
-    _check(_load().orc_recursive(d, n, pa, pc, X.ctypes.data, int(nmin)), "orc_recursive")
+    _check(_load().orc_recursive(d, n, pa, pc, X.ctypes.data, int(nmin), 1 if transpose else 0), "orc_recursive")
     return X
 
 

@@ -254,6 +254,22 @@ static int backsub_box(const orc_ctx* c, double* X, const int64_t* off, const in
                 else { lo[mu] = off[mu]; hi[mu] = g[mu] + sz[mu]; }
                 v[mu] = lo[mu];
             }
+            if (c->C == NULL) {
+                /* Laplace form: the Kronecker sum Eq. (1.4) couples u only with
+                 * positions on one of its mode lines, v = u except in mode mu */
+                for (int mu = 0; mu < d; mu++) {
+                    for (int q = 0; q < d; q++) v[q] = u[q];
+                    for (int64_t k = lo[mu]; k < hi[mu]; k++) {
+                        if (k >= g[mu] && k < g[mu] + sz[mu]) continue;   /* inside the group */
+                        v[mu] = k;
+                        double e = transpose ? op_entry(d, c->n, c->A, c->C, v, u)
+                                             : op_entry(d, c->n, c->A, c->C, u, v);
+                        if (e != 0.0) acc -= e * X[lin(c, v)];
+                    }
+                }
+                rhs[p] = acc;
+                continue;
+            }
             for (;;) {
                 int in_group = 1;
                 for (int mu = 0; mu < d; mu++) if (v[mu] < g[mu] || v[mu] >= g[mu] + sz[mu]) { in_group = 0; break; }
@@ -332,26 +348,36 @@ static void box_io(const orc_ctx* c, double* X, const int64_t* off, const int64_
  * M_{term,mu}(off+0:k, off+k:m) and in every other mode the diagonal block
  * of the current sub-problem.  For the Laplace form only term == mu survives
  * (the identity has no off-diagonal block). */
-static int rec_update(rec_ctx* r, int mu, const int64_t* off, const int64_t* ext, int64_t k) {
+/* Transposed operator (lower block triangular coefficients M^T): the solved
+ * part is the leading one, X1 (mode-mu rows [off, off+k)), and the update goes
+ * to the trailing right-hand side,
+ *   B2 -= sum_term X1 x_1 M_{term,1}^T ... x_d M_{term,d}^T
+ * with M_{term,mu}(off+0:k, off+k:m)^T in the split mode. */
+static int rec_update(rec_ctx* r, int mu, const int64_t* off, const int64_t* ext, int64_t k, int transpose) {
     const orc_ctx* c = &r->c; int d = c->d;
     int64_t m = ext[mu];
     int64_t e2[ORC_MAXD], o2[ORC_MAXD], e1[ORC_MAXD];
     for (int q = 0; q < d; q++) { e2[q] = ext[q]; o2[q] = off[q]; e1[q] = ext[q]; }
     e2[mu] = m - k; o2[mu] = off[mu] + k; e1[mu] = k;
-    int64_t N2 = prod_range(e2, 0, d), N1 = prod_range(e1, 0, d);
-    int64_t Nmax = N2 > N1 ? N2 : N1;
-    double* x2 = (double*)malloc(sizeof(double) * (size_t)N2);
+    /* source box (solved) and target box (right-hand side to update) */
+    const int64_t* so = transpose ? off : o2;
+    const int64_t* se = transpose ? e1 : e2;
+    const int64_t* to = transpose ? o2 : off;
+    const int64_t* te = transpose ? e2 : e1;
+    int64_t Ns = prod_range(se, 0, d), Nt = prod_range(te, 0, d);
+    int64_t Nmax = Ns > Nt ? Ns : Nt;
+    double* xs = (double*)malloc(sizeof(double) * (size_t)Ns);
     double* t0 = (double*)malloc(sizeof(double) * (size_t)Nmax);
     double* t1 = (double*)malloc(sizeof(double) * (size_t)Nmax);
-    double* b1 = (double*)malloc(sizeof(double) * (size_t)N1);
-    if (!x2 || !t0 || !t1 || !b1) { free(x2); free(t0); free(t1); free(b1); return -1; }
-    box_io(c, r->X, o2, e2, x2, 1);
-    box_io(c, r->X, off, e1, b1, 1);
+    double* bt = (double*)malloc(sizeof(double) * (size_t)Nt);
+    if (!xs || !t0 || !t1 || !bt) { free(xs); free(t0); free(t1); free(bt); return -1; }
+    box_io(c, r->X, so, se, xs, 1);
+    box_io(c, r->X, to, te, bt, 1);
     for (int term = 0; term < d; term++) {
         if (c->C == NULL && term != mu) continue;
         int64_t cur[ORC_MAXD];
-        for (int q = 0; q < d; q++) cur[q] = e2[q];
-        memcpy(t0, x2, sizeof(double) * (size_t)N2);
+        for (int q = 0; q < d; q++) cur[q] = se[q];
+        memcpy(t0, xs, sizeof(double) * (size_t)Ns);
         for (int eta = 0; eta < d; eta++) {
             const double* M;
             if (eta == term) M = c->A[eta];
@@ -359,46 +385,61 @@ static int rec_update(rec_ctx* r, int mu, const int64_t* off, const int64_t* ext
             else M = c->C[eta];
             int64_t ld = c->n[eta];
             if (eta == mu) {
-                mode_product_block(d, cur, eta, M, ld, off[mu], off[mu] + k, k, 0, t0, t1);
-                cur[eta] = k;
+                /* rows of the off-diagonal block: leading indices off..off+k-1,
+                 * columns: trailing indices off+k..off+m-1 */
+                if (!transpose)
+                    mode_product_block(d, cur, eta, M, ld, off[mu], off[mu] + k, k, 0, t0, t1);
+                else
+                    mode_product_block(d, cur, eta, M, ld, off[mu] + k, off[mu], m - k, 1, t0, t1);
+                cur[eta] = te[mu];
             } else {
-                mode_product_block(d, cur, eta, M, ld, off[eta], off[eta], ext[eta], 0, t0, t1);
+                mode_product_block(d, cur, eta, M, ld, off[eta], off[eta], ext[eta], transpose, t0, t1);
             }
             double* t = t0; t0 = t1; t1 = t;
         }
-        for (int64_t q = 0; q < N1; q++) b1[q] -= t0[q];
+        for (int64_t q = 0; q < Nt; q++) bt[q] -= t0[q];
     }
-    box_io(c, r->X, off, e1, b1, 0);
-    free(x2); free(t0); free(t1); free(b1);
+    box_io(c, r->X, to, te, bt, 0);
+    free(xs); free(t0); free(t1); free(bt);
     return 0;
 }
 
-static int rec_solve(rec_ctx* r, const int64_t* off, const int64_t* ext) {
+/* transpose = 1: the same split tree for A^T (lower block triangular
+ * coefficients) -- the leading part is solved first and updates the
+ * trailing right-hand side (the recursion order reversed). */
+static int rec_solve(rec_ctx* r, const int64_t* off, const int64_t* ext, int transpose) {
     const orc_ctx* c = &r->c; int d = c->d;
     int mu = 0;
     for (int q = 1; q < d; q++) if (ext[q] > ext[mu]) mu = q;    /* lowest mode on ties */
-    if (ext[mu] <= r->nmin) return backsub_box(c, r->X, off, ext, 0);
+    if (ext[mu] <= r->nmin) return backsub_box(c, r->X, off, ext, transpose);
     int64_t m = ext[mu], k = m / 2;
     /* Alg. 2, line 3: do not cut a 2x2 block, i.e. A_mu(k+1, k) != 0 (1-based) */
     if (c->A[mu][(off[mu] + k) + c->n[mu] * (off[mu] + k - 1)] != 0.0) k += 1;
-    if (k >= m) return backsub_box(c, r->X, off, ext, 0);
+    if (k >= m) return backsub_box(c, r->X, off, ext, transpose);
     int64_t o2[ORC_MAXD], e2[ORC_MAXD], e1[ORC_MAXD];
     for (int q = 0; q < d; q++) { o2[q] = off[q]; e2[q] = ext[q]; e1[q] = ext[q]; }
     o2[mu] = off[mu] + k; e2[mu] = m - k; e1[mu] = k;
-    int s = rec_solve(r, o2, e2);                   /* Alg. 2, line 5 */
+    if (!transpose) {
+        int s = rec_solve(r, o2, e2, 0);                   /* Alg. 2, line 5 */
+        if (s) return s;
+        if (rec_update(r, mu, off, ext, k, 0)) return -1;  /* Alg. 2, line 6 */
+        return rec_solve(r, off, e1, 0);                   /* Alg. 2, line 7 (with the updated B1) */
+    }
+    int s = rec_solve(r, off, e1, 1);
     if (s) return s;
-    if (rec_update(r, mu, off, ext, k)) return -1;  /* Alg. 2, line 6 */
-    return rec_solve(r, off, e1);                   /* Alg. 2, line 7 (with the updated B1) */
+    if (rec_update(r, mu, off, ext, k, 1)) return -1;
+    return rec_solve(r, o2, e2, 1);
 }
 
-/* O-B: Alg. 2 recursion with leaf size nmin (>= 1). X: B on entry, X on exit. */
+/* O-B: Alg. 2 recursion with leaf size nmin (>= 1) for A (transpose = 0) or
+ * A^T (transpose = 1). X: B on entry, X on exit. */
 int orc_recursive(int d, const int64_t* n, const double* const* A, const double* const* C,
-                  double* X, int64_t nmin) {
+                  double* X, int64_t nmin, int transpose) {
     if (orc_check_structure(d, n, A) || nmin < 1) return -1;
     rec_ctx r; r.X = X; r.nmin = nmin;
     if (ctx_init(&r.c, d, n, A, C)) { ctx_free(&r.c); return -1; }
     int64_t off[ORC_MAXD] = {0};
-    int s = rec_solve(&r, off, n);
+    int s = rec_solve(&r, off, n, transpose ? 1 : 0);
     ctx_free(&r.c);
     return s;
 }

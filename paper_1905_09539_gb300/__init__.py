@@ -20,7 +20,7 @@ from ._lib import (TSYLV_BF16_REFINED, TSYLV_FP32_REFINED, TSYLV_FP64, TSYLV_RES
                    TSYLV_TF32_REFINED, Info, Opts, default_opts, load, status_string)
 
 __all__ = ["tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
-           "tsylv_residual", "tsylv_backward", "tsylv_solve_batched", "solve", "fortran", "TsylvError",
+           "tsylv_residual", "tsylv_backward", "tsylv_solve_batched", "BatchPools", "solve", "fortran", "TsylvError",
            "Opts", "Info", "default_opts", "TSYLV_FP64", "TSYLV_FP32_REFINED", "TSYLV_TF32_REFINED",
            "TSYLV_BF16_REFINED", "TSYLV_RESID_DF64", "TSYLV_RESID_FP64", "workspace"]
 
@@ -215,4 +215,4 @@ def tsylv_backward(A, X, dX, C=None, *, want_dB=True, want_dA=True, want_dC=True
 
 
 from .autograd import solve  # noqa: E402
-from .batched import tsylv_solve_batched  # noqa: E402
+from .batched import BatchPools, tsylv_solve_batched  # noqa: E402

@@ -65,7 +65,7 @@ struct BatchPlan {
 
 // Regions of the batched workspace (byte offsets from its base).
 struct BatchLayout {
-    size_t ctl = 0;    // heads [4], done [count], errs [count]
+    size_t ctl = 0;    // heads [4], abort, pad [3], done [count], errs [count]
     size_t sub = 0;    // sub-diagonals of every A_mu, then the gather tables
     size_t tab = 0;    // WaveArgs [count], BatchGeom [count], jobs, coefficient jobs, partition ints
     size_t data = 0;   // block tensors and coefficient tiles
@@ -103,7 +103,7 @@ BatchLayout make_batch_layout(int count, const int* d, const int64_t* n_packed, 
     BatchLayout L;
     size_t off = 0;
     L.ctl = off;
-    off += al256((4 + 2 * static_cast<size_t>(count)) * sizeof(int));
+    off += al256((8 + 2 * static_cast<size_t>(count)) * sizeof(int));
     size_t nsub = 0, nmats = 0, k = 0;
     for (int e = 0; e < count; e++)
         for (int mu = 0; mu < d[e]; mu++, k++) {
@@ -339,7 +339,7 @@ void fill_table(const BatchPlan& p, const BatchLayout& L, char* base, int policy
     out.assign(L.tab_bytes, 0);
     char* dev_tab = base + L.tab;
     char* dev_data = base + L.data;
-    int* errs = reinterpret_cast<int*>(base + L.ctl) + 4 + p.count;
+    int* errs = reinterpret_cast<int*>(base + L.ctl) + 8 + p.count;
     const int* dev_part = reinterpret_cast<const int*>(dev_tab + L.o_part);
     int* hpart = reinterpret_cast<int*>(out.data() + L.o_part);
     WaveArgs* hw = reinterpret_cast<WaveArgs*>(out.data() + L.o_wave);
@@ -464,7 +464,7 @@ cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
     int* ctl = reinterpret_cast<int*>(c.base + c.L.ctl);
     char* tab = c.base + c.L.tab;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(ctl, 0, (4 + 2 * static_cast<size_t>(p.count)) * sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctl, 0, (8 + 2 * static_cast<size_t>(p.count)) * sizeof(int), s)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(tab, c.htab, c.L.tab_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
     const BatchGeom* geo = reinterpret_cast<const BatchGeom*>(tab + c.L.o_geom);
     const BatchJob* jobs = reinterpret_cast<const BatchJob*>(tab + c.L.o_jobs);
@@ -480,7 +480,8 @@ cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
         a.jobs = jobs + p.seg_off[g];
         a.njobs = p.seg_cnt[g];
         a.head = ctl + g;
-        a.done = ctl + 4;
+        a.abort = ctl + 4;
+        a.done = ctl + 8;
         a.timeout_ns = kTimeoutNs;
         const int dd = p.dlist[g];
         int grid = c.grid_per_sm[dd] * sm_count();
@@ -490,7 +491,7 @@ cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
     }
     if (c.ev1 && (e = cudaEventRecord(c.ev1, s)) != cudaSuccess) return e;
     if ((e = launch_batch_unpack<double>(geo, jobs, njobs, c.X, s)) != cudaSuccess) return e;
-    return cudaMemcpyAsync(c.herr, ctl + 4 + p.count, sizeof(int) * p.count, cudaMemcpyDeviceToHost, s);
+    return cudaMemcpyAsync(c.herr, ctl + 8 + p.count, sizeof(int) * p.count, cudaMemcpyDeviceToHost, s);
 }
 
 // Same precedence as a single solve.

@@ -50,6 +50,7 @@ struct BatchArgs {
     int njobs;
     int* head;                 // next job (zeroed before the launch)
     int* done;                 // finished blocks per equation (zeroed before the launch)
+    int* abort;                // set when any wait ran out of time: later waits give up at once
     long long timeout_ns;
 };
 

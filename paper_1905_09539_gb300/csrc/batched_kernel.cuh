@@ -21,11 +21,16 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 // visible) before later bulk copies, in every state space.
 __device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
-__device__ __forceinline__ bool wait_count(const int* p, int need, long long timeout_ns) {
+// Wait (bounded) until *p >= need.  A timeout raises *abort, which makes
+// every later wait of the launch give up at once.
+__device__ __forceinline__ bool wait_count(const int* p, int need, int* abort, long long timeout_ns) {
     if (ld_acquire(p) >= need) return true;
     const unsigned long long t0 = global_ns();
     while (ld_acquire(p) < need) {
-        if (static_cast<long long>(global_ns() - t0) > timeout_ns) return false;
+        if (ld_acquire(abort) || static_cast<long long>(global_ns() - t0) > timeout_ns) {
+            atomicExch(abort, 1);
+            return false;
+        }
         __nanosleep(128);
     }
     return true;
@@ -55,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) k_batched(const BatchArgs b) {
         const BatchJob jb = b.jobs[j];
         if (threadIdx.x == 0) {
             int ok = 1;
-            if (jb.need > 0 && !dev::wait_count(&b.done[jb.eq], jb.need, b.timeout_ns)) ok = 0;
+            if (jb.need > 0 && !dev::wait_count(&b.done[jb.eq], jb.need, b.abort, b.timeout_ns)) ok = 0;
             if (!ok) atomicOr(b.eqs[jb.eq].err, kErrTimeout);
             dev::fence_proxy_async_all();
             s_ok = ok;

@@ -55,7 +55,7 @@ __global__ void k_batch_pack(const BatchGeom* __restrict__ geo, const BatchJob* 
             const long long gi0 = g.start[mu][cj.I], gj0 = g.start[mu][cj.J];
             const long long tri = static_cast<long long>(cj.J) * (cj.J + 1) / 2 + cj.I;
             T* ta = static_cast<T*>(g.At[mu]) + tri * tc;
-            T* tcp = C ? static_cast<T*>(g.Ct[mu]) + tri * tc : nullptr;
+            T* tcp = (C && g.Ct[mu]) ? static_cast<T*>(g.Ct[mu]) + tri * tc : nullptr;
             const double* Am = A + g.aoff[mu];
             const double* Cm = C ? C + g.aoff[mu] : nullptr;
             for (int e = threadIdx.x; e < tc; e += blockDim.x) {
@@ -64,7 +64,7 @@ __global__ void k_batch_pack(const BatchGeom* __restrict__ geo, const BatchJob* 
                 if (i < si && j < sj) {
                     const long long gi = gi0 + i, gj = gj0 + j;
                     if (gi <= gj + 1) va = static_cast<T>(Am[gi + n * gj]);
-                    if (Cm && gi <= gj) vc = static_cast<T>(Cm[gi + n * gj]);
+                    if (tcp && gi <= gj) vc = static_cast<T>(Cm[gi + n * gj]);
                 }
                 ta[e] = va;
                 if (tcp) tcp[e] = vc;

@@ -111,6 +111,18 @@ def test_transposed_solve_matches_dense(shape, gen):
     assert np.linalg.norm(L - Ld) / np.linalg.norm(Ld) <= 1e-13
 
 
+@pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_transposed_recursion_matches_dense(shape, gen):
+    """O-B on A^T (reversed recursion order) against LAPACK on the assembled M^T."""
+    p = _prob(shape, gen, seed=6, force=[[n // 2 - 1] if n >= 4 else [] for n in shape])
+    M = operator(p["A"], p["C"])
+    Ld = unvec(np.linalg.solve(M.T, vec(p["B"])), shape)
+    for nm in (2, 3, 5):
+        L = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=nm, transpose=True)
+        assert np.linalg.norm(L - Ld) / np.linalg.norm(Ld) <= 1e-13
+
+
 def test_d1_triangular():
     rng = np.random.default_rng(7)
     A = np.triu(rng.standard_normal((12, 12))) + 3 * np.eye(12)
