@@ -101,6 +101,10 @@ typedef struct tsylv_opts {
     int host_io;      /* 1: B, X, A, C (and backward buffers) are host pointers; the
                          call copies them through `work` inside the call             */
     int timing;       /* 1: time the phases with CUDA events (fields t_* of info)    */
+    int schedule;     /* block schedule of a solve: 0 (default) one persistent
+                         dataflow launch (a block starts as soon as each source
+                         block it reads is solved); 1 one launch per anti-diagonal
+                         wavefront (split over a cluster when the wavefront is short) */
 } tsylv_opts;
 
 typedef struct tsylv_info {

@@ -39,6 +39,7 @@ extern "C" void tsylv_opts_default(tsylv_opts* o) {
     o->use_graph = 1;
     o->host_io = 0;
     o->timing = 0;
+    o->schedule = 0;
 }
 
 extern "C" const char* tsylv_status_string(int s) {

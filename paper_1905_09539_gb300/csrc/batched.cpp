@@ -38,6 +38,7 @@ struct EqPlan {
     // workspace offsets (bytes, from the data region)
     size_t X = 0, P[kMaxD] = {}, G[kMaxD] = {}, At[kMaxD] = {}, Ct[kMaxD] = {};
     size_t part_off[kMaxD] = {};  // ints in the table: start (nb), then size (nb)
+    size_t flag_off = 0;          // first "solved" flag of this equation's blocks
 };
 
 struct BatchGraph {
@@ -66,6 +67,7 @@ struct BatchPlan {
 // Regions of the batched workspace (byte offsets from its base).
 struct BatchLayout {
     size_t ctl = 0;    // heads [4], abort, pad [3], done [count], errs [count]
+    size_t flags = 0;  // per-block "solved" flags of every equation
     size_t sub = 0;    // sub-diagonals of every A_mu, then the gather tables
     size_t tab = 0;    // WaveArgs [count], BatchGeom [count], jobs, coefficient jobs, partition ints
     size_t data = 0;   // block tensors and coefficient tiles
@@ -74,28 +76,25 @@ struct BatchLayout {
     size_t o_aoff = 0, o_nmat = 0, o_ooff = 0, nsub = 0;
 };
 
-// Upper bounds of one equation's block counts (any admissible structure).
-void eq_bounds(int d, const int64_t* n, long long& tiles, long long& ctiles, long long& pints) {
+// Upper bounds of one equation's block counts and data bytes (any admissible
+// structure), region by region as get_batch_plan lays them out.
+void eq_bounds(int d, const int64_t* n, bool gen, int elem, long long& tiles, long long& ctiles, long long& pints,
+               size_t& data) {
     const int te = tile_extent(d);
+    const size_t td = static_cast<size_t>(ipow(te, d)), tc = static_cast<size_t>(te) * te;
+    const bool g = gen && d >= 2;
     tiles = 1;
     ctiles = 0;
     pints = 0;
+    data = 0;
     for (int mu = 0; mu < d; mu++) {
         const long long nb = max_blocks(static_cast<int>(n[mu]), te);
         tiles *= nb;
         ctiles += nb * (nb + 1) / 2;
         pints += 2 * nb;
+        data += (g ? 2 : 1) * al256(static_cast<size_t>(nb * (nb + 1) / 2) * tc * elem);
     }
-}
-
-size_t eq_data_bytes(int d, long long tiles, long long ctiles, bool gen, int elem) {
-    const int te = tile_extent(d);
-    const size_t td = static_cast<size_t>(ipow(te, d)), tc = static_cast<size_t>(te) * te;
-    const bool g = gen && d >= 2;
-    size_t b = al256(tiles * td * elem);
-    if (g) b += 2 * (d - 1) * al256(tiles * td * elem);
-    b += (g ? 2 : 1) * al256(ctiles * tc * elem);
-    return b;
+    data += (g ? 1 + 2 * (d - 1) : 1) * al256(static_cast<size_t>(tiles) * td * elem);
 }
 
 BatchLayout make_batch_layout(int count, const int* d, const int64_t* n_packed, bool gen, int elem,
@@ -104,6 +103,8 @@ BatchLayout make_batch_layout(int count, const int* d, const int64_t* n_packed, 
     size_t off = 0;
     L.ctl = off;
     off += al256((8 + 2 * static_cast<size_t>(count)) * sizeof(int));
+    L.flags = off;
+    off += al256(static_cast<size_t>(njobs) * sizeof(int));
     size_t nsub = 0, nmats = 0, k = 0;
     for (int e = 0; e < count; e++)
         for (int mu = 0; mu < d[e]; mu++, k++) {
@@ -151,11 +152,12 @@ Bounds batch_bounds(int count, const int* d, const int64_t* n_packed, bool gen, 
     size_t k = 0;
     for (int e = 0; e < count; e++) {
         long long t, c, p;
-        eq_bounds(d[e], n_packed + k, t, c, p);
+        size_t db;
+        eq_bounds(d[e], n_packed + k, gen, elem, t, c, p, db);
         b.jobs += t;
         b.cjobs += c;
         b.pints += p;
-        b.data += eq_data_bytes(d[e], t, c, gen, elem);
+        b.data += db;
         k += static_cast<size_t>(d[e]);
     }
     return b;
@@ -220,7 +222,8 @@ void order_jobs(const BatchPlan& p, const std::vector<int>& eqs, int policy, std
             return a.wave < b.wave;
         });
     }
-    for (const Item& it : items) out.push_back({it.eq, it.tile, it.need, 0});
+    // every job waits per source block on its "solved" flag, so no count is needed
+    for (const Item& it : items) out.push_back({it.eq, it.tile, 0, 0});
 }
 
 double eq_flops(const EqPlan& q, bool gen) {
@@ -268,7 +271,7 @@ std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t
     p->gen = gen;
     p->eq.resize(count);
     k = 0;
-    size_t soff = 0, data = 0, pints = 0;
+    size_t soff = 0, data = 0, pints = 0, flags = 0;
     for (int e = 0; e < count; e++) {
         EqPlan& q = p->eq[e];
         q.d = d[e];
@@ -290,6 +293,8 @@ std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t
         }
         q.ntiles = ts;
         q.nwaves = nw;
+        q.flag_off = flags;
+        flags += static_cast<size_t>(ts);
         const size_t td = static_cast<size_t>(ipow(te, q.d)), tc = static_cast<size_t>(te) * te;
         const bool g = gen && q.d >= 2;
         q.X = data;
@@ -378,6 +383,8 @@ void fill_table(const BatchPlan& p, const BatchLayout& L, char* base, int policy
         wa.X = dev_data + q.X;
         wa.err = errs + e;
         wa.timeout_ns = kTimeoutNs;
+        wa.ready = reinterpret_cast<const int*>(base + L.flags) + q.flag_off;
+        wa.abort = reinterpret_cast<int*>(base + L.ctl) + 4;
         ge.X = dev_data + q.X;
         hw[e] = wa;
         hg[e] = ge;
@@ -465,6 +472,7 @@ cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
     char* tab = c.base + c.L.tab;
     cudaError_t e;
     if ((e = cudaMemsetAsync(ctl, 0, (8 + 2 * static_cast<size_t>(p.count)) * sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c.base + c.L.flags, 0, p.jobs[0].size() * sizeof(int), s)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(tab, c.htab, c.L.tab_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
     const BatchGeom* geo = reinterpret_cast<const BatchGeom*>(tab + c.L.o_geom);
     const BatchJob* jobs = reinterpret_cast<const BatchJob*>(tab + c.L.o_jobs);
@@ -698,10 +706,12 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
             if (g.key == key) exec = g.exec;
         if (!exec) {
             cudaGraph_t graph = nullptr;
-            if ((e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            cudaStream_t cs = capture_stream();
+            if (!cs) return cuda_fail_msg("batched: capture stream");
+            if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                 return cuda_fail(e, "batched: begin capture");
-            const cudaError_t ee = enqueue_batch(c, stream);
-            e = cudaStreamEndCapture(stream, &graph);
+            const cudaError_t ee = enqueue_batch(c, cs);
+            e = cudaStreamEndCapture(cs, &graph);
             if (ee != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
                 return cuda_fail(ee, "batched: capture");

@@ -3,11 +3,13 @@
 //
 // Every equation keeps the block grid of a single solve (block tensor,
 // coefficient tiles, partition tables).  One persistent launch works through
-// a job queue holding every block of every equation; a block of wavefront w
-// of equation e may start once equation e has finished all blocks of its
-// wavefronts before w.  Jobs are queued so that every job's prerequisites
-// sit earlier in the queue; a CTA that waits therefore only waits on jobs that
-// running CTAs already hold, and the launch needs no co-residency guarantee.
+// a job queue holding every block of every equation; before a block reads a
+// source block for its update it waits until that block's "solved" flag is
+// set (optionally, a job may also wait for a count of finished blocks of its
+// equation).  Jobs are queued so that every block's sources sit earlier in the
+// queue; a CTA that waits therefore only waits on jobs that running CTAs
+// already hold, and the launch needs no co-residency guarantee.  The single
+// solve uses the same kernel with a queue of one equation's blocks.
 #pragma once
 
 #include "tsylv_internal.h"
@@ -46,10 +48,12 @@ struct BatchCoefJob {
 
 struct BatchArgs {
     const WaveArgs* eqs;       // one wavefront parameter block per equation (tiles unused)
-    const BatchJob* jobs;
+    const BatchJob* jobs;      // nullptr: job j is block tiles[j] of equation 0, no count to wait for
+    const int* tiles;
     int njobs;
     int* head;                 // next job (zeroed before the launch)
-    int* done;                 // finished blocks per equation (zeroed before the launch)
+    int* done;                 // finished blocks per equation (zeroed before the launch; may be
+                               // nullptr when jobs is)
     int* abort;                // set when any wait ran out of time: later waits give up at once
     long long timeout_ns;
 };
@@ -59,6 +63,8 @@ template <typename T>
 cudaError_t launch_batched(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s);
 template <typename T>
 cudaError_t prepare_batched();
+// *dst = a, by one thread (a captured launch keeps `a` by value).
+cudaError_t launch_store_args(const WaveArgs& a, WaveArgs* dst, cudaStream_t s);
 // Resident CTAs per SM of the persistent kernel.
 template <typename T>
 int batched_occupancy(int d, bool gen);

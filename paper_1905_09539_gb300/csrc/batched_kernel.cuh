@@ -9,35 +9,6 @@
 
 namespace tsylv {
 
-namespace dev {
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Order earlier generic-proxy accesses (including what an acquire made
-// visible) before later bulk copies, in every state space.
-__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
-
-// Wait (bounded) until *p >= need.  A timeout raises *abort, which makes
-// every later wait of the launch give up at once.
-__device__ __forceinline__ bool wait_count(const int* p, int need, int* abort, long long timeout_ns) {
-    if (ld_acquire(p) >= need) return true;
-    const unsigned long long t0 = global_ns();
-    while (ld_acquire(p) < need) {
-        if (ld_acquire(abort) || static_cast<long long>(global_ns() - t0) > timeout_ns) {
-            atomicExch(abort, 1);
-            return false;
-        }
-        __nanosleep(128);
-    }
-    return true;
-}
-
-}  // namespace dev
-
 template <typename T, int D, bool GENF>
 __global__ void __launch_bounds__(kThreads) k_batched(const BatchArgs b) {
     using C = WaveCfg<T, D, GENF>;
@@ -57,23 +28,31 @@ __global__ void __launch_bounds__(kThreads) k_batched(const BatchArgs b) {
         __syncthreads();
         const int j = s_job;
         if (j >= b.njobs) break;
-        const BatchJob jb = b.jobs[j];
+        BatchJob jb;
+        if (b.jobs) {
+            jb = b.jobs[j];
+        } else {
+            jb.eq = 0;
+            jb.tile = b.tiles[j];
+            jb.need = 0;
+        }
+        const WaveArgs& a = b.eqs[jb.eq];
         if (threadIdx.x == 0) {
             int ok = 1;
-            if (jb.need > 0 && !dev::wait_count(&b.done[jb.eq], jb.need, b.abort, b.timeout_ns)) ok = 0;
-            if (!ok) atomicOr(b.eqs[jb.eq].err, kErrTimeout);
+            if (jb.need > 0 && !dev::wait_at_least(&b.done[jb.eq], jb.need, b.abort, b.timeout_ns)) ok = 0;
+            if (!ok) atomicOr(a.err, kErrTimeout);
             dev::fence_proxy_async_all();
             s_ok = ok;
         }
         __syncthreads();
-        if (alive && s_ok) {
-            const WaveArgs& a = b.eqs[jb.eq];
-            alive = wave_tile<T, D, GENF>(a, jb.tile, 0, 1, uses);
-        }
-        // publish the block: every thread's stores, then the count (release)
+        if (alive && s_ok) alive = wave_tile<T, D, GENF>(a, jb.tile, 0, 1, uses);
+        // publish the block: every thread's stores, then the count / flag (release)
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(&b.done[jb.eq], 1);
+        if (threadIdx.x == 0) {
+            if (b.done) atomicAdd(&b.done[jb.eq], 1);
+            if (a.ready) dev::st_release(const_cast<int*>(a.ready) + jb.tile, 1);
+        }
     }
 }
 

@@ -115,6 +115,10 @@ __global__ void k_batch_subdiag(const long long* __restrict__ aoff, const long l
     }
 }
 
+__global__ void k_store_args(const WaveArgs a, WaveArgs* dst) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = a;
+}
+
 inline int blocks_for(long long n) {
     long long b = n < 1 ? 1 : n;
     if (b > 152LL * 16) b = 152LL * 16;
@@ -142,6 +146,11 @@ cudaError_t launch_batch_subdiag(const long long* aoff, const long long* nmat, c
     const unsigned gx = static_cast<unsigned>((maxn + 127) / 128 > 0 ? (maxn + 127) / 128 : 1);
     const unsigned gy = static_cast<unsigned>(nmats < 65535 ? (nmats > 0 ? nmats : 1) : 65535);
     k_batch_subdiag<<<dim3(gx, gy), 128, 0, s>>>(aoff, nmat, ooff, nmats, A, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_args(const WaveArgs& a, WaveArgs* dst, cudaStream_t s) {
+    k_store_args<<<1, 32, 0, s>>>(a, dst);
     return cudaGetLastError();
 }
 
@@ -190,6 +199,9 @@ cudaError_t prepare_batched() {
 template cudaError_t launch_batched<double>(int, bool, const BatchArgs&, int, cudaStream_t);
 template int batched_occupancy<double>(int, bool);
 template cudaError_t prepare_batched<double>();
+template cudaError_t launch_batched<float>(int, bool, const BatchArgs&, int, cudaStream_t);
+template int batched_occupancy<float>(int, bool);
+template cudaError_t prepare_batched<float>();
 template cudaError_t launch_batch_pack<double>(const BatchGeom*, const BatchJob*, int, const BatchCoefJob*, int,
                                                const double*, const double*, const double*, cudaStream_t);
 template cudaError_t launch_batch_unpack<double>(const BatchGeom*, const BatchJob*, int, double*, cudaStream_t);

@@ -95,6 +95,37 @@ __device__ __forceinline__ float ld_dsmem(const float* local, uint32_t rank) {
     return v;
 }
 
+// ---- inter-CTA signalling through global memory (persistent kernels)
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Order earlier generic-proxy accesses (including what an acquire made
+// visible) before later bulk copies, in every state space.
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// Wait (bounded) until *p >= need.  A timeout raises *abort, which makes
+// every later wait of the launch give up at once.  Returns false on either.
+__device__ __forceinline__ bool wait_at_least(const int* p, int need, int* abort, long long timeout_ns) {
+    if (ld_acquire(p) >= need) return true;
+    const unsigned long long t0 = global_ns();
+    while (ld_acquire(p) < need) {
+        if (ld_acquire(abort) || static_cast<long long>(global_ns() - t0) > timeout_ns) {
+            atomicExch(abort, 1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
 template <typename T>
 __device__ __forceinline__ T fmadd(T a, T b, T c);
 template <>

@@ -96,6 +96,12 @@ Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem,
             o = align256(o + ntri * tc * elem);
         }
     }
+    L.fargs = o;
+    o = align256(o + sizeof(WaveArgs));
+    L.fctl = o;
+    o = align256(o + 64);
+    L.flags = o;
+    o = align256(o + ntiles * sizeof(int));
     L.total = o;
     return L;
 }

@@ -60,6 +60,7 @@ struct Plan {
 // Workspace regions, as byte offsets from the (256-byte aligned) base.
 struct Layout {
     size_t err = 0, sub = 0, tab = 0;
+    size_t fargs = 0, fctl = 0, flags = 0;  // persistent schedule: parameter block, queue head + abort, solved flags
     size_t X = 0, P[kMaxD] = {}, G[kMaxD] = {}, At[kMaxD] = {}, Ct[kMaxD] = {};
     size_t total = 0;
 };

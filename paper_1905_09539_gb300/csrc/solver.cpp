@@ -6,9 +6,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
+#include "batched.h"
 #include "plan.h"
 #include "refine.h"
 
@@ -18,6 +20,10 @@ namespace {
 
 constexpr long long kTimeoutNs = 2000000000LL;  // bound of every device-side wait
 
+}  // namespace
+
+// Private non-blocking stream on which CUDA graphs are captured (capture on
+// the caller's stream is not possible when it is the legacy default stream).
 cudaStream_t capture_stream() {
     static std::mutex m;
     static cudaStream_t s[64] = {};
@@ -28,6 +34,8 @@ cudaStream_t capture_stream() {
     if (!s[dev]) cudaStreamCreateWithFlags(&s[dev], cudaStreamNonBlocking);
     return s[dev];
 }
+
+namespace {
 
 // Upper bound of the block-table size for any admissible structure.
 size_t tab_ints_bound(int d, const long long* n, const int* nb) {
@@ -129,6 +137,8 @@ struct Call {
     Layout L;
     RefLayout R;
     bool timing = false;
+    bool persistent = true;   // opts->schedule == 0
+    int flow_grid = 0;        // CTAs of the persistent launch
 };
 
 inline cudaError_t mark(const Call& c, int i, cudaStream_t s) {
@@ -161,10 +171,36 @@ WaveArgs wave_args(const Plan& p, const Layout& L, char* base) {
     return wa;
 }
 
+// The block schedule of one solve: one persistent dataflow launch (every
+// block taken from a queue in wavefront order; a block's update waits, per
+// source block, until that block is solved), or one launch per wavefront.
 template <typename T>
-cudaError_t enqueue_waves(const Plan& p, const Layout& L, char* base, cudaStream_t s) {
+cudaError_t enqueue_waves(const Call& c, const Layout& L, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    char* base = c.base;
     WaveArgs wa = wave_args(p, L, base);
     const int* tab = reinterpret_cast<const int*>(base + L.tab);
+    if (c.persistent) {
+        int* ctl = reinterpret_cast<int*>(base + L.fctl);
+        int* flags = reinterpret_cast<int*>(base + L.flags);
+        TRY(cudaMemsetAsync(ctl, 0, 64, s));
+        TRY(cudaMemsetAsync(flags, 0, static_cast<size_t>(p.ntiles) * sizeof(int), s));
+        wa.ready = flags;
+        wa.abort = ctl + 1;
+        wa.csize = 1;
+        WaveArgs* dargs = reinterpret_cast<WaveArgs*>(base + L.fargs);
+        TRY(launch_store_args(wa, dargs, s));
+        BatchArgs ba{};
+        ba.eqs = dargs;
+        ba.jobs = nullptr;
+        ba.tiles = tab + p.t_wave;
+        ba.njobs = static_cast<int>(p.ntiles);
+        ba.head = ctl;
+        ba.done = nullptr;
+        ba.abort = ctl + 1;
+        ba.timeout_ns = kTimeoutNs;
+        return launch_batched<T>(p.d, p.gen, ba, c.flow_grid, s);
+    }
     for (size_t w = 0; w < p.wave_off.size(); w++) {
         wa.tiles = tab + p.t_wave + p.wave_off[w];
         wa.ntiles = p.wave_cnt[w];
@@ -191,7 +227,7 @@ cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
     double* Xt = reinterpret_cast<double*>(base + L.X);
     TRY(launch_pack_tensor<double>(g, c.B, Xt, 1.0, s));
     TRY(mark(c, 1, s));
-    TRY(enqueue_waves<double>(p, L, base, s));
+    TRY(enqueue_waves<double>(c, L, s));
     TRY(mark(c, 2, s));
     TRY(launch_unpack_tensor<double>(g, Xt, c.X, s));
     return mark(c, 3, s);
@@ -338,7 +374,7 @@ cudaError_t enqueue_ref_iter(const Call& c, cudaStream_t s) {
     TRY(mark(c, 0, s));
     // low-precision solve of A(D) = R / max|R|
     TRY(launch_scale_to_f32(reinterpret_cast<double*>(b + R.Rt), reinterpret_cast<float*>(b + L.X), nrm, nel, s));
-    TRY(enqueue_waves<float>(p, L, b, s));
+    TRY(enqueue_waves<float>(c, L, s));
     // X += max|R| D  (FP64), its float-pair split, block sums of X^2
     TRY(launch_update_x(reinterpret_cast<double*>(b + R.Xt), reinterpret_cast<float*>(b + L.X), nrm,
                         c.df ? reinterpret_cast<float*>(b + R.Xh) : nullptr,
@@ -428,6 +464,30 @@ int run_enqueue(Plan& p, const std::vector<const void*>& key, bool use_graph, cu
     return 0;
 }
 
+// CTAs of a persistent launch: every resident slot of the GPU, at most one per block.
+int flow_grid(int elem, int d, bool gen, long long ntiles) {
+    static std::mutex m;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int key = ((dev * 2 + (elem == 4 ? 1 : 0)) * 8 + d) * 2 + (gen ? 1 : 0);
+    int slots = 0;
+    {
+        std::lock_guard<std::mutex> lk(m);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            slots = it->second;
+        } else {
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+            const int occ = elem == 4 ? batched_occupancy<float>(d, gen) : batched_occupancy<double>(d, gen);
+            slots = sms * occ;
+            cache[key] = slots;
+        }
+    }
+    return static_cast<int>(ntiles < slots ? ntiles : slots);
+}
+
 int prepare_kernels() {
     static std::mutex pm;
     static bool prepared[64] = {};
@@ -439,6 +499,8 @@ int prepare_kernels() {
         if (e == cudaSuccess) e = prepare_wave<float>();
         if (e == cudaSuccess) e = prepare_apply<false>();
         if (e == cudaSuccess) e = prepare_apply<true>();
+        if (e == cudaSuccess) e = prepare_batched<double>();
+        if (e == cudaSuccess) e = prepare_batched<float>();
         if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
         prepared[dev] = true;
     }
@@ -570,7 +632,8 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -(6 + sh);
     if (work_bytes < solver_workspace_bytes(d, n, gen, o, transposed)) return -(7 + sh);
     if (o.precision < TSYLV_FP64 || o.precision > TSYLV_BF16_REFINED || o.max_refine < 0 || !(o.tol > 0) ||
-        (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < 0)
+        (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < 0 ||
+        o.schedule < 0 || o.schedule > 1)
         return -(8 + sh);
     if (o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d))) return TSYLV_EUNSUPPORTED;
     if (o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) return TSYLV_EUNSUPPORTED;
@@ -598,7 +661,9 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (int st = prepare_kernels()) return st;
     c.timing = o.timing != 0;
     if (int st = ensure_events(c)) return st;
-    const int tagbase = (transposed ? 1 : 0) | (c.timing ? 2 : 0) | (c.df ? 4 : 0);
+    c.persistent = o.schedule == 0;
+    if (c.persistent) c.flow_grid = flow_grid(refined ? 4 : 8, d, c.gen, c.plan->ntiles);
+    const int tagbase = (transposed ? 1 : 0) | (c.timing ? 2 : 0) | (c.df ? 4 : 0) | (c.persistent ? 256 : 0);
 
     if (!refined) {
         c.L = make_layout(d, c.n, c.plan->nb, c.gen, 8, c.plan->tab.size());
@@ -614,7 +679,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
         if (info) {
             std::memset(info, 0, sizeof(*info));
             info->waves = static_cast<int>(c.plan->wave_off.size());
-            info->launches = info->waves + d * (c.gen ? 2 : 1) + 2;
+            info->launches = (c.persistent ? 2 : info->waves) + d * (c.gen ? 2 : 1) + 2;
             info->tiles = static_cast<int>(c.plan->ntiles);
             info->resid = -1;
             info->norm_A = -1;
@@ -700,7 +765,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
         std::memset(info, 0, sizeof(*info));
         info->iterations = iters;
         info->waves = static_cast<int>(c.plan->wave_off.size());
-        info->launches = iters * (info->waves + (c.gen ? d : 1) + 4) + 4 * d + 8;
+        info->launches = iters * ((c.persistent ? 2 : info->waves) + (c.gen ? d : 1) + 4) + 4 * d + 8;
         info->tiles = static_cast<int>(c.plan->ntiles);
         info->resid = rho;
         info->norm_A = nA;

@@ -22,6 +22,8 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
                    const double* A_pool, const double* C_pool, const double* B_pool, double* X_pool, void* work,
                    size_t work_bytes, const tsylv_opts* opts, int* per_status, tsylv_info* info, cudaStream_t stream);
 
+cudaStream_t capture_stream();
+
 int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const double* B, double* X,
                          const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
 

@@ -50,6 +50,11 @@ struct WaveArgs {
     const void* Ct[kMaxD];      // same for C_mu (generalized form)
     int* err;                   // status word
     long long timeout_ns;       // bound of every device-side wait
+    // persistent launches: per-block "solved" flags (nullptr: every source
+    // block is already solved, as in a wavefront launch) and the launch-wide
+    // abort word raised by a timed-out wait
+    const int* ready;
+    int* abort;
 };
 
 // Launch one wavefront.  T = double or float; generalized selects the d-term form.

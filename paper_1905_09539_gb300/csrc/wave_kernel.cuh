@@ -629,30 +629,44 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
 #pragma unroll
     for (int mu = 0; mu < D; mu++) I[mu] = static_cast<int>((t / a.tstride[mu]) % a.nb[mu]);
 
-    // ---- job list: level L covers mode L (Laplace) or d-1-L (generalized)
-    int cnt[D], w[D];
+    // ---- job list: level L covers mode L (Laplace) or d-1-L (generalized).
+    // Jobs run in decreasing distance dd = J' - I_mu of the source block
+    // (levels in order within one distance): in a persistent launch the
+    // nearest source blocks are the last ones to be solved.
+    int cnt[D], w[D], maxc = 0;
     long long W = 0;
 #pragma unroll
     for (int L = 0; L < D; L++) {
         const int mu = GEN ? D - 1 - L : L;
         cnt[L] = a.hi[mu] - 1 - I[mu];
         if (cnt[L] < 0) cnt[L] = 0;
+        if (cnt[L] > maxc) maxc = cnt[L];
         w[L] = GEN ? ((L == 0 || L == D - 1) ? 2 : 3) : 1;
         W += static_cast<long long>(cnt[L]) * w[L];
     }
-    const long long wlo = W * rank / csize, whi = W * (rank + 1) / csize;
-    int j0 = 0, j1 = 0, jt = 0;
-    {
+    // number of jobs whose distance is at least dd
+    auto at_least = [&](int dd) {
+        int n = 0;
+#pragma unroll
+        for (int L = 0; L < D; L++) n += cnt[L] >= dd ? cnt[L] - dd + 1 : 0;
+        return n;
+    };
+    const int jt = at_least(1);
+    int j0 = 0, j1 = jt;
+    if (csize > 1) {
+        // split the jobs over the cluster by weight, in job order
+        const long long wlo = W * rank / csize, whi = W * (rank + 1) / csize;
         long long cw = 0;
+        int j = 0;
         bool f0 = false, f1 = false;
-        for (int L = 0; L < D; L++) {
-            for (int k = 0; k < cnt[L]; k++) {
-                if (!f0 && cw >= wlo) { j0 = jt; f0 = true; }
-                if (!f1 && cw >= whi) { j1 = jt; f1 = true; }
+        for (int dd = maxc; dd >= 1; dd--)
+            for (int L = 0; L < D; L++) {
+                if (cnt[L] < dd) continue;
+                if (!f0 && cw >= wlo) { j0 = j; f0 = true; }
+                if (!f1 && cw >= whi) { j1 = j; f1 = true; }
                 cw += w[L];
-                jt++;
+                j++;
             }
-        }
         if (!f0) j0 = jt;
         if (!f1) j1 = jt;
     }
@@ -660,10 +674,20 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
 
     // job j -> (level, source block J')
     auto decode = [&](int j, int& L, int& Jp) {
+        int lo = 1, hi = maxc;  // largest dd with at_least(dd) > j
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (at_least(mid) > j) lo = mid; else hi = mid - 1;
+        }
+        int r = j - at_least(lo + 1);
         L = 0;
-        while (L < D - 1 && j >= cnt[L]) { j -= cnt[L]; L++; }
+        for (int q = 0; q < D; q++) {
+            if (cnt[q] < lo) continue;
+            if (r == 0) { L = q; break; }
+            r--;
+        }
         const int mu = GEN ? D - 1 - L : L;
-        Jp = I[mu] + 1 + j;
+        Jp = I[mu] + lo;
     };
     auto issue = [&](int j, int stg) {
         int L, Jp;
@@ -688,6 +712,11 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             }
             M1 = static_cast<const T*>(a.Ct[mu]) + tri * TC;
             M2 = static_cast<const T*>(a.At[mu]) + tri * TC;
+        }
+        if (a.ready) {
+            // persistent launch: the source block must be solved (bounded wait)
+            if (!dev::wait_at_least(a.ready + ts, 1, a.abort, a.timeout_ns)) atomicOr(a.err, kErrTimeout);
+            dev::fence_proxy_async_all();
         }
         const uint32_t bytes = static_cast<uint32_t>(((S2 ? 2 : 1) * TD + (M2 ? 2 : 1) * TC) * sizeof(T));
         dev::mbar_expect_tx(&bar[stg], bytes);

@@ -7,6 +7,7 @@ with the oracle to that relative error.
 """
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import synthetic
@@ -137,11 +138,40 @@ def test_repeat_calls_replay_graph(lib):
 
 @pytest.mark.parametrize("split", [1, 2, 8])
 def test_cluster_split_sizes_agree(lib, split):
+    """Wavefront schedule: short wavefronts split over clusters of 1, 2, 8 CTAs."""
     p = synthetic.problem(6, (40, 33, 24), generalized=True)
     Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=8)
-    X, st = lib.gtsylv_solve([to_dev(a) for a in p["A"]], [to_dev(c) for c in p["C"]], to_dev(p["B"]), split=split)
+    X, st = lib.gtsylv_solve([to_dev(a) for a in p["A"]], [to_dev(c) for c in p["C"]], to_dev(p["B"]), split=split,
+                             schedule=1)
     assert st == 0
     assert rel_err(to_host(X), Xo) <= TOL
+
+
+@pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("d,shape", [(1, (100,)), (2, (33, 17)), (3, (24, 17, 13)), (3, (33, 30, 31)),
+                                     (4, (13, 11, 10, 9))])
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_schedules_agree_with_oracle(lib, d, shape, gen, precision):
+    """The persistent dataflow schedule (default) and the wavefront schedule
+    (automatic cluster split, and no split) all match the oracle; without a
+    cluster split the wavefront schedule sums every block update in the same
+    order as the persistent one, so those two agree to the last bit."""
+    p = synthetic.problem(2, shape, generalized=gen, force_blocks=_split_force(shape, _te(d)))
+    Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+    prec = lib.TSYLV_FP64 if precision == "fp64" else lib.TSYLV_FP32_REFINED
+    A = [to_dev(a) for a in p["A"]]
+    B = to_dev(p["B"])
+    out = []
+    for sched, split in ((0, 0), (1, 1), (1, 0)):
+        if gen:
+            X, st = lib.gtsylv_solve(A, [to_dev(c) for c in p["C"]], B, schedule=sched, split=split, precision=prec)
+        else:
+            X, st = lib.tsylv_solve(A, B, schedule=sched, split=split, precision=prec)
+        assert st == 0
+        assert rel_err(to_host(X), Xo) <= TOL
+        out.append(X)
+    if precision == "fp64":
+        assert torch.equal(out[0], out[1])
 
 
 def test_singular_reported(lib):
