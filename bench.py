@@ -391,6 +391,24 @@ def run_ours(args, ws, rank, local):
     def launches_of_step():
         return sum(i.launches for i in infos.values())
 
+    if args.only:
+        table = {name: (lambda name=name, gen=gen, prec=prec: solve(name, gen, prec)) for name, gen, prec in SOLVE_PARTS}
+        table.update({"adjoint_fp64": lambda: adjoint(0), "adjoint_fp32r": lambda: adjoint(1), "batched_fp64": batched})
+        fn = table[args.only]
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "ms": e0.elapsed_time(e1) / max(1, args.steps)}), flush=True)
+        return
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -593,6 +611,9 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--fp64-peak", action="store_true", help="build and run the FP64 throughput probe")
+    ap.add_argument("--only", default=None,
+                    help="profiling aid: run just this part of the step (e.g. fp64_generalized) for the warm-up "
+                         "and timed steps, print its time and exit")
     args = ap.parse_args()
     if args.fp64_peak:
         run_fp64_peak()

@@ -100,10 +100,16 @@ def _fd_check(lib, shape, gen, seed, recompute=False, h=1e-6, ndir=20):
     gA = [to_host(a.grad) for a in A]
     gC = [to_host(c.grad) for c in C] if gen else None
 
-    def L(Ah, Bh, Ch):
+    def X_of(Ah, Bh, Ch):
         with torch.no_grad():
-            Xh = lib.solve([to_dev(a) for a in Ah], to_dev(Bh), [to_dev(c) for c in Ch] if Ch is not None else None)
-            return 0.5 * float(torch.sum((Xh - Xs) ** 2))
+            return lib.solve([to_dev(a) for a in Ah], to_dev(Bh), [to_dev(c) for c in Ch] if Ch is not None else None)
+
+    def central(pl, mi):
+        # (L(X+) - L(X-)) / 2h with L = 0.5 ||X - X*||^2, the difference of the
+        # two losses written as 0.5 sum (X+ - X-)(X+ + X- - 2 X*): the same
+        # central difference, without cancelling two large sums
+        Xp, Xm = X_of(*pl), X_of(*mi)
+        return 0.5 * float(torch.sum((Xp - Xm) * (Xp + Xm - 2 * Xs))) / (2 * h)
 
     rng = np.random.default_rng(seed + 1000)
     Ah, Bh, Ch = p["A"], p["B"], p["C"]
@@ -115,7 +121,7 @@ def _fd_check(lib, shape, gen, seed, recompute=False, h=1e-6, ndir=20):
         if which == 0:
             E = np.asfortranarray(rng.standard_normal(shape))
             g = float(np.sum(gB * E))
-            fp, fm = L(Ah, Bh + h * E, Ch), L(Ah, Bh - h * E, Ch)
+            fd = central((Ah, Bh + h * E, Ch), (Ah, Bh - h * E, Ch))
         elif which == 1:
             E = np.triu(rng.standard_normal((n, n)))
             for s in p["blocks"][mu]:
@@ -125,7 +131,7 @@ def _fd_check(lib, shape, gen, seed, recompute=False, h=1e-6, ndir=20):
             Am = [a.copy() for a in Ah]
             Ap[mu] += h * E
             Am[mu] -= h * E
-            fp, fm = L(Ap, Bh, Ch), L(Am, Bh, Ch)
+            fd = central((Ap, Bh, Ch), (Am, Bh, Ch))
         else:
             E = np.triu(rng.standard_normal((n, n)))
             g = float(np.sum(gC[mu] * E))
@@ -133,8 +139,7 @@ def _fd_check(lib, shape, gen, seed, recompute=False, h=1e-6, ndir=20):
             Cm = [c.copy() for c in Ch]
             Cp[mu] += h * E
             Cm[mu] -= h * E
-            fp, fm = L(Ah, Bh, Cp), L(Ah, Bh, Cm)
-        fd = (fp - fm) / (2 * h)
+            fd = central((Ah, Bh, Cp), (Ah, Bh, Cm))
         err = abs(fd - g) / max(1.0, abs(g))
         worst = max(worst, err)
     assert worst <= 1e-6, worst
