@@ -105,6 +105,15 @@ typedef struct tsylv_opts {
                          dataflow launch (a block starts as soon as each source
                          block it reads is solved); 1 one launch per anti-diagonal
                          wavefront (split over a cluster when the wavefront is short) */
+    int partition;    /* blocks of each mode: 0 (default) tile-aligned blocks of the
+                         largest extent, a boundary moved back by one where it
+                         would cut a 2x2 block; 1 the leaves of the halving split
+                         rule of Alg. 2.  Both give the same solution up to rounding. */
+    int resid_update; /* *_REFINED: 0 (default) from the second refinement step on,
+                         once the relative residual is <= 1e-5, the residual is
+                         updated from the step's FP32 correction, R -= s A(D) in
+                         FP32 (error ~2^-24 |A| |s D|, far below the residual);
+                         1: the full FP64-accurate residual at every step         */
 } tsylv_opts;
 
 typedef struct tsylv_info {

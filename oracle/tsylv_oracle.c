@@ -23,9 +23,9 @@
  *       visited in decreasing lexicographic order; the right-hand side of a
  *       group subtracts every already-solved unknown times the operator entry
  *       computed from its definition; the group system is solved by Gaussian
- *       elimination with partial pivoting.  This is the "assemble and solve the
- *       block triangular system by backward substitution" step of Alg. 2,
- *       line 2 (Sec. 2.1), applied to a whole tensor.
+ *       elimination with partial pivoting.  This is the base case of Alg. 2
+ *       (Sec. 2.1: the small block-triangular system solved by
+ *       back-substitution), applied to a whole tensor.
  *  O-B  orc_recursive: Alg. 2 (Sec. 2.1) -- split the largest mode at
  *       k = floor(n_mu/2), k+1 if that cuts a 2x2 block; solve the trailing
  *       part; update the leading right-hand side (Eq. (2.3a)); solve the
@@ -413,17 +413,17 @@ static int rec_solve(rec_ctx* r, const int64_t* off, const int64_t* ext, int tra
     for (int q = 1; q < d; q++) if (ext[q] > ext[mu]) mu = q;    /* lowest mode on ties */
     if (ext[mu] <= r->nmin) return backsub_box(c, r->X, off, ext, transpose);
     int64_t m = ext[mu], k = m / 2;
-    /* Alg. 2, line 3: do not cut a 2x2 block, i.e. A_mu(k+1, k) != 0 (1-based) */
+    /* split rule of Alg. 2: do not cut a 2x2 block, i.e. A_mu(k+1, k) != 0 (1-based) */
     if (c->A[mu][(off[mu] + k) + c->n[mu] * (off[mu] + k - 1)] != 0.0) k += 1;
     if (k >= m) return backsub_box(c, r->X, off, ext, transpose);
     int64_t o2[ORC_MAXD], e2[ORC_MAXD], e1[ORC_MAXD];
     for (int q = 0; q < d; q++) { o2[q] = off[q]; e2[q] = ext[q]; e1[q] = ext[q]; }
     o2[mu] = off[mu] + k; e2[mu] = m - k; e1[mu] = k;
     if (!transpose) {
-        int s = rec_solve(r, o2, e2, 0);                   /* Alg. 2, line 5 */
+        int s = rec_solve(r, o2, e2, 0);                   /* trailing part X2 first (Alg. 2) */
         if (s) return s;
-        if (rec_update(r, mu, off, ext, k, 0)) return -1;  /* Alg. 2, line 6 */
-        return rec_solve(r, off, e1, 0);                   /* Alg. 2, line 7 (with the updated B1) */
+        if (rec_update(r, mu, off, ext, k, 0)) return -1;  /* update of B1, Eq. (2.3a) */
+        return rec_solve(r, off, e1, 0);                   /* leading part X1 with the updated B1 */
     }
     int s = rec_solve(r, off, e1, 1);
     if (s) return s;

@@ -40,6 +40,8 @@ extern "C" void tsylv_opts_default(tsylv_opts* o) {
     o->host_io = 0;
     o->timing = 0;
     o->schedule = 0;
+    o->partition = 0;
+    o->resid_update = 0;
 }
 
 extern "C" const char* tsylv_status_string(int s) {

@@ -44,6 +44,7 @@ struct ApplyArgs {
     void* o2;
     void* o2l;
     const double* B;   // right-hand side (double tiles) for kApplyLaplace / kApplyFinal
+    const double* scale;  // nullptr: R = B - A(X); else R = B - scale[1] * A(S) (B may alias R)
     double* R;         // residual (double tiles)
     double* part;      // [ntiles][2]: sum of R^2, max |R| of every block
     // coefficient tiles (upper block triangle), per mode: FP64 A/C (double),
@@ -60,6 +61,10 @@ template <bool DF>
 cudaError_t launch_apply(int d, const ApplyArgs& a, cudaStream_t s);
 template <bool DF>
 cudaError_t prepare_apply();
+// FP32 sources and coefficient tiles, FP32 accumulation (the refinement's
+// residual update from its FP32 correction).
+cudaError_t launch_apply_f32(int d, const ApplyArgs& a, cudaStream_t s);
+cudaError_t prepare_apply_f32();
 
 
 }  // namespace tsylv

@@ -1,4 +1,6 @@
-// Operator application kernels (residual of the refinement), FP64 and DF64.
+// Operator application kernels (residual of the refinement): FP64, DF64
+// (float pairs on the FP32 pipes) and plain FP32 (the residual update of a
+// refinement step from its FP32 correction).
 #include "apply_kernel.cuh"
 #include "device_common.cuh"
 
@@ -36,13 +38,15 @@ namespace {
 
 using namespace apply_detail;
 
-template <int D, bool DF>
+// arithmetic of an apply: 0 FP64, 1 DF64, 2 FP32
+enum : int { kModeF64 = 0, kModeDF = 1, kModeF32 = 2 };
+
+template <int D, int M>
 struct ApplyCfg {
     static constexpr int TE = tile_extent(D);
     static constexpr int TD = ipow(TE, D);
     static constexpr int TC = TE * TE;
     static constexpr int EPT = (TD + kThreads - 1) / kThreads;
-    static constexpr int P = DF ? 2 : 1;                  // words per logical entry
     // one stage: S1, S2 (P x TD each), M1, M2 (P x TC each), in 8-byte units
     static constexpr int STAGE_BYTES = (2 * TD + 2 * TC) * 8;
     static constexpr size_t oBar = 2 * STAGE_BYTES;
@@ -85,14 +89,49 @@ __device__ __forceinline__ void acc_df(float (&yh)[EPT], float (&yl)[EPT], const
     }
 }
 
-template <int D, bool DF, int MU>
-__device__ __forceinline__ void do_job(int kind, const unsigned char* stg, double (&y1)[ApplyCfg<D, DF>::EPT],
-                                       double (&y2)[ApplyCfg<D, DF>::EPT], float (&h1)[ApplyCfg<D, DF>::EPT],
-                                       float (&l1)[ApplyCfg<D, DF>::EPT], float (&h2)[ApplyCfg<D, DF>::EPT],
-                                       float (&l2)[ApplyCfg<D, DF>::EPT]) {
-    using C = ApplyCfg<D, DF>;
+// y[q] += (M x_MU S)[e_q]: FP32
+template <int D, int MU, int EPT>
+__device__ __forceinline__ void acc_f32(float (&y)[EPT], const float* __restrict__ M, const float* __restrict__ S) {
+    constexpr int TE = tile_extent(D), TD = ipow(TE, D), st = ipow(TE, MU);
+#pragma unroll
+    for (int q = 0; q < EPT; q++) {
+        const int e = threadIdx.x + q * kThreads;
+        if ((TD % kThreads) != 0 && e >= TD) continue;
+        const int i = (e / st) % TE, base = e - i * st;
+        float v = y[q];
+#pragma unroll
+        for (int k = 0; k < TE; k++) v = fmaf(M[i + TE * k], S[base + k * st], v);
+        y[q] = v;
+    }
+}
+
+template <int D, int MD, int MU>
+__device__ __forceinline__ void do_job(int kind, const unsigned char* stg, double (&y1)[ApplyCfg<D, MD>::EPT],
+                                       double (&y2)[ApplyCfg<D, MD>::EPT], float (&h1)[ApplyCfg<D, MD>::EPT],
+                                       float (&l1)[ApplyCfg<D, MD>::EPT], float (&h2)[ApplyCfg<D, MD>::EPT],
+                                       float (&l2)[ApplyCfg<D, MD>::EPT]) {
+    using C = ApplyCfg<D, MD>;
     constexpr int TD = C::TD, TC = C::TC, EPT = C::EPT;
-    if constexpr (!DF) {
+    if constexpr (MD == kModeF32) {
+        // same staging layout as DF64, the low words unused
+        const float* S1 = reinterpret_cast<const float*>(stg);
+        const float* S2 = S1 + 2 * TD;
+        const float* M1 = S1 + 4 * TD;
+        const float* M2 = M1 + 2 * TC;
+        if (kind == kApplyLaplace) {
+            acc_f32<D, MU, EPT>(h1, M1, S1);
+        } else if (kind == kApplyFirst) {
+            acc_f32<D, MU, EPT>(h1, M1, S1);
+            acc_f32<D, MU, EPT>(h2, M2, S1);
+        } else if (kind == kApplyMiddle) {
+            acc_f32<D, MU, EPT>(h1, M1, S1);
+            acc_f32<D, MU, EPT>(h2, M1, S2);
+            acc_f32<D, MU, EPT>(h2, M2, S1);
+        } else {
+            acc_f32<D, MU, EPT>(h1, M1, S2);
+            acc_f32<D, MU, EPT>(h1, M2, S1);
+        }
+    } else if constexpr (MD == kModeF64) {
         const double* S1 = reinterpret_cast<const double*>(stg);
         const double* S2 = S1 + TD;
         const double* M1 = S2 + TD;
@@ -135,22 +174,23 @@ __device__ __forceinline__ void do_job(int kind, const unsigned char* stg, doubl
     }
 }
 
-template <int D, bool DF, int MU = 0>
-__device__ __forceinline__ void dispatch(int mu, int kind, const unsigned char* stg, double (&y1)[ApplyCfg<D, DF>::EPT],
-                                         double (&y2)[ApplyCfg<D, DF>::EPT], float (&h1)[ApplyCfg<D, DF>::EPT],
-                                         float (&l1)[ApplyCfg<D, DF>::EPT], float (&h2)[ApplyCfg<D, DF>::EPT],
-                                         float (&l2)[ApplyCfg<D, DF>::EPT]) {
+template <int D, int MD, int MU = 0>
+__device__ __forceinline__ void dispatch(int mu, int kind, const unsigned char* stg, double (&y1)[ApplyCfg<D, MD>::EPT],
+                                         double (&y2)[ApplyCfg<D, MD>::EPT], float (&h1)[ApplyCfg<D, MD>::EPT],
+                                         float (&l1)[ApplyCfg<D, MD>::EPT], float (&h2)[ApplyCfg<D, MD>::EPT],
+                                         float (&l2)[ApplyCfg<D, MD>::EPT]) {
     if constexpr (MU < D) {
         if (mu == MU)
-            do_job<D, DF, MU>(kind, stg, y1, y2, h1, l1, h2, l2);
+            do_job<D, MD, MU>(kind, stg, y1, y2, h1, l1, h2, l2);
         else
-            dispatch<D, DF, MU + 1>(mu, kind, stg, y1, y2, h1, l1, h2, l2);
+            dispatch<D, MD, MU + 1>(mu, kind, stg, y1, y2, h1, l1, h2, l2);
     }
 }
 
-template <int D, bool DF>
+template <int D, int MD>
 __global__ void __launch_bounds__(kThreads) k_apply(const ApplyArgs a) {
-    using C = ApplyCfg<D, DF>;
+    using C = ApplyCfg<D, MD>;
+    constexpr bool DF = MD == kModeDF;
     constexpr int TE = C::TE, TD = C::TD, TC = C::TC, EPT = C::EPT;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::oBar);
@@ -188,7 +228,19 @@ __global__ void __launch_bounds__(kThreads) k_apply(const ApplyArgs a) {
         const long long tri = static_cast<long long>(J) * (J + 1) / 2 + I[mu];
         unsigned char* sb = smem + stg * C::STAGE_BYTES;
         uint32_t bytes = 0;
-        if constexpr (!DF) {
+        if constexpr (MD == kModeF32) {
+            float* S1 = reinterpret_cast<float*>(sb);
+            float* S2 = S1 + 2 * TD;
+            float* M1 = S1 + 4 * TD;
+            float* M2 = M1 + 2 * TC;
+            bytes = (two_src ? 2 : 1) * TD * 4 + (two_coef ? 2 : 1) * TC * 4;
+            dev::mbar_expect_tx(&bar[stg], bytes);
+            dev::bulk_g2s(S1, static_cast<const float*>(a.s1) + ts * TD, TD * 4, &bar[stg]);
+            if (two_src) dev::bulk_g2s(S2, static_cast<const float*>(a.s2) + ts * TD, TD * 4, &bar[stg]);
+            const float* m1 = static_cast<const float*>(lap ? a.A[mu] : a.C[mu]) + tri * TC;
+            dev::bulk_g2s(M1, m1, TC * 4, &bar[stg]);
+            if (two_coef) dev::bulk_g2s(M2, static_cast<const float*>(a.A[mu]) + tri * TC, TC * 4, &bar[stg]);
+        } else if constexpr (MD == kModeF64) {
             double* S1 = reinterpret_cast<double*>(sb);
             double* S2 = S1 + TD;
             double* M1 = S2 + TD;
@@ -250,7 +302,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const ApplyArgs a) {
         }
         int mu, J;
         decode(jj, mu, J);
-        dispatch<D, DF>(mu, a.kind, smem + stg * C::STAGE_BYTES, y1, y2, h1, l1, h2, l2);
+        dispatch<D, MD>(mu, a.kind, smem + stg * C::STAGE_BYTES, y1, y2, h1, l1, h2, l2);
         __syncthreads();
         if (tid == 0 && jj + 2 < njob) {
             dev::fence_proxy_async();
@@ -264,8 +316,10 @@ __global__ void __launch_bounds__(kThreads) k_apply(const ApplyArgs a) {
         for (int q = 0; q < EPT; q++) {
             const int e = tid + q * kThreads;
             if ((TD % kThreads) != 0 && e >= TD) continue;
-            const double v = DF ? df_to_double(h1[q], l1[q]) : y1[q];
-            const double r = a.B[t * TD + e] - v;
+            const double v = MD == kModeDF ? df_to_double(h1[q], l1[q])
+                             : MD == kModeF32 ? static_cast<double>(h1[q]) : y1[q];
+            // scale given: R = B - scale * A(S) (B may be R itself: update in place)
+            const double r = a.scale ? a.B[t * TD + e] - a.scale[1] * v : a.B[t * TD + e] - v;
             a.R[t * TD + e] = r;
             ss += r * r;
             mx = fmax(mx, fabs(r));
@@ -288,7 +342,10 @@ __global__ void __launch_bounds__(kThreads) k_apply(const ApplyArgs a) {
         for (int q = 0; q < EPT; q++) {
             const int e = tid + q * kThreads;
             if ((TD % kThreads) != 0 && e >= TD) continue;
-            if constexpr (!DF) {
+            if constexpr (MD == kModeF32) {
+                static_cast<float*>(a.o1)[t * TD + e] = h1[q];
+                static_cast<float*>(a.o2)[t * TD + e] = h2[q];
+            } else if constexpr (MD == kModeF64) {
                 static_cast<double*>(a.o1)[t * TD + e] = y1[q];
                 static_cast<double*>(a.o2)[t * TD + e] = y2[q];
             } else {
@@ -304,40 +361,53 @@ __global__ void __launch_bounds__(kThreads) k_apply(const ApplyArgs a) {
     }
 }
 
-template <int D, bool DF>
+template <int D, int MD>
 cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t s) {
-    using C = ApplyCfg<D, DF>;
-    k_apply<D, DF><<<static_cast<unsigned>(a.ntiles), kThreads, C::smem, s>>>(a);
+    using C = ApplyCfg<D, MD>;
+    k_apply<D, MD><<<static_cast<unsigned>(a.ntiles), kThreads, C::smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int D, bool DF>
+template <int D, int MD>
 cudaError_t prepare_apply_t() {
-    return cudaFuncSetAttribute(k_apply<D, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(ApplyCfg<D, DF>::smem));
+    return cudaFuncSetAttribute(k_apply<D, MD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(ApplyCfg<D, MD>::smem));
+}
+
+template <int MD>
+cudaError_t launch_apply_m(int d, const ApplyArgs& a, cudaStream_t s) {
+    switch (d) {
+        case 1: return launch_apply_t<1, MD>(a, s);
+        case 2: return launch_apply_t<2, MD>(a, s);
+        case 3: return launch_apply_t<3, MD>(a, s);
+        case 4: return launch_apply_t<4, MD>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int MD>
+cudaError_t prepare_apply_m() {
+    cudaError_t e;
+    if ((e = prepare_apply_t<1, MD>()) != cudaSuccess) return e;
+    if ((e = prepare_apply_t<2, MD>()) != cudaSuccess) return e;
+    if ((e = prepare_apply_t<3, MD>()) != cudaSuccess) return e;
+    return prepare_apply_t<4, MD>();
 }
 
 }  // namespace
 
 template <bool DF>
 cudaError_t launch_apply(int d, const ApplyArgs& a, cudaStream_t s) {
-    switch (d) {
-        case 1: return launch_apply_t<1, DF>(a, s);
-        case 2: return launch_apply_t<2, DF>(a, s);
-        case 3: return launch_apply_t<3, DF>(a, s);
-        case 4: return launch_apply_t<4, DF>(a, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return launch_apply_m<DF ? kModeDF : kModeF64>(d, a, s);
 }
 
 template <bool DF>
 cudaError_t prepare_apply() {
-    cudaError_t e;
-    if ((e = prepare_apply_t<1, DF>()) != cudaSuccess) return e;
-    if ((e = prepare_apply_t<2, DF>()) != cudaSuccess) return e;
-    if ((e = prepare_apply_t<3, DF>()) != cudaSuccess) return e;
-    return prepare_apply_t<4, DF>();
+    return prepare_apply_m<DF ? kModeDF : kModeF64>();
 }
+
+cudaError_t launch_apply_f32(int d, const ApplyArgs& a, cudaStream_t s) { return launch_apply_m<kModeF32>(d, a, s); }
+cudaError_t prepare_apply_f32() { return prepare_apply_m<kModeF32>(); }
 
 template cudaError_t launch_apply<false>(int, const ApplyArgs&, cudaStream_t);
 template cudaError_t launch_apply<true>(int, const ApplyArgs&, cudaStream_t);

@@ -243,8 +243,8 @@ double eq_flops(const EqPlan& q, bool gen) {
 }
 
 std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t* n_packed, bool gen, int elem,
-                                          const std::vector<uint8_t>& sub) {
-    std::vector<long long> key = {count, gen ? 1 : 0, elem};
+                                          const std::vector<uint8_t>& sub, int partition) {
+    std::vector<long long> key = {count, gen ? 1 : 0, elem, partition};
     size_t k = 0;
     for (int e = 0; e < count; e++) {
         key.push_back(d[e]);
@@ -283,7 +283,7 @@ std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t
             std::vector<uint8_t> s(sub.begin() + static_cast<long long>(soff),
                                    sub.begin() + static_cast<long long>(soff + q.n[mu] - 1));
             soff += static_cast<size_t>(q.n[mu] - 1);
-            q.part[mu] = make_part(static_cast<int>(q.n[mu]), s, te);
+            q.part[mu] = make_part(static_cast<int>(q.n[mu]), s, te, partition);
             q.nb[mu] = q.part[mu].nb;
             q.tstride[mu] = ts;
             ts *= q.nb[mu];
@@ -541,7 +541,7 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     if (o.precision != TSYLV_FP64) return TSYLV_EUNSUPPORTED;
     const size_t need = solver_batched_workspace_bytes(count, d, n_packed, gen, o);
     if (!need || work_bytes < need) return -11;
-    if (o.split < 0) return -12;
+    if (o.split < 0 || o.partition < 0 || o.partition > 1) return -12;
     size_t nmats = 0;
     for (int e = 0; e < count; e++) nmats += static_cast<size_t>(d[e]);
     for (size_t k = 0; k < nmats; k++)
@@ -613,7 +613,7 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     }
 
     // ---- plan (cached per shapes and structure), tables, launch
-    std::shared_ptr<BatchPlan> plan = get_batch_plan(count, d, n_packed, gen, 8, sub);
+    std::shared_ptr<BatchPlan> plan = get_batch_plan(count, d, n_packed, gen, 8, sub, o.partition == 1 ? 1 : 0);
     if (!plan) return cuda_fail_msg("batched: plan");
     if (plan->data_bytes > bd.data) return cuda_fail_msg("batched: workspace bound");
     if (int st = prepare_batched_once()) return st;

@@ -16,12 +16,11 @@ __global__ void __launch_bounds__(kThreads) k_batched(const BatchArgs b) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::oBar);
     __shared__ int s_job, s_ok;
     if (threadIdx.x == 0) {
-        dev::mbar_init(&bar[0], 1);
-        dev::mbar_init(&bar[1], 1);
+        for (int q = 0; q < C::NST; q++) dev::mbar_init(&bar[q], 1);
         dev::fence_mbar_init();
     }
     __syncthreads();
-    uint32_t uses[2] = {0u, 0u};
+    uint32_t uses[C::NST] = {};
     bool alive = true;  // false after a timed-out copy: no further copies on these barriers
     for (;;) {
         if (threadIdx.x == 0) s_job = atomicAdd(b.head, 1);

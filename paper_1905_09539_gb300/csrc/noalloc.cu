@@ -120,7 +120,7 @@ int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const 
             if (s[i] && s[i + 1]) return -3;
         off += static_cast<size_t>(n[mu] - 1);
         p.n[mu] = n[mu];
-        p.part[mu] = make_part(static_cast<int>(n[mu]), s, p.te);
+        p.part[mu] = make_part(static_cast<int>(n[mu]), s, p.te, o.partition == 1 ? 1 : 0);
         p.nb[mu] = p.part[mu].nb;
         p.tstride[mu] = ts;
         ts *= p.nb[mu];

@@ -25,10 +25,27 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 }  // namespace
 
-Part make_part(int n, const std::vector<uint8_t>& sub, int te) {
+// Leaf boundaries of one mode.  rule 0 (aligned): blocks of te entries from
+// the start, a boundary moved back by one where it would cut a 2x2 block (so
+// every block has te or te - 1 entries, the last one possibly fewer: the least
+// padding of the te-wide tiles).  rule 1: the split rule of Alg. 2,
+// applied recursively (halving, moved by one at a 2x2 block) until every piece
+// has at most te entries.  Both partitions keep every 2x2 block whole, so
+// they give the same solution up to rounding.
+Part make_part(int n, const std::vector<uint8_t>& sub, int te, int rule) {
     Part p;
     p.n = n;
-    split_rec(sub, 0, n, te, p.start);
+    if (rule == 1) {
+        split_rec(sub, 0, n, te, p.start);
+    } else {
+        int start = 0;
+        while (start < n) {
+            p.start.push_back(start);
+            int end = std::min(start + te, n);
+            if (end < n && sub[end - 1]) end -= 1;  // A(end+1, end) != 0 (1-based): keep the 2x2 block whole
+            start = end;
+        }
+    }
     p.nb = static_cast<int>(p.start.size());
     p.size.resize(p.nb);
     p.blk_of.resize(n);
@@ -40,6 +57,7 @@ Part make_part(int n, const std::vector<uint8_t>& sub, int te) {
     return p;
 }
 
+// Largest number of leaves either rule can produce for any admissible structure.
 int max_blocks(int n, int te) {
     std::vector<int> memo(static_cast<size_t>(n) + 1, -1);
     std::function<int(int)> f = [&](int m) -> int {
@@ -51,7 +69,9 @@ int max_blocks(int n, int te) {
         memo[m] = best;
         return best;
     };
-    return f(n);
+    // aligned rule: every block but the last has at least te - 1 entries
+    const int aligned = te > 1 ? (n - 1) / (te - 1) + 1 : n;
+    return std::max(f(n), aligned);
 }
 
 Plan::~Plan() {
@@ -169,8 +189,9 @@ void build_waves(Plan& p, int split) {
 }  // namespace
 
 std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, int split,
-                               const std::vector<uint8_t>* sub) {
-    std::string key = std::to_string(d) + (gen ? "g" : "l") + std::to_string(elem) + "s" + std::to_string(split);
+                               const std::vector<uint8_t>* sub, int partition) {
+    std::string key = std::to_string(d) + (gen ? "g" : "l") + std::to_string(elem) + "s" + std::to_string(split) +
+                      "p" + std::to_string(partition);
     size_t off = 0;
     for (int mu = 0; mu < d; mu++) {
         key += ":" + std::to_string(n[mu]) + ":";
@@ -194,7 +215,7 @@ std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, in
         std::vector<uint8_t> s(static_cast<size_t>(n[mu]), 0);
         for (long long i = 0; i + 1 < n[mu]; i++) s[i] = sub[0][off + i];
         off += static_cast<size_t>(n[mu] - 1);
-        p->part[mu] = make_part(static_cast<int>(n[mu]), s, p->te);
+        p->part[mu] = make_part(static_cast<int>(n[mu]), s, p->te, partition);
         p->nb[mu] = p->part[mu].nb;
         p->tstride[mu] = ts;
         ts *= p->nb[mu];

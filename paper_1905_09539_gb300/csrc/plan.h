@@ -21,10 +21,10 @@ struct Part {
     std::vector<int> start, size, blk_of;
 };
 
-// Alg. 2, lines 3-4 applied recursively to one mode: split m at
+// The split rule of Alg. 2 applied recursively to one mode: split m at
 // k = floor(m/2), k+1 when A(k+1, k) != 0 (1-based) so that no 2x2 block is
 // cut, until every piece has at most te entries.  sub[i] != 0 marks A(i+1, i).
-Part make_part(int n, const std::vector<uint8_t>& sub, int te);
+Part make_part(int n, const std::vector<uint8_t>& sub, int te, int rule);
 
 // Largest number of leaves any admissible block structure can produce.
 int max_blocks(int n, int te);
@@ -68,7 +68,7 @@ struct Layout {
 Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem, size_t tab_ints);
 
 std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, int split,
-                               const std::vector<uint8_t>* sub);
+                               const std::vector<uint8_t>* sub, int partition);
 
 GeomArgs geom_of(const Plan& p, const Layout& L, char* base, bool flip);
 

@@ -139,6 +139,7 @@ struct Call {
     bool timing = false;
     bool persistent = true;   // opts->schedule == 0
     int flow_grid = 0;        // CTAs of the persistent launch
+    bool update = false;      // refinement step: residual updated from the FP32 correction
 };
 
 inline cudaError_t mark(const Call& c, int i, cudaStream_t s) {
@@ -235,15 +236,24 @@ cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
 
 // ------------------------------------------------- residual R = B - A(X) (tiles)
 
+// R = B - A(X) in FP64-accurate arithmetic (FP64 or DF64), or, with c.update,
+// R -= s A(D) in FP32 for the FP32 correction D of the step (X += s D, s the
+// scale max|R| of the step's right-hand side): the residual of the corrected
+// X without re-evaluating A(X).  The update is accurate to about 2^-24 |A| |s D|,
+// far below the residual once the correction is small.
 cudaError_t enqueue_residual(const Call& c, cudaStream_t s) {
     const Plan& p = *c.plan;
     const RefLayout& R = c.R;
     char* b = c.base;
     ApplyArgs a{};
+    const bool up = c.update;
     for (int mu = 0; mu < p.d; mu++) {
         a.nb[mu] = p.nb[mu];
         a.tstride[mu] = p.tstride[mu];
-        if (c.df) {
+        if (up) {
+            a.A[mu] = b + R.L32.At[mu];
+            a.C[mu] = p.gen ? b + R.L32.Ct[mu] : nullptr;
+        } else if (c.df) {
             a.A[mu] = b + R.Ah[mu];
             a.Al[mu] = b + R.Al[mu];
             a.C[mu] = p.gen ? b + R.Ch[mu] : nullptr;
@@ -254,18 +264,23 @@ cudaError_t enqueue_residual(const Call& c, cudaStream_t s) {
         }
     }
     a.ntiles = p.ntiles;
-    a.B = reinterpret_cast<const double*>(b + R.Bt);
+    a.B = reinterpret_cast<const double*>(b + (up ? R.Rt : R.Bt));
     a.R = reinterpret_cast<double*>(b + R.Rt);
+    a.scale = up ? reinterpret_cast<const double*>(b + R.nrm) : nullptr;
     a.part = reinterpret_cast<double*>(b + R.part);
     a.err = reinterpret_cast<int*>(b + R.L32.err);
     a.timeout_ns = kTimeoutNs;
-    const void* xs = c.df ? static_cast<const void*>(b + R.Xh) : static_cast<const void*>(b + R.Xt);
-    const void* xsl = c.df ? static_cast<const void*>(b + R.Xl) : nullptr;
+    const void* xs = up ? static_cast<const void*>(b + R.L32.X)
+                        : c.df ? static_cast<const void*>(b + R.Xh) : static_cast<const void*>(b + R.Xt);
+    const void* xsl = c.df && !up ? static_cast<const void*>(b + R.Xl) : nullptr;
+    auto launch = [&](const ApplyArgs& aa) {
+        return up ? launch_apply_f32(p.d, aa, s) : c.df ? launch_apply<true>(p.d, aa, s) : launch_apply<false>(p.d, aa, s);
+    };
     if (!p.gen) {
         a.kind = kApplyLaplace;
         a.s1 = xs;
         a.s1l = xsl;
-        return c.df ? launch_apply<true>(p.d, a, s) : launch_apply<false>(p.d, a, s);
+        return launch(a);
     }
     // Horner levels d-1 .. 0, ping-pong between the two intermediate sets
     int cur = 0;
@@ -278,7 +293,7 @@ cudaError_t enqueue_residual(const Call& c, cudaStream_t s) {
     a.o1l = setp(0, 1);
     a.o2 = setp(0, 2);
     a.o2l = setp(0, 3);
-    TRY(c.df ? launch_apply<true>(p.d, a, s) : launch_apply<false>(p.d, a, s));
+    TRY(launch(a));
     for (int l = p.d - 2; l >= 0; l--) {
         a.kind = l == 0 ? kApplyFinal : kApplyMiddle;
         a.mode = l;
@@ -290,7 +305,7 @@ cudaError_t enqueue_residual(const Call& c, cudaStream_t s) {
         a.o1l = setp(1 - cur, 1);
         a.o2 = setp(1 - cur, 2);
         a.o2l = setp(1 - cur, 3);
-        TRY(c.df ? launch_apply<true>(p.d, a, s) : launch_apply<false>(p.d, a, s));
+        TRY(launch(a));
         cur = 1 - cur;
     }
     return cudaSuccess;
@@ -376,12 +391,13 @@ cudaError_t enqueue_ref_iter(const Call& c, cudaStream_t s) {
     TRY(launch_scale_to_f32(reinterpret_cast<double*>(b + R.Rt), reinterpret_cast<float*>(b + L.X), nrm, nel, s));
     TRY(enqueue_waves<float>(c, L, s));
     // X += max|R| D  (FP64), its float-pair split, block sums of X^2
+    const bool split = c.df && !c.update;  // the float-pair X only feeds a full DF64 residual
     TRY(launch_update_x(reinterpret_cast<double*>(b + R.Xt), reinterpret_cast<float*>(b + L.X), nrm,
-                        c.df ? reinterpret_cast<float*>(b + R.Xh) : nullptr,
-                        c.df ? reinterpret_cast<float*>(b + R.Xl) : nullptr, reinterpret_cast<double*>(b + R.xpart),
+                        split ? reinterpret_cast<float*>(b + R.Xh) : nullptr,
+                        split ? reinterpret_cast<float*>(b + R.Xl) : nullptr, reinterpret_cast<double*>(b + R.xpart),
                         nel, p.td, s));
     TRY(mark(c, 1, s));
-    // R = B - A(X) in FP64-accurate arithmetic
+    // R = B - A(X) in FP64-accurate arithmetic, or R -= s A(D) in FP32
     TRY(enqueue_residual(c, s));
     TRY(mark(c, 2, s));
     TRY(launch_reduce(reinterpret_cast<double*>(b + R.part), reinterpret_cast<double*>(b + R.xpart), p.ntiles,
@@ -499,6 +515,7 @@ int prepare_kernels() {
         if (e == cudaSuccess) e = prepare_wave<float>();
         if (e == cudaSuccess) e = prepare_apply<false>();
         if (e == cudaSuccess) e = prepare_apply<true>();
+        if (e == cudaSuccess) e = prepare_apply_f32();
         if (e == cudaSuccess) e = prepare_batched<double>();
         if (e == cudaSuccess) e = prepare_batched<float>();
         if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
@@ -633,7 +650,8 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (work_bytes < solver_workspace_bytes(d, n, gen, o, transposed)) return -(7 + sh);
     if (o.precision < TSYLV_FP64 || o.precision > TSYLV_BF16_REFINED || o.max_refine < 0 || !(o.tol > 0) ||
         (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < 0 ||
-        o.schedule < 0 || o.schedule > 1)
+        o.schedule < 0 || o.schedule > 1 || o.partition < 0 || o.partition > 1 || o.resid_update < 0 ||
+        o.resid_update > 1)
         return -(8 + sh);
     if (o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d))) return TSYLV_EUNSUPPORTED;
     if (o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) return TSYLV_EUNSUPPORTED;
@@ -656,7 +674,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
 
     std::vector<uint8_t> sub;
     if (int st = read_structure(d, c.n, c.A, c.base, transposed, stream, sub)) return st;
-    c.plan = get_plan(d, c.n, c.gen, refined ? 4 : 8, o.split, &sub);
+    c.plan = get_plan(d, c.n, c.gen, refined ? 4 : 8, o.split, &sub, o.partition);
     if (!c.plan) return cuda_fail_msg("plan: pinned host allocation");
     if (int st = prepare_kernels()) return st;
     c.timing = o.timing != 0;
@@ -724,7 +742,11 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
         double prev = HUGE_VAL;
         int stall = 0;
         for (int it = 0; it < std::max(1, o.max_refine); it++) {
-            st = run_enqueue(*c.plan, make_key(c, tagbase | 32), o.use_graph != 0, stream, enqueue_ref_iter, c);
+            // from the second step on, once the correction is small, the
+            // residual is updated from the FP32 correction instead of re-evaluated
+            if (o.resid_update == 0 && it > 0 && prev <= 1e-5) c.update = true;
+            st = run_enqueue(*c.plan, make_key(c, tagbase | 32 | (c.update ? 512 : 0)), o.use_graph != 0, stream,
+                             enqueue_ref_iter, c);
             if (st) return st;
             if ((e = cudaMemcpyAsync(hn, c.base + c.R.nrm, 3 * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
                 return cuda_fail(e, "read residual norm");
@@ -823,7 +845,7 @@ int solver_residual(int d, const int64_t* n, const double* const* A, const doubl
     (void)cudaGetLastError();
     std::vector<uint8_t> sub;
     if (int st = read_structure(d, c.n, c.A, c.base, false, stream, sub)) return st;
-    c.plan = get_plan(d, c.n, c.gen, 4, 0, &sub);
+    c.plan = get_plan(d, c.n, c.gen, 4, 0, &sub, o.partition == 1 ? 1 : 0);
     if (!c.plan) return cuda_fail_msg("plan: pinned host allocation");
     if (int st = prepare_kernels()) return st;
     c.R = make_ref_layout(d, c.n, c.plan->nb, c.gen, c.plan->tab.size());

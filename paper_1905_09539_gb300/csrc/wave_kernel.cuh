@@ -30,10 +30,13 @@ struct WaveCfg {
     static constexpr int NACC = GEN ? 2 * (D - 1) + 1 : 1;
     static constexpr int NL = GEN ? D - 1 : 0;  // stored levels l = 1..d-1
     static constexpr int STAGE = 2 * TD + 2 * TC;
+    // stages of the bulk-copy ring: the FP64 updates are bound by the FP64
+    // pipes, the FP32 ones by the copy latency
+    static constexpr int NST = sizeof(T) == 8 ? 2 : (GEN ? 4 : 6);
     // the staging ring of the block updates and the base case's running
     // line sums share one region
     static constexpr int MINV = 1024;  // budget (entries) for precomputed coupled-group inverses
-    static constexpr int UNION = (2 * STAGE > NACC * TD + MINV) ? 2 * STAGE : NACC * TD + MINV;
+    static constexpr int UNION = (NST * STAGE > NACC * TD + MINV) ? NST * STAGE : NACC * TD + MINV;
     static constexpr int oStage = 0;
     static constexpr int oLin = 0;
     static constexpr int oMinv = NACC * TD;
@@ -47,7 +50,7 @@ struct WaveCfg {
     static constexpr int oE = oD + D * TC;
     static constexpr int oEnd = oE + (GEN ? D * TC : 0);
     static constexpr size_t oBar = ((oEnd * sizeof(T)) + 15) / 16 * 16;
-    static constexpr size_t oMeta = oBar + 16;
+    static constexpr size_t oMeta = oBar + ((8 * NST + 15) / 16) * 16;
     // meta: gs, gl, gidx [D][TE]; ng, bs [D]; flag [4]; coupled-group lists
     static constexpr int MAXSTEP = D * TE;
     static constexpr size_t smem =
@@ -602,14 +605,14 @@ __device__ int group_inverse(const TileSmem<T, D, GEN>& sm, int e, T* out) {
 
 // One block T of the block grid: its right-hand-side update (split over the
 // `csize` CTAs of a cluster, this CTA being `rank`) and, on rank 0, its base
-// case.  The CTA's two staging barriers are initialised by the caller;
+// case.  The CTA's NST staging barriers are initialised by the caller;
 // uses[s] counts the phases barrier s has completed so far (a persistent
 // caller runs many blocks on the same barriers).  Returns false when a wait
 // ran out of time (the error word is set; no copy of this call is left in
 // flight).
 template <typename T, int D, bool GENF>
 __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, const int rank, const int csize,
-                                          uint32_t (&uses)[2]) {
+                                          uint32_t (&uses)[WaveCfg<T, D, GENF>::NST]) {
     using C = WaveCfg<T, D, GENF>;
     constexpr int TE = C::TE, TD = C::TD, TC = C::TC, EPT = C::EPT, NACC = C::NACC;
     constexpr bool GEN = C::GEN;
@@ -732,15 +735,15 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
 #pragma unroll
         for (int q = 0; q < EPT; q++) acc[s][q] = T(0);
 
+    constexpr int NST = C::NST;
     if (tid == 0) {
         dev::fence_proxy_async();
-        if (njob > 0) issue(j0, 0);
-        if (njob > 1) issue(j0 + 1, 1);
+        for (int q = 0; q < NST && q < njob; q++) issue(j0 + q, q);
     }
     bool dead = false;
     for (int jj = 0; jj < njob && !dead; jj++) {
-        const int stg = jj & 1;
-        const bool ok = dev::mbar_wait(&bar[stg], (uses[stg] + static_cast<uint32_t>(jj >> 1)) & 1u, a.timeout_ns);
+        const int stg = jj % NST;
+        const bool ok = dev::mbar_wait(&bar[stg], (uses[stg] + static_cast<uint32_t>(jj / NST)) & 1u, a.timeout_ns);
         if (__syncthreads_or(!ok)) {
             dead = true;
             if (tid == 0) atomicOr(a.err, kErrTimeout);
@@ -750,18 +753,18 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         decode(j0 + jj, L, Jp);
         dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE);
         __syncthreads();
-        if (tid == 0 && jj + 2 < njob) {
+        if (tid == 0 && jj + NST < njob) {
             dev::fence_proxy_async();
-            issue(j0 + jj + 2, stg);
+            issue(j0 + jj + NST, stg);
         }
     }
     if (dead && tid == 0) {
         // let copies still in flight land before the buffers go away (bounded);
         // the block is finished with whatever it holds (the error word is set)
-        for (int jj = 0; jj < 2 && jj < njob; jj++) (void)dev::mbar_wait(&bar[jj], uses[jj] & 1u, a.timeout_ns / 8);
+        for (int q = 0; q < NST && q < njob; q++) (void)dev::mbar_wait(&bar[q], uses[q] & 1u, a.timeout_ns / 8);
     }
-    uses[0] += static_cast<uint32_t>((njob + 1) / 2);
-    uses[1] += static_cast<uint32_t>(njob / 2);
+#pragma unroll
+    for (int q = 0; q < NST; q++) uses[q] += static_cast<uint32_t>((njob - q + NST - 1) / NST);
 
     // ---- partial sums -> shared memory, cluster reduction into rank 0
 #pragma unroll
@@ -1060,12 +1063,11 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
     const int csize = a.csize;
     const int rank = csize > 1 ? static_cast<int>(dev::cluster_rank()) : 0;
     if (threadIdx.x == 0) {
-        dev::mbar_init(&bar[0], 1);
-        dev::mbar_init(&bar[1], 1);
+        for (int q = 0; q < C::NST; q++) dev::mbar_init(&bar[q], 1);
         dev::fence_mbar_init();
     }
     __syncthreads();
-    uint32_t uses[2] = {0u, 0u};
+    uint32_t uses[C::NST] = {};
     (void)wave_tile<T, D, GENF>(a, a.tiles[blockIdx.x / csize], rank, csize, uses);
 }
 

@@ -102,3 +102,26 @@ def test_refined_iteration_cap(ts):
                            max_refine=1, check=False, info=info)
     assert st == ts._lib.TSYLV_ENOCONV
     assert info.iterations == 1 and 1e-12 < info.resid < 1e-4
+
+
+@pytest.mark.parametrize("update", [0, 1])
+@pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("shape", [(24, 20, 16), (9, 7, 5, 6)])
+def test_reported_residual_is_the_true_one(ts, shape, gen, update):
+    """The residual the refinement reports (updated from the FP32 corrections
+    by default, re-evaluated at every step with resid_update = 1) is the true
+    residual of the returned X: equal to the oracle's up to the power-iteration
+    estimate of ||A|| (1e-2 relative) and the update's rounding (2e-15)."""
+    p = synthetic.problem(36, shape, generalized=gen, force_blocks=[[n // 2 - 1] for n in shape])
+    A = [to_dev(a) for a in p["A"]]
+    info = ts.Info()
+    if gen:
+        X, st = ts.gtsylv_solve(A, [to_dev(c) for c in p["C"]], to_dev(p["B"]), precision=ts.TSYLV_FP32_REFINED,
+                                resid_update=update, info=info)
+    else:
+        X, st = ts.tsylv_solve(A, to_dev(p["B"]), precision=ts.TSYLV_FP32_REFINED, resid_update=update, info=info)
+    assert st == 0 and info.iterations >= 2
+    Xg = to_host(X)
+    R = p["B"] - oracle.apply(p["A"], Xg, p["C"])
+    rho = np.linalg.norm(R) / (norm_op(p["A"], p["C"]) * np.linalg.norm(Xg))
+    assert abs(info.resid - rho) <= 2e-2 * rho + 2e-15
