@@ -65,6 +65,10 @@ cudaError_t prepare_apply();
 // residual update from its FP32 correction).
 cudaError_t launch_apply_f32(int d, const ApplyArgs& a, cudaStream_t s);
 cudaError_t prepare_apply_f32();
+// One launch of many applies of order d: CTA b computes block jobs[b].y of
+// the apply eqs[jobs[b].x] (device arrays).  mode: 0 FP64, 1 DF64, 2 FP32.
+cudaError_t launch_apply_batched(int d, int mode, const ApplyArgs* eqs, const int2* jobs, int njobs, cudaStream_t s);
+cudaError_t prepare_apply_batched();
 
 
 }  // namespace tsylv

@@ -187,17 +187,15 @@ __device__ __forceinline__ void dispatch(int mu, int kind, const unsigned char* 
     }
 }
 
+// Block t of one apply (one CTA, barriers freshly initialised by the caller).
 template <int D, int MD>
-__global__ void __launch_bounds__(kThreads) k_apply(const ApplyArgs a) {
+__device__ __forceinline__ void apply_tile(const ApplyArgs& a, const long long t, unsigned char* smem) {
     using C = ApplyCfg<D, MD>;
     constexpr bool DF = MD == kModeDF;
     constexpr int TE = C::TE, TD = C::TD, TC = C::TC, EPT = C::EPT;
-    extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::oBar);
     double* red = reinterpret_cast<double*>(smem + C::oRed);
     const int tid = threadIdx.x;
-    const long long t = blockIdx.x;
-    if (t >= a.ntiles) return;
     int I[D];
 #pragma unroll
     for (int mu = 0; mu < D; mu++) I[mu] = static_cast<int>((t / a.tstride[mu]) % a.nb[mu]);
@@ -284,12 +282,6 @@ __global__ void __launch_bounds__(kThreads) k_apply(const ApplyArgs a) {
 #pragma unroll
     for (int q = 0; q < EPT; q++) { y1[q] = y2[q] = 0.0; h1[q] = l1[q] = h2[q] = l2[q] = 0.f; }
     if (tid == 0) {
-        dev::mbar_init(&bar[0], 1);
-        dev::mbar_init(&bar[1], 1);
-        dev::fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
         if (njob > 0) issue(0, 0);
         if (njob > 1) issue(1, 1);
     }
@@ -362,6 +354,37 @@ __global__ void __launch_bounds__(kThreads) k_apply(const ApplyArgs a) {
 }
 
 template <int D, int MD>
+__device__ __forceinline__ void init_apply_barriers(unsigned char* smem) {
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + ApplyCfg<D, MD>::oBar);
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&bar[0], 1);
+        dev::mbar_init(&bar[1], 1);
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+template <int D, int MD>
+__global__ void __launch_bounds__(kThreads) k_apply(const ApplyArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (static_cast<long long>(blockIdx.x) >= a.ntiles) return;
+    init_apply_barriers<D, MD>(smem);
+    apply_tile<D, MD>(a, blockIdx.x, smem);
+}
+
+// Many independent applies in one launch: CTA b runs block jobs[b].y of the
+// apply eqs[jobs[b].x] (every CTA owns one block, as in k_apply).
+template <int D, int MD>
+__global__ void __launch_bounds__(kThreads) k_apply_batched(const ApplyArgs* __restrict__ eqs,
+                                                            const int2* __restrict__ jobs, int njobs) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (static_cast<int>(blockIdx.x) >= njobs) return;
+    const int2 jb = jobs[blockIdx.x];
+    init_apply_barriers<D, MD>(smem);
+    apply_tile<D, MD>(eqs[jb.x], jb.y, smem);
+}
+
+template <int D, int MD>
 cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t s) {
     using C = ApplyCfg<D, MD>;
     k_apply<D, MD><<<static_cast<unsigned>(a.ntiles), kThreads, C::smem, s>>>(a);
@@ -371,6 +394,20 @@ cudaError_t launch_apply_t(const ApplyArgs& a, cudaStream_t s) {
 template <int D, int MD>
 cudaError_t prepare_apply_t() {
     return cudaFuncSetAttribute(k_apply<D, MD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(ApplyCfg<D, MD>::smem));
+}
+
+template <int D, int MD>
+cudaError_t launch_apply_batched_t(const ApplyArgs* eqs, const int2* jobs, int njobs, cudaStream_t s) {
+    using C = ApplyCfg<D, MD>;
+    if (njobs <= 0) return cudaSuccess;
+    k_apply_batched<D, MD><<<static_cast<unsigned>(njobs), kThreads, C::smem, s>>>(eqs, jobs, njobs);
+    return cudaGetLastError();
+}
+
+template <int D, int MD>
+cudaError_t prepare_apply_batched_t() {
+    return cudaFuncSetAttribute(k_apply_batched<D, MD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(ApplyCfg<D, MD>::smem));
 }
 
@@ -408,6 +445,35 @@ cudaError_t prepare_apply() {
 
 cudaError_t launch_apply_f32(int d, const ApplyArgs& a, cudaStream_t s) { return launch_apply_m<kModeF32>(d, a, s); }
 cudaError_t prepare_apply_f32() { return prepare_apply_m<kModeF32>(); }
+
+cudaError_t launch_apply_batched(int d, int mode, const ApplyArgs* eqs, const int2* jobs, int njobs, cudaStream_t s) {
+#define TSYLV_APPLY_B(DD)                                                                          \
+    if (d == DD) {                                                                                 \
+        if (mode == kModeF64) return launch_apply_batched_t<DD, kModeF64>(eqs, jobs, njobs, s);   \
+        if (mode == kModeDF) return launch_apply_batched_t<DD, kModeDF>(eqs, jobs, njobs, s);     \
+        if (mode == kModeF32) return launch_apply_batched_t<DD, kModeF32>(eqs, jobs, njobs, s);   \
+    }
+    TSYLV_APPLY_B(1)
+    TSYLV_APPLY_B(2)
+    TSYLV_APPLY_B(3)
+    TSYLV_APPLY_B(4)
+#undef TSYLV_APPLY_B
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t prepare_apply_batched() {
+    cudaError_t e = cudaSuccess;
+#define TSYLV_PREP_B(DD)                                                                              \
+    if (e == cudaSuccess) e = prepare_apply_batched_t<DD, kModeF64>();                                \
+    if (e == cudaSuccess) e = prepare_apply_batched_t<DD, kModeDF>();                                 \
+    if (e == cudaSuccess) e = prepare_apply_batched_t<DD, kModeF32>();
+    TSYLV_PREP_B(1)
+    TSYLV_PREP_B(2)
+    TSYLV_PREP_B(3)
+    TSYLV_PREP_B(4)
+#undef TSYLV_PREP_B
+    return e;
+}
 
 template cudaError_t launch_apply<false>(int, const ApplyArgs&, cudaStream_t);
 template cudaError_t launch_apply<true>(int, const ApplyArgs&, cudaStream_t);

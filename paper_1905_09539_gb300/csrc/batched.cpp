@@ -8,14 +8,17 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <numeric>
 #include <vector>
 
+#include "apply_kernel.cuh"
 #include "batched.h"
 #include "plan.h"
+#include "refine.h"
 #include "solver.h"
 
 namespace tsylv {
@@ -55,6 +58,7 @@ struct BatchPlan {
     std::vector<int> seg_off, seg_cnt;      // per entry of dlist (same for every policy)
     std::vector<BatchCoefJob> cjobs;
     size_t data_bytes = 0;
+    std::vector<long long> tile_off;        // first global block of every equation (count + 1 entries)
     double flops = 0;
     int tuned_policy = -1, tuned_grid = 0;
     std::vector<BatchGraph> graphs;
@@ -297,8 +301,6 @@ std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t
         flags += static_cast<size_t>(ts);
         const size_t td = static_cast<size_t>(ipow(te, q.d)), tc = static_cast<size_t>(te) * te;
         const bool g = gen && q.d >= 2;
-        q.X = data;
-        data += al256(q.ntiles * td * elem);
         if (g)
             for (int l = 1; l < q.d; l++) {
                 q.P[l] = data;
@@ -319,6 +321,17 @@ std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t
         }
         p->flops += eq_flops(q, gen);
     }
+    // the block tensors of all equations form one pool, in equation order, one
+    // block after the other (pooled elementwise kernels index it by global block)
+    p->tile_off.assign(static_cast<size_t>(count) + 1, 0);
+    for (int e = 0; e < count; e++) {
+        EqPlan& q = p->eq[e];
+        const size_t td = static_cast<size_t>(ipow(tile_extent(q.d), q.d));
+        p->tile_off[e + 1] = p->tile_off[e] + q.ntiles;
+        q.X = data;
+        data += q.ntiles * td * elem;
+    }
+    data = al256(data);
     p->data_bytes = data;
     for (int e = 0; e < count; e++)
         if (std::find(p->dlist.begin(), p->dlist.end(), d[e]) == p->dlist.end()) p->dlist.push_back(d[e]);
@@ -414,16 +427,16 @@ struct Pinned {
 // by their synchronisation at the end).
 thread_local Pinned t_pin_tab, t_pin_small;
 
-int occupancy_cached(int d, bool gen) {
+int occupancy_cached(int d, bool gen, int elem = 8) {
     static std::mutex m;
     static std::map<int, int> cache;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int key = dev * 16 + d * 2 + (gen ? 1 : 0);
+    const int key = (dev * 16 + d * 2 + (gen ? 1 : 0)) * 2 + (elem == 4 ? 1 : 0);
     std::lock_guard<std::mutex> lk(m);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    const int o = batched_occupancy<double>(d, gen);
+    const int o = elem == 4 ? batched_occupancy<float>(d, gen) : batched_occupancy<double>(d, gen);
     cache[key] = o;
     return o;
 }
@@ -448,7 +461,10 @@ int prepare_batched_once() {
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(pm);
     if (dev >= 0 && dev < 64 && !prepared[dev]) {
-        if (cudaError_t e = prepare_batched<double>(); e != cudaSuccess) return cuda_fail(e, "batched kernel attributes");
+        cudaError_t e = prepare_batched<double>();
+        if (e == cudaSuccess) e = prepare_batched<float>();
+        if (e == cudaSuccess) e = prepare_apply_batched();
+        if (e != cudaSuccess) return cuda_fail(e, "batched kernel attributes");
         prepared[dev] = true;
     }
     return 0;
@@ -502,6 +518,43 @@ cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
     return cudaMemcpyAsync(c.herr, ctl + 8 + p.count, sizeof(int) * p.count, cudaMemcpyDeviceToHost, s);
 }
 
+// Capture (once per key) and launch a CUDA graph of `fn`, or run it eagerly.
+int run_graph(BatchPlan& plan, const std::vector<const void*>& key, bool use_graph, cudaStream_t stream,
+              const std::function<cudaError_t(cudaStream_t)>& fn, const char* what) {
+    cudaError_t e;
+    if (!use_graph) {
+        if ((e = fn(stream)) != cudaSuccess) return cuda_fail(e, what);
+        return 0;
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : plan.graphs)
+        if (g.key == key) exec = g.exec;
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        cudaStream_t cs = capture_stream();
+        if (!cs) return cuda_fail_msg("batched: capture stream");
+        if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(e, "batched: begin capture");
+        const cudaError_t ee = fn(cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(ee, what);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "batched: end capture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "batched: instantiate");
+        if (plan.graphs.size() >= 16) {
+            cudaGraphExecDestroy(plan.graphs.front().exec);
+            plan.graphs.erase(plan.graphs.begin());
+        }
+        plan.graphs.push_back({key, exec});
+    }
+    if ((e = cudaGraphLaunch(exec, stream)) != cudaSuccess) return cuda_fail(e, "batched: graph launch");
+    return 0;
+}
+
 // Same precedence as a single solve.
 int map_status(int e) {
     if (e & kErrBounds) return cuda_fail_msg("device self-check: index outside a block array");
@@ -511,49 +564,13 @@ int map_status(int e) {
     return TSYLV_OK;
 }
 
-}  // namespace
-
-size_t solver_batched_workspace_bytes(int count, const int* d, const int64_t* n_packed, bool gen,
-                                      const tsylv_opts& o) {
-    if (!shapes_ok(count, d, n_packed)) return 0;
-    if (o.precision != TSYLV_FP64) return 0;
-    const Bounds b = batch_bounds(count, d, n_packed, gen, 8);
-    const BatchLayout L = make_batch_layout(count, d, n_packed, gen, 8, b.jobs, b.cjobs, b.pints, b.data);
-    return L.total;
-}
-
-int solver_batched(int count, const int* d, const int64_t* n_packed, const int64_t* off_A, const int64_t* off_X,
-                   const double* A_pool, const double* C_pool, const double* B_pool, double* X_pool, void* work,
-                   size_t work_bytes, const tsylv_opts* opts, int* per_status, tsylv_info* info,
-                   cudaStream_t stream) {
-    tsylv_opts o;
-    if (opts) o = *opts; else tsylv_opts_default(&o);
-    if (count < 1) return -1;
-    if (!d) return -2;
-    if (!n_packed || !shapes_ok(count, d, n_packed)) return -3;
-    if (!off_A) return -4;
-    if (!off_X) return -5;
-    if (!A_pool) return -6;
-    const bool gen = C_pool != nullptr;
-    if (!B_pool) return -8;
-    if (!X_pool) return -9;
-    if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -10;
-    if (o.precision != TSYLV_FP64) return TSYLV_EUNSUPPORTED;
-    const size_t need = solver_batched_workspace_bytes(count, d, n_packed, gen, o);
-    if (!need || work_bytes < need) return -11;
-    if (o.split < 0 || o.partition < 0 || o.partition > 1) return -12;
+// The 2x2 structure of every A_mu (sub-diagonals gathered in one launch and
+// read back), validated; herr receives pinned room for the status words.
+int batch_structure(int count, const int* d, const int64_t* n_packed, const int64_t* off_A, const double* A_pool,
+                    char* base, const BatchLayout& L, int* per_status, cudaStream_t stream, std::vector<uint8_t>& sub,
+                    int*& herr) {
     size_t nmats = 0;
     for (int e = 0; e < count; e++) nmats += static_cast<size_t>(d[e]);
-    for (size_t k = 0; k < nmats; k++)
-        if (off_A[k] < 0) return -4;
-    for (int e = 0; e < count; e++)
-        if (off_X[e] < 0) return -5;
-    (void)cudaGetLastError();
-    char* base = static_cast<char*>(work);
-    const Bounds bd = batch_bounds(count, d, n_packed, gen, 8);
-    BatchLayout L = make_batch_layout(count, d, n_packed, gen, 8, bd.jobs, bd.cjobs, bd.pints, bd.data);
-
-    // ---- 2x2 structure of every A_mu (sub-diagonals gathered in one launch)
     std::vector<long long> aoff(nmats), nmat(nmats), ooff(nmats);
     long long maxn = 1;
     {
@@ -571,7 +588,7 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     if (!t_pin_small.reserve(small_bytes)) return cuda_fail_msg("batched: pinned host allocation");
     long long* hoffs = reinterpret_cast<long long*>(t_pin_small.ptr);
     double* hsub = reinterpret_cast<double*>(t_pin_small.ptr + 3 * nmats * sizeof(long long));
-    int* herr = reinterpret_cast<int*>(t_pin_small.ptr + 3 * nmats * sizeof(long long) + (L.nsub + 1) * sizeof(double));
+    herr = reinterpret_cast<int*>(t_pin_small.ptr + 3 * nmats * sizeof(long long) + (L.nsub + 1) * sizeof(double));
     std::memcpy(hoffs, aoff.data(), nmats * sizeof(long long));
     std::memcpy(hoffs + nmats, nmat.data(), nmats * sizeof(long long));
     std::memcpy(hoffs + 2 * nmats, ooff.data(), nmats * sizeof(long long));
@@ -595,7 +612,7 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
             return cuda_fail(e, "batched: read sub-diagonals");
     }
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "batched: synchronize before planning");
-    std::vector<uint8_t> sub(L.nsub + 1, 0);
+    sub.assign(L.nsub + 1, 0);
     {
         size_t k = 0, so = 0;
         for (int q = 0; q < count; q++)
@@ -611,6 +628,428 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
                 so += static_cast<size_t>(m - 1);
             }
     }
+
+    return 0;
+}
+
+
+// ------------------------------------------------ batched mixed-precision refinement
+//
+// All equations of one order d (the pooled elementwise kernels need one block
+// size).  FP32 side: the batch plan with 4-byte entries (block tensors pooled,
+// FP32 coefficient tiles, the persistent FP32 solve).  FP64 side, after it in
+// the workspace: pooled B, X, R block tensors, FP64 coefficient tiles, the
+// Horner intermediates of the generalized residual, block and equation norms.
+struct RefExtra {
+    size_t Bt = 0, Xt = 0, Rt = 0, set[2][2] = {}, part = 0, xpart = 0, nrm = 0, nA = 0;
+    size_t tab = 0, tab_bytes = 0;  // geo64, geoX, args[2][4][count], ajobs, tile_eq, tile_off, norm tables
+    size_t o_geo64 = 0, o_geoX = 0, o_args = 0, o_ajobs = 0, o_teq = 0, o_toff = 0, o_noff = 0, o_nn = 0, o_nup = 0;
+    size_t coef = 0;                 // FP64 coefficient tiles
+    size_t total = 0;
+};
+
+RefExtra make_ref_extra(size_t start, int count, int d, bool gen, long long tiles, long long ctiles, int nmats) {
+    RefExtra E;
+    const int te = tile_extent(d);
+    const size_t td = static_cast<size_t>(ipow(te, d)), tc = static_cast<size_t>(te) * te;
+    const bool g = gen && d >= 2;
+    size_t o = al256(start);
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = al256(o + bytes);
+        return at;
+    };
+    E.Bt = take(tiles * td * 8);
+    E.Xt = take(tiles * td * 8);
+    E.Rt = take(tiles * td * 8);
+    if (g)
+        for (int k = 0; k < 2; k++)
+            for (int j = 0; j < 2; j++) E.set[k][j] = take(tiles * td * 8);
+    E.part = take(tiles * 2 * 8);
+    E.xpart = take(tiles * 8);
+    E.nrm = take(static_cast<size_t>(count) * 4 * 8);
+    E.nA = take(static_cast<size_t>(nmats) * 8);
+    E.coef = take(static_cast<size_t>(ctiles) * tc * 8 * (g ? 2 : 1) + static_cast<size_t>(count) * d * 2 * 256);
+    size_t t = 0;
+    auto tt = [&](size_t bytes) {
+        const size_t at = t;
+        t = al256(t + bytes);
+        return at;
+    };
+    E.o_geo64 = tt(count * sizeof(BatchGeom));
+    E.o_geoX = tt(count * sizeof(BatchGeom));
+    E.o_args = tt(static_cast<size_t>(2) * kMaxD * count * sizeof(ApplyArgs));
+    E.o_ajobs = tt(tiles * sizeof(int2));
+    E.o_teq = tt(tiles * sizeof(int));
+    E.o_toff = tt((count + 1) * sizeof(long long));
+    E.o_noff = tt(static_cast<size_t>(nmats) * sizeof(long long));
+    E.o_nn = tt(static_cast<size_t>(nmats) * sizeof(long long));
+    E.o_nup = tt(static_cast<size_t>(nmats) * sizeof(int));
+    E.tab_bytes = t;
+    E.tab = take(t);
+    E.total = o;
+    return E;
+}
+
+bool uniform_order(int count, const int* d) {
+    for (int e = 1; e < count; e++)
+        if (d[e] != d[0]) return false;
+    return true;
+}
+
+size_t refined_workspace_bytes(int count, const int* d, const int64_t* n_packed, bool gen) {
+    const Bounds b = batch_bounds(count, d, n_packed, gen, 4);
+    const BatchLayout L = make_batch_layout(count, d, n_packed, gen, 4, b.jobs, b.cjobs, b.pints, b.data);
+    int nm = 0;
+    for (int e = 0; e < count; e++) nm += d[e] * (gen ? 2 : 1);
+    return make_ref_extra(L.total, count, d[0], gen, b.jobs, b.cjobs, nm).total;
+}
+
+thread_local Pinned t_pin_nrm;
+
+int solver_batched_refined(int count, const int* d, const int64_t* n_packed, const int64_t* off_A,
+                           const int64_t* off_X, const double* A_pool, const double* C_pool, const double* B_pool,
+                           double* X_pool, char* base, size_t work_bytes, const tsylv_opts& o,
+                           const std::vector<uint8_t>& sub, int* herr, int* per_status, tsylv_info* info,
+                           cudaStream_t stream) {
+    const bool gen = C_pool != nullptr;
+    const int dd = d[0];
+    const bool g = gen && dd >= 2;
+    const int te = tile_extent(dd), td = ipow(te, dd), tc = te * te;
+    const Bounds bd = batch_bounds(count, d, n_packed, gen, 4);
+    const BatchLayout L = make_batch_layout(count, d, n_packed, gen, 4, bd.jobs, bd.cjobs, bd.pints, bd.data);
+    const int nmA = count * dd, nm = nmA * (gen ? 2 : 1);
+    std::shared_ptr<BatchPlan> plan = get_batch_plan(count, d, n_packed, gen, 4, sub, o.partition == 1 ? 1 : 0);
+    if (!plan) return cuda_fail_msg("batched: plan");
+    if (plan->data_bytes > bd.data) return cuda_fail_msg("batched: workspace bound");
+    const long long T = plan->tile_off[count];
+    long long ctiles = 0;
+    for (const EqPlan& q : plan->eq)
+        for (int mu = 0; mu < q.d; mu++) ctiles += static_cast<long long>(q.nb[mu]) * (q.nb[mu] + 1) / 2;
+    const RefExtra E = make_ref_extra(L.total, count, dd, gen, bd.jobs, bd.cjobs, nm);
+    if (E.total > work_bytes) return -11;
+    if (int st = prepare_batched_once()) return st;
+
+    // ---- host tables: the FP32 solve's (as a plain batched solve), then the FP64 side's
+    std::vector<unsigned char> tabv;
+    const int policy = plan->tuned_policy >= 0 ? plan->tuned_policy : 0;
+    fill_table(*plan, L, base, policy, tabv, off_A, off_X);
+    std::vector<unsigned char> xt(E.tab_bytes, 0);
+    BatchGeom* g64 = reinterpret_cast<BatchGeom*>(xt.data() + E.o_geo64);
+    BatchGeom* gX = reinterpret_cast<BatchGeom*>(xt.data() + E.o_geoX);
+    ApplyArgs* args = reinterpret_cast<ApplyArgs*>(xt.data() + E.o_args);  // [mode 0 full, 1 update][level][eq]
+    int2* ajobs = reinterpret_cast<int2*>(xt.data() + E.o_ajobs);
+    int* teq = reinterpret_cast<int*>(xt.data() + E.o_teq);
+    long long* toff = reinterpret_cast<long long*>(xt.data() + E.o_toff);
+    long long* noff = reinterpret_cast<long long*>(xt.data() + E.o_noff);
+    long long* nn = reinterpret_cast<long long*>(xt.data() + E.o_nn);
+    int* nup = reinterpret_cast<int*>(xt.data() + E.o_nup);
+    const BatchGeom* g32 = reinterpret_cast<const BatchGeom*>(tabv.data() + L.o_geom);
+    const WaveArgs* w32 = reinterpret_cast<const WaveArgs*>(tabv.data() + L.o_wave);
+    char* dt = base + E.tab;
+    double* Bt = reinterpret_cast<double*>(base + E.Bt);
+    double* Xt = reinterpret_cast<double*>(base + E.Xt);
+    double* Rt = reinterpret_cast<double*>(base + E.Rt);
+    double* part = reinterpret_cast<double*>(base + E.part);
+    double* xpart = reinterpret_cast<double*>(base + E.xpart);
+    double* nrm = reinterpret_cast<double*>(base + E.nrm);
+    double* nA = reinterpret_cast<double*>(base + E.nA);
+    int* errs = reinterpret_cast<int*>(base + L.ctl) + 8 + count;
+    size_t coff = E.coef;
+    size_t k = 0;
+    for (int e = 0; e < count; e++) {
+        const EqPlan& q = plan->eq[e];
+        const long long t0 = plan->tile_off[e];
+        toff[e] = t0;
+        for (long long t = 0; t < q.ntiles; t++) {
+            ajobs[t0 + t] = make_int2(e, static_cast<int>(t));
+            teq[t0 + t] = e;
+        }
+        BatchGeom a = g32[e];
+        a.X = Bt + t0 * td;
+        for (int mu = 0; mu < dd; mu++, k++) {
+            const size_t bytes = static_cast<size_t>(q.nb[mu]) * (q.nb[mu] + 1) / 2 * tc * 8;
+            a.At[mu] = base + coff;
+            coff = al256(coff + bytes);
+            a.Ct[mu] = nullptr;
+            if (g) {
+                a.Ct[mu] = base + coff;
+                coff = al256(coff + bytes);
+            }
+            noff[e * dd + mu] = off_A[k];
+            nn[e * dd + mu] = q.n[mu];
+            nup[e * dd + mu] = 0;
+            if (gen) {
+                noff[nmA + e * dd + mu] = off_A[k];
+                nn[nmA + e * dd + mu] = q.n[mu];
+                nup[nmA + e * dd + mu] = 1;
+            }
+        }
+        g64[e] = a;
+        BatchGeom x = a;
+        x.X = Xt + t0 * td;
+        gX[e] = x;
+        // residual applies: [0] full FP64 R = B - A(X), [1] FP32 update R -= s A(D)
+        for (int mode = 0; mode < 2; mode++) {
+            const int levels = g ? dd : 1;
+            int cur = 0;
+            for (int lv = 0; lv < levels; lv++) {
+                ApplyArgs r{};
+                for (int mu = 0; mu < dd; mu++) {
+                    r.nb[mu] = q.nb[mu];
+                    r.tstride[mu] = q.tstride[mu];
+                    r.A[mu] = mode == 0 ? a.At[mu] : w32[e].At[mu];
+                    r.C[mu] = g ? (mode == 0 ? a.Ct[mu] : w32[e].Ct[mu]) : nullptr;
+                }
+                r.ntiles = q.ntiles;
+                r.B = mode == 0 ? Bt + t0 * td : Rt + t0 * td;
+                r.R = Rt + t0 * td;
+                r.scale = mode == 0 ? nullptr : nrm + 4 * e;
+                r.part = part + 2 * t0;
+                r.err = errs + e;
+                r.timeout_ns = kTimeoutNs;
+                const void* xs = mode == 0 ? static_cast<const void*>(Xt + t0 * td) : w32[e].X;
+                auto setp = [&](int kk, int j) -> void* {
+                    return base + E.set[kk][j] + static_cast<size_t>(t0) * td * 8;
+                };
+                if (!g) {
+                    r.kind = kApplyLaplace;
+                    r.s1 = xs;
+                } else if (lv == 0) {
+                    r.kind = kApplyFirst;
+                    r.mode = dd - 1;
+                    r.s1 = xs;
+                    r.o1 = setp(0, 0);
+                    r.o2 = setp(0, 1);
+                    cur = 0;
+                } else {
+                    const int l = dd - 1 - lv;  // mode of this level
+                    r.kind = l == 0 ? kApplyFinal : kApplyMiddle;
+                    r.mode = l;
+                    r.s1 = setp(cur, 0);
+                    r.s2 = setp(cur, 1);
+                    r.o1 = setp(1 - cur, 0);
+                    r.o2 = setp(1 - cur, 1);
+                    cur = 1 - cur;
+                }
+                args[(static_cast<size_t>(mode) * kMaxD + lv) * count + e] = r;
+            }
+        }
+    }
+    toff[count] = T;
+    const size_t tab_all = L.tab_bytes + E.tab_bytes;
+    if (!t_pin_tab.reserve(tab_all)) return cuda_fail_msg("batched: pinned host allocation");
+    std::memcpy(t_pin_tab.ptr, tabv.data(), L.tab_bytes);
+    std::memcpy(t_pin_tab.ptr + L.tab_bytes, xt.data(), E.tab_bytes);
+    if (!t_pin_nrm.reserve(static_cast<size_t>(count) * 4 * 8 + static_cast<size_t>(nm) * 8))
+        return cuda_fail_msg("batched: pinned host allocation");
+    double* hn = reinterpret_cast<double*>(t_pin_nrm.ptr);
+    double* hA = hn + 4 * count;
+
+    int per_sm = o.split > 0 ? o.split : occupancy_cached(dd, gen, 4);
+    per_sm = std::max(1, std::min(per_sm, occupancy_cached(dd, gen, 4)));
+    int grid = per_sm * sm_count();
+    if (grid > T) grid = static_cast<int>(T);
+    if (grid < 1) grid = 1;
+    char* tab32 = base + L.tab;
+    const BatchGeom* dgeo32 = reinterpret_cast<const BatchGeom*>(tab32 + L.o_geom);
+    const BatchJob* djobs = reinterpret_cast<const BatchJob*>(tab32 + L.o_jobs);
+    const BatchCoefJob* dcjobs = reinterpret_cast<const BatchCoefJob*>(tab32 + L.o_cjobs);
+    const BatchGeom* dgeo64 = reinterpret_cast<const BatchGeom*>(dt + E.o_geo64);
+    const BatchGeom* dgeoX = reinterpret_cast<const BatchGeom*>(dt + E.o_geoX);
+    const ApplyArgs* dargs = reinterpret_cast<const ApplyArgs*>(dt + E.o_args);
+    const int2* dajobs = reinterpret_cast<const int2*>(dt + E.o_ajobs);
+    const int* dteq = reinterpret_cast<const int*>(dt + E.o_teq);
+    const long long* dtoff = reinterpret_cast<const long long*>(dt + E.o_toff);
+    const long long* dnoff = reinterpret_cast<const long long*>(dt + E.o_noff);
+    const long long* dnn = reinterpret_cast<const long long*>(dt + E.o_nn);
+    const int* dnup = reinterpret_cast<const int*>(dt + E.o_nup);
+    int* ctl = reinterpret_cast<int*>(base + L.ctl);
+    const int njobs = static_cast<int>(plan->jobs[0].size());
+    const int ncj = static_cast<int>(plan->cjobs.size());
+    long long nmax = 1;
+    for (int q = 0; q < nm; q++) nmax = std::max(nmax, nn[q]);
+    float* X32 = static_cast<float*>(w32[0].X);  // the pooled FP32 block tensors start with equation 0
+
+#define TRYB(x)                               \
+    do {                                      \
+        cudaError_t e_ = (x);                 \
+        if (e_ != cudaSuccess) return e_;     \
+    } while (0)
+    auto setup = [&](cudaStream_t s) -> cudaError_t {
+        TRYB(cudaMemsetAsync(ctl, 0, (8 + 2 * static_cast<size_t>(count)) * sizeof(int), s));
+        TRYB(cudaMemcpyAsync(tab32, t_pin_tab.ptr, L.tab_bytes, cudaMemcpyHostToDevice, s));
+        TRYB(cudaMemcpyAsync(dt, t_pin_tab.ptr + L.tab_bytes, E.tab_bytes, cudaMemcpyHostToDevice, s));
+        TRYB(launch_batch_pack<float>(dgeo32, djobs, 0, dcjobs, ncj, nullptr, A_pool, C_pool, s));
+        TRYB(launch_batch_pack<double>(dgeo64, djobs, njobs, dcjobs, ncj, B_pool, A_pool, C_pool, s));
+        TRYB(cudaMemsetAsync(Xt, 0, static_cast<size_t>(T) * td * 8, s));
+        TRYB(cudaMemcpyAsync(Rt, Bt, static_cast<size_t>(T) * td * 8, cudaMemcpyDeviceToDevice, s));
+        TRYB(launch_tile_stats(Rt, part, T, td, s));
+        TRYB(launch_breduce(part, nullptr, dtoff, count, nrm, s));
+        TRYB(launch_bnorm2(A_pool, dnoff, dnn, dnup, nmA, nmax, nA, s));
+        if (gen) TRYB(launch_bnorm2(C_pool, dnoff + nmA, dnn + nmA, dnup + nmA, nmA, nmax, nA + nmA, s));
+        TRYB(cudaMemcpyAsync(hn, nrm, static_cast<size_t>(count) * 4 * 8, cudaMemcpyDeviceToHost, s));
+        return cudaMemcpyAsync(hA, nA, static_cast<size_t>(nm) * 8, cudaMemcpyDeviceToHost, s);
+    };
+    auto iterate = [&](bool update, cudaStream_t s) -> cudaError_t {
+        TRYB(launch_bscale(Rt, X32, dteq, nrm, T * td, td, s));
+        TRYB(cudaMemsetAsync(ctl, 0, 8 * sizeof(int) + static_cast<size_t>(count) * sizeof(int), s));
+        TRYB(cudaMemsetAsync(base + L.flags, 0, static_cast<size_t>(T) * sizeof(int), s));
+        BatchArgs ba{};
+        ba.eqs = reinterpret_cast<const WaveArgs*>(tab32 + L.o_wave);
+        ba.jobs = djobs;
+        ba.njobs = njobs;
+        ba.head = ctl;
+        ba.abort = ctl + 4;
+        ba.done = ctl + 8;
+        ba.timeout_ns = kTimeoutNs;
+        TRYB(launch_batched<float>(dd, gen, ba, grid, s));
+        TRYB(launch_bupdate(Xt, X32, dteq, nrm, xpart, T, td, s));
+        const int levels = g ? dd : 1;
+        const int mode = update ? 1 : 0;
+        for (int lv = 0; lv < levels; lv++)
+            TRYB(launch_apply_batched(dd, update ? 2 : 0, dargs + (static_cast<size_t>(mode) * kMaxD + lv) * count,
+                                      dajobs, static_cast<int>(T), s));
+        TRYB(launch_breduce(part, xpart, dtoff, count, nrm, s));
+        return cudaMemcpyAsync(hn, nrm, static_cast<size_t>(count) * 4 * 8, cudaMemcpyDeviceToHost, s);
+    };
+    auto finish = [&](cudaStream_t s) -> cudaError_t {
+        TRYB(launch_batch_unpack<double>(dgeoX, djobs, njobs, X_pool, s));
+        return cudaMemcpyAsync(herr, errs, sizeof(int) * count, cudaMemcpyDeviceToHost, s);
+    };
+#undef TRYB
+
+    std::vector<const void*> kb = {base, A_pool, C_pool, B_pool, X_pool, t_pin_tab.ptr, t_pin_nrm.ptr, herr,
+                                   reinterpret_cast<const void*>(static_cast<uintptr_t>(per_sm))};
+    auto key = [&](int tag) {
+        std::vector<const void*> kk = kb;
+        kk.push_back(reinterpret_cast<const void*>(static_cast<uintptr_t>(1000 + tag)));
+        return kk;
+    };
+    const bool ug = o.use_graph != 0;
+    if (int st = run_graph(*plan, key(0), ug, stream, setup, "batched refinement: set-up")) return st;
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "batched refinement: synchronize");
+    std::vector<double> normA(count, 0.0), rho(count, -1.0);
+    for (int q = 0; q < count; q++) {
+        double s = 0;
+        for (int mu = 0; mu < dd; mu++) {
+            double t = hA[q * dd + mu];
+            if (gen)
+                for (int eta = 0; eta < dd; eta++)
+                    if (eta != mu) t *= hA[nmA + q * dd + eta];
+            s += t;
+        }
+        normA[q] = s;
+    }
+    std::vector<char> zero(count, 0);
+    for (int q = 0; q < count; q++) zero[q] = !(hn[4 * q + 1] > 0);
+    int iters = 0, stall = 0;
+    double prev = HUGE_VAL, worst = 0;
+    bool update = false;
+    for (int it = 0; it < std::max(1, o.max_refine); it++) {
+        if (o.resid_update == 0 && it > 0 && prev <= 1e-5) update = true;
+        if (int st = run_graph(*plan, key(update ? 2 : 1), ug, stream,
+                               [&](cudaStream_t s) { return iterate(update, s); }, "batched refinement: step"))
+            return st;
+        if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "batched refinement: synchronize");
+        iters = it + 1;
+        worst = 0;
+        bool bad = false;
+        for (int q = 0; q < count; q++) {
+            const double xn = std::sqrt(hn[4 * q + 2]);
+            rho[q] = zero[q] ? 0.0 : (xn > 0 && normA[q] > 0 ? std::sqrt(hn[4 * q]) / (normA[q] * xn) : 0.0);
+            if (!std::isfinite(rho[q])) bad = true;
+            worst = std::max(worst, rho[q]);
+        }
+        if (bad || worst <= o.tol) break;
+        if (worst > 0.5 * prev) {
+            if (++stall >= 2) break;
+        } else {
+            stall = 0;
+        }
+        prev = worst;
+    }
+    if (int st = run_graph(*plan, key(3), ug, stream, finish, "batched refinement: unpack")) return st;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "batched refinement: synchronize");
+    int status = TSYLV_OK;
+    for (int q = 0; q < count; q++) {
+        int s = map_status(herr[q]);
+        if (s == TSYLV_OK && !std::isfinite(rho[q])) s = TSYLV_ENONFINITE;
+        if (s == TSYLV_OK && !(rho[q] <= o.tol)) s = TSYLV_ENOCONV;
+        if (per_status) per_status[q] = s;
+        if (status == TSYLV_OK && s != TSYLV_OK) status = s;
+    }
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        int waves = 0;
+        for (const EqPlan& q : plan->eq) waves = std::max(waves, q.nwaves);
+        info->iterations = iters;
+        info->waves = waves;
+        info->launches = 6 + (gen ? 2 : 1) + iters * (4 + (g ? dd : 1)) + 1;
+        info->tiles = static_cast<int>(T);
+        info->resid = worst;
+        info->norm_A = -1;
+        info->flops = plan->flops * iters;
+        info->batch_order = policy;
+        info->batch_ctas_per_sm = per_sm;
+    }
+    (void)ctiles;
+    return status;
+}
+}  // namespace
+
+size_t solver_batched_workspace_bytes(int count, const int* d, const int64_t* n_packed, bool gen,
+                                      const tsylv_opts& o) {
+    if (!shapes_ok(count, d, n_packed)) return 0;
+    if (o.precision == TSYLV_FP32_REFINED) return uniform_order(count, d) ? refined_workspace_bytes(count, d, n_packed, gen) : 0;
+    if (o.precision != TSYLV_FP64) return 0;
+    const Bounds b = batch_bounds(count, d, n_packed, gen, 8);
+    const BatchLayout L = make_batch_layout(count, d, n_packed, gen, 8, b.jobs, b.cjobs, b.pints, b.data);
+    return L.total;
+}
+
+int solver_batched(int count, const int* d, const int64_t* n_packed, const int64_t* off_A, const int64_t* off_X,
+                   const double* A_pool, const double* C_pool, const double* B_pool, double* X_pool, void* work,
+                   size_t work_bytes, const tsylv_opts* opts, int* per_status, tsylv_info* info,
+                   cudaStream_t stream) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    if (count < 1) return -1;
+    if (!d) return -2;
+    if (!n_packed || !shapes_ok(count, d, n_packed)) return -3;
+    if (!off_A) return -4;
+    if (!off_X) return -5;
+    if (!A_pool) return -6;
+    const bool gen = C_pool != nullptr;
+    if (!B_pool) return -8;
+    if (!X_pool) return -9;
+    if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -10;
+    if (o.precision != TSYLV_FP64 && o.precision != TSYLV_FP32_REFINED) return TSYLV_EUNSUPPORTED;
+    const bool refined = o.precision == TSYLV_FP32_REFINED;
+    if (refined && !uniform_order(count, d)) return TSYLV_EUNSUPPORTED;
+    const size_t need = solver_batched_workspace_bytes(count, d, n_packed, gen, o);
+    if (!need || work_bytes < need) return -11;
+    if (o.split < 0 || o.partition < 0 || o.partition > 1) return -12;
+    size_t nmats = 0;
+    for (int e = 0; e < count; e++) nmats += static_cast<size_t>(d[e]);
+    for (size_t k = 0; k < nmats; k++)
+        if (off_A[k] < 0) return -4;
+    for (int e = 0; e < count; e++)
+        if (off_X[e] < 0) return -5;
+    (void)cudaGetLastError();
+    char* base = static_cast<char*>(work);
+    const int elem = refined ? 4 : 8;
+    const Bounds bd = batch_bounds(count, d, n_packed, gen, elem);
+    BatchLayout L = make_batch_layout(count, d, n_packed, gen, elem, bd.jobs, bd.cjobs, bd.pints, bd.data);
+
+    std::vector<uint8_t> sub;
+    int* herr = nullptr;
+    if (int st = batch_structure(count, d, n_packed, off_A, A_pool, base, L, per_status, stream, sub, herr)) return st;
+    if (refined)
+        return solver_batched_refined(count, d, n_packed, off_A, off_X, A_pool, C_pool, B_pool, X_pool, base,
+                                      work_bytes, o, sub, herr, per_status, info, stream);
+    cudaError_t e;
 
     // ---- plan (cached per shapes and structure), tables, launch
     std::shared_ptr<BatchPlan> plan = get_batch_plan(count, d, n_packed, gen, 8, sub, o.partition == 1 ? 1 : 0);

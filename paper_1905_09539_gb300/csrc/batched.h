@@ -79,4 +79,15 @@ cudaError_t launch_batch_unpack(const BatchGeom* g, const BatchJob* jobs, int nj
 cudaError_t launch_batch_subdiag(const long long* aoff, const long long* nmat, const long long* ooff, int nmats,
                                  long long maxn, const double* A, double* out, cudaStream_t s);
 
+// Batched refinement (pools of all equations; tile_eq maps a block to its
+// equation, nrm holds 4 doubles per equation: sum r^2, max |r|, sum x^2).
+cudaError_t launch_bscale(const double* r, float* r32, const int* tile_eq, const double* nrm, long long n, int td,
+                          cudaStream_t s);
+cudaError_t launch_bupdate(double* x, const float* d32, const int* tile_eq, const double* nrm, double* xpart,
+                           long long ntiles, int td, cudaStream_t s);
+cudaError_t launch_breduce(const double* part, const double* xpart, const long long* tile_off, int count, double* nrm,
+                           cudaStream_t s);
+cudaError_t launch_bnorm2(const double* pool, const long long* off, const long long* nmat, const int* upper, int count,
+                          long long nmax, double* out, cudaStream_t s);
+
 }  // namespace tsylv

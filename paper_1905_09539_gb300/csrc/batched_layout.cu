@@ -205,5 +205,7 @@ template cudaError_t prepare_batched<float>();
 template cudaError_t launch_batch_pack<double>(const BatchGeom*, const BatchJob*, int, const BatchCoefJob*, int,
                                                const double*, const double*, const double*, cudaStream_t);
 template cudaError_t launch_batch_unpack<double>(const BatchGeom*, const BatchJob*, int, double*, cudaStream_t);
+template cudaError_t launch_batch_pack<float>(const BatchGeom*, const BatchJob*, int, const BatchCoefJob*, int,
+                                              const double*, const double*, const double*, cudaStream_t);
 
 }  // namespace tsylv

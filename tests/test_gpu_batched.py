@@ -132,3 +132,41 @@ def test_batch_workload_512(lib, gen):
         p = ps[int(i)]
         Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
         assert rel_err(to_host(Xs[int(i)]), Xo) <= 1e-11
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_batch_refined_small(lib, gen):
+    """FP32-refined batch: every equation reaches rel. residual <= 1e-12 and
+    matches the oracle to 1e-10 (the refinement's accuracy, not FP64 parity)."""
+    ps = synthetic.batch(12, count=20, lo=8, hi=24)
+    ps = [synthetic.problem([12, 200 + i], p["shape"], generalized=gen,
+                            force_blocks=[[n // 2 - 1] for n in p["shape"]] if i % 4 == 0 else None)
+          for i, p in enumerate(ps)]
+    prs = _problems(ps, gen)
+    info = lib.Info()
+    Xs, st = lib.tsylv_solve_batched(prs, generalized=gen, precision=lib.TSYLV_FP32_REFINED, info=info)
+    assert all(s == 0 for s in st)
+    assert 2 <= info.iterations <= 4 and info.resid <= 1e-12
+    for p, X in zip(ps, Xs):
+        Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+        assert rel_err(to_host(X), Xo) <= 1e-10
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_batch_refined_workload_512(lib, gen):
+    ps = synthetic.batch(0, count=512, generalized=gen)
+    prs = _problems(ps, gen)
+    X64, st64 = lib.tsylv_solve_batched(prs, generalized=gen)
+    info = lib.Info()
+    X32, st32 = lib.tsylv_solve_batched(prs, generalized=gen, precision=lib.TSYLV_FP32_REFINED, info=info)
+    assert all(s == 0 for s in st64) and all(s == 0 for s in st32)
+    assert info.resid <= 1e-12
+    worst = max(rel_err(to_host(a), to_host(b)) for a, b in zip(X32, X64))
+    assert worst <= 1e-10, worst
+
+
+def test_batch_refined_mixed_orders_unsupported(lib):
+    shapes = [(9, 8, 7), (5, 6)]
+    ps = [synthetic.problem([13, i], s) for i, s in enumerate(shapes)]
+    with pytest.raises((lib.TsylvError, ValueError)):
+        lib.tsylv_solve_batched(_problems(ps, False), precision=lib.TSYLV_FP32_REFINED)

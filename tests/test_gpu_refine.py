@@ -111,7 +111,8 @@ def test_reported_residual_is_the_true_one(ts, shape, gen, update):
     """The residual the refinement reports (updated from the FP32 corrections
     by default, re-evaluated at every step with resid_update = 1) is the true
     residual of the returned X: equal to the oracle's up to the power-iteration
-    estimate of ||A|| (1e-2 relative) and the update's rounding (2e-15)."""
+    estimate of ||A|| (2e-2 relative) and the rounding of the residual itself
+    (1e-14: DF64 evaluation, 2^-48 per operation, or the FP32 update)."""
     p = synthetic.problem(36, shape, generalized=gen, force_blocks=[[n // 2 - 1] for n in shape])
     A = [to_dev(a) for a in p["A"]]
     info = ts.Info()
@@ -124,4 +125,4 @@ def test_reported_residual_is_the_true_one(ts, shape, gen, update):
     Xg = to_host(X)
     R = p["B"] - oracle.apply(p["A"], Xg, p["C"])
     rho = np.linalg.norm(R) / (norm_op(p["A"], p["C"]) * np.linalg.norm(Xg))
-    assert abs(info.resid - rho) <= 2e-2 * rho + 2e-15
+    assert abs(info.resid - rho) <= 2e-2 * rho + 1e-14

@@ -114,7 +114,12 @@ def test_batched_workspace_and_validation(lib):
     bad = (ctypes.c_int64 * 8)(8, 48, 0, 33, 9, 17, 40, 40)
     assert lib.tsylv_batched_workspace_bytes(count, d, bad, 0, ctypes.byref(o)) == 0
     o32 = _lib.default_opts(precision=_lib.TSYLV_FP32_REFINED)
+    # the refined batch needs one order d for all equations
     assert lib.tsylv_batched_workspace_bytes(count, d, n, 0, ctypes.byref(o32)) == 0
+    d3 = (ctypes.c_int * 2)(3, 3)
+    n3 = (ctypes.c_int64 * 6)(8, 48, 20, 33, 9, 17)
+    assert lib.tsylv_batched_workspace_bytes(2, d3, n3, 0, ctypes.byref(o32)) > \
+        lib.tsylv_batched_workspace_bytes(2, d3, n3, 0, ctypes.byref(o))
     P = ctypes.c_void_p
     offA = (ctypes.c_int64 * 8)(*range(8))
     offX = (ctypes.c_int64 * 3)(0, 1, 2)
