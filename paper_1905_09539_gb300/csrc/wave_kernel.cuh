@@ -53,8 +53,12 @@ struct WaveCfg {
     static constexpr size_t oMeta = oBar + ((8 * NST + 15) / 16) * 16;
     // meta: gs, gl, gidx [D][TE]; ng, bs [D]; flag [4]; coupled-group lists
     static constexpr int MAXSTEP = D * TE;
-    static constexpr size_t smem =
+    static constexpr size_t oJob =
         oMeta + (3 * D * TE + 3 * D + 4 + 3 * MAXSTEP + 1 + 2 * (TD / 2 + 1) + 3 * MAXSTEP + 1 + TD) * sizeof(int);
+    // decoded jobs (level << 24 | source block) and "source solved" bits of the
+    // first JT jobs of a block, filled by all threads at once
+    static constexpr int JT = kThreads;
+    static constexpr size_t smem = oJob + (JT + JT / 32) * sizeof(int);
     static constexpr int slotP(int l) { return 2 * (D - 1 - l); }
     static constexpr int slotG(int l) { return 2 * (D - 1 - l) + 1; }
 };
@@ -692,9 +696,21 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         const int mu = GEN ? D - 1 - L : L;
         Jp = I[mu] + lo;
     };
+    int* jtab = reinterpret_cast<int*>(smem_raw + C::oJob);
+    unsigned* jready = reinterpret_cast<unsigned*>(jtab + C::JT);
+    auto job = [&](int j, int& L, int& Jp) {
+        const int r = j - j0;
+        if (r < C::JT) {
+            const int v = jtab[r];
+            L = v >> 24;
+            Jp = v & 0xffffff;
+        } else {
+            decode(j, L, Jp);
+        }
+    };
     auto issue = [&](int j, int stg) {
         int L, Jp;
-        decode(j, L, Jp);
+        job(j, L, Jp);
         const int mu = GEN ? D - 1 - L : L;
         const long long ts = t + static_cast<long long>(Jp - I[mu]) * a.tstride[mu];
         const long long tri = static_cast<long long>(Jp) * (Jp + 1) / 2 + I[mu];
@@ -716,7 +732,8 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             M1 = static_cast<const T*>(a.Ct[mu]) + tri * TC;
             M2 = static_cast<const T*>(a.At[mu]) + tri * TC;
         }
-        if (a.ready) {
+        const int r = j - j0;
+        if (a.ready && !(r < C::JT && ((jready[r >> 5] >> (r & 31)) & 1u))) {
             // persistent launch: the source block must be solved (bounded wait)
             if (!dev::wait_at_least(a.ready + ts, 1, a.abort, a.timeout_ns)) atomicOr(a.err, kErrTimeout);
             dev::fence_proxy_async_all();
@@ -736,8 +753,26 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         for (int q = 0; q < EPT; q++) acc[s][q] = T(0);
 
     constexpr int NST = C::NST;
+    // decode the first JT jobs and, in a persistent launch, test their source
+    // blocks' flags, one job per thread (one round trip instead of one per job)
+    {
+        const int r = tid;
+        bool rdy = false;
+        if (r < C::JT && r < njob) {
+            int L, Jp;
+            decode(j0 + r, L, Jp);
+            jtab[r] = (L << 24) | Jp;
+            if (a.ready) {
+                const int mu = GEN ? D - 1 - L : L;
+                rdy = dev::ld_acquire(a.ready + t + static_cast<long long>(Jp - I[mu]) * a.tstride[mu]) != 0;
+            }
+        }
+        const unsigned bits = __ballot_sync(0xffffffffu, rdy);
+        if ((tid & 31) == 0 && tid < C::JT) jready[tid >> 5] = bits;
+        __syncthreads();
+    }
     if (tid == 0) {
-        dev::fence_proxy_async();
+        dev::fence_proxy_async_all();
         for (int q = 0; q < NST && q < njob; q++) issue(j0 + q, q);
     }
     bool dead = false;
@@ -750,7 +785,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             break;
         }
         int L, Jp;
-        decode(j0 + jj, L, Jp);
+        job(j0 + jj, L, Jp);
         dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE);
         __syncthreads();
         if (tid == 0 && jj + NST < njob) {
