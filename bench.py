@@ -36,9 +36,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 peak measured on this GB300 model (DMMA m8n8k4 loop over 152 SMs;
 # DFMA 1.06, cuBLAS DGEMM 1.10): `python bench.py --fp64-peak`
 FP64_PEAK_TFLOPS = 1.10
-# DRAM bytes (read + write) per launch of the dominant kernel from an ncu
-# capture of the same kernel; None until a capture of the current kernel exists
-TRAFFIC_PER_LAUNCH_BYTES = None
+# DRAM bytes (read + write) per launch of the dominant kernel (one FP64 solve of
+# the 256^3 generalized form) from an ncu capture of the current kernel:
+# 10.592 GB read + 0.792 GB written (the capture is summarised under profiles/)
+TRAFFIC_PER_LAUNCH_BYTES = 11.384e9
 
 
 def algorithmic_flops(A, C=None):

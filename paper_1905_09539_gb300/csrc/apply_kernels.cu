@@ -49,8 +49,11 @@ struct ApplyCfg {
     static constexpr int EPT = (TD + kThreads - 1) / kThreads;
     // one stage: S1, S2 (P x TD each), M1, M2 (P x TC each), in 8-byte units
     static constexpr int STAGE_BYTES = (2 * TD + 2 * TC) * 8;
-    static constexpr size_t oBar = 2 * STAGE_BYTES;
-    static constexpr size_t oRed = oBar + 16;
+    // stages of the bulk-copy ring (every block is independent here: the
+    // ring only has to cover the copy latency)
+    static constexpr int NST = 4;
+    static constexpr size_t oBar = NST * STAGE_BYTES;
+    static constexpr size_t oRed = oBar + 8 * NST;
     static constexpr size_t smem = oRed + 2 * (kThreads / 32) * sizeof(double);
 };
 
@@ -282,12 +285,11 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& a, const long long t
 #pragma unroll
     for (int q = 0; q < EPT; q++) { y1[q] = y2[q] = 0.0; h1[q] = l1[q] = h2[q] = l2[q] = 0.f; }
     if (tid == 0) {
-        if (njob > 0) issue(0, 0);
-        if (njob > 1) issue(1, 1);
+        for (int q = 0; q < C::NST && q < njob; q++) issue(q, q);
     }
     for (int jj = 0; jj < njob; jj++) {
-        const int stg = jj & 1;
-        const bool ok = dev::mbar_wait(&bar[stg], static_cast<uint32_t>((jj >> 1) & 1), a.timeout_ns);
+        const int stg = jj % C::NST;
+        const bool ok = dev::mbar_wait(&bar[stg], static_cast<uint32_t>((jj / C::NST) & 1), a.timeout_ns);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicOr(a.err, kErrTimeout);
             break;
@@ -296,9 +298,9 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& a, const long long t
         decode(jj, mu, J);
         dispatch<D, MD>(mu, a.kind, smem + stg * C::STAGE_BYTES, y1, y2, h1, l1, h2, l2);
         __syncthreads();
-        if (tid == 0 && jj + 2 < njob) {
+        if (tid == 0 && jj + C::NST < njob) {
             dev::fence_proxy_async();
-            issue(jj + 2, stg);
+            issue(jj + C::NST, stg);
         }
     }
     // ---- epilogue
@@ -357,8 +359,7 @@ template <int D, int MD>
 __device__ __forceinline__ void init_apply_barriers(unsigned char* smem) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + ApplyCfg<D, MD>::oBar);
     if (threadIdx.x == 0) {
-        dev::mbar_init(&bar[0], 1);
-        dev::mbar_init(&bar[1], 1);
+        for (int q = 0; q < ApplyCfg<D, MD>::NST; q++) dev::mbar_init(&bar[q], 1);
         dev::fence_mbar_init();
     }
     __syncthreads();
