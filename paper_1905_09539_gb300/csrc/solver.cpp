@@ -20,6 +20,32 @@ namespace {
 
 constexpr long long kTimeoutNs = 2000000000LL;  // bound of every device-side wait
 
+// Second stream and fork/join events of one device: work that overlaps the
+// main sequence of a solve (captured into the same graph as a parallel branch).
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+SideStream* side_stream() {
+    static std::mutex m;
+    static SideStream st[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(m);
+    SideStream& x = st[dev];
+    if (!x.s) {
+        if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+    }
+    return &x;
+}
+
 }  // namespace
 
 // Private non-blocking stream on which CUDA graphs are captured (capture on
@@ -374,9 +400,8 @@ cudaError_t enqueue_ref_setup(const Call& c, cudaStream_t s) {
     TRY(cudaMemsetAsync(b + R.Xl, 0, nel * 4, s));
     TRY(launch_tile_stats(reinterpret_cast<double*>(b + R.Rt), reinterpret_cast<double*>(b + R.part), p.ntiles, p.td,
                           s));
-    TRY(launch_reduce(reinterpret_cast<double*>(b + R.part), nullptr, p.ntiles, reinterpret_cast<double*>(b + R.nrm),
-                      s));
-    return enqueue_norms(c, s);
+    return launch_reduce(reinterpret_cast<double*>(b + R.part), nullptr, p.ntiles,
+                         reinterpret_cast<double*>(b + R.nrm), s);
 }
 
 cudaError_t enqueue_ref_iter(const Call& c, cudaStream_t s) {
@@ -387,6 +412,19 @@ cudaError_t enqueue_ref_iter(const Call& c, cudaStream_t s) {
     const long long nel = p.ntiles * p.td;
     const double* nrm = reinterpret_cast<const double*>(b + R.nrm);
     TRY(mark(c, 0, s));
+    // a full step also estimates the coefficient norms (they scale the
+    // stopping test), on a parallel branch that overlaps the FP32 solve
+    SideStream* side = c.update ? nullptr : side_stream();
+    if (!c.update) {
+        if (side) {
+            TRY(cudaEventRecord(side->fork, s));
+            TRY(cudaStreamWaitEvent(side->s, side->fork, 0));
+            TRY(enqueue_norms(c, side->s));
+            TRY(cudaEventRecord(side->join, side->s));
+        } else {
+            TRY(enqueue_norms(c, s));
+        }
+    }
     // low-precision solve of A(D) = R / max|R|
     TRY(launch_scale_to_f32(reinterpret_cast<double*>(b + R.Rt), reinterpret_cast<float*>(b + L.X), nrm, nel, s));
     TRY(enqueue_waves<float>(c, L, s));
@@ -400,6 +438,7 @@ cudaError_t enqueue_ref_iter(const Call& c, cudaStream_t s) {
     // R = B - A(X) in FP64-accurate arithmetic, or R -= s A(D) in FP32
     TRY(enqueue_residual(c, s));
     TRY(mark(c, 2, s));
+    if (side) TRY(cudaStreamWaitEvent(s, side->join, 0));
     TRY(launch_reduce(reinterpret_cast<double*>(b + R.part), reinterpret_cast<double*>(b + R.xpart), p.ntiles,
                       reinterpret_cast<double*>(b + R.nrm), s));
     return mark(c, 3, s);
@@ -727,12 +766,10 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (st) return st;
     double hA[2 * kMaxD] = {}, hn[3] = {};
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(hA, c.base + c.R.nA, 2 * kMaxD * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-        return cuda_fail(e, "read norms");
     if ((e = cudaMemcpyAsync(hn, c.base + c.R.nrm, 3 * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
         return cuda_fail(e, "read norms");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize after set-up");
-    const double nA = norm_op(c, hA);
+    double nA = -1;
     int iters = 0, status = TSYLV_ENOCONV;
     double rho = -1, t_resid = 0, t_waves = 0;
     if (!(hn[1] > 0)) {
@@ -750,7 +787,11 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
             if (st) return st;
             if ((e = cudaMemcpyAsync(hn, c.base + c.R.nrm, 3 * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
                 return cuda_fail(e, "read residual norm");
+            if (!c.update &&
+                (e = cudaMemcpyAsync(hA, c.base + c.R.nA, 2 * kMaxD * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+                return cuda_fail(e, "read norms");
             if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize in refinement");
+            if (!c.update) nA = norm_op(c, hA);
             iters = it + 1;
             if (c.timing) {
                 float a = 0, b2 = 0;

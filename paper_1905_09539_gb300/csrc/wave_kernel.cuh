@@ -33,18 +33,22 @@ struct WaveCfg {
     // stages of the bulk-copy ring: the FP64 updates are bound by the FP64
     // pipes, the FP32 ones by the copy latency
     static constexpr int NST = sizeof(T) == 8 ? 2 : (GEN ? 4 : 6);
-    // the staging ring of the block updates and the base case's running
-    // line sums share one region
+    // the staging ring of the block updates and the base case's coupled-group
+    // inverses share one region; the base case's running line sums of
+    // coupled-group members reuse the block-update sums `red` once those are
+    // consumed (the generalized form's level sums are parked in the output
+    // P, G blocks meanwhile), and the reciprocal diagonal of a 1x1 group sits
+    // in its not yet solved X entry
     static constexpr int MINV = 1024;  // budget (entries) for precomputed coupled-group inverses
-    static constexpr int UNION = (NST * STAGE > NACC * TD + MINV) ? NST * STAGE : NACC * TD + MINV;
+    static constexpr int UNION = (NST * STAGE > MINV) ? NST * STAGE : MINV;
     static constexpr int oStage = 0;
-    static constexpr int oLin = 0;
-    static constexpr int oMinv = NACC * TD;
+    static constexpr int oMinv = 0;
     static constexpr int oRed = UNION;
+    static constexpr int oLin = oRed;
     static constexpr int oR = oRed + NACC * TD;
     static constexpr int oX = oR + TD;
-    static constexpr int oRd = oX + TD;
-    static constexpr int oPin = oRd + TD;
+    static constexpr int oRd = oX;
+    static constexpr int oPin = oX + TD;
     static constexpr int oGin = oPin + NL * TD;
     static constexpr int oD = oGin + NL * TD;
     static constexpr int oE = oD + D * TC;
@@ -854,7 +858,6 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         Rs[e] = Xg[e];
         Xs[e] = T(0);
     }
-    for (int e = tid; e < NACC * TD; e += kThreads) Lin[e] = T(0);
     int* cg_cnt = gidx + D * TE;        // coupled groups per anti-diagonal
     int* cg_off = cg_cnt + C::MAXSTEP;  // their offsets in cg_list
     int* cg_fill = cg_off + C::MAXSTEP + 1;
@@ -937,6 +940,21 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         for (int e = tid; e < TD; e += kThreads) Rs[e] -= red[e];
     }
     __syncthreads();
+    if constexpr (GEN) {
+        // park the level sums of the block updates in the output blocks (the
+        // in-block parts are added at the end), freeing `red` for Lin
+#pragma unroll
+        for (int l = 1; l < D; l++) {
+            T* Pg = static_cast<T*>(a.P[l]) + t * TD;
+            T* Gg = static_cast<T*>(a.G[l]) + t * TD;
+            for (int e = tid; e < TD; e += kThreads) {
+                Pg[e] = red[C::slotP(l) * TD + e];
+                Gg[e] = red[C::slotG(l) * TD + e];
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < NACC * TD; e += kThreads) Lin[e] = T(0);
 
     // ---- back-substitution over coupled groups in anti-diagonal order.
     // Every thread owns the elements e = tid + q*kThreads: it solves those
@@ -1039,39 +1057,48 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     for (int i = tid; i < ncg; i += kThreads)
         if (cg_moff[i] >= 0) status |= group_inverse<T, D, GEN>(sm, cg_list[i], Minv + cg_moff[i]);
     __syncthreads();
-    for (int step = nsum - D; step >= 0; step--) {
-        // elements of this anti-diagonal: line sums from the solved positions,
-        // then the 1x1 groups are solved by their threads; members of coupled
-        // groups publish their sums for the solving warp
-        const int a0 = act_off[step], an = act_cnt[step];
-        for (int i = tid; i < an; i += kThreads) {
-            const int code = act_list[a0 + i];
-            const int e = code & 0xffff;
-            int u[D], g[D], rem = e;
+    // all warps take part (a one-warp variant with warp barriers between the
+    // anti-diagonals measured slower for FP32 too: the line sums of one step
+    // are then serialised over fewer lanes)
+    constexpr bool SOLO = false;
+    if (!SOLO || tid < 32) {
+        const int lane = tid & 31;
+        for (int step = nsum - D; step >= 0; step--) {
+            // elements of this anti-diagonal: line sums from the solved positions,
+            // then the 1x1 groups are solved by their threads; members of coupled
+            // groups publish their sums for the solving warp
+            const int a0 = act_off[step], an = act_cnt[step];
+            for (int i = SOLO ? lane : tid; i < an; i += SOLO ? 32 : kThreads) {
+                const int code = act_list[a0 + i];
+                const int e = code & 0xffff;
+                int u[D], g[D], rem = e;
 #pragma unroll
-            for (int mu = 0; mu < D; mu++) {
-                u[mu] = rem % TE;
-                rem /= TE;
-                g[mu] = gidx[mu * TE + u[mu]];
-            }
-            T L[NACC];
-            pull_lines<T, D, GEN>(sm, e, u, g, L);
-            if (!(code >> 16)) {
-                status |= solve_single<T, D, GEN>(sm, e, u, L);
-            } else {
+                for (int mu = 0; mu < D; mu++) {
+                    u[mu] = rem % TE;
+                    rem /= TE;
+                    g[mu] = gidx[mu * TE + u[mu]];
+                }
+                T L[NACC];
+                pull_lines<T, D, GEN>(sm, e, u, g, L);
+                if (!(code >> 16)) {
+                    status |= solve_single<T, D, GEN>(sm, e, u, L);
+                } else {
 #pragma unroll
-                for (int k = 0; k < NACC; k++) Lin[k * TD + e] = L[k];
+                    for (int k = 0; k < NACC; k++) Lin[k * TD + e] = L[k];
+                }
             }
+            const int c0 = cg_off[step], cn = cg_cnt[step];
+            if (cn > 0) {
+                if constexpr (SOLO) __syncwarp(); else __syncthreads();
+                const int warp = SOLO ? 0 : tid >> 5, nw = SOLO ? 1 : kThreads >> 5;
+                for (int k = warp; k < cn; k += nw)
+                    status |= warp_group<T, D, GEN>(sm, cg_list[c0 + k],
+                                                    cg_moff[c0 + k] >= 0 ? Minv + cg_moff[c0 + k] : nullptr);
+            }
+            if constexpr (SOLO) __syncwarp(); else __syncthreads();
         }
-        const int c0 = cg_off[step], cn = cg_cnt[step];
-        if (cn > 0) {
-            __syncthreads();
-            const int warp = tid >> 5, nw = kThreads >> 5;
-            for (int k = warp; k < cn; k += nw)
-                status |= warp_group<T, D, GEN>(sm, cg_list[c0 + k], cg_moff[c0 + k] >= 0 ? Minv + cg_moff[c0 + k] : nullptr);
-        }
-        __syncthreads();
     }
+    if constexpr (SOLO) __syncthreads();
     if (status) atomicOr(a.err, status);
 
     // ---- write the solved block (and its intermediates)
@@ -1081,9 +1108,9 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         for (int l = 1; l < D; l++) {
             T* Pg = static_cast<T*>(a.P[l]) + t * TD;
             T* Gg = static_cast<T*>(a.G[l]) + t * TD;
-            for (int e = tid; e < TD; e += kThreads) {
-                Pg[e] = red[C::slotP(l) * TD + e] + Pin[(l - 1) * TD + e];
-                Gg[e] = red[C::slotG(l) * TD + e] + Gin[(l - 1) * TD + e];
+            for (int e = tid; e < TD; e += kThreads) {  // the same thread parked Pg[e], Gg[e]
+                Pg[e] += Pin[(l - 1) * TD + e];
+                Gg[e] += Gin[(l - 1) * TD + e];
             }
         }
     }
