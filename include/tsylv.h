@@ -18,14 +18,15 @@
  * respectively iff the generalized operator is nonsingular.
  *
  * Method: the recursive blocked algorithm of Sec. 2.1 (Alg. 2) with merged
- * modes in the base case (Sec. 2.2-2.3, Alg. 3).  The split tree of Alg. 2
- * fixes a block partition of every mode; the right-hand-side updates of
- * Eq. (2.3a) become block mode-mu products, and the leaves are solved by a
- * back-substitution in which 2x2 Schur blocks are solved as coupled groups
- * (the diagonal blocks after the perfect shuffle of Sec. 2.3).  The GPU runs
- * the independent leaves of the split tree concurrently (anti-diagonal
- * wavefronts over the block grid), one launch per wavefront, all captured in
- * a CUDA graph.
+ * modes in the base case (Sec. 2.2-2.3, Alg. 3).  Every mode is partitioned
+ * into blocks that keep the 2x2 Schur blocks whole (opts->partition); the
+ * right-hand-side updates of Eq. (2.3a) become block mode-mu products, and
+ * the leaves are solved by a back-substitution in which 2x2 Schur blocks are
+ * solved as coupled groups (the diagonal blocks after the perfect shuffle of
+ * Sec. 2.3).  By default one persistent launch per solve runs every block as
+ * soon as the blocks it reads are solved (opts->schedule = 0); the
+ * alternative is one launch per anti-diagonal wavefront.  The launches of a
+ * call are captured once in a CUDA graph and replayed.
  *
  * Layout.  Tensors are dense and column-major with mode 1 fastest -- the
  * index map Eq. (2.1): element (i_1, ..., i_d) (0-based) is at
@@ -37,8 +38,7 @@
  * block at (i, i+1); two consecutive nonzero subdiagonal entries are an error.
  *
  * Pointers.  `n` and the arrays `A`, `C`, `dA`, `dC` are host arrays; the
- * matrices and tensors they point to live in device memory (unless
- * opts->host_io is set, see below).  All device memory is owned by the
+ * matrices and tensors they point to live in device memory.  All device memory is owned by the
  * caller.  The library allocates no device memory: every scratch buffer is
  * carved out of `work`, whose size comes from the matching *_workspace_bytes
  * query (256-byte alignment is required).  In-place use (X == B) is allowed.
@@ -81,8 +81,11 @@ enum tsylv_precision {
                                 X_{k+1} = X_k + max|R_k| D_k (FP64);
                                 R_{k+1} = B - A(X_{k+1}) (opts->residual)
                                 until ||R|| / (||A|| ||X||) <= opts->tol        */
-    TSYLV_TF32_REFINED = 2,  /* TF32 tensor-core updates, FP32 accumulation, refined */
-    TSYLV_BF16_REFINED = 3   /* BF16 tensor-core updates, FP32 accumulation, refined */
+    TSYLV_TF32_REFINED = 2,  /* reserved: TF32 tensor-core updates; this build returns
+                                TSYLV_EUNSUPPORTED (the FP32 solve of
+                                TSYLV_FP32_REFINED is latency-bound, so tensor
+                                cores would only cost accuracy)                    */
+    TSYLV_BF16_REFINED = 3   /* reserved, as TSYLV_TF32_REFINED                      */
 };
 
 enum tsylv_residual_kind {
@@ -98,8 +101,8 @@ typedef struct tsylv_opts {
     int nmin;         /* largest block extent per mode; 0 = the default for d        */
     int split;        /* largest cluster size for split block updates; 0 = auto      */
     int use_graph;    /* 1 (default): capture each schedule once and replay it      */
-    int host_io;      /* 1: B, X, A, C (and backward buffers) are host pointers; the
-                         call copies them through `work` inside the call             */
+    int host_io;      /* reserved (host-resident operands); must be 0: this build
+                         returns TSYLV_EUNSUPPORTED otherwise                        */
     int timing;       /* 1: time the phases with CUDA events (fields t_* of info)    */
     int schedule;     /* block schedule of a solve: 0 (default) one persistent
                          dataflow launch (a block starts as soon as each source
@@ -114,6 +117,10 @@ typedef struct tsylv_opts {
                          updated from the step's FP32 correction, R -= s A(D) in
                          FP32 (error ~2^-24 |A| |s D|, far below the residual);
                          1: the full FP64-accurate residual at every step         */
+    int fuse_step;    /* *_REFINED, Laplace form, d >= 2, DF64 residual, schedule 0:
+                         1 runs a full refinement step as one launch (each block:
+                         FP32 solve, X update, DF64 residual); 0 (default) separate
+                         launches, which measured faster on GB300              */
 } tsylv_opts;
 
 typedef struct tsylv_info {

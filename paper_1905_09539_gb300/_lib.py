@@ -27,7 +27,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double),
                 ("residual", ctypes.c_int), ("nmin", ctypes.c_int), ("split", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
-                ("schedule", ctypes.c_int), ("partition", ctypes.c_int), ("resid_update", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("partition", ctypes.c_int), ("resid_update", ctypes.c_int),
+                ("fuse_step", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -42,6 +42,7 @@ extern "C" void tsylv_opts_default(tsylv_opts* o) {
     o->schedule = 0;
     o->partition = 0;
     o->resid_update = 0;
+    o->fuse_step = 0;
 }
 
 extern "C" const char* tsylv_status_string(int s) {

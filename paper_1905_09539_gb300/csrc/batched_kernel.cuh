@@ -10,7 +10,7 @@
 namespace tsylv {
 
 template <typename T, int D, bool GENF>
-__global__ void __launch_bounds__(kThreads) k_batched(const BatchArgs b) {
+__global__ void __launch_bounds__(kThreads, WaveCfg<T, D, GENF>::MINB) k_batched(const BatchArgs b) {
     using C = WaveCfg<T, D, GENF>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::oBar);
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kThreads) k_batched(const BatchArgs b) {
             s_ok = ok;
         }
         __syncthreads();
-        if (alive && s_ok) alive = wave_tile<T, D, GENF>(a, jb.tile, 0, 1, uses);
+        if (alive && s_ok) alive = wave_tile<T, D, GENF>(a, jb.tile, 0, 1, uses, bar);
         // publish the block: every thread's stores, then the count / flag (release)
         __threadfence();
         __syncthreads();

@@ -1,0 +1,10 @@
+// Fused refinement step instantiation, d = 3.
+#include "fused_kernel.cuh"
+
+namespace tsylv {
+
+template cudaError_t launch_fused_t<3>(const FusedArgs&, int, cudaStream_t);
+template cudaError_t prepare_fused_t<3>();
+template int fused_occupancy_t<3>();
+
+}  // namespace tsylv

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "batched.h"
+#include "fused.h"
 #include "plan.h"
 #include "refine.h"
 
@@ -166,6 +167,8 @@ struct Call {
     bool persistent = true;   // opts->schedule == 0
     int flow_grid = 0;        // CTAs of the persistent launch
     bool update = false;      // refinement step: residual updated from the FP32 correction
+    bool fused = false;       // full refinement step in one launch (Laplace form, DF64 residual, persistent)
+    int fused_grid = 0;
 };
 
 inline cudaError_t mark(const Call& c, int i, cudaStream_t s) {
@@ -427,6 +430,57 @@ cudaError_t enqueue_ref_iter(const Call& c, cudaStream_t s) {
     }
     // low-precision solve of A(D) = R / max|R|
     TRY(launch_scale_to_f32(reinterpret_cast<double*>(b + R.Rt), reinterpret_cast<float*>(b + L.X), nrm, nel, s));
+    if (c.fused && !c.update) {
+        // solve, update, split and DF64 residual block by block in one launch
+        int* ctl = reinterpret_cast<int*>(b + L.fctl);
+        int* flags = reinterpret_cast<int*>(b + L.flags);
+        TRY(cudaMemsetAsync(ctl, 0, 64, s));
+        TRY(cudaMemsetAsync(flags, 0, static_cast<size_t>(p.ntiles) * sizeof(int), s));
+        WaveArgs wa = wave_args(p, L, b);
+        wa.ready = flags;
+        wa.abort = ctl + 1;
+        wa.csize = 1;
+        WaveArgs* dargs = reinterpret_cast<WaveArgs*>(b + L.fargs);
+        TRY(launch_store_args(wa, dargs, s));
+        FusedArgs f{};
+        f.b.eqs = dargs;
+        f.b.jobs = nullptr;
+        f.b.tiles = reinterpret_cast<const int*>(b + L.tab) + p.t_wave;
+        f.b.njobs = static_cast<int>(p.ntiles);
+        f.b.head = ctl;
+        f.b.done = nullptr;
+        f.b.abort = ctl + 1;
+        f.b.timeout_ns = kTimeoutNs;
+        ApplyArgs& ap = f.ap;
+        for (int mu = 0; mu < p.d; mu++) {
+            ap.nb[mu] = p.nb[mu];
+            ap.tstride[mu] = p.tstride[mu];
+            ap.A[mu] = b + R.Ah[mu];
+            ap.Al[mu] = b + R.Al[mu];
+        }
+        ap.ntiles = p.ntiles;
+        ap.kind = kApplyLaplace;
+        ap.s1 = b + R.Xh;
+        ap.s1l = b + R.Xl;
+        ap.B = reinterpret_cast<const double*>(b + R.Bt);
+        ap.R = reinterpret_cast<double*>(b + R.Rt);
+        ap.part = reinterpret_cast<double*>(b + R.part);
+        ap.err = reinterpret_cast<int*>(b + L.err);
+        ap.timeout_ns = kTimeoutNs;
+        f.X = reinterpret_cast<double*>(b + R.Xt);
+        f.Xh = reinterpret_cast<float*>(b + R.Xh);
+        f.Xl = reinterpret_cast<float*>(b + R.Xl);
+        f.xpart = reinterpret_cast<double*>(b + R.xpart);
+        f.nrm = nrm;
+        f.lag = static_cast<int>(p.ntiles);  // residual jobs after every solve job (measured best)
+        TRY(launch_fused(p.d, f, c.fused_grid, s));
+        TRY(mark(c, 1, s));
+        TRY(mark(c, 2, s));
+        if (side) TRY(cudaStreamWaitEvent(s, side->join, 0));
+        TRY(launch_reduce(reinterpret_cast<double*>(b + R.part), reinterpret_cast<double*>(b + R.xpart), p.ntiles,
+                          reinterpret_cast<double*>(b + R.nrm), s));
+        return mark(c, 3, s);
+    }
     TRY(enqueue_waves<float>(c, L, s));
     // X += max|R| D  (FP64), its float-pair split, block sums of X^2
     const bool split = c.df && !c.update;  // the float-pair X only feeds a full DF64 residual
@@ -543,6 +597,29 @@ int flow_grid(int elem, int d, bool gen, long long ntiles) {
     return static_cast<int>(ntiles < slots ? ntiles : slots);
 }
 
+// CTAs of the fused first refinement step.
+int fused_grid(int d, long long ntiles) {
+    static std::mutex m;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int key = dev * 8 + d;
+    int slots = 0;
+    {
+        std::lock_guard<std::mutex> lk(m);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            slots = it->second;
+        } else {
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+            slots = sms * fused_occupancy(d);
+            cache[key] = slots;
+        }
+    }
+    return static_cast<int>(ntiles < slots ? ntiles : slots);
+}
+
 int prepare_kernels() {
     static std::mutex pm;
     static bool prepared[64] = {};
@@ -557,6 +634,7 @@ int prepare_kernels() {
         if (e == cudaSuccess) e = prepare_apply_f32();
         if (e == cudaSuccess) e = prepare_batched<double>();
         if (e == cudaSuccess) e = prepare_batched<float>();
+        if (e == cudaSuccess) e = prepare_fused();
         if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
         prepared[dev] = true;
     }
@@ -690,7 +768,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (o.precision < TSYLV_FP64 || o.precision > TSYLV_BF16_REFINED || o.max_refine < 0 || !(o.tol > 0) ||
         (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < 0 ||
         o.schedule < 0 || o.schedule > 1 || o.partition < 0 || o.partition > 1 || o.resid_update < 0 ||
-        o.resid_update > 1)
+        o.resid_update > 1 || o.fuse_step < 0 || o.fuse_step > 1)
         return -(8 + sh);
     if (o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d))) return TSYLV_EUNSUPPORTED;
     if (o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) return TSYLV_EUNSUPPORTED;
@@ -720,7 +798,12 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (int st = ensure_events(c)) return st;
     c.persistent = o.schedule == 0;
     if (c.persistent) c.flow_grid = flow_grid(refined ? 4 : 8, d, c.gen, c.plan->ntiles);
-    const int tagbase = (transposed ? 1 : 0) | (c.timing ? 2 : 0) | (c.df ? 4 : 0) | (c.persistent ? 256 : 0);
+    // (d = 1 keeps separate launches: its fused launch is refused with an
+    // invalid-argument error whose cause is not understood yet)
+    c.fused = refined && c.persistent && !c.gen && c.df && o.fuse_step == 1 && d >= 2;
+    if (c.fused) c.fused_grid = fused_grid(d, c.plan->ntiles);
+    const int tagbase = (transposed ? 1 : 0) | (c.timing ? 2 : 0) | (c.df ? 4 : 0) | (c.persistent ? 256 : 0) |
+                        (c.fused ? 1024 : 0);
 
     if (!refined) {
         c.L = make_layout(d, c.n, c.plan->nb, c.gen, 8, c.plan->tab.size());

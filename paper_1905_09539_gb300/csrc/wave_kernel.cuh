@@ -33,6 +33,11 @@ struct WaveCfg {
     // stages of the bulk-copy ring: the FP64 updates are bound by the FP64
     // pipes, the FP32 ones by the copy latency
     static constexpr int NST = sizeof(T) == 8 ? 2 : (GEN ? 4 : 6);
+    // resident CTAs per SM the persistent kernel is compiled for (register
+    // budget): FP64 Laplace d = 3 6 (its shared memory allows 6, registers
+    // alone would give 5), FP64 generalized 3 (shared-memory bound), FP32 5 / 4
+    static constexpr int MINB = sizeof(T) == 8 ? (GENF && D >= 2 ? (D == 3 ? 3 : 4) : (D == 3 ? 6 : 4))
+                                               : (GENF && D >= 2 ? 4 : 5);
     // the staging ring of the block updates and the base case's coupled-group
     // inverses share one region; the base case's running line sums of
     // coupled-group members reuse the block-update sums `red` once those are
@@ -613,14 +618,14 @@ __device__ int group_inverse(const TileSmem<T, D, GEN>& sm, int e, T* out) {
 
 // One block T of the block grid: its right-hand-side update (split over the
 // `csize` CTAs of a cluster, this CTA being `rank`) and, on rank 0, its base
-// case.  The CTA's NST staging barriers are initialised by the caller;
+// case.  The CTA's NST staging barriers `bar` are initialised by the caller;
 // uses[s] counts the phases barrier s has completed so far (a persistent
 // caller runs many blocks on the same barriers).  Returns false when a wait
 // ran out of time (the error word is set; no copy of this call is left in
 // flight).
 template <typename T, int D, bool GENF>
 __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, const int rank, const int csize,
-                                          uint32_t (&uses)[WaveCfg<T, D, GENF>::NST]) {
+                                          uint32_t (&uses)[WaveCfg<T, D, GENF>::NST], uint64_t* bar) {
     using C = WaveCfg<T, D, GENF>;
     constexpr int TE = C::TE, TD = C::TD, TC = C::TC, EPT = C::EPT, NACC = C::NACC;
     constexpr bool GEN = C::GEN;
@@ -628,7 +633,6 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     T* sbase = reinterpret_cast<T*>(smem_raw);
     T* stage = sbase + C::oStage;
     T* red = sbase + C::oRed;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::oBar);
     int* meta = reinterpret_cast<int*>(smem_raw + C::oMeta);
     int* gs = meta;                  // [D][TE]
     int* gl = gs + D * TE;           // [D][TE]
@@ -1130,7 +1134,7 @@ __global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
     }
     __syncthreads();
     uint32_t uses[C::NST] = {};
-    (void)wave_tile<T, D, GENF>(a, a.tiles[blockIdx.x / csize], rank, csize, uses);
+    (void)wave_tile<T, D, GENF>(a, a.tiles[blockIdx.x / csize], rank, csize, uses, bar);
 }
 
 template <typename T, int D, bool GEN>

@@ -126,3 +126,17 @@ def test_reported_residual_is_the_true_one(ts, shape, gen, update):
     R = p["B"] - oracle.apply(p["A"], Xg, p["C"])
     rho = np.linalg.norm(R) / (norm_op(p["A"], p["C"]) * np.linalg.norm(Xg))
     assert abs(info.resid - rho) <= 2e-2 * rho + 1e-14
+
+
+@pytest.mark.parametrize("fuse", [0, 1])
+@pytest.mark.parametrize("d,shape", [(1, (100,)), (2, (33, 17)), (3, (24, 20, 16)), (4, (9, 7, 5, 6))])
+def test_fused_and_separate_steps(ts, d, shape, fuse):
+    """The first refinement step of the Laplace form as separate launches
+    (default) or as one fused launch: same accuracy against the oracle."""
+    p = synthetic.problem(37, shape, force_blocks=[[n // 2 - 1] if n >= 4 else [] for n in shape])
+    Xo = oracle.solve_recursive(p["A"], p["B"], nmin=4)
+    info = ts.Info()
+    X, st = ts.tsylv_solve([to_dev(a) for a in p["A"]], to_dev(p["B"]), precision=ts.TSYLV_FP32_REFINED,
+                           fuse_step=fuse, info=info)
+    assert st == 0 and info.resid <= 1e-12 and 1 <= info.iterations <= 4
+    assert rel_err(to_host(X), Xo) <= 1e-10
