@@ -44,7 +44,8 @@ struct ApplyArgs {
     void* o2;
     void* o2l;
     const double* B;   // right-hand side (double tiles) for kApplyLaplace / kApplyFinal
-    const double* scale;  // nullptr: R = B - A(X); else R = B - scale[1] * A(S) (B may alias R)
+    const double* scale;  // nullptr: R = B - A(X); else R = B - s A(S) with s the power of two at or
+                          // above scale[1] (B may alias R)
     double* R;         // residual (double tiles)
     double* part;      // [ntiles][2]: sum of R^2, max |R| of every block
     // coefficient tiles (upper block triangle), per mode: FP64 A/C (double),
@@ -65,6 +66,10 @@ cudaError_t prepare_apply();
 // residual update from its FP32 correction).
 cudaError_t launch_apply_f32(int d, const ApplyArgs& a, cudaStream_t s);
 cudaError_t prepare_apply_f32();
+// DF64 arithmetic on an FP32 source s1 (s1l unused), the coefficients as
+// float pairs; kinds Laplace and First only (one source)
+cudaError_t launch_apply_dfh(int d, const ApplyArgs& a, cudaStream_t s);
+cudaError_t prepare_apply_dfh();
 // One launch of many applies of order d: CTA b computes block jobs[b].y of
 // the apply eqs[jobs[b].x] (device arrays).  mode: 0 FP64, 1 DF64, 2 FP32.
 cudaError_t launch_apply_batched(int d, int mode, const ApplyArgs* eqs, const int2* jobs, int njobs, cudaStream_t s);

@@ -1,6 +1,7 @@
 // Operator application kernels (residual of the refinement): FP64, DF64
-// (float pairs on the FP32 pipes) and plain FP32 (the residual update of a
-// refinement step from its FP32 correction).
+// (float pairs on the FP32 pipes), DF64 on a float source (the first
+// refinement step, whose iterate is a scaled FP32 solution) and plain FP32
+// (the residual update of a refinement step from its FP32 correction).
 #include "apply_kernel.cuh"
 #include "device_common.cuh"
 
@@ -103,6 +104,9 @@ cudaError_t prepare_apply() {
 
 cudaError_t launch_apply_f32(int d, const ApplyArgs& a, cudaStream_t s) { return launch_apply_m<kModeF32>(d, a, s); }
 cudaError_t prepare_apply_f32() { return prepare_apply_m<kModeF32>(); }
+
+cudaError_t launch_apply_dfh(int d, const ApplyArgs& a, cudaStream_t s) { return launch_apply_m<kModeDFh>(d, a, s); }
+cudaError_t prepare_apply_dfh() { return prepare_apply_m<kModeDFh>(); }
 
 cudaError_t launch_apply_batched(int d, int mode, const ApplyArgs* eqs, const int2* jobs, int njobs, cudaStream_t s) {
 #define TSYLV_APPLY_B(DD)                                                                          \

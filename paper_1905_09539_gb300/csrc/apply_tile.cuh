@@ -39,7 +39,9 @@ namespace tsylv {
 namespace apply_detail {
 
 // arithmetic of an apply: 0 FP64, 1 DF64, 2 FP32
-enum : int { kModeF64 = 0, kModeDF = 1, kModeF32 = 2 };
+// 3: DF64 arithmetic on FP32 sources (the source's low word is zero: the
+// first refinement step's iterate s D with s a power of two)
+enum : int { kModeF64 = 0, kModeDF = 1, kModeF32 = 2, kModeDFh = 3 };
 
 template <int D, int M>
 struct ApplyCfg {
@@ -87,6 +89,32 @@ __device__ __forceinline__ void acc_df(float (&yh)[EPT], float (&yl)[EPT], const
         float h = yh[q], l = yl[q];
 #pragma unroll
         for (int k = 0; k < TE; k++) df_fma(Mh[i + TE * k], Ml[i + TE * k], Sh[base + k * st], Sl[base + k * st], h, l);
+        yh[q] = h;
+        yl[q] = l;
+    }
+}
+
+// (yh, yl)[q] += (M x_MU S)[e_q]: DF64, M a (hi, lo) float tile, S an exact float tile
+template <int D, int MU, int EPT>
+__device__ __forceinline__ void acc_dfh(float (&yh)[EPT], float (&yl)[EPT], const float* __restrict__ Mh,
+                                        const float* __restrict__ Ml, const float* __restrict__ Sh) {
+    constexpr int TE = tile_extent(D), TD = ipow(TE, D), st = ipow(TE, MU);
+#pragma unroll
+    for (int q = 0; q < EPT; q++) {
+        const int e = threadIdx.x + q * kThreads;
+        if ((TD % kThreads) != 0 && e >= TD) continue;
+        const int i = (e / st) % TE, base = e - i * st;
+        float h = yh[q], l = yl[q];
+#pragma unroll
+        for (int k = 0; k < TE; k++) {
+            const float mh = Mh[i + TE * k], ml = Ml[i + TE * k], x = Sh[base + k * st];
+            const float pr = mh * x;
+            const float t = fmaf(ml, x, fmaf(mh, x, -pr));  // exact low part of mh x, plus ml x
+            float sum, err;
+            two_sum(h, pr, sum, err);
+            h = sum;
+            l += err + t;
+        }
         yh[q] = h;
         yl[q] = l;
     }
@@ -151,6 +179,20 @@ __device__ __forceinline__ void do_job(int kind, const unsigned char* stg, doubl
         } else {
             acc_f64<D, MU, EPT>(y1, M1, S2);
             acc_f64<D, MU, EPT>(y1, M2, S1);
+        }
+    } else if constexpr (MD == kModeDFh) {
+        // same staging layout as DF64 (the source's low words not copied);
+        // only the kinds with one source occur
+        const float* S1h = reinterpret_cast<const float*>(stg);
+        const float* M1h = S1h + 4 * TD;
+        const float* M1l = M1h + TC;
+        const float* M2h = M1l + TC;
+        const float* M2l = M2h + TC;
+        if (kind == kApplyLaplace) {
+            acc_dfh<D, MU, EPT>(h1, l1, M1h, M1l, S1h);
+        } else {
+            acc_dfh<D, MU, EPT>(h1, l1, M1h, M1l, S1h);
+            acc_dfh<D, MU, EPT>(h2, l2, M2h, M2l, S1h);
         }
     } else {
         const float* S1h = reinterpret_cast<const float*>(stg);
@@ -255,6 +297,23 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& a, const long long t
             const double* m1 = static_cast<const double*>(lap ? a.A[mu] : a.C[mu]) + tri * TC;
             dev::bulk_g2s(M1, m1, TC * 8, &bar[stg]);
             if (two_coef) dev::bulk_g2s(M2, static_cast<const double*>(a.A[mu]) + tri * TC, TC * 8, &bar[stg]);
+        } else if constexpr (MD == kModeDFh) {
+            float* S1h = reinterpret_cast<float*>(sb);
+            float* M1h = S1h + 4 * TD;
+            float* M1l = M1h + TC;
+            float* M2h = M1l + TC;
+            float* M2l = M2h + TC;
+            bytes = TD * 4 + (two_coef ? 2 : 1) * TC * 8;
+            dev::mbar_expect_tx(&bar[stg], bytes);
+            dev::bulk_g2s(S1h, static_cast<const float*>(a.s1) + ts * TD, TD * 4, &bar[stg]);
+            const float* m1h = static_cast<const float*>(lap ? a.A[mu] : a.C[mu]) + tri * TC;
+            const float* m1l = static_cast<const float*>(lap ? a.Al[mu] : a.Cl[mu]) + tri * TC;
+            dev::bulk_g2s(M1h, m1h, TC * 4, &bar[stg]);
+            dev::bulk_g2s(M1l, m1l, TC * 4, &bar[stg]);
+            if (two_coef) {
+                dev::bulk_g2s(M2h, static_cast<const float*>(a.A[mu]) + tri * TC, TC * 4, &bar[stg]);
+                dev::bulk_g2s(M2l, static_cast<const float*>(a.Al[mu]) + tri * TC, TC * 4, &bar[stg]);
+            }
         } else {
             float* S1h = reinterpret_cast<float*>(sb);
             float* S1l = S1h + TD;
@@ -315,10 +374,10 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& a, const long long t
         for (int q = 0; q < EPT; q++) {
             const int e = tid + q * kThreads;
             if ((TD % kThreads) != 0 && e >= TD) continue;
-            const double v = MD == kModeDF ? df_to_double(h1[q], l1[q])
+            const double v = (MD == kModeDF || MD == kModeDFh) ? df_to_double(h1[q], l1[q])
                              : MD == kModeF32 ? static_cast<double>(h1[q]) : y1[q];
             // scale given: R = B - scale * A(S) (B may be R itself: update in place)
-            const double r = a.scale ? a.B[t * TD + e] - a.scale[1] * v : a.B[t * TD + e] - v;
+            const double r = a.scale ? a.B[t * TD + e] - dev::step_scale(a.scale[1]) * v : a.B[t * TD + e] - v;
             a.R[t * TD + e] = r;
             ss += r * r;
             mx = fmax(mx, fabs(r));

@@ -3,6 +3,7 @@
 // back (equation e owns the blocks [tile_off[e], tile_off[e+1]) of td entries
 // each); per-equation scalars are indexed through the block -> equation map.
 #include "batched.h"
+#include "device_common.cuh"
 
 namespace tsylv {
 
@@ -15,23 +16,21 @@ inline int grid_for(long long total) {
     return static_cast<int>(b);
 }
 
-// r32 = r / max|r_e|   (nrm[4 e + 1] = max|r| of equation e)
+// r32 = r / s_e, s_e the power of two at or above max|r_e| (nrm[4 e + 1])
 __global__ void k_bscale(const double* __restrict__ r, float* __restrict__ r32, const int* __restrict__ tile_eq,
                          const double* __restrict__ nrm, long long n, int td) {
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const double mx = nrm[4 * tile_eq[i / td] + 1];
-        r32[i] = static_cast<float>(r[i] * (mx > 0 ? 1.0 / mx : 1.0));
+        r32[i] = static_cast<float>(r[i] * (1.0 / dev::step_scale(nrm[4 * tile_eq[i / td] + 1])));
     }
 }
 
-// x += max|r_e| d32 per block, and the block's sum of x^2
+// x += s_e d32 per block, and the block's sum of x^2
 __global__ void k_bupdate(double* __restrict__ x, const float* __restrict__ d32, const int* __restrict__ tile_eq,
                           const double* __restrict__ nrm, double* __restrict__ xpart, long long ntiles, int td) {
     __shared__ double red[32];
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const double mx = nrm[4 * tile_eq[t] + 1];
-        const double sc = mx > 0 ? mx : 1.0;
+        const double sc = dev::step_scale(nrm[4 * tile_eq[t] + 1]);
         double ss = 0;
         for (int e = threadIdx.x; e < td; e += blockDim.x) {
             const long long i = t * td + e;

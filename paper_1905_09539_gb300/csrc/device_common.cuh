@@ -126,6 +126,15 @@ __device__ __forceinline__ bool wait_at_least(const int* p, int need, int* abort
     return true;
 }
 
+// Scale of a refinement step: the power of two at or above max|R| (1 when R
+// is zero or not finite), so that R / s and s * D are exact.
+__device__ __forceinline__ double step_scale(double mx) {
+    if (!(mx > 0) || !isfinite(mx)) return 1.0;
+    int ex = 0;
+    (void)frexp(mx, &ex);  // mx = f 2^ex, 1/2 <= f < 1
+    return ldexp(1.0, ex);
+}
+
 template <typename T>
 __device__ __forceinline__ T fmadd(T a, T b, T c);
 template <>

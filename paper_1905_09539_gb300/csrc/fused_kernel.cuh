@@ -52,8 +52,7 @@ __global__ void __launch_bounds__(kThreads) k_fused_step(const FusedArgs f) {
     uint32_t usesA[CA::NST] = {};
     bool alive = true;
     const WaveArgs& a = f.b.eqs[0];
-    const double mx = f.nrm[1];
-    const double sc = mx > 0 ? mx : 1.0;
+    const double sc = dev::step_scale(f.nrm[1]);
     for (;;) {
         if (threadIdx.x == 0) s_job = atomicAdd(f.b.head, 1);
         __syncthreads();

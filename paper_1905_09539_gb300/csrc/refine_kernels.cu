@@ -2,6 +2,7 @@
 // scaling of the residual into the FP32 solve, the FP64 correction update of
 // X, double -> float-pair splitting for the DF64 residual, norm reductions and
 // spectral-norm estimates of the coefficients.
+#include "device_common.cuh"
 #include "refine.h"
 
 namespace tsylv {
@@ -26,24 +27,23 @@ __global__ void k_split(const double* __restrict__ x, float* __restrict__ h, flo
     }
 }
 
-// r32 = r64 / max|r64|   (scale read from the device-side norm record)
+// r32 = r64 / s, s = the power of two at or above max|r64| (read from the
+// device-side norm record)
 __global__ void k_scale_to_f32(const double* __restrict__ r, float* __restrict__ r32, const double* __restrict__ nrm,
                                long long n) {
-    const double mx = nrm[1];
-    const double s = mx > 0 ? 1.0 / mx : 1.0;
+    const double s = 1.0 / dev::step_scale(nrm[1]);
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<long long>(gridDim.x) * blockDim.x)
         r32[i] = static_cast<float>(r[i] * s);
 }
 
-// x += max|r| * d32 (the correction of the scaled system), optional split of
+// x += s * d32 (the correction of the scaled system), optional split of
 // the new x, and per-block partial sums of x^2 into part[2*blk + 0] (the
 // residual kernels own part[.. + 0, 1] of another array).
 __global__ void k_update_x(double* __restrict__ x, const float* __restrict__ d32, const double* __restrict__ nrm,
                            float* __restrict__ xh, float* __restrict__ xl, double* __restrict__ xpart, long long n,
                            int td) {
-    const double mx = nrm[1];
-    const double s = mx > 0 ? mx : 1.0;
+    const double s = dev::step_scale(nrm[1]);
     for (long long blk = blockIdx.x; blk * td < n; blk += gridDim.x) {
         double ss = 0;
         for (int e = threadIdx.x; e < td; e += blockDim.x) {

@@ -167,6 +167,7 @@ struct Call {
     bool persistent = true;   // opts->schedule == 0
     int flow_grid = 0;        // CTAs of the persistent launch
     bool update = false;      // refinement step: residual updated from the FP32 correction
+    bool first = false;       // first refinement step (X = 0 before it: X after it is s D exactly)
     bool fused = false;       // full refinement step in one launch (Laplace form, DF64 residual, persistent)
     int fused_grid = 0;
 };
@@ -276,6 +277,9 @@ cudaError_t enqueue_residual(const Call& c, cudaStream_t s) {
     char* b = c.base;
     ApplyArgs a{};
     const bool up = c.update;
+    // first step from X = 0: X = s D with s a power of two, so A(X) = s A(D)
+    // is evaluated in DF64 on the float correction D itself
+    const bool fst = c.first && c.df && !up;
     for (int mu = 0; mu < p.d; mu++) {
         a.nb[mu] = p.nb[mu];
         a.tstride[mu] = p.tstride[mu];
@@ -295,14 +299,15 @@ cudaError_t enqueue_residual(const Call& c, cudaStream_t s) {
     a.ntiles = p.ntiles;
     a.B = reinterpret_cast<const double*>(b + (up ? R.Rt : R.Bt));
     a.R = reinterpret_cast<double*>(b + R.Rt);
-    a.scale = up ? reinterpret_cast<const double*>(b + R.nrm) : nullptr;
+    a.scale = up || fst ? reinterpret_cast<const double*>(b + R.nrm) : nullptr;
     a.part = reinterpret_cast<double*>(b + R.part);
     a.err = reinterpret_cast<int*>(b + R.L32.err);
     a.timeout_ns = kTimeoutNs;
-    const void* xs = up ? static_cast<const void*>(b + R.L32.X)
-                        : c.df ? static_cast<const void*>(b + R.Xh) : static_cast<const void*>(b + R.Xt);
-    const void* xsl = c.df && !up ? static_cast<const void*>(b + R.Xl) : nullptr;
+    const void* xs = up || fst ? static_cast<const void*>(b + R.L32.X)
+                               : c.df ? static_cast<const void*>(b + R.Xh) : static_cast<const void*>(b + R.Xt);
+    const void* xsl = c.df && !up && !fst ? static_cast<const void*>(b + R.Xl) : nullptr;
     auto launch = [&](const ApplyArgs& aa) {
+        if (fst && aa.s1l == nullptr) return launch_apply_dfh(p.d, aa, s);  // the levels reading D
         return up ? launch_apply_f32(p.d, aa, s) : c.df ? launch_apply<true>(p.d, aa, s) : launch_apply<false>(p.d, aa, s);
     };
     if (!p.gen) {
@@ -483,7 +488,8 @@ cudaError_t enqueue_ref_iter(const Call& c, cudaStream_t s) {
     }
     TRY(enqueue_waves<float>(c, L, s));
     // X += max|R| D  (FP64), its float-pair split, block sums of X^2
-    const bool split = c.df && !c.update;  // the float-pair X only feeds a full DF64 residual
+    // the float-pair X only feeds a full DF64 residual of a later step
+    const bool split = c.df && !c.update && !c.first;
     TRY(launch_update_x(reinterpret_cast<double*>(b + R.Xt), reinterpret_cast<float*>(b + L.X), nrm,
                         split ? reinterpret_cast<float*>(b + R.Xh) : nullptr,
                         split ? reinterpret_cast<float*>(b + R.Xl) : nullptr, reinterpret_cast<double*>(b + R.xpart),
@@ -632,6 +638,7 @@ int prepare_kernels() {
         if (e == cudaSuccess) e = prepare_apply<false>();
         if (e == cudaSuccess) e = prepare_apply<true>();
         if (e == cudaSuccess) e = prepare_apply_f32();
+        if (e == cudaSuccess) e = prepare_apply_dfh();
         if (e == cudaSuccess) e = prepare_batched<double>();
         if (e == cudaSuccess) e = prepare_batched<float>();
         if (e == cudaSuccess) e = prepare_fused();
@@ -865,8 +872,9 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
             // from the second step on, once the correction is small, the
             // residual is updated from the FP32 correction instead of re-evaluated
             if (o.resid_update == 0 && it > 0 && prev <= 1e-5) c.update = true;
-            st = run_enqueue(*c.plan, make_key(c, tagbase | 32 | (c.update ? 512 : 0)), o.use_graph != 0, stream,
-                             enqueue_ref_iter, c);
+            c.first = it == 0;
+            st = run_enqueue(*c.plan, make_key(c, tagbase | 32 | (c.update ? 512 : 0) | (c.first ? 2048 : 0)),
+                             o.use_graph != 0, stream, enqueue_ref_iter, c);
             if (st) return st;
             if ((e = cudaMemcpyAsync(hn, c.base + c.R.nrm, 3 * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
                 return cuda_fail(e, "read residual norm");
