@@ -173,6 +173,7 @@ def barrier(ws):
 SOLVE_PARTS = [("fp64_laplace", False, 0), ("fp64_generalized", True, 0),
                ("fp32r_laplace", False, 1), ("fp32r_generalized", True, 1)]
 ADJ_SHAPE = (200, 160, 120)
+D4_SHAPES = ((64, 64, 64, 64), (128, 96, 64, 32))
 BATCH = dict(count=512, lo=8, hi=48)
 
 
@@ -493,6 +494,42 @@ def run_ours(args, ws, rank, local):
                              "queue_order": ib.batch_order, "ctas_per_sm": ib.batch_ctas_per_sm}
     mixed_vs_fp64 = {"laplace": parts["fp64_laplace"]["ms"] / parts["fp32r_laplace"]["ms"],
                      "generalized": parts["fp64_generalized"]["ms"] / parts["fp32r_generalized"]["ms"]}
+
+    # ---- the other configurations, measured beside the step (not part of
+    # `value`): the d = 4 generalized form FP64 vs FP32-refined, and the
+    # 512-equation batch FP32-refined against its FP64 solutions
+    other = {}
+    if not args.no_other:
+        for shp in D4_SHAPES:
+            q = synthetic.problem(args.seed + rank, shp, generalized=True)
+            qA = [to_dev(a) for a in q["A"]]
+            qC = [to_dev(c) for c in q["C"]]
+            qB = to_dev(q["B"])
+            res = {}
+            for prec in (0, 1):
+                qX = ts.empty_fortran(shp, dev)
+                qi = _lib.Info()
+                fn = lambda: ts.gtsylv_solve(qA, qC, qB, X=qX, info=qi, precision=PREC[prec])
+                fn()
+                tm = event_ms(fn, 3)
+                _, rho, _ = ts.tsylv_residual(qA, qB, qX, qC, residual=_lib.TSYLV_RESID_FP64)
+                res["fp64" if prec == 0 else "fp32r"] = {"ms": tm, "iterations": qi.iterations,
+                                                         "rel_residual_fp64": rho}
+                del qX
+            res["mixed_vs_fp64"] = res["fp64"]["ms"] / res["fp32r"]["ms"]
+            other["d4_generalized_" + "x".join(str(v) for v in shp)] = res
+            del qA, qC, qB
+        X64 = pools.X.clone()
+        ir = _lib.Info()
+        fnr = lambda: pools.solve(info=ir, precision=_lib.TSYLV_FP32_REFINED)
+        fnr()
+        tr = event_ms(fnr, max(3, args.steps))
+        other["batched_fp32r"] = {
+            "ms": tr, "unknowns_per_s": units_rank["batched"] / (tr * 1e-3), "iterations": ir.iterations,
+            "mixed_vs_fp64": parts["batched_fp64"]["ms"] / tr,
+            "rel_diff_vs_fp64": float(torch.linalg.vector_norm(pools.X - X64) / torch.linalg.vector_norm(X64))}
+        pools.solve(info=infos["batched_fp64"])  # leave the FP64 solutions in place
+        del X64
     # the dominant kernel: the persistent FP64 solve of the generalized form,
     # one launch per solve; its duration is taken with CUDA events recorded on
     # the launching stream around the launch inside the captured graph
@@ -583,6 +620,7 @@ def run_ours(args, ws, rank, local):
                    "units_per_step": units_rank},
         "parts": parts,
         "mixed_vs_fp64": mixed_vs_fp64,
+        "other_configs": other,
         "roofline": roofline,
         "e2e": {"value": units / (e2e_ms * 1e-3), "unit": "unknowns/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
@@ -613,6 +651,8 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the measurements of the d = 4 and batched FP32-refined configurations")
     ap.add_argument("--fp64-peak", action="store_true", help="build and run the FP64 throughput probe")
     ap.add_argument("--only", default=None,
                     help="profiling aid: run just this part of the step (e.g. fp64_generalized) for the warm-up "

@@ -482,25 +482,32 @@ __device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e,
         const int k0 = sm.gs[mu * TE + g[mu]] + sm.gl[mu * TE + g[mu]];  // first index beyond the group
         const int kb = sm.bs[mu];
         T a0 = 0, a1 = 0, b0 = 0, b1 = 0, c0 = 0, c1 = 0;
-#pragma unroll 2
-        for (int k = k0; k < kb; k++) {
-            const int v = e + (k - u[mu]) * st;
-            const T dv = sm.Ds[mu * TC + u[mu] + TE * k];
+        // FP32: all TE terms with the coefficients before k0 masked to zero
+        // (positions beyond the block extent hold zeros), fully unrolled so
+        // that every load is in flight at once; FP64: only the terms needed
+        // (the FP64 pipe is the scarce resource there)
+        constexpr bool FULL = sizeof(T) == 4;
+        const int klo = FULL ? 0 : k0, khi = FULL ? TE : kb;
+#pragma unroll(FULL ? TE : 2)
+        for (int k = klo; k < khi; k++) {
+            const bool in = !FULL || k >= k0;
+            const int v = in ? e + (k - u[mu]) * st : e;
+            const T dv = in ? sm.Ds[mu * TC + u[mu] + TE * k] : T(0);
             const bool odd = k & 1;
             if constexpr (!GEN) {
-                const T t = dv * Xs[v];
+                const T t = dv * (in ? Xs[v] : T(0));
                 if (odd) a1 += t; else a0 += t;
             } else {
-                const T ev = sm.Es[mu * TC + u[mu] + TE * k];
+                const T ev = in ? sm.Es[mu * TC + u[mu] + TE * k] : T(0);
                 if (mu == D - 1) {
-                    const T xv = Xs[v];
+                    const T xv = in ? Xs[v] : T(0);
                     if (odd) { a1 += ev * xv; b1 += dv * xv; } else { a0 += ev * xv; b0 += dv * xv; }
                 } else if (mu >= 1) {
-                    const T pv = sm.Pin[mu * TD + v], gv = sm.Gin[mu * TD + v];  // level mu + 1
+                    const T pv = in ? sm.Pin[mu * TD + v] : T(0), gv = in ? sm.Gin[mu * TD + v] : T(0);  // level mu + 1
                     if (odd) { a1 += ev * pv; b1 += ev * gv; c1 += dv * pv; }
                     else { a0 += ev * pv; b0 += ev * gv; c0 += dv * pv; }
                 } else {
-                    const T pv = sm.Pin[v], gv = sm.Gin[v];                       // level 1
+                    const T pv = in ? sm.Pin[v] : T(0), gv = in ? sm.Gin[v] : T(0);                       // level 1
                     if (odd) { a1 += ev * gv; b1 += dv * pv; } else { a0 += ev * gv; b0 += dv * pv; }
                 }
             }
@@ -795,11 +802,11 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         int L, Jp;
         job(j0 + jj, L, Jp);
         dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE);
+        // every thread is done reading the stage (the barrier orders those
+        // reads before the copies that refill it, as for a consumer-release
+        // mbarrier arrival)
         __syncthreads();
-        if (tid == 0 && jj + NST < njob) {
-            dev::fence_proxy_async();
-            issue(j0 + jj + NST, stg);
-        }
+        if (tid == 0 && jj + NST < njob) issue(j0 + jj + NST, stg);
     }
     if (dead && tid == 0) {
         // let copies still in flight land before the buffers go away (bounded);
