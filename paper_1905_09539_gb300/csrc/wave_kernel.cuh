@@ -487,9 +487,9 @@ __device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e,
         // that every load is in flight at once; FP64: only the terms needed
         // (the FP64 pipe is the scarce resource there)
         constexpr bool FULL = sizeof(T) == 4;
-        const int klo = FULL ? 0 : k0, khi = FULL ? TE : kb;
-#pragma unroll(FULL ? TE : 2)
-        for (int k = klo; k < khi; k++) {
+#pragma unroll
+        for (int k = 0; k < TE; k++) {
+            if (!FULL && (k < k0 || k >= kb)) continue;
             const bool in = !FULL || k >= k0;
             const int v = in ? e + (k - u[mu]) * st : e;
             const T dv = in ? sm.Ds[mu * TC + u[mu] + TE * k] : T(0);
