@@ -45,13 +45,11 @@ __global__ void __launch_bounds__(kThreads, WaveCfg<T, D, GENF>::MINB) k_batched
         }
         __syncthreads();
         if (alive && s_ok) alive = wave_tile<T, D, GENF>(a, jb.tile, 0, 1, uses, bar);
-        // publish the block: every thread's stores, then the count / flag (release)
-        __threadfence();
+        // publish the block: every thread's stores, then the count / flag
+        // (one release by one thread after the barrier)
         __syncthreads();
-        if (threadIdx.x == 0) {
-            if (b.done) atomicAdd(&b.done[jb.eq], 1);
-            if (a.ready) dev::st_release(const_cast<int*>(a.ready) + jb.tile, 1);
-        }
+        if (threadIdx.x == 0)
+            dev::publish(a.ready ? const_cast<int*>(a.ready) + jb.tile : nullptr, 1, b.done ? &b.done[jb.eq] : nullptr);
     }
 }
 

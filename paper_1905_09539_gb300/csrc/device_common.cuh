@@ -107,22 +107,52 @@ __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(int* p, int v) {
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_relaxed_add(int* p, int v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Acquire-release fence at GPU scope: after a relaxed load that saw a flag
+// it completes an acquire; before relaxed stores it makes them a release
+// (cumulative: it covers what the CTA's barrier ordered before it).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Publish a CTA's results: after a barrier of the CTA, one thread makes every
+// thread's earlier stores visible at GPU scope before the flag (and counter).
+__device__ __forceinline__ void publish(int* flag, int v, int* counter) {
+    fence_acq_rel_gpu();
+    if (counter) red_relaxed_add(counter, 1);
+    if (flag) st_relaxed(flag, v);
+}
+
 // Order earlier generic-proxy accesses (including what an acquire made
 // visible) before later bulk copies, in every state space.
 __device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
-// Wait (bounded) until *p >= need.  A timeout raises *abort, which makes
+// Wait (bounded) until *p >= need: relaxed polls (one L2 round trip each,
+// no sleep), then an acquire fence.  A timeout raises *abort, which makes
 // every later wait of the launch give up at once.  Returns false on either.
 __device__ __forceinline__ bool wait_at_least(const int* p, int need, int* abort, long long timeout_ns) {
     if (ld_acquire(p) >= need) return true;
     const unsigned long long t0 = global_ns();
-    while (ld_acquire(p) < need) {
-        if (ld_acquire(abort) || static_cast<long long>(global_ns() - t0) > timeout_ns) {
+    for (unsigned it = 1;; it++) {
+        if (ld_relaxed(p) >= need) break;
+        if ((it & 15u) == 0 &&
+            (ld_relaxed(abort) || static_cast<long long>(global_ns() - t0) > timeout_ns)) {
             atomicExch(abort, 1);
             return false;
         }
-        __nanosleep(64);
     }
+    fence_acq_rel_gpu();
     return true;
 }
 

@@ -790,65 +790,11 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         dev::fence_proxy_async_all();
         for (int q = 0; q < NST && q < njob; q++) issue(j0 + q, q);
     }
-    bool dead = false;
-    for (int jj = 0; jj < njob && !dead; jj++) {
-        const int stg = jj % NST;
-        const bool ok = dev::mbar_wait(&bar[stg], (uses[stg] + static_cast<uint32_t>(jj / NST)) & 1u, a.timeout_ns);
-        if (__syncthreads_or(!ok)) {
-            dead = true;
-            if (tid == 0) atomicOr(a.err, kErrTimeout);
-            break;
-        }
-        int L, Jp;
-        job(j0 + jj, L, Jp);
-        dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE);
-        // every thread is done reading the stage (the barrier orders those
-        // reads before the copies that refill it, as for a consumer-release
-        // mbarrier arrival)
-        __syncthreads();
-        if (tid == 0 && jj + NST < njob) issue(j0 + jj + NST, stg);
-    }
-    if (dead && tid == 0) {
-        // let copies still in flight land before the buffers go away (bounded);
-        // the block is finished with whatever it holds (the error word is set)
-        for (int q = 0; q < NST && q < njob; q++) (void)dev::mbar_wait(&bar[q], uses[q] & 1u, a.timeout_ns / 8);
-    }
-#pragma unroll
-    for (int q = 0; q < NST; q++) uses[q] += static_cast<uint32_t>((njob - q + NST - 1) / NST);
-
-    // ---- partial sums -> shared memory, cluster reduction into rank 0
-#pragma unroll
-    for (int s = 0; s < NACC; s++)
-#pragma unroll
-        for (int q = 0; q < EPT; q++) {
-            const int e = tid + q * kThreads;
-            if ((TD % kThreads) == 0 || e < TD) red[s * TD + e] = acc[s][q];
-        }
-    if (csize > 1) {
-        dev::cluster_sync();
-        if (rank == 0) {
-            for (int r = 1; r < csize; r++) {
-#pragma unroll
-                for (int s = 0; s < NACC; s++)
-#pragma unroll
-                    for (int q = 0; q < EPT; q++) {
-                        const int e = tid + q * kThreads;
-                        if ((TD % kThreads) == 0 || e < TD) acc[s][q] += dev::ld_dsmem(&red[s * TD + e], r);
-                    }
-            }
-#pragma unroll
-            for (int s = 0; s < NACC; s++)
-#pragma unroll
-                for (int q = 0; q < EPT; q++) {
-                    const int e = tid + q * kThreads;
-                    if ((TD % kThreads) == 0 || e < TD) red[s * TD + e] = acc[s][q];
-                }
-        }
-        dev::cluster_sync();
-        if (rank != 0) return !dead;
-    }
-
-    // ---- rank 0: base case of block T
+    // ---- base case of block T, the part that depends only on the diagonal
+    // blocks of the coefficients (done while the first copies are in flight,
+    // so that only the rest follows the wait for the nearest source blocks):
+    // diagonal tiles, right-hand side, 2x2 group structure, reciprocal
+    // diagonal, the anti-diagonal buckets and the coupled-group list
     T* Rs = sbase + C::oR;
     T* Xs = sbase + C::oX;
     T* Rd = sbase + C::oRd;
@@ -902,75 +848,10 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         for (int k = b; k < TE; k++) gidx[mu * TE + k] = 0;
         ng[mu] = n;
     }
-    if constexpr (GEN) {
-        // Horner chain over the diagonal blocks (levels d-2 .. 1), then the
-        // mode-1 level: off(T) = A(X with block T set to zero) restricted to T.
-#pragma unroll
-        for (int l = D - 2; l >= 1; l--) {
-            __syncthreads();
-            const int st = ipow(TE, l);
-            const T* Pn = red + C::slotP(l + 1) * TD;
-            const T* Gn = red + C::slotG(l + 1) * TD;
-            T vp[EPT], vg[EPT];
-#pragma unroll
-            for (int q = 0; q < EPT; q++) {
-                const int e = tid + q * kThreads;
-                vp[q] = T(0); vg[q] = T(0);
-                if ((TD % kThreads) != 0 && e >= TD) continue;
-                const int i = (e / st) % TE, base = e - i * st;
-                T p = red[C::slotP(l) * TD + e], g = red[C::slotG(l) * TD + e];
-                for (int k = 0; k < TE; k++) {
-                    const T ev = Es[l * TC + i + TE * k], dv = Ds[l * TC + i + TE * k];
-                    const T pv = Pn[base + k * st], gv = Gn[base + k * st];
-                    p += ev * pv;
-                    g += ev * gv + dv * pv;
-                }
-                vp[q] = p; vg[q] = g;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < EPT; q++) {
-                const int e = tid + q * kThreads;
-                if ((TD % kThreads) != 0 && e >= TD) continue;
-                red[C::slotP(l) * TD + e] = vp[q];
-                red[C::slotG(l) * TD + e] = vg[q];
-            }
-        }
-        __syncthreads();
-        {
-            const T* Pn = red + C::slotP(1) * TD;
-            const T* Gn = red + C::slotG(1) * TD;
-            for (int e = tid; e < TD; e += kThreads) {
-                const int i = e % TE, base = e - i;
-                T off = red[(NACC - 1) * TD + e];
-                for (int k = 0; k < TE; k++) off += Es[i + TE * k] * Gn[base + k] + Ds[i + TE * k] * Pn[base + k];
-                Rs[e] -= off;
-            }
-        }
-    } else {
-        for (int e = tid; e < TD; e += kThreads) Rs[e] -= red[e];
-    }
-    __syncthreads();
-    if constexpr (GEN) {
-        // park the level sums of the block updates in the output blocks (the
-        // in-block parts are added at the end), freeing `red` for Lin
-#pragma unroll
-        for (int l = 1; l < D; l++) {
-            T* Pg = static_cast<T*>(a.P[l]) + t * TD;
-            T* Gg = static_cast<T*>(a.G[l]) + t * TD;
-            for (int e = tid; e < TD; e += kThreads) {
-                Pg[e] = red[C::slotP(l) * TD + e];
-                Gg[e] = red[C::slotG(l) * TD + e];
-            }
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < NACC * TD; e += kThreads) Lin[e] = T(0);
-
-    // ---- back-substitution over coupled groups in anti-diagonal order.
+    __syncthreads();  // the group tables are read by every thread below
     // Every thread owns the elements e = tid + q*kThreads: it solves those
     // that are 1x1 groups (or leads a coupled group) when their anti-diagonal
-    // comes, and keeps their running line sums current.
+    // comes.
     int status = 0;
     int uq[EPT][D], gq[EPT][D], sq[EPT];
     bool okq[EPT], lead[EPT], single[EPT];
@@ -1064,6 +945,132 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         }
     }
     __syncthreads();
+    bool dead = false;
+    for (int jj = 0; jj < njob && !dead; jj++) {
+        const int stg = jj % NST;
+        const bool ok = dev::mbar_wait(&bar[stg], (uses[stg] + static_cast<uint32_t>(jj / NST)) & 1u, a.timeout_ns);
+        if (__syncthreads_or(!ok)) {
+            dead = true;
+            if (tid == 0) atomicOr(a.err, kErrTimeout);
+            break;
+        }
+        int L, Jp;
+        job(j0 + jj, L, Jp);
+        dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE);
+        // every thread is done reading the stage (the barrier orders those
+        // reads before the copies that refill it, as for a consumer-release
+        // mbarrier arrival)
+        __syncthreads();
+        if (tid == 0 && jj + NST < njob) issue(j0 + jj + NST, stg);
+    }
+    if (dead && tid == 0) {
+        // let copies still in flight land before the buffers go away (bounded);
+        // the block is finished with whatever it holds (the error word is set)
+        for (int q = 0; q < NST && q < njob; q++) (void)dev::mbar_wait(&bar[q], uses[q] & 1u, a.timeout_ns / 8);
+    }
+#pragma unroll
+    for (int q = 0; q < NST; q++) uses[q] += static_cast<uint32_t>((njob - q + NST - 1) / NST);
+
+    // ---- partial sums -> shared memory, cluster reduction into rank 0
+#pragma unroll
+    for (int s = 0; s < NACC; s++)
+#pragma unroll
+        for (int q = 0; q < EPT; q++) {
+            const int e = tid + q * kThreads;
+            if ((TD % kThreads) == 0 || e < TD) red[s * TD + e] = acc[s][q];
+        }
+    if (csize > 1) {
+        dev::cluster_sync();
+        if (rank == 0) {
+            for (int r = 1; r < csize; r++) {
+#pragma unroll
+                for (int s = 0; s < NACC; s++)
+#pragma unroll
+                    for (int q = 0; q < EPT; q++) {
+                        const int e = tid + q * kThreads;
+                        if ((TD % kThreads) == 0 || e < TD) acc[s][q] += dev::ld_dsmem(&red[s * TD + e], r);
+                    }
+            }
+#pragma unroll
+            for (int s = 0; s < NACC; s++)
+#pragma unroll
+                for (int q = 0; q < EPT; q++) {
+                    const int e = tid + q * kThreads;
+                    if ((TD % kThreads) == 0 || e < TD) red[s * TD + e] = acc[s][q];
+                }
+        }
+        dev::cluster_sync();
+        if (rank != 0) return !dead;
+    }
+
+    // ---- base case, the rest: right-hand side minus the block updates, then
+    // back-substitution over the coupled groups in anti-diagonal order
+    __syncthreads();
+    if constexpr (GEN) {
+        // Horner chain over the diagonal blocks (levels d-2 .. 1), then the
+        // mode-1 level: off(T) = A(X with block T set to zero) restricted to T.
+#pragma unroll
+        for (int l = D - 2; l >= 1; l--) {
+            __syncthreads();
+            const int st = ipow(TE, l);
+            const T* Pn = red + C::slotP(l + 1) * TD;
+            const T* Gn = red + C::slotG(l + 1) * TD;
+            T vp[EPT], vg[EPT];
+#pragma unroll
+            for (int q = 0; q < EPT; q++) {
+                const int e = tid + q * kThreads;
+                vp[q] = T(0); vg[q] = T(0);
+                if ((TD % kThreads) != 0 && e >= TD) continue;
+                const int i = (e / st) % TE, base = e - i * st;
+                T p = red[C::slotP(l) * TD + e], g = red[C::slotG(l) * TD + e];
+                for (int k = 0; k < TE; k++) {
+                    const T ev = Es[l * TC + i + TE * k], dv = Ds[l * TC + i + TE * k];
+                    const T pv = Pn[base + k * st], gv = Gn[base + k * st];
+                    p += ev * pv;
+                    g += ev * gv + dv * pv;
+                }
+                vp[q] = p; vg[q] = g;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < EPT; q++) {
+                const int e = tid + q * kThreads;
+                if ((TD % kThreads) != 0 && e >= TD) continue;
+                red[C::slotP(l) * TD + e] = vp[q];
+                red[C::slotG(l) * TD + e] = vg[q];
+            }
+        }
+        __syncthreads();
+        {
+            const T* Pn = red + C::slotP(1) * TD;
+            const T* Gn = red + C::slotG(1) * TD;
+            for (int e = tid; e < TD; e += kThreads) {
+                const int i = e % TE, base = e - i;
+                T off = red[(NACC - 1) * TD + e];
+                for (int k = 0; k < TE; k++) off += Es[i + TE * k] * Gn[base + k] + Ds[i + TE * k] * Pn[base + k];
+                Rs[e] -= off;
+            }
+        }
+    } else {
+        for (int e = tid; e < TD; e += kThreads) Rs[e] -= red[e];
+    }
+    __syncthreads();
+    if constexpr (GEN) {
+        // park the level sums of the block updates in the output blocks (the
+        // in-block parts are added at the end), freeing `red` for Lin
+#pragma unroll
+        for (int l = 1; l < D; l++) {
+            T* Pg = static_cast<T*>(a.P[l]) + t * TD;
+            T* Gg = static_cast<T*>(a.G[l]) + t * TD;
+            for (int e = tid; e < TD; e += kThreads) {
+                Pg[e] = red[C::slotP(l) * TD + e];
+                Gg[e] = red[C::slotG(l) * TD + e];
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < NACC * TD; e += kThreads) Lin[e] = T(0);
+
     TileSmem<T, D, GEN> sm{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
     for (int i = tid; i < ncg; i += kThreads)
         if (cg_moff[i] >= 0) status |= group_inverse<T, D, GEN>(sm, cg_list[i], Minv + cg_moff[i]);
