@@ -510,65 +510,115 @@ def run_ours(args, ws, rank, local):
                 "per_launch_gflop": f_dom / 1e9, "per_launch_ms": w_dom}
 
     # ---- end to end through the public API: pinned host buffers, H2D of every
-    # input and D2H of every result inside the timed region
-    host = {}
-    h2d = d2h = 0
+    # input and D2H of every result inside the timed region.  The copies run on
+    # a copy stream, overlapped with the solves of the other parts (every part
+    # has its own device inputs and outputs; events order each copy against
+    # the solve that produces or consumes its buffer)
     rev = lambda t: t.permute(*range(t.dim() - 1, -1, -1))
-    for gen in (False, True):
-        pr = probs[gen]
-        hb = rev(torch.empty(pr["B"].shape[::-1], dtype=torch.float64).pin_memory())
-        hb.copy_(pr["B"])
-        hA = [a.cpu().pin_memory() for a in pr["A"]]
-        hC = [c.cpu().pin_memory() for c in pr["C"]] if gen else []
-        hx = rev(torch.empty(pr["B"].shape[::-1], dtype=torch.float64).pin_memory())
-        host[gen] = (hb, hA, hC, hx)
+
+    def pinned_like(t):
+        if t.dim() >= 2:
+            h = rev(torch.empty(t.shape[::-1], dtype=t.dtype).pin_memory())
+        else:
+            h = torch.empty(t.shape, dtype=t.dtype).pin_memory()
+        h.copy_(t)
+        return h
+
+    def dev_like(t):
+        return torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=dev)
+
+    jobs = []  # (inputs [(host, device)], run(), outputs() -> [device tensors], host outputs)
     for name, gen, prec in SOLVE_PARTS:
-        hb, hA, hC, hx = host[gen]
-        h2d += hb.numel() * 8 + sum(a.numel() * 8 for a in hA) + sum(c.numel() * 8 for c in hC)
-        d2h += hx.numel() * 8
-    hadj_B = rev(torch.empty(ADJ_SHAPE[::-1], dtype=torch.float64).pin_memory())
-    hadj_B.copy_(adj["B"])
-    hadj_Xs = rev(torch.empty(ADJ_SHAPE[::-1], dtype=torch.float64).pin_memory())
-    hadj_Xs.copy_(adj["Xs"])
-    hadj_A = [a.cpu().pin_memory() for a in adj["A"]]
-    hadj_dB = rev(torch.empty(ADJ_SHAPE[::-1], dtype=torch.float64).pin_memory())
-    hadj_dA = [torch.empty(a.shape, dtype=torch.float64).pin_memory() for a in adj["A"]]
-    h2d += 2 * (hadj_B.numel() * 8 + hadj_Xs.numel() * 8 + sum(a.numel() * 8 for a in hadj_A))
-    d2h += 2 * (hadj_dB.numel() * 8 + sum(a.numel() * 8 for a in hadj_dA))
-    hpB = pools.B.cpu().pin_memory()
-    hpA = pools.A.cpu().pin_memory()
-    hpX = torch.empty_like(hpB).pin_memory()
-    h2d += hpB.numel() * 8 + hpA.numel() * 8
-    d2h += hpX.numel() * 8
+        pr = probs[gen]
+        dA = [dev_like(a) for a in pr["A"]]
+        dC = [dev_like(c) for c in pr["C"]] if gen else None
+        dB = dev_like(pr["B"])
+        dXo = ts.empty_fortran(tuple(pr["B"].shape), dev)
+        ins = [(pinned_like(pr["B"]), dB)] + [(pinned_like(a), d) for a, d in zip(pr["A"], dA)]
+        if gen:
+            ins += [(pinned_like(c), d) for c, d in zip(pr["C"], dC)]
+
+        def run(gen=gen, prec=prec, dA=dA, dC=dC, dB=dB, dXo=dXo, name=name):
+            if gen:
+                ts.gtsylv_solve(dA, dC, dB, X=dXo, info=infos[name], precision=PREC[prec])
+            else:
+                ts.tsylv_solve(dA, dB, X=dXo, info=infos[name], precision=PREC[prec])
+            return [dXo]
+        jobs.append((ins, run, [pinned_like(dXo)]))
+    for prec in (0, 1):
+        tag = "adjoint_fp64" if prec == 0 else "adjoint_fp32r"
+        dA = [dev_like(a) for a in adj["A"]]
+        dB = dev_like(adj["B"])
+        dXs = dev_like(adj["Xs"])
+        Xa = ts.empty_fortran(ADJ_SHAPE, dev)
+        ins = [(pinned_like(adj["B"]), dB), (pinned_like(adj["Xs"]), dXs)] + \
+              [(pinned_like(a), d) for a, d in zip(adj["A"], dA)]
+
+        gX = ts.empty_fortran(ADJ_SHAPE, dev)
+        gB = ts.empty_fortran(ADJ_SHAPE, dev)
+        gA = [ts.empty_fortran((m, m), dev) for m in ADJ_SHAPE]
+
+        def run(prec=prec, tag=tag, dA=dA, dB=dB, dXs=dXs, Xa=Xa, gX=gX, gB=gB, gA=gA):
+            ts.tsylv_solve(dA, dB, X=Xa, info=infos[tag + "_fwd"], precision=PREC[prec])
+            torch.sub(Xa, dXs, out=gX)
+            ts.tsylv_backward(dA, Xa, gX, want_dB=True, want_dA=True, info=infos[tag + "_bwd"],
+                              precision=PREC[prec], out=(gB, gA, None))
+            return [gB] + gA
+        outs_h = [pinned_like(adj["out"][prec][0])] + [pinned_like(g) for g in adj["out"][prec][1]]
+        jobs.append((ins, run, outs_h))
+    ins = [(pinned_like(pools.B), pools.B), (pinned_like(pools.A), pools.A)]
+
+    def run_batch():
+        batched()
+        return [pools.X]
+    jobs.append((ins, run_batch, [pinned_like(pools.X)]))
+    h2d = sum(h.numel() * h.element_size() for ins, _, _ in jobs for h, _ in ins)
+    d2h = sum(h.numel() * h.element_size() for _, _, outs in jobs for h in outs)
+
+    cs = torch.cuda.Stream(dev)
+    ev_in = [torch.cuda.Event() for _ in jobs]     # inputs of job k on the device
+    ev_run = [torch.cuda.Event() for _ in jobs]    # job k's solve done
+    ev_out = [torch.cuda.Event() for _ in jobs]    # job k's results on the host
+    ev_done = torch.cuda.Event()
+
+    def copy_in(k):
+        with torch.cuda.stream(cs):
+            for h, d in jobs[k][0]:
+                d.copy_(h, non_blocking=True)
+            ev_in[k].record(cs)
+
+    def e2e_step(first):
+        # every step copies its own inputs in and its results out
+        if not first:
+            cs.wait_event(ev_run[0])  # the previous step's job 0 is done with its inputs
+        copy_in(0)
+        for k, (ins, run, outs_h) in enumerate(jobs):
+            if k + 1 < len(jobs):
+                if not first:
+                    cs.wait_event(ev_run[k + 1])
+                copy_in(k + 1)  # prefetched while job k runs
+            stream.wait_event(ev_in[k])
+            if not first:
+                stream.wait_event(ev_out[k])  # the previous step's results of job k are on the host
+            outs_d = run()
+            ev_run[k].record(stream)
+            with torch.cuda.stream(cs):
+                cs.wait_event(ev_run[k])
+                for h, d in zip(outs_h, outs_d):
+                    h.copy_(d, non_blocking=True)
+                ev_out[k].record(cs)
+
+    # one untimed pass (first=True) so that the graphs for the new buffers exist
+    e2e_step(True)
+    torch.cuda.synchronize(dev)
     barrier(ws)
     torch.cuda.synchronize(dev)
     e0.record(stream)
+    cs.wait_event(e0)
     for _ in range(args.steps):
-        for name, gen, prec in SOLVE_PARTS:
-            pr = probs[gen]
-            hb, hA, hC, hx = host[gen]
-            pr["B"].copy_(hb, non_blocking=True)
-            for a, h in zip(pr["A"], hA):
-                a.copy_(h, non_blocking=True)
-            if gen:
-                for c, h in zip(pr["C"], hC):
-                    c.copy_(h, non_blocking=True)
-            solve(name, gen, prec)
-            hx.copy_(pr["X"][prec], non_blocking=True)
-        for prec in (0, 1):
-            adj["B"].copy_(hadj_B, non_blocking=True)
-            adj["Xs"].copy_(hadj_Xs, non_blocking=True)
-            for a, h in zip(adj["A"], hadj_A):
-                a.copy_(h, non_blocking=True)
-            adjoint(prec)
-            dB, dA, _ = adj["out"][prec]
-            hadj_dB.copy_(dB, non_blocking=True)
-            for h, g in zip(hadj_dA, dA):
-                h.copy_(g, non_blocking=True)
-        pools.B.copy_(hpB, non_blocking=True)
-        pools.A.copy_(hpA, non_blocking=True)
-        batched()
-        hpX.copy_(pools.X, non_blocking=True)
+        e2e_step(False)
+    ev_done.record(cs)
+    stream.wait_event(ev_done)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(ws)

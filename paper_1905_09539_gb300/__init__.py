@@ -184,9 +184,21 @@ def tsylv_residual(A, B, X, C=None, R=None, *, opts=None, check=True, stream=Non
     return R, rel.value, st
 
 
+def _out_buffer(t, shape, device, what):
+    if tuple(t.shape) != tuple(shape) or t.dtype != torch.float64 or t.device != torch.device(device) or \
+            not is_fortran(t):
+        raise ValueError("tsylv_backward: out %s must be a column-major float64 tensor of shape %s on %s"
+                         % (what, tuple(shape), device))
+    return t
+
+
 def tsylv_backward(A, X, dX, C=None, *, want_dB=True, want_dA=True, want_dC=True, opts=None, check=True,
-                   stream=None, info=None, **kw):
-    """(dB, dA list, dC list) of a scalar loss with gradient dX at the solution X."""
+                   stream=None, info=None, out=None, **kw):
+    """(dB, dA list, dC list) of a scalar loss with gradient dX at the solution X.
+
+    out: optional (dB, dA list, dC list) of column-major float64 device tensors
+    to write the requested gradients into (entries for gradients not requested
+    may be None), so that repeated calls allocate nothing."""
     lib = load()
     _check_cuda(X, dX, *A, *(C or []))
     o = _opts(opts, kw)
@@ -198,9 +210,21 @@ def tsylv_backward(A, X, dX, C=None, *, want_dB=True, want_dA=True, want_dC=True
     gen = C is not None
     if gen:
         C_, pc = _mats(C)
-    dB = empty_fortran(X.shape, X.device) if want_dB else None
-    dA = [empty_fortran((m, m), X.device) for m in X.shape] if want_dA else None
-    dC = [empty_fortran((m, m), X.device) for m in X.shape] if (gen and want_dC) else None
+    oB, oA, oC = out if out is not None else (None, None, None)
+    if want_dB:
+        dB = _out_buffer(oB, X.shape, X.device, "dB") if oB is not None else empty_fortran(X.shape, X.device)
+    else:
+        dB = None
+    if want_dA:
+        dA = [_out_buffer(t, (m, m), X.device, "dA") for t, m in zip(oA, X.shape)] if oA is not None else \
+            [empty_fortran((m, m), X.device) for m in X.shape]
+    else:
+        dA = None
+    if gen and want_dC:
+        dC = [_out_buffer(t, (m, m), X.device, "dC") for t, m in zip(oC, X.shape)] if oC is not None else \
+            [empty_fortran((m, m), X.device) for m in X.shape]
+    else:
+        dC = None
     pdA = (ctypes.c_void_p * d)(*[t.data_ptr() for t in dA]) if dA else None
     pdC = (ctypes.c_void_p * d)(*[t.data_ptr() for t in dC]) if dC else None
     n = _dims(X.shape)

@@ -158,6 +158,27 @@ __device__ __forceinline__ void dispatch_job(int level, T (&acc)[WaveCfg<T, D, G
     }
 }
 
+// Packed per-element data of the back-substitution, built once per block:
+// the in-block element (12 bits), whether it belongs to a coupled group, and
+// for every mode the first in-block index beyond the element's group (the
+// start of its line sums), so that a step reads no group tables.
+template <int D>
+struct ElemCode {
+    static constexpr int TE = tile_extent(D);
+    static constexpr int KB = TE >= 32 ? 6 : TE >= 16 ? 5 : TE >= 8 ? 4 : 3;  // bits of a value in [0, TE]
+    static_assert(ipow(TE, D) <= 4096 && 13 + KB * D <= 31, "element code does not fit in 31 bits");
+    template <typename F>
+    __device__ static int make(int e, bool coupled, F k0_of) {
+        int c = e | (coupled ? 1 << 12 : 0);
+#pragma unroll
+        for (int mu = 0; mu < D; mu++) c |= k0_of(mu) << (13 + KB * mu);
+        return c;
+    }
+    __device__ static int elem(int c) { return c & 0xfff; }
+    __device__ static bool coupled(int c) { return (c >> 12) & 1; }
+    __device__ static int k0(int c, int mu) { return (c >> (13 + KB * mu)) & ((1 << KB) - 1); }
+};
+
 template <typename T, int D, bool GEN>
 struct TileSmem {
     const T* Ds;   // [D][TC] diagonal tiles of A
@@ -468,7 +489,7 @@ __device__ int warp_group(const TileSmem<T, D, GEN>& sm, int e, const T* minv) {
 // recurrence).  The modes are independent and each sum runs as two
 // interleaved chains, so the latency is that of a few multiply-adds.
 template <typename T, int D, bool GEN>
-__device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e, const int (&u)[D], const int (&g)[D],
+__device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e, const int (&u)[D], const int (&k0s)[D],
                                            T (&L)[WaveCfg<T, D, GEN>::NACC]) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
@@ -479,7 +500,7 @@ __device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e,
 #pragma unroll
     for (int mu = 0; mu < D; mu++) {
         const int st = ipow(TE, mu);
-        const int k0 = sm.gs[mu * TE + g[mu]] + sm.gl[mu * TE + g[mu]];  // first index beyond the group
+        const int k0 = k0s[mu];  // first index beyond e's group along mode mu
         const int kb = sm.bs[mu];
         T a0 = 0, a1 = 0, b0 = 0, b1 = 0, c0 = 0, c1 = 0;
         // FP32: all TE terms with the coefficients before k0 masked to zero
@@ -823,7 +844,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     int* act_cnt = cg_moff + (TD / 2 + 1);  // elements per anti-diagonal
     int* act_off = act_cnt + C::MAXSTEP;
     int* act_fill = act_off + C::MAXSTEP + 1;
-    int* act_list = act_fill + C::MAXSTEP;  // element | (member of a coupled group) << 16
+    int* act_list = act_fill + C::MAXSTEP;  // element codes (ElemCode)
     T* Minv = sbase + C::oMinv;
     for (int i = tid; i < C::MAXSTEP; i += kThreads) { cg_cnt[i] = 0; cg_fill[i] = 0; act_cnt[i] = 0; act_fill[i] = 0; }
     if (GEN)
@@ -920,7 +941,8 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     for (int q = 0; q < EPT; q++) {
         if (lead[q]) cg_list[cg_off[sq[q]] + atomicAdd(&cg_fill[sq[q]], 1)] = tid + q * kThreads;
         if (okq[q])
-            act_list[act_off[sq[q]] + atomicAdd(&act_fill[sq[q]], 1)] = (tid + q * kThreads) | (single[q] ? 0 : 1 << 16);
+            act_list[act_off[sq[q]] + atomicAdd(&act_fill[sq[q]], 1)] = ElemCode<D>::make(
+                tid + q * kThreads, !single[q], [&](int mu) { return gs[mu * TE + gq[q][mu]] + gl[mu * TE + gq[q][mu]]; });
     }
     __syncthreads();
     // inverses of the coupled groups with <= 4 members (the system depends only
@@ -971,14 +993,17 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
 #pragma unroll
     for (int q = 0; q < NST; q++) uses[q] += static_cast<uint32_t>((njob - q + NST - 1) / NST);
 
-    // ---- partial sums -> shared memory, cluster reduction into rank 0
+    // ---- partial sums -> shared memory (the generalized form's Horner chain
+    // mixes elements; a cluster reduces through it), cluster reduction into rank 0
+    if (GEN || csize > 1) {
 #pragma unroll
-    for (int s = 0; s < NACC; s++)
+        for (int s = 0; s < NACC; s++)
 #pragma unroll
-        for (int q = 0; q < EPT; q++) {
-            const int e = tid + q * kThreads;
-            if ((TD % kThreads) == 0 || e < TD) red[s * TD + e] = acc[s][q];
-        }
+            for (int q = 0; q < EPT; q++) {
+                const int e = tid + q * kThreads;
+                if ((TD % kThreads) == 0 || e < TD) red[s * TD + e] = acc[s][q];
+            }
+    }
     if (csize > 1) {
         dev::cluster_sync();
         if (rank == 0) {
@@ -1005,8 +1030,8 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
 
     // ---- base case, the rest: right-hand side minus the block updates, then
     // back-substitution over the coupled groups in anti-diagonal order
-    __syncthreads();
     if constexpr (GEN) {
+        __syncthreads();
         // Horner chain over the diagonal blocks (levels d-2 .. 1), then the
         // mode-1 level: off(T) = A(X with block T set to zero) restricted to T.
 #pragma unroll
@@ -1051,10 +1076,15 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
                 Rs[e] -= off;
             }
         }
+        __syncthreads();
     } else {
-        for (int e = tid; e < TD; e += kThreads) Rs[e] -= red[e];
+        // the thread's own elements (it loaded their right-hand side)
+#pragma unroll
+        for (int q = 0; q < EPT; q++) {
+            const int e = tid + q * kThreads;
+            if ((TD % kThreads) == 0 || e < TD) Rs[e] -= acc[0][q];
+        }
     }
-    __syncthreads();
     if constexpr (GEN) {
         // park the level sums of the block updates in the output blocks (the
         // in-block parts are added at the end), freeing `red` for Lin
@@ -1088,17 +1118,17 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             const int a0 = act_off[step], an = act_cnt[step];
             for (int i = SOLO ? lane : tid; i < an; i += SOLO ? 32 : kThreads) {
                 const int code = act_list[a0 + i];
-                const int e = code & 0xffff;
-                int u[D], g[D], rem = e;
+                const int e = ElemCode<D>::elem(code);
+                int u[D], k0s[D], rem = e;
 #pragma unroll
                 for (int mu = 0; mu < D; mu++) {
                     u[mu] = rem % TE;
                     rem /= TE;
-                    g[mu] = gidx[mu * TE + u[mu]];
+                    k0s[mu] = ElemCode<D>::k0(code, mu);
                 }
                 T L[NACC];
-                pull_lines<T, D, GEN>(sm, e, u, g, L);
-                if (!(code >> 16)) {
+                pull_lines<T, D, GEN>(sm, e, u, k0s, L);
+                if (!ElemCode<D>::coupled(code)) {
                     status |= solve_single<T, D, GEN>(sm, e, u, L);
                 } else {
 #pragma unroll

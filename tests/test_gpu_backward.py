@@ -86,6 +86,35 @@ def test_backward_without_dB(lib):
         assert _mat_err(to_host(b), to_host(a)) <= 1e-13
 
 
+@pytest.mark.parametrize("gen", [False, True])
+def test_backward_into_out_buffers(lib, gen):
+    """out=(dB, dA, dC): the gradients land in the caller's tensors and equal
+    freshly allocated ones (dB bit for bit; dA, dC to rounding: their
+    contractions sum partial products with atomics, in no fixed order); a
+    wrong layout is refused."""
+    shape = (24, 17, 13)
+    p = synthetic.problem(23, shape, generalized=gen, force_blocks=_force(shape))
+    A = [to_dev(a) for a in p["A"]]
+    C = [to_dev(c) for c in p["C"]] if gen else None
+    X = to_dev(oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4))
+    dX = to_dev(p["Xstar"])
+    dB1, dA1, dC1 = lib.tsylv_backward(A, X, dX, C)
+    oB = lib.empty_fortran(shape, X.device)
+    oA = [lib.empty_fortran((m, m), X.device) for m in shape]
+    oC = [lib.empty_fortran((m, m), X.device) for m in shape] if gen else None
+    dB2, dA2, dC2 = lib.tsylv_backward(A, X, dX, C, out=(oB, oA, oC))
+    assert dB2 is oB and all(a is b for a, b in zip(dA2, oA))
+    assert torch.equal(dB1, dB2)
+    for a, b in zip(dA1, dA2):
+        assert _mat_err(to_host(b), to_host(a)) <= 1e-13
+    if gen:
+        assert all(a is b for a, b in zip(dC2, oC))
+        for a, b in zip(dC1, dC2):
+            assert _mat_err(to_host(b), to_host(a)) <= 1e-13
+    with pytest.raises(ValueError):
+        lib.tsylv_backward(A, X, dX, C, out=(torch.empty(shape, dtype=torch.float64, device=X.device), oA, oC))
+
+
 def _fd_check(lib, shape, gen, seed, recompute=False, h=1e-6, ndir=20):
     p = synthetic.problem(seed, shape, generalized=gen, force_blocks=_force(shape))
     d = len(shape)
