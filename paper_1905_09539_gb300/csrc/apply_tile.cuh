@@ -18,8 +18,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 // (sh, sl) += (ah + al) * (xh + xl), dropping al * xl
 __device__ __forceinline__ void df_fma(float ah, float al, float xh, float xl, float& sh, float& sl) {
-    const float p = ah * xh;
-    const float e = fmaf(ah, xh, -p);  // exact: ah * xh = p + e
+    const float p = __fmul_rn(ah, xh);  // rounded product, never fused into the sum below
+    const float e = fmaf(ah, xh, -p);    // exact: ah * xh = p + e
     const float t = fmaf(ah, xl, fmaf(al, xh, e));
     float s, err;
     two_sum(sh, p, s, err);
@@ -108,7 +108,7 @@ __device__ __forceinline__ void acc_dfh(float (&yh)[EPT], float (&yl)[EPT], cons
 #pragma unroll
         for (int k = 0; k < TE; k++) {
             const float mh = Mh[i + TE * k], ml = Ml[i + TE * k], x = Sh[base + k * st];
-            const float pr = mh * x;
+            const float pr = __fmul_rn(mh, x);  // rounded product, never fused into the sum below
             const float t = fmaf(ml, x, fmaf(mh, x, -pr));  // exact low part of mh x, plus ml x
             float sum, err;
             two_sum(h, pr, sum, err);

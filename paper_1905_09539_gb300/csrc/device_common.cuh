@@ -165,6 +165,11 @@ __device__ __forceinline__ double step_scale(double mx) {
     return ldexp(1.0, ex);
 }
 
+// a + b rounded on its own (the compiler may not fuse it with the product
+// that produced a or b)
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
 template <typename T>
 __device__ __forceinline__ T fmadd(T a, T b, T c);
 template <>

@@ -219,26 +219,27 @@ __device__ __forceinline__ int solve_single(const TileSmem<T, D, GEN>& sm, int o
 #pragma unroll
         for (int l = D - 2; l >= 1; l--) {
             const T ep = sm.Es[l * TC + u[l] * (TE + 1)], dp = sm.Ds[l * TC + u[l] * (TE + 1)];
-            const T np = ep * p0 + L[C::slotP(l)];
-            const T ng_ = ep * g0 + dp * p0 + L[C::slotG(l)];
+            const T np = dev::fmadd(ep, p0, L[C::slotP(l)]);
+            const T ng_ = dev::fmadd(ep, g0, dev::fmadd(dp, p0, L[C::slotG(l)]));
             p0 = np;
             g0 = ng_;
             P0s[l] = p0;
             G0s[l] = g0;
         }
-        const T off = sm.Es[u[0] * (TE + 1)] * g0 + sm.Ds[u[0] * (TE + 1)] * p0 + L[C::NACC - 1];
+        const T off = dev::fmadd(sm.Es[u[0] * (TE + 1)], g0, dev::fmadd(sm.Ds[u[0] * (TE + 1)], p0, L[C::NACC - 1]));
         x = (sm.Rs[o] - off) * sm.Rd[o];
-        T pc = sm.Es[(D - 1) * TC + u[D - 1] * (TE + 1)] * x;
-        T gc = sm.Ds[(D - 1) * TC + u[D - 1] * (TE + 1)] * x;
-        sm.Pin[(D - 2) * TD + o] = P0s[D - 1] + pc;
-        sm.Gin[(D - 2) * TD + o] = G0s[D - 1] + gc;
+        const T e1 = sm.Es[(D - 1) * TC + u[D - 1] * (TE + 1)], d1 = sm.Ds[(D - 1) * TC + u[D - 1] * (TE + 1)];
+        T pc = e1 * x;
+        T gc = d1 * x;
+        sm.Pin[(D - 2) * TD + o] = dev::fmadd(e1, x, P0s[D - 1]);
+        sm.Gin[(D - 2) * TD + o] = dev::fmadd(d1, x, G0s[D - 1]);
 #pragma unroll
         for (int l = D - 2; l >= 1; l--) {
             const T ep = sm.Es[l * TC + u[l] * (TE + 1)], dp = sm.Ds[l * TC + u[l] * (TE + 1)];
-            gc = ep * gc + dp * pc;
-            pc = ep * pc;
-            sm.Pin[(l - 1) * TD + o] = P0s[l] + pc;
+            gc = dev::fmadd(ep, gc, dp * pc);
+            sm.Pin[(l - 1) * TD + o] = dev::fmadd(ep, pc, P0s[l]);
             sm.Gin[(l - 1) * TD + o] = G0s[l] + gc;
+            pc = ep * pc;
         }
     }
     sm.Xs[o] = x;
@@ -310,8 +311,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
                 const T gg = __shfl_sync(full, G0[l + 1], src);
                 if (k == 0 || two) {
                     const int kk = two ? a[l] + k : u[l];
-                    p += Em(l, u[l], kk) * pp;
-                    q += Em(l, u[l], kk) * gg + Dm(l, u[l], kk) * pp;
+                    p = dev::fmadd(Em(l, u[l], kk), pp, p);
+                    q = dev::fmadd(Em(l, u[l], kk), gg, dev::fmadd(Dm(l, u[l], kk), pp, q));
                 }
             }
             P0[l] = p;
@@ -327,7 +328,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
                 const T gg = __shfl_sync(full, G0[1], src);
                 if (k == 0 || two) {
                     const int kk = two ? a[0] + k : u[0];
-                    of += Em(0, u[0], kk) * gg + Dm(0, u[0], kk) * pp;
+                    of = dev::fmadd(Em(0, u[0], kk), gg, dev::fmadd(Dm(0, u[0], kk), pp, of));
                 }
             }
         }
@@ -360,7 +361,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
 #pragma unroll
         for (int k = 0; k < S; k++) {
             const T rk = __shfl_sync(full, r, k);
-            if (act) x += minv[m * S + k] * rk;
+            if (act) x = dev::fmadd(minv[m * S + k], rk, x);
         }
     } else {
     // scale for the pivot test: 16 eps max |M|
@@ -396,8 +397,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
         if (act && lane > c) {
             const T f = row[c] / prow[c];
 #pragma unroll
-            for (int k = c + 1; k < S; k++) row[k] -= f * prow[k];
-            r -= f * pr;
+            for (int k = c + 1; k < S; k++) row[k] = dev::fmadd(-f, prow[k], row[k]);
+            r = dev::fmadd(-f, pr, r);
         }
     }
     // back substitution; lane m ends with x_m
@@ -406,7 +407,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
         const T xc_local = r / row[c];
         const T xc = __shfl_sync(full, xc_local, c);
         if (lane == c) x = xc;
-        if (act && lane < c) r -= row[c] * xc;
+        if (act && lane < c) r = dev::fmadd(-row[c], xc, r);
     }
     }
     if (act) {
@@ -425,8 +426,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
                 const T xv = __shfl_sync(full, x, member_with(mask, m, mu, k));
                 if (k == 0 || two) {
                     const int kk = two ? a[mu] + k : u[mu];
-                    p += Em(mu, u[mu], kk) * xv;
-                    q += Dm(mu, u[mu], kk) * xv;
+                    p = dev::fmadd(Em(mu, u[mu], kk), xv, p);
+                    q = dev::fmadd(Dm(mu, u[mu], kk), xv, q);
                 }
             }
             pc[mu] = p;
@@ -443,8 +444,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
                 const T gg = __shfl_sync(full, gc[l + 1], src);
                 if (k == 0 || two) {
                     const int kk = two ? a[l] + k : u[l];
-                    p += Em(l, u[l], kk) * pp;
-                    q += Em(l, u[l], kk) * gg + Dm(l, u[l], kk) * pp;
+                    p = dev::fmadd(Em(l, u[l], kk), pp, p);
+                    q = dev::fmadd(Em(l, u[l], kk), gg, dev::fmadd(Dm(l, u[l], kk), pp, q));
                 }
             }
             pc[l] = p;
@@ -516,20 +517,22 @@ __device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e,
             const T dv = in ? sm.Ds[mu * TC + u[mu] + TE * k] : T(0);
             const bool odd = k & 1;
             if constexpr (!GEN) {
-                const T t = dv * (in ? Xs[v] : T(0));
-                if (odd) a1 += t; else a0 += t;
+                const T xv = in ? Xs[v] : T(0);
+                if (odd) a1 = dev::fmadd(dv, xv, a1); else a0 = dev::fmadd(dv, xv, a0);
             } else {
                 const T ev = in ? sm.Es[mu * TC + u[mu] + TE * k] : T(0);
                 if (mu == D - 1) {
                     const T xv = in ? Xs[v] : T(0);
-                    if (odd) { a1 += ev * xv; b1 += dv * xv; } else { a0 += ev * xv; b0 += dv * xv; }
+                    if (odd) { a1 = dev::fmadd(ev, xv, a1); b1 = dev::fmadd(dv, xv, b1); }
+                    else { a0 = dev::fmadd(ev, xv, a0); b0 = dev::fmadd(dv, xv, b0); }
                 } else if (mu >= 1) {
                     const T pv = in ? sm.Pin[mu * TD + v] : T(0), gv = in ? sm.Gin[mu * TD + v] : T(0);  // level mu + 1
-                    if (odd) { a1 += ev * pv; b1 += ev * gv; c1 += dv * pv; }
-                    else { a0 += ev * pv; b0 += ev * gv; c0 += dv * pv; }
+                    if (odd) { a1 = dev::fmadd(ev, pv, a1); b1 = dev::fmadd(ev, gv, b1); c1 = dev::fmadd(dv, pv, c1); }
+                    else { a0 = dev::fmadd(ev, pv, a0); b0 = dev::fmadd(ev, gv, b0); c0 = dev::fmadd(dv, pv, c0); }
                 } else {
                     const T pv = in ? sm.Pin[v] : T(0), gv = in ? sm.Gin[v] : T(0);                       // level 1
-                    if (odd) { a1 += ev * gv; b1 += dv * pv; } else { a0 += ev * gv; b0 += dv * pv; }
+                    if (odd) { a1 = dev::fmadd(ev, gv, a1); b1 = dev::fmadd(dv, pv, b1); }
+                    else { a0 = dev::fmadd(ev, gv, a0); b0 = dev::fmadd(dv, pv, b0); }
                 }
             }
         }
@@ -617,7 +620,7 @@ __device__ int group_inverse_s(const TileSmem<T, D, GEN>& sm, const int (&a)[D],
             if (q == c) continue;
             const T f = W[q][c];
 #pragma unroll
-            for (int k = 0; k < 2 * S; k++) W[q][k] -= f * W[c][k];
+            for (int k = 0; k < 2 * S; k++) W[q][k] = dev::fmadd(-f, W[c][k], W[q][k]);
         }
     }
 #pragma unroll
@@ -910,7 +913,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
                     for (int eta = 0; eta < D; eta++)
                         if (eta != mu) tt *= Es[eta * TC + uq[q][eta] * (TE + 1)];
                 }
-                diag += tt;
+                diag = dev::add_rn(diag, tt);  // never fused with the product above
                 mag += fabs(tt);
             }
             if (!(fabs(diag) > T(16) * dev::Eps<T>::v * mag)) status |= kErrSingular;
@@ -949,6 +952,16 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     // on the diagonal blocks), all groups in parallel
     const int ncg = cg_off[C::MAXSTEP];
     if (tid == 0) {
+        // canonical order within every anti-diagonal (the fill order above
+        // depends on the atomics), so that which groups get an inverse within
+        // the budget, and hence the rounding, is the same in every run
+        for (int st = 0; st < C::MAXSTEP; st++)
+            for (int i = cg_off[st] + 1; i < cg_off[st + 1]; i++) {
+                const int v = cg_list[i];
+                int k = i - 1;
+                for (; k >= cg_off[st] && cg_list[k] > v; k--) cg_list[k + 1] = cg_list[k];
+                cg_list[k + 1] = v;
+            }
         int run = 0;
         for (int i = 0; i < ncg; i++) {
             int rem = cg_list[i], mask = 0;
@@ -985,10 +998,13 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         __syncthreads();
         if (tid == 0 && jj + NST < njob) issue(j0 + jj + NST, stg);
     }
-    if (dead && tid == 0) {
-        // let copies still in flight land before the buffers go away (bounded);
-        // the block is finished with whatever it holds (the error word is set)
-        for (int q = 0; q < NST && q < njob; q++) (void)dev::mbar_wait(&bar[q], uses[q] & 1u, a.timeout_ns / 8);
+    if (dead) {  // uniform over the CTA
+        // let copies still in flight land before the buffers are reused
+        // (bounded); the block is finished with whatever it holds (the error
+        // word is set)
+        if (tid == 0)
+            for (int q = 0; q < NST && q < njob; q++) (void)dev::mbar_wait(&bar[q], uses[q] & 1u, a.timeout_ns / 8);
+        __syncthreads();
     }
 #pragma unroll
     for (int q = 0; q < NST; q++) uses[q] += static_cast<uint32_t>((njob - q + NST - 1) / NST);
@@ -1051,8 +1067,8 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
                 for (int k = 0; k < TE; k++) {
                     const T ev = Es[l * TC + i + TE * k], dv = Ds[l * TC + i + TE * k];
                     const T pv = Pn[base + k * st], gv = Gn[base + k * st];
-                    p += ev * pv;
-                    g += ev * gv + dv * pv;
+                    p = dev::fmadd(ev, pv, p);
+                    g = dev::fmadd(ev, gv, dev::fmadd(dv, pv, g));
                 }
                 vp[q] = p; vg[q] = g;
             }
@@ -1072,7 +1088,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             for (int e = tid; e < TD; e += kThreads) {
                 const int i = e % TE, base = e - i;
                 T off = red[(NACC - 1) * TD + e];
-                for (int k = 0; k < TE; k++) off += Es[i + TE * k] * Gn[base + k] + Ds[i + TE * k] * Pn[base + k];
+                for (int k = 0; k < TE; k++) off = dev::fmadd(Es[i + TE * k], Gn[base + k], dev::fmadd(Ds[i + TE * k], Pn[base + k], off));
                 Rs[e] -= off;
             }
         }
@@ -1165,8 +1181,11 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     return !dead;
 }
 
+// Compiled for the same resident count as the persistent kernel, so that a
+// block runs the same machine code (the same contractions into FMAs) in both
+// schedules.
 template <typename T, int D, bool GENF>
-__global__ void __launch_bounds__(kThreads) k_wave(const WaveArgs a) {
+__global__ void __launch_bounds__(kThreads, WaveCfg<T, D, GENF>::MINB) k_wave(const WaveArgs a) {
     using C = WaveCfg<T, D, GENF>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::oBar);
