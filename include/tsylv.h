@@ -118,9 +118,14 @@ typedef struct tsylv_opts {
                          FP32 (error ~2^-24 |A| |s D|, far below the residual);
                          1: the full FP64-accurate residual at every step         */
     int fuse_step;    /* *_REFINED, Laplace form, d >= 2, DF64 residual, schedule 0:
-                         1 runs a full refinement step as one launch (each block:
-                         FP32 solve, X update, DF64 residual); 0 (default) separate
-                         launches, which measured faster on GB300              */
+                         2 runs the first two steps as one launch, the second
+                         solve and both residuals following the first solve block
+                         by block (the same result as separate steps, bit for
+                         bit); 1 runs the first step as one launch (each block:
+                         FP32 solve, X update, DF64 residual); 3 separate launches;
+                         0 (default) 2 when the solve's largest wavefront has
+                         fewer blocks than the GPU has resident CTAs for it
+                         (latency-bound), 3 otherwise. Other forms: separate.   */
 } tsylv_opts;
 
 typedef struct tsylv_info {

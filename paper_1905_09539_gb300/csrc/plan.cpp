@@ -234,6 +234,20 @@ std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, in
     }
     p->t_wave = p->tab.size();
     p->tab.insert(p->tab.end(), p->wave_tiles.begin(), p->wave_tiles.end());
+    if (elem == 4 && !p->gen && d >= 2 && p->ntiles < (1LL << 26)) {
+        // S1, R1, S2, R2 of anti-diagonal w at virtual times w, w + lag,
+        // w + 2 lag, w + 3 lag: every job comes after the jobs it waits for
+        p->t_rjobs = p->tab.size();
+        const int nw = static_cast<int>(p->wave_off.size());
+        for (int tau = 0; tau < nw + 3 * kRefine2Lag; tau++)
+            for (int kind = 0; kind < 4; kind++) {
+                const int w = tau - kind * kRefine2Lag;
+                if (w < 0 || w >= nw) continue;
+                for (int i = 0; i < p->wave_cnt[w]; i++)
+                    p->tab.push_back((kind << 26) | p->wave_tiles[p->wave_off[w] + i]);
+            }
+        p->n_rjobs = static_cast<int>(p->tab.size() - p->t_rjobs);
+    }
     if (cudaMallocHost(&p->h_tab, p->tab.size() * sizeof(int)) != cudaSuccess) return nullptr;
     std::memcpy(p->h_tab, p->tab.data(), p->tab.size() * sizeof(int));
     g_plans[key] = p;

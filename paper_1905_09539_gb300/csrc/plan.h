@@ -51,11 +51,18 @@ struct Plan {
     // device tables (ints): start/size/blk_of per mode, then wave tiles
     std::vector<int> tab;
     size_t t_start[kMaxD] = {}, t_size[kMaxD] = {}, t_blk[kMaxD] = {}, t_wave = 0;
+    // job queue of the pipelined first two refinement steps (FP32 Laplace
+    // plans, d >= 2): kind << 26 | block, kinds S1, R1, S2, R2 of each
+    // anti-diagonal kRefine2Lag anti-diagonals apart
+    size_t t_rjobs = 0;
+    int n_rjobs = 0;
     int* h_tab = nullptr;            // pinned copy of tab (source of the graph's upload)
     std::vector<GraphEntry> graphs;
     cudaEvent_t ev[4] = {};          // opts->timing: call start, waves begin/end, call end
     ~Plan();
 };
+
+constexpr int kRefine2Lag = 2;
 
 // Workspace regions, as byte offsets from the (256-byte aligned) base.
 struct Layout {

@@ -71,7 +71,7 @@ size_t tab_ints_bound(int d, const long long* n, const int* nb) {
         t += 2 * static_cast<size_t>(nb[mu]) + static_cast<size_t>(n[mu]);
         nt *= static_cast<size_t>(nb[mu]);
     }
-    return t + nt;
+    return t + nt + 4 * nt;  // + the job queue of the pipelined refinement steps
 }
 
 bool shape_ok(int d, const int64_t* n) {
@@ -105,6 +105,7 @@ struct RefLayout {
     size_t A64[kMaxD] = {}, C64[kMaxD] = {}, Ah[kMaxD] = {}, Al[kMaxD] = {}, Ch[kMaxD] = {}, Cl[kMaxD] = {};
     size_t set[2][4] = {};
     size_t part = 0, xpart = 0, xstat = 0, nrm = 0, nA = 0;
+    size_t w2args = 0, flags2 = 0, nrm1 = 0;  // pipelined first two steps
     size_t total = 0;
 };
 
@@ -145,6 +146,9 @@ RefLayout make_ref_layout(int d, const long long* n, const int* nb, bool gen, si
     R.xstat = take(nt * 2 * 8);
     R.nrm = take(8 * 8);
     R.nA = take(2 * kMaxD * 8);
+    R.w2args = take(sizeof(WaveArgs));
+    R.flags2 = take(nt * 2 * sizeof(int));
+    R.nrm1 = take(8 * 8);
     R.total = o;
     return R;
 }
@@ -170,6 +174,8 @@ struct Call {
     bool first = false;       // first refinement step (X = 0 before it: X after it is s D exactly)
     bool fused = false;       // full refinement step in one launch (Laplace form, DF64 residual, persistent)
     int fused_grid = 0;
+    bool pipe = false;        // first two refinement steps pipelined in one launch (Laplace form)
+    int pipe_grid = 0;
 };
 
 inline cudaError_t mark(const Call& c, int i, cudaStream_t s) {
@@ -504,6 +510,113 @@ cudaError_t enqueue_ref_iter(const Call& c, cudaStream_t s) {
     return mark(c, 3, s);
 }
 
+// First two refinement steps (Laplace form) in one pipelined launch: the
+// second FP32 solve, and both residuals, follow the first solve block by
+// block instead of waiting for it to finish (see Refine2Args).  The same
+// arithmetic as two separate steps: R1 = B - s A(D1) in double-float on the
+// float correction, D2 = solve(R1 / s), R2 = R1 - s A(D2) in FP32, X = s D1 + s D2
+// (the second step's scale s is the first's: power-of-two scalings are exact).
+cudaError_t enqueue_ref_pipe(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    const RefLayout& R = c.R;
+    const Layout& L = R.L32;
+    char* b = c.base;
+    const long long nel = p.ntiles * p.td;
+    double* nrm = reinterpret_cast<double*>(b + R.nrm);
+    TRY(mark(c, 0, s));
+    SideStream* side = side_stream();
+    if (side) {
+        TRY(cudaEventRecord(side->fork, s));
+        TRY(cudaStreamWaitEvent(side->s, side->fork, 0));
+        TRY(enqueue_norms(c, side->s));
+        TRY(cudaEventRecord(side->join, side->s));
+    } else {
+        TRY(enqueue_norms(c, s));
+    }
+    TRY(launch_scale_to_f32(reinterpret_cast<double*>(b + R.Rt), reinterpret_cast<float*>(b + L.X), nrm, nel, s));
+    int* ctl = reinterpret_cast<int*>(b + L.fctl);
+    int* flags1 = reinterpret_cast<int*>(b + L.flags);
+    int* flags2 = reinterpret_cast<int*>(b + R.flags2);  // [r1done | s2done]
+    TRY(cudaMemsetAsync(ctl, 0, 64, s));
+    TRY(cudaMemsetAsync(flags1, 0, static_cast<size_t>(p.ntiles) * sizeof(int), s));
+    TRY(cudaMemsetAsync(flags2, 0, static_cast<size_t>(p.ntiles) * 2 * sizeof(int), s));
+    WaveArgs w1 = wave_args(p, L, b);
+    w1.ready = flags1;
+    w1.abort = ctl + 1;
+    w1.csize = 1;
+    WaveArgs w2 = w1;
+    w2.X = b + R.Xh;  // the second solve's right-hand side / solution (the float split is not needed here)
+    w2.ready = flags2 + p.ntiles;
+    WaveArgs* d1 = reinterpret_cast<WaveArgs*>(b + L.fargs);
+    WaveArgs* d2 = reinterpret_cast<WaveArgs*>(b + R.w2args);
+    TRY(launch_store_args(w1, d1, s));
+    TRY(launch_store_args(w2, d2, s));
+    Refine2Args f{};
+    f.w1 = d1;
+    f.w2 = d2;
+    f.jobs = reinterpret_cast<const int*>(b + L.tab) + p.t_rjobs;
+    f.njobs = p.n_rjobs;
+    f.head = ctl;
+    f.abort = ctl + 1;
+    f.timeout_ns = kTimeoutNs;
+    f.r1done = flags2;
+    for (ApplyArgs* ap : {&f.r1, &f.r2}) {
+        for (int mu = 0; mu < p.d; mu++) {
+            ap->nb[mu] = p.nb[mu];
+            ap->tstride[mu] = p.tstride[mu];
+        }
+        ap->ntiles = p.ntiles;
+        ap->kind = kApplyLaplace;
+        ap->R = reinterpret_cast<double*>(b + R.Rt);
+        ap->scale = nrm;
+        ap->err = reinterpret_cast<int*>(b + L.err);
+        ap->timeout_ns = kTimeoutNs;
+    }
+    for (int mu = 0; mu < p.d; mu++) {
+        f.r1.A[mu] = b + R.Ah[mu];
+        f.r1.Al[mu] = b + R.Al[mu];
+        f.r2.A[mu] = b + L.At[mu];
+    }
+    f.r1.s1 = b + L.X;
+    f.r1.B = reinterpret_cast<const double*>(b + R.Bt);
+    f.r1.part = reinterpret_cast<double*>(b + R.xstat);  // the first residual's block norms
+    f.r2.s1 = b + R.Xh;
+    f.r2.B = reinterpret_cast<const double*>(b + R.Rt);  // updated in place
+    f.r2.part = reinterpret_cast<double*>(b + R.part);
+    f.X2 = reinterpret_cast<float*>(b + R.Xh);
+    f.nrm = nrm;
+    // timing marks: 0 -> 1 both solves with their residuals, 1 -> 2 the X update
+    TRY(launch_refine2(p.d, f, c.pipe_grid, s));
+    TRY(mark(c, 1, s));
+    // X = s D1 + s D2 (FP64), block sums of X^2
+    double* xpart = reinterpret_cast<double*>(b + R.xpart);
+    TRY(launch_update_x(reinterpret_cast<double*>(b + R.Xt), reinterpret_cast<float*>(b + L.X), nrm, nullptr, nullptr,
+                        xpart, nel, p.td, s));
+    TRY(launch_update_x(reinterpret_cast<double*>(b + R.Xt), reinterpret_cast<float*>(b + R.Xh), nrm, nullptr, nullptr,
+                        xpart, nel, p.td, s));
+    TRY(mark(c, 2, s));
+    if (side) TRY(cudaStreamWaitEvent(s, side->join, 0));
+    TRY(launch_reduce(reinterpret_cast<double*>(b + R.xstat), nullptr, p.ntiles, reinterpret_cast<double*>(b + R.nrm1),
+                      s));
+    TRY(launch_reduce(reinterpret_cast<double*>(b + R.part), xpart, p.ntiles, nrm, s));
+    return mark(c, 3, s);
+}
+
+// The full FP64-accurate residual of the current X (after the pipelined steps,
+// where separate steps would have re-evaluated the second residual in full).
+cudaError_t enqueue_ref_resid_full(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    const RefLayout& R = c.R;
+    char* b = c.base;
+    const long long nel = p.ntiles * p.td;
+    if (c.df)
+        TRY(launch_split(reinterpret_cast<double*>(b + R.Xt), reinterpret_cast<float*>(b + R.Xh),
+                         reinterpret_cast<float*>(b + R.Xl), nel, s));
+    TRY(enqueue_residual(c, s));
+    return launch_reduce(reinterpret_cast<double*>(b + R.part), reinterpret_cast<double*>(b + R.xpart), p.ntiles,
+                         reinterpret_cast<double*>(b + R.nrm), s);
+}
+
 cudaError_t enqueue_ref_final(const Call& c, cudaStream_t s) {
     const Plan& p = *c.plan;
     GeomArgs g = geom_of(p, c.R.L32, c.base, c.flip);
@@ -620,6 +733,29 @@ int fused_grid(int d, long long ntiles) {
             int sms = 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
             slots = sms * fused_occupancy(d);
+            cache[key] = slots;
+        }
+    }
+    return static_cast<int>(ntiles < slots ? ntiles : slots);
+}
+
+// CTAs of the pipelined first two refinement steps.
+int pipe_grid(int d, long long ntiles) {
+    static std::mutex m;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int key = dev * 8 + d;
+    int slots = 0;
+    {
+        std::lock_guard<std::mutex> lk(m);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            slots = it->second;
+        } else {
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+            slots = sms * refine2_occupancy(d);
             cache[key] = slots;
         }
     }
@@ -775,7 +911,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (o.precision < TSYLV_FP64 || o.precision > TSYLV_BF16_REFINED || o.max_refine < 0 || !(o.tol > 0) ||
         (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < 0 ||
         o.schedule < 0 || o.schedule > 1 || o.partition < 0 || o.partition > 1 || o.resid_update < 0 ||
-        o.resid_update > 1 || o.fuse_step < 0 || o.fuse_step > 1)
+        o.resid_update > 1 || o.fuse_step < 0 || o.fuse_step > 3)
         return -(8 + sh);
     if (o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d))) return TSYLV_EUNSUPPORTED;
     if (o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) return TSYLV_EUNSUPPORTED;
@@ -809,6 +945,19 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     // invalid-argument error whose cause is not understood yet)
     c.fused = refined && c.persistent && !c.gen && c.df && o.fuse_step == 1 && d >= 2;
     if (c.fused) c.fused_grid = fused_grid(d, c.plan->ntiles);
+    // pipelined first two steps: always (2), or by default (0) when the solve is
+    // latency-bound, i.e. its largest wavefront has fewer blocks than a
+    // persistent launch has resident CTAs (measured: faster there, slower on
+    // wavefronts that fill the GPU)
+    bool want_pipe = o.fuse_step == 2;
+    if (o.fuse_step == 0 && refined && c.plan->n_rjobs > 0) {
+        int wmax = 0;
+        for (int w : c.plan->wave_cnt) wmax = std::max(wmax, w);
+        want_pipe = wmax < flow_grid(4, d, false, 1LL << 40);
+    }
+    c.pipe = refined && c.persistent && !c.gen && c.df && want_pipe && d >= 2 && c.plan->n_rjobs > 0 &&
+             o.max_refine >= 2;
+    if (c.pipe) c.pipe_grid = pipe_grid(d, 4 * c.plan->ntiles);
     const int tagbase = (transposed ? 1 : 0) | (c.timing ? 2 : 0) | (c.df ? 4 : 0) | (c.persistent ? 256 : 0) |
                         (c.fused ? 1024 : 0);
 
@@ -873,9 +1022,35 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
             // residual is updated from the FP32 correction instead of re-evaluated
             if (o.resid_update == 0 && it > 0 && prev <= 1e-5) c.update = true;
             c.first = it == 0;
-            st = run_enqueue(*c.plan, make_key(c, tagbase | 32 | (c.update ? 512 : 0) | (c.first ? 2048 : 0)),
-                             o.use_graph != 0, stream, enqueue_ref_iter, c);
+            const bool pipe2 = c.pipe && it == 0;  // steps 1 and 2 in one launch
+            st = run_enqueue(*c.plan,
+                             make_key(c, tagbase | 32 | (pipe2 ? 4096 : (c.update ? 512 : 0) | (c.first ? 2048 : 0))),
+                             o.use_graph != 0, stream, pipe2 ? enqueue_ref_pipe : enqueue_ref_iter, c);
             if (st) return st;
+            if (pipe2) {
+                // the first residual's norm decides, as for separate steps, whether
+                // the second residual may be the FP32 update; if not, re-evaluate it
+                double h1[3] = {}, hx[3] = {};
+                if ((e = cudaMemcpyAsync(h1, c.base + c.R.nrm1, 3 * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync(hx, c.base + c.R.nrm, 3 * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync(hA, c.base + c.R.nA, 2 * kMaxD * 8, cudaMemcpyDeviceToHost, stream)) !=
+                        cudaSuccess)
+                    return cuda_fail(e, "read norms");
+                if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize in refinement");
+                nA = norm_op(c, hA);
+                const double xn = std::sqrt(hx[2]);
+                const double rho1 = (xn > 0 && nA > 0) ? std::sqrt(h1[0]) / (nA * xn) : 0.0;
+                if (o.resid_update != 0 || !(rho1 <= 1e-5)) {
+                    c.update = false;
+                    c.first = false;
+                    st = run_enqueue(*c.plan, make_key(c, tagbase | 8192), o.use_graph != 0, stream,
+                                     enqueue_ref_resid_full, c);
+                    if (st) return st;
+                }
+                prev = std::isfinite(rho1) ? rho1 : HUGE_VAL;
+                c.update = false;
+                it = 1;  // two steps done
+            }
             if ((e = cudaMemcpyAsync(hn, c.base + c.R.nrm, 3 * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
                 return cuda_fail(e, "read residual norm");
             if (!c.update &&

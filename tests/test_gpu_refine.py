@@ -9,6 +9,7 @@ these coefficient distributions), tested at 1e-10.
 """
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import synthetic
@@ -128,11 +129,46 @@ def test_reported_residual_is_the_true_one(ts, shape, gen, update):
     assert abs(info.resid - rho) <= 2e-2 * rho + 1e-14
 
 
-@pytest.mark.parametrize("fuse", [0, 1])
+@pytest.mark.parametrize("d,shape", [(2, (33, 17)), (3, (24, 20, 16)), (3, (40, 33, 17)), (4, (9, 7, 5, 6))])
+@pytest.mark.parametrize("max_refine", [10, 2])
+def test_pipelined_first_two_steps(ts, d, shape, max_refine):
+    """fuse_step = 2 (the first two steps of the Laplace form in one pipelined
+    launch) gives the result of separate steps bit for bit, with the same
+    iteration count and reported residual."""
+    p = synthetic.problem(41, shape, force_blocks=[[n // 2 - 1] if n >= 4 else [] for n in shape])
+    A = [to_dev(a) for a in p["A"]]
+    B = to_dev(p["B"])
+    out = []
+    for fuse in (3, 2):
+        info = ts.Info()
+        X, st = ts.tsylv_solve(A, B, precision=ts.TSYLV_FP32_REFINED, fuse_step=fuse, max_refine=max_refine,
+                               info=info, check=False)
+        out.append((X, st, info.iterations, info.resid))
+    (X0, st0, it0, r0), (X2, st2, it2, r2) = out
+    assert st0 == st2 and it0 == it2 and r0 == r2
+    assert torch.equal(X0, X2)
+    if max_refine >= 3:
+        assert st2 == 0 and r2 <= 1e-12
+
+
+def test_pipelined_steps_full_second_residual(ts):
+    """With resid_update = 1 the second residual is re-evaluated in full after
+    the pipelined launch, as separate steps do: still the same result."""
+    shape = (24, 20, 16)
+    p = synthetic.problem(43, shape)
+    A = [to_dev(a) for a in p["A"]]
+    B = to_dev(p["B"])
+    X0, _ = ts.tsylv_solve(A, B, precision=ts.TSYLV_FP32_REFINED, fuse_step=3, resid_update=1)
+    X2, _ = ts.tsylv_solve(A, B, precision=ts.TSYLV_FP32_REFINED, fuse_step=2, resid_update=1)
+    assert torch.equal(X0, X2)
+
+
+@pytest.mark.parametrize("fuse", [0, 1, 2, 3])
 @pytest.mark.parametrize("d,shape", [(1, (100,)), (2, (33, 17)), (3, (24, 20, 16)), (4, (9, 7, 5, 6))])
 def test_fused_and_separate_steps(ts, d, shape, fuse):
-    """The first refinement step of the Laplace form as separate launches
-    (default) or as one fused launch: same accuracy against the oracle."""
+    """The first refinement steps of the Laplace form chosen automatically
+    (0), as one fused launch (1), the first two pipelined in one launch (2) or
+    as separate launches (3): same accuracy against the oracle."""
     p = synthetic.problem(37, shape, force_blocks=[[n // 2 - 1] if n >= 4 else [] for n in shape])
     Xo = oracle.solve_recursive(p["A"], p["B"], nmin=4)
     info = ts.Info()
