@@ -67,7 +67,7 @@ __device__ __forceinline__ void acc_f64(double (&y)[EPT], const double* __restri
     for (int q = 0; q < EPT; q++) {
         const int e = threadIdx.x + q * kThreads;
         if ((TD % kThreads) != 0 && e >= TD) continue;
-        const int i = (e / st) % TE, base = e - i * st;
+        const int i = row_of<TE, st>(e), base = e - i * st;
         double s = y[q];
 #pragma unroll
         for (int k = 0; k < TE; k++) s = fma(M[i + TE * k], S[base + k * st], s);
@@ -85,7 +85,7 @@ __device__ __forceinline__ void acc_df(float (&yh)[EPT], float (&yl)[EPT], const
     for (int q = 0; q < EPT; q++) {
         const int e = threadIdx.x + q * kThreads;
         if ((TD % kThreads) != 0 && e >= TD) continue;
-        const int i = (e / st) % TE, base = e - i * st;
+        const int i = row_of<TE, st>(e), base = e - i * st;
         float h = yh[q], l = yl[q];
 #pragma unroll
         for (int k = 0; k < TE; k++) df_fma(Mh[i + TE * k], Ml[i + TE * k], Sh[base + k * st], Sl[base + k * st], h, l);
@@ -103,7 +103,7 @@ __device__ __forceinline__ void acc_dfh(float (&yh)[EPT], float (&yl)[EPT], cons
     for (int q = 0; q < EPT; q++) {
         const int e = threadIdx.x + q * kThreads;
         if ((TD % kThreads) != 0 && e >= TD) continue;
-        const int i = (e / st) % TE, base = e - i * st;
+        const int i = row_of<TE, st>(e), base = e - i * st;
         float h = yh[q], l = yl[q];
 #pragma unroll
         for (int k = 0; k < TE; k++) {
@@ -128,7 +128,7 @@ __device__ __forceinline__ void acc_f32(float (&y)[EPT], const float* __restrict
     for (int q = 0; q < EPT; q++) {
         const int e = threadIdx.x + q * kThreads;
         if ((TD % kThreads) != 0 && e >= TD) continue;
-        const int i = (e / st) % TE, base = e - i * st;
+        const int i = row_of<TE, st>(e), base = e - i * st;
         float v = y[q];
 #pragma unroll
         for (int k = 0; k < TE; k++) v = fmaf(M[i + TE * k], S[base + k * st], v);

@@ -23,6 +23,18 @@ __host__ __device__ constexpr int ipow(int b, int e) {
     return r;
 }
 
+// Row (mode-MU index) of in-block element e = threadIdx.x + q * kThreads for a
+// mode of stride st: when st * TE divides kThreads it is the same for every
+// slot q of the thread, and is written so, so that the loads of a coefficient
+// row are shared by the thread's slots.
+#if defined(__CUDACC__)
+template <int TE, int st>
+__device__ __forceinline__ int row_of(int e) {
+    if constexpr (kThreads % (st * TE) == 0) return (static_cast<int>(threadIdx.x) / st) % TE;
+    else return (e / st) % TE;
+}
+#endif
+
 // Record a CUDA failure for tsylv_last_error(); returns TSYLV_ECUDA.
 int cuda_fail(cudaError_t e, const char* where);
 // Same for a failure with no CUDA error code of its own.

@@ -38,26 +38,32 @@ struct WaveCfg {
     // alone would give 5), FP64 generalized 3 (shared-memory bound), FP32 5 / 4
     static constexpr int MINB = sizeof(T) == 8 ? (GENF && D >= 2 ? (D == 3 ? 3 : 4) : (D == 3 ? 6 : 4))
                                                : (GENF && D >= 2 ? 4 : 5);
-    // the staging ring of the block updates and the base case's coupled-group
-    // inverses share one region; the base case's running line sums of
-    // coupled-group members reuse the block-update sums `red` once those are
-    // consumed (the generalized form's level sums are parked in the output
-    // P, G blocks meanwhile), and the reciprocal diagonal of a 1x1 group sits
-    // in its not yet solved X entry
+    // The coupled-group inverses depend only on the diagonal blocks: they are
+    // computed when the block starts, off the critical path, in a region of
+    // their own (INV_EARLY), except for the FP64 Laplace form, whose shared
+    // memory budget (6 resident CTAs) keeps them in the staging ring (so does d = 1), computed
+    // after the block updates.  The FP64 generalized form's in-block
+    // intermediates Pin, Gin (base case only) use the staging ring instead.
+    // The base case's running line sums of coupled-group members reuse the
+    // block-update sums `red` once those are consumed (the generalized form's
+    // level sums are parked in the output P, G blocks meanwhile), and the
+    // reciprocal diagonal of a 1x1 group sits in its not yet solved X entry.
     static constexpr int MINV = 1024;  // budget (entries) for precomputed coupled-group inverses
-    static constexpr int UNION = (NST * STAGE > MINV) ? NST * STAGE : MINV;
+    static constexpr bool INV_EARLY = D >= 2 && !(sizeof(T) == 8 && !GEN);
+    static constexpr bool PIN_IN_RING = GEN && sizeof(T) == 8 && 2 * NL * TD <= NST * STAGE;
+    static constexpr int UNION = (NST * STAGE > MINV || INV_EARLY) ? NST * STAGE : MINV;
     static constexpr int oStage = 0;
-    static constexpr int oMinv = 0;
     static constexpr int oRed = UNION;
     static constexpr int oLin = oRed;
     static constexpr int oR = oRed + NACC * TD;
     static constexpr int oX = oR + TD;
     static constexpr int oRd = oX;
-    static constexpr int oPin = oX + TD;
+    static constexpr int oPin = PIN_IN_RING ? 0 : oX + TD;
     static constexpr int oGin = oPin + NL * TD;
-    static constexpr int oD = oGin + NL * TD;
+    static constexpr int oD = PIN_IN_RING ? oX + TD : oGin + NL * TD;
     static constexpr int oE = oD + D * TC;
-    static constexpr int oEnd = oE + (GEN ? D * TC : 0);
+    static constexpr int oMinv = INV_EARLY ? oE + (GEN ? D * TC : 0) : 0;
+    static constexpr int oEnd = INV_EARLY ? oMinv + MINV : oE + (GEN ? D * TC : 0);
     static constexpr size_t oBar = ((oEnd * sizeof(T)) + 15) / 16 * 16;
     static constexpr size_t oMeta = oBar + ((8 * NST + 15) / 16) * 16;
     // meta: gs, gl, gidx [D][TE]; ng, bs [D]; flag [4]; coupled-group lists
@@ -83,7 +89,7 @@ __device__ __forceinline__ void prod_acc(T (&acc)[EPT], const T* __restrict__ M,
     for (int q = 0; q < EPT; q++) {
         const int e = threadIdx.x + q * kThreads;
         if ((TD % kThreads) != 0 && e >= TD) continue;
-        const int i = (e / st) % TE;
+        const int i = row_of<TE, st>(e);
         const int base = e - i * st;
         T s = acc[q];
 #pragma unroll
@@ -103,7 +109,7 @@ __device__ __forceinline__ void prod_acc2(T (&acc)[EPT], const T* __restrict__ M
     for (int q = 0; q < EPT; q++) {
         const int e = threadIdx.x + q * kThreads;
         if ((TD % kThreads) != 0 && e >= TD) continue;
-        const int i = (e / st) % TE;
+        const int i = row_of<TE, st>(e);
         const int base = e - i * st;
         T s = acc[q];
 #pragma unroll
@@ -850,7 +856,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     int* act_list = act_fill + C::MAXSTEP;  // element codes (ElemCode)
     T* Minv = sbase + C::oMinv;
     for (int i = tid; i < C::MAXSTEP; i += kThreads) { cg_cnt[i] = 0; cg_fill[i] = 0; act_cnt[i] = 0; act_fill[i] = 0; }
-    if (GEN)
+    if (GEN && !C::PIN_IN_RING)
         for (int e = tid; e < C::NL * TD; e += kThreads) { Pin[e] = T(0); Gin[e] = T(0); }
     if (tid < D) bs[tid] = a.bsize[tid][I[tid]];
     __syncthreads();
@@ -949,7 +955,8 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     }
     __syncthreads();
     // inverses of the coupled groups with <= 4 members (the system depends only
-    // on the diagonal blocks), all groups in parallel
+    // on the diagonal blocks), all groups in parallel: here when they have a
+    // region of their own, else after the block updates (in the staging ring)
     const int ncg = cg_off[C::MAXSTEP];
     if (tid == 0) {
         // canonical order within every anti-diagonal (the fill order above
@@ -980,6 +987,11 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         }
     }
     __syncthreads();
+    if constexpr (C::INV_EARLY) {
+        const TileSmem<T, D, GEN> smi{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
+        for (int i = tid; i < ncg; i += kThreads)
+            if (cg_moff[i] >= 0) status |= group_inverse<T, D, GEN>(smi, cg_list[i], Minv + cg_moff[i]);
+    }
     bool dead = false;
     for (int jj = 0; jj < njob && !dead; jj++) {
         const int stg = jj % NST;
@@ -1116,10 +1128,13 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         __syncthreads();
     }
     for (int e = tid; e < NACC * TD; e += kThreads) Lin[e] = T(0);
+    if (GEN && C::PIN_IN_RING)  // the ring is free now: every copy has landed and been read
+        for (int e = tid; e < C::NL * TD; e += kThreads) { Pin[e] = T(0); Gin[e] = T(0); }
 
     TileSmem<T, D, GEN> sm{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
-    for (int i = tid; i < ncg; i += kThreads)
-        if (cg_moff[i] >= 0) status |= group_inverse<T, D, GEN>(sm, cg_list[i], Minv + cg_moff[i]);
+    if constexpr (!C::INV_EARLY)
+        for (int i = tid; i < ncg; i += kThreads)
+            if (cg_moff[i] >= 0) status |= group_inverse<T, D, GEN>(sm, cg_list[i], Minv + cg_moff[i]);
     __syncthreads();
     // all warps take part (a one-warp variant with warp barriers between the
     // anti-diagonals measured slower for FP32 too: the line sums of one step
