@@ -174,6 +174,30 @@ def test_schedules_agree_with_oracle(lib, d, shape, gen, precision):
         assert torch.equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_inverse_budget_overflow(lib, gen, precision):
+    """Two modes made of 2x2 blocks throughout: every 8^3 block has 128
+    four-member coupled groups, 2048 inverse entries, twice the budget of
+    precomputed inverses; the rest are solved by in-step elimination.  The
+    result matches the oracle and is the same, bit for bit, in every run."""
+    shape = (16, 16, 12)
+    pairs = list(range(0, 16, 2))
+    p = synthetic.problem(47, shape, generalized=gen, force_blocks=[pairs, pairs, []], block_prob=0.0)
+    Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+    prec = lib.TSYLV_FP64 if precision == "fp64" else lib.TSYLV_FP32_REFINED
+    A = [to_dev(a) for a in p["A"]]
+    C = [to_dev(c) for c in p["C"]] if gen else None
+    B = to_dev(p["B"])
+    out = []
+    for _ in range(2):
+        X, st = lib.gtsylv_solve(A, C, B, precision=prec) if gen else lib.tsylv_solve(A, B, precision=prec)
+        assert st == 0
+        out.append(X)
+    assert rel_err(to_host(out[0]), Xo) <= (TOL if precision == "fp64" else 1e-10)
+    assert torch.equal(out[0], out[1])
+
+
 def test_singular_reported(lib):
     # a1_i + a2_j + a3_k = 0 at one position: exactly singular
     shape = (9, 8, 7)

@@ -75,6 +75,26 @@ def test_argument_validation_without_gpu(lib):
     assert lib.tsylv_solve(2, n, fake, P(16), P(16), P(256), 16, ctypes.byref(o), None, None) == -7
 
 
+def test_option_validation_without_gpu(lib):
+    """Out-of-range options are refused with -8 (the opts argument) before any
+    CUDA call; every documented value passes validation."""
+    from paper_1905_09539_gb300 import _lib
+    n = (ctypes.c_int64 * 2)(4, 4)
+    P = ctypes.c_void_p
+    fake = (P * 2)(16, 16)
+    wb = 1 << 30
+
+    def st(**kw):
+        o = _lib.default_opts(**kw)
+        return lib.tsylv_solve(2, n, fake, P(16), P(16), P(256), wb, ctypes.byref(o), None, None)
+
+    for kw in ({"fuse_step": 4}, {"fuse_step": -1}, {"schedule": 2}, {"partition": 2}, {"resid_update": 2},
+               {"precision": 9}, {"tol": 0.0}, {"split": -1}, {"max_refine": -1}, {"residual": 7}):
+        assert st(**kw) == -8, kw
+    for kw in ({"host_io": 1}, {"precision": _lib.TSYLV_TF32_REFINED}, {"precision": _lib.TSYLV_BF16_REFINED}):
+        assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
+
+
 def test_backward_workspace_and_validation(lib):
     from paper_1905_09539_gb300 import _lib
     o = _lib.default_opts()
