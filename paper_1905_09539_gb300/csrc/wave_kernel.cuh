@@ -31,8 +31,9 @@ struct WaveCfg {
     static constexpr int NL = GEN ? D - 1 : 0;  // stored levels l = 1..d-1
     static constexpr int STAGE = 2 * TD + 2 * TC;
     // stages of the bulk-copy ring: the FP64 updates are bound by the FP64
-    // pipes, the FP32 ones by the copy latency
-    static constexpr int NST = sizeof(T) == 8 ? 2 : (GEN ? 4 : 6);
+    // pipes, the FP32 ones by the copy latency (4 stages measured a little
+    // faster than 6 for the FP32 Laplace form)
+    static constexpr int NST = sizeof(T) == 8 ? 2 : 4;
     // resident CTAs per SM the persistent kernel is compiled for (register
     // budget): FP64 Laplace d = 3 6 (its shared memory allows 6, registers
     // alone would give 5), FP64 generalized 3 (shared-memory bound), FP32 5 / 4
