@@ -292,6 +292,18 @@ int tsylv_solve_batched(int count, const int* d, const int64_t* n_packed, const 
 int tsylv_solve_noalloc(int d, const int64_t* n, const double* const* A, const double* B, double* X,
                         const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
 
+/* Diagnostic of the failure path of the persistent schedule (every inter-block
+ * wait of a solve is bounded): runs the dataflow launch of a small FP64 solve
+ * (d = 2, 32 x 32, 2 x 2 blocks) with its first block withheld from the job
+ * queue, so that the blocks reading it wait for a "solved" flag that nothing
+ * sets.  The wait runs out after timeout_ns (1 ms .. 10 s), raises the
+ * launch-wide abort word, every other wait gives up at once, the kernel ends
+ * and the status word is read back: the call returns TSYLV_ETIMEOUT when this
+ * path works (TSYLV_ECUDA, or another code, otherwise), and the CUDA context
+ * stays usable.  It allocates and frees its own device memory (cudaMalloc /
+ * cudaFree) and synchronises `stream`.  Not a solver entry point. */
+int tsylv_selftest_wait_timeout(long long timeout_ns, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -238,5 +238,13 @@ def tsylv_backward(A, X, dX, C=None, *, want_dB=True, want_dA=True, want_dC=True
     return dB, dA, dC
 
 
+def selftest_wait_timeout(timeout_s=0.05, stream=None):
+    """Run the library's failure-path diagnostic (a solve whose first block is
+    withheld, so that a bounded wait runs out); returns the status, which is
+    TSYLV_ETIMEOUT when the path works."""
+    lib = load()
+    return lib.tsylv_selftest_wait_timeout(int(timeout_s * 1e9), _stream(stream))
+
+
 from .autograd import solve  # noqa: E402
 from .batched import BatchPools, tsylv_solve_batched  # noqa: E402

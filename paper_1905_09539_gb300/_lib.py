@@ -47,7 +47,7 @@ EXPORTS = [
     "tsylv_opts_default", "tsylv_status_string", "tsylv_workspace_bytes", "tsylv_solve", "gtsylv_solve",
     "tsylv_solve_transposed", "gtsylv_solve_transposed", "tsylv_residual", "tsylv_backward_workspace_bytes",
     "tsylv_backward", "tsylv_batched_workspace_bytes", "tsylv_solve_batched", "tsylv_last_error",
-    "tsylv_solve_noalloc", "tsylv_residual_workspace_bytes",
+    "tsylv_solve_noalloc", "tsylv_residual_workspace_bytes", "tsylv_selftest_wait_timeout",
 ]
 
 _lib = None
@@ -92,6 +92,8 @@ def load(path=LIB_PATH):
                                         ctypes.POINTER(I), IP, P]
     lib.tsylv_solve_noalloc.argtypes = [I, I64P, P, P, P, OP, IP, P]
     lib.tsylv_solve_noalloc.restype = I
+    lib.tsylv_selftest_wait_timeout.argtypes = [ctypes.c_longlong, P]
+    lib.tsylv_selftest_wait_timeout.restype = I
     for f in ("tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
               "tsylv_residual", "tsylv_backward", "tsylv_solve_batched"):
         getattr(lib, f).restype = I

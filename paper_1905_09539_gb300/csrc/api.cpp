@@ -89,6 +89,10 @@ extern "C" int gtsylv_solve_transposed(int d, const int64_t* n, const double* co
     return solver_solve(d, n, A, C, G, L, work, work_bytes, opts, info, stream, true, true);
 }
 
+extern "C" int tsylv_selftest_wait_timeout(long long timeout_ns, cudaStream_t stream) {
+    return solver_selftest_wait_timeout(timeout_ns, stream);
+}
+
 extern "C" size_t tsylv_residual_workspace_bytes(int d, const int64_t* n, int generalized) {
     return solver_residual_workspace_bytes(d, n, generalized != 0);
 }

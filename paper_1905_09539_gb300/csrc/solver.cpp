@@ -1116,6 +1116,53 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     return status;
 }
 
+// The failure path of the persistent schedule, exercised on purpose: the
+// first block of a small solve is left out of the job queue, so the blocks
+// that read it wait for a flag nothing sets until the bounded wait runs out.
+int solver_selftest_wait_timeout(long long timeout_ns, cudaStream_t stream) {
+    if (!(timeout_ns >= 1000000LL && timeout_ns <= 10000000000LL)) return -1;
+    if (int st = prepare_kernels()) return st;
+    const int d = 2;
+    const long long n[2] = {32, 32};
+    std::vector<uint8_t> sub(static_cast<size_t>(n[0] - 1 + n[1] - 1 + 1), 0);
+    auto plan = get_plan(d, n, false, 8, 0, &sub, 0);
+    if (!plan || plan->ntiles < 2) return cuda_fail_msg("self-test: plan");
+    const Plan& p = *plan;
+    const Layout L = make_layout(d, n, p.nb, false, 8, p.tab.size());
+    void* mem = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&mem, L.total)) != cudaSuccess) return cuda_fail(e, "self-test: cudaMalloc");
+    char* base = static_cast<char*>(mem);  // cudaMalloc memory is 256-byte aligned
+    int herr = 0;
+    auto run = [&]() -> cudaError_t {
+        TRY(cudaMemsetAsync(base, 0, L.total, stream));  // zero coefficients and right-hand side
+        TRY(cudaMemcpyAsync(base + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+        int* ctl = reinterpret_cast<int*>(base + L.fctl);
+        WaveArgs wa = wave_args(p, L, base);
+        wa.ready = reinterpret_cast<int*>(base + L.flags);
+        wa.abort = ctl + 1;
+        wa.csize = 1;
+        wa.timeout_ns = timeout_ns;
+        WaveArgs* dargs = reinterpret_cast<WaveArgs*>(base + L.fargs);
+        TRY(launch_store_args(wa, dargs, stream));
+        BatchArgs ba{};
+        ba.eqs = dargs;
+        ba.jobs = nullptr;
+        ba.tiles = reinterpret_cast<const int*>(base + L.tab) + p.t_wave + 1;  // the first block withheld
+        ba.njobs = static_cast<int>(p.ntiles) - 1;
+        ba.head = ctl;
+        ba.abort = ctl + 1;
+        ba.timeout_ns = timeout_ns;
+        TRY(launch_batched<double>(d, false, ba, static_cast<int>(p.ntiles), stream));
+        TRY(cudaMemcpyAsync(&herr, base + L.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        return cudaStreamSynchronize(stream);
+    };
+    e = run();
+    cudaFree(mem);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test: launch");
+    return map_err(herr);
+}
+
 int solver_residual(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,
                     const double* X, double* R, double* rel, void* work, size_t work_bytes, const tsylv_opts* opts,
                     cudaStream_t stream) {

@@ -10,6 +10,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
                  void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream,
                  bool gen, bool transposed);
 size_t solver_residual_workspace_bytes(int d, const int64_t* n, bool gen);
+int solver_selftest_wait_timeout(long long timeout_ns, cudaStream_t stream);
 int solver_residual(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,
                     const double* X, double* R, double* rel, void* work, size_t work_bytes, const tsylv_opts* opts,
                     cudaStream_t stream);

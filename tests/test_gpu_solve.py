@@ -198,6 +198,23 @@ def test_inverse_budget_overflow(lib, gen, precision):
     assert torch.equal(out[0], out[1])
 
 
+def test_bounded_wait_times_out_and_context_survives(lib):
+    """Failure detection without a GPU fault: a persistent solve whose first
+    block is withheld waits for a flag nothing sets; the bounded wait runs out
+    (50 ms), the launch ends with TSYLV_ETIMEOUT read back on the host, and the
+    next solve in the same context is correct."""
+    import time
+    t0 = time.perf_counter()
+    st = lib.selftest_wait_timeout(0.05)
+    dt = time.perf_counter() - t0
+    assert st == lib._lib.TSYLV_ETIMEOUT
+    assert dt < 30.0
+    p = synthetic.problem(3, (20, 17, 9))
+    Xo = oracle.solve_recursive(p["A"], p["B"], nmin=4)
+    X, st = lib.tsylv_solve([to_dev(a) for a in p["A"]], to_dev(p["B"]))
+    assert st == 0 and rel_err(to_host(X), Xo) <= TOL
+
+
 def test_singular_reported(lib):
     # a1_i + a2_j + a3_k = 0 at one position: exactly singular
     shape = (9, 8, 7)

@@ -95,6 +95,13 @@ def test_option_validation_without_gpu(lib):
         assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
 
 
+def test_selftest_argument_check_without_gpu(lib):
+    """The wait-timeout diagnostic refuses a limit outside 1 ms .. 10 s before any CUDA call."""
+    assert lib.tsylv_selftest_wait_timeout(0, None) == -1
+    assert lib.tsylv_selftest_wait_timeout(999_999, None) == -1
+    assert lib.tsylv_selftest_wait_timeout(10_000_000_001, None) == -1
+
+
 def test_backward_workspace_and_validation(lib):
     from paper_1905_09539_gb300 import _lib
     o = _lib.default_opts()
