@@ -507,7 +507,9 @@ def run_ours(args, ws, rank, local):
                 "traffic": TRAFFIC_PER_LAUNCH_BYTES,
                 "peak_source": "of measured: FP64 DMMA/DFMA probe on this GB300 (bench_fp64_peak.cu); "
                                "MEASURED_PEAKS.json has no FP64 entry (its bf16 1956.8 x 1.25/2250 gives 1.09)",
-                "per_launch_gflop": f_dom / 1e9, "per_launch_ms": w_dom}
+                "per_launch_gflop": f_dom / 1e9, "per_launch_ms": w_dom,
+                "dram_gbs_from_traffic": (TRAFFIC_PER_LAUNCH_BYTES / 1e9 / (w_dom * 1e-3)
+                                          if TRAFFIC_PER_LAUNCH_BYTES else None)}
 
     # ---- end to end through the public API: pinned host buffers, H2D of every
     # input and D2H of every result inside the timed region.  The copies run on
