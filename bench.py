@@ -651,6 +651,30 @@ def run_ours(args, ws, rank, local):
             res["mixed_vs_fp64"] = res["fp64"]["ms"] / res["fp32r"]["ms"]
             other["d4_generalized_" + "x".join(str(v) for v in shp)] = res
             del qA, qC, qB
+        # general (dense) coefficients, Alg. 1: host Schur reduction, GPU
+        # change-of-basis transforms (dense FP64 mode products) and the FP64
+        # triangular solve, 256^3 Laplace form
+        from paper_1905_09539_gb300.general import reduce_coefficients, solve_general, transform
+        rg = np.random.default_rng(args.seed + rank + 1000)
+        Ag = [to_dev(np.asfortranarray(rg.standard_normal((n, n)) / np.sqrt(n) + 2.5 * np.eye(n))) for n in shape]
+        Bg = probs[False]["B"]
+        th = time.perf_counter()
+        red = reduce_coefficients([a.cpu().numpy() for a in Ag], device=dev)
+        th = time.perf_counter() - th
+        Xg = ts.empty_fortran(shape, dev)
+        fn = lambda: solve_general(Ag, Bg, X=Xg, reduced=red)
+        fn()
+        tg = event_ms(fn, 3)
+        Ug = [u for _, u in red]
+        Tb = ts.empty_fortran(shape, dev)
+        tt = event_ms(lambda: transform(Bg, Ug, trans=[True] * 3, Y=Tb), 3)
+        ftr = 2.0 * N * sum(shape)  # one transform: a dense mode product per mode
+        other["general_laplace_256"] = {
+            "ms_gpu": tg, "host_reduction_s": th, "transform_ms": tt,
+            "transform_tflops": ftr / (tt * 1e-3) / 1e12,
+            "transform_frac_fp64_peak": ftr / (tt * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+            "note": "two transforms (B x U^T, X x U) + FP64 triangular solve on the GPU; real Schur forms on the host"}
+        del Ag, Ug, Tb, Xg
         X64 = pools.X.clone()
         ir = _lib.Info()
         fnr = lambda: pools.solve(info=ir, precision=_lib.TSYLV_FP32_REFINED)

@@ -292,6 +292,23 @@ int tsylv_solve_batched(int count, const int* d, const int64_t* n_packed, const 
 int tsylv_solve_noalloc(int d, const int64_t* n, const double* const* A, const double* B, double* X,
                         const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
 
+/* Change of basis of a tensor (Alg. 1, lines 3 and 5; Sec. 3's generalized
+ * Schur factors Q, Z for the d-term form): Y = X x_1 op(M_1) x_2 op(M_2) ...
+ * x_d op(M_d), with op(M) = M (trans[mu] == 0) or M^T (trans[mu] != 0; trans
+ * may be NULL: no transposes) and X x_mu N the mode-mu product
+ * (Y(.., i, ..) = sum_k N(i, k) X(.., k, ..)).  M[mu] == NULL skips mode mu.
+ * With orthogonal Schur factors this takes an equation with general
+ * coefficients to the quasi-triangular form tsylv_solve / gtsylv_solve take
+ * (B x_mu U_mu^T), and the solution back (X x_mu U_mu).  Dense FP64 matrix
+ * products through cuBLAS (strided-batched DGEMM on `stream`; cuBLAS keeps its
+ * own handle per device).  X, Y: column-major device tensors, Y may equal X;
+ * M[mu]: column-major n_mu x n_mu device matrices.  work: device memory of at
+ * least tsylv_transform_workspace_bytes(d, n) bytes, 256-byte aligned.
+ * Returns 0, -i for a bad i-th argument (before any GPU work), or TSYLV_ECUDA. */
+size_t tsylv_transform_workspace_bytes(int d, const int64_t* n);
+int tsylv_transform(int d, const int64_t* n, const double* const* M, const int* trans, const double* X, double* Y,
+                    void* work, size_t work_bytes, cudaStream_t stream);
+
 /* Diagnostic of the failure path of the persistent schedule (every inter-block
  * wait of a solve is bounded): runs the dataflow launch of a small FP64 solve
  * (d = 2, 32 x 32, 2 x 2 blocks) with its first block withheld from the job

@@ -122,6 +122,26 @@ def grad(A, X, Lam, C=None, want_dC=True):
     return dA, dC
 
 
+def solve_dense(A, B, C=None):
+    """General (dense, not triangular) coefficients, small sizes only: the
+    assembled operator of Eq. (1.4) -- sum over mu of the Kronecker product
+    with A_mu in position mu (mode 1 rightmost, column-major vec) and the
+    identity, or C_eta for the d-term form, in every other position -- solved
+    by LAPACK (numpy.linalg.solve).  This is the plain definition of what
+    Alg. 1 computes (Schur reduction, triangular solve, back-transformation)."""
+    from functools import reduce
+    d = len(A)
+    shape = tuple(int(a.shape[0]) for a in A)
+    N = int(np.prod(shape))
+    M = np.zeros((N, N))
+    for mu in range(d):
+        facs = [np.asarray(A[eta], dtype=np.float64) if eta == mu else
+                (np.eye(shape[eta]) if C is None else np.asarray(C[eta], dtype=np.float64)) for eta in range(d)]
+        M += reduce(np.kron, facs[::-1])
+    x = np.linalg.solve(M, np.asarray(B, dtype=np.float64).reshape(-1, order="F"))
+    return np.asfortranarray(x.reshape(shape, order="F"))
+
+
 def check_structure(A, shape):
     A_, pa = _mats(A)
     n = (ctypes.c_int64 * len(shape))(*shape)

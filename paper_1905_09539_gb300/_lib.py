@@ -48,6 +48,7 @@ EXPORTS = [
     "tsylv_solve_transposed", "gtsylv_solve_transposed", "tsylv_residual", "tsylv_backward_workspace_bytes",
     "tsylv_backward", "tsylv_batched_workspace_bytes", "tsylv_solve_batched", "tsylv_last_error",
     "tsylv_solve_noalloc", "tsylv_residual_workspace_bytes", "tsylv_selftest_wait_timeout",
+    "tsylv_transform", "tsylv_transform_workspace_bytes",
 ]
 
 _lib = None
@@ -94,6 +95,10 @@ def load(path=LIB_PATH):
     lib.tsylv_solve_noalloc.restype = I
     lib.tsylv_selftest_wait_timeout.argtypes = [ctypes.c_longlong, P]
     lib.tsylv_selftest_wait_timeout.restype = I
+    lib.tsylv_transform_workspace_bytes.argtypes = [I, I64P]
+    lib.tsylv_transform_workspace_bytes.restype = S
+    lib.tsylv_transform.argtypes = [I, I64P, P, ctypes.POINTER(I), P, P, P, S, P]
+    lib.tsylv_transform.restype = I
     for f in ("tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
               "tsylv_residual", "tsylv_backward", "tsylv_solve_batched"):
         getattr(lib, f).restype = I

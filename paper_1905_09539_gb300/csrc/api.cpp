@@ -89,6 +89,13 @@ extern "C" int gtsylv_solve_transposed(int d, const int64_t* n, const double* co
     return solver_solve(d, n, A, C, G, L, work, work_bytes, opts, info, stream, true, true);
 }
 
+extern "C" size_t tsylv_transform_workspace_bytes(int d, const int64_t* n) { return transform_workspace_bytes(d, n); }
+
+extern "C" int tsylv_transform(int d, const int64_t* n, const double* const* M, const int* trans, const double* X,
+                               double* Y, void* work, size_t work_bytes, cudaStream_t stream) {
+    return transform(d, n, M, trans, X, Y, work, work_bytes, stream);
+}
+
 extern "C" int tsylv_selftest_wait_timeout(long long timeout_ns, cudaStream_t stream) {
     return solver_selftest_wait_timeout(timeout_ns, stream);
 }

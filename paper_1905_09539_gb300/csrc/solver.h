@@ -11,6 +11,9 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
                  bool gen, bool transposed);
 size_t solver_residual_workspace_bytes(int d, const int64_t* n, bool gen);
 int solver_selftest_wait_timeout(long long timeout_ns, cudaStream_t stream);
+size_t transform_workspace_bytes(int d, const int64_t* n);
+int transform(int d, const int64_t* n, const double* const* M, const int* trans, const double* X, double* Y,
+              void* work, size_t work_bytes, cudaStream_t stream);
 int solver_residual(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,
                     const double* X, double* R, double* rel, void* work, size_t work_bytes, const tsylv_opts* opts,
                     cudaStream_t stream);
