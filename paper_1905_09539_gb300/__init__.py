@@ -22,7 +22,8 @@ from ._lib import (TSYLV_BF16_REFINED, TSYLV_FP32_REFINED, TSYLV_FP64, TSYLV_RES
 __all__ = ["tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
            "tsylv_residual", "tsylv_backward", "tsylv_solve_batched", "BatchPools", "solve", "fortran", "TsylvError",
            "Opts", "Info", "default_opts", "TSYLV_FP64", "TSYLV_FP32_REFINED", "TSYLV_TF32_REFINED",
-           "TSYLV_BF16_REFINED", "TSYLV_RESID_DF64", "TSYLV_RESID_FP64", "workspace"]
+           "TSYLV_BF16_REFINED", "TSYLV_RESID_DF64", "TSYLV_RESID_FP64", "workspace", "solve_general",
+           "reduce_coefficients", "transform", "selftest_wait_timeout", "empty_fortran"]
 
 
 class TsylvError(RuntimeError):
@@ -247,4 +248,5 @@ def selftest_wait_timeout(timeout_s=0.05, stream=None):
 
 
 from .autograd import solve  # noqa: E402
+from .general import reduce_coefficients, solve_general, transform  # noqa: E402
 from .batched import BatchPools, tsylv_solve_batched  # noqa: E402
