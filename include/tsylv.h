@@ -300,8 +300,8 @@ int tsylv_solve_noalloc(int d, const int64_t* n, const double* const* A, const d
  * With orthogonal Schur factors this takes an equation with general
  * coefficients to the quasi-triangular form tsylv_solve / gtsylv_solve take
  * (B x_mu U_mu^T), and the solution back (X x_mu U_mu).  Dense FP64 matrix
- * products through cuBLAS (strided-batched DGEMM on `stream`; cuBLAS keeps its
- * own handle per device).  X, Y: column-major device tensors, Y may equal X;
+ * products through cuBLAS (strided-batched DGEMM on `stream`; the library keeps
+ * one cuBLAS handle per host thread and device).  X, Y: column-major device tensors, Y may equal X;
  * M[mu]: column-major n_mu x n_mu device matrices.  work: device memory of at
  * least tsylv_transform_workspace_bytes(d, n) bytes, 256-byte aligned.
  * Returns 0, -i for a bad i-th argument (before any GPU work), or TSYLV_ECUDA. */

@@ -8,7 +8,6 @@
 
 #include <cstring>
 #include <map>
-#include <mutex>
 
 #include "solver.h"
 #include "tsylv_internal.h"
@@ -17,12 +16,12 @@ namespace tsylv {
 
 namespace {
 
+// One cuBLAS handle per host thread and device (a handle's stream is set per
+// call, so threads must not share one).
 cublasHandle_t handle_for_device() {
-    static std::mutex m;
-    static std::map<int, cublasHandle_t> handles;
+    thread_local std::map<int, cublasHandle_t> handles;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> lk(m);
     auto it = handles.find(dev);
     if (it != handles.end()) return it->second;
     cublasHandle_t h = nullptr;
