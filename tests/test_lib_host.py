@@ -102,6 +102,25 @@ def test_selftest_argument_check_without_gpu(lib):
     assert lib.tsylv_selftest_wait_timeout(10_000_000_001, None) == -1
 
 
+def test_transform_validation_without_gpu(lib):
+    """tsylv_transform: bad arguments are refused with -i before any CUDA call."""
+    P = ctypes.c_void_p
+    n = (ctypes.c_int64 * 2)(4, 5)
+    M = (P * 2)(16, 16)
+    wb = lib.tsylv_transform_workspace_bytes(2, n)
+    assert wb >= 4 * 5 * 8
+    assert lib.tsylv_transform_workspace_bytes(0, n) == 0
+    bad = (ctypes.c_int64 * 2)(4, 0)
+    assert lib.tsylv_transform_workspace_bytes(2, bad) == 0
+    assert lib.tsylv_transform(0, n, M, None, P(16), P(16), P(256), wb, None) == -1
+    assert lib.tsylv_transform(2, bad, M, None, P(16), P(16), P(256), wb, None) == -2
+    assert lib.tsylv_transform(2, n, None, None, P(16), P(16), P(256), wb, None) == -3
+    assert lib.tsylv_transform(2, n, M, None, None, P(16), P(256), wb, None) == -5
+    assert lib.tsylv_transform(2, n, M, None, P(16), None, P(256), wb, None) == -6
+    assert lib.tsylv_transform(2, n, M, None, P(16), P(16), P(257), wb, None) == -7
+    assert lib.tsylv_transform(2, n, M, None, P(16), P(16), P(256), wb - 1, None) == -8
+
+
 def test_backward_workspace_and_validation(lib):
     from paper_1905_09539_gb300 import _lib
     o = _lib.default_opts()
