@@ -1094,7 +1094,13 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
         std::memset(info, 0, sizeof(*info));
         info->iterations = iters;
         info->waves = static_cast<int>(c.plan->wave_off.size());
-        info->launches = iters * ((c.persistent ? 2 : info->waves) + (c.gen ? d : 1) + 4) + 4 * d + 8;
+        // separate steps: the solve (parameter store + launch, or one launch per
+        // wavefront), the residual launches, scaling, update, reduction; the
+        // pipelined first two steps: scaling, two parameter stores, one launch,
+        // two updates, two reductions
+        const int piped = c.pipe && iters >= 2 ? 2 : 0;
+        info->launches = (iters - piped) * ((c.persistent ? 2 : info->waves) + (c.gen ? d : 1) + 4) +
+                         (piped ? 8 : 0) + 4 * d + 8;
         info->tiles = static_cast<int>(c.plan->ntiles);
         info->resid = rho;
         info->norm_A = nA;
