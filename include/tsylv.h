@@ -26,7 +26,10 @@
  * Sec. 2.3).  By default one persistent launch per solve runs every block as
  * soon as the blocks it reads are solved (opts->schedule = 0); the
  * alternative is one launch per anti-diagonal wavefront.  The launches of a
- * call are captured once in a CUDA graph and replayed.
+ * call are captured once in a CUDA graph and replayed.  The mixed-precision
+ * solves (TSYLV_FP32_REFINED) solve in FP32 and refine in FP64 with a
+ * double-float residual; their first two steps run pipelined in one launch
+ * when the solve is latency-bound (opts->fuse_step).
  *
  * Layout.  Tensors are dense and column-major with mode 1 fastest -- the
  * index map Eq. (2.1): element (i_1, ..., i_d) (0-based) is at
@@ -39,9 +42,11 @@
  *
  * Pointers.  `n` and the arrays `A`, `C`, `dA`, `dC` are host arrays; the
  * matrices and tensors they point to live in device memory.  All device memory is owned by the
- * caller.  The library allocates no device memory: every scratch buffer is
- * carved out of `work`, whose size comes from the matching *_workspace_bytes
- * query (256-byte alignment is required).  In-place use (X == B) is allowed.
+ * caller.  The solver entry points allocate no device memory: every scratch
+ * buffer is carved out of `work`, whose size comes from the matching
+ * *_workspace_bytes query (256-byte alignment is required).  In-place use
+ * (X == B) is allowed.  (tsylv_transform's cuBLAS handle and the diagnostic
+ * tsylv_selftest_wait_timeout are the documented exceptions.)
  *
  * Streams.  Work is queued on `stream`.  Each call reads the 2x2 block
  * structure of A back to the host (a short synchronisation on `stream`
