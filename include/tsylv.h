@@ -261,7 +261,10 @@ size_t tsylv_batched_workspace_bytes(int count, const int* d, const int64_t* n_p
  *               B_pool
  *   work        device workspace of tsylv_batched_workspace_bytes bytes,
  *               256-byte aligned, caller-owned
- * Precision: TSYLV_FP64 only (other values return TSYLV_EUNSUPPORTED).
+ * Precision: TSYLV_FP64, or TSYLV_FP32_REFINED when every equation of the
+ * batch has the same order d (FP32 solves of all equations in one persistent
+ * launch, FP64 residuals and corrections per equation, each equation refined to
+ * opts->tol); other values return TSYLV_EUNSUPPORTED.
  * Launch parameters: on the first call for a given set of shapes and 2x2
  * structures a built-in autotuner times the job-queue orders (longest
  * remaining path first, wavefront-major, equation-major) and the resident
@@ -290,10 +293,16 @@ int tsylv_solve_batched(int count, const int* d, const int64_t* n_packed, const 
  * tsylv_workspace_bytes bound) exceeds it are rejected with TSYLV_ESCRATCH and
  * a tsylv_last_error() message, before any GPU work.  The first call on each
  * device looks up the array's device address and sets kernel attributes; make
- * that first call before any stream capture.  Calls share the array, so calls
- * whose GPU work overlaps race on it: serialise them.  The status word is
- * cleared by every call.  Arguments and the other status codes as
- * tsylv_solve (opts->precision must be TSYLV_FP64, else -6). */
+ * that first call before any stream capture.  Like tsylv_solve, every call
+ * synchronises `stream` twice: after reading back the 2x2 structure of A and
+ * at the end, to read the status.  Calls share the array, so calls whose GPU
+ * work overlaps race on it: serialise them.  The status word is cleared by
+ * every call.  Arguments and status codes as tsylv_solve, with opts the 6th
+ * argument: its fields are checked as tsylv_solve checks them (-6 for a field
+ * out of range, TSYLV_EUNSUPPORTED for host_io or a non-default nmin);
+ * opts->precision must be TSYLV_FP64 (else -6) and opts->timing 0 (else
+ * TSYLV_EUNSUPPORTED).  The schedule is always one launch per anti-diagonal
+ * wavefront (opts->schedule is not used). */
 int tsylv_solve_noalloc(int d, const int64_t* n, const double* const* A, const double* B, double* X,
                         const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
 

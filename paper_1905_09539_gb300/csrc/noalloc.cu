@@ -65,15 +65,17 @@ int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const 
     tsylv_opts o;
     if (opts) o = *opts; else tsylv_opts_default(&o);
     if (d < 1 || d > kMaxD) return -1;
-    if (!n) return -2;
-    for (int mu = 0; mu < d; mu++)
-        if (n[mu] < 1 || n[mu] > (1 << 20)) return -2;
+    if (!solve_shape_ok(d, n)) return -2;
     if (!A) return -3;
     for (int mu = 0; mu < d; mu++)
         if (!A[mu]) return -3;
     if (!B) return -4;
     if (!X) return -5;
+    // the option checks of tsylv_solve; then what this entry point serves:
+    // the FP64 solve, without event timing
+    if (int st = check_opts(o, d)) return st < 0 ? -6 : st;
     if (o.precision != TSYLV_FP64) return -6;
+    if (o.timing) return TSYLV_EUNSUPPORTED;
     // the largest workspace any admissible block structure needs must fit
     const size_t need = solver_workspace_bytes(d, n, false, o, false);
     if (need == 0) return -2;
@@ -86,69 +88,15 @@ int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const 
     (void)cudaGetLastError();
 
     long long nn[kMaxD];
-    size_t nsub = 0;
-    for (int mu = 0; mu < d; mu++) {
-        nn[mu] = n[mu];
-        nsub += static_cast<size_t>(n[mu] - 1);
-    }
-    // 2x2 block structure of A (read back through the scratch)
-    std::vector<double> hsub(nsub + 1, 0.0);
-    cudaError_t e;
-    const size_t sub_off = 256;
-    if (nsub > 0) {
-        if ((e = launch_gather_subdiag(d, nn, A, reinterpret_cast<double*>(base + sub_off), stream)) != cudaSuccess)
-            return cuda_fail(e, "gather sub-diagonal");
-        if ((e = cudaMemcpyAsync(hsub.data(), base + sub_off, nsub * sizeof(double), cudaMemcpyDeviceToHost,
-                                 stream)) != cudaSuccess)
-            return cuda_fail(e, "read sub-diagonal");
-    }
-    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize before planning");
-
-    // split tree of every mode (Alg. 2) and the block grid
+    for (int mu = 0; mu < d; mu++) nn[mu] = n[mu];
+    // 2x2 block structure of A (read back through the scratch), then the
+    // schedule exactly as tsylv_solve plans it: block partition, wavefronts
+    // (cluster split of short ones), device tables
+    std::vector<uint8_t> sub;
+    if (int st = solve_read_structure(d, nn, A, base, false, stream, sub)) return st;
     Plan p;
-    p.d = d;
-    p.gen = false;
-    p.te = tile_extent(d);
-    p.td = ipow(p.te, d);
-    p.tc = p.te * p.te;
-    long long ts = 1;
-    size_t off = 0;
-    for (int mu = 0; mu < d; mu++) {
-        std::vector<uint8_t> s(static_cast<size_t>(n[mu]), 0);
-        for (long long i = 0; i + 1 < n[mu]; i++) s[i] = hsub[off + i] != 0.0 ? 1 : 0;
-        for (long long i = 0; i + 2 < n[mu]; i++)
-            if (s[i] && s[i + 1]) return -3;
-        off += static_cast<size_t>(n[mu] - 1);
-        p.n[mu] = n[mu];
-        p.part[mu] = make_part(static_cast<int>(n[mu]), s, p.te, o.partition == 1 ? 1 : 0);
-        p.nb[mu] = p.part[mu].nb;
-        p.tstride[mu] = ts;
-        ts *= p.nb[mu];
-    }
-    p.ntiles = ts;
-    // anti-diagonal wavefronts, one CTA per block
-    int smax = 0;
-    for (int mu = 0; mu < d; mu++) smax += p.nb[mu] - 1;
-    std::vector<std::vector<int>> by_s(static_cast<size_t>(smax) + 1);
-    for (long long t = 0; t < p.ntiles; t++) {
-        int s = 0;
-        for (int mu = 0; mu < d; mu++) s += static_cast<int>((t / p.tstride[mu]) % p.nb[mu]);
-        by_s[s].push_back(static_cast<int>(t));
-    }
-    for (int mu = 0; mu < d; mu++) {
-        p.t_start[mu] = p.tab.size();
-        p.tab.insert(p.tab.end(), p.part[mu].start.begin(), p.part[mu].start.end());
-        p.t_size[mu] = p.tab.size();
-        p.tab.insert(p.tab.end(), p.part[mu].size.begin(), p.part[mu].size.end());
-        p.t_blk[mu] = p.tab.size();
-        p.tab.insert(p.tab.end(), p.part[mu].blk_of.begin(), p.part[mu].blk_of.end());
-    }
-    p.t_wave = p.tab.size();
-    for (int s = smax; s >= 0; s--) {
-        p.wave_off.push_back(static_cast<int>(p.tab.size() - p.t_wave));
-        p.wave_cnt.push_back(static_cast<int>(by_s[s].size()));
-        p.tab.insert(p.tab.end(), by_s[s].begin(), by_s[s].end());
-    }
+    fill_plan(p, d, nn, false, 8, o.split, sub, o.partition);
+    cudaError_t e;
     Layout L = make_layout(d, nn, p.nb, false, 8, p.tab.size());
     if (L.total > kStaticScratchBytes) {
         cuda_fail_msg("problem needs more scratch than the static array of tsylv_solve_noalloc (32 MiB)");
@@ -180,10 +128,10 @@ int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const 
     wa.X = Xt;
     wa.err = reinterpret_cast<int*>(base + L.err);
     wa.timeout_ns = kNoallocTimeoutNs;
-    wa.csize = 1;
     for (size_t w = 0; w < p.wave_off.size(); w++) {
         wa.tiles = tab + p.t_wave + p.wave_off[w];
         wa.ntiles = p.wave_cnt[w];
+        wa.csize = p.wave_csize[w];
         if ((e = launch_wave<double>(d, false, kProdNative, wa, stream)) != cudaSuccess)
             return cuda_fail(e, "wavefront launch");
     }

@@ -188,6 +188,56 @@ void build_waves(Plan& p, int split) {
 
 }  // namespace
 
+void fill_plan(Plan& p, int d, const long long* n, bool gen, int elem, int split, const std::vector<uint8_t>& sub,
+               int partition) {
+    p.d = d;
+    p.gen = gen && d >= 2;
+    p.te = tile_extent(d);
+    p.td = ipow(p.te, d);
+    p.tc = p.te * p.te;
+    p.elem = elem;
+    size_t off = 0;
+    long long ts = 1;
+    for (int mu = 0; mu < d; mu++) {
+        p.n[mu] = n[mu];
+        std::vector<uint8_t> s(static_cast<size_t>(n[mu]), 0);
+        for (long long i = 0; i + 1 < n[mu]; i++) s[i] = sub[off + i];
+        off += static_cast<size_t>(n[mu] - 1);
+        p.part[mu] = make_part(static_cast<int>(n[mu]), s, p.te, partition);
+        p.nb[mu] = p.part[mu].nb;
+        p.tstride[mu] = ts;
+        ts *= p.nb[mu];
+    }
+    p.ntiles = ts;
+    build_waves(p, split);
+    // device tables
+    p.tab.clear();
+    for (int mu = 0; mu < d; mu++) {
+        p.t_start[mu] = p.tab.size();
+        p.tab.insert(p.tab.end(), p.part[mu].start.begin(), p.part[mu].start.end());
+        p.t_size[mu] = p.tab.size();
+        p.tab.insert(p.tab.end(), p.part[mu].size.begin(), p.part[mu].size.end());
+        p.t_blk[mu] = p.tab.size();
+        p.tab.insert(p.tab.end(), p.part[mu].blk_of.begin(), p.part[mu].blk_of.end());
+    }
+    p.t_wave = p.tab.size();
+    p.tab.insert(p.tab.end(), p.wave_tiles.begin(), p.wave_tiles.end());
+    if (elem == 4 && !p.gen && d >= 2 && p.ntiles < (1LL << 26)) {
+        // S1, R1, S2, R2 of anti-diagonal w at virtual times w, w + lag,
+        // w + 2 lag, w + 3 lag: every job comes after the jobs it waits for
+        p.t_rjobs = p.tab.size();
+        const int nw = static_cast<int>(p.wave_off.size());
+        for (int tau = 0; tau < nw + 3 * kRefine2Lag; tau++)
+            for (int kind = 0; kind < 4; kind++) {
+                const int w = tau - kind * kRefine2Lag;
+                if (w < 0 || w >= nw) continue;
+                for (int i = 0; i < p.wave_cnt[w]; i++)
+                    p.tab.push_back((kind << 26) | p.wave_tiles[p.wave_off[w] + i]);
+            }
+        p.n_rjobs = static_cast<int>(p.tab.size() - p.t_rjobs);
+    }
+}
+
 std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, int split,
                                const std::vector<uint8_t>* sub, int partition) {
     std::string key = std::to_string(d) + (gen ? "g" : "l") + std::to_string(elem) + "s" + std::to_string(split) +
@@ -202,52 +252,7 @@ std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, in
     auto it = g_plans.find(key);
     if (it != g_plans.end()) return it->second;
     auto p = std::make_shared<Plan>();
-    p->d = d;
-    p->gen = gen && d >= 2;
-    p->te = tile_extent(d);
-    p->td = ipow(p->te, d);
-    p->tc = p->te * p->te;
-    p->elem = elem;
-    off = 0;
-    long long ts = 1;
-    for (int mu = 0; mu < d; mu++) {
-        p->n[mu] = n[mu];
-        std::vector<uint8_t> s(static_cast<size_t>(n[mu]), 0);
-        for (long long i = 0; i + 1 < n[mu]; i++) s[i] = sub[0][off + i];
-        off += static_cast<size_t>(n[mu] - 1);
-        p->part[mu] = make_part(static_cast<int>(n[mu]), s, p->te, partition);
-        p->nb[mu] = p->part[mu].nb;
-        p->tstride[mu] = ts;
-        ts *= p->nb[mu];
-    }
-    p->ntiles = ts;
-    build_waves(*p, split);
-    // device tables
-    p->tab.clear();
-    for (int mu = 0; mu < d; mu++) {
-        p->t_start[mu] = p->tab.size();
-        p->tab.insert(p->tab.end(), p->part[mu].start.begin(), p->part[mu].start.end());
-        p->t_size[mu] = p->tab.size();
-        p->tab.insert(p->tab.end(), p->part[mu].size.begin(), p->part[mu].size.end());
-        p->t_blk[mu] = p->tab.size();
-        p->tab.insert(p->tab.end(), p->part[mu].blk_of.begin(), p->part[mu].blk_of.end());
-    }
-    p->t_wave = p->tab.size();
-    p->tab.insert(p->tab.end(), p->wave_tiles.begin(), p->wave_tiles.end());
-    if (elem == 4 && !p->gen && d >= 2 && p->ntiles < (1LL << 26)) {
-        // S1, R1, S2, R2 of anti-diagonal w at virtual times w, w + lag,
-        // w + 2 lag, w + 3 lag: every job comes after the jobs it waits for
-        p->t_rjobs = p->tab.size();
-        const int nw = static_cast<int>(p->wave_off.size());
-        for (int tau = 0; tau < nw + 3 * kRefine2Lag; tau++)
-            for (int kind = 0; kind < 4; kind++) {
-                const int w = tau - kind * kRefine2Lag;
-                if (w < 0 || w >= nw) continue;
-                for (int i = 0; i < p->wave_cnt[w]; i++)
-                    p->tab.push_back((kind << 26) | p->wave_tiles[p->wave_off[w] + i]);
-            }
-        p->n_rjobs = static_cast<int>(p->tab.size() - p->t_rjobs);
-    }
+    fill_plan(*p, d, n, gen, elem, split, *sub, partition);
     if (cudaMallocHost(&p->h_tab, p->tab.size() * sizeof(int)) != cudaSuccess) return nullptr;
     std::memcpy(p->h_tab, p->tab.data(), p->tab.size() * sizeof(int));
     g_plans[key] = p;

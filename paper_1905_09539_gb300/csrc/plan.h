@@ -74,6 +74,12 @@ struct Layout {
 
 Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem, size_t tab_ints);
 
+// Schedule of one solve (partition, wavefronts, device tables) without the
+// pinned host copy of the tables and without caching.
+void fill_plan(Plan& p, int d, const long long* n, bool gen, int elem, int split, const std::vector<uint8_t>& sub,
+               int partition);
+
+// Cached schedule with a pinned copy of its tables (the source of a captured upload).
 std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, int split,
                                const std::vector<uint8_t>* sub, int partition);
 

@@ -852,6 +852,24 @@ double norm_op(const Call& c, const double* nA) {
 
 }  // namespace
 
+bool solve_shape_ok(int d, const int64_t* n) { return shape_ok(d, n); }
+
+int solve_read_structure(int d, const long long* n, const double* const* A, char* base, bool flip,
+                         cudaStream_t stream, std::vector<uint8_t>& sub) {
+    return read_structure(d, n, A, base, flip, stream, sub);
+}
+
+int check_opts(const tsylv_opts& o, int d) {
+    if (o.precision < TSYLV_FP64 || o.precision > TSYLV_BF16_REFINED || o.max_refine < 0 || !(o.tol > 0) ||
+        (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < 0 ||
+        o.schedule < 0 || o.schedule > 1 || o.partition < 0 || o.partition > 1 || o.resid_update < 0 ||
+        o.resid_update > 1 || o.fuse_step < 0 || o.fuse_step > 3 || o.timing < 0 || o.timing > 1 ||
+        o.use_graph < 0 || o.use_graph > 1)
+        return -1;
+    if (o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d))) return TSYLV_EUNSUPPORTED;
+    return 0;
+}
+
 size_t solver_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o, bool transposed) {
     (void)transposed;
     if (!shape_ok(d, n)) return 0;
@@ -908,12 +926,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (!X) return -(5 + sh);
     if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -(6 + sh);
     if (work_bytes < solver_workspace_bytes(d, n, gen, o, transposed)) return -(7 + sh);
-    if (o.precision < TSYLV_FP64 || o.precision > TSYLV_BF16_REFINED || o.max_refine < 0 || !(o.tol > 0) ||
-        (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < 0 ||
-        o.schedule < 0 || o.schedule > 1 || o.partition < 0 || o.partition > 1 || o.resid_update < 0 ||
-        o.resid_update > 1 || o.fuse_step < 0 || o.fuse_step > 3)
-        return -(8 + sh);
-    if (o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d))) return TSYLV_EUNSUPPORTED;
+    if (int st = check_opts(o, d)) return st < 0 ? -(8 + sh) : st;
     if (o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) return TSYLV_EUNSUPPORTED;
     const bool refined = o.precision != TSYLV_FP64;
 

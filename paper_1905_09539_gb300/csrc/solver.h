@@ -1,6 +1,8 @@
 // Solver entry points behind the C ABI.
 #pragma once
 
+#include <vector>
+
 #include "tsylv_internal.h"
 
 namespace tsylv {
@@ -27,6 +29,17 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
                    size_t work_bytes, const tsylv_opts* opts, int* per_status, tsylv_info* info, cudaStream_t stream);
 
 cudaStream_t capture_stream();
+
+// Shared argument checks of the solve entry points.
+bool solve_shape_ok(int d, const int64_t* n);
+// 0, -1 for an option field out of its range, or TSYLV_EUNSUPPORTED for a
+// valid request this build does not serve (host_io, a non-default nmin).
+int check_opts(const tsylv_opts& o, int d);
+// 2x2 block structure of every A_mu: the sub-diagonal is gathered into
+// base + 256, read back (a synchronisation of `stream`) and validated (-3
+// for two adjacent 2x2 blocks); flipped for the transposed equation.
+int solve_read_structure(int d, const long long* n, const double* const* A, char* base, bool flip,
+                         cudaStream_t stream, std::vector<uint8_t>& sub);
 
 int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const double* B, double* X,
                          const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);

@@ -95,6 +95,32 @@ def test_option_validation_without_gpu(lib):
         assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
 
 
+def test_noalloc_option_validation_without_gpu(lib):
+    """tsylv_solve_noalloc checks its options as tsylv_solve does (-6, its
+    opts argument, for a field out of range; TSYLV_EUNSUPPORTED for host_io or
+    a non-default nmin), refuses any precision but FP64 with -6 and event
+    timing with TSYLV_EUNSUPPORTED -- all before any CUDA call."""
+    from paper_1905_09539_gb300 import _lib
+    n = (ctypes.c_int64 * 2)(4, 4)
+    P = ctypes.c_void_p
+    fake = (P * 2)(16, 16)
+
+    def st(**kw):
+        o = _lib.default_opts(**kw)
+        return lib.tsylv_solve_noalloc(2, n, fake, P(16), P(16), ctypes.byref(o), None, None)
+
+    for kw in ({"fuse_step": 4}, {"schedule": 2}, {"partition": 2}, {"resid_update": 2}, {"precision": 9},
+               {"tol": 0.0}, {"split": -1}, {"max_refine": -1}, {"residual": 7}, {"timing": 2},
+               {"precision": _lib.TSYLV_FP32_REFINED}):
+        assert st(**kw) == -6, kw
+    for kw in ({"host_io": 1}, {"nmin": 5}, {"timing": 1}):
+        assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
+    bad = (ctypes.c_int64 * 2)(4, 0)
+    assert lib.tsylv_solve_noalloc(2, bad, fake, P(16), P(16), None, None, None) == -2
+    assert lib.tsylv_solve_noalloc(5, n, fake, P(16), P(16), None, None, None) == -1
+    assert lib.tsylv_solve_noalloc(2, n, None, P(16), P(16), None, None, None) == -3
+
+
 def test_selftest_argument_check_without_gpu(lib):
     """The wait-timeout diagnostic refuses a limit outside 1 ms .. 10 s before any CUDA call."""
     assert lib.tsylv_selftest_wait_timeout(0, None) == -1
