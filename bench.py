@@ -333,7 +333,8 @@ def run_ours(args, ws, rank, local):
     ts.load()
     shape = (args.n, args.n, args.n)
     N = float(np.prod(shape))
-    PREC = {0: _lib.TSYLV_FP64, 1: _lib.TSYLV_FP32_REFINED}
+    PREC = {0: _lib.TSYLV_FP64, 1: _lib.TSYLV_FP32_REFINED, 2: _lib.TSYLV_TF32_REFINED, 3: _lib.TSYLV_BF16_REFINED}
+    PNAME = {0: "fp64", 1: "fp32r", 2: "tf32r", 3: "bf16r"}
 
     def to_dev(a):
         a = np.asfortranarray(a)
@@ -396,6 +397,13 @@ def run_ours(args, ws, rank, local):
     if args.only:
         table = {name: (lambda name=name, gen=gen, prec=prec: solve(name, gen, prec)) for name, gen, prec in SOLVE_PARTS}
         table.update({"adjoint_fp64": lambda: adjoint(0), "adjoint_fp32r": lambda: adjoint(1), "batched_fp64": batched})
+        for prec in (2, 3):
+            for gen in (False, True):
+                pr = probs[gen]
+                pr["X"][prec] = ts.empty_fortran(shape, dev)
+                name = "%s_%s" % (PNAME[prec], "generalized" if gen else "laplace")
+                infos[name] = _lib.Info()
+                table[name] = (lambda gen=gen, prec=prec, name=name: solve(name, gen, prec))
         fn = table[args.only]
         for _ in range(args.warmup):
             fn()
@@ -628,29 +636,67 @@ def run_ours(args, ws, rank, local):
 
     # ---- the other configurations, measured beside the step (not part of
     # `value`; after the end-to-end leg, whose captured schedules a larger
-    # workspace would invalidate): the d = 4 generalized form FP64 vs FP32-refined, and the
+    # workspace would invalidate): the d = 4 generalized form in FP64 and every
+    # refined precision (FP32 solves; TF32 / BF16 tensor-core block updates),
+    # the tensor-core precisions at 256^3 and in the adjoint, and the
     # 512-equation batch FP32-refined against its FP64 solutions
     other = {}
+
+    def precision_sweep(qA, qC, qB, shp, precs):
+        res = {}
+        for prec in precs:
+            qX = ts.empty_fortran(shp, dev)
+            qi = _lib.Info()
+            if qC is not None:
+                fn = lambda: ts.gtsylv_solve(qA, qC, qB, X=qX, info=qi, precision=PREC[prec], max_refine=40)
+            else:
+                fn = lambda: ts.tsylv_solve(qA, qB, X=qX, info=qi, precision=PREC[prec], max_refine=40)
+            fn()
+            tm = event_ms(fn, 3)
+            _, rho, _ = ts.tsylv_residual(qA, qB, qX, qC, residual=_lib.TSYLV_RESID_FP64)
+            res[PNAME[prec]] = {"ms": tm, "iterations": qi.iterations, "rel_residual_fp64": rho}
+            del qX
+        if 0 in precs:
+            for prec in precs:
+                if prec:
+                    res[PNAME[prec]]["vs_fp64"] = res["fp64"]["ms"] / res[PNAME[prec]]["ms"]
+        return res
+
     if not args.no_other:
         for shp in D4_SHAPES:
             q = synthetic.problem(args.seed + rank, shp, generalized=True)
             qA = [to_dev(a) for a in q["A"]]
             qC = [to_dev(c) for c in q["C"]]
             qB = to_dev(q["B"])
-            res = {}
-            for prec in (0, 1):
-                qX = ts.empty_fortran(shp, dev)
-                qi = _lib.Info()
-                fn = lambda: ts.gtsylv_solve(qA, qC, qB, X=qX, info=qi, precision=PREC[prec])
-                fn()
-                tm = event_ms(fn, 3)
-                _, rho, _ = ts.tsylv_residual(qA, qB, qX, qC, residual=_lib.TSYLV_RESID_FP64)
-                res["fp64" if prec == 0 else "fp32r"] = {"ms": tm, "iterations": qi.iterations,
-                                                         "rel_residual_fp64": rho}
-                del qX
+            res = precision_sweep(qA, qC, qB, shp, (0, 1, 2, 3))
             res["mixed_vs_fp64"] = res["fp64"]["ms"] / res["fp32r"]["ms"]
             other["d4_generalized_" + "x".join(str(v) for v in shp)] = res
             del qA, qC, qB
+        for gen in (False, True):
+            pr = probs[gen]
+            other["tensorcore_256_" + ("generalized" if gen else "laplace")] = precision_sweep(
+                pr["A"], pr["C"], pr["B"], shape, (2, 3))
+        tag = "adjoint_tf32r"
+        infos[tag + "_fwd"] = _lib.Info()
+        infos[tag + "_bwd"] = _lib.Info()
+        Xt = ts.empty_fortran(ADJ_SHAPE, dev)
+
+        def adjoint_tc():
+            ts.tsylv_solve(adj["A"], adj["B"], X=Xt, info=infos[tag + "_fwd"], precision=PREC[2])
+            adj["out"][2] = ts.tsylv_backward(adj["A"], Xt, Xt - adj["Xs"], want_dB=True, want_dA=True,
+                                              info=infos[tag + "_bwd"], precision=PREC[2])
+        adjoint_tc()
+        tm = event_ms(adjoint_tc, max(3, args.steps))
+        dB, dA, _ = adj["out"][2]
+        dB0, dA0, _ = adj["out"][0]
+        other[tag] = {"ms": tm, "unknowns_per_s": 2 * Na / (tm * 1e-3),
+                      "iterations_fwd_bwd": [infos[tag + "_fwd"].iterations, infos[tag + "_bwd"].iterations],
+                      "vs_fp64": parts["adjoint_fp64"]["ms"] / tm,
+                      "rel_diff_vs_fp64": {
+                          "dB": float(torch.linalg.vector_norm(dB - dB0) / torch.linalg.vector_norm(dB0)),
+                          "dA": max(float(torch.linalg.matrix_norm(a - b) / torch.linalg.matrix_norm(b))
+                                    for a, b in zip(dA, dA0))}}
+        del Xt
         # general (dense) coefficients, Alg. 1: host Schur reduction, GPU
         # change-of-basis transforms (dense FP64 mode products) and the FP64
         # triangular solve, 256^3 Laplace form

@@ -27,9 +27,10 @@
  * soon as the blocks it reads are solved (opts->schedule = 0); the
  * alternative is one launch per anti-diagonal wavefront.  The launches of a
  * call are captured once in a CUDA graph and replayed.  The mixed-precision
- * solves (TSYLV_FP32_REFINED) solve in FP32 and refine in FP64 with a
- * double-float residual; their first two steps run pipelined in one launch
- * when the solve is latency-bound (opts->fuse_step).
+ * solves (TSYLV_FP32_REFINED, and TSYLV_TF32_REFINED / TSYLV_BF16_REFINED
+ * with tensor-core block updates) solve in low precision and refine in FP64
+ * with a double-float residual; their first two steps run pipelined in one
+ * launch when the solve is latency-bound (opts->fuse_step).
  *
  * Layout.  Tensors are dense and column-major with mode 1 fastest -- the
  * index map Eq. (2.1): element (i_1, ..., i_d) (0-based) is at
@@ -86,11 +87,17 @@ enum tsylv_precision {
                                 X_{k+1} = X_k + max|R_k| D_k (FP64);
                                 R_{k+1} = B - A(X_{k+1}) (opts->residual)
                                 until ||R|| / (||A|| ||X||) <= opts->tol        */
-    TSYLV_TF32_REFINED = 2,  /* reserved: TF32 tensor-core updates; this build returns
-                                TSYLV_EUNSUPPORTED (the FP32 solve of
-                                TSYLV_FP32_REFINED is latency-bound, so tensor
-                                cores would only cost accuracy)                    */
-    TSYLV_BF16_REFINED = 3   /* reserved, as TSYLV_TF32_REFINED                      */
+    TSYLV_TF32_REFINED = 2,  /* as TSYLV_FP32_REFINED, with the block updates of the
+                                low-precision solve on the tensor cores: operands
+                                rounded to TF32, FP32 accumulation (warp-level
+                                mma.sync); the in-block back-substitution stays
+                                FP32, the residual and X FP64-accurate.  The less
+                                accurate correction takes about one refinement
+                                step more than TSYLV_FP32_REFINED.  Persistent
+                                schedule only (opts->schedule = 1 returns
+                                TSYLV_EUNSUPPORTED)                                */
+    TSYLV_BF16_REFINED = 3   /* as TSYLV_TF32_REFINED with BF16 operands (about
+                                two steps more than TSYLV_FP32_REFINED)          */
 };
 
 enum tsylv_residual_kind {
@@ -126,11 +133,11 @@ typedef struct tsylv_opts {
                          2 runs the first two steps as one launch, the second
                          solve and both residuals following the first solve block
                          by block (the same result as separate steps, bit for
-                         bit); 1 runs the first step as one launch (each block:
-                         FP32 solve, X update, DF64 residual); 3 separate launches;
-                         0 (default) 2 when the solve's largest wavefront has
-                         fewer blocks than the GPU has resident CTAs for it
-                         (latency-bound), 3 otherwise. Other forms: separate.   */
+                         bit); 3 separate launches; 0 (default) 2 when the
+                         solve's largest wavefront has fewer blocks than the GPU
+                         has resident CTAs for it (latency-bound), 3 otherwise.
+                         Other forms: separate.  1 (the first step alone in one
+                         launch) is no longer offered: TSYLV_EUNSUPPORTED       */
 } tsylv_opts;
 
 typedef struct tsylv_info {

@@ -1,0 +1,13 @@
+// Persistent batched kernel instantiations: FP32 solve with TF32 tensor-core block updates, d = 3.
+#include "batched_kernel.cuh"
+
+namespace tsylv {
+
+template cudaError_t launch_batched_t<float, 3, false, kProdTF32>(const BatchArgs&, int, cudaStream_t);
+template cudaError_t prepare_batched_t<float, 3, false, kProdTF32>();
+template int batched_occupancy_t<float, 3, false, kProdTF32>();
+template cudaError_t launch_batched_t<float, 3, true, kProdTF32>(const BatchArgs&, int, cudaStream_t);
+template cudaError_t prepare_batched_t<float, 3, true, kProdTF32>();
+template int batched_occupancy_t<float, 3, true, kProdTF32>();
+
+}  // namespace tsylv

@@ -58,16 +58,18 @@ struct BatchArgs {
     long long timeout_ns;
 };
 
-// Persistent launch of `grid` CTAs (equations of order d, one form).
+// Persistent launch of `grid` CTAs (equations of order d, one form).  prod
+// (ProductKind) selects the arithmetic of the block updates: native, or for
+// T = float TF32 / BF16 tensor-core products.
 template <typename T>
-cudaError_t launch_batched(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_batched(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s, int prod = kProdNative);
 template <typename T>
 cudaError_t prepare_batched();
 // *dst = a, by one thread (a captured launch keeps `a` by value).
 cudaError_t launch_store_args(const WaveArgs& a, WaveArgs* dst, cudaStream_t s);
 // Resident CTAs per SM of the persistent kernel.
 template <typename T>
-int batched_occupancy(int d, bool gen);
+int batched_occupancy(int d, bool gen, int prod = kProdNative);
 
 // Block tensors of B and coefficient tiles of every equation; back to X.
 template <typename T>

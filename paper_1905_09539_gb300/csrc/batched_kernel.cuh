@@ -9,7 +9,7 @@
 
 namespace tsylv {
 
-template <typename T, int D, bool GENF>
+template <typename T, int D, bool GENF, int PK = kProdNative>
 __global__ void __launch_bounds__(kThreads, WaveCfg<T, D, GENF>::MINB) k_batched(const BatchArgs b) {
     using C = WaveCfg<T, D, GENF>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kThreads, WaveCfg<T, D, GENF>::MINB) k_batched
             s_ok = ok;
         }
         __syncthreads();
-        if (alive && s_ok) alive = wave_tile<T, D, GENF>(a, jb.tile, 0, 1, uses, bar);
+        if (alive && s_ok) alive = wave_tile<T, D, GENF, PK>(a, jb.tile, 0, 1, uses, bar);
         // publish the block: every thread's stores, then the count / flag
         // (one release by one thread after the barrier)
         __syncthreads();
@@ -53,25 +53,25 @@ __global__ void __launch_bounds__(kThreads, WaveCfg<T, D, GENF>::MINB) k_batched
     }
 }
 
-template <typename T, int D, bool GEN>
+template <typename T, int D, bool GEN, int PK = kProdNative>
 cudaError_t prepare_batched_t() {
     using C = WaveCfg<T, D, GEN>;
-    return cudaFuncSetAttribute(k_batched<T, D, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_batched<T, D, GEN, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(C::smem));
 }
 
-template <typename T, int D, bool GEN>
+template <typename T, int D, bool GEN, int PK = kProdNative>
 cudaError_t launch_batched_t(const BatchArgs& a, int grid, cudaStream_t s) {
     using C = WaveCfg<T, D, GEN>;
-    k_batched<T, D, GEN><<<grid, kThreads, C::smem, s>>>(a);
+    k_batched<T, D, GEN, PK><<<grid, kThreads, C::smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int D, bool GEN>
+template <typename T, int D, bool GEN, int PK = kProdNative>
 int batched_occupancy_t() {
     using C = WaveCfg<T, D, GEN>;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched<T, D, GEN>, kThreads, C::smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched<T, D, GEN, PK>, kThreads, C::smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return 1;
     }

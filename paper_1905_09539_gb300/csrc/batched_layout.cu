@@ -1,14 +1,16 @@
 // Layout kernels of the batched solve (one launch for all equations) and the
 // dispatch of the persistent kernel over (element type, d, form).
+#include <type_traits>
+
 #include "batched.h"
 
 namespace tsylv {
 
-template <typename T, int D, bool GEN>
+template <typename T, int D, bool GEN, int PK = kProdNative>
 cudaError_t launch_batched_t(const BatchArgs& a, int grid, cudaStream_t s);
-template <typename T, int D, bool GEN>
+template <typename T, int D, bool GEN, int PK = kProdNative>
 cudaError_t prepare_batched_t();
-template <typename T, int D, bool GEN>
+template <typename T, int D, bool GEN, int PK = kProdNative>
 int batched_occupancy_t();
 
 namespace {
@@ -154,53 +156,86 @@ cudaError_t launch_store_args(const WaveArgs& a, WaveArgs* dst, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_batched(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s) {
+namespace {
+
+template <typename T, int PK>
+cudaError_t launch_batched_pk(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s) {
     switch (d * 2 + (gen ? 1 : 0)) {
         case 2:
-        case 3: return launch_batched_t<T, 1, false>(a, grid, s);
-        case 4: return launch_batched_t<T, 2, false>(a, grid, s);
-        case 5: return launch_batched_t<T, 2, true>(a, grid, s);
-        case 6: return launch_batched_t<T, 3, false>(a, grid, s);
-        case 7: return launch_batched_t<T, 3, true>(a, grid, s);
-        case 8: return launch_batched_t<T, 4, false>(a, grid, s);
-        case 9: return launch_batched_t<T, 4, true>(a, grid, s);
+        case 3: return launch_batched_t<T, 1, false, PK>(a, grid, s);
+        case 4: return launch_batched_t<T, 2, false, PK>(a, grid, s);
+        case 5: return launch_batched_t<T, 2, true, PK>(a, grid, s);
+        case 6: return launch_batched_t<T, 3, false, PK>(a, grid, s);
+        case 7: return launch_batched_t<T, 3, true, PK>(a, grid, s);
+        case 8: return launch_batched_t<T, 4, false, PK>(a, grid, s);
+        case 9: return launch_batched_t<T, 4, true, PK>(a, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T>
-int batched_occupancy(int d, bool gen) {
+template <typename T, int PK>
+int batched_occupancy_pk(int d, bool gen) {
     switch (d * 2 + (gen ? 1 : 0)) {
         case 2:
-        case 3: return batched_occupancy_t<T, 1, false>();
-        case 4: return batched_occupancy_t<T, 2, false>();
-        case 5: return batched_occupancy_t<T, 2, true>();
-        case 6: return batched_occupancy_t<T, 3, false>();
-        case 7: return batched_occupancy_t<T, 3, true>();
-        case 8: return batched_occupancy_t<T, 4, false>();
-        case 9: return batched_occupancy_t<T, 4, true>();
+        case 3: return batched_occupancy_t<T, 1, false, PK>();
+        case 4: return batched_occupancy_t<T, 2, false, PK>();
+        case 5: return batched_occupancy_t<T, 2, true, PK>();
+        case 6: return batched_occupancy_t<T, 3, false, PK>();
+        case 7: return batched_occupancy_t<T, 3, true, PK>();
+        case 8: return batched_occupancy_t<T, 4, false, PK>();
+        case 9: return batched_occupancy_t<T, 4, true, PK>();
         default: return 1;
     }
 }
 
-template <typename T>
-cudaError_t prepare_batched() {
+template <typename T, int PK>
+cudaError_t prepare_batched_pk() {
     cudaError_t e = cudaSuccess;
-    if ((e = prepare_batched_t<T, 1, false>()) != cudaSuccess) return e;
-    if ((e = prepare_batched_t<T, 2, false>()) != cudaSuccess) return e;
-    if ((e = prepare_batched_t<T, 2, true>()) != cudaSuccess) return e;
-    if ((e = prepare_batched_t<T, 3, false>()) != cudaSuccess) return e;
-    if ((e = prepare_batched_t<T, 3, true>()) != cudaSuccess) return e;
-    if ((e = prepare_batched_t<T, 4, false>()) != cudaSuccess) return e;
-    return prepare_batched_t<T, 4, true>();
+    if ((e = prepare_batched_t<T, 1, false, PK>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<T, 2, false, PK>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<T, 2, true, PK>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<T, 3, false, PK>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<T, 3, true, PK>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<T, 4, false, PK>()) != cudaSuccess) return e;
+    return prepare_batched_t<T, 4, true, PK>();
 }
 
-template cudaError_t launch_batched<double>(int, bool, const BatchArgs&, int, cudaStream_t);
-template int batched_occupancy<double>(int, bool);
+}  // namespace
+
+template <typename T>
+cudaError_t launch_batched(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s, int prod) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (prod == kProdTF32) return launch_batched_pk<float, kProdTF32>(d, gen, a, grid, s);
+        if (prod == kProdBF16) return launch_batched_pk<float, kProdBF16>(d, gen, a, grid, s);
+    }
+    if (prod != kProdNative) return cudaErrorInvalidValue;
+    return launch_batched_pk<T, kProdNative>(d, gen, a, grid, s);
+}
+
+template <typename T>
+int batched_occupancy(int d, bool gen, int prod) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (prod == kProdTF32) return batched_occupancy_pk<float, kProdTF32>(d, gen);
+        if (prod == kProdBF16) return batched_occupancy_pk<float, kProdBF16>(d, gen);
+    }
+    return batched_occupancy_pk<T, kProdNative>(d, gen);
+}
+
+template <typename T>
+cudaError_t prepare_batched() {
+    cudaError_t e = prepare_batched_pk<T, kProdNative>();
+    if constexpr (std::is_same<T, float>::value) {
+        if (e == cudaSuccess) e = prepare_batched_pk<float, kProdTF32>();
+        if (e == cudaSuccess) e = prepare_batched_pk<float, kProdBF16>();
+    }
+    return e;
+}
+
+template cudaError_t launch_batched<double>(int, bool, const BatchArgs&, int, cudaStream_t, int);
+template int batched_occupancy<double>(int, bool, int);
 template cudaError_t prepare_batched<double>();
-template cudaError_t launch_batched<float>(int, bool, const BatchArgs&, int, cudaStream_t);
-template int batched_occupancy<float>(int, bool);
+template cudaError_t launch_batched<float>(int, bool, const BatchArgs&, int, cudaStream_t, int);
+template int batched_occupancy<float>(int, bool, int);
 template cudaError_t prepare_batched<float>();
 template cudaError_t launch_batch_pack<double>(const BatchGeom*, const BatchJob*, int, const BatchCoefJob*, int,
                                                const double*, const double*, const double*, cudaStream_t);

@@ -1,23 +1,11 @@
-// Fused first refinement step (FP32 solve + FP64 update + DF64 residual) of
-// the Laplace form: launch declarations.
+// Pipelined first two refinement steps of the Laplace form: launch
+// declarations.
 #pragma once
 
 #include "apply_kernel.cuh"
 #include "batched.h"
 
 namespace tsylv {
-
-struct FusedArgs {
-    BatchArgs b;          // one equation's blocks in wavefront order (jobs == nullptr)
-    ApplyArgs ap;         // the DF64 residual (kind Laplace) of every block
-    double* X;            // FP64 block tensor of the iterate
-    float* Xh;            // its float-pair split
-    float* Xl;
-    double* xpart;        // per-block sums of X^2
-    const double* nrm;    // nrm[1]: scale s of the step
-    int lag;              // residual job i follows solve job i + lag in the queue
-};
-
 
 // First two refinement steps of the Laplace form in one launch, pipelined
 // over the blocks: queue jobs (kind << 26 | block), kinds
@@ -45,11 +33,9 @@ struct Refine2Args {
     const double* nrm;
 };
 
-cudaError_t launch_refine2(int d, const Refine2Args& f, int grid, cudaStream_t s);
-int refine2_occupancy(int d);
-
-cudaError_t launch_fused(int d, const FusedArgs& f, int grid, cudaStream_t s);
-cudaError_t prepare_fused();
-int fused_occupancy(int d);
+// prod (ProductKind): arithmetic of the FP32 solves' block updates.
+cudaError_t launch_refine2(int d, int prod, const Refine2Args& f, int grid, cudaStream_t s);
+int refine2_occupancy(int d, int prod);
+cudaError_t prepare_refine2();
 
 }  // namespace tsylv

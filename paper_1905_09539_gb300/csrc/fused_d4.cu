@@ -1,12 +1,16 @@
-// Fused refinement step instantiation, d = 4.
+// Pipelined refinement launch instantiations, d = 4 (native, TF32 and BF16 block updates).
 #include "fused_kernel.cuh"
 
 namespace tsylv {
 
-template cudaError_t launch_fused_t<4>(const FusedArgs&, int, cudaStream_t);
-template cudaError_t prepare_fused_t<4>();
-template int fused_occupancy_t<4>();
-template cudaError_t launch_refine2_t<4>(const Refine2Args&, int, cudaStream_t);
-template int refine2_occupancy_t<4>();
+template cudaError_t launch_refine2_t<4, kProdNative>(const Refine2Args&, int, cudaStream_t);
+template int refine2_occupancy_t<4, kProdNative>();
+template cudaError_t prepare_refine2_t<4, kProdNative>();
+template cudaError_t launch_refine2_t<4, kProdTF32>(const Refine2Args&, int, cudaStream_t);
+template int refine2_occupancy_t<4, kProdTF32>();
+template cudaError_t prepare_refine2_t<4, kProdTF32>();
+template cudaError_t launch_refine2_t<4, kProdBF16>(const Refine2Args&, int, cudaStream_t);
+template int refine2_occupancy_t<4, kProdBF16>();
+template cudaError_t prepare_refine2_t<4, kProdBF16>();
 
 }  // namespace tsylv

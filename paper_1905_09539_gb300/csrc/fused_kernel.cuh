@@ -1,17 +1,6 @@
-// First step of the mixed-precision refinement of the Laplace form in one
-// persistent launch.  The queue holds two jobs per block: the solve jobs in
-// the dataflow order of a solve, and, `lag` solve jobs behind, the residual
-// jobs interleaved with them (S_0 .. S_{lag-1}, S_lag, R_0, S_lag+1, R_1, ...):
-//   solve job:    the FP32 solve of the block (the same per-block function as
-//                 a solve), X += s D on the block (FP64) with its float-pair
-//                 split, then publication of the block (its "solved" flag);
-//   residual job: the double-float residual R = B - A(X) of the block.  It
-//                 reads the blocks on the block's mode lines with a larger or
-//                 equal index -- the block itself and its solve's sources, all
-//                 solved before it -- so it waits for the block's own flag only.
-// By the time R_i is taken, block i has normally been solved, so residual
-// jobs (bound by the FP32 pipes) fill the SM time the latency-bound solve
-// leaves idle instead of queueing after it.
+// First two steps of the mixed-precision refinement of the Laplace form in
+// one persistent launch (see Refine2Args): the second FP32 solve and both
+// residuals follow the first solve block by block.
 #pragma once
 
 #include "apply_tile.cuh"
@@ -31,92 +20,7 @@ struct FusedCfg {
     static constexpr size_t smem = oBarA + 8 * CA::NST;
 };
 
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_fused_step(const FusedArgs f) {
-    using F = FusedCfg<D>;
-    using CW = typename F::CW;
-    using CA = typename F::CA;
-    constexpr int TD = CW::TD;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* barW = reinterpret_cast<uint64_t*>(smem_raw + F::oBarW);
-    uint64_t* barA = reinterpret_cast<uint64_t*>(smem_raw + F::oBarA);
-    __shared__ int s_job;
-    __shared__ double s_red[kThreads / 32];
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < CW::NST; q++) dev::mbar_init(&barW[q], 1);
-        for (int q = 0; q < CA::NST; q++) dev::mbar_init(&barA[q], 1);
-        dev::fence_mbar_init();
-    }
-    __syncthreads();
-    uint32_t usesW[CW::NST] = {};
-    uint32_t usesA[CA::NST] = {};
-    bool alive = true;
-    const WaveArgs& a = f.b.eqs[0];
-    const double sc = dev::step_scale(f.nrm[1]);
-    for (;;) {
-        if (threadIdx.x == 0) s_job = atomicAdd(f.b.head, 1);
-        __syncthreads();
-        const int j = s_job;
-        const int N = f.b.njobs, K = f.lag < N ? f.lag : N;
-        if (j >= 2 * N) break;
-        // job j -> solve job or residual job of the queue position's block
-        int idx;
-        bool resid;
-        if (j < K) {
-            idx = j;
-            resid = false;
-        } else if (j < K + 2 * (N - K)) {
-            const int r = j - K;
-            resid = r & 1;
-            idx = resid ? r >> 1 : K + (r >> 1);
-        } else {
-            idx = (N - K) + (j - K - 2 * (N - K));
-            resid = true;
-        }
-        if (resid) {
-            const long long t = f.b.tiles[idx];
-            if (threadIdx.x == 0) {
-                if (!dev::wait_at_least(a.ready + t, 1, f.b.abort, f.b.timeout_ns)) atomicOr(a.err, kErrTimeout);
-                dev::fence_proxy_async_all();
-            }
-            __syncthreads();
-            if (alive) apply_detail::apply_tile<D, apply_detail::kModeDF>(f.ap, t, smem_raw, barA, usesA);
-            __syncthreads();
-            continue;
-        }
-        const long long t = f.b.tiles[idx];
-        if (alive) alive = wave_tile<float, D, false>(a, t, 0, 1, usesW, barW);
-        __syncthreads();
-        // X += s D on the block, its split, and the block's sum of X^2
-        const float* Dt = static_cast<const float*>(a.X) + t * TD;
-        double ss = 0;
-        for (int e = threadIdx.x; e < TD; e += kThreads) {
-            const long long i = t * TD + e;
-            const double v = f.X[i] + sc * static_cast<double>(Dt[e]);
-            f.X[i] = v;
-            const float hv = static_cast<float>(v);
-            f.Xh[i] = hv;
-            f.Xl[i] = static_cast<float>(v - static_cast<double>(hv));
-            ss += v * v;
-        }
-        for (int w = 16; w >= 1; w >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, w);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ss;
-        // publish the block (every thread's stores, then the flag); the
-        // residual below reads the split through bulk copies (async proxy)
-        __threadfence();
-        dev::fence_proxy_async_all();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0;
-            for (int w = 0; w < kThreads / 32; w++) tot += s_red[w];
-            f.xpart[t] = tot;
-            dev::st_release(const_cast<int*>(a.ready) + t, 1);
-        }
-        __syncthreads();
-    }
-}
-
-template <int D>
+template <int D, int PK>
 __global__ void __launch_bounds__(kThreads) k_refine2(const Refine2Args f) {
     using F = FusedCfg<D>;
     using CW = typename F::CW;
@@ -154,7 +58,7 @@ __global__ void __launch_bounds__(kThreads) k_refine2(const Refine2Args f) {
         }
         __syncthreads();
         if (kind == 0 || kind == 2) {
-            if (alive) alive = wave_tile<float, D, false>(kind == 0 ? w1 : w2, t, 0, 1, usesW, barW);
+            if (alive) alive = wave_tile<float, D, false, PK>(kind == 0 ? w1 : w2, t, 0, 1, usesW, barW);
             __syncthreads();
             if (threadIdx.x == 0) dev::publish(const_cast<int*>((kind == 0 ? w1 : w2).ready) + t, 1, nullptr);
         } else if (kind == 1) {
@@ -172,35 +76,10 @@ __global__ void __launch_bounds__(kThreads) k_refine2(const Refine2Args f) {
     }
 }
 
-template <int D>
+template <int D, int PK>
 int refine2_occupancy_t() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refine2<D>, kThreads, FusedCfg<D>::smem) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return 1;
-    }
-    return nb > 0 ? nb : 1;
-}
-
-template <int D>
-cudaError_t launch_refine2_t(const Refine2Args& f, int grid, cudaStream_t s) {
-    k_refine2<D><<<grid, kThreads, FusedCfg<D>::smem, s>>>(f);
-    return cudaGetLastError();
-}
-
-template <int D>
-cudaError_t prepare_fused_t() {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_step<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(FusedCfg<D>::smem));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_refine2<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(FusedCfg<D>::smem));
-}
-
-template <int D>
-int fused_occupancy_t() {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fused_step<D>, kThreads, FusedCfg<D>::smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refine2<D, PK>, kThreads, FusedCfg<D>::smem) !=
         cudaSuccess) {
         (void)cudaGetLastError();
         return 1;
@@ -208,10 +87,16 @@ int fused_occupancy_t() {
     return nb > 0 ? nb : 1;
 }
 
-template <int D>
-cudaError_t launch_fused_t(const FusedArgs& f, int grid, cudaStream_t s) {
-    k_fused_step<D><<<grid, kThreads, FusedCfg<D>::smem, s>>>(f);
+template <int D, int PK>
+cudaError_t launch_refine2_t(const Refine2Args& f, int grid, cudaStream_t s) {
+    k_refine2<D, PK><<<grid, kThreads, FusedCfg<D>::smem, s>>>(f);
     return cudaGetLastError();
+}
+
+template <int D, int PK>
+cudaError_t prepare_refine2_t() {
+    return cudaFuncSetAttribute(k_refine2<D, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(FusedCfg<D>::smem));
 }
 
 }  // namespace tsylv

@@ -172,8 +172,7 @@ struct Call {
     int flow_grid = 0;        // CTAs of the persistent launch
     bool update = false;      // refinement step: residual updated from the FP32 correction
     bool first = false;       // first refinement step (X = 0 before it: X after it is s D exactly)
-    bool fused = false;       // full refinement step in one launch (Laplace form, DF64 residual, persistent)
-    int fused_grid = 0;
+    int prod = kProdNative;   // arithmetic of the FP32 solve's block updates (native / TF32 / BF16 tensor cores)
     bool pipe = false;        // first two refinement steps pipelined in one launch (Laplace form)
     int pipe_grid = 0;
 };
@@ -236,7 +235,7 @@ cudaError_t enqueue_waves(const Call& c, const Layout& L, cudaStream_t s) {
         ba.done = nullptr;
         ba.abort = ctl + 1;
         ba.timeout_ns = kTimeoutNs;
-        return launch_batched<T>(p.d, p.gen, ba, c.flow_grid, s);
+        return launch_batched<T>(p.d, p.gen, ba, c.flow_grid, s, sizeof(T) == 4 ? c.prod : kProdNative);
     }
     for (size_t w = 0; w < p.wave_off.size(); w++) {
         wa.tiles = tab + p.t_wave + p.wave_off[w];
@@ -441,57 +440,6 @@ cudaError_t enqueue_ref_iter(const Call& c, cudaStream_t s) {
     }
     // low-precision solve of A(D) = R / max|R|
     TRY(launch_scale_to_f32(reinterpret_cast<double*>(b + R.Rt), reinterpret_cast<float*>(b + L.X), nrm, nel, s));
-    if (c.fused && !c.update) {
-        // solve, update, split and DF64 residual block by block in one launch
-        int* ctl = reinterpret_cast<int*>(b + L.fctl);
-        int* flags = reinterpret_cast<int*>(b + L.flags);
-        TRY(cudaMemsetAsync(ctl, 0, 64, s));
-        TRY(cudaMemsetAsync(flags, 0, static_cast<size_t>(p.ntiles) * sizeof(int), s));
-        WaveArgs wa = wave_args(p, L, b);
-        wa.ready = flags;
-        wa.abort = ctl + 1;
-        wa.csize = 1;
-        WaveArgs* dargs = reinterpret_cast<WaveArgs*>(b + L.fargs);
-        TRY(launch_store_args(wa, dargs, s));
-        FusedArgs f{};
-        f.b.eqs = dargs;
-        f.b.jobs = nullptr;
-        f.b.tiles = reinterpret_cast<const int*>(b + L.tab) + p.t_wave;
-        f.b.njobs = static_cast<int>(p.ntiles);
-        f.b.head = ctl;
-        f.b.done = nullptr;
-        f.b.abort = ctl + 1;
-        f.b.timeout_ns = kTimeoutNs;
-        ApplyArgs& ap = f.ap;
-        for (int mu = 0; mu < p.d; mu++) {
-            ap.nb[mu] = p.nb[mu];
-            ap.tstride[mu] = p.tstride[mu];
-            ap.A[mu] = b + R.Ah[mu];
-            ap.Al[mu] = b + R.Al[mu];
-        }
-        ap.ntiles = p.ntiles;
-        ap.kind = kApplyLaplace;
-        ap.s1 = b + R.Xh;
-        ap.s1l = b + R.Xl;
-        ap.B = reinterpret_cast<const double*>(b + R.Bt);
-        ap.R = reinterpret_cast<double*>(b + R.Rt);
-        ap.part = reinterpret_cast<double*>(b + R.part);
-        ap.err = reinterpret_cast<int*>(b + L.err);
-        ap.timeout_ns = kTimeoutNs;
-        f.X = reinterpret_cast<double*>(b + R.Xt);
-        f.Xh = reinterpret_cast<float*>(b + R.Xh);
-        f.Xl = reinterpret_cast<float*>(b + R.Xl);
-        f.xpart = reinterpret_cast<double*>(b + R.xpart);
-        f.nrm = nrm;
-        f.lag = static_cast<int>(p.ntiles);  // residual jobs after every solve job (measured best)
-        TRY(launch_fused(p.d, f, c.fused_grid, s));
-        TRY(mark(c, 1, s));
-        TRY(mark(c, 2, s));
-        if (side) TRY(cudaStreamWaitEvent(s, side->join, 0));
-        TRY(launch_reduce(reinterpret_cast<double*>(b + R.part), reinterpret_cast<double*>(b + R.xpart), p.ntiles,
-                          reinterpret_cast<double*>(b + R.nrm), s));
-        return mark(c, 3, s);
-    }
     TRY(enqueue_waves<float>(c, L, s));
     // X += max|R| D  (FP64), its float-pair split, block sums of X^2
     // the float-pair X only feeds a full DF64 residual of a later step
@@ -586,7 +534,7 @@ cudaError_t enqueue_ref_pipe(const Call& c, cudaStream_t s) {
     f.X2 = reinterpret_cast<float*>(b + R.Xh);
     f.nrm = nrm;
     // timing marks: 0 -> 1 both solves with their residuals, 1 -> 2 the X update
-    TRY(launch_refine2(p.d, f, c.pipe_grid, s));
+    TRY(launch_refine2(p.d, c.prod, f, c.pipe_grid, s));
     TRY(mark(c, 1, s));
     // X = s D1 + s D2 (FP64), block sums of X^2
     double* xpart = reinterpret_cast<double*>(b + R.xpart);
@@ -693,12 +641,12 @@ int run_enqueue(Plan& p, const std::vector<const void*>& key, bool use_graph, cu
 }
 
 // CTAs of a persistent launch: every resident slot of the GPU, at most one per block.
-int flow_grid(int elem, int d, bool gen, long long ntiles) {
+int flow_grid(int elem, int d, bool gen, long long ntiles, int prod = kProdNative) {
     static std::mutex m;
     static std::map<int, int> cache;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int key = ((dev * 2 + (elem == 4 ? 1 : 0)) * 8 + d) * 2 + (gen ? 1 : 0);
+    const int key = (((dev * 2 + (elem == 4 ? 1 : 0)) * 8 + d) * 2 + (gen ? 1 : 0)) * 4 + prod;
     int slots = 0;
     {
         std::lock_guard<std::mutex> lk(m);
@@ -708,7 +656,7 @@ int flow_grid(int elem, int d, bool gen, long long ntiles) {
         } else {
             int sms = 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
-            const int occ = elem == 4 ? batched_occupancy<float>(d, gen) : batched_occupancy<double>(d, gen);
+            const int occ = elem == 4 ? batched_occupancy<float>(d, gen, prod) : batched_occupancy<double>(d, gen);
             slots = sms * occ;
             cache[key] = slots;
         }
@@ -716,36 +664,13 @@ int flow_grid(int elem, int d, bool gen, long long ntiles) {
     return static_cast<int>(ntiles < slots ? ntiles : slots);
 }
 
-// CTAs of the fused first refinement step.
-int fused_grid(int d, long long ntiles) {
-    static std::mutex m;
-    static std::map<int, int> cache;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const int key = dev * 8 + d;
-    int slots = 0;
-    {
-        std::lock_guard<std::mutex> lk(m);
-        auto it = cache.find(key);
-        if (it != cache.end()) {
-            slots = it->second;
-        } else {
-            int sms = 0;
-            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
-            slots = sms * fused_occupancy(d);
-            cache[key] = slots;
-        }
-    }
-    return static_cast<int>(ntiles < slots ? ntiles : slots);
-}
-
 // CTAs of the pipelined first two refinement steps.
-int pipe_grid(int d, long long ntiles) {
+int pipe_grid(int d, long long ntiles, int prod) {
     static std::mutex m;
     static std::map<int, int> cache;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int key = dev * 8 + d;
+    const int key = (dev * 8 + d) * 4 + prod;
     int slots = 0;
     {
         std::lock_guard<std::mutex> lk(m);
@@ -755,7 +680,7 @@ int pipe_grid(int d, long long ntiles) {
         } else {
             int sms = 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
-            slots = sms * refine2_occupancy(d);
+            slots = sms * refine2_occupancy(d, prod);
             cache[key] = slots;
         }
     }
@@ -777,7 +702,7 @@ int prepare_kernels() {
         if (e == cudaSuccess) e = prepare_apply_dfh();
         if (e == cudaSuccess) e = prepare_batched<double>();
         if (e == cudaSuccess) e = prepare_batched<float>();
-        if (e == cudaSuccess) e = prepare_fused();
+        if (e == cudaSuccess) e = prepare_refine2();
         if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
         prepared[dev] = true;
     }
@@ -867,6 +792,9 @@ int check_opts(const tsylv_opts& o, int d) {
         o.use_graph < 0 || o.use_graph > 1)
         return -1;
     if (o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d))) return TSYLV_EUNSUPPORTED;
+    // fuse_step 1 (the first step as one launch) is no longer offered: it
+    // measured slower than separate launches
+    if (o.fuse_step == 1) return TSYLV_EUNSUPPORTED;
     return 0;
 }
 
@@ -927,14 +855,17 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -(6 + sh);
     if (work_bytes < solver_workspace_bytes(d, n, gen, o, transposed)) return -(7 + sh);
     if (int st = check_opts(o, d)) return st < 0 ? -(8 + sh) : st;
-    if (o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) return TSYLV_EUNSUPPORTED;
     const bool refined = o.precision != TSYLV_FP64;
+    // the tensor-core precisions run the persistent schedule only
+    if ((o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) && o.schedule != 0)
+        return TSYLV_EUNSUPPORTED;
 
     Call c;
     c.d = d;
     c.gen = gen && d >= 2;
     c.flip = transposed;
     c.df = o.residual == TSYLV_RESID_DF64;
+    c.prod = o.precision == TSYLV_TF32_REFINED ? kProdTF32 : o.precision == TSYLV_BF16_REFINED ? kProdBF16 : kProdNative;
     for (int mu = 0; mu < d; mu++) {
         c.n[mu] = n[mu];
         c.A[mu] = A[mu];
@@ -953,11 +884,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     c.timing = o.timing != 0;
     if (int st = ensure_events(c)) return st;
     c.persistent = o.schedule == 0;
-    if (c.persistent) c.flow_grid = flow_grid(refined ? 4 : 8, d, c.gen, c.plan->ntiles);
-    // (d = 1 keeps separate launches: its fused launch is refused with an
-    // invalid-argument error whose cause is not understood yet)
-    c.fused = refined && c.persistent && !c.gen && c.df && o.fuse_step == 1 && d >= 2;
-    if (c.fused) c.fused_grid = fused_grid(d, c.plan->ntiles);
+    if (c.persistent) c.flow_grid = flow_grid(refined ? 4 : 8, d, c.gen, c.plan->ntiles, c.prod);
     // pipelined first two steps: always (2), or by default (0) when the solve is
     // latency-bound, i.e. its largest wavefront has fewer blocks than a
     // persistent launch has resident CTAs (measured: faster there, slower on
@@ -966,13 +893,13 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (o.fuse_step == 0 && refined && c.plan->n_rjobs > 0) {
         int wmax = 0;
         for (int w : c.plan->wave_cnt) wmax = std::max(wmax, w);
-        want_pipe = wmax < flow_grid(4, d, false, 1LL << 40);
+        want_pipe = wmax < flow_grid(4, d, false, 1LL << 40, c.prod);
     }
     c.pipe = refined && c.persistent && !c.gen && c.df && want_pipe && d >= 2 && c.plan->n_rjobs > 0 &&
              o.max_refine >= 2;
-    if (c.pipe) c.pipe_grid = pipe_grid(d, 4 * c.plan->ntiles);
+    if (c.pipe) c.pipe_grid = pipe_grid(d, 4 * c.plan->ntiles, c.prod);
     const int tagbase = (transposed ? 1 : 0) | (c.timing ? 2 : 0) | (c.df ? 4 : 0) | (c.persistent ? 256 : 0) |
-                        (c.fused ? 1024 : 0);
+                        (c.prod << 14);
 
     if (!refined) {
         c.L = make_layout(d, c.n, c.plan->nb, c.gen, 8, c.plan->tab.size());

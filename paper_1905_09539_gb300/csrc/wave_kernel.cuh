@@ -16,6 +16,7 @@
 #pragma once
 
 #include "device_common.cuh"
+#include "mma_update.cuh"
 #include "tsylv_internal.h"
 
 namespace tsylv {
@@ -661,12 +662,18 @@ __device__ int group_inverse(const TileSmem<T, D, GEN>& sm, int e, T* out) {
 // caller runs many blocks on the same barriers).  Returns false when a wait
 // ran out of time (the error word is set; no copy of this call is left in
 // flight).
-template <typename T, int D, bool GENF>
+// PK selects the arithmetic of the block updates: the native FMA pipes, or
+// (FP32 solves only) TF32 / BF16 tensor-core products with FP32 accumulation.
+template <typename T, int D, bool GENF, int PK = kProdNative>
 __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, const int rank, const int csize,
                                           uint32_t (&uses)[WaveCfg<T, D, GENF>::NST], uint64_t* bar) {
     using C = WaveCfg<T, D, GENF>;
     constexpr int TE = C::TE, TD = C::TD, TC = C::TC, EPT = C::EPT, NACC = C::NACC;
     constexpr bool GEN = C::GEN;
+    constexpr bool TCU = PK != kProdNative;  // tensor-core updates
+    static_assert(!TCU || sizeof(T) == 4, "tensor-core block updates serve the FP32 solve");
+    using Q = MmaCfg<D, TCU ? PK : kProdTF32>;
+    constexpr int NS = GEN ? NACC : D;        // accumulator slots of the fragments
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* sbase = reinterpret_cast<T*>(smem_raw);
     T* stage = sbase + C::oStage;
@@ -797,6 +804,15 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     for (int s = 0; s < NACC; s++)
 #pragma unroll
         for (int q = 0; q < EPT; q++) acc[s][q] = T(0);
+    float cfr[TCU ? NS : 1][TCU ? Q::UPW : 1][4];
+    if constexpr (TCU) {
+#pragma unroll
+        for (int s = 0; s < NS; s++)
+#pragma unroll
+            for (int u = 0; u < Q::UPW; u++)
+#pragma unroll
+                for (int h = 0; h < 4; h++) cfr[s][u][h] = 0.f;
+    }
 
     constexpr int NST = C::NST;
     // decode the first JT jobs and, in a persistent launch, test their source
@@ -1004,7 +1020,10 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         }
         int L, Jp;
         job(j0 + jj, L, Jp);
-        dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE);
+        if constexpr (TCU)
+            mma_dispatch<D, GEN, PK, NS>(L, cfr, reinterpret_cast<const float*>(stage + stg * C::STAGE));
+        else
+            dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE);
         // every thread is done reading the stage (the barrier orders those
         // reads before the copies that refill it, as for a consumer-release
         // mbarrier arrival)
@@ -1021,6 +1040,17 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     }
 #pragma unroll
     for (int q = 0; q < NST; q++) uses[q] += static_cast<uint32_t>((njob - q + NST - 1) / NST);
+    if constexpr (TCU) {
+        // fragments -> element order (shared memory) -> the thread's own elements
+        mma_store<D, GEN, PK, NS>(cfr, reinterpret_cast<float*>(red));
+#pragma unroll
+        for (int s = 0; s < NACC; s++)
+#pragma unroll
+            for (int q = 0; q < EPT; q++) {
+                const int e = tid + q * kThreads;
+                if ((TD % kThreads) == 0 || e < TD) acc[s][q] = red[s * TD + e];
+            }
+    }
 
     // ---- partial sums -> shared memory (the generalized form's Horner chain
     // mixes elements; a cluster reduces through it), cluster reduction into rank 0

@@ -32,3 +32,15 @@ def norm_op(A, C=None):
         return sum(np.linalg.norm(a, 2) for a in A)
     return sum(np.linalg.norm(A[mu], 2) * np.prod([np.linalg.norm(C[e], 2) for e in range(d) if e != mu])
                for mu in range(d))
+
+
+def oracle_recursive_job(args):
+    """O-B solve of a seeded problem in a worker process (started with the
+    'spawn' method, so that no CUDA state is inherited): (seed, shape,
+    generalized, nmin) -> X.  Used to compute large oracle results in
+    parallel with each other."""
+    import oracle
+    import synthetic
+    seed, shape, gen, nmin = args
+    p = synthetic.problem(seed, shape, generalized=gen)
+    return oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=nmin)

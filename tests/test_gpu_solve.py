@@ -241,3 +241,27 @@ def test_bad_structure_rejected(lib):
     A[1][4, 3] = 0.5      # two consecutive subdiagonal entries
     _, st = lib.tsylv_solve([to_dev(a) for a in A], to_dev(p["B"]), check=False)
     assert st == -3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32r"])
+@pytest.mark.parametrize("shape,force", [
+    # d = 3: 12 x 10 x 9 = 1080 blocks, more than the resident CTAs of the
+    # persistent d-term kernel, so blocks wait on blocks of running CTAs
+    ((96, 80, 72), [[7, 31, 55], [15, 39], [23, 47]]),
+    # d = 4: 6 x 6 x 5 x 5 = 900 blocks, more than the d = 4 kernel's resident CTAs
+    ((24, 24, 20, 20), [[3, 11], [7], [3, 15], [11]]),
+])
+def test_dterm_deep_queue_parity(lib, shape, force, prec):
+    """d-term form in the deep-queue regime of the persistent schedule, 2x2
+    blocks across block boundaries: element by element against O-B."""
+    p = synthetic.problem(9, shape, generalized=True, force_blocks=force)
+    Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+    A = [to_dev(a) for a in p["A"]]
+    C = [to_dev(c) for c in p["C"]]
+    prec_id = lib.TSYLV_FP64 if prec == "fp64" else lib.TSYLV_FP32_REFINED
+    X, st = lib.gtsylv_solve(A, C, to_dev(p["B"]), precision=prec_id)
+    assert st == 0
+    Xg = to_host(X)
+    tol = TOL if prec == "fp64" else 1e-10
+    assert rel_err(Xg, Xo) <= tol
+    assert max_rel(Xg, Xo) <= tol

@@ -91,7 +91,9 @@ def test_option_validation_without_gpu(lib):
     for kw in ({"fuse_step": 4}, {"fuse_step": -1}, {"schedule": 2}, {"partition": 2}, {"resid_update": 2},
                {"precision": 9}, {"tol": 0.0}, {"split": -1}, {"max_refine": -1}, {"residual": 7}):
         assert st(**kw) == -8, kw
-    for kw in ({"host_io": 1}, {"precision": _lib.TSYLV_TF32_REFINED}, {"precision": _lib.TSYLV_BF16_REFINED}):
+    for kw in ({"host_io": 1}, {"fuse_step": 1}, {"nmin": 5},
+               {"precision": _lib.TSYLV_TF32_REFINED, "schedule": 1},
+               {"precision": _lib.TSYLV_BF16_REFINED, "schedule": 1}):
         assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
 
 
