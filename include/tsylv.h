@@ -46,8 +46,8 @@
  * caller.  The solver entry points allocate no device memory: every scratch
  * buffer is carved out of `work`, whose size comes from the matching
  * *_workspace_bytes query (256-byte alignment is required).  In-place use
- * (X == B) is allowed.  (tsylv_transform's cuBLAS handle and the diagnostic
- * tsylv_selftest_wait_timeout are the documented exceptions.)
+ * (X == B) is allowed.  (The diagnostic tsylv_selftest_wait_timeout is the
+ * documented exception.)
  *
  * Streams.  Work is queued on `stream`.  Each call reads the 2x2 block
  * structure of A back to the host (a short synchronisation on `stream`
@@ -313,7 +313,7 @@ int tsylv_solve_batched(int count, const int* d, const int64_t* n_packed, const 
 int tsylv_solve_noalloc(int d, const int64_t* n, const double* const* A, const double* B, double* X,
                         const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
 
-/* Change of basis of a tensor (Alg. 1, lines 3 and 5; Sec. 3's generalized
+/* Change of basis of a tensor (Alg. 1: right-hand side in, solution out; Sec. 3's generalized
  * Schur factors Q, Z for the d-term form): Y = X x_1 op(M_1) x_2 op(M_2) ...
  * x_d op(M_d), with op(M) = M (trans[mu] == 0) or M^T (trans[mu] != 0; trans
  * may be NULL: no transposes) and X x_mu N the mode-mu product
@@ -321,8 +321,8 @@ int tsylv_solve_noalloc(int d, const int64_t* n, const double* const* A, const d
  * With orthogonal Schur factors this takes an equation with general
  * coefficients to the quasi-triangular form tsylv_solve / gtsylv_solve take
  * (B x_mu U_mu^T), and the solution back (X x_mu U_mu).  Dense FP64 matrix
- * products through cuBLAS (strided-batched DGEMM on `stream`; the library keeps
- * one cuBLAS handle per host thread and device).  X, Y: column-major device tensors, Y may equal X;
+ * products on the FP64 tensor cores (the library's own DMMA kernel, one launch
+ * per transformed mode, on `stream`).  X, Y: column-major device tensors, Y may equal X;
  * M[mu]: column-major n_mu x n_mu device matrices.  work: device memory of at
  * least tsylv_transform_workspace_bytes(d, n) bytes, 256-byte aligned.
  * Returns 0, -i for a bad i-th argument (before any GPU work), or TSYLV_ECUDA. */

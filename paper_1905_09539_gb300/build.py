@@ -68,7 +68,7 @@ def build(verbose=False, jobs=None, extra=()):
     if todo or not os.path.exists(LIB):
         tmp = LIB + ".tmp%d" % os.getpid()
         run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs +
-            ["-lcublas", "-Xlinker", "-rpath", "-Xlinker", "/usr/local/cuda/lib64"])
+            ["-Xlinker", "-rpath", "-Xlinker", "/usr/local/cuda/lib64"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -1,39 +1,20 @@
 // Dense mode transforms Y = X x_1 op(M_1) x_2 ... x_d op(M_d) of column-major
-// tensors: the orthogonal changes of basis of Alg. 1 (lines 3 and 5) and of
-// its generalized counterpart (Sec. 3, the Q and Z factors of the
+// tensors: the orthogonal changes of basis of Alg. 1 (right-hand side in,
+// solution out) and of its generalized counterpart (Sec. 3, the Q and Z factors of the
 // generalized Schur forms), which take an equation with general coefficients
 // to the (quasi-)triangular one the solver handles and its solution back.
-// Plain dense FP64 matrix products: cuBLAS (strided-batched DGEMM).
-#include <cublas_v2.h>
-
+// Dense FP64 mode products on the tensor cores (DMMA, dmma_modeprod.cu).
 #include <cstring>
-#include <map>
 
 #include "solver.h"
 #include "tsylv_internal.h"
 
 namespace tsylv {
 
+cudaError_t launch_dmma_modeprod(const double* X, const double* M, bool trans, double* Y, long long L, long long m,
+                                 long long R, cudaStream_t s);
+
 namespace {
-
-// One cuBLAS handle per host thread and device (a handle's stream is set per
-// call, so threads must not share one).
-cublasHandle_t handle_for_device() {
-    thread_local std::map<int, cublasHandle_t> handles;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    auto it = handles.find(dev);
-    if (it != handles.end()) return it->second;
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
-    handles[dev] = h;
-    return h;
-}
-
-int cublas_fail(cublasStatus_t st, const char* where) {
-    (void)st;
-    return cuda_fail_msg(where);
-}
 
 bool dims_ok(int d, const int64_t* n, long long* N) {
     if (d < 1 || d > kMaxD || !n) return false;
@@ -58,7 +39,8 @@ size_t transform_workspace_bytes(int d, const int64_t* n) {
 // Y(.., i_mu, ..) = sum_k op(M_mu)(i_mu, k) X(.., k, ..) applied mode after
 // mode.  For mode mu the tensor is R = prod_{eta > mu} n_eta column-major
 // L x n_mu matrices (L = prod_{eta < mu} n_eta) and each becomes X_r op(M)^T;
-// for L = 1 the whole mode is the single product op(M) X (n_mu x R).
+// for L = 1 the whole mode is the single product op(M) X (n_mu x R).  Every
+// product runs in the project's DMMA kernel (no library GEMM).
 int transform(int d, const int64_t* n, const double* const* M, const int* trans, const double* X, double* Y,
               void* work, size_t work_bytes, cudaStream_t stream) {
     long long N = 0;
@@ -78,17 +60,12 @@ int transform(int d, const int64_t* n, const double* const* M, const int* trans,
             return cuda_fail(e, "transform: copy");
         return TSYLV_OK;
     }
-    cublasHandle_t h = handle_for_device();
-    if (!h) return cuda_fail_msg("transform: cublasCreate");
-    cublasStatus_t cs;
-    if ((cs = cublasSetStream(h, stream)) != CUBLAS_STATUS_SUCCESS) return cublas_fail(cs, "transform: cublasSetStream");
     double* tmp = static_cast<double*>(work);
     // products alternate between tmp and Y so that the last one writes Y;
     // the first reads X, which may alias Y: then it writes tmp and an odd
     // count ends with a copy
     const bool alias = X == Y;
     const double* src = X;
-    const double one = 1.0, zero = 0.0;
     for (int j = 0; j < na; j++) {
         const int mu = active[j];
         double* dst;
@@ -96,23 +73,11 @@ int transform(int d, const int64_t* n, const double* const* M, const int* trans,
             dst = (j % 2 == 0) ? tmp : Y;
         else
             dst = ((na - 1 - j) % 2 == 0) ? Y : tmp;
-        const int m = static_cast<int>(n[mu]);
         long long L = 1, R = 1;
         for (int eta = 0; eta < mu; eta++) L *= n[eta];
         for (int eta = mu + 1; eta < d; eta++) R *= n[eta];
-        const cublasOperation_t opM = (trans && trans[mu]) ? CUBLAS_OP_T : CUBLAS_OP_N;
-        if (L == 1) {
-            if (R > (1LL << 31) - 1) return cuda_fail_msg("transform: mode too long");
-            cs = cublasDgemm(h, opM, CUBLAS_OP_N, m, static_cast<int>(R), m, &one, M[mu], m, src, m, &zero, dst, m);
-        } else {
-            if (L > (1LL << 31) - 1 || R > (1LL << 31) - 1) return cuda_fail_msg("transform: mode too long");
-            // dst_r (L x m) = src_r (L x m) op(M)^T
-            const cublasOperation_t opB = opM == CUBLAS_OP_N ? CUBLAS_OP_T : CUBLAS_OP_N;
-            cs = cublasDgemmStridedBatched(h, CUBLAS_OP_N, opB, static_cast<int>(L), m, m, &one, src,
-                                           static_cast<int>(L), L * m, M[mu], m, 0, &zero, dst,
-                                           static_cast<int>(L), L * m, static_cast<int>(R));
-        }
-        if (cs != CUBLAS_STATUS_SUCCESS) return cublas_fail(cs, "transform: DGEMM");
+        if ((e = launch_dmma_modeprod(src, M[mu], trans && trans[mu], dst, L, n[mu], R, stream)) != cudaSuccess)
+            return cuda_fail(e, "transform: mode product");
         src = dst;
     }
     if (src != Y) {
