@@ -198,51 +198,87 @@ def grad_flops(shape):
 
 # ----------------------------------------------------------------- CPU oracle
 
-def oracle_step_seconds(sizes, seed=0):
-    """Single-thread oracle time of one step, from bounded samples scaled to
-    the full workload by the algorithmic-flop ratio of each part.
-
-    sizes: (laplace sample shape, generalized sample shape, adjoint sample
-    shape, number of batch equations sampled)."""
+def _batch_worker(args):
+    """One batch equation solved by the oracle in a worker process ('spawn'; one thread)."""
     import oracle
     import synthetic
-    sl, sg, sa, nb = sizes
-    full = (256, 256, 256)
-    detail = {}
-    t_step = 0.0
-    for gen, shape in ((False, sl), (True, sg)):
-        p = synthetic.problem(seed, shape, generalized=gen)
+    seed, e, shape = args
+    q = synthetic.problem([seed, 1 + e], shape)
+    t0 = time.perf_counter()
+    oracle.solve_recursive(q["A"], q["B"], None, nmin=8)
+    return time.perf_counter() - t0
+
+
+# The sampling rule of the CPU oracle, one rule for the reference arm and for
+# the cpu_baseline object of the GPU arm.  A 256^3 generalized solve takes the
+# oracle about three minutes, so the two 256^3 parts are timed on a 128^3
+# sample of the same distributions and scaled by the ratio of algorithmic
+# flops (every off-diagonal entry of the update blocks once): checked against
+# full 256^3 runs on an x86 host, 1.07 s -> 17.2 s predicted vs 17.6 s run
+# (Laplace), 10.5 s -> 171 s vs 180 s (generalized).  The adjoint workload
+# (200,160,120) and the 512-equation batch run in full.  The oracle is serial
+# C: a single solve uses one core (its recursion is a chain of dependent
+# steps); with more than one core the batch's independent equations are
+# spread over worker processes, one core each.
+ORACLE_PARTS = ("laplace", "generalized", "adjoint", "batched")
+ORACLE_SAMPLE = (128, 128, 128)
+_FULL_FLOPS = {}
+
+
+def oracle_part_seconds(part, threads, seed=0):
+    """Oracle seconds of one part of the bench step (FP64 and refined parts
+    counted), by the rule above, on `threads` host cores."""
+    import multiprocessing
+    import oracle
+    import synthetic
+    used = threads if threads > 0 else (os.cpu_count() or 1)
+    if part in ("laplace", "generalized"):
+        gen = part == "generalized"
+        if gen not in _FULL_FLOPS:
+            q = synthetic.problem(seed, (256, 256, 256), generalized=gen)
+            _FULL_FLOPS[gen] = algorithmic_flops(q["A"], q["C"])
+        p = synthetic.problem(seed, ORACLE_SAMPLE, generalized=gen)
         t0 = time.perf_counter()
         oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=8)
         dt = time.perf_counter() - t0
-        ff = gen_flops_dense(full) if gen else laplace_flops_dense(full)
-        scaled = dt * ff / algorithmic_flops(p["A"], p["C"])
-        t_step += 2 * scaled  # the FP64 and the refined part: one oracle solve each
-        detail["generalized" if gen else "laplace"] = {"shape": list(shape), "seconds": dt}
-    # adjoint: forward solve, transposed solve, masked contractions
-    p = synthetic.problem(seed, sa)
-    t0 = time.perf_counter()
-    X = oracle.solve_recursive(p["A"], p["B"], None, nmin=8)
-    Lam = oracle.solve_recursive(p["A"], X - p["Xstar"], None, nmin=8, transpose=True)
-    oracle.grad(p["A"], X, Lam)
-    dt = time.perf_counter() - t0
-    fs = 2 * algorithmic_flops(p["A"]) + grad_flops(sa)
-    ff = 2 * laplace_flops_dense(ADJ_SHAPE) + grad_flops(ADJ_SHAPE)
-    t_step += 2 * dt * ff / fs  # FP64 and refined adjoint parts
-    detail["adjoint"] = {"shape": list(sa), "seconds": dt}
-    # batch: the first nb equations, scaled by the flops of all of them
+        pred = dt * _FULL_FLOPS[gen] / algorithmic_flops(p["A"], p["C"])
+        return 2 * pred, {"sample": list(ORACLE_SAMPLE), "sample_s": dt, "predicted_256_s": pred, "cores": 1}
+    if part == "adjoint":
+        p = synthetic.problem(seed, ADJ_SHAPE)
+        t0 = time.perf_counter()
+        X = oracle.solve_recursive(p["A"], p["B"], None, nmin=8)
+        t_fwd = time.perf_counter() - t0
+        Lam = oracle.solve_recursive(p["A"], X - p["Xstar"], None, nmin=8, transpose=True)
+        oracle.grad(p["A"], X, Lam)
+        dt = time.perf_counter() - t0
+        return 2 * dt, {"shape": list(ADJ_SHAPE), "seconds": dt, "forward_s": t_fwd, "cores": 1}
     shapes = synthetic.batch_shapes(seed, BATCH["count"], BATCH["lo"], BATCH["hi"])
+    jobs = [(seed, e, s) for e, s in enumerate(shapes)]
     t0 = time.perf_counter()
-    fs = 0.0
-    for e in range(nb):
-        q = synthetic.problem([seed, 1 + e], shapes[e])
-        oracle.solve_recursive(q["A"], q["B"], None, nmin=8)
-        fs += algorithmic_flops(q["A"])
+    if used <= 1:
+        for j in jobs:
+            _batch_worker(j)
+    else:  # the equations spread over the threads, one thread each
+        with multiprocessing.get_context("spawn").Pool(used) as pool:
+            pool.map(_batch_worker, jobs, chunksize=8)
     dt = time.perf_counter() - t0
-    ff = sum(laplace_flops_dense(s) for s in shapes)
-    t_step += dt * ff / fs
-    detail["batched"] = {"equations": nb, "seconds": dt}
-    return t_step, detail
+    return dt, {"equations": len(jobs), "seconds": dt, "processes": used}
+
+
+def oracle_step_seconds(threads, seed=0):
+    """Oracle seconds of one whole bench step (every part), and the details."""
+    total, det = 0.0, {}
+    for part in ORACLE_PARTS:
+        t, det[part] = oracle_part_seconds(part, threads, seed)
+        total += t
+    det["threads"] = threads if threads > 0 else (os.cpu_count() or 1)
+    return total, det
+
+
+ORACLE_RULE = ("oracle O-B (serial C, -O3, FP64) on the host: the 256^3 Laplace and generalized solves timed on "
+               "128^3 samples and scaled by the algorithmic-flop ratio, each counted for the FP64 and the refined "
+               "part; the (200,160,120) forward solve + transposed solve + gradient run in full (counted for both "
+               "adjoint parts); the 512 batch equations run in full, spread over worker processes (one core each)")
 
 
 def step_units():
@@ -262,27 +298,37 @@ WORKLOAD = ("d=3: 256^3 FP64 and FP32-refined solves (Laplace + generalized); (2
 
 
 def run_reference(args, ws, rank):
+    """The oracle under the sampling rule above, on all host cores.  Each
+    iteration times one part of the step, the parts in rotation, so that an
+    iteration is a bounded sample; a step's time is the sum of the parts'
+    mean timed samples (parts without a timed sample, when there are fewer
+    timed iterations than parts, are timed once more after the loop)."""
     if rank != 0:
         return
     units = sum(step_units().values())
-    times = []
+    timed = {p: [] for p in ORACLE_PARTS}
+    det = {}
+    threads = os.cpu_count() or 1
     for it in range(args.warmup + args.steps):
-        t, _ = oracle_step_seconds(((96, 96, 96), (64, 64, 64), (100, 80, 60), 32), seed=it % 3)
+        part = ORACLE_PARTS[it % len(ORACLE_PARTS)]
+        t, det[part] = oracle_part_seconds(part, 0, seed=0)
         if it >= args.warmup:
-            times.append(t)
-    step = float(np.mean(times))
+            timed[part].append(t)
+    for part in ORACLE_PARTS:
+        if not timed[part]:
+            t, det[part] = oracle_part_seconds(part, 0, seed=0)
+            timed[part].append(t)
+    step = float(sum(np.mean(v) for v in timed.values()))
     value = units / step
-    sample = ("oracle O-B (single thread) per step: 96^3 Laplace + 64^3 generalized (each counted for the FP64 and "
-              "the refined part), (100,80,60) forward + reversed-order transposed solve + gradient, 32 of the 512 "
-              "batch equations; "
-              "each part's time scaled to the full workload by its algorithmic-flop ratio")
+    sample = ORACLE_RULE + "; %d host cores; one part per iteration, in rotation" % threads
     line = {
         "impl": "reference", "metric": METRIC,
         "value": value, "unit": "unknowns/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (synthetic.py, seed 0..2)",
+        "dtype": "f64", "data": "synthetic (synthetic.py, seed 0)",
         "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": threads, "kind": "oracle",
+                         "sample": sample, "detail": det},
         "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -752,16 +798,17 @@ def run_ours(args, ws, rank, local):
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:
-        t_step, samp = oracle_step_seconds(((160, 160, 160), (112, 112, 112), (160, 128, 96), 512),
-                                           seed=args.seed)
+        # all host cores (the single solves take one core each, the batch all),
+        # and one core: the single-solve parts are the same runs, the batch is
+        # timed again on one core
+        t_all, det_all = oracle_step_seconds(0, seed=args.seed)
+        t_b1, det_b1 = oracle_part_seconds("batched", 1, seed=args.seed)
+        t_one = t_all - det_all["batched"]["seconds"] + t_b1
+        units_step = sum(units_rank.values())
         line["cpu_baseline"] = {
-            "value": sum(units_rank.values()) / t_step, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-            "sample": "oracle O-B, single thread: 160^3 Laplace (%.1f s) + 112^3 generalized (%.1f s), each counted "
-                      "for the FP64 and the refined part; (160,128,96) forward + transposed solve + gradient "
-                      "(%.1f s, counted for both adjoint parts); all 512 batch equations (%.1f s); each part's time "
-                      "scaled to the step's workload by its algorithmic-flop ratio" %
-                      (samp["laplace"]["seconds"], samp["generalized"]["seconds"], samp["adjoint"]["seconds"],
-                       samp["batched"]["seconds"])}
+            "value": units_step / t_all, "unit": "unknowns/s", "cores": det_all["threads"], "kind": "oracle",
+            "sample": ORACLE_RULE + "; %d host cores" % det_all["threads"],
+            "value_1core": units_step / t_one, "batched_1core_s": t_b1, "detail": det_all}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

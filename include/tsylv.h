@@ -138,6 +138,11 @@ typedef struct tsylv_opts {
                          has resident CTAs for it (latency-bound), 3 otherwise.
                          Other forms: separate.  1 (the first step alone in one
                          launch) is no longer offered: TSYLV_EUNSUPPORTED       */
+    int wait_ms;      /* bound of every device-side wait (a source block's "solved"
+                         flag, a bulk copy), in milliseconds: 1 .. 600000, default
+                         2000.  A wait that runs out ends the launch and the call
+                         returns TSYLV_ETIMEOUT; raise it on a GPU shared with
+                         long-running work                                        */
 } tsylv_opts;
 
 typedef struct tsylv_info {

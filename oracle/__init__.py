@@ -28,7 +28,7 @@ def build(force=False):
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         # -std=c11 keeps a * b + c unfused (ISO C contraction rules) on every host
-        subprocess.check_call(["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -44,18 +44,10 @@ def _load():
         lib.orc_recursive.argtypes = [ctypes.c_int, i64p, P, P, P, ctypes.c_int64, ctypes.c_int]
         lib.orc_grad.argtypes = [ctypes.c_int, i64p, P, P, P, P, P, P]
         lib.orc_check_structure.argtypes = [ctypes.c_int, i64p, P]
-        lib.orc_set_threads.argtypes = [ctypes.c_int]
-        lib.orc_set_threads.restype = ctypes.c_int
         for f in (lib.orc_apply, lib.orc_backsub, lib.orc_recursive, lib.orc_grad, lib.orc_check_structure):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
-
-
-def set_threads(t=0):
-    """Threads of the oracle's dense loops (t <= 0: all cores); returns the
-    count in use.  Results do not depend on it (one thread per output element)."""
-    return _load().orc_set_threads(int(t))
 
 
 class OracleError(RuntimeError):

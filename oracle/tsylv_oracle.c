@@ -43,24 +43,6 @@
 
 #define ORC_MAXD 8
 
-#ifdef _OPENMP
-#include <omp.h>
-#endif
-
-/* Threads of the dense loops (mode products, contractions, sums): every
- * output element is computed by one thread with the same operation order as
- * the serial loop, so the results do not depend on the thread count.
- * t <= 0 leaves the OpenMP default (all cores).  Returns the count in use. */
-int orc_set_threads(int t) {
-#ifdef _OPENMP
-    if (t > 0) omp_set_num_threads(t);
-    return omp_get_max_threads();
-#else
-    (void)t;
-    return 1;
-#endif
-}
-
 /* ---------------------------------------------------------------- helpers */
 
 static int64_t prod_range(const int64_t* n, int lo, int hi) {
@@ -141,7 +123,6 @@ static void mode_product_block(int d, const int64_t* nx, int mu, const double* M
                                int64_t mrow0, int64_t mcol0, int64_t nr, int transpose,
                                const double* X, double* Y) {
     int64_t L = prod_range(nx, 0, mu), nc = nx[mu], R = prod_range(nx, mu + 1, d);
-#pragma omp parallel for collapse(2) schedule(static) if (R * nr * L * nc > 262144)
     for (int64_t r = 0; r < R; r++)
         for (int64_t ip = 0; ip < nr; ip++)
             for (int64_t l = 0; l < L; l++) {
@@ -176,7 +157,6 @@ int orc_apply(int d, const int64_t* n, const double* const* A, const double* con
             mode_product_block(d, n, eta, M, n[eta], 0, 0, n[eta], transpose, t0, t1);
             double* t = t0; t0 = t1; t1 = t;
         }
-#pragma omp parallel for schedule(static) if (N > 262144)
         for (int64_t q = 0; q < N; q++) Y[q] += t0[q];
     }
     free(t0); free(t1);
@@ -417,7 +397,6 @@ static int rec_update(rec_ctx* r, int mu, const int64_t* off, const int64_t* ext
             }
             double* t = t0; t0 = t1; t1 = t;
         }
-#pragma omp parallel for schedule(static) if (Nt > 262144)
         for (int64_t q = 0; q < Nt; q++) bt[q] -= t0[q];
     }
     box_io(c, r->X, to, te, bt, 0);
@@ -478,7 +457,6 @@ int orc_recursive(int d, const int64_t* n, const double* const* A, const double*
  * dC may be NULL (or C NULL: Laplace form, no dC). */
 static void contract_mode(int d, const int64_t* n, int mu, const double* L, const double* W, double* G, double sign) {
     int64_t Lw = prod_range(n, 0, mu), m = n[mu], R = prod_range(n, mu + 1, d);
-#pragma omp parallel for collapse(2) schedule(dynamic, 1) if (m * m * R * Lw > 262144)
     for (int64_t i = 0; i < m; i++)
         for (int64_t j = 0; j < m; j++) {
             double s = 0.0;

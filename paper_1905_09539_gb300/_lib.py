@@ -28,7 +28,7 @@ class Opts(ctypes.Structure):
                 ("residual", ctypes.c_int), ("nmin", ctypes.c_int), ("split", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("partition", ctypes.c_int), ("resid_update", ctypes.c_int),
-                ("fuse_step", ctypes.c_int)]
+                ("fuse_step", ctypes.c_int), ("wait_ms", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

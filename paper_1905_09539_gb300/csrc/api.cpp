@@ -43,6 +43,7 @@ extern "C" void tsylv_opts_default(tsylv_opts* o) {
     o->partition = 0;
     o->resid_update = 0;
     o->fuse_step = 0;
+    o->wait_ms = 2000;
 }
 
 extern "C" const char* tsylv_status_string(int s) {

@@ -25,7 +25,9 @@ namespace tsylv {
 
 namespace {
 
-constexpr long long kTimeoutNs = 2000000000LL;
+// bound of every device-side wait of the current call (opts->wait_ms), set
+// at the start of each call on the calling thread
+thread_local long long t_timeout_ns = 2000000000LL;
 constexpr int kPolicies = 3;  // 0: longest remaining path first, 1: wavefront-major, 2: equation-major
 
 size_t al256(size_t v) { return (v + 255) / 256 * 256; }
@@ -395,7 +397,7 @@ void fill_table(const BatchPlan& p, const BatchLayout& L, char* base, int policy
         wa.csize = 1;
         wa.X = dev_data + q.X;
         wa.err = errs + e;
-        wa.timeout_ns = kTimeoutNs;
+        wa.timeout_ns = t_timeout_ns;
         wa.ready = reinterpret_cast<const int*>(base + L.flags) + q.flag_off;
         wa.abort = reinterpret_cast<int*>(base + L.ctl) + 4;
         ge.X = dev_data + q.X;
@@ -506,7 +508,7 @@ cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
         a.head = ctl + g;
         a.abort = ctl + 4;
         a.done = ctl + 8;
-        a.timeout_ns = kTimeoutNs;
+        a.timeout_ns = t_timeout_ns;
         const int dd = p.dlist[g];
         int grid = c.grid_per_sm[dd] * sm_count();
         if (grid > a.njobs) grid = a.njobs;
@@ -807,7 +809,7 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
                 r.scale = mode == 0 ? nullptr : nrm + 4 * e;
                 r.part = part + 2 * t0;
                 r.err = errs + e;
-                r.timeout_ns = kTimeoutNs;
+                r.timeout_ns = t_timeout_ns;
                 const void* xs = mode == 0 ? static_cast<const void*>(Xt + t0 * td) : w32[e].X;
                 auto setp = [&](int kk, int j) -> void* {
                     return base + E.set[kk][j] + static_cast<size_t>(t0) * td * 8;
@@ -902,7 +904,7 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
         ba.head = ctl;
         ba.abort = ctl + 4;
         ba.done = ctl + 8;
-        ba.timeout_ns = kTimeoutNs;
+        ba.timeout_ns = t_timeout_ns;
         TRYB(launch_batched<float>(dd, gen, ba, grid, s));
         TRYB(launch_bupdate(Xt, X32, dteq, nrm, xpart, T, td, s));
         const int levels = g ? dd : 1;
@@ -920,7 +922,8 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
 #undef TRYB
 
     std::vector<const void*> kb = {base, A_pool, C_pool, B_pool, X_pool, t_pin_tab.ptr, t_pin_nrm.ptr, herr,
-                                   reinterpret_cast<const void*>(static_cast<uintptr_t>(per_sm))};
+                                   reinterpret_cast<const void*>(static_cast<uintptr_t>(per_sm)),
+                                   reinterpret_cast<const void*>(static_cast<uintptr_t>(t_timeout_ns))};
     auto key = [&](int tag) {
         std::vector<const void*> kk = kb;
         kk.push_back(reinterpret_cast<const void*>(static_cast<uintptr_t>(1000 + tag)));
@@ -1030,7 +1033,8 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     if (refined && !uniform_order(count, d)) return TSYLV_EUNSUPPORTED;
     const size_t need = solver_batched_workspace_bytes(count, d, n_packed, gen, o);
     if (!need || work_bytes < need) return -11;
-    if (o.split < 0 || o.partition < 0 || o.partition > 1) return -12;
+    if (o.split < 0 || o.partition < 0 || o.partition > 1 || o.wait_ms < 1 || o.wait_ms > 600000) return -12;
+    t_timeout_ns = static_cast<long long>(o.wait_ms) * 1000000LL;
     size_t nmats = 0;
     for (int e = 0; e < count; e++) nmats += static_cast<size_t>(d[e]);
     for (size_t k = 0; k < nmats; k++)
@@ -1139,7 +1143,8 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     const int launches = 3 + static_cast<int>(plan->dlist.size());
     if (o.use_graph) {
         std::vector<const void*> key = {base, A_pool, C_pool, B_pool, X_pool, t_pin_tab.ptr, herr,
-                                        reinterpret_cast<const void*>(static_cast<uintptr_t>(policy * 64 + per_sm))};
+                                        reinterpret_cast<const void*>(static_cast<uintptr_t>(policy * 64 + per_sm)),
+                                        reinterpret_cast<const void*>(static_cast<uintptr_t>(t_timeout_ns))};
         cudaGraphExec_t exec = nullptr;
         for (auto& g : plan->graphs)
             if (g.key == key) exec = g.exec;

@@ -28,7 +28,6 @@ namespace tsylv {
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB per device
-constexpr long long kNoallocTimeoutNs = 2000000000LL;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -127,7 +126,7 @@ int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const 
     }
     wa.X = Xt;
     wa.err = reinterpret_cast<int*>(base + L.err);
-    wa.timeout_ns = kNoallocTimeoutNs;
+    wa.timeout_ns = static_cast<long long>(o.wait_ms) * 1000000LL;
     for (size_t w = 0; w < p.wave_off.size(); w++) {
         wa.tiles = tab + p.t_wave + p.wave_off[w];
         wa.ntiles = p.wave_cnt[w];

@@ -173,6 +173,7 @@ struct Call {
     bool update = false;      // refinement step: residual updated from the FP32 correction
     bool first = false;       // first refinement step (X = 0 before it: X after it is s D exactly)
     int prod = kProdNative;   // arithmetic of the FP32 solve's block updates (native / TF32 / BF16 tensor cores)
+    long long timeout_ns = kTimeoutNs;  // bound of every device-side wait (opts->wait_ms)
     bool pipe = false;        // first two refinement steps pipelined in one launch (Laplace form)
     int pipe_grid = 0;
 };
@@ -188,7 +189,7 @@ inline cudaError_t mark(const Call& c, int i, cudaStream_t s) {
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
-WaveArgs wave_args(const Plan& p, const Layout& L, char* base) {
+WaveArgs wave_args(const Plan& p, const Layout& L, char* base, long long timeout_ns) {
     WaveArgs wa{};
     const int* tab = reinterpret_cast<const int*>(base + L.tab);
     for (int mu = 0; mu < p.d; mu++) {
@@ -203,7 +204,7 @@ WaveArgs wave_args(const Plan& p, const Layout& L, char* base) {
     }
     wa.X = base + L.X;
     wa.err = reinterpret_cast<int*>(base + L.err);
-    wa.timeout_ns = kTimeoutNs;
+    wa.timeout_ns = timeout_ns;
     return wa;
 }
 
@@ -214,7 +215,7 @@ template <typename T>
 cudaError_t enqueue_waves(const Call& c, const Layout& L, cudaStream_t s) {
     const Plan& p = *c.plan;
     char* base = c.base;
-    WaveArgs wa = wave_args(p, L, base);
+    WaveArgs wa = wave_args(p, L, base, c.timeout_ns);
     const int* tab = reinterpret_cast<const int*>(base + L.tab);
     if (c.persistent) {
         int* ctl = reinterpret_cast<int*>(base + L.fctl);
@@ -234,7 +235,7 @@ cudaError_t enqueue_waves(const Call& c, const Layout& L, cudaStream_t s) {
         ba.head = ctl;
         ba.done = nullptr;
         ba.abort = ctl + 1;
-        ba.timeout_ns = kTimeoutNs;
+        ba.timeout_ns = c.timeout_ns;
         return launch_batched<T>(p.d, p.gen, ba, c.flow_grid, s, sizeof(T) == 4 ? c.prod : kProdNative);
     }
     for (size_t w = 0; w < p.wave_off.size(); w++) {
@@ -307,7 +308,7 @@ cudaError_t enqueue_residual(const Call& c, cudaStream_t s) {
     a.scale = up || fst ? reinterpret_cast<const double*>(b + R.nrm) : nullptr;
     a.part = reinterpret_cast<double*>(b + R.part);
     a.err = reinterpret_cast<int*>(b + R.L32.err);
-    a.timeout_ns = kTimeoutNs;
+    a.timeout_ns = c.timeout_ns;
     const void* xs = up || fst ? static_cast<const void*>(b + R.L32.X)
                                : c.df ? static_cast<const void*>(b + R.Xh) : static_cast<const void*>(b + R.Xt);
     const void* xsl = c.df && !up && !fst ? static_cast<const void*>(b + R.Xl) : nullptr;
@@ -488,7 +489,7 @@ cudaError_t enqueue_ref_pipe(const Call& c, cudaStream_t s) {
     TRY(cudaMemsetAsync(ctl, 0, 64, s));
     TRY(cudaMemsetAsync(flags1, 0, static_cast<size_t>(p.ntiles) * sizeof(int), s));
     TRY(cudaMemsetAsync(flags2, 0, static_cast<size_t>(p.ntiles) * 2 * sizeof(int), s));
-    WaveArgs w1 = wave_args(p, L, b);
+    WaveArgs w1 = wave_args(p, L, b, c.timeout_ns);
     w1.ready = flags1;
     w1.abort = ctl + 1;
     w1.csize = 1;
@@ -506,7 +507,7 @@ cudaError_t enqueue_ref_pipe(const Call& c, cudaStream_t s) {
     f.njobs = p.n_rjobs;
     f.head = ctl;
     f.abort = ctl + 1;
-    f.timeout_ns = kTimeoutNs;
+    f.timeout_ns = c.timeout_ns;
     f.r1done = flags2;
     for (ApplyArgs* ap : {&f.r1, &f.r2}) {
         for (int mu = 0; mu < p.d; mu++) {
@@ -518,7 +519,7 @@ cudaError_t enqueue_ref_pipe(const Call& c, cudaStream_t s) {
         ap->R = reinterpret_cast<double*>(b + R.Rt);
         ap->scale = nrm;
         ap->err = reinterpret_cast<int*>(b + L.err);
-        ap->timeout_ns = kTimeoutNs;
+        ap->timeout_ns = c.timeout_ns;
     }
     for (int mu = 0; mu < p.d; mu++) {
         f.r1.A[mu] = b + R.Ah[mu];
@@ -753,6 +754,7 @@ std::vector<const void*> make_key(const Call& c, int tag) {
     key.push_back(c.Rout);
     key.push_back(c.base);
     key.push_back(reinterpret_cast<const void*>(static_cast<uintptr_t>(tag)));
+    key.push_back(reinterpret_cast<const void*>(static_cast<uintptr_t>(c.timeout_ns)));
     return key;
 }
 
@@ -789,7 +791,7 @@ int check_opts(const tsylv_opts& o, int d) {
         (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < 0 ||
         o.schedule < 0 || o.schedule > 1 || o.partition < 0 || o.partition > 1 || o.resid_update < 0 ||
         o.resid_update > 1 || o.fuse_step < 0 || o.fuse_step > 3 || o.timing < 0 || o.timing > 1 ||
-        o.use_graph < 0 || o.use_graph > 1)
+        o.use_graph < 0 || o.use_graph > 1 || o.wait_ms < 1 || o.wait_ms > 600000)
         return -1;
     if (o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d))) return TSYLV_EUNSUPPORTED;
     // fuse_step 1 (the first step as one launch) is no longer offered: it
@@ -866,6 +868,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     c.flip = transposed;
     c.df = o.residual == TSYLV_RESID_DF64;
     c.prod = o.precision == TSYLV_TF32_REFINED ? kProdTF32 : o.precision == TSYLV_BF16_REFINED ? kProdBF16 : kProdNative;
+    c.timeout_ns = static_cast<long long>(o.wait_ms) * 1000000LL;
     for (int mu = 0; mu < d; mu++) {
         c.n[mu] = n[mu];
         c.A[mu] = A[mu];
@@ -1084,7 +1087,7 @@ int solver_selftest_wait_timeout(long long timeout_ns, cudaStream_t stream) {
         TRY(cudaMemsetAsync(base, 0, L.total, stream));  // zero coefficients and right-hand side
         TRY(cudaMemcpyAsync(base + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
         int* ctl = reinterpret_cast<int*>(base + L.fctl);
-        WaveArgs wa = wave_args(p, L, base);
+        WaveArgs wa = wave_args(p, L, base, timeout_ns);
         wa.ready = reinterpret_cast<int*>(base + L.flags);
         wa.abort = ctl + 1;
         wa.csize = 1;
@@ -1128,11 +1131,13 @@ int solver_residual(int d, const int64_t* n, const double* const* A, const doubl
     if (!R) return -7;
     if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -9;
     if (work_bytes < solver_residual_workspace_bytes(d, n, gen)) return -10;
-    if (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) return -11;
+    if (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64 || o.wait_ms < 1 || o.wait_ms > 600000)
+        return -11;
     Call c;
     c.d = d;
     c.gen = gen && d >= 2;
     c.df = o.residual == TSYLV_RESID_DF64;
+    c.timeout_ns = static_cast<long long>(o.wait_ms) * 1000000LL;
     for (int mu = 0; mu < d; mu++) {
         c.n[mu] = n[mu];
         c.A[mu] = A[mu];

@@ -265,3 +265,23 @@ def test_dterm_deep_queue_parity(lib, shape, force, prec):
     tol = TOL if prec == "fp64" else 1e-10
     assert rel_err(Xg, Xo) <= tol
     assert max_rel(Xg, Xo) <= tol
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_wait_limit_option(lib, gen):
+    """opts.wait_ms only bounds the device-side waits: a solve with a longer
+    limit (its own captured schedule) gives the default solve's result bit
+    for bit."""
+    p = synthetic.problem(2, (24, 20, 16), generalized=gen)
+    A = [to_dev(a) for a in p["A"]]
+    B = to_dev(p["B"])
+    C = [to_dev(c) for c in p["C"]] if gen else None
+    out = []
+    for w in (2000, 30000):
+        if gen:
+            X, st = lib.gtsylv_solve(A, C, B, wait_ms=w)
+        else:
+            X, st = lib.tsylv_solve(A, B, wait_ms=w)
+        assert st == 0
+        out.append(X)
+    assert torch.equal(out[0], out[1])

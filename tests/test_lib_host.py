@@ -38,6 +38,7 @@ def test_defaults_and_status(lib):
     from paper_1905_09539_gb300 import _lib
     o = _lib.default_opts()
     assert o.precision == 0 and o.use_graph == 1 and abs(o.tol - 1e-12) < 1e-20 and o.max_refine == 10
+    assert o.wait_ms == 2000
     for s in range(0, 7):
         assert len(_lib.status_string(s)) > 0
     assert "argument" in _lib.status_string(-3)
@@ -89,7 +90,8 @@ def test_option_validation_without_gpu(lib):
         return lib.tsylv_solve(2, n, fake, P(16), P(16), P(256), wb, ctypes.byref(o), None, None)
 
     for kw in ({"fuse_step": 4}, {"fuse_step": -1}, {"schedule": 2}, {"partition": 2}, {"resid_update": 2},
-               {"precision": 9}, {"tol": 0.0}, {"split": -1}, {"max_refine": -1}, {"residual": 7}):
+               {"precision": 9}, {"tol": 0.0}, {"split": -1}, {"max_refine": -1}, {"residual": 7},
+               {"wait_ms": 0}, {"wait_ms": 600001}):
         assert st(**kw) == -8, kw
     for kw in ({"host_io": 1}, {"fuse_step": 1}, {"nmin": 5},
                {"precision": _lib.TSYLV_TF32_REFINED, "schedule": 1},
@@ -113,7 +115,7 @@ def test_noalloc_option_validation_without_gpu(lib):
 
     for kw in ({"fuse_step": 4}, {"schedule": 2}, {"partition": 2}, {"resid_update": 2}, {"precision": 9},
                {"tol": 0.0}, {"split": -1}, {"max_refine": -1}, {"residual": 7}, {"timing": 2},
-               {"precision": _lib.TSYLV_FP32_REFINED}):
+               {"wait_ms": 0}, {"precision": _lib.TSYLV_FP32_REFINED}):
         assert st(**kw) == -6, kw
     for kw in ({"host_io": 1}, {"nmin": 5}, {"timing": 1}):
         assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
