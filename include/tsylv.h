@@ -110,7 +110,17 @@ typedef struct tsylv_opts {
     int max_refine;   /* refinement steps for *_REFINED (default 10)                 */
     double tol;       /* target ||B - A(X)|| / (||A|| ||X||) (default 1e-12)         */
     int residual;     /* enum tsylv_residual_kind, default TSYLV_RESID_DF64          */
-    int nmin;         /* largest block extent per mode; 0 = the default for d        */
+    int nmin;         /* recursion cutoff: the largest block extent per mode (leaf
+                         bound of the split tree).  0 (default): the tile extent
+                         TE of the order d (32, 16, 8, 4 for d = 1..4); 2..TE: that
+                         bound for every mode; -1: autotuned.  A single solve tunes
+                         on its first call per order, mode sizes, form, direction
+                         and precision (each candidate tile shape -- every mode TE,
+                         3/4 TE or TE/2, or TE/2 in the first or the last mode
+                         only -- solves once, timed; X is written, B is not; an
+                         in-place call takes the default).  tsylv_solve_batched
+                         tunes by default (0 or -1) together with its launch.
+                         Values above TE, and 1, return TSYLV_EUNSUPPORTED.       */
     int split;        /* largest cluster size for split block updates; 0 = auto      */
     int use_graph;    /* 1 (default): capture each schedule once and replay it      */
     int host_io;      /* reserved (host-resident operands); must be 0: this build
@@ -143,6 +153,10 @@ typedef struct tsylv_opts {
                          2000.  A wait that runs out ends the launch and the call
                          returns TSYLV_ETIMEOUT; raise it on a GPU shared with
                          long-running work                                        */
+    int leaf[4];      /* per-mode leaf bounds (tile shape), overriding nmin mode by
+                         mode: entry mu in 2..TE bounds the blocks of mode mu, 0
+                         takes nmin's bound (TE when nmin <= 0).  Any nonzero entry
+                         fixes the shape (no autotuning).  Default all 0.         */
 } tsylv_opts;
 
 typedef struct tsylv_info {
@@ -159,6 +173,9 @@ typedef struct tsylv_info {
     int batch_order;      /* tsylv_solve_batched: job-queue order used (0 longest remaining
                              path first, 1 wavefront-major, 2 equation-major)      */
     int batch_ctas_per_sm;/* tsylv_solve_batched: resident CTAs per SM used          */
+    int leaf[4];          /* leaf bound (recursion cutoff) of every mode in the block
+                             partition used -- the tile shape (opts->nmin); for a
+                             batch, that of its equations of the highest order d   */
 } tsylv_info;
 
 /* Fill *opts with the defaults listed above. */
@@ -311,9 +328,9 @@ int tsylv_solve_batched(int count, const int* d, const int64_t* n_packed, const 
  * work overlaps race on it: serialise them.  The status word is cleared by
  * every call.  Arguments and status codes as tsylv_solve, with opts the 6th
  * argument: its fields are checked as tsylv_solve checks them (-6 for a field
- * out of range, TSYLV_EUNSUPPORTED for host_io or a non-default nmin);
- * opts->precision must be TSYLV_FP64 (else -6) and opts->timing 0 (else
- * TSYLV_EUNSUPPORTED).  The schedule is always one launch per anti-diagonal
+ * out of range, TSYLV_EUNSUPPORTED for host_io or an nmin outside 0, 2..TE);
+ * opts->precision must be TSYLV_FP64 (else -6), opts->timing 0 and
+ * opts->nmin not -1 (no autotuning runs; else TSYLV_EUNSUPPORTED).  The schedule is always one launch per anti-diagonal
  * wavefront (opts->schedule is not used). */
 int tsylv_solve_noalloc(int d, const int64_t* n, const double* const* A, const double* B, double* X,
                         const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);

@@ -47,8 +47,9 @@ class BatchPools:
         self.c_offX = (ctypes.c_int64 * len(offX))(*offX)
         self.per = (ctypes.c_int * self.count)()
 
-    def solve(self, *, opts=None, check=True, stream=None, info=None, **kw):
-        """Solve every equation into self.X; returns the list of statuses."""
+    def solve(self, *, opts=None, check=True, stream=None, info=None, inplace=False, **kw):
+        """Solve every equation into self.X (inplace: into the B pool, which
+        then becomes self.X); returns the list of statuses."""
         from . import TsylvError, _opts, _stream, workspace
         lib = _lib.load()
         o = _opts(opts, kw)
@@ -60,8 +61,10 @@ class BatchPools:
         inf = info if info is not None else _lib.Info()
         st = lib.tsylv_solve_batched(self.count, self.c_d, self.c_n, self.c_offA, self.c_offX, self.A.data_ptr(),
                                      self.C.data_ptr() if self.C is not None else None, self.B.data_ptr(),
-                                     self.X.data_ptr(), work.data_ptr(), work.numel(), ctypes.byref(o), self.per,
-                                     ctypes.byref(inf), _stream(stream))
+                                     (self.B if inplace else self.X).data_ptr(), work.data_ptr(), work.numel(),
+                                     ctypes.byref(o), self.per, ctypes.byref(inf), _stream(stream))
+        if inplace:
+            self.X = self.B
         if check and st != 0:
             raise TsylvError(st, "tsylv_solve_batched")
         return [self.per[i] for i in range(self.count)]

@@ -62,7 +62,7 @@ struct BatchPlan {
     size_t data_bytes = 0;
     std::vector<long long> tile_off;        // first global block of every equation (count + 1 entries)
     double flops = 0;
-    int tuned_policy = -1, tuned_grid = 0;
+    int tuned_policy = -1, tuned_grid = 0, tuned_shape = 0;  // autotuner result (kept on the default-shape plan)
     std::vector<BatchGraph> graphs;
     ~BatchPlan() {
         for (auto& g : graphs)
@@ -84,8 +84,8 @@ struct BatchLayout {
 
 // Upper bounds of one equation's block counts and data bytes (any admissible
 // structure), region by region as get_batch_plan lays them out.
-void eq_bounds(int d, const int64_t* n, bool gen, int elem, long long& tiles, long long& ctiles, long long& pints,
-               size_t& data) {
+void eq_bounds(int d, const int64_t* n, bool gen, int elem, int shape, long long& tiles, long long& ctiles,
+               long long& pints, size_t& data) {
     const int te = tile_extent(d);
     const size_t td = static_cast<size_t>(ipow(te, d)), tc = static_cast<size_t>(te) * te;
     const bool g = gen && d >= 2;
@@ -94,7 +94,7 @@ void eq_bounds(int d, const int64_t* n, bool gen, int elem, long long& tiles, lo
     pints = 0;
     data = 0;
     for (int mu = 0; mu < d; mu++) {
-        const long long nb = max_blocks(static_cast<int>(n[mu]), te);
+        const long long nb = max_blocks(static_cast<int>(n[mu]), shape_min_cut(d, mu, shape));
         tiles *= nb;
         ctiles += nb * (nb + 1) / 2;
         pints += 2 * nb;
@@ -153,13 +153,14 @@ struct Bounds {
     size_t data = 0;
 };
 
-Bounds batch_bounds(int count, const int* d, const int64_t* n_packed, bool gen, int elem) {
+// shape: the tile shape the call uses (-1: any candidate of the autotuner)
+Bounds batch_bounds(int count, const int* d, const int64_t* n_packed, bool gen, int elem, int shape) {
     Bounds b;
     size_t k = 0;
     for (int e = 0; e < count; e++) {
         long long t, c, p;
         size_t db;
-        eq_bounds(d[e], n_packed + k, gen, elem, t, c, p, db);
+        eq_bounds(d[e], n_packed + k, gen, elem, shape, t, c, p, db);
         b.jobs += t;
         b.cjobs += c;
         b.pints += p;
@@ -249,8 +250,8 @@ double eq_flops(const EqPlan& q, bool gen) {
 }
 
 std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t* n_packed, bool gen, int elem,
-                                          const std::vector<uint8_t>& sub, int partition) {
-    std::vector<long long> key = {count, gen ? 1 : 0, elem, partition};
+                                          const std::vector<uint8_t>& sub, int partition, int shape) {
+    std::vector<long long> key = {count, gen ? 1 : 0, elem, partition, shape};
     size_t k = 0;
     for (int e = 0; e < count; e++) {
         key.push_back(d[e]);
@@ -271,7 +272,7 @@ std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t
     std::lock_guard<std::mutex> lk(g_bmu);
     auto it = g_bplans.find(key);
     if (it != g_bplans.end()) return it->second;
-    if (g_bplans.size() > 16) g_bplans.clear();
+    if (g_bplans.size() > 64) g_bplans.clear();
     auto p = std::make_shared<BatchPlan>();
     p->count = count;
     p->gen = gen;
@@ -289,7 +290,7 @@ std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t
             std::vector<uint8_t> s(sub.begin() + static_cast<long long>(soff),
                                    sub.begin() + static_cast<long long>(soff + q.n[mu] - 1));
             soff += static_cast<size_t>(q.n[mu] - 1);
-            q.part[mu] = make_part(static_cast<int>(q.n[mu]), s, te, partition);
+            q.part[mu] = make_part(static_cast<int>(q.n[mu]), s, shape_cut(q.d, mu, shape), partition);
             q.nb[mu] = q.part[mu].nb;
             q.tstride[mu] = ts;
             ts *= q.nb[mu];
@@ -482,6 +483,7 @@ struct BatchCall {
     int grid_per_sm[kMaxD + 1] = {};
     int* herr = nullptr;   // pinned host copy of the per-equation status words
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the persistent launches (autotuner)
+    bool unpack = true;    // false for the autotuner's timing runs: X may alias B
 };
 
 cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
@@ -516,7 +518,7 @@ cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
         if ((e = launch_batched<double>(dd, p.gen, a, grid, s)) != cudaSuccess) return e;
     }
     if (c.ev1 && (e = cudaEventRecord(c.ev1, s)) != cudaSuccess) return e;
-    if ((e = launch_batch_unpack<double>(geo, jobs, njobs, c.X, s)) != cudaSuccess) return e;
+    if (c.unpack && (e = launch_batch_unpack<double>(geo, jobs, njobs, c.X, s)) != cudaSuccess) return e;
     return cudaMemcpyAsync(c.herr, ctl + 8 + p.count, sizeof(int) * p.count, cudaMemcpyDeviceToHost, s);
 }
 
@@ -699,8 +701,31 @@ bool uniform_order(int count, const int* d) {
     return true;
 }
 
-size_t refined_workspace_bytes(int count, const int* d, const int64_t* n_packed, bool gen) {
-    const Bounds b = batch_bounds(count, d, n_packed, gen, 4);
+// Fixed tile shape of the options (opts->nmin > 0 or opts->leaf), else -1.
+// Every equation of a batch takes the same per-mode bounds (each clipped to
+// its own order's tile extent).
+int fixed_shape_of(const tsylv_opts& o) {
+    bool per_mode = false;
+    for (int mu = 0; mu < kMaxD; mu++) per_mode |= o.leaf[mu] > 0;
+    if (!per_mode) return o.nmin > 0 ? kShapeFixed + o.nmin : -1;
+    const int dflt = o.nmin > 0 ? o.nmin : 63;
+    int code = 0;
+    for (int mu = 0; mu < kMaxD; mu++) code |= (o.leaf[mu] > 0 ? o.leaf[mu] : dflt) << (6 * mu);
+    return kShapeFixed + code;
+}
+
+// The FP64 batch tunes the tile shape with its launch (-1 marks "any
+// candidate" for the workspace bounds) unless the options fix it.
+int fp64_shape(const tsylv_opts& o) { return fixed_shape_of(o); }
+
+// The FP32-refined batch runs one fixed tile shape: the default, or the options'.
+int refined_shape(const tsylv_opts& o) {
+    const int f = fixed_shape_of(o);
+    return f >= 0 ? f : 0;
+}
+
+size_t refined_workspace_bytes(int count, const int* d, const int64_t* n_packed, bool gen, int shape) {
+    const Bounds b = batch_bounds(count, d, n_packed, gen, 4, shape);
     const BatchLayout L = make_batch_layout(count, d, n_packed, gen, 4, b.jobs, b.cjobs, b.pints, b.data);
     int nm = 0;
     for (int e = 0; e < count; e++) nm += d[e] * (gen ? 2 : 1);
@@ -718,10 +743,12 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
     const int dd = d[0];
     const bool g = gen && dd >= 2;
     const int te = tile_extent(dd), td = ipow(te, dd), tc = te * te;
-    const Bounds bd = batch_bounds(count, d, n_packed, gen, 4);
+    const int shape = refined_shape(o);
+    const Bounds bd = batch_bounds(count, d, n_packed, gen, 4, shape);
     const BatchLayout L = make_batch_layout(count, d, n_packed, gen, 4, bd.jobs, bd.cjobs, bd.pints, bd.data);
     const int nmA = count * dd, nm = nmA * (gen ? 2 : 1);
-    std::shared_ptr<BatchPlan> plan = get_batch_plan(count, d, n_packed, gen, 4, sub, o.partition == 1 ? 1 : 0);
+    std::shared_ptr<BatchPlan> plan =
+        get_batch_plan(count, d, n_packed, gen, 4, sub, o.partition == 1 ? 1 : 0, shape);
     if (!plan) return cuda_fail_msg("batched: plan");
     if (plan->data_bytes > bd.data) return cuda_fail_msg("batched: workspace bound");
     const long long T = plan->tile_off[count];
@@ -996,6 +1023,8 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
         info->flops = plan->flops * iters;
         info->batch_order = policy;
         info->batch_ctas_per_sm = per_sm;
+        const int dmax = plan->dlist.back();
+        for (int mu = 0; mu < dmax; mu++) info->leaf[mu] = shape_cut(dmax, mu, shape);
     }
     (void)ctiles;
     return status;
@@ -1005,9 +1034,10 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
 size_t solver_batched_workspace_bytes(int count, const int* d, const int64_t* n_packed, bool gen,
                                       const tsylv_opts& o) {
     if (!shapes_ok(count, d, n_packed)) return 0;
-    if (o.precision == TSYLV_FP32_REFINED) return uniform_order(count, d) ? refined_workspace_bytes(count, d, n_packed, gen) : 0;
+    if (o.precision == TSYLV_FP32_REFINED)
+        return uniform_order(count, d) ? refined_workspace_bytes(count, d, n_packed, gen, refined_shape(o)) : 0;
     if (o.precision != TSYLV_FP64) return 0;
-    const Bounds b = batch_bounds(count, d, n_packed, gen, 8);
+    const Bounds b = batch_bounds(count, d, n_packed, gen, 8, fp64_shape(o));
     const BatchLayout L = make_batch_layout(count, d, n_packed, gen, 8, b.jobs, b.cjobs, b.pints, b.data);
     return L.total;
 }
@@ -1033,7 +1063,15 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     if (refined && !uniform_order(count, d)) return TSYLV_EUNSUPPORTED;
     const size_t need = solver_batched_workspace_bytes(count, d, n_packed, gen, o);
     if (!need || work_bytes < need) return -11;
-    if (o.split < 0 || o.partition < 0 || o.partition > 1 || o.wait_ms < 1 || o.wait_ms > 600000) return -12;
+    if (o.split < 0 || o.partition < 0 || o.partition > 1 || o.wait_ms < 1 || o.wait_ms > 600000 || o.nmin < -1)
+        return -12;
+    for (int mu = 0; mu < kMaxD; mu++)
+        if (o.leaf[mu] < 0) return -12;
+    for (int e = 0; e < count; e++) {
+        if (o.nmin == 1 || o.nmin > tile_extent(d[e])) return TSYLV_EUNSUPPORTED;
+        for (int mu = 0; mu < kMaxD; mu++)
+            if (o.leaf[mu] == 1 || (mu < d[e] && o.leaf[mu] > tile_extent(d[e]))) return TSYLV_EUNSUPPORTED;
+    }
     t_timeout_ns = static_cast<long long>(o.wait_ms) * 1000000LL;
     size_t nmats = 0;
     for (int e = 0; e < count; e++) nmats += static_cast<size_t>(d[e]);
@@ -1044,7 +1082,7 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     (void)cudaGetLastError();
     char* base = static_cast<char*>(work);
     const int elem = refined ? 4 : 8;
-    const Bounds bd = batch_bounds(count, d, n_packed, gen, elem);
+    const Bounds bd = batch_bounds(count, d, n_packed, gen, elem, refined ? refined_shape(o) : fp64_shape(o));
     BatchLayout L = make_batch_layout(count, d, n_packed, gen, elem, bd.jobs, bd.cjobs, bd.pints, bd.data);
 
     std::vector<uint8_t> sub;
@@ -1056,12 +1094,15 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     cudaError_t e;
 
     // ---- plan (cached per shapes and structure), tables, launch
-    std::shared_ptr<BatchPlan> plan = get_batch_plan(count, d, n_packed, gen, 8, sub, o.partition == 1 ? 1 : 0);
-    if (!plan) return cuda_fail_msg("batched: plan");
-    if (plan->data_bytes > bd.data) return cuda_fail_msg("batched: workspace bound");
+    const int fixed_shape = fixed_shape_of(o);
+    const int part_rule = o.partition == 1 ? 1 : 0;
+    std::shared_ptr<BatchPlan> plan0 =
+        get_batch_plan(count, d, n_packed, gen, 8, sub, part_rule, fixed_shape >= 0 ? fixed_shape : 0);
+    if (!plan0) return cuda_fail_msg("batched: plan");
+    if (plan0->data_bytes > bd.data) return cuda_fail_msg("batched: workspace bound");
     if (int st = prepare_batched_once()) return st;
     BatchCall c;
-    c.plan = plan.get();
+    c.plan = plan0.get();
     c.L = L;
     c.base = base;
     c.A = A_pool;
@@ -1073,68 +1114,98 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     std::vector<unsigned char> tabv;
 
     auto set_grid = [&](int per_sm) {
-        for (int dd : plan->dlist) {
+        for (int dd : plan0->dlist) {
             const int occ = occupancy_cached(dd, gen);
             c.grid_per_sm[dd] = std::max(1, std::min(per_sm, occ));
         }
     };
 
-    // autotuner: queue order x resident CTAs per SM, timed on this batch once
-    int policy = plan->tuned_policy, per_sm = plan->tuned_grid;
+    // autotuner: tile shape (the recursion cutoff of every mode) x queue order
+    // x resident CTAs per SM, timed on this batch once (the persistent launches
+    // with CUDA events; the timing runs leave X_pool untouched)
+    int shape = fixed_shape >= 0 ? fixed_shape : plan0->tuned_shape;
+    int policy = plan0->tuned_policy, per_sm = plan0->tuned_grid;
+    std::shared_ptr<BatchPlan> plan = plan0;
     if (o.split > 0) {
+        shape = fixed_shape >= 0 ? fixed_shape : 0;
         policy = policy >= 0 ? policy : 0;
         per_sm = o.split;
     } else if (policy < 0) {
         int occ = 1;
-        for (int dd : plan->dlist) occ = std::max(occ, occupancy_cached(dd, gen));
+        for (int dd : plan0->dlist) occ = std::max(occ, occupancy_cached(dd, gen));
         std::vector<int> grids = {occ};
         if (occ >= 2) grids.push_back((occ + 1) / 2);
         if (occ >= 3) grids.push_back(1);
+        std::vector<int> shapes;
+        if (fixed_shape >= 0) {
+            shapes.push_back(fixed_shape);
+        } else {
+            const bool only_d1 = plan0->dlist.size() == 1 && plan0->dlist[0] == 1;
+            for (int sc = 0; sc < kShapes; sc++)
+                if (!(only_d1 && sc >= 3)) shapes.push_back(sc);  // 3, 4 coincide with 2 for one mode
+        }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
             if (e0) cudaEventDestroy(e0);
             return cuda_fail_msg("batched: autotuner events");
         }
         float best = 1e30f;
-        int bp = 0, bg = occ;
-        for (int pol = 0; pol < kPolicies; pol++) {
-            fill_table(*plan, L, base, pol, tabv, off_A, off_X);
-            std::memcpy(t_pin_tab.ptr, tabv.data(), tabv.size());
-            c.htab = t_pin_tab.ptr;
-            for (int gsz : grids) {
-                set_grid(gsz);
-                c.ev0 = e0;
-                c.ev1 = e1;
-                float ms = 0;
-                for (int rep = 0; rep < 2; rep++) {  // first run warms caches and code
-                    if ((e = enqueue_batch(c, stream)) != cudaSuccess) {
-                        cudaEventDestroy(e0);
-                        cudaEventDestroy(e1);
-                        return cuda_fail(e, "batched: autotuner launch");
+        int bs = shapes[0], bp = 0, bg = occ;
+        for (int sc : shapes) {
+            std::shared_ptr<BatchPlan> ps =
+                sc == (fixed_shape >= 0 ? fixed_shape : 0) ? plan0 : get_batch_plan(count, d, n_packed, gen, 8, sub,
+                                                                                     part_rule, sc);
+            if (!ps || ps->data_bytes > bd.data) continue;
+            c.plan = ps.get();
+            for (int pol = 0; pol < kPolicies; pol++) {
+                fill_table(*ps, L, base, pol, tabv, off_A, off_X);
+                std::memcpy(t_pin_tab.ptr, tabv.data(), tabv.size());
+                c.htab = t_pin_tab.ptr;
+                for (int gsz : grids) {
+                    set_grid(gsz);
+                    c.ev0 = e0;
+                    c.ev1 = e1;
+                    c.unpack = false;  // the timing runs leave X_pool (which may be B_pool) untouched
+                    float ms = 0;
+                    for (int rep = 0; rep < 2; rep++) {  // first run warms caches and code
+                        if ((e = enqueue_batch(c, stream)) != cudaSuccess) {
+                            cudaEventDestroy(e0);
+                            cudaEventDestroy(e1);
+                            return cuda_fail(e, "batched: autotuner launch");
+                        }
+                        if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) {
+                            cudaEventDestroy(e0);
+                            cudaEventDestroy(e1);
+                            return cuda_fail(e, "batched: autotuner synchronize");
+                        }
+                        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = 1e30f;
                     }
-                    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) {
-                        cudaEventDestroy(e0);
-                        cudaEventDestroy(e1);
-                        return cuda_fail(e, "batched: autotuner synchronize");
+                    int bad = 0;
+                    for (int q = 0; q < count; q++) bad |= herr[q];
+                    if (bad & kErrTimeout) ms = 1e30f;
+                    if (ms < best) {
+                        best = ms;
+                        bs = sc;
+                        bp = pol;
+                        bg = gsz;
                     }
-                    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = 1e30f;
-                }
-                int bad = 0;
-                for (int q = 0; q < count; q++) bad |= herr[q];
-                if (bad & kErrTimeout) ms = 1e30f;
-                if (ms < best) {
-                    best = ms;
-                    bp = pol;
-                    bg = gsz;
                 }
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         c.ev0 = c.ev1 = nullptr;
-        plan->tuned_policy = policy = bp;
-        plan->tuned_grid = per_sm = bg;
+        c.unpack = true;
+        plan0->tuned_shape = shape = bs;
+        plan0->tuned_policy = policy = bp;
+        plan0->tuned_grid = per_sm = bg;
     }
+    if (shape != (fixed_shape >= 0 ? fixed_shape : 0)) {
+        plan = get_batch_plan(count, d, n_packed, gen, 8, sub, part_rule, shape);
+        if (!plan) return cuda_fail_msg("batched: plan");
+        if (plan->data_bytes > bd.data) return cuda_fail_msg("batched: workspace bound");
+    }
+    c.plan = plan.get();
     set_grid(per_sm);
     fill_table(*plan, L, base, policy, tabv, off_A, off_X);
     std::memcpy(t_pin_tab.ptr, tabv.data(), tabv.size());
@@ -1197,6 +1268,8 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
         info->flops = plan->flops;
         info->batch_order = policy;
         info->batch_ctas_per_sm = per_sm;
+        const int dmax = plan->dlist.back();
+        for (int mu = 0; mu < dmax; mu++) info->leaf[mu] = shape_cut(dmax, mu, shape);
     }
     return status;
 }

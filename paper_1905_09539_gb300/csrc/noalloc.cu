@@ -74,7 +74,7 @@ int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const 
     // the FP64 solve, without event timing
     if (int st = check_opts(o, d)) return st < 0 ? -6 : st;
     if (o.precision != TSYLV_FP64) return -6;
-    if (o.timing) return TSYLV_EUNSUPPORTED;
+    if (o.timing || o.nmin < 0) return TSYLV_EUNSUPPORTED;  // no event timing, no autotuning runs
     // the largest workspace any admissible block structure needs must fit
     const size_t need = solver_workspace_bytes(d, n, false, o, false);
     if (need == 0) return -2;
@@ -94,7 +94,7 @@ int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const 
     std::vector<uint8_t> sub;
     if (int st = solve_read_structure(d, nn, A, base, false, stream, sub)) return st;
     Plan p;
-    fill_plan(p, d, nn, false, 8, o.split, sub, o.partition);
+    fill_plan(p, d, nn, false, 8, o.split, sub, o.partition, shape_of_opts(o, d));
     cudaError_t e;
     Layout L = make_layout(d, nn, p.nb, false, 8, p.tab.size());
     if (L.total > kStaticScratchBytes) {
@@ -144,6 +144,7 @@ int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const 
         info->waves = static_cast<int>(p.wave_off.size());
         info->launches = info->waves + d + 3;
         info->tiles = static_cast<int>(p.ntiles);
+        for (int mu = 0; mu < d; mu++) info->leaf[mu] = shape_cut(d, mu, p.shape);
         info->resid = -1;
         info->norm_A = -1;
     }

@@ -74,6 +74,31 @@ int max_blocks(int n, int te) {
     return std::max(f(n), aligned);
 }
 
+int shape_cut(int d, int mu, int shape) {
+    const int te = tile_extent(d);
+    if (shape >= kShapeFixed) {  // fixed bounds: 6 bits per mode, a zero field takes mode 1's
+        const int code = shape - kShapeFixed;
+        int c = (code >> (6 * mu)) & 63;
+        if (c == 0) c = code & 63;
+        return std::max(2, std::min(te, c));
+    }
+    const int half = std::max(2, te / 2), three = std::max(2, (3 * te) / 4);
+    switch (shape) {
+        case 1: return three;
+        case 2: return half;
+        case 3: return mu == d - 1 ? half : te;
+        case 4: return mu == 0 ? half : te;
+        default: return te;
+    }
+}
+
+int shape_min_cut(int d, int mu, int shape) {
+    if (shape >= 0) return shape_cut(d, mu, shape);
+    int c = tile_extent(d);
+    for (int s = 0; s < kShapes; s++) c = std::min(c, shape_cut(d, mu, s));
+    return c;
+}
+
 Plan::~Plan() {
     for (auto& g : graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -189,8 +214,9 @@ void build_waves(Plan& p, int split) {
 }  // namespace
 
 void fill_plan(Plan& p, int d, const long long* n, bool gen, int elem, int split, const std::vector<uint8_t>& sub,
-               int partition) {
+               int partition, int shape) {
     p.d = d;
+    p.shape = shape;
     p.gen = gen && d >= 2;
     p.te = tile_extent(d);
     p.td = ipow(p.te, d);
@@ -203,7 +229,7 @@ void fill_plan(Plan& p, int d, const long long* n, bool gen, int elem, int split
         std::vector<uint8_t> s(static_cast<size_t>(n[mu]), 0);
         for (long long i = 0; i + 1 < n[mu]; i++) s[i] = sub[off + i];
         off += static_cast<size_t>(n[mu] - 1);
-        p.part[mu] = make_part(static_cast<int>(n[mu]), s, p.te, partition);
+        p.part[mu] = make_part(static_cast<int>(n[mu]), s, shape_cut(d, mu, shape), partition);
         p.nb[mu] = p.part[mu].nb;
         p.tstride[mu] = ts;
         ts *= p.nb[mu];
@@ -239,9 +265,9 @@ void fill_plan(Plan& p, int d, const long long* n, bool gen, int elem, int split
 }
 
 std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, int split,
-                               const std::vector<uint8_t>* sub, int partition) {
+                               const std::vector<uint8_t>* sub, int partition, int shape) {
     std::string key = std::to_string(d) + (gen ? "g" : "l") + std::to_string(elem) + "s" + std::to_string(split) +
-                      "p" + std::to_string(partition);
+                      "p" + std::to_string(partition) + "t" + std::to_string(shape);
     size_t off = 0;
     for (int mu = 0; mu < d; mu++) {
         key += ":" + std::to_string(n[mu]) + ":";
@@ -252,7 +278,7 @@ std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, in
     auto it = g_plans.find(key);
     if (it != g_plans.end()) return it->second;
     auto p = std::make_shared<Plan>();
-    fill_plan(*p, d, n, gen, elem, split, *sub, partition);
+    fill_plan(*p, d, n, gen, elem, split, *sub, partition, shape);
     if (cudaMallocHost(&p->h_tab, p->tab.size() * sizeof(int)) != cudaSuccess) return nullptr;
     std::memcpy(p->h_tab, p->tab.data(), p->tab.size() * sizeof(int));
     g_plans[key] = p;

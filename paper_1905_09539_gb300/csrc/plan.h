@@ -29,6 +29,20 @@ Part make_part(int n, const std::vector<uint8_t>& sub, int te, int rule);
 // Largest number of leaves any admissible block structure can produce.
 int max_blocks(int n, int te);
 
+// Tile shapes: the leaf bound (the recursion cutoff n_min of the split tree)
+// of every mode, at most the tile extent TE of the order d.  Candidates of
+// the autotuner: 0 every mode TE; 1 every mode 3/4 TE; 2 every mode TE/2;
+// 3 the last mode TE/2, the others TE; 4 the first mode TE/2, the others TE.
+// A shape id >= kShapeFixed holds fixed bounds (opts->nmin, opts->leaf): the
+// bound of mode mu in bits 6 mu .. 6 mu + 5 of id - kShapeFixed, a zero field
+// taking the bound of mode 1 (so id - kShapeFixed = c is the uniform bound c).
+constexpr int kShapes = 5;
+constexpr int kShapeFixed = 100;
+int shape_cut(int d, int mu, int shape);
+// Smallest bound of mode mu over the shapes a call may use (shape < 0: every
+// candidate) -- the workspace bounds take it.
+int shape_min_cut(int d, int mu, int shape);
+
 struct GraphEntry {
     std::vector<const void*> key;
     cudaGraphExec_t exec = nullptr;
@@ -37,6 +51,7 @@ struct GraphEntry {
 // One solve schedule: a block grid with its anti-diagonal wavefronts.
 struct Plan {
     int d = 0, te = 0, td = 0, tc = 0;
+    int shape = 0;                   // tile shape (leaf bound of every mode, shape_cut)
     bool gen = false;
     int elem = 8;                    // bytes per block-tensor entry
     long long n[kMaxD] = {};
@@ -77,11 +92,11 @@ Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem,
 // Schedule of one solve (partition, wavefronts, device tables) without the
 // pinned host copy of the tables and without caching.
 void fill_plan(Plan& p, int d, const long long* n, bool gen, int elem, int split, const std::vector<uint8_t>& sub,
-               int partition);
+               int partition, int shape = 0);
 
 // Cached schedule with a pinned copy of its tables (the source of a captured upload).
 std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, int split,
-                               const std::vector<uint8_t>* sub, int partition);
+                               const std::vector<uint8_t>* sub, int partition, int shape = 0);
 
 GeomArgs geom_of(const Plan& p, const Layout& L, char* base, bool flip);
 

@@ -788,16 +788,33 @@ int solve_read_structure(int d, const long long* n, const double* const* A, char
 
 int check_opts(const tsylv_opts& o, int d) {
     if (o.precision < TSYLV_FP64 || o.precision > TSYLV_BF16_REFINED || o.max_refine < 0 || !(o.tol > 0) ||
-        (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < 0 ||
+        (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < -1 ||
         o.schedule < 0 || o.schedule > 1 || o.partition < 0 || o.partition > 1 || o.resid_update < 0 ||
         o.resid_update > 1 || o.fuse_step < 0 || o.fuse_step > 3 || o.timing < 0 || o.timing > 1 ||
         o.use_graph < 0 || o.use_graph > 1 || o.wait_ms < 1 || o.wait_ms > 600000)
         return -1;
-    if (o.host_io || (o.nmin != 0 && o.nmin != tile_extent(d))) return TSYLV_EUNSUPPORTED;
+    if (o.nmin < -1) return -1;
+    for (int mu = 0; mu < kMaxD; mu++)
+        if (o.leaf[mu] < 0) return -1;
+    if (o.host_io || o.nmin == 1 || o.nmin > tile_extent(d)) return TSYLV_EUNSUPPORTED;
+    for (int mu = 0; mu < d; mu++)
+        if (o.leaf[mu] == 1 || o.leaf[mu] > tile_extent(d)) return TSYLV_EUNSUPPORTED;
     // fuse_step 1 (the first step as one launch) is no longer offered: it
     // measured slower than separate launches
     if (o.fuse_step == 1) return TSYLV_EUNSUPPORTED;
     return 0;
+}
+
+int shape_of_nmin(int nmin) { return nmin == 0 ? 0 : nmin > 0 ? kShapeFixed + nmin : -1; }
+
+int shape_of_opts(const tsylv_opts& o, int d) {
+    bool per_mode = false;
+    for (int mu = 0; mu < d; mu++) per_mode |= o.leaf[mu] > 0;
+    if (!per_mode) return shape_of_nmin(o.nmin);
+    const int dflt = o.nmin > 0 ? o.nmin : tile_extent(d);
+    int code = 0;
+    for (int mu = 0; mu < d; mu++) code |= (o.leaf[mu] > 0 ? o.leaf[mu] : dflt) << (6 * mu);
+    return kShapeFixed + code;
 }
 
 size_t solver_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o, bool transposed) {
@@ -805,10 +822,10 @@ size_t solver_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opt
     if (!shape_ok(d, n)) return 0;
     long long nn[kMaxD];
     int nb[kMaxD];
-    const int te = tile_extent(d);
+    const int shape = shape_of_opts(o, d);
     for (int mu = 0; mu < d; mu++) {
         nn[mu] = n[mu];
-        nb[mu] = max_blocks(static_cast<int>(n[mu]), te);
+        nb[mu] = max_blocks(static_cast<int>(n[mu]), shape_min_cut(d, mu, shape));
     }
     const bool g = gen && d >= 2;
     size_t total = o.precision == TSYLV_FP64 ? make_layout(d, nn, nb, g, 8, tab_ints_bound(d, nn, nb)).total
@@ -836,6 +853,13 @@ size_t solver_residual_workspace_bytes(int d, const int64_t* n, bool gen) {
     return make_ref_layout(d, nn, nb, gen && d >= 2, tab_ints_bound(d, nn, nb)).total;
 }
 
+int solve_body(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B, double* X,
+               void* work, size_t work_bytes, const tsylv_opts& o, int shape, tsylv_info* info, cudaStream_t stream,
+               bool gen, bool transposed);
+int solve_tuned(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B, double* X,
+                void* work, size_t work_bytes, const tsylv_opts& o, tsylv_info* info, cudaStream_t stream, bool gen,
+                bool transposed);
+
 int solver_solve(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B, double* X,
                  void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream,
                  bool gen, bool transposed) {
@@ -857,11 +881,84 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -(6 + sh);
     if (work_bytes < solver_workspace_bytes(d, n, gen, o, transposed)) return -(7 + sh);
     if (int st = check_opts(o, d)) return st < 0 ? -(8 + sh) : st;
-    const bool refined = o.precision != TSYLV_FP64;
     // the tensor-core precisions run the persistent schedule only
     if ((o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) && o.schedule != 0)
         return TSYLV_EUNSUPPORTED;
+    const int shape = shape_of_opts(o, d);
+    if (shape >= 0) return solve_body(d, n, A, C, B, X, work, work_bytes, o, shape, info, stream, gen, transposed);
+    return solve_tuned(d, n, A, C, B, X, work, work_bytes, o, info, stream, gen, transposed);
+}
 
+namespace {
+
+// The autotuner of single solves (opts->nmin = -1): on the first call for a
+// given order, mode sizes, form, direction and precision, every candidate
+// tile shape (the leaf bound of every mode, shape_cut) solves the equation
+// once, timed with CUDA events on `stream`; the fastest shape is kept for
+// later calls.  The timing runs write X, never B: an in-place call (X == B)
+// is not tuned and takes the default shape.
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, int> g_tuned;
+
+}  // namespace
+
+int solve_tuned(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B, double* X,
+                void* work, size_t work_bytes, const tsylv_opts& o, tsylv_info* info, cudaStream_t stream, bool gen,
+                bool transposed) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<long long> key = {dev, d, gen ? 1 : 0, transposed ? 1 : 0, o.precision, o.schedule, o.partition,
+                                  o.residual, o.fuse_step, o.resid_update};
+    for (int mu = 0; mu < d; mu++) key.push_back(n[mu]);
+    int shape = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) shape = it->second;
+    }
+    if (shape < 0 && static_cast<const void*>(X) == static_cast<const void*>(B)) shape = 0;
+    if (shape < 0) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
+            return cuda_fail_msg("autotuner events");
+        }
+        float best = 1e30f;
+        int bs = 0;
+        for (int s = 0; s < kShapes; s++) {
+            if (d == 1 && s >= 3) break;  // shapes 3, 4 coincide with 2 for one mode
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {  // the first run builds the plan and its graphs
+                cudaEventRecord(e0, stream);
+                const int st = solve_body(d, n, A, C, B, X, work, work_bytes, o, s, nullptr, stream, gen, transposed);
+                cudaEventRecord(e1, stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess || st == TSYLV_ECUDA || st == TSYLV_ETIMEOUT) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return st ? st : cuda_fail_msg("autotuner: synchronize");
+                }
+                if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = 1e30f;
+            }
+            if (ms < best) {
+                best = ms;
+                bs = s;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        (void)cudaGetLastError();
+        shape = bs;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = shape;
+    }
+    return solve_body(d, n, A, C, B, X, work, work_bytes, o, shape, info, stream, gen, transposed);
+}
+
+int solve_body(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B, double* X,
+               void* work, size_t work_bytes, const tsylv_opts& o, int shape, tsylv_info* info, cudaStream_t stream,
+               bool gen, bool transposed) {
+    const int sh = gen ? 1 : 0;
+    const bool refined = o.precision != TSYLV_FP64;
     Call c;
     c.d = d;
     c.gen = gen && d >= 2;
@@ -881,7 +978,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
 
     std::vector<uint8_t> sub;
     if (int st = read_structure(d, c.n, c.A, c.base, transposed, stream, sub)) return st;
-    c.plan = get_plan(d, c.n, c.gen, refined ? 4 : 8, o.split, &sub, o.partition);
+    c.plan = get_plan(d, c.n, c.gen, refined ? 4 : 8, o.split, &sub, o.partition, shape);
     if (!c.plan) return cuda_fail_msg("plan: pinned host allocation");
     if (int st = prepare_kernels()) return st;
     c.timing = o.timing != 0;
@@ -920,6 +1017,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
             info->waves = static_cast<int>(c.plan->wave_off.size());
             info->launches = (c.persistent ? 2 : info->waves) + d * (c.gen ? 2 : 1) + 2;
             info->tiles = static_cast<int>(c.plan->ntiles);
+            for (int mu = 0; mu < d; mu++) info->leaf[mu] = shape_cut(d, mu, shape);
             info->resid = -1;
             info->norm_A = -1;
             info->flops = c.plan->flops;
@@ -1045,6 +1143,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
         info->launches = (iters - piped) * ((c.persistent ? 2 : info->waves) + (c.gen ? d : 1) + 4) +
                          (piped ? 8 : 0) + 4 * d + 8;
         info->tiles = static_cast<int>(c.plan->ntiles);
+        for (int mu = 0; mu < d; mu++) info->leaf[mu] = shape_cut(d, mu, shape);
         info->resid = rho;
         info->norm_A = nA;
         info->flops = c.plan->flops * iters;

@@ -30,10 +30,18 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
 
 cudaStream_t capture_stream();
 
+// Tile shape of opts->nmin: 0 the default, nmin > 0 that uniform leaf bound,
+// -1 (autotuned) any candidate.
+int shape_of_nmin(int nmin);
+// Tile shape of the options: opts->leaf (per-mode bounds, zero entries take
+// nmin's) when any entry is set, else shape_of_nmin.
+int shape_of_opts(const tsylv_opts& o, int d);
+
 // Shared argument checks of the solve entry points.
 bool solve_shape_ok(int d, const int64_t* n);
 // 0, -1 for an option field out of its range, or TSYLV_EUNSUPPORTED for a
-// valid request this build does not serve (host_io, a non-default nmin).
+// valid request this build does not serve (host_io, nmin 1 or above the tile
+// extent, fuse_step 1).
 int check_opts(const tsylv_opts& o, int d);
 // 2x2 block structure of every A_mu: the sub-diagonal is gathered into
 // base + 256, read back (a synchronisation of `stream`) and validated (-3

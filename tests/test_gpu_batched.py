@@ -170,3 +170,52 @@ def test_batch_refined_mixed_orders_unsupported(lib):
     ps = [synthetic.problem([13, i], s) for i, s in enumerate(shapes)]
     with pytest.raises((lib.TsylvError, ValueError)):
         lib.tsylv_solve_batched(_problems(ps, False), precision=lib.TSYLV_FP32_REFINED)
+
+
+def test_batch_in_place_first_call_tuned(lib):
+    """X_pool == B_pool on the first call of a new batch: the autotuner's
+    timing runs must leave B untouched (each equation against the oracle)."""
+    ps = synthetic.batch(17, count=20, lo=8, hi=24)
+    prs = _problems(ps, False)
+    pools = lib.BatchPools(prs)
+    info = lib.Info()
+    st = pools.solve(info=info, inplace=True)
+    assert all(s == 0 for s in st)
+    for p, X in zip(ps, pools.solutions()):
+        Xo = oracle.solve_recursive(p["A"], p["B"], None, nmin=4)
+        assert rel_err(to_host(X), Xo) <= 1e-11
+
+
+SHAPE_CANDIDATES = {3: [(8, 8, 8), (6, 6, 6), (4, 4, 4), (8, 8, 4), (4, 8, 8)],
+                    2: [(16, 16), (12, 12), (8, 8), (16, 8), (8, 16)]}
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_batch_tuned_tile_shape(lib, gen):
+    """The batch autotuner picks a tile shape among its candidates; every
+    equation agrees with the oracle."""
+    ps = synthetic.batch(19, count=40, lo=8, hi=40)
+    ps = [synthetic.problem([19, 200 + i], p["shape"], generalized=gen) for i, p in enumerate(ps)]
+    info = lib.Info()
+    Xs, st = lib.tsylv_solve_batched(_problems(ps, gen), generalized=gen, info=info)
+    assert all(s == 0 for s in st)
+    assert tuple(info.leaf[:3]) in SHAPE_CANDIDATES[3]
+    for p, X in zip(ps, Xs):
+        assert rel_err(to_host(X), oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)) <= 1e-11
+
+
+@pytest.mark.parametrize("leaf", [(8, 8, 8), (6, 6, 6), (4, 4, 4), (8, 8, 4), (4, 8, 8), (2, 3, 5)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32r"])
+def test_batch_fixed_tile_shape(lib, leaf, prec):
+    """Every tile shape the tuner can pick (and an odd one), fixed through
+    opts.leaf, FP64 and FP32-refined: each equation against the oracle."""
+    ps = synthetic.batch(23, count=12, lo=8, hi=30)
+    ps = [synthetic.problem([23, 300 + i], p["shape"], force_blocks=[[n // 2 - 1] for n in p["shape"]])
+          for i, p in enumerate(ps)]
+    info = lib.Info()
+    precision = lib.TSYLV_FP64 if prec == "fp64" else lib.TSYLV_FP32_REFINED
+    Xs, st = lib.tsylv_solve_batched(_problems(ps, False), info=info, leaf=leaf, precision=precision)
+    assert all(s == 0 for s in st)
+    tol = 1e-11 if prec == "fp64" else 1e-10
+    for p, X in zip(ps, Xs):
+        assert rel_err(to_host(X), oracle.solve_recursive(p["A"], p["B"], None, nmin=4)) <= tol

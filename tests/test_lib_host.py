@@ -91,9 +91,9 @@ def test_option_validation_without_gpu(lib):
 
     for kw in ({"fuse_step": 4}, {"fuse_step": -1}, {"schedule": 2}, {"partition": 2}, {"resid_update": 2},
                {"precision": 9}, {"tol": 0.0}, {"split": -1}, {"max_refine": -1}, {"residual": 7},
-               {"wait_ms": 0}, {"wait_ms": 600001}):
+               {"wait_ms": 0}, {"wait_ms": 600001}, {"nmin": -2}):
         assert st(**kw) == -8, kw
-    for kw in ({"host_io": 1}, {"fuse_step": 1}, {"nmin": 5},
+    for kw in ({"host_io": 1}, {"fuse_step": 1}, {"nmin": 17}, {"nmin": 1},
                {"precision": _lib.TSYLV_TF32_REFINED, "schedule": 1},
                {"precision": _lib.TSYLV_BF16_REFINED, "schedule": 1}):
         assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
@@ -102,8 +102,9 @@ def test_option_validation_without_gpu(lib):
 def test_noalloc_option_validation_without_gpu(lib):
     """tsylv_solve_noalloc checks its options as tsylv_solve does (-6, its
     opts argument, for a field out of range; TSYLV_EUNSUPPORTED for host_io or
-    a non-default nmin), refuses any precision but FP64 with -6 and event
-    timing with TSYLV_EUNSUPPORTED -- all before any CUDA call."""
+    an nmin above the tile extent), refuses any precision but FP64 with -6, and
+    event timing and autotuning (nmin -1) with TSYLV_EUNSUPPORTED -- all before
+    any CUDA call."""
     from paper_1905_09539_gb300 import _lib
     n = (ctypes.c_int64 * 2)(4, 4)
     P = ctypes.c_void_p
@@ -117,7 +118,7 @@ def test_noalloc_option_validation_without_gpu(lib):
                {"tol": 0.0}, {"split": -1}, {"max_refine": -1}, {"residual": 7}, {"timing": 2},
                {"wait_ms": 0}, {"precision": _lib.TSYLV_FP32_REFINED}):
         assert st(**kw) == -6, kw
-    for kw in ({"host_io": 1}, {"nmin": 5}, {"timing": 1}):
+    for kw in ({"host_io": 1}, {"nmin": 17}, {"nmin": -1}, {"timing": 1}):
         assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
     bad = (ctypes.c_int64 * 2)(4, 0)
     assert lib.tsylv_solve_noalloc(2, bad, fake, P(16), P(16), None, None, None) == -2
@@ -194,8 +195,12 @@ def test_batched_workspace_and_validation(lib):
     assert lib.tsylv_batched_workspace_bytes(count, d, n, 0, ctypes.byref(o32)) == 0
     d3 = (ctypes.c_int * 2)(3, 3)
     n3 = (ctypes.c_int64 * 6)(8, 48, 20, 33, 9, 17)
+    o8 = _lib.default_opts(nmin=8)  # FP64 with the tile shape fixed (no tuning over smaller cutoffs)
     assert lib.tsylv_batched_workspace_bytes(2, d3, n3, 0, ctypes.byref(o32)) > \
-        lib.tsylv_batched_workspace_bytes(2, d3, n3, 0, ctypes.byref(o))
+        lib.tsylv_batched_workspace_bytes(2, d3, n3, 0, ctypes.byref(o8))
+    # the default FP64 batch tunes the tile shape: its bound covers the smallest cutoff
+    assert lib.tsylv_batched_workspace_bytes(2, d3, n3, 0, ctypes.byref(o)) > \
+        lib.tsylv_batched_workspace_bytes(2, d3, n3, 0, ctypes.byref(o8))
     P = ctypes.c_void_p
     offA = (ctypes.c_int64 * 8)(*range(8))
     offX = (ctypes.c_int64 * 3)(0, 1, 2)
