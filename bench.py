@@ -545,7 +545,8 @@ def run_ours(args, ws, rank, local):
     ib = infos["batched_fp64"]
     parts["batched_fp64"] = {"ms": tb, "unknowns_per_s": units_rank["batched"] / (tb * 1e-3), "equations": pools.count,
                              "unknowns": pools.unknowns, "tiles": ib.tiles, "max_waves": ib.waves,
-                             "queue_order": ib.batch_order, "ctas_per_sm": ib.batch_ctas_per_sm}
+                             "queue_order": ib.batch_order, "ctas_per_sm": ib.batch_ctas_per_sm,
+                             "tile_shape": list(ib.leaf[:3])}
     mixed_vs_fp64 = {"laplace": parts["fp64_laplace"]["ms"] / parts["fp32r_laplace"]["ms"],
                      "generalized": parts["fp64_generalized"]["ms"] / parts["fp32r_generalized"]["ms"]}
 
@@ -767,7 +768,56 @@ def run_ours(args, ws, rank, local):
             "transform_frac_fp64_peak": ftr / (tt * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
             "note": "two transforms (B x U^T, X x U) + FP64 triangular solve on the GPU; real Schur forms on the host"}
         del Ag, Ug, Tb, Xg
+        # the batch with the tile shape fixed at the default (8, 8, 8): what the
+        # shape search of the autotuner gains
         X64 = pools.X.clone()
+        iff = _lib.Info()
+        fnf = lambda: pools.solve(info=iff, leaf=(8, 8, 8))
+        fnf()
+        tf = event_ms(fnf, max(3, args.steps))
+        other["batched_fp64_fixed_shape_8x8x8"] = {
+            "ms": tf, "tuned_ms": parts["batched_fp64"]["ms"], "tuned_shape": parts["batched_fp64"]["tile_shape"],
+            "tuned_vs_fixed": tf / parts["batched_fp64"]["ms"], "queue_order": iff.batch_order,
+            "ctas_per_sm": iff.batch_ctas_per_sm,
+            "rel_diff_vs_tuned": float(torch.linalg.vector_norm(pools.X - X64) / torch.linalg.vector_norm(X64))}
+        # single solves with the autotuned tile shape (opts.nmin = -1; the first
+        # call tunes, the timed calls reuse the choice)
+        tuned = {}
+        for name, gen, prec in SOLVE_PARTS:
+            pr = probs[gen]
+            Xt = ts.empty_fortran(shape, dev)
+            it_ = _lib.Info()
+            if gen:
+                fnt = lambda: ts.gtsylv_solve(pr["A"], pr["C"], pr["B"], X=Xt, info=it_, precision=PREC[prec], nmin=-1)
+            else:
+                fnt = lambda: ts.tsylv_solve(pr["A"], pr["B"], X=Xt, info=it_, precision=PREC[prec], nmin=-1)
+            fnt()
+            tt = event_ms(fnt, 3)
+            tuned[name] = {"ms": tt, "tile_shape": list(it_.leaf[:3]), "default_ms": parts[name]["ms"],
+                           "tuned_vs_default": parts[name]["ms"] / tt}
+            del Xt
+        other["autotuned_256"] = tuned
+        # the 64^3 workload (Laplace FP64, and the generalized form): default
+        # tile shape against the autotuned one
+        small = {}
+        for gen in (False, True):
+            q = synthetic.problem(args.seed + rank, (64, 64, 64), generalized=gen)
+            qA = [to_dev(a) for a in q["A"]]
+            qC = [to_dev(c) for c in q["C"]] if gen else None
+            qB = to_dev(q["B"])
+            qX = ts.empty_fortran((64, 64, 64), dev)
+            row = {}
+            for tag, nm in (("default", 0), ("tuned", -1)):
+                qi = _lib.Info()
+                if gen:
+                    fq = lambda: ts.gtsylv_solve(qA, qC, qB, X=qX, info=qi, nmin=nm)
+                else:
+                    fq = lambda: ts.tsylv_solve(qA, qB, X=qX, info=qi, nmin=nm)
+                fq()
+                row[tag] = {"ms": event_ms(fq, 5), "tile_shape": list(qi.leaf[:3])}
+            row["tuned_vs_default"] = row["default"]["ms"] / row["tuned"]["ms"]
+            small["generalized" if gen else "laplace"] = row
+        other["autotuned_64"] = small
         ir = _lib.Info()
         fnr = lambda: pools.solve(info=ir, precision=_lib.TSYLV_FP32_REFINED)
         fnr()

@@ -116,8 +116,8 @@ typedef struct tsylv_opts {
                          bound for every mode; -1: autotuned.  A single solve tunes
                          on its first call per order, mode sizes, form, direction
                          and precision (each candidate tile shape -- every mode TE,
-                         3/4 TE or TE/2, or TE/2 in the first or the last mode
-                         only -- solves once, timed; X is written, B is not; an
+                         TE - 1, 3/4 TE or TE/2, or TE/2 in the last mode only
+                         -- solves once, timed; X is written, B is not; an
                          in-place call takes the default).  tsylv_solve_batched
                          tunes by default (0 or -1) together with its launch.
                          Values above TE, and 1, return TSYLV_EUNSUPPORTED.       */

@@ -353,6 +353,17 @@ std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t
     return p;
 }
 
+// Layout of one plan with its own table and data sizes (within the bounds'
+// layout the workspace was sized for): the table uploaded per call is then no
+// larger than the plan needs.
+BatchLayout plan_layout(const BatchPlan& p, const int* d, const int64_t* n_packed, int elem) {
+    long long pints = 0;
+    for (const EqPlan& q : p.eq)
+        for (int mu = 0; mu < q.d; mu++) pints += 2 * q.nb[mu];
+    return make_batch_layout(p.count, d, n_packed, p.gen, elem, static_cast<long long>(p.jobs[0].size()),
+                             static_cast<long long>(p.cjobs.size()), pints, p.data_bytes);
+}
+
 // The uploaded table of one call: parameter blocks with device pointers into
 // this workspace, the job lists and the partitions.
 void fill_table(const BatchPlan& p, const BatchLayout& L, char* base, int policy, std::vector<unsigned char>& out,
@@ -1142,7 +1153,7 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
         } else {
             const bool only_d1 = plan0->dlist.size() == 1 && plan0->dlist[0] == 1;
             for (int sc = 0; sc < kShapes; sc++)
-                if (!(only_d1 && sc >= 3)) shapes.push_back(sc);  // 3, 4 coincide with 2 for one mode
+                if (!(only_d1 && sc >= 4)) shapes.push_back(sc);  // 4 coincides with 3 for one mode
         }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1157,8 +1168,10 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
                                                                                      part_rule, sc);
             if (!ps || ps->data_bytes > bd.data) continue;
             c.plan = ps.get();
+            c.L = plan_layout(*ps, d, n_packed, 8);
+            if (c.L.total > L.total) continue;
             for (int pol = 0; pol < kPolicies; pol++) {
-                fill_table(*ps, L, base, pol, tabv, off_A, off_X);
+                fill_table(*ps, c.L, base, pol, tabv, off_A, off_X);
                 std::memcpy(t_pin_tab.ptr, tabv.data(), tabv.size());
                 c.htab = t_pin_tab.ptr;
                 for (int gsz : grids) {
@@ -1206,8 +1219,10 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
         if (plan->data_bytes > bd.data) return cuda_fail_msg("batched: workspace bound");
     }
     c.plan = plan.get();
+    c.L = plan_layout(*plan, d, n_packed, 8);
+    if (c.L.total > L.total) return cuda_fail_msg("batched: workspace bound");
     set_grid(per_sm);
-    fill_table(*plan, L, base, policy, tabv, off_A, off_X);
+    fill_table(*plan, c.L, base, policy, tabv, off_A, off_X);
     std::memcpy(t_pin_tab.ptr, tabv.data(), tabv.size());
     c.htab = t_pin_tab.ptr;
 

@@ -82,12 +82,12 @@ int shape_cut(int d, int mu, int shape) {
         if (c == 0) c = code & 63;
         return std::max(2, std::min(te, c));
     }
-    const int half = std::max(2, te / 2), three = std::max(2, (3 * te) / 4);
+    const int half = std::max(2, te / 2), three = std::max(2, (3 * te) / 4), less = std::max(2, te - 1);
     switch (shape) {
-        case 1: return three;
-        case 2: return half;
-        case 3: return mu == d - 1 ? half : te;
-        case 4: return mu == 0 ? half : te;
+        case 1: return less;
+        case 2: return three;
+        case 3: return half;
+        case 4: return mu == d - 1 ? half : te;
         default: return te;
     }
 }

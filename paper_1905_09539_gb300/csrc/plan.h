@@ -31,8 +31,8 @@ int max_blocks(int n, int te);
 
 // Tile shapes: the leaf bound (the recursion cutoff n_min of the split tree)
 // of every mode, at most the tile extent TE of the order d.  Candidates of
-// the autotuner: 0 every mode TE; 1 every mode 3/4 TE; 2 every mode TE/2;
-// 3 the last mode TE/2, the others TE; 4 the first mode TE/2, the others TE.
+// the autotuner: 0 every mode TE; 1 every mode TE - 1; 2 every mode 3/4 TE;
+// 3 every mode TE/2; 4 the last mode TE/2, the others TE (bounds at least 2).
 // A shape id >= kShapeFixed holds fixed bounds (opts->nmin, opts->leaf): the
 // bound of mode mu in bits 6 mu .. 6 mu + 5 of id - kShapeFixed, a zero field
 // taking the bound of mode 1 (so id - kShapeFixed = c is the uniform bound c).

@@ -926,7 +926,7 @@ int solve_tuned(int d, const int64_t* n, const double* const* A, const double* c
         float best = 1e30f;
         int bs = 0;
         for (int s = 0; s < kShapes; s++) {
-            if (d == 1 && s >= 3) break;  // shapes 3, 4 coincide with 2 for one mode
+            if (d == 1 && s >= 4) break;  // shape 4 coincides with 3 for one mode
             float ms = 1e30f;
             for (int rep = 0; rep < 2; rep++) {  // the first run builds the plan and its graphs
                 cudaEventRecord(e0, stream);

@@ -186,8 +186,8 @@ def test_batch_in_place_first_call_tuned(lib):
         assert rel_err(to_host(X), Xo) <= 1e-11
 
 
-SHAPE_CANDIDATES = {3: [(8, 8, 8), (6, 6, 6), (4, 4, 4), (8, 8, 4), (4, 8, 8)],
-                    2: [(16, 16), (12, 12), (8, 8), (16, 8), (8, 16)]}
+SHAPE_CANDIDATES = {3: [(8, 8, 8), (7, 7, 7), (6, 6, 6), (4, 4, 4), (8, 8, 4)],
+                    2: [(16, 16), (15, 15), (12, 12), (8, 8), (16, 8)]}
 
 
 @pytest.mark.parametrize("gen", [False, True])
@@ -204,7 +204,7 @@ def test_batch_tuned_tile_shape(lib, gen):
         assert rel_err(to_host(X), oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)) <= 1e-11
 
 
-@pytest.mark.parametrize("leaf", [(8, 8, 8), (6, 6, 6), (4, 4, 4), (8, 8, 4), (4, 8, 8), (2, 3, 5)])
+@pytest.mark.parametrize("leaf", [(8, 8, 8), (7, 7, 7), (6, 6, 6), (4, 4, 4), (8, 8, 4), (2, 3, 5)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32r"])
 def test_batch_fixed_tile_shape(lib, leaf, prec):
     """Every tile shape the tuner can pick (and an odd one), fixed through

@@ -16,10 +16,10 @@ from tests.gpu_helpers import max_rel, rel_err, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-# the autotuner's candidates: every mode TE, 3/4 TE, TE/2; TE/2 in the last or the first mode only
-CANDIDATES = {2: [(16, 16), (12, 12), (8, 8), (16, 8), (8, 16)],
-              3: [(8, 8, 8), (6, 6, 6), (4, 4, 4), (8, 8, 4), (4, 8, 8)],
-              4: [(4, 4, 4, 4), (3, 3, 3, 3), (2, 2, 2, 2), (4, 4, 4, 2), (2, 4, 4, 4)]}
+# the autotuner's candidates: every mode TE, TE - 1, 3/4 TE, TE/2; TE/2 in the last mode only
+CANDIDATES = {2: [(16, 16), (15, 15), (12, 12), (8, 8), (16, 8)],
+              3: [(8, 8, 8), (7, 7, 7), (6, 6, 6), (4, 4, 4), (8, 8, 4)],
+              4: [(4, 4, 4, 4), (3, 3, 3, 3), (2, 2, 2, 2), (4, 4, 4, 2)]}
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +40,7 @@ def _solve(ts, p, **kw):
     return X, st, info
 
 
-SHAPES = [(3, (37, 30, 23), leaf) for leaf in CANDIDATES[3] + [(2, 3, 7), (5, 5, 5)]] + \
+SHAPES = [(3, (37, 30, 23), leaf) for leaf in CANDIDATES[3] + [(2, 3, 7), (5, 5, 5), (4, 8, 8)]] + \
          [(4, (13, 11, 10, 9), leaf) for leaf in CANDIDATES[4] + [(3, 2, 4, 3)]]
 
 
