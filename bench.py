@@ -818,6 +818,30 @@ def run_ours(args, ws, rank, local):
             row["tuned_vs_default"] = row["default"]["ms"] / row["tuned"]["ms"]
             small["generalized" if gen else "laplace"] = row
         other["autotuned_64"] = small
+        # the paper's n_min sweep shapes (Sec. 2.4: n = 80 for d = 3, n = 25 for
+        # d = 4; the merged-mode sweep also covers d = 5, here n = 14): the FP64
+        # Laplace solve at every recursion cutoff the block tiles allow, and a
+        # d = 5 workload (20^5) in every precision
+        sweep = {}
+        for dd, nn_ in ((3, 80), (4, 25), (5, 14)):
+            shp = (nn_,) * dd
+            q = synthetic.problem(args.seed + rank, shp)
+            qA = [to_dev(a) for a in q["A"]]
+            qB = to_dev(q["B"])
+            qX = ts.empty_fortran(shp, dev)
+            te = {3: 8, 4: 4, 5: 4}[dd]
+            row = {}
+            for nm in range(2, te + 1):
+                fq = lambda: ts.tsylv_solve(qA, qB, X=qX, nmin=nm)
+                fq()
+                row[str(nm)] = event_ms(fq, 5)
+            sweep["d%d_n%d_laplace_fp64_ms_by_nmin" % (dd, nn_)] = row
+        other["paper_nmin_sweeps"] = sweep
+        q = synthetic.problem(args.seed + rank, (20,) * 5)
+        qA = [to_dev(a) for a in q["A"]]
+        qB = to_dev(q["B"])
+        other["d5_laplace_20"] = precision_sweep(qA, None, qB, (20,) * 5, (0, 1, 2, 3))
+        del qA, qB
         ir = _lib.Info()
         fnr = lambda: pools.solve(info=ir, precision=_lib.TSYLV_FP32_REFINED)
         fnr()

@@ -112,7 +112,7 @@ typedef struct tsylv_opts {
     int residual;     /* enum tsylv_residual_kind, default TSYLV_RESID_DF64          */
     int nmin;         /* recursion cutoff: the largest block extent per mode (leaf
                          bound of the split tree).  0 (default): the tile extent
-                         TE of the order d (32, 16, 8, 4 for d = 1..4); 2..TE: that
+                         TE of the order d (32, 16, 8, 4, 4 for d = 1..5); 2..TE: that
                          bound for every mode; -1: autotuned.  A single solve tunes
                          on its first call per order, mode sizes, form, direction
                          and precision (each candidate tile shape -- every mode TE,
@@ -153,7 +153,7 @@ typedef struct tsylv_opts {
                          2000.  A wait that runs out ends the launch and the call
                          returns TSYLV_ETIMEOUT; raise it on a GPU shared with
                          long-running work                                        */
-    int leaf[4];      /* per-mode leaf bounds (tile shape), overriding nmin mode by
+    int leaf[5];      /* per-mode leaf bounds (tile shape), overriding nmin mode by
                          mode: entry mu in 2..TE bounds the blocks of mode mu, 0
                          takes nmin's bound (TE when nmin <= 0).  Any nonzero entry
                          fixes the shape (no autotuning).  Default all 0.         */
@@ -173,7 +173,7 @@ typedef struct tsylv_info {
     int batch_order;      /* tsylv_solve_batched: job-queue order used (0 longest remaining
                              path first, 1 wavefront-major, 2 equation-major)      */
     int batch_ctas_per_sm;/* tsylv_solve_batched: resident CTAs per SM used          */
-    int leaf[4];          /* leaf bound (recursion cutoff) of every mode in the block
+    int leaf[5];          /* leaf bound (recursion cutoff) of every mode in the block
                              partition used -- the tile shape (opts->nmin); for a
                              batch, that of its equations of the highest order d   */
 } tsylv_info;
@@ -191,11 +191,11 @@ const char* tsylv_last_error(void);
 
 /* Workspace bytes for tsylv_solve (generalized = 0) / gtsylv_solve
  * (generalized = 1) and their transposed variants.  Returns 0 for invalid
- * arguments.  d in 1..4, every n[mu] >= 1. */
+ * arguments.  d in 1..5 (1..4 for the generalized form), every n[mu] >= 1. */
 size_t tsylv_workspace_bytes(int d, const int64_t* n, int generalized, const tsylv_opts* opts);
 
 /* Solve the Laplace-like equation Eq. (2.2).
- *   d          number of modes (1..4)
+ *   d          number of modes (1..5)
  *   n          host array of d mode sizes
  *   A          host array of d pointers to the n_mu x n_mu upper
  *              quasi-triangular coefficients
@@ -278,7 +278,7 @@ size_t tsylv_batched_workspace_bytes(int count, const int* d, const int64_t* n_p
  * from the split rule of Alg. 2, same block updates and base case), so every
  * result equals the corresponding single solve up to rounding.
  *   count       number of equations (>= 1)
- *   d           host array [count] of orders (1..4)
+ *   d           host array [count] of orders (1..5; 1..4 with C_pool)
  *   n_packed    host array: the mode sizes of all equations, concatenated
  *   off_A       host array [sum d]: element offset of each A_mu (and C_mu) in
  *               A_pool / C_pool, in the order of n_packed; every matrix is

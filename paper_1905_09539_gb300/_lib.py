@@ -28,7 +28,7 @@ class Opts(ctypes.Structure):
                 ("residual", ctypes.c_int), ("nmin", ctypes.c_int), ("split", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("partition", ctypes.c_int), ("resid_update", ctypes.c_int),
-                ("fuse_step", ctypes.c_int), ("wait_ms", ctypes.c_int), ("leaf", ctypes.c_int * 4)]
+                ("fuse_step", ctypes.c_int), ("wait_ms", ctypes.c_int), ("leaf", ctypes.c_int * 5)]
 
 
 class Info(ctypes.Structure):
@@ -38,7 +38,7 @@ class Info(ctypes.Structure):
                 ("t_resid_ms", ctypes.c_double),
                 ("batch_order", ctypes.c_int),
                 ("batch_ctas_per_sm", ctypes.c_int),
-                ("leaf", ctypes.c_int * 4)]
+                ("leaf", ctypes.c_int * 5)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if k == "leaf" else getattr(self, k)) for k, _ in self._fields_}
@@ -114,7 +114,7 @@ def default_opts(**kw):
         if not hasattr(o, k):
             raise TypeError("unknown option %r" % k)
         if k == "leaf":
-            v = (ctypes.c_int * 4)(*(list(v) + [0] * (4 - len(v))))
+            v = (ctypes.c_int * 5)(*(list(v) + [0] * (5 - len(v))))
         setattr(o, k, v)
     return o
 

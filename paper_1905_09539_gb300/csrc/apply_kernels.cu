@@ -77,6 +77,7 @@ cudaError_t launch_apply_m(int d, const ApplyArgs& a, cudaStream_t s) {
         case 2: return launch_apply_t<2, MD>(a, s);
         case 3: return launch_apply_t<3, MD>(a, s);
         case 4: return launch_apply_t<4, MD>(a, s);
+        case 5: return launch_apply_t<5, MD>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -87,7 +88,8 @@ cudaError_t prepare_apply_m() {
     if ((e = prepare_apply_t<1, MD>()) != cudaSuccess) return e;
     if ((e = prepare_apply_t<2, MD>()) != cudaSuccess) return e;
     if ((e = prepare_apply_t<3, MD>()) != cudaSuccess) return e;
-    return prepare_apply_t<4, MD>();
+    if ((e = prepare_apply_t<4, MD>()) != cudaSuccess) return e;
+    return prepare_apply_t<5, MD>();
 }
 
 }  // namespace
@@ -119,6 +121,7 @@ cudaError_t launch_apply_batched(int d, int mode, const ApplyArgs* eqs, const in
     TSYLV_APPLY_B(2)
     TSYLV_APPLY_B(3)
     TSYLV_APPLY_B(4)
+    TSYLV_APPLY_B(5)
 #undef TSYLV_APPLY_B
     return cudaErrorInvalidValue;
 }
@@ -133,6 +136,7 @@ cudaError_t prepare_apply_batched() {
     TSYLV_PREP_B(2)
     TSYLV_PREP_B(3)
     TSYLV_PREP_B(4)
+    TSYLV_PREP_B(5)
 #undef TSYLV_PREP_B
     return e;
 }

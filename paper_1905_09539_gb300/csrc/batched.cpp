@@ -1072,6 +1072,9 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     if (o.precision != TSYLV_FP64 && o.precision != TSYLV_FP32_REFINED) return TSYLV_EUNSUPPORTED;
     const bool refined = o.precision == TSYLV_FP32_REFINED;
     if (refined && !uniform_order(count, d)) return TSYLV_EUNSUPPORTED;
+    if (gen)  // the generalized form is built for d <= 4
+        for (int e = 0; e < count; e++)
+            if (d[e] > 4) return TSYLV_EUNSUPPORTED;
     const size_t need = solver_batched_workspace_bytes(count, d, n_packed, gen, o);
     if (!need || work_bytes < need) return -11;
     if (o.split < 0 || o.partition < 0 || o.partition > 1 || o.wait_ms < 1 || o.wait_ms > 600000 || o.nmin < -1)

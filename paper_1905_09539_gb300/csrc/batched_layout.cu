@@ -169,6 +169,7 @@ cudaError_t launch_batched_pk(int d, bool gen, const BatchArgs& a, int grid, cud
         case 7: return launch_batched_t<T, 3, true, PK>(a, grid, s);
         case 8: return launch_batched_t<T, 4, false, PK>(a, grid, s);
         case 9: return launch_batched_t<T, 4, true, PK>(a, grid, s);
+        case 10: return launch_batched_t<T, 5, false, PK>(a, grid, s);  // d = 5: the Laplace form only
         default: return cudaErrorInvalidValue;
     }
 }
@@ -184,6 +185,7 @@ int batched_occupancy_pk(int d, bool gen) {
         case 7: return batched_occupancy_t<T, 3, true, PK>();
         case 8: return batched_occupancy_t<T, 4, false, PK>();
         case 9: return batched_occupancy_t<T, 4, true, PK>();
+        case 10: return batched_occupancy_t<T, 5, false, PK>();
         default: return 1;
     }
 }
@@ -197,7 +199,8 @@ cudaError_t prepare_batched_pk() {
     if ((e = prepare_batched_t<T, 3, false, PK>()) != cudaSuccess) return e;
     if ((e = prepare_batched_t<T, 3, true, PK>()) != cudaSuccess) return e;
     if ((e = prepare_batched_t<T, 4, false, PK>()) != cudaSuccess) return e;
-    return prepare_batched_t<T, 4, true, PK>();
+    if ((e = prepare_batched_t<T, 4, true, PK>()) != cudaSuccess) return e;
+    return prepare_batched_t<T, 5, false, PK>();
 }
 
 }  // namespace

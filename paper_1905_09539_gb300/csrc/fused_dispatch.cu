@@ -18,6 +18,7 @@ cudaError_t launch_pk(int d, const Refine2Args& f, int grid, cudaStream_t s) {
         case 2: return launch_refine2_t<2, PK>(f, grid, s);
         case 3: return launch_refine2_t<3, PK>(f, grid, s);
         case 4: return launch_refine2_t<4, PK>(f, grid, s);
+        case 5: return launch_refine2_t<5, PK>(f, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -28,6 +29,7 @@ int occupancy_pk(int d) {
         case 2: return refine2_occupancy_t<2, PK>();
         case 3: return refine2_occupancy_t<3, PK>();
         case 4: return refine2_occupancy_t<4, PK>();
+        case 5: return refine2_occupancy_t<5, PK>();
         default: return 1;
     }
 }
@@ -37,7 +39,8 @@ cudaError_t prepare_pk() {
     cudaError_t e;
     if ((e = prepare_refine2_t<2, PK>()) != cudaSuccess) return e;
     if ((e = prepare_refine2_t<3, PK>()) != cudaSuccess) return e;
-    return prepare_refine2_t<4, PK>();
+    if ((e = prepare_refine2_t<4, PK>()) != cudaSuccess) return e;
+    return prepare_refine2_t<5, PK>();
 }
 
 }  // namespace

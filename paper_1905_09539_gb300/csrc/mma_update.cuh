@@ -225,7 +225,8 @@ __device__ __forceinline__ void mma_store(float (&c)[NS][MmaCfg<D, PK>::UPW][4],
                             case 0: e = mma_detail::elem_of<D, 0>(r, i); break;
                             case 1: e = mma_detail::elem_of<D, (D > 1 ? 1 : 0)>(r, i); break;
                             case 2: e = mma_detail::elem_of<D, (D > 2 ? 2 : 0)>(r, i); break;
-                            default: e = mma_detail::elem_of<D, (D > 3 ? 3 : 0)>(r, i); break;
+                            case 3: e = mma_detail::elem_of<D, (D > 3 ? 3 : 0)>(r, i); break;
+                            default: e = mma_detail::elem_of<D, (D > 4 ? 4 : 0)>(r, i); break;
                         }
                         dst[e] = first ? c[s][u][h] : dst[e] + c[s][u][h];
                     }

@@ -881,9 +881,11 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -(6 + sh);
     if (work_bytes < solver_workspace_bytes(d, n, gen, o, transposed)) return -(7 + sh);
     if (int st = check_opts(o, d)) return st < 0 ? -(8 + sh) : st;
-    // the tensor-core precisions run the persistent schedule only
+    // the tensor-core precisions run the persistent schedule only; the
+    // generalized form is built for d <= 4
     if ((o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) && o.schedule != 0)
         return TSYLV_EUNSUPPORTED;
+    if (gen && d > 4) return TSYLV_EUNSUPPORTED;
     const int shape = shape_of_opts(o, d);
     if (shape >= 0) return solve_body(d, n, A, C, B, X, work, work_bytes, o, shape, info, stream, gen, transposed);
     return solve_tuned(d, n, A, C, B, X, work, work_bytes, o, info, stream, gen, transposed);
@@ -1232,6 +1234,7 @@ int solver_residual(int d, const int64_t* n, const double* const* A, const doubl
     if (work_bytes < solver_residual_workspace_bytes(d, n, gen)) return -10;
     if (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64 || o.wait_ms < 1 || o.wait_ms > 600000)
         return -11;
+    if (gen && d > 4) return TSYLV_EUNSUPPORTED;  // the generalized form is built for d <= 4
     Call c;
     c.d = d;
     c.gen = gen && d >= 2;

@@ -10,12 +10,12 @@
 
 namespace tsylv {
 
-constexpr int kMaxD = 4;
+constexpr int kMaxD = 5;
 constexpr int kThreads = 128;       // threads per CTA of the block kernels
 constexpr int kMaxCluster = 8;      // portable cluster size for split block updates
 
 // Block extent per mode (the leaf size n_min of the split tree) as a function
-// of the order d: the block holds at most 512 unknowns.
+// of the order d: the block holds at most 512 unknowns (1024 for d = 5).
 __host__ __device__ constexpr int tile_extent(int d) { return d == 1 ? 32 : d == 2 ? 16 : d == 3 ? 8 : 4; }
 __host__ __device__ constexpr int ipow(int b, int e) {
     int r = 1;

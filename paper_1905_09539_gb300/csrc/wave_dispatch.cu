@@ -20,6 +20,7 @@ cudaError_t launch_wave(int d, bool gen, int prod, const WaveArgs& a, cudaStream
         case 7: return launch_wave_t<T, 3, true>(a, s);
         case 8: return launch_wave_t<T, 4, false>(a, s);
         case 9: return launch_wave_t<T, 4, true>(a, s);
+        case 10: return launch_wave_t<T, 5, false>(a, s);  // d = 5: the Laplace form only
         default: return cudaErrorInvalidValue;
     }
 }
@@ -33,7 +34,8 @@ cudaError_t prepare_wave() {
     if ((e = prepare_wave_t<T, 3, false>()) != cudaSuccess) return e;
     if ((e = prepare_wave_t<T, 3, true>()) != cudaSuccess) return e;
     if ((e = prepare_wave_t<T, 4, false>()) != cudaSuccess) return e;
-    return prepare_wave_t<T, 4, true>();
+    if ((e = prepare_wave_t<T, 4, true>()) != cudaSuccess) return e;
+    return prepare_wave_t<T, 5, false>();
 }
 
 template cudaError_t launch_wave<double>(int, bool, int, const WaveArgs&, cudaStream_t);

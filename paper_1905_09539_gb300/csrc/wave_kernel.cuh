@@ -38,8 +38,9 @@ struct WaveCfg {
     // resident CTAs per SM the persistent kernel is compiled for (register
     // budget): FP64 Laplace d = 3 6 (its shared memory allows 6, registers
     // alone would give 5), FP64 generalized 3 (shared-memory bound), FP32 5 / 4
-    static constexpr int MINB = sizeof(T) == 8 ? (GENF && D >= 2 ? (D == 3 ? 3 : 4) : (D == 3 ? 6 : 4))
-                                               : (GENF && D >= 2 ? 4 : 5);
+    static constexpr int MINB = D == 5 ? 3  // d = 5: 1024-entry blocks, shared memory allows 3 CTAs/SM
+                                : sizeof(T) == 8 ? (GENF && D >= 2 ? (D == 3 ? 3 : 4) : (D == 3 ? 6 : 4))
+                                                 : (GENF && D >= 2 ? 4 : 5);
     // The coupled-group inverses depend only on the diagonal blocks: they are
     // computed when the block starts, off the critical path, in a region of
     // their own (INV_EARLY), except for the FP64 Laplace form, whose shared
@@ -487,6 +488,7 @@ __device__ int warp_group(const TileSmem<T, D, GEN>& sm, int e, const T* minv) {
         case 2: return warp_group_solve<T, D, GEN, 4>(sm, a, mask, minv);
         case 3: if constexpr (D >= 3) return warp_group_solve<T, D, GEN, 8>(sm, a, mask, nullptr); else return 0;
         case 4: if constexpr (D >= 4) return warp_group_solve<T, D, GEN, 16>(sm, a, mask, nullptr); else return 0;
+        case 5: if constexpr (D >= 5) return warp_group_solve<T, D, GEN, 32>(sm, a, mask, nullptr); else return 0;
         default: return 0;
     }
 }

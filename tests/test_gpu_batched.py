@@ -219,3 +219,14 @@ def test_batch_fixed_tile_shape(lib, leaf, prec):
     tol = 1e-11 if prec == "fp64" else 1e-10
     for p, X in zip(ps, Xs):
         assert rel_err(to_host(X), oracle.solve_recursive(p["A"], p["B"], None, nmin=4)) <= tol
+
+
+def test_batch_with_d5_equations(lib):
+    """A batch mixing orders 3, 4 and 5 (the Laplace form; one persistent
+    launch per order): each equation against the oracle."""
+    shapes = [(12, 9, 10), (6, 5, 7, 6), (5, 4, 6, 5, 4), (9, 7, 5, 6, 4), (20, 13, 9)]
+    ps = [synthetic.problem([37, i], s, force_blocks=[[0] for _ in s]) for i, s in enumerate(shapes)]
+    Xs, st = lib.tsylv_solve_batched(_problems(ps, False))
+    assert all(s == 0 for s in st)
+    for p, X in zip(ps, Xs):
+        assert rel_err(to_host(X), oracle.solve_recursive(p["A"], p["B"], None, nmin=4)) <= 1e-11

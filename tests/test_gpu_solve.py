@@ -285,3 +285,54 @@ def test_wait_limit_option(lib, gen):
         assert st == 0
         out.append(X)
     assert torch.equal(out[0], out[1])
+
+
+def _force_d5(shape):
+    """A 2x2 block at the first index of every mode (a 32-member coupled group
+    in the corner block) and one across the first tile boundary."""
+    out = []
+    for n in shape:
+        f = [0]
+        if n > 5:
+            f.append(3)  # (3, 4) straddles the boundary at 4 of the 4-wide tiles
+        out.append(f)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32r", "tf32r"])
+@pytest.mark.parametrize("shape", [(4, 4, 4, 4, 4), (9, 7, 6, 5, 6), (13, 9, 8, 7, 6)])
+def test_d5_laplace_parity(lib, shape, prec):
+    """d = 5, the Laplace form (the order of the paper's merged-mode sweeps):
+    element by element against O-B, every precision."""
+    p = synthetic.problem(31, shape, force_blocks=_force_d5(shape))
+    Xo = oracle.solve_recursive(p["A"], p["B"], None, nmin=4)
+    prec_id = {"fp64": lib.TSYLV_FP64, "fp32r": lib.TSYLV_FP32_REFINED, "tf32r": lib.TSYLV_TF32_REFINED}[prec]
+    info = lib.Info()
+    X, st = lib.tsylv_solve([to_dev(a) for a in p["A"]], to_dev(p["B"]), precision=prec_id, max_refine=40,
+                            info=info)
+    assert st == 0
+    tol = TOL if prec == "fp64" else 1e-10
+    Xg = to_host(X)
+    assert rel_err(Xg, Xo) <= tol and max_rel(Xg, Xo) <= tol
+
+
+def test_d5_transposed_and_schedules(lib):
+    """d = 5: the transposed solve against O-A on A^T, and both block
+    schedules (persistent and wavefront) bit for bit."""
+    shape = (9, 8, 6, 5, 6)
+    p = synthetic.problem(32, shape, force_blocks=_force_d5(shape))
+    A = [to_dev(a) for a in p["A"]]
+    B = to_dev(p["B"])
+    Lo = oracle.solve_backsub(p["A"], p["B"], None, transpose=True)
+    L, st = lib.tsylv_solve_transposed(A, B)
+    assert st == 0 and rel_err(to_host(L), Lo) <= TOL
+    X0, _ = lib.tsylv_solve(A, B, schedule=0)
+    X1, _ = lib.tsylv_solve(A, B, schedule=1, split=1)
+    assert torch.equal(X0, X1)
+
+
+def test_d5_generalized_unsupported(lib):
+    from paper_1905_09539_gb300 import _lib
+    p = synthetic.problem(33, (4, 4, 4, 4, 4), generalized=True)
+    _, st = lib.gtsylv_solve([to_dev(a) for a in p["A"]], [to_dev(c) for c in p["C"]], to_dev(p["B"]), check=False)
+    assert st == _lib.TSYLV_EUNSUPPORTED

@@ -64,7 +64,7 @@ def test_argument_validation_without_gpu(lib):
     null2 = (P * 2)(None, None)
     # d out of range -> -1, before any CUDA call
     assert lib.tsylv_solve(0, n, null2, None, None, None, 0, ctypes.byref(o), None, None) == -1
-    assert lib.tsylv_solve(5, n, null2, None, None, None, 0, ctypes.byref(o), None, None) == -1
+    assert lib.tsylv_solve(6, n, null2, None, None, None, 0, ctypes.byref(o), None, None) == -1
     bad = (ctypes.c_int64 * 2)(4, -1)
     assert lib.tsylv_solve(2, bad, null2, None, None, None, 0, ctypes.byref(o), None, None) == -2
     assert lib.tsylv_solve(2, n, None, None, None, None, 0, ctypes.byref(o), None, None) == -3
@@ -122,7 +122,7 @@ def test_noalloc_option_validation_without_gpu(lib):
         assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
     bad = (ctypes.c_int64 * 2)(4, 0)
     assert lib.tsylv_solve_noalloc(2, bad, fake, P(16), P(16), None, None, None) == -2
-    assert lib.tsylv_solve_noalloc(5, n, fake, P(16), P(16), None, None, None) == -1
+    assert lib.tsylv_solve_noalloc(6, n, fake, P(16), P(16), None, None, None) == -1
     assert lib.tsylv_solve_noalloc(2, n, None, P(16), P(16), None, None, None) == -3
 
 
@@ -219,3 +219,16 @@ def test_batched_workspace_and_validation(lib):
     assert lib.tsylv_solve_batched(*args(X=None)) == -9
     assert lib.tsylv_solve_batched(*args(work=P(300))) == -10
     assert lib.tsylv_solve_batched(*args(wb=16)) == -11
+
+
+def test_generalized_d5_unsupported_without_gpu(lib):
+    """The generalized form is built for d <= 4: a d = 5 call returns
+    TSYLV_EUNSUPPORTED before any CUDA call (the Laplace form takes d = 5)."""
+    from paper_1905_09539_gb300 import _lib
+    n = (ctypes.c_int64 * 5)(4, 4, 4, 4, 4)
+    P = ctypes.c_void_p
+    fake = (P * 5)(16, 16, 16, 16, 16)
+    o = _lib.default_opts()
+    assert lib.gtsylv_solve(5, n, fake, fake, P(16), P(16), P(256), 1 << 30, ctypes.byref(o), None, None) == \
+        _lib.TSYLV_EUNSUPPORTED
+    assert lib.tsylv_workspace_bytes(5, n, 0, ctypes.byref(o)) > 4 ** 5 * 8

@@ -19,7 +19,7 @@ import oracle
 import synthetic
 from tests.kron_helpers import mode_product, operator, unvec, vec
 
-SHAPES = [(5,), (6, 5), (4, 5, 6), (3, 4, 3, 4)]
+SHAPES = [(5,), (6, 5), (4, 5, 6), (3, 4, 3, 4), (2, 3, 2, 3, 2)]
 
 
 def _prob(shape, gen, seed=0, force=None):
@@ -27,7 +27,7 @@ def _prob(shape, gen, seed=0, force=None):
 
 
 @pytest.mark.parametrize("gen", [False, True])
-@pytest.mark.parametrize("shape", [(7,), (6, 5), (5, 4, 6), (3, 4, 2, 5)])
+@pytest.mark.parametrize("shape", [(7,), (6, 5), (5, 4, 6), (3, 4, 2, 5), (3, 2, 4, 2, 3)])
 def test_closed_form_diagonal(shape, gen):
     rng = np.random.default_rng(1)
     a = [rng.uniform(1, 2, n) for n in shape]
@@ -68,7 +68,7 @@ def _split_points(n, nmin):
 
 
 @pytest.mark.parametrize("gen", [False, True])
-@pytest.mark.parametrize("shape", [(9,), (8, 7), (6, 6, 6), (4, 5, 6), (3, 4, 5, 6)])
+@pytest.mark.parametrize("shape", [(9,), (8, 7), (6, 6, 6), (4, 5, 6), (3, 4, 5, 6), (3, 4, 2, 3, 4)])
 def test_dense_assembled_solve(shape, gen):
     # 2x2 blocks placed across split points, so the recursion's k+1 guard is exercised
     force = []
@@ -230,7 +230,8 @@ def test_c_identity_reduces_to_laplace(shape):
 
 
 @pytest.mark.parametrize("gen", [False, True])
-@pytest.mark.parametrize("shape,nmins", [((20, 17, 15), (2, 5, 8, 20)), ((9, 8, 7, 6), (2, 3, 9))])
+@pytest.mark.parametrize("shape,nmins", [((20, 17, 15), (2, 5, 8, 20)), ((9, 8, 7, 6), (2, 3, 9)),
+                                         ((6, 5, 4, 5, 4), (2, 3, 6))])
 def test_routes_agree_and_residual(shape, nmins, gen):
     p = _prob(shape, gen, seed=11)
     A, C, B = p["A"], p["C"], p["B"]
