@@ -233,6 +233,30 @@ int gtsylv_solve_transposed(int d, const int64_t* n, const double* const* A,
                             size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
                             cudaStream_t stream);
 
+/* The paper's own generalized form, Sec. 3, Eq. (3.1):
+ *       X x_1 A_1 + X x_1 C x_2 A_2 x_3 ... x_d A_d = B,
+ * i.e. (I x ... x I x A_1 + A_d x ... x A_2 x C) vec(X) = vec(B) (Eq. (1.5)),
+ * with every A_mu upper quasi-triangular and C upper triangular (the form
+ * Alg. 4 reduces general coefficients to).  With A_1 = -lambda I it is the
+ * shifted Kronecker system of Eq. (1.6).  Solved by the recursion of
+ * Sec. 3.1 (Alg. 5; the merged base case of Alg. 6 solved directly): the
+ * same block partition and persistent schedule as tsylv_solve, the block
+ * updates being the A_1 term along mode 1 and the chain
+ * Q_l = X x_l A_l ... x_d A_d carried per block (Horner order over the modes,
+ * C in mode 1); 2x2 blocks of any A_mu are solved as coupled groups.
+ *   d      2..4 (1 and 5 return TSYLV_EUNSUPPORTED)
+ *   A      host array of d device pointers: A_1 .. A_d, n_mu x n_mu
+ *   C      device pointer: the n_1 x n_1 upper triangular C
+ *   B, X   as tsylv_solve (X may equal B); work of gsylvten_workspace_bytes
+ * Options: FP64 only (other precisions, opts->schedule = 1 and autotuning
+ * nmin = -1 return TSYLV_EUNSUPPORTED); nmin >= 2, leaf, split, partition,
+ * use_graph, timing, wait_ms as for tsylv_solve.  Arguments: 1 d, 2 n, 3 A,
+ * 4 C, 5 B, 6 X, 7 work, 8 work_bytes, 9 opts; statuses as tsylv_solve. */
+size_t gsylvten_workspace_bytes(int d, const int64_t* n, const tsylv_opts* opts);
+int gsylvten_solve(int d, const int64_t* n, const double* const* A, const double* C, const double* B,
+                   double* X, void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
+                   cudaStream_t stream);
+
 /* Workspace bytes for tsylv_residual. */
 size_t tsylv_residual_workspace_bytes(int d, const int64_t* n, int generalized);
 

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (TSYLV_BF16_REFINED, TSYLV_FP32_REFINED, TSYLV_FP64, TSYLV_RESID_DF64, TSYLV_RESID_FP64,
                    TSYLV_TF32_REFINED, Info, Opts, default_opts, load, status_string)
 
-__all__ = ["tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
+__all__ = ["tsylv_solve", "gtsylv_solve", "gsylvten_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
            "tsylv_residual", "tsylv_backward", "tsylv_solve_batched", "BatchPools", "solve", "fortran", "TsylvError",
            "Opts", "Info", "default_opts", "TSYLV_FP64", "TSYLV_FP32_REFINED", "TSYLV_TF32_REFINED",
            "TSYLV_BF16_REFINED", "TSYLV_RESID_DF64", "TSYLV_RESID_FP64", "workspace", "solve_general",
@@ -145,6 +145,33 @@ def gtsylv_solve(A, C, B, X=None, *, opts=None, check=True, stream=None, info=No
     lib = load()
     return _solve(lib.gtsylv_solve, lib.tsylv_workspace_bytes, True, False, A, C, B, X, opts, check, stream,
                   info, kw)
+
+
+def gsylvten_solve(A, C, B, X=None, *, opts=None, check=True, stream=None, info=None, **kw):
+    """X with X x_1 A_1 + X x_1 C x_2 A_2 ... x_d A_d = B (the paper's two-term
+    form, Eq. (3.1)); C is one n_1 x n_1 upper triangular matrix.  Returns (X, status)."""
+    lib = load()
+    _check_cuda(B, C, *A)
+    o = _opts(opts, kw)
+    B = fortran(B)
+    d = B.dim()
+    if X is None:
+        X = empty_fortran(B.shape, B.device)
+    elif not is_fortran(X) or X.dtype != torch.float64:
+        raise ValueError("X must be a float64 column-major tensor (see fortran())")
+    A_, pa = _mats(A)
+    C_ = fortran(C)
+    n = _dims(B.shape)
+    nbytes = lib.gsylvten_workspace_bytes(d, n, ctypes.byref(o))
+    if nbytes == 0:
+        raise ValueError("gsylvten_solve: invalid or unsupported shape %s (d = 2..4)" % (tuple(B.shape),))
+    work = workspace(nbytes, B.device)
+    inf = info if info is not None else Info()
+    st = lib.gsylvten_solve(d, n, pa, C_.data_ptr(), B.data_ptr(), X.data_ptr(), work.data_ptr(), work.numel(),
+                            ctypes.byref(o), ctypes.byref(inf), _stream(stream))
+    if check and st != 0:
+        raise TsylvError(st, "gsylvten_solve")
+    return X, st
 
 
 def tsylv_solve_transposed(A, G, L=None, *, opts=None, check=True, stream=None, info=None, **kw):

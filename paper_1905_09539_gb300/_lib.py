@@ -49,7 +49,7 @@ EXPORTS = [
     "tsylv_solve_transposed", "gtsylv_solve_transposed", "tsylv_residual", "tsylv_backward_workspace_bytes",
     "tsylv_backward", "tsylv_batched_workspace_bytes", "tsylv_solve_batched", "tsylv_last_error",
     "tsylv_solve_noalloc", "tsylv_residual_workspace_bytes", "tsylv_selftest_wait_timeout",
-    "tsylv_transform", "tsylv_transform_workspace_bytes",
+    "tsylv_transform", "tsylv_transform_workspace_bytes", "gsylvten_solve", "gsylvten_workspace_bytes",
 ]
 
 _lib = None
@@ -100,6 +100,10 @@ def load(path=LIB_PATH):
     lib.tsylv_transform_workspace_bytes.restype = S
     lib.tsylv_transform.argtypes = [I, I64P, P, ctypes.POINTER(I), P, P, P, S, P]
     lib.tsylv_transform.restype = I
+    lib.gsylvten_workspace_bytes.argtypes = [I, I64P, OP]
+    lib.gsylvten_workspace_bytes.restype = S
+    lib.gsylvten_solve.argtypes = [I, I64P, P, P, P, P, P, S, OP, IP, P]
+    lib.gsylvten_solve.restype = I
     for f in ("tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
               "tsylv_residual", "tsylv_backward", "tsylv_solve_batched"):
         getattr(lib, f).restype = I

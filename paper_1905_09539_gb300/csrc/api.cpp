@@ -90,6 +90,18 @@ extern "C" int gtsylv_solve_transposed(int d, const int64_t* n, const double* co
     return solver_solve(d, n, A, C, G, L, work, work_bytes, opts, info, stream, true, true);
 }
 
+extern "C" size_t gsylvten_workspace_bytes(int d, const int64_t* n, const tsylv_opts* opts) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    return solver_tt_workspace_bytes(d, n, o);
+}
+
+extern "C" int gsylvten_solve(int d, const int64_t* n, const double* const* A, const double* C, const double* B,
+                              double* X, void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
+                              cudaStream_t stream) {
+    return solver_solve_tt(d, n, A, C, B, X, work, work_bytes, opts, info, stream);
+}
+
 extern "C" size_t tsylv_transform_workspace_bytes(int d, const int64_t* n) { return transform_workspace_bytes(d, n); }
 
 extern "C" int tsylv_transform(int d, const int64_t* n, const double* const* M, const int* trans, const double* X,

@@ -65,6 +65,11 @@ template <typename T>
 cudaError_t launch_batched(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s, int prod = kProdNative);
 template <typename T>
 cudaError_t prepare_batched();
+// The paper's two-term form Eq. (3.1), FP64, d = 2..4: persistent launch,
+// its occupancy and kernel attributes.
+cudaError_t launch_batched_tt(int d, const BatchArgs& a, int grid, cudaStream_t s);
+int batched_occupancy_tt(int d);
+cudaError_t prepare_batched_tt();
 // *dst = a, by one thread (a captured launch keeps `a` by value).
 cudaError_t launch_store_args(const WaveArgs& a, WaveArgs* dst, cudaStream_t s);
 // Resident CTAs per SM of the persistent kernel.

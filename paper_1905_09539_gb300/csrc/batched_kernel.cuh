@@ -9,7 +9,7 @@
 
 namespace tsylv {
 
-template <typename T, int D, bool GENF, int PK = kProdNative>
+template <typename T, int D, int GENF, int PK = kProdNative>
 __global__ void __launch_bounds__(kThreads, WaveCfg<T, D, GENF>::MINB) k_batched(const BatchArgs b) {
     using C = WaveCfg<T, D, GENF>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -53,21 +53,21 @@ __global__ void __launch_bounds__(kThreads, WaveCfg<T, D, GENF>::MINB) k_batched
     }
 }
 
-template <typename T, int D, bool GEN, int PK = kProdNative>
+template <typename T, int D, int GEN, int PK = kProdNative>
 cudaError_t prepare_batched_t() {
     using C = WaveCfg<T, D, GEN>;
     return cudaFuncSetAttribute(k_batched<T, D, GEN, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(C::smem));
 }
 
-template <typename T, int D, bool GEN, int PK = kProdNative>
+template <typename T, int D, int GEN, int PK = kProdNative>
 cudaError_t launch_batched_t(const BatchArgs& a, int grid, cudaStream_t s) {
     using C = WaveCfg<T, D, GEN>;
     k_batched<T, D, GEN, PK><<<grid, kThreads, C::smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int D, bool GEN, int PK = kProdNative>
+template <typename T, int D, int GEN, int PK = kProdNative>
 int batched_occupancy_t() {
     using C = WaveCfg<T, D, GEN>;
     int nb = 0;

@@ -6,11 +6,11 @@
 
 namespace tsylv {
 
-template <typename T, int D, bool GEN, int PK = kProdNative>
+template <typename T, int D, int GEN, int PK = kProdNative>
 cudaError_t launch_batched_t(const BatchArgs& a, int grid, cudaStream_t s);
-template <typename T, int D, bool GEN, int PK = kProdNative>
+template <typename T, int D, int GEN, int PK = kProdNative>
 cudaError_t prepare_batched_t();
-template <typename T, int D, bool GEN, int PK = kProdNative>
+template <typename T, int D, int GEN, int PK = kProdNative>
 int batched_occupancy_t();
 
 namespace {
@@ -204,6 +204,31 @@ cudaError_t prepare_batched_pk() {
 }
 
 }  // namespace
+
+cudaError_t launch_batched_tt(int d, const BatchArgs& a, int grid, cudaStream_t s) {
+    switch (d) {
+        case 2: return launch_batched_t<double, 2, kFormTwoTerm>(a, grid, s);
+        case 3: return launch_batched_t<double, 3, kFormTwoTerm>(a, grid, s);
+        case 4: return launch_batched_t<double, 4, kFormTwoTerm>(a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int batched_occupancy_tt(int d) {
+    switch (d) {
+        case 2: return batched_occupancy_t<double, 2, kFormTwoTerm>();
+        case 3: return batched_occupancy_t<double, 3, kFormTwoTerm>();
+        case 4: return batched_occupancy_t<double, 4, kFormTwoTerm>();
+        default: return 1;
+    }
+}
+
+cudaError_t prepare_batched_tt() {
+    cudaError_t e;
+    if ((e = prepare_batched_t<double, 2, kFormTwoTerm>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<double, 3, kFormTwoTerm>()) != cudaSuccess) return e;
+    return prepare_batched_t<double, 4, kFormTwoTerm>();
+}
 
 template <typename T>
 cudaError_t launch_batched(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s, int prod) {

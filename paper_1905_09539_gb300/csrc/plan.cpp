@@ -107,7 +107,7 @@ Plan::~Plan() {
         if (e) cudaEventDestroy(e);
 }
 
-Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem, size_t tab_ints) {
+Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem, size_t tab_ints, bool tt) {
     Layout L;
     const int te = tile_extent(d);
     const size_t td = static_cast<size_t>(ipow(te, d)), tc = static_cast<size_t>(te) * te;
@@ -125,10 +125,11 @@ Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem,
     o = align256(o + tab_ints * sizeof(int));
     L.X = o;
     o = align256(o + ntiles * td * elem);
-    if (gen)
+    if (gen || tt)
         for (int l = 1; l < d; l++) {
             L.P[l] = o;
             o = align256(o + ntiles * td * elem);
+            if (tt) continue;
             L.G[l] = o;
             o = align256(o + ntiles * td * elem);
         }
@@ -136,7 +137,7 @@ Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem,
         const size_t ntri = static_cast<size_t>(nb[mu]) * (nb[mu] + 1) / 2;
         L.At[mu] = o;
         o = align256(o + ntri * tc * elem);
-        if (gen) {
+        if (gen || (tt && mu == 0)) {
             L.Ct[mu] = o;
             o = align256(o + ntri * tc * elem);
         }
@@ -169,7 +170,7 @@ void build_waves(Plan& p, int split) {
         for (int mu = 0; mu < d; mu++) {
             const int I = static_cast<int>((t / p.tstride[mu]) % p.nb[mu]);
             s += I;
-            const int w = p.gen && d >= 2 ? ((mu == 0 || mu == d - 1) ? 2 : 3) : 1;
+            const int w = p.tt ? (mu == 0 ? 2 : 1) : p.gen && d >= 2 ? ((mu == 0 || mu == d - 1) ? 2 : 3) : 1;
             c += static_cast<long long>(p.nb[mu] - 1 - I) * w;
         }
         by_s[s].push_back(static_cast<int>(t));
@@ -205,18 +206,20 @@ void build_waves(Plan& p, int split) {
     double f = 0;
     for (long long t = 0; t < p.ntiles; t++) f += cost[t] * unit;
     if (p.gen && d >= 2) f += p.ntiles * (3.0 * (d - 2) + 2) * unit;
+    if (p.tt) f += p.ntiles * (d - 1.0) * unit;  // the diagonal chain of the level sums
     double inblock = 0;
     for (int mu = 0; mu < d; mu++) inblock += (p.te - 1) / 2.0;
-    f += p.ntiles * p.td * 2.0 * inblock * (p.gen ? (3.0 * d - 2) : 1.0);
+    f += p.ntiles * p.td * 2.0 * inblock * (p.gen ? (3.0 * d - 2) : p.tt ? 1.0 + (d - 1.0) : 1.0);
     p.flops = f;
 }
 
 }  // namespace
 
 void fill_plan(Plan& p, int d, const long long* n, bool gen, int elem, int split, const std::vector<uint8_t>& sub,
-               int partition, int shape) {
+               int partition, int shape, bool tt) {
     p.d = d;
     p.shape = shape;
+    p.tt = tt && d >= 2;
     p.gen = gen && d >= 2;
     p.te = tile_extent(d);
     p.td = ipow(p.te, d);
@@ -248,7 +251,7 @@ void fill_plan(Plan& p, int d, const long long* n, bool gen, int elem, int split
     }
     p.t_wave = p.tab.size();
     p.tab.insert(p.tab.end(), p.wave_tiles.begin(), p.wave_tiles.end());
-    if (elem == 4 && !p.gen && d >= 2 && p.ntiles < (1LL << 26)) {
+    if (elem == 4 && !p.gen && !p.tt && d >= 2 && p.ntiles < (1LL << 26)) {
         // S1, R1, S2, R2 of anti-diagonal w at virtual times w, w + lag,
         // w + 2 lag, w + 3 lag: every job comes after the jobs it waits for
         p.t_rjobs = p.tab.size();
@@ -265,9 +268,9 @@ void fill_plan(Plan& p, int d, const long long* n, bool gen, int elem, int split
 }
 
 std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, int split,
-                               const std::vector<uint8_t>* sub, int partition, int shape) {
-    std::string key = std::to_string(d) + (gen ? "g" : "l") + std::to_string(elem) + "s" + std::to_string(split) +
-                      "p" + std::to_string(partition) + "t" + std::to_string(shape);
+                               const std::vector<uint8_t>* sub, int partition, int shape, bool tt) {
+    std::string key = std::to_string(d) + (tt ? "w" : gen ? "g" : "l") + std::to_string(elem) + "s" +
+                      std::to_string(split) + "p" + std::to_string(partition) + "t" + std::to_string(shape);
     size_t off = 0;
     for (int mu = 0; mu < d; mu++) {
         key += ":" + std::to_string(n[mu]) + ":";
@@ -278,7 +281,7 @@ std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, in
     auto it = g_plans.find(key);
     if (it != g_plans.end()) return it->second;
     auto p = std::make_shared<Plan>();
-    fill_plan(*p, d, n, gen, elem, split, *sub, partition, shape);
+    fill_plan(*p, d, n, gen, elem, split, *sub, partition, shape, tt);
     if (cudaMallocHost(&p->h_tab, p->tab.size() * sizeof(int)) != cudaSuccess) return nullptr;
     std::memcpy(p->h_tab, p->tab.data(), p->tab.size() * sizeof(int));
     g_plans[key] = p;

@@ -53,6 +53,7 @@ struct Plan {
     int d = 0, te = 0, td = 0, tc = 0;
     int shape = 0;                   // tile shape (leaf bound of every mode, shape_cut)
     bool gen = false;
+    bool tt = false;                 // the two-term form Eq. (3.1)
     int elem = 8;                    // bytes per block-tensor entry
     long long n[kMaxD] = {};
     Part part[kMaxD];
@@ -87,16 +88,17 @@ struct Layout {
     size_t total = 0;
 };
 
-Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem, size_t tab_ints);
+// tt: the two-term form (stored intermediates Q_l in P, C tiles of mode 1 only).
+Layout make_layout(int d, const long long* n, const int* nb, bool gen, int elem, size_t tab_ints, bool tt = false);
 
 // Schedule of one solve (partition, wavefronts, device tables) without the
 // pinned host copy of the tables and without caching.
 void fill_plan(Plan& p, int d, const long long* n, bool gen, int elem, int split, const std::vector<uint8_t>& sub,
-               int partition, int shape = 0);
+               int partition, int shape = 0, bool tt = false);
 
 // Cached schedule with a pinned copy of its tables (the source of a captured upload).
 std::shared_ptr<Plan> get_plan(int d, const long long* n, bool gen, int elem, int split,
-                               const std::vector<uint8_t>* sub, int partition, int shape = 0);
+                               const std::vector<uint8_t>* sub, int partition, int shape = 0, bool tt = false);
 
 GeomArgs geom_of(const Plan& p, const Layout& L, char* base, bool flip);
 

@@ -173,6 +173,7 @@ struct Call {
     bool update = false;      // refinement step: residual updated from the FP32 correction
     bool first = false;       // first refinement step (X = 0 before it: X after it is s D exactly)
     int prod = kProdNative;   // arithmetic of the FP32 solve's block updates (native / TF32 / BF16 tensor cores)
+    bool tt = false;          // the paper's two-term form Eq. (3.1): C[0] is its C (mode 1)
     long long timeout_ns = kTimeoutNs;  // bound of every device-side wait (opts->wait_ms)
     bool pipe = false;        // first two refinement steps pipelined in one launch (Laplace form)
     int pipe_grid = 0;
@@ -198,8 +199,8 @@ WaveArgs wave_args(const Plan& p, const Layout& L, char* base, long long timeout
         wa.tstride[mu] = p.tstride[mu];
         wa.bsize[mu] = tab + p.t_size[mu];
         wa.At[mu] = base + L.At[mu];
-        wa.Ct[mu] = p.gen ? base + L.Ct[mu] : nullptr;
-        wa.P[mu] = p.gen && mu >= 1 ? base + L.P[mu] : nullptr;
+        wa.Ct[mu] = p.gen || (p.tt && mu == 0) ? base + L.Ct[mu] : nullptr;
+        wa.P[mu] = (p.gen || p.tt) && mu >= 1 ? base + L.P[mu] : nullptr;
         wa.G[mu] = p.gen && mu >= 1 ? base + L.G[mu] : nullptr;
     }
     wa.X = base + L.X;
@@ -236,6 +237,7 @@ cudaError_t enqueue_waves(const Call& c, const Layout& L, cudaStream_t s) {
         ba.done = nullptr;
         ba.abort = ctl + 1;
         ba.timeout_ns = c.timeout_ns;
+        if (p.tt) return launch_batched_tt(p.d, ba, c.flow_grid, s);
         return launch_batched<T>(p.d, p.gen, ba, c.flow_grid, s, sizeof(T) == 4 ? c.prod : kProdNative);
     }
     for (size_t w = 0; w < p.wave_off.size(); w++) {
@@ -261,6 +263,29 @@ cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
         TRY(launch_pack_coef<double>(g, mu, c.A[mu], reinterpret_cast<double*>(base + L.At[mu]), false, s));
         if (p.gen) TRY(launch_pack_coef<double>(g, mu, c.C[mu], reinterpret_cast<double*>(base + L.Ct[mu]), true, s));
     }
+    double* Xt = reinterpret_cast<double*>(base + L.X);
+    TRY(launch_pack_tensor<double>(g, c.B, Xt, 1.0, s));
+    TRY(mark(c, 1, s));
+    TRY(enqueue_waves<double>(c, L, s));
+    TRY(mark(c, 2, s));
+    TRY(launch_unpack_tensor<double>(g, Xt, c.X, s));
+    return mark(c, 3, s);
+}
+
+// The paper's two-term form Eq. (3.1), FP64: A_mu tiles of every mode (the
+// A_1 term and the chain factors A_2 .. A_d), C tiles of mode 1, the
+// persistent solve (the two-term form of the block kernel).
+cudaError_t enqueue_tt(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    const Layout& L = c.L;
+    char* base = c.base;
+    GeomArgs g = geom_of(p, L, base, false);
+    TRY(mark(c, 0, s));
+    TRY(cudaMemsetAsync(base + L.err, 0, 64, s));
+    TRY(cudaMemcpyAsync(base + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int mu = 0; mu < p.d; mu++)
+        TRY(launch_pack_coef<double>(g, mu, c.A[mu], reinterpret_cast<double*>(base + L.At[mu]), false, s));
+    TRY(launch_pack_coef<double>(g, 0, c.C[0], reinterpret_cast<double*>(base + L.Ct[0]), true, s));
     double* Xt = reinterpret_cast<double*>(base + L.X);
     TRY(launch_pack_tensor<double>(g, c.B, Xt, 1.0, s));
     TRY(mark(c, 1, s));
@@ -703,6 +728,7 @@ int prepare_kernels() {
         if (e == cudaSuccess) e = prepare_apply_dfh();
         if (e == cudaSuccess) e = prepare_batched<double>();
         if (e == cudaSuccess) e = prepare_batched<float>();
+        if (e == cudaSuccess) e = prepare_batched_tt();
         if (e == cudaSuccess) e = prepare_refine2();
         if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
         prepared[dev] = true;
@@ -1164,6 +1190,112 @@ int solve_body(int d, const int64_t* n, const double* const* A, const double* co
     if (ms == TSYLV_ETIMEOUT || ms == TSYLV_ECUDA) return ms;
     if (status == TSYLV_OK && ms == TSYLV_ESINGULAR) return ms;
     return status;
+}
+
+size_t solver_tt_workspace_bytes(int d, const int64_t* n, const tsylv_opts& o) {
+    if (!shape_ok(d, n) || d < 2 || d > 4) return 0;
+    long long nn[kMaxD];
+    int nb[kMaxD];
+    const int shape = shape_of_opts(o, d);
+    for (int mu = 0; mu < d; mu++) {
+        nn[mu] = n[mu];
+        nb[mu] = max_blocks(static_cast<int>(n[mu]), shape_min_cut(d, mu, shape < 0 ? 0 : shape));
+    }
+    return make_layout(d, nn, nb, false, 8, tab_ints_bound(d, nn, nb), true).total;
+}
+
+// The paper's own generalized form Eq. (3.1): X x_1 A_1 + X x_1 C x_2 A_2
+// ... x_d A_d = B, A_mu upper quasi-triangular, C upper triangular; the
+// recursion of Sec. 3.1 as the block schedule of the other forms.  FP64,
+// persistent schedule, d = 2..4.
+int solver_solve_tt(int d, const int64_t* n, const double* const* A, const double* Cm, const double* B, double* X,
+                    void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    if (d < 1 || d > kMaxD) return -1;
+    if (!shape_ok(d, n)) return -2;
+    if (!A) return -3;
+    for (int mu = 0; mu < d; mu++)
+        if (!A[mu]) return -3;
+    if (!Cm) return -4;
+    if (!B) return -5;
+    if (!X) return -6;
+    if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -7;
+    if (d < 2 || d > 4) return TSYLV_EUNSUPPORTED;
+    if (work_bytes < solver_tt_workspace_bytes(d, n, o)) return -8;
+    if (int st = check_opts(o, d)) return st < 0 ? -9 : st;
+    if (o.precision != TSYLV_FP64 || o.schedule != 0 || o.nmin < 0) return TSYLV_EUNSUPPORTED;
+    const int shape = shape_of_opts(o, d);
+    Call c;
+    c.d = d;
+    c.gen = false;
+    c.tt = true;
+    c.timeout_ns = static_cast<long long>(o.wait_ms) * 1000000LL;
+    for (int mu = 0; mu < d; mu++) {
+        c.n[mu] = n[mu];
+        c.A[mu] = A[mu];
+    }
+    c.C[0] = Cm;
+    c.B = B;
+    c.X = X;
+    c.base = static_cast<char*>(work);
+    (void)cudaGetLastError();
+    std::vector<uint8_t> sub;
+    if (int st = read_structure(d, c.n, c.A, c.base, false, stream, sub)) return st;
+    c.plan = get_plan(d, c.n, false, 8, o.split, &sub, o.partition, shape, true);
+    if (!c.plan) return cuda_fail_msg("plan: pinned host allocation");
+    if (int st = prepare_kernels()) return st;
+    c.timing = o.timing != 0;
+    if (int st = ensure_events(c)) return st;
+    c.persistent = true;
+    {
+        static std::mutex m;
+        static std::map<int, int> occ;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        int slots = 0;
+        {
+            std::lock_guard<std::mutex> lk(m);
+            auto it = occ.find(dev * 8 + d);
+            if (it != occ.end()) {
+                slots = it->second;
+            } else {
+                int sms = 0;
+                if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+                slots = sms * batched_occupancy_tt(d);
+                occ[dev * 8 + d] = slots;
+            }
+        }
+        c.flow_grid = static_cast<int>(c.plan->ntiles < slots ? c.plan->ntiles : slots);
+    }
+    c.L = make_layout(d, c.n, c.plan->nb, false, 8, c.plan->tab.size(), true);
+    if (c.L.total > work_bytes) return -8;
+    const int tag = 8192 * 4 | (c.timing ? 2 : 0);
+    if (int st = run_enqueue(*c.plan, make_key(c, tag), o.use_graph != 0, stream, enqueue_tt, c)) return st;
+    int herr = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&herr, c.base + c.L.err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_fail(e, "read status");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize after solve");
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->waves = static_cast<int>(c.plan->wave_off.size());
+        info->launches = 2 + d + 1 + 2;
+        info->tiles = static_cast<int>(c.plan->ntiles);
+        for (int mu = 0; mu < d; mu++) info->leaf[mu] = shape_cut(d, mu, shape);
+        info->resid = -1;
+        info->norm_A = -1;
+        info->flops = c.plan->flops;
+        if (c.timing) {
+            float a = -1, b = -1;
+            if (cudaEventElapsedTime(&a, c.plan->ev[0], c.plan->ev[3]) != cudaSuccess) a = -1;
+            if (cudaEventElapsedTime(&b, c.plan->ev[1], c.plan->ev[2]) != cudaSuccess) b = -1;
+            (void)cudaGetLastError();
+            info->t_total_ms = a;
+            info->t_waves_ms = b;
+        }
+    }
+    return map_err(herr);
 }
 
 // The failure path of the persistent schedule, exercised on purpose: the

@@ -43,6 +43,10 @@ int cuda_fail_msg(const char* where);
 // Device-side error bits (OR-ed into the workspace status word).
 enum : int { kErrSingular = 1, kErrNonfinite = 2, kErrTimeout = 4, kErrBounds = 8 };
 
+// Forms of the equation (the block kernels' form parameter): Eq. (2.2), the
+// d-term generalized form, and the paper's two-term form Eq. (3.1).
+enum : int { kFormLaplace = 0, kFormDTerm = 1, kFormTwoTerm = 2 };
+
 // Arithmetic used for the block products of a wavefront.
 enum ProductKind : int { kProdNative = 0, kProdTF32 = 1, kProdBF16 = 2 };
 

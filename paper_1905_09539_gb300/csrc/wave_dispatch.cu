@@ -3,9 +3,9 @@
 
 namespace tsylv {
 
-template <typename T, int D, bool GEN>
+template <typename T, int D, int GEN>
 cudaError_t launch_wave_t(const WaveArgs& a, cudaStream_t s);
-template <typename T, int D, bool GEN>
+template <typename T, int D, int GEN>
 cudaError_t prepare_wave_t();
 
 template <typename T>

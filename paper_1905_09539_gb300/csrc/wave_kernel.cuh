@@ -21,15 +21,21 @@
 
 namespace tsylv {
 
-template <typename T, int D, bool GENF>
+// Forms (kForm*, tsylv_internal.h): the two-term form Eq. (3.1) is
+// X x_1 A_1 + X x_1 C x_2 A_2 ... x_d A_d.
+template <typename T, int D, int FM>
 struct WaveCfg {
     static constexpr int TE = tile_extent(D);
     static constexpr int TD = ipow(TE, D);
     static constexpr int TC = TE * TE;
     static constexpr int EPT = (TD + kThreads - 1) / kThreads;
-    static constexpr bool GEN = GENF && D >= 2;
-    static constexpr int NACC = GEN ? 2 * (D - 1) + 1 : 1;
-    static constexpr int NL = GEN ? D - 1 : 0;  // stored levels l = 1..d-1
+    static constexpr bool GEN = FM == kFormDTerm && D >= 2;
+    static constexpr bool TT = FM == kFormTwoTerm && D >= 2;
+    static constexpr bool CHAIN = GEN || TT;  // Horner chain over the modes, stored intermediates
+    // accumulator slots: Laplace one; d-term P_l, G_l (l = d-1..1) and the
+    // mode-1 level; two-term Q_l (l = d-1..1, slot d-1-l) and the mode-1 level
+    static constexpr int NACC = GEN ? 2 * (D - 1) + 1 : TT ? D : 1;
+    static constexpr int NL = CHAIN ? D - 1 : 0;  // stored levels l = 1..d-1
     static constexpr int STAGE = 2 * TD + 2 * TC;
     // stages of the bulk-copy ring: the FP64 updates are bound by the FP64
     // pipes, the FP32 ones by the copy latency (4 stages measured a little
@@ -39,8 +45,8 @@ struct WaveCfg {
     // budget): FP64 Laplace d = 3 6 (its shared memory allows 6, registers
     // alone would give 5), FP64 generalized 3 (shared-memory bound), FP32 5 / 4
     static constexpr int MINB = D == 5 ? 3  // d = 5: 1024-entry blocks, shared memory allows 3 CTAs/SM
-                                : sizeof(T) == 8 ? (GENF && D >= 2 ? (D == 3 ? 3 : 4) : (D == 3 ? 6 : 4))
-                                                 : (GENF && D >= 2 ? 4 : 5);
+                                : sizeof(T) == 8 ? (CHAIN ? (D == 3 ? 3 : 4) : (D == 3 ? 6 : 4))
+                                                 : (CHAIN ? 4 : 5);
     // The coupled-group inverses depend only on the diagonal blocks: they are
     // computed when the block starts, off the critical path, in a region of
     // their own (INV_EARLY), except for the FP64 Laplace form, whose shared
@@ -52,8 +58,8 @@ struct WaveCfg {
     // level sums are parked in the output P, G blocks meanwhile), and the
     // reciprocal diagonal of a 1x1 group sits in its not yet solved X entry.
     static constexpr int MINV = 1024;  // budget (entries) for precomputed coupled-group inverses
-    static constexpr bool INV_EARLY = D >= 2 && !(sizeof(T) == 8 && !GEN);
-    static constexpr bool PIN_IN_RING = GEN && sizeof(T) == 8 && 2 * NL * TD <= NST * STAGE;
+    static constexpr bool INV_EARLY = D >= 2 && !(sizeof(T) == 8 && !CHAIN);
+    static constexpr bool PIN_IN_RING = CHAIN && sizeof(T) == 8 && 2 * NL * TD <= NST * STAGE;
     static constexpr int UNION = (NST * STAGE > MINV || INV_EARLY) ? NST * STAGE : MINV;
     static constexpr int oStage = 0;
     static constexpr int oRed = UNION;
@@ -65,8 +71,8 @@ struct WaveCfg {
     static constexpr int oGin = oPin + NL * TD;
     static constexpr int oD = PIN_IN_RING ? oX + TD : oGin + NL * TD;
     static constexpr int oE = oD + D * TC;
-    static constexpr int oMinv = INV_EARLY ? oE + (GEN ? D * TC : 0) : 0;
-    static constexpr int oEnd = INV_EARLY ? oMinv + MINV : oE + (GEN ? D * TC : 0);
+    static constexpr int oMinv = INV_EARLY ? oE + (CHAIN ? D * TC : 0) : 0;
+    static constexpr int oEnd = INV_EARLY ? oMinv + MINV : oE + (CHAIN ? D * TC : 0);
     static constexpr size_t oBar = ((oEnd * sizeof(T)) + 15) / 16 * 16;
     static constexpr size_t oMeta = oBar + ((8 * NST + 15) / 16) * 16;
     // meta: gs, gl, gidx [D][TE]; ng, bs [D]; flag [4]; coupled-group lists
@@ -77,7 +83,7 @@ struct WaveCfg {
     // first JT jobs of a block, filled by all threads at once
     static constexpr int JT = kThreads;
     static constexpr size_t smem = oJob + (JT + JT / 32) * sizeof(int);
-    static constexpr int slotP(int l) { return 2 * (D - 1 - l); }
+    static constexpr int slotP(int l) { return TT ? D - 1 - l : 2 * (D - 1 - l); }
     static constexpr int slotG(int l) { return 2 * (D - 1 - l) + 1; }
 };
 
@@ -125,18 +131,28 @@ __device__ __forceinline__ void prod_acc2(T (&acc)[EPT], const T* __restrict__ M
 }
 
 // Compile-time dispatch of one block-update job of level L.
-template <typename T, int D, bool GEN, int L>
+template <typename T, int D, int FM, int L>
 struct JobCompute {
     template <int NACC, int EPT>
     __device__ __forceinline__ static void run(T (&acc)[NACC][EPT], const T* stage) {
         constexpr int TE = tile_extent(D);
         constexpr int TD = ipow(TE, D);
         constexpr int TC = TE * TE;
+        using C = WaveCfg<T, D, FM>;
         const T* S1 = stage;
         const T* S2 = stage + TD;
         const T* M1 = stage + 2 * TD;
         const T* M2 = stage + 2 * TD + TC;
-        if constexpr (!GEN) {
+        if constexpr (C::TT) {
+            constexpr int MU = D - 1 - L;            // modes d-1, ..., 0
+            if constexpr (MU >= 1) {
+                // L^Q_mu += Q_{mu+1} x A_mu  (Q_d = X)
+                prod_acc<T, D, MU, EPT>(acc[L], M1, S1);
+            } else {
+                // L_0 += Q_1 x C + X x A_1
+                prod_acc2<T, D, 0, EPT>(acc[NACC - 1], M1, S2, M2, S1);
+            }
+        } else if constexpr (!C::GEN) {
             prod_acc<T, D, L, EPT>(acc[0], M1, S1);  // Laplace: level L = mode L
         } else {
             constexpr int MU = D - 1 - L;            // modes d-1, ..., 0
@@ -156,14 +172,14 @@ struct JobCompute {
     }
 };
 
-template <typename T, int D, bool GEN, int L = 0>
-__device__ __forceinline__ void dispatch_job(int level, T (&acc)[WaveCfg<T, D, GEN>::NACC][WaveCfg<T, D, GEN>::EPT],
+template <typename T, int D, int FM, int L = 0>
+__device__ __forceinline__ void dispatch_job(int level, T (&acc)[WaveCfg<T, D, FM>::NACC][WaveCfg<T, D, FM>::EPT],
                                              const T* stage) {
     if constexpr (L < D) {
         if (level == L)
-            JobCompute<T, D, WaveCfg<T, D, GEN>::GEN, L>::run(acc, stage);
+            JobCompute<T, D, FM, L>::run(acc, stage);
         else
-            dispatch_job<T, D, GEN, L + 1>(level, acc, stage);
+            dispatch_job<T, D, FM, L + 1>(level, acc, stage);
     }
 }
 
@@ -188,10 +204,11 @@ struct ElemCode {
     __device__ static int k0(int c, int mu) { return (c >> (13 + KB * mu)) & ((1 << KB) - 1); }
 };
 
-template <typename T, int D, bool GEN>
+template <typename T, int D, int FM>
 struct TileSmem {
     const T* Ds;   // [D][TC] diagonal tiles of A
-    const T* Es;   // [D][TC] diagonal tiles of C (generalized)
+    const T* Es;   // [D][TC] diagonal tiles of C (d-term form) / of the chain factor
+                   // (two-term form: C in mode 1, A_mu in the others)
     const T* Rs;   // right-hand side of the diagonal-block equation
     const T* Rd;   // reciprocal of the diagonal entry of every 1x1 group
     T* Xs;         // solution (0 where not yet solved)
@@ -209,15 +226,38 @@ struct TileSmem {
 // groups are already in the running line sums Lin, so the solve is the
 // Horner chain over the diagonal entries (generalized form) and one product
 // with the reciprocal diagonal.
-template <typename T, int D, bool GEN>
-__device__ __forceinline__ int solve_single(const TileSmem<T, D, GEN>& sm, int o, const int (&u)[D],
-                                            const T (&L)[WaveCfg<T, D, GEN>::NACC]) {
+template <typename T, int D, int FM>
+__device__ __forceinline__ int solve_single(const TileSmem<T, D, FM>& sm, int o, const int (&u)[D],
+                                            const T (&L)[WaveCfg<T, D, FM>::NACC]) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int TC = TE * TE;
-    using C = WaveCfg<T, D, GEN>;
+    using C = WaveCfg<T, D, FM>;
     T x;
-    if constexpr (!GEN) {
+    if constexpr (C::TT) {
+        // Horner chain of the line sums through the own diagonal entries of the
+        // chain factors: Q_l(u) = e_l Q_{l+1}(u) + L_l, Q_d = x; then
+        // a_1 x + c Q_1(u) + L_0 = r
+        T p0 = L[C::slotP(D - 1)];
+        T P0s[D];
+        P0s[D - 1] = p0;
+#pragma unroll
+        for (int l = D - 2; l >= 1; l--) {
+            p0 = dev::fmadd(sm.Es[l * TC + u[l] * (TE + 1)], p0, L[C::slotP(l)]);
+            P0s[l] = p0;
+        }
+        const T off = dev::fmadd(sm.Es[u[0] * (TE + 1)], p0, L[C::NACC - 1]);
+        x = (sm.Rs[o] - off) * sm.Rd[o];
+        const T e1 = sm.Es[(D - 1) * TC + u[D - 1] * (TE + 1)];
+        T pc = e1 * x;
+        sm.Pin[(D - 2) * TD + o] = dev::fmadd(e1, x, P0s[D - 1]);
+#pragma unroll
+        for (int l = D - 2; l >= 1; l--) {
+            const T ep = sm.Es[l * TC + u[l] * (TE + 1)];
+            sm.Pin[(l - 1) * TD + o] = dev::fmadd(ep, pc, P0s[l]);
+            pc = ep * pc;
+        }
+    } else if constexpr (!C::GEN) {
         x = (sm.Rs[o] - L[0]) * sm.Rd[o];
     } else {
         T p0 = L[C::slotP(D - 1)];
@@ -269,12 +309,13 @@ __device__ __forceinline__ int member_with(int mask, int m, int mu, int k) {
     return (m & ~(1 << b)) | (k << b);
 }
 
-template <typename T, int D, bool GEN, int S>
-__device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D], int mask, const T* minv) {
+template <typename T, int D, int FM, int S>
+__device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D], int mask, const T* minv) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int TC = TE * TE;
-    using C = WaveCfg<T, D, GEN>;
+    using C = WaveCfg<T, D, FM>;
+    constexpr bool GEN = C::GEN;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const bool act = lane < S;
@@ -290,7 +331,47 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
     T r;
     T row[S];
     T P0[D], G0[D];
-    if constexpr (!GEN) {
+    if constexpr (C::TT) {
+        // chain of the line sums through the group's diagonal blocks (other
+        // members along each 2x2 mode), then the mode-1 level: c Q_1 + L_0
+        P0[D - 1] = sm.Lin[C::slotP(D - 1) * TD + o];
+#pragma unroll
+        for (int l = D - 2; l >= 1; l--) {
+            T p = sm.Lin[C::slotP(l) * TD + o];
+            const bool two = (mask >> l) & 1;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int src = member_with(mask, m, l, k);
+                const T pp = __shfl_sync(full, P0[l + 1], src);
+                if (k == 0 || two) p = dev::fmadd(Em(l, u[l], two ? a[l] + k : u[l]), pp, p);
+            }
+            P0[l] = p;
+        }
+        T of = sm.Lin[(C::NACC - 1) * TD + o];
+        {
+            const bool two = mask & 1;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int src = member_with(mask, m, 0, k);
+                const T pp = __shfl_sync(full, P0[1], src);
+                if (k == 0 || two) of = dev::fmadd(Em(0, u[0], two ? a[0] + k : u[0]), pp, of);
+            }
+        }
+        r = sm.Rs[o] - of;
+        // group system: A_1 (identity in the other modes) + C x A_2 x ... x A_d
+#pragma unroll
+        for (int k = 0; k < S; k++) {
+            if (minv != nullptr) { row[k] = 0; continue; }
+            bool same = true;
+#pragma unroll
+            for (int eta = 1; eta < D; eta++)
+                if (member_delta(mask, m, eta) != member_delta(mask, k, eta)) same = false;
+            T t = Em(0, u[0], a[0] + member_delta(mask, k, 0));
+#pragma unroll
+            for (int eta = 1; eta < D; eta++) t *= Em(eta, u[eta], a[eta] + member_delta(mask, k, eta));
+            row[k] = same ? Dm(0, u[0], a[0] + member_delta(mask, k, 0)) + t : t;
+        }
+    } else if constexpr (!GEN) {
         r = sm.Rs[o] - sm.Lin[o];
 #pragma unroll
         for (int k = 0; k < S; k++) {
@@ -423,6 +504,36 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
         if (!isfinite(x)) status |= kErrNonfinite;
         sm.Xs[o] = x;
     }
+    if constexpr (C::TT) {
+        // completion of the in-block intermediates Q_l at the group positions
+        T pc[D];
+        {
+            constexpr int mu = D - 1;
+            const bool two = (mask >> mu) & 1;
+            T p = 0;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const T xv = __shfl_sync(full, x, member_with(mask, m, mu, k));
+                if (k == 0 || two) p = dev::fmadd(Em(mu, u[mu], two ? a[mu] + k : u[mu]), xv, p);
+            }
+            pc[mu] = p;
+        }
+#pragma unroll
+        for (int l = D - 2; l >= 1; l--) {
+            const bool two = (mask >> l) & 1;
+            T p = 0;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const T pp = __shfl_sync(full, pc[l + 1], member_with(mask, m, l, k));
+                if (k == 0 || two) p = dev::fmadd(Em(l, u[l], two ? a[l] + k : u[l]), pp, p);
+            }
+            pc[l] = p;
+        }
+        if (act) {
+#pragma unroll
+            for (int l = 1; l < D; l++) sm.Pin[(l - 1) * TD + o] = P0[l] + pc[l];
+        }
+    }
     if constexpr (GEN) {
         // completion of the in-block intermediates at the group positions
         T pc[D], gc[D];
@@ -472,8 +583,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, GEN>& sm, const int (&a)[D]
 }
 
 // Warp-uniform entry: the group whose first member is the in-block element e.
-template <typename T, int D, bool GEN>
-__device__ int warp_group(const TileSmem<T, D, GEN>& sm, int e, const T* minv) {
+template <typename T, int D, int FM>
+__device__ int warp_group(const TileSmem<T, D, FM>& sm, int e, const T* minv) {
     constexpr int TE = tile_extent(D);
     int a[D], mask = 0, rem = e;
 #pragma unroll
@@ -484,11 +595,11 @@ __device__ int warp_group(const TileSmem<T, D, GEN>& sm, int e, const T* minv) {
         if (sm.gl[mu * TE + gi] == 2) mask |= 1 << mu;
     }
     switch (__popc(mask)) {
-        case 1: return warp_group_solve<T, D, GEN, 2>(sm, a, mask, minv);
-        case 2: return warp_group_solve<T, D, GEN, 4>(sm, a, mask, minv);
-        case 3: if constexpr (D >= 3) return warp_group_solve<T, D, GEN, 8>(sm, a, mask, nullptr); else return 0;
-        case 4: if constexpr (D >= 4) return warp_group_solve<T, D, GEN, 16>(sm, a, mask, nullptr); else return 0;
-        case 5: if constexpr (D >= 5) return warp_group_solve<T, D, GEN, 32>(sm, a, mask, nullptr); else return 0;
+        case 1: return warp_group_solve<T, D, FM, 2>(sm, a, mask, minv);
+        case 2: return warp_group_solve<T, D, FM, 4>(sm, a, mask, minv);
+        case 3: if constexpr (D >= 3) return warp_group_solve<T, D, FM, 8>(sm, a, mask, nullptr); else return 0;
+        case 4: if constexpr (D >= 4) return warp_group_solve<T, D, FM, 16>(sm, a, mask, nullptr); else return 0;
+        case 5: if constexpr (D >= 5) return warp_group_solve<T, D, FM, 32>(sm, a, mask, nullptr); else return 0;
         default: return 0;
     }
 }
@@ -499,13 +610,14 @@ __device__ int warp_group(const TileSmem<T, D, GEN>& sm, int e, const T* minv) {
 // the Laplace form; X, P_{l+1}, G_{l+1} for the levels of the generalized
 // recurrence).  The modes are independent and each sum runs as two
 // interleaved chains, so the latency is that of a few multiply-adds.
-template <typename T, int D, bool GEN>
-__device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e, const int (&u)[D], const int (&k0s)[D],
-                                           T (&L)[WaveCfg<T, D, GEN>::NACC]) {
+template <typename T, int D, int FM>
+__device__ __forceinline__ void pull_lines(const TileSmem<T, D, FM>& sm, int e, const int (&u)[D], const int (&k0s)[D],
+                                           T (&L)[WaveCfg<T, D, FM>::NACC]) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int TC = TE * TE;
-    using C = WaveCfg<T, D, GEN>;
+    using C = WaveCfg<T, D, FM>;
+    constexpr bool GEN = C::GEN;
     const T* __restrict__ Xs = sm.Xs;
     T lap[D];
 #pragma unroll
@@ -526,7 +638,22 @@ __device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e,
             const int v = in ? e + (k - u[mu]) * st : e;
             const T dv = in ? sm.Ds[mu * TC + u[mu] + TE * k] : T(0);
             const bool odd = k & 1;
-            if constexpr (!GEN) {
+            if constexpr (C::TT) {
+                // chain factor (C in mode 1, A_mu elsewhere) on X (mode d) or
+                // on Q_{mu+1}; mode 1 also carries A_1 on X
+                const T ev = in ? sm.Es[mu * TC + u[mu] + TE * k] : T(0);
+                if (mu == D - 1) {
+                    const T xv = in ? Xs[v] : T(0);
+                    if (odd) a1 = dev::fmadd(ev, xv, a1); else a0 = dev::fmadd(ev, xv, a0);
+                } else if (mu >= 1) {
+                    const T pv = in ? sm.Pin[mu * TD + v] : T(0);  // level mu + 1
+                    if (odd) a1 = dev::fmadd(ev, pv, a1); else a0 = dev::fmadd(ev, pv, a0);
+                } else {
+                    const T pv = in ? sm.Pin[v] : T(0), xv = in ? Xs[v] : T(0);  // level 1
+                    if (odd) { a1 = dev::fmadd(ev, pv, a1); b1 = dev::fmadd(dv, xv, b1); }
+                    else { a0 = dev::fmadd(ev, pv, a0); b0 = dev::fmadd(dv, xv, b0); }
+                }
+            } else if constexpr (!GEN) {
                 const T xv = in ? Xs[v] : T(0);
                 if (odd) a1 = dev::fmadd(dv, xv, a1); else a0 = dev::fmadd(dv, xv, a0);
             } else {
@@ -546,7 +673,10 @@ __device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e,
                 }
             }
         }
-        if constexpr (!GEN) {
+        if constexpr (C::TT) {
+            if (mu >= 1) L[C::slotP(mu)] = a0 + a1;
+            else L[C::NACC - 1] = (a0 + a1) + (b0 + b1);
+        } else if constexpr (!GEN) {
             lap[mu] = a0 + a1;
         } else {
             if (mu == D - 1) {
@@ -560,7 +690,7 @@ __device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e,
             }
         }
     }
-    if constexpr (!GEN) {
+    if constexpr (!GEN && !C::TT) {
         T sum = lap[0];
 #pragma unroll
         for (int mu = 1; mu < D; mu++) sum += lap[mu];
@@ -571,10 +701,24 @@ __device__ __forceinline__ void pull_lines(const TileSmem<T, D, GEN>& sm, int e,
 // Entry (m, k) of the system of a coupled group with first element a and 2x2
 // modes `mask`: the operator restricted to the group (Laplace: the Kronecker
 // sum of the diagonal blocks; generalized: sum_mu A_mu x prod_{eta!=mu} C_eta).
-template <typename T, int D, bool GEN>
-__device__ __forceinline__ T group_entry(const TileSmem<T, D, GEN>& sm, const int (&a)[D], int mask, int m, int k) {
+template <typename T, int D, int FM>
+__device__ __forceinline__ T group_entry(const TileSmem<T, D, FM>& sm, const int (&a)[D], int mask, int m, int k) {
     constexpr int TE = tile_extent(D);
     constexpr int TC = TE * TE;
+    constexpr bool GEN = WaveCfg<T, D, FM>::GEN;
+    if constexpr (WaveCfg<T, D, FM>::TT) {
+        // A_1 (identity in the other modes) + C x A_2 x ... x A_d on the group
+        bool same = true;
+        T t = 1;
+#pragma unroll
+        for (int mu = 0; mu < D; mu++) {
+            const int i = a[mu] + member_delta(mask, m, mu), j = a[mu] + member_delta(mask, k, mu);
+            t *= sm.Es[mu * TC + i + TE * j];
+            if (mu >= 1 && i != j) same = false;
+        }
+        const int i0 = a[0] + member_delta(mask, m, 0), j0 = a[0] + member_delta(mask, k, 0);
+        return same ? sm.Ds[i0 + TE * j0] + t : t;
+    }
     T e = 0;
 #pragma unroll
     for (int mu = 0; mu < D; mu++) {
@@ -595,7 +739,7 @@ __device__ __forceinline__ T group_entry(const TileSmem<T, D, GEN>& sm, const in
 // Inverse of a coupled group's system (S x S, row-major into out), by
 // Gauss-Jordan elimination with partial pivoting.  Returns kErrSingular for a
 // pivot below 16 eps max|M|.
-template <typename T, int D, bool GEN, int S>
+template <typename T, int D, int GEN, int S>
 __device__ int group_inverse_s(const TileSmem<T, D, GEN>& sm, const int (&a)[D], int mask, T* out) {
     T W[S][2 * S];
     T big = 0;
@@ -640,7 +784,7 @@ __device__ int group_inverse_s(const TileSmem<T, D, GEN>& sm, const int (&a)[D],
     return status;
 }
 
-template <typename T, int D, bool GEN>
+template <typename T, int D, int GEN>
 __device__ int group_inverse(const TileSmem<T, D, GEN>& sm, int e, T* out) {
     constexpr int TE = tile_extent(D);
     int a[D], mask = 0, rem = e;
@@ -666,12 +810,12 @@ __device__ int group_inverse(const TileSmem<T, D, GEN>& sm, int e, T* out) {
 // flight).
 // PK selects the arithmetic of the block updates: the native FMA pipes, or
 // (FP32 solves only) TF32 / BF16 tensor-core products with FP32 accumulation.
-template <typename T, int D, bool GENF, int PK = kProdNative>
+template <typename T, int D, int GENF, int PK = kProdNative>
 __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, const int rank, const int csize,
                                           uint32_t (&uses)[WaveCfg<T, D, GENF>::NST], uint64_t* bar) {
     using C = WaveCfg<T, D, GENF>;
     constexpr int TE = C::TE, TD = C::TD, TC = C::TC, EPT = C::EPT, NACC = C::NACC;
-    constexpr bool GEN = C::GEN;
+    constexpr bool GEN = C::GEN, TT = C::TT, CHAIN = C::CHAIN;
     constexpr bool TCU = PK != kProdNative;  // tensor-core updates
     static_assert(!TCU || sizeof(T) == 4, "tensor-core block updates serve the FP32 solve");
     using Q = MmaCfg<D, TCU ? PK : kProdTF32>;
@@ -699,11 +843,11 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     long long W = 0;
 #pragma unroll
     for (int L = 0; L < D; L++) {
-        const int mu = GEN ? D - 1 - L : L;
+        const int mu = CHAIN ? D - 1 - L : L;
         cnt[L] = a.hi[mu] - 1 - I[mu];
         if (cnt[L] < 0) cnt[L] = 0;
         if (cnt[L] > maxc) maxc = cnt[L];
-        w[L] = GEN ? ((L == 0 || L == D - 1) ? 2 : 3) : 1;
+        w[L] = GEN ? ((L == 0 || L == D - 1) ? 2 : 3) : TT ? (L == D - 1 ? 2 : 1) : 1;
         W += static_cast<long long>(cnt[L]) * w[L];
     }
     // number of jobs whose distance is at least dd
@@ -748,7 +892,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             if (r == 0) { L = q; break; }
             r--;
         }
-        const int mu = GEN ? D - 1 - L : L;
+        const int mu = CHAIN ? D - 1 - L : L;
         Jp = I[mu] + lo;
     };
     int* jtab = reinterpret_cast<int*>(smem_raw + C::oJob);
@@ -766,7 +910,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     auto issue = [&](int j, int stg) {
         int L, Jp;
         job(j, L, Jp);
-        const int mu = GEN ? D - 1 - L : L;
+        const int mu = CHAIN ? D - 1 - L : L;
         const long long ts = t + static_cast<long long>(Jp - I[mu]) * a.tstride[mu];
         const long long tri = static_cast<long long>(Jp) * (Jp + 1) / 2 + I[mu];
         T* sb = stage + stg * C::STAGE;
@@ -774,7 +918,18 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         const T* S2 = nullptr;
         const T* M1;
         const T* M2 = nullptr;
-        if (!GEN) {
+        if (TT) {
+            // two-term form: Q_{mu+1} x A_mu (Q_d = X); mode 1: Q_1 x C + X x A_1
+            if (mu >= 1) {
+                S1 = static_cast<const T*>(L == 0 ? a.X : a.P[mu + 1]) + ts * TD;
+                M1 = static_cast<const T*>(a.At[mu]) + tri * TC;
+            } else {
+                S1 = static_cast<const T*>(a.X) + ts * TD;
+                S2 = static_cast<const T*>(D >= 2 ? a.P[1] : a.X) + ts * TD;
+                M1 = static_cast<const T*>(a.Ct[0]) + tri * TC;
+                M2 = static_cast<const T*>(a.At[0]) + tri * TC;
+            }
+        } else if (!GEN) {
             S1 = static_cast<const T*>(a.X) + ts * TD;
             M1 = static_cast<const T*>(a.At[mu]) + tri * TC;
         } else {
@@ -827,7 +982,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             decode(j0 + r, L, Jp);
             jtab[r] = (L << 24) | Jp;
             if (a.ready) {
-                const int mu = GEN ? D - 1 - L : L;
+                const int mu = CHAIN ? D - 1 - L : L;
                 rdy = dev::ld_acquire(a.ready + t + static_cast<long long>(Jp - I[mu]) * a.tstride[mu]) != 0;
             }
         }
@@ -859,6 +1014,8 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         const long long tri = static_cast<long long>(I[mu]) * (I[mu] + 1) / 2 + I[mu];
         Ds[idx] = static_cast<const T*>(a.At[mu])[tri * TC + e];
         if (GEN) Es[idx] = static_cast<const T*>(a.Ct[mu])[tri * TC + e];
+        // two-term form: the chain factor of every mode (C in mode 1, A_mu elsewhere)
+        if (TT) Es[idx] = static_cast<const T*>(mu == 0 ? a.Ct[0] : a.At[mu])[tri * TC + e];
     }
     for (int e = tid; e < TD; e += kThreads) {
         Rs[e] = Xg[e];
@@ -875,7 +1032,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     int* act_list = act_fill + C::MAXSTEP;  // element codes (ElemCode)
     T* Minv = sbase + C::oMinv;
     for (int i = tid; i < C::MAXSTEP; i += kThreads) { cg_cnt[i] = 0; cg_fill[i] = 0; act_cnt[i] = 0; act_fill[i] = 0; }
-    if (GEN && !C::PIN_IN_RING)
+    if (CHAIN && !C::PIN_IN_RING)
         for (int e = tid; e < C::NL * TD; e += kThreads) { Pin[e] = T(0); Gin[e] = T(0); }
     if (tid < D) bs[tid] = a.bsize[tid][I[tid]];
     __syncthreads();
@@ -927,7 +1084,16 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         sq[q] = sgv;
         single[q] = okq[q] && S == 1;
         lead[q] = okq[q] && S > 1 && ld;
-        if (single[q]) {
+        if (single[q] && TT) {
+            // two-term form: a_1,ii + c_ii prod_{mu >= 2} a_mu,jj
+            T t2 = Es[uq[q][0] * (TE + 1)];
+#pragma unroll
+            for (int mu = 1; mu < D; mu++) t2 *= Es[mu * TC + uq[q][mu] * (TE + 1)];
+            const T t1 = Ds[uq[q][0] * (TE + 1)];
+            const T diag = dev::add_rn(t1, t2);  // never fused with the product above
+            if (!(fabs(diag) > T(16) * dev::Eps<T>::v * (fabs(t1) + fabs(t2)))) status |= kErrSingular;
+            Rd[e] = T(1) / diag;
+        } else if (single[q]) {
             // reciprocal of the diagonal entry sum_mu a_mu,ii prod_{eta != mu} c_eta,jj
             T diag = 0, mag = 0;
 #pragma unroll
@@ -1007,9 +1173,9 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     }
     __syncthreads();
     if constexpr (C::INV_EARLY) {
-        const TileSmem<T, D, GEN> smi{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
+        const TileSmem<T, D, GENF> smi{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
         for (int i = tid; i < ncg; i += kThreads)
-            if (cg_moff[i] >= 0) status |= group_inverse<T, D, GEN>(smi, cg_list[i], Minv + cg_moff[i]);
+            if (cg_moff[i] >= 0) status |= group_inverse<T, D, GENF>(smi, cg_list[i], Minv + cg_moff[i]);
     }
     bool dead = false;
     for (int jj = 0; jj < njob && !dead; jj++) {
@@ -1056,7 +1222,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
 
     // ---- partial sums -> shared memory (the generalized form's Horner chain
     // mixes elements; a cluster reduces through it), cluster reduction into rank 0
-    if (GEN || csize > 1) {
+    if (CHAIN || csize > 1) {
 #pragma unroll
         for (int s = 0; s < NACC; s++)
 #pragma unroll
@@ -1091,7 +1257,47 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
 
     // ---- base case, the rest: right-hand side minus the block updates, then
     // back-substitution over the coupled groups in anti-diagonal order
-    if constexpr (GEN) {
+    if constexpr (TT) {
+        __syncthreads();
+        // two-term form: the level sums of the Q chain through the diagonal
+        // blocks of the chain factors (levels d-2 .. 1), then the mode-1
+        // level: off(T) = c x Q_1 + (the A_1 sums already in the last slot)
+#pragma unroll
+        for (int l = D - 2; l >= 1; l--) {
+            __syncthreads();
+            const int st = ipow(TE, l);
+            const T* Pn = red + C::slotP(l + 1) * TD;
+            T vp[EPT];
+#pragma unroll
+            for (int q = 0; q < EPT; q++) {
+                const int e = tid + q * kThreads;
+                vp[q] = T(0);
+                if ((TD % kThreads) != 0 && e >= TD) continue;
+                const int i = (e / st) % TE, base = e - i * st;
+                T p = red[C::slotP(l) * TD + e];
+                for (int k = 0; k < TE; k++) p = dev::fmadd(Es[l * TC + i + TE * k], Pn[base + k * st], p);
+                vp[q] = p;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < EPT; q++) {
+                const int e = tid + q * kThreads;
+                if ((TD % kThreads) != 0 && e >= TD) continue;
+                red[C::slotP(l) * TD + e] = vp[q];
+            }
+        }
+        __syncthreads();
+        {
+            const T* Pn = red + C::slotP(1) * TD;
+            for (int e = tid; e < TD; e += kThreads) {
+                const int i = e % TE, base = e - i;
+                T off = red[(NACC - 1) * TD + e];
+                for (int k = 0; k < TE; k++) off = dev::fmadd(Es[i + TE * k], Pn[base + k], off);
+                Rs[e] -= off;
+            }
+        }
+        __syncthreads();
+    } else if constexpr (GEN) {
         __syncthreads();
         // Horner chain over the diagonal blocks (levels d-2 .. 1), then the
         // mode-1 level: off(T) = A(X with block T set to zero) restricted to T.
@@ -1146,6 +1352,15 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             if ((TD % kThreads) == 0 || e < TD) Rs[e] -= acc[0][q];
         }
     }
+    if constexpr (TT) {
+        // park the level sums of the Q chain in the output blocks
+#pragma unroll
+        for (int l = 1; l < D; l++) {
+            T* Pg = static_cast<T*>(a.P[l]) + t * TD;
+            for (int e = tid; e < TD; e += kThreads) Pg[e] = red[C::slotP(l) * TD + e];
+        }
+        __syncthreads();
+    }
     if constexpr (GEN) {
         // park the level sums of the block updates in the output blocks (the
         // in-block parts are added at the end), freeing `red` for Lin
@@ -1161,13 +1376,13 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         __syncthreads();
     }
     for (int e = tid; e < NACC * TD; e += kThreads) Lin[e] = T(0);
-    if (GEN && C::PIN_IN_RING)  // the ring is free now: every copy has landed and been read
+    if (CHAIN && C::PIN_IN_RING)  // the ring is free now: every copy has landed and been read
         for (int e = tid; e < C::NL * TD; e += kThreads) { Pin[e] = T(0); Gin[e] = T(0); }
 
-    TileSmem<T, D, GEN> sm{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
+    TileSmem<T, D, GENF> sm{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
     if constexpr (!C::INV_EARLY)
         for (int i = tid; i < ncg; i += kThreads)
-            if (cg_moff[i] >= 0) status |= group_inverse<T, D, GEN>(sm, cg_list[i], Minv + cg_moff[i]);
+            if (cg_moff[i] >= 0) status |= group_inverse<T, D, GENF>(sm, cg_list[i], Minv + cg_moff[i]);
     __syncthreads();
     // all warps take part (a one-warp variant with warp barriers between the
     // anti-diagonals measured slower for FP32 too: the line sums of one step
@@ -1191,9 +1406,9 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
                     k0s[mu] = ElemCode<D>::k0(code, mu);
                 }
                 T L[NACC];
-                pull_lines<T, D, GEN>(sm, e, u, k0s, L);
+                pull_lines<T, D, GENF>(sm, e, u, k0s, L);
                 if (!ElemCode<D>::coupled(code)) {
-                    status |= solve_single<T, D, GEN>(sm, e, u, L);
+                    status |= solve_single<T, D, GENF>(sm, e, u, L);
                 } else {
 #pragma unroll
                     for (int k = 0; k < NACC; k++) Lin[k * TD + e] = L[k];
@@ -1204,7 +1419,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
                 if constexpr (SOLO) __syncwarp(); else __syncthreads();
                 const int warp = SOLO ? 0 : tid >> 5, nw = SOLO ? 1 : kThreads >> 5;
                 for (int k = warp; k < cn; k += nw)
-                    status |= warp_group<T, D, GEN>(sm, cg_list[c0 + k],
+                    status |= warp_group<T, D, GENF>(sm, cg_list[c0 + k],
                                                     cg_moff[c0 + k] >= 0 ? Minv + cg_moff[c0 + k] : nullptr);
             }
             if constexpr (SOLO) __syncwarp(); else __syncthreads();
@@ -1215,6 +1430,13 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
 
     // ---- write the solved block (and its intermediates)
     for (int e = tid; e < TD; e += kThreads) Xg[e] = Xs[e];
+    if constexpr (TT) {
+#pragma unroll
+        for (int l = 1; l < D; l++) {
+            T* Pg = static_cast<T*>(a.P[l]) + t * TD;
+            for (int e = tid; e < TD; e += kThreads) Pg[e] += Pin[(l - 1) * TD + e];  // parked by this thread
+        }
+    }
     if constexpr (GEN) {
 #pragma unroll
         for (int l = 1; l < D; l++) {
@@ -1232,7 +1454,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
 // Compiled for the same resident count as the persistent kernel, so that a
 // block runs the same machine code (the same contractions into FMAs) in both
 // schedules.
-template <typename T, int D, bool GENF>
+template <typename T, int D, int GENF>
 __global__ void __launch_bounds__(kThreads, WaveCfg<T, D, GENF>::MINB) k_wave(const WaveArgs a) {
     using C = WaveCfg<T, D, GENF>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1248,14 +1470,14 @@ __global__ void __launch_bounds__(kThreads, WaveCfg<T, D, GENF>::MINB) k_wave(co
     (void)wave_tile<T, D, GENF>(a, a.tiles[blockIdx.x / csize], rank, csize, uses, bar);
 }
 
-template <typename T, int D, bool GEN>
+template <typename T, int D, int GEN>
 cudaError_t prepare_wave_t() {
     using C = WaveCfg<T, D, GEN>;
     return cudaFuncSetAttribute(k_wave<T, D, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(C::smem));
 }
 
-template <typename T, int D, bool GEN>
+template <typename T, int D, int GEN>
 cudaError_t launch_wave_t(const WaveArgs& a, cudaStream_t s) {
     using C = WaveCfg<T, D, GEN>;
     cudaLaunchConfig_t cfg = {};

@@ -22,7 +22,7 @@ def lib():
 def _declared():
     src = open(os.path.join(ROOT, "include", "tsylv.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b((?:g?tsylv)_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b((?:g?tsylv|gsylvten)_[a-z_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(lib):
@@ -232,3 +232,33 @@ def test_generalized_d5_unsupported_without_gpu(lib):
     assert lib.gtsylv_solve(5, n, fake, fake, P(16), P(16), P(256), 1 << 30, ctypes.byref(o), None, None) == \
         _lib.TSYLV_EUNSUPPORTED
     assert lib.tsylv_workspace_bytes(5, n, 0, ctypes.byref(o)) > 4 ** 5 * 8
+
+
+def test_two_term_validation_without_gpu(lib):
+    """gsylvten_solve (Eq. (3.1)): bad arguments give -i, orders outside 2..4,
+    precisions other than FP64, the wavefront schedule and autotuning give
+    TSYLV_EUNSUPPORTED -- all before any CUDA call."""
+    from paper_1905_09539_gb300 import _lib
+    P = ctypes.c_void_p
+    n = (ctypes.c_int64 * 3)(8, 8, 8)
+    fake = (P * 3)(16, 16, 16)
+    o = _lib.default_opts()
+    wb = lib.gsylvten_workspace_bytes(3, n, ctypes.byref(o))
+    assert wb > 8 ** 3 * 8
+    assert lib.gsylvten_workspace_bytes(1, n, ctypes.byref(o)) == 0
+    assert lib.gsylvten_solve(0, n, fake, P(16), P(16), P(16), P(256), wb, ctypes.byref(o), None, None) == -1
+    assert lib.gsylvten_solve(3, n, None, P(16), P(16), P(16), P(256), wb, ctypes.byref(o), None, None) == -3
+    assert lib.gsylvten_solve(3, n, fake, None, P(16), P(16), P(256), wb, ctypes.byref(o), None, None) == -4
+    assert lib.gsylvten_solve(3, n, fake, P(16), None, P(16), P(256), wb, ctypes.byref(o), None, None) == -5
+    assert lib.gsylvten_solve(3, n, fake, P(16), P(16), None, P(256), wb, ctypes.byref(o), None, None) == -6
+    assert lib.gsylvten_solve(3, n, fake, P(16), P(16), P(16), P(257), wb, ctypes.byref(o), None, None) == -7
+    assert lib.gsylvten_solve(3, n, fake, P(16), P(16), P(16), P(256), 16, ctypes.byref(o), None, None) == -8
+    n1 = (ctypes.c_int64 * 1)(8)
+    assert lib.gsylvten_solve(1, n1, fake, P(16), P(16), P(16), P(256), wb, ctypes.byref(o), None, None) == \
+        _lib.TSYLV_EUNSUPPORTED
+    for kw in ({"precision": _lib.TSYLV_FP32_REFINED}, {"schedule": 1}, {"nmin": -1}):
+        ok = _lib.default_opts(**kw)
+        assert lib.gsylvten_solve(3, n, fake, P(16), P(16), P(16), P(256), wb, ctypes.byref(ok), None, None) == \
+            _lib.TSYLV_EUNSUPPORTED, kw
+    bad = _lib.default_opts(wait_ms=0)
+    assert lib.gsylvten_solve(3, n, fake, P(16), P(16), P(16), P(256), wb, ctypes.byref(bad), None, None) == -9
