@@ -837,6 +837,30 @@ def run_ours(args, ws, rank, local):
                 row[str(nm)] = event_ms(fq, 5)
             sweep["d%d_n%d_laplace_fp64_ms_by_nmin" % (dd, nn_)] = row
         other["paper_nmin_sweeps"] = sweep
+        # the paper's own two-term form Eq. (3.1) at 256^3 (FP64): time, and
+        # the FP64 residual of the result, evaluated with the library's
+        # change-of-basis (dense mode product) kernel
+        from paper_1905_09539_gb300.general import transform
+        q = synthetic.problem(args.seed + rank, shape, generalized=True)
+        qA = [to_dev(a) for a in q["A"]]
+        qC = to_dev(q["C"][0])
+        qB = probs[True]["B"]
+        qX = ts.empty_fortran(shape, dev)
+        qi = _lib.Info()
+        fq = lambda: ts.gsylvten_solve(qA, qC, qB, X=qX, info=qi)
+        fq()
+        tq = event_ms(fq, 3)
+        T1 = transform(qX, [qA[0], None, None])
+        T2 = transform(qX, [qC] + qA[1:])
+        Rq = qB - T1 - T2
+        nrm = lambda a: float(np.linalg.norm(a, 2))
+        opn = nrm(q["A"][0]) + nrm(q["C"][0]) * nrm(q["A"][1]) * nrm(q["A"][2])
+        other["two_term_256_fp64"] = {
+            "ms": tq, "unknowns_per_s": N / (tq * 1e-3), "executed_gflop": qi.flops / 1e9,
+            "rel_residual_fp64": float(torch.linalg.vector_norm(Rq) / (opn * torch.linalg.vector_norm(qX))),
+            "note": "gsylvten_solve, Eq. (3.1): X x_1 A_1 + X x_1 C x_2 A_2 x_3 A_3 = B; residual by the DMMA "
+                    "mode-product kernel"}
+        del qA, qC, qX, T1, T2, Rq
         q = synthetic.problem(args.seed + rank, (20,) * 5)
         qA = [to_dev(a) for a in q["A"]]
         qB = to_dev(q["B"])
