@@ -38,8 +38,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.10
 # DRAM bytes (read + write) per launch of the dominant kernel (one FP64 solve of
 # the 256^3 generalized form) from an ncu capture of the current kernel:
-# 10.590 GB read + 0.837 GB written (the capture is summarised under profiles/)
-TRAFFIC_PER_LAUNCH_BYTES = 11.427e9
+# 10.600 GB read + 0.836 GB written (the capture is summarised under profiles/)
+TRAFFIC_PER_LAUNCH_BYTES = 11.435e9
 
 
 def algorithmic_flops(A, C=None):
