@@ -233,6 +233,28 @@ int gtsylv_solve_transposed(int d, const int64_t* n, const double* const* A,
                             size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
                             cudaStream_t stream);
 
+/* The complex-triangular variant (Sec. 2.4: the paper's experiments reduce
+ * every coefficient to complex Schur form, which is upper triangular): the
+ * Laplace form Eq. (2.2) (ztsylv_solve) or the d-term generalized form
+ * (zgtsylv_solve) with complex FP64 coefficients, right-hand side and
+ * solution.  Every complex array is interleaved (re, im) pairs of doubles --
+ * C99 double complex, std::complex<double>, torch.complex128 -- in the
+ * layouts of tsylv_solve (tensors column-major, matrices column-major
+ * n_mu x n_mu); the pointers are passed as double*.  A_mu and C_mu are upper
+ * triangular: entries below the diagonal are never read (no 2x2 blocks).  The
+ * same block partition, persistent schedule and back-substitution as the real
+ * solves, in complex arithmetic (a complex multiply-add is four real FP64
+ * fused multiply-adds; the reciprocal of a diagonal entry uses Smith's
+ * quotient).  d = 1..4; FP64 only (other precisions, opts->schedule = 1 and
+ * nmin = -1 return TSYLV_EUNSUPPORTED); arguments and statuses as
+ * tsylv_solve / gtsylv_solve.  work: ztsylv_workspace_bytes(d, n, generalized, opts). */
+size_t ztsylv_workspace_bytes(int d, const int64_t* n, int generalized, const tsylv_opts* opts);
+int ztsylv_solve(int d, const int64_t* n, const double* const* A, const double* B, double* X, void* work,
+                 size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
+int zgtsylv_solve(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,
+                  double* X, void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
+                  cudaStream_t stream);
+
 /* The paper's own generalized form, Sec. 3, Eq. (3.1):
  *       X x_1 A_1 + X x_1 C x_2 A_2 x_3 ... x_d A_d = B,
  * i.e. (I x ... x I x A_1 + A_d x ... x A_2 x C) vec(X) = vec(B) (Eq. (1.5)),

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (TSYLV_BF16_REFINED, TSYLV_FP32_REFINED, TSYLV_FP64, TSYLV_RESID_DF64, TSYLV_RESID_FP64,
                    TSYLV_TF32_REFINED, Info, Opts, default_opts, load, status_string)
 
-__all__ = ["tsylv_solve", "gtsylv_solve", "gsylvten_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
+__all__ = ["tsylv_solve", "gtsylv_solve", "gsylvten_solve", "ztsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
            "tsylv_residual", "tsylv_backward", "tsylv_solve_batched", "BatchPools", "solve", "fortran", "TsylvError",
            "Opts", "Info", "default_opts", "TSYLV_FP64", "TSYLV_FP32_REFINED", "TSYLV_TF32_REFINED",
            "TSYLV_BF16_REFINED", "TSYLV_RESID_DF64", "TSYLV_RESID_FP64", "workspace", "solve_general",
@@ -171,6 +171,40 @@ def gsylvten_solve(A, C, B, X=None, *, opts=None, check=True, stream=None, info=
                             ctypes.byref(o), ctypes.byref(inf), _stream(stream))
     if check and st != 0:
         raise TsylvError(st, "gsylvten_solve")
+    return X, st
+
+
+def ztsylv_solve(A, B, C=None, X=None, *, opts=None, check=True, stream=None, info=None, **kw):
+    """Complex-triangular variant: X with sum_mu X x_mu A_mu = B (C None) or
+    sum_mu X x_mu A_mu x_{eta != mu} C_eta = B, every tensor and matrix
+    complex128 (A_mu, C_mu upper triangular).  Returns (X, status)."""
+    lib = load()
+    _check_cuda(B, *A, *(C or []))
+    o = _opts(opts, kw)
+    z = torch.complex128
+    B = fortran(B, z)
+    d = B.dim()
+    if X is None:
+        X = empty_fortran(B.shape, B.device, z)
+    elif not is_fortran(X) or X.dtype != z:
+        raise ValueError("X must be a complex128 column-major tensor")
+    ms = [fortran(a, z) for a in A]
+    pa = (ctypes.c_void_p * d)(*[m.data_ptr() for m in ms])
+    gen = C is not None
+    if gen:
+        cs = [fortran(c, z) for c in C]
+        pc = (ctypes.c_void_p * d)(*[m.data_ptr() for m in cs])
+    n = _dims(B.shape)
+    nbytes = lib.ztsylv_workspace_bytes(d, n, 1 if gen else 0, ctypes.byref(o))
+    if nbytes == 0:
+        raise ValueError("ztsylv_solve: invalid or unsupported shape %s (d = 1..4)" % (tuple(B.shape),))
+    work = workspace(nbytes, B.device)
+    inf = info if info is not None else Info()
+    tail = [B.data_ptr(), X.data_ptr(), work.data_ptr(), work.numel(), ctypes.byref(o), ctypes.byref(inf),
+            _stream(stream)]
+    st = lib.zgtsylv_solve(d, n, pa, pc, *tail) if gen else lib.ztsylv_solve(d, n, pa, *tail)
+    if check and st != 0:
+        raise TsylvError(st, "ztsylv_solve")
     return X, st
 
 

@@ -50,6 +50,7 @@ EXPORTS = [
     "tsylv_backward", "tsylv_batched_workspace_bytes", "tsylv_solve_batched", "tsylv_last_error",
     "tsylv_solve_noalloc", "tsylv_residual_workspace_bytes", "tsylv_selftest_wait_timeout",
     "tsylv_transform", "tsylv_transform_workspace_bytes", "gsylvten_solve", "gsylvten_workspace_bytes",
+    "ztsylv_solve", "zgtsylv_solve", "ztsylv_workspace_bytes",
 ]
 
 _lib = None
@@ -104,6 +105,12 @@ def load(path=LIB_PATH):
     lib.gsylvten_workspace_bytes.restype = S
     lib.gsylvten_solve.argtypes = [I, I64P, P, P, P, P, P, S, OP, IP, P]
     lib.gsylvten_solve.restype = I
+    lib.ztsylv_workspace_bytes.argtypes = [I, I64P, I, OP]
+    lib.ztsylv_workspace_bytes.restype = S
+    lib.ztsylv_solve.argtypes = [I, I64P, P, P, P, P, S, OP, IP, P]
+    lib.ztsylv_solve.restype = I
+    lib.zgtsylv_solve.argtypes = [I, I64P, P, P, P, P, P, S, OP, IP, P]
+    lib.zgtsylv_solve.restype = I
     for f in ("tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
               "tsylv_residual", "tsylv_backward", "tsylv_solve_batched"):
         getattr(lib, f).restype = I

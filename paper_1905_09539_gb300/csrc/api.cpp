@@ -90,6 +90,23 @@ extern "C" int gtsylv_solve_transposed(int d, const int64_t* n, const double* co
     return solver_solve(d, n, A, C, G, L, work, work_bytes, opts, info, stream, true, true);
 }
 
+extern "C" size_t ztsylv_workspace_bytes(int d, const int64_t* n, int generalized, const tsylv_opts* opts) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    return solver_z_workspace_bytes(d, n, generalized != 0, o);
+}
+
+extern "C" int ztsylv_solve(int d, const int64_t* n, const double* const* A, const double* B, double* X, void* work,
+                            size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream) {
+    return solver_solve_z(d, n, A, nullptr, B, X, work, work_bytes, opts, info, stream, false);
+}
+
+extern "C" int zgtsylv_solve(int d, const int64_t* n, const double* const* A, const double* const* C,
+                             const double* B, double* X, void* work, size_t work_bytes, const tsylv_opts* opts,
+                             tsylv_info* info, cudaStream_t stream) {
+    return solver_solve_z(d, n, A, C, B, X, work, work_bytes, opts, info, stream, true);
+}
+
 extern "C" size_t gsylvten_workspace_bytes(int d, const int64_t* n, const tsylv_opts* opts) {
     tsylv_opts o;
     if (opts) o = *opts; else tsylv_opts_default(&o);

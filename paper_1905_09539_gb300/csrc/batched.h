@@ -70,6 +70,10 @@ cudaError_t prepare_batched();
 cudaError_t launch_batched_tt(int d, const BatchArgs& a, int grid, cudaStream_t s);
 int batched_occupancy_tt(int d);
 cudaError_t prepare_batched_tt();
+// Complex FP64 (complex-triangular coefficients), d = 1..4, Laplace or d-term form.
+cudaError_t launch_batched_z(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s);
+int batched_occupancy_z(int d, bool gen);
+cudaError_t prepare_batched_z();
 // *dst = a, by one thread (a captured launch keeps `a` by value).
 cudaError_t launch_store_args(const WaveArgs& a, WaveArgs* dst, cudaStream_t s);
 // Resident CTAs per SM of the persistent kernel.

@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "complex_z.h"
+
 namespace tsylv {
 namespace dev {
 
@@ -183,6 +185,18 @@ template <>
 struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
 template <>
 struct Eps<float> { static constexpr float v = 1.1920929e-07f; };
+template <>
+struct Eps<zd> { static constexpr double v = 2.220446049250313e-16; };
+
+// complex multiply-add c + a b as four real fused multiply-adds
+template <>
+__device__ __forceinline__ zd fmadd<zd>(zd a, zd b, zd c) {
+    return zd(fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im)));
+}
+__device__ __forceinline__ zd add_rn(zd a, zd b) { return zd(__dadd_rn(a.re, b.re), __dadd_rn(a.im, b.im)); }
+__device__ __forceinline__ zd ld_dsmem(const zd* local, uint32_t rank) {
+    return zd(ld_dsmem(&local->re, rank), ld_dsmem(&local->im, rank));
+}
 
 }  // namespace dev
 }  // namespace tsylv

@@ -7,8 +7,8 @@ namespace {
 
 // Block tensor element (tile t, local e) <-> global index.  flip reverses
 // every mode (the index flip J of the transposed solve).
-template <typename T>
-__global__ void k_pack_tensor(const GeomArgs g, const double* __restrict__ src, T* __restrict__ tiles,
+template <typename T, typename S = double>
+__global__ void k_pack_tensor(const GeomArgs g, const S* __restrict__ src, T* __restrict__ tiles,
                               double scale) {
     const int d = g.d;
     const int te = tile_extent(d);
@@ -34,8 +34,8 @@ __global__ void k_pack_tensor(const GeomArgs g, const double* __restrict__ src, 
     }
 }
 
-template <typename T>
-__global__ void k_unpack_tensor(const GeomArgs g, const T* __restrict__ tiles, double* __restrict__ dst) {
+template <typename T, typename S = double>
+__global__ void k_unpack_tensor(const GeomArgs g, const T* __restrict__ tiles, S* __restrict__ dst) {
     const int d = g.d;
     const int te = tile_extent(d);
     const int td = ipow(te, d);
@@ -54,7 +54,7 @@ __global__ void k_unpack_tensor(const GeomArgs g, const T* __restrict__ tiles, d
             e += static_cast<int>(gi - g.part.start[mu][I]) * est;
             est *= te;
         }
-        dst[idx] = static_cast<double>(tiles[t * td + e]);
+        dst[idx] = static_cast<S>(tiles[t * td + e]);
     }
 }
 
@@ -62,8 +62,8 @@ __global__ void k_unpack_tensor(const GeomArgs g, const T* __restrict__ tiles, d
 // structure makes zero (below the first subdiagonal of A, below the diagonal
 // of C) are written as zero without being read.  With flip, the tile holds
 // J M^T J: entry (i, j) = M(n-1-j, n-1-i).
-template <typename T>
-__global__ void k_pack_coef(const GeomArgs g, int mu, const double* __restrict__ M, T* __restrict__ tiles,
+template <typename T, typename S = double>
+__global__ void k_pack_coef(const GeomArgs g, int mu, const S* __restrict__ M, T* __restrict__ tiles,
                             int upper_only) {
     const int te = tile_extent(g.d);
     const int tc = te * te;
@@ -151,6 +151,28 @@ cudaError_t launch_gather_subdiag(int d, const long long* n, const double* const
         if (n[mu] > mx) mx = n[mu];
     }
     k_gather_subdiag<<<grid_for(mx), 256, 0, s>>>(a, out);
+    return cudaGetLastError();
+}
+
+// Complex tensors and coefficients (interleaved re, im): the same index maps;
+// complex triangular coefficients keep the upper triangle only.
+cudaError_t launch_pack_tensor_z(const GeomArgs& g, const zd* src, zd* tiles, cudaStream_t s) {
+    const long long total = g.ntiles * ipow(tile_extent(g.d), g.d);
+    k_pack_tensor<zd, zd><<<grid_for(total), 256, 0, s>>>(g, src, tiles, 1.0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_tensor_z(const GeomArgs& g, const zd* tiles, zd* dst, cudaStream_t s) {
+    long long total = 1;
+    for (int mu = 0; mu < g.d; mu++) total *= g.n[mu];
+    k_unpack_tensor<zd, zd><<<grid_for(total), 256, 0, s>>>(g, tiles, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_coef_z(const GeomArgs& g, int mu, const zd* M, zd* tiles, cudaStream_t s) {
+    const int te = tile_extent(g.d);
+    const long long total = static_cast<long long>(g.nb[mu]) * g.nb[mu] * te * te;
+    k_pack_coef<zd, zd><<<grid_for(total), 256, 0, s>>>(g, mu, M, tiles, 1);
     return cudaGetLastError();
 }
 

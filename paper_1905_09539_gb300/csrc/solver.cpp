@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "batched.h"
@@ -238,15 +239,22 @@ cudaError_t enqueue_waves(const Call& c, const Layout& L, cudaStream_t s) {
         ba.abort = ctl + 1;
         ba.timeout_ns = c.timeout_ns;
         if (p.tt) return launch_batched_tt(p.d, ba, c.flow_grid, s);
-        return launch_batched<T>(p.d, p.gen, ba, c.flow_grid, s, sizeof(T) == 4 ? c.prod : kProdNative);
+        if constexpr (std::is_same<T, zd>::value)
+            return launch_batched_z(p.d, p.gen, ba, c.flow_grid, s);
+        else
+            return launch_batched<T>(p.d, p.gen, ba, c.flow_grid, s, sizeof(T) == 4 ? c.prod : kProdNative);
     }
-    for (size_t w = 0; w < p.wave_off.size(); w++) {
-        wa.tiles = tab + p.t_wave + p.wave_off[w];
-        wa.ntiles = p.wave_cnt[w];
-        wa.csize = p.wave_csize[w];
-        TRY(launch_wave<T>(p.d, p.gen, kProdNative, wa, s));
+    if constexpr (std::is_same<T, zd>::value) {
+        return cudaErrorInvalidValue;  // the complex solve runs the persistent schedule only
+    } else {
+        for (size_t w = 0; w < p.wave_off.size(); w++) {
+            wa.tiles = tab + p.t_wave + p.wave_off[w];
+            wa.ntiles = p.wave_cnt[w];
+            wa.csize = p.wave_csize[w];
+            TRY(launch_wave<T>(p.d, p.gen, kProdNative, wa, s));
+        }
+        return cudaSuccess;
     }
-    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- FP64 solve
@@ -292,6 +300,31 @@ cudaError_t enqueue_tt(const Call& c, cudaStream_t s) {
     TRY(enqueue_waves<double>(c, L, s));
     TRY(mark(c, 2, s));
     TRY(launch_unpack_tensor<double>(g, Xt, c.X, s));
+    return mark(c, 3, s);
+}
+
+// Complex FP64 solve (complex-triangular coefficients): complex coefficient
+// tiles (upper triangle), the complex block tensor of B, the persistent solve.
+cudaError_t enqueue_z(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    const Layout& L = c.L;
+    char* base = c.base;
+    GeomArgs g = geom_of(p, L, base, false);
+    TRY(mark(c, 0, s));
+    TRY(cudaMemsetAsync(base + L.err, 0, 64, s));
+    TRY(cudaMemcpyAsync(base + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int mu = 0; mu < p.d; mu++) {
+        TRY(launch_pack_coef_z(g, mu, reinterpret_cast<const zd*>(c.A[mu]), reinterpret_cast<zd*>(base + L.At[mu]), s));
+        if (p.gen)
+            TRY(launch_pack_coef_z(g, mu, reinterpret_cast<const zd*>(c.C[mu]), reinterpret_cast<zd*>(base + L.Ct[mu]),
+                                   s));
+    }
+    zd* Xt = reinterpret_cast<zd*>(base + L.X);
+    TRY(launch_pack_tensor_z(g, reinterpret_cast<const zd*>(c.B), Xt, s));
+    TRY(mark(c, 1, s));
+    TRY(enqueue_waves<zd>(c, L, s));
+    TRY(mark(c, 2, s));
+    TRY(launch_unpack_tensor_z(g, Xt, reinterpret_cast<zd*>(c.X), s));
     return mark(c, 3, s);
 }
 
@@ -729,6 +762,7 @@ int prepare_kernels() {
         if (e == cudaSuccess) e = prepare_batched<double>();
         if (e == cudaSuccess) e = prepare_batched<float>();
         if (e == cudaSuccess) e = prepare_batched_tt();
+        if (e == cudaSuccess) e = prepare_batched_z();
         if (e == cudaSuccess) e = prepare_refine2();
         if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
         prepared[dev] = true;
@@ -1286,6 +1320,122 @@ int solver_solve_tt(int d, const int64_t* n, const double* const* A, const doubl
         info->resid = -1;
         info->norm_A = -1;
         info->flops = c.plan->flops;
+        if (c.timing) {
+            float a = -1, b = -1;
+            if (cudaEventElapsedTime(&a, c.plan->ev[0], c.plan->ev[3]) != cudaSuccess) a = -1;
+            if (cudaEventElapsedTime(&b, c.plan->ev[1], c.plan->ev[2]) != cudaSuccess) b = -1;
+            (void)cudaGetLastError();
+            info->t_total_ms = a;
+            info->t_waves_ms = b;
+        }
+    }
+    return map_err(herr);
+}
+
+size_t solver_z_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o) {
+    if (!shape_ok(d, n) || d > 4) return 0;
+    long long nn[kMaxD];
+    int nb[kMaxD];
+    const int shape = shape_of_opts(o, d);
+    for (int mu = 0; mu < d; mu++) {
+        nn[mu] = n[mu];
+        nb[mu] = max_blocks(static_cast<int>(n[mu]), shape_min_cut(d, mu, shape < 0 ? 0 : shape));
+    }
+    return make_layout(d, nn, nb, gen && d >= 2, 16, tab_ints_bound(d, nn, nb)).total;
+}
+
+// The complex-triangular variant (Sec. 2.4: the coefficients reduced to
+// complex Schur form, so every A_mu and C_mu is upper triangular and there are
+// no coupled groups): the Laplace form Eq. (2.2) or the d-term form with
+// complex FP64 coefficients and tensors (interleaved re, im); the same block
+// partition, persistent schedule and base case as the real solves, in complex
+// arithmetic.  d = 1..4, FP64, persistent schedule.
+int solver_solve_z(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,
+                   double* X, void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
+                   cudaStream_t stream, bool gen) {
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    const int sh = gen ? 1 : 0;
+    if (d < 1 || d > kMaxD) return -1;
+    if (!shape_ok(d, n)) return -2;
+    if (!A) return -3;
+    for (int mu = 0; mu < d; mu++)
+        if (!A[mu]) return -3;
+    if (gen) {
+        if (!C) return -4;
+        for (int mu = 0; mu < d; mu++)
+            if (!C[mu]) return -4;
+    }
+    if (!B) return -(4 + sh);
+    if (!X) return -(5 + sh);
+    if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -(6 + sh);
+    if (d > 4) return TSYLV_EUNSUPPORTED;
+    if (work_bytes < solver_z_workspace_bytes(d, n, gen, o)) return -(7 + sh);
+    if (int st = check_opts(o, d)) return st < 0 ? -(8 + sh) : st;
+    if (o.precision != TSYLV_FP64 || o.schedule != 0 || o.nmin < 0) return TSYLV_EUNSUPPORTED;
+    const int shape = shape_of_opts(o, d);
+    Call c;
+    c.d = d;
+    c.gen = gen && d >= 2;
+    c.timeout_ns = static_cast<long long>(o.wait_ms) * 1000000LL;
+    for (int mu = 0; mu < d; mu++) {
+        c.n[mu] = n[mu];
+        c.A[mu] = A[mu];
+        c.C[mu] = gen ? C[mu] : nullptr;
+    }
+    c.B = B;
+    c.X = X;
+    c.base = static_cast<char*>(work);
+    (void)cudaGetLastError();
+    // complex triangular coefficients: no 2x2 blocks, nothing to read back
+    size_t nsub = 0;
+    for (int mu = 0; mu < d; mu++) nsub += static_cast<size_t>(n[mu] - 1);
+    std::vector<uint8_t> sub(nsub + 1, 0);
+    c.plan = get_plan(d, c.n, c.gen, 16, o.split, &sub, o.partition, shape);
+    if (!c.plan) return cuda_fail_msg("plan: pinned host allocation");
+    if (int st = prepare_kernels()) return st;
+    c.timing = o.timing != 0;
+    if (int st = ensure_events(c)) return st;
+    c.persistent = true;
+    {
+        static std::mutex m;
+        static std::map<int, int> occ;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const int key = (dev * 8 + d) * 2 + (c.gen ? 1 : 0);
+        int slots = 0;
+        {
+            std::lock_guard<std::mutex> lk(m);
+            auto it = occ.find(key);
+            if (it != occ.end()) {
+                slots = it->second;
+            } else {
+                int sms = 0;
+                if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+                slots = sms * batched_occupancy_z(d, c.gen);
+                occ[key] = slots;
+            }
+        }
+        c.flow_grid = static_cast<int>(c.plan->ntiles < slots ? c.plan->ntiles : slots);
+    }
+    c.L = make_layout(d, c.n, c.plan->nb, c.gen, 16, c.plan->tab.size());
+    if (c.L.total > work_bytes) return -(7 + sh);
+    const int tag = 65536 | (c.timing ? 2 : 0);
+    if (int st = run_enqueue(*c.plan, make_key(c, tag), o.use_graph != 0, stream, enqueue_z, c)) return st;
+    int herr = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&herr, c.base + c.L.err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_fail(e, "read status");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize after solve");
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->waves = static_cast<int>(c.plan->wave_off.size());
+        info->launches = 2 + d * (c.gen ? 2 : 1) + 2;
+        info->tiles = static_cast<int>(c.plan->ntiles);
+        for (int mu = 0; mu < d; mu++) info->leaf[mu] = shape_cut(d, mu, shape);
+        info->resid = -1;
+        info->norm_A = -1;
+        info->flops = 4.0 * c.plan->flops;  // a complex multiply-add is four real ones
         if (c.timing) {
             float a = -1, b = -1;
             if (cudaEventElapsedTime(&a, c.plan->ev[0], c.plan->ev[3]) != cudaSuccess) a = -1;

@@ -31,6 +31,10 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
 cudaStream_t capture_stream();
 
 size_t solver_tt_workspace_bytes(int d, const int64_t* n, const tsylv_opts& o);
+size_t solver_z_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o);
+int solver_solve_z(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,
+                   double* X, void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
+                   cudaStream_t stream, bool gen);
 int solver_solve_tt(int d, const int64_t* n, const double* const* A, const double* Cm, const double* B, double* X,
                     void* work, size_t work_bytes, const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
 

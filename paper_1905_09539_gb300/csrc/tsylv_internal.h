@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/tsylv.h"
+#include "complex_z.h"
 
 namespace tsylv {
 
@@ -109,6 +110,10 @@ cudaError_t launch_unpack_tensor(const GeomArgs& g, const T* tiles, double* dst,
 template <typename T>
 cudaError_t launch_pack_coef(const GeomArgs& g, int mu, const double* M, T* tiles, bool upper_only,
                              cudaStream_t s);
+// Complex (interleaved) tensors and triangular coefficients.
+cudaError_t launch_pack_tensor_z(const GeomArgs& g, const zd* src, zd* tiles, cudaStream_t s);
+cudaError_t launch_unpack_tensor_z(const GeomArgs& g, const zd* tiles, zd* dst, cudaStream_t s);
+cudaError_t launch_pack_coef_z(const GeomArgs& g, int mu, const zd* M, zd* tiles, cudaStream_t s);
 // out[i] = sub-diagonal entries of every A_mu (concatenated, n_mu - 1 each).
 cudaError_t launch_gather_subdiag(int d, const long long* n, const double* const* A, double* out,
                                   cudaStream_t s);

@@ -40,11 +40,12 @@ struct WaveCfg {
     // stages of the bulk-copy ring: the FP64 updates are bound by the FP64
     // pipes, the FP32 ones by the copy latency (4 stages measured a little
     // faster than 6 for the FP32 Laplace form)
-    static constexpr int NST = sizeof(T) == 8 ? 2 : 4;
+    static constexpr int NST = sizeof(T) >= 8 ? 2 : 4;
     // resident CTAs per SM the persistent kernel is compiled for (register
     // budget): FP64 Laplace d = 3 6 (its shared memory allows 6, registers
     // alone would give 5), FP64 generalized 3 (shared-memory bound), FP32 5 / 4
     static constexpr int MINB = D == 5 ? 3  // d = 5: 1024-entry blocks, shared memory allows 3 CTAs/SM
+                                : sizeof(T) == 16 ? 3  // complex FP64: 16-byte entries
                                 : sizeof(T) == 8 ? (CHAIN ? (D == 3 ? 3 : 4) : (D == 3 ? 6 : 4))
                                                  : (CHAIN ? 4 : 5);
     // The coupled-group inverses depend only on the diagonal blocks: they are
@@ -58,7 +59,9 @@ struct WaveCfg {
     // level sums are parked in the output P, G blocks meanwhile), and the
     // reciprocal diagonal of a 1x1 group sits in its not yet solved X entry.
     static constexpr int MINV = 1024;  // budget (entries) for precomputed coupled-group inverses
-    static constexpr bool INV_EARLY = D >= 2 && !(sizeof(T) == 8 && !CHAIN);
+    // (complex triangular coefficients have no 2x2 blocks, hence no inverses)
+    static constexpr bool CPLX = IsComplex<T>::value;
+    static constexpr bool INV_EARLY = D >= 2 && !CPLX && !(sizeof(T) == 8 && !CHAIN);
     static constexpr bool PIN_IN_RING = CHAIN && sizeof(T) == 8 && 2 * NL * TD <= NST * STAGE;
     static constexpr int UNION = (NST * STAGE > MINV || INV_EARLY) ? NST * STAGE : MINV;
     static constexpr int oStage = 0;
@@ -1040,7 +1043,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         const int mu = tid, b = bs[mu];
         int n = 0, i = 0;
         while (i < b) {
-            if (i + 1 < b && Ds[mu * TC + (i + 1) + TE * i] != T(0)) {
+            if (!C::CPLX && i + 1 < b && Ds[mu * TC + (i + 1) + TE * i] != T(0)) {
                 gs[mu * TE + n] = i; gl[mu * TE + n] = 2;
                 gidx[mu * TE + i] = n; gidx[mu * TE + i + 1] = n;
                 i += 2;
@@ -1091,11 +1094,13 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             for (int mu = 1; mu < D; mu++) t2 *= Es[mu * TC + uq[q][mu] * (TE + 1)];
             const T t1 = Ds[uq[q][0] * (TE + 1)];
             const T diag = dev::add_rn(t1, t2);  // never fused with the product above
-            if (!(fabs(diag) > T(16) * dev::Eps<T>::v * (fabs(t1) + fabs(t2)))) status |= kErrSingular;
+            if (!(fabs(diag) > typename RealOf<T>::type(16) * dev::Eps<T>::v * (fabs(t1) + fabs(t2))))
+                status |= kErrSingular;
             Rd[e] = T(1) / diag;
         } else if (single[q]) {
             // reciprocal of the diagonal entry sum_mu a_mu,ii prod_{eta != mu} c_eta,jj
-            T diag = 0, mag = 0;
+            T diag = 0;
+            typename RealOf<T>::type mag = 0;
 #pragma unroll
             for (int mu = 0; mu < D; mu++) {
                 T tt = Ds[mu * TC + uq[q][mu] * (TE + 1)];
@@ -1107,7 +1112,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
                 diag = dev::add_rn(diag, tt);  // never fused with the product above
                 mag += fabs(tt);
             }
-            if (!(fabs(diag) > T(16) * dev::Eps<T>::v * mag)) status |= kErrSingular;
+            if (!(fabs(diag) > typename RealOf<T>::type(16) * dev::Eps<T>::v * mag)) status |= kErrSingular;
             Rd[e] = T(1) / diag;
         }
     }
@@ -1175,7 +1180,8 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     if constexpr (C::INV_EARLY) {
         const TileSmem<T, D, GENF> smi{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
         for (int i = tid; i < ncg; i += kThreads)
-            if (cg_moff[i] >= 0) status |= group_inverse<T, D, GENF>(smi, cg_list[i], Minv + cg_moff[i]);
+            if constexpr (!C::CPLX)
+                if (cg_moff[i] >= 0) status |= group_inverse<T, D, GENF>(smi, cg_list[i], Minv + cg_moff[i]);
     }
     bool dead = false;
     for (int jj = 0; jj < njob && !dead; jj++) {
@@ -1380,7 +1386,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         for (int e = tid; e < C::NL * TD; e += kThreads) { Pin[e] = T(0); Gin[e] = T(0); }
 
     TileSmem<T, D, GENF> sm{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
-    if constexpr (!C::INV_EARLY)
+    if constexpr (!C::INV_EARLY && !C::CPLX)
         for (int i = tid; i < ncg; i += kThreads)
             if (cg_moff[i] >= 0) status |= group_inverse<T, D, GENF>(sm, cg_list[i], Minv + cg_moff[i]);
     __syncthreads();
@@ -1418,9 +1424,10 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             if (cn > 0) {
                 if constexpr (SOLO) __syncwarp(); else __syncthreads();
                 const int warp = SOLO ? 0 : tid >> 5, nw = SOLO ? 1 : kThreads >> 5;
-                for (int k = warp; k < cn; k += nw)
-                    status |= warp_group<T, D, GENF>(sm, cg_list[c0 + k],
-                                                    cg_moff[c0 + k] >= 0 ? Minv + cg_moff[c0 + k] : nullptr);
+                if constexpr (!C::CPLX)  // no coupled groups with complex triangular coefficients
+                    for (int k = warp; k < cn; k += nw)
+                        status |= warp_group<T, D, GENF>(sm, cg_list[c0 + k],
+                                                        cg_moff[c0 + k] >= 0 ? Minv + cg_moff[c0 + k] : nullptr);
             }
             if constexpr (SOLO) __syncwarp(); else __syncthreads();
         }

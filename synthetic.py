@@ -86,3 +86,47 @@ def batch_shapes(seed, count=512, lo=8, hi=48, d=3):
 def batch(seed, count=512, lo=8, hi=48, d=3, generalized=False):
     shapes = batch_shapes(seed, count, lo, hi, d)
     return [problem([seed, 1 + e], s, generalized=generalized) for e, s in enumerate(shapes)]
+
+
+# ---- the complex-triangular variant (the coefficients of Sec. 2.4 after a
+# complex Schur reduction): complex upper triangular A_mu whose diagonal holds
+# the eigenvalues of the real recipe above -- real part U[1,2]; the pairs a +- b i
+# of 2x2 blocks (walk as above, b ~ U[0.1,1]) as two conjugate diagonal entries --
+# strictly upper entries (N(0,1) + i N(0,1)) / sqrt(2 n); C_mu complex upper
+# triangular with diagonal U[1,2] + i U[-0.5,0.5] and the same strictly upper
+# entries; B, X*: (N(0,1) + i N(0,1)) / sqrt(2).  Streams as problem().
+
+def complex_triangular(rng, n, block_prob=BLOCK_PROB):
+    """Complex upper triangular n x n matrix with the eigenvalue recipe above."""
+    A = np.triu(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), 1) / np.sqrt(2.0 * n)
+    diag = rng.uniform(1.0, 2.0, n).astype(np.complex128)
+    i = 0
+    while i < n - 1:
+        if rng.uniform() < block_prob:
+            a = rng.uniform(1.0, 2.0)
+            b = rng.uniform(0.1, 1.0)
+            diag[i], diag[i + 1] = a + 1j * b, a - 1j * b
+            i += 2
+        else:
+            i += 1
+    A[np.arange(n), np.arange(n)] = diag
+    return np.asfortranarray(A)
+
+
+def complex_upper(rng, n):
+    C = np.triu(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), 1) / np.sqrt(2.0 * n)
+    C[np.arange(n), np.arange(n)] = rng.uniform(1.0, 2.0, n) + 1j * rng.uniform(-0.5, 0.5, n)
+    return np.asfortranarray(C)
+
+
+def complex_problem(seed, shape, generalized=False):
+    """Seeded complex-triangular problem of the given mode sizes."""
+    d = len(shape)
+    kids = np.random.SeedSequence(seed).spawn(2 * d + 2)
+    A = [complex_triangular(np.random.Generator(np.random.PCG64(kids[mu])), shape[mu]) for mu in range(d)]
+    C = None
+    if generalized:
+        C = [complex_upper(np.random.Generator(np.random.PCG64(kids[d + mu])), shape[mu]) for mu in range(d)]
+    rb = np.random.Generator(np.random.PCG64(kids[2 * d]))
+    B = np.asfortranarray((rb.standard_normal(tuple(shape)) + 1j * rb.standard_normal(tuple(shape))) / np.sqrt(2.0))
+    return {"A": A, "C": C, "B": B, "shape": tuple(shape)}

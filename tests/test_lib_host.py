@@ -22,7 +22,7 @@ def lib():
 def _declared():
     src = open(os.path.join(ROOT, "include", "tsylv.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b((?:g?tsylv|gsylvten)_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b((?:z?g?tsylv|gsylvten)_[a-z_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(lib):
@@ -262,3 +262,39 @@ def test_two_term_validation_without_gpu(lib):
             _lib.TSYLV_EUNSUPPORTED, kw
     bad = _lib.default_opts(wait_ms=0)
     assert lib.gsylvten_solve(3, n, fake, P(16), P(16), P(16), P(256), wb, ctypes.byref(bad), None, None) == -9
+
+
+def test_complex_validation_without_gpu(lib):
+    """ztsylv_solve / zgtsylv_solve: bad arguments give -i, d = 5, precisions
+    other than FP64, the wavefront schedule and autotuning give
+    TSYLV_EUNSUPPORTED -- all before any CUDA call."""
+    from paper_1905_09539_gb300 import _lib
+    P = ctypes.c_void_p
+    n = (ctypes.c_int64 * 3)(8, 8, 8)
+    fake = (P * 3)(16, 16, 16)
+    o = _lib.default_opts()
+    w = lib.ztsylv_workspace_bytes(3, n, 0, ctypes.byref(o))
+    wg = lib.ztsylv_workspace_bytes(3, n, 1, ctypes.byref(o))
+    assert w >= 8 ** 3 * 16 and wg > w
+    assert w > lib.tsylv_workspace_bytes(3, n, 0, ctypes.byref(o))
+    assert lib.ztsylv_workspace_bytes(0, n, 0, ctypes.byref(o)) == 0
+    z = lib.ztsylv_solve
+    zg = lib.zgtsylv_solve
+    assert z(0, n, fake, P(16), P(16), P(256), w, ctypes.byref(o), None, None) == -1
+    assert z(3, n, None, P(16), P(16), P(256), w, ctypes.byref(o), None, None) == -3
+    assert z(3, n, fake, None, P(16), P(256), w, ctypes.byref(o), None, None) == -4
+    assert z(3, n, fake, P(16), None, P(256), w, ctypes.byref(o), None, None) == -5
+    assert z(3, n, fake, P(16), P(16), P(257), w, ctypes.byref(o), None, None) == -6
+    assert z(3, n, fake, P(16), P(16), P(256), 16, ctypes.byref(o), None, None) == -7
+    assert zg(3, n, fake, None, P(16), P(16), P(256), wg, ctypes.byref(o), None, None) == -4
+    assert zg(3, n, fake, fake, None, P(16), P(256), wg, ctypes.byref(o), None, None) == -5
+    assert zg(3, n, fake, fake, P(16), P(16), P(256), w if w < wg else 16, ctypes.byref(o), None, None) == -8
+    n5 = (ctypes.c_int64 * 5)(4, 4, 4, 4, 4)
+    f5 = (P * 5)(16, 16, 16, 16, 16)
+    assert z(5, n5, f5, P(16), P(16), P(256), 1 << 30, ctypes.byref(o), None, None) == _lib.TSYLV_EUNSUPPORTED
+    for kw in ({"precision": _lib.TSYLV_FP32_REFINED}, {"schedule": 1}, {"nmin": -1}):
+        ok = _lib.default_opts(**kw)
+        assert z(3, n, fake, P(16), P(16), P(256), 1 << 30, ctypes.byref(ok), None, None) == \
+            _lib.TSYLV_EUNSUPPORTED, kw
+    bad = _lib.default_opts(wait_ms=0)
+    assert z(3, n, fake, P(16), P(16), P(256), 1 << 30, ctypes.byref(bad), None, None) == -8
