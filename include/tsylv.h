@@ -157,6 +157,16 @@ typedef struct tsylv_opts {
                          mode: entry mu in 2..TE bounds the blocks of mode mu, 0
                          takes nmin's bound (TE when nmin <= 0).  Any nonzero entry
                          fixes the shape (no autotuning).  Default all 0.         */
+    int fp64_update;  /* arithmetic of the block updates of a TSYLV_FP64 solve
+                         (ignored by the refined precisions): 0 (default) and 1
+                         FP64 fused multiply-adds; 2 FP64 DMMA tensor-core
+                         instructions (mma m8n8k4, FP64 accumulation), built for
+                         tsylv_solve / gtsylv_solve (and the transposed solves)
+                         at d = 2, 3 on the persistent schedule -- elsewhere
+                         TSYLV_EUNSUPPORTED.  DMMA and FMA share the FP64 units of
+                         this GPU; DMMA measured 0-18% slower, hence not the
+                         default.  Both skip the zero padding of short blocks;
+                         results agree to rounding.                              */
 } tsylv_opts;
 
 typedef struct tsylv_info {

@@ -28,7 +28,8 @@ class Opts(ctypes.Structure):
                 ("residual", ctypes.c_int), ("nmin", ctypes.c_int), ("split", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("host_io", ctypes.c_int), ("timing", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("partition", ctypes.c_int), ("resid_update", ctypes.c_int),
-                ("fuse_step", ctypes.c_int), ("wait_ms", ctypes.c_int), ("leaf", ctypes.c_int * 5)]
+                ("fuse_step", ctypes.c_int), ("wait_ms", ctypes.c_int), ("leaf", ctypes.c_int * 5),
+                ("fp64_update", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -1077,8 +1077,10 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
             if (d[e] > 4) return TSYLV_EUNSUPPORTED;
     const size_t need = solver_batched_workspace_bytes(count, d, n_packed, gen, o);
     if (!need || work_bytes < need) return -11;
-    if (o.split < 0 || o.partition < 0 || o.partition > 1 || o.wait_ms < 1 || o.wait_ms > 600000 || o.nmin < -1)
+    if (o.split < 0 || o.partition < 0 || o.partition > 1 || o.wait_ms < 1 || o.wait_ms > 600000 || o.nmin < -1 ||
+        o.fp64_update < 0 || o.fp64_update > 2)
         return -12;
+    if (o.fp64_update == 2) return TSYLV_EUNSUPPORTED;  // the batch runs FMA block updates
     for (int mu = 0; mu < kMaxD; mu++)
         if (o.leaf[mu] < 0) return -12;
     for (int e = 0; e < count; e++) {

@@ -203,6 +203,36 @@ cudaError_t prepare_batched_pk() {
     return prepare_batched_t<T, 5, false, PK>();
 }
 
+// FP64 DMMA block updates: d = 2, 3 (tile extents 16 and 8 fill the 8 x 8
+// output tiles; the 4-wide tiles of d >= 4 would leave half of each idle)
+cudaError_t launch_batched_dmma(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s) {
+    switch (d * 2 + (gen ? 1 : 0)) {
+        case 4: return launch_batched_t<double, 2, false, kProdDMMA>(a, grid, s);
+        case 5: return launch_batched_t<double, 2, true, kProdDMMA>(a, grid, s);
+        case 6: return launch_batched_t<double, 3, false, kProdDMMA>(a, grid, s);
+        case 7: return launch_batched_t<double, 3, true, kProdDMMA>(a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int batched_occupancy_dmma(int d, bool gen) {
+    switch (d * 2 + (gen ? 1 : 0)) {
+        case 4: return batched_occupancy_t<double, 2, false, kProdDMMA>();
+        case 5: return batched_occupancy_t<double, 2, true, kProdDMMA>();
+        case 6: return batched_occupancy_t<double, 3, false, kProdDMMA>();
+        case 7: return batched_occupancy_t<double, 3, true, kProdDMMA>();
+        default: return 1;
+    }
+}
+
+cudaError_t prepare_batched_dmma() {
+    cudaError_t e;
+    if ((e = prepare_batched_t<double, 2, false, kProdDMMA>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<double, 2, true, kProdDMMA>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<double, 3, false, kProdDMMA>()) != cudaSuccess) return e;
+    return prepare_batched_t<double, 3, true, kProdDMMA>();
+}
+
 }  // namespace
 
 cudaError_t launch_batched_z(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s) {
@@ -274,6 +304,8 @@ cudaError_t launch_batched(int d, bool gen, const BatchArgs& a, int grid, cudaSt
     if constexpr (std::is_same<T, float>::value) {
         if (prod == kProdTF32) return launch_batched_pk<float, kProdTF32>(d, gen, a, grid, s);
         if (prod == kProdBF16) return launch_batched_pk<float, kProdBF16>(d, gen, a, grid, s);
+    } else {
+        if (prod == kProdDMMA) return launch_batched_dmma(d, gen, a, grid, s);
     }
     if (prod != kProdNative) return cudaErrorInvalidValue;
     return launch_batched_pk<T, kProdNative>(d, gen, a, grid, s);
@@ -284,6 +316,8 @@ int batched_occupancy(int d, bool gen, int prod) {
     if constexpr (std::is_same<T, float>::value) {
         if (prod == kProdTF32) return batched_occupancy_pk<float, kProdTF32>(d, gen);
         if (prod == kProdBF16) return batched_occupancy_pk<float, kProdBF16>(d, gen);
+    } else {
+        if (prod == kProdDMMA) return batched_occupancy_dmma(d, gen);
     }
     return batched_occupancy_pk<T, kProdNative>(d, gen);
 }
@@ -294,6 +328,8 @@ cudaError_t prepare_batched() {
     if constexpr (std::is_same<T, float>::value) {
         if (e == cudaSuccess) e = prepare_batched_pk<float, kProdTF32>();
         if (e == cudaSuccess) e = prepare_batched_pk<float, kProdBF16>();
+    } else {
+        if (e == cudaSuccess) e = prepare_batched_dmma();
     }
     return e;
 }

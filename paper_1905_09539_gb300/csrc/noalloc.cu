@@ -74,7 +74,8 @@ int solver_solve_noalloc(int d, const int64_t* n, const double* const* A, const 
     // the FP64 solve, without event timing
     if (int st = check_opts(o, d)) return st < 0 ? -6 : st;
     if (o.precision != TSYLV_FP64) return -6;
-    if (o.timing || o.nmin < 0) return TSYLV_EUNSUPPORTED;  // no event timing, no autotuning runs
+    // no event timing, no autotuning runs; FMA block updates
+    if (o.timing || o.nmin < 0 || o.fp64_update == 2) return TSYLV_EUNSUPPORTED;
     // the largest workspace any admissible block structure needs must fit
     const size_t need = solver_workspace_bytes(d, n, false, o, false);
     if (need == 0) return -2;

@@ -242,7 +242,7 @@ cudaError_t enqueue_waves(const Call& c, const Layout& L, cudaStream_t s) {
         if constexpr (std::is_same<T, zd>::value)
             return launch_batched_z(p.d, p.gen, ba, c.flow_grid, s);
         else
-            return launch_batched<T>(p.d, p.gen, ba, c.flow_grid, s, sizeof(T) == 4 ? c.prod : kProdNative);
+            return launch_batched<T>(p.d, p.gen, ba, c.flow_grid, s, c.prod);
     }
     if constexpr (std::is_same<T, zd>::value) {
         return cudaErrorInvalidValue;  // the complex solve runs the persistent schedule only
@@ -715,7 +715,7 @@ int flow_grid(int elem, int d, bool gen, long long ntiles, int prod = kProdNativ
         } else {
             int sms = 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
-            const int occ = elem == 4 ? batched_occupancy<float>(d, gen, prod) : batched_occupancy<double>(d, gen);
+            const int occ = elem == 4 ? batched_occupancy<float>(d, gen, prod) : batched_occupancy<double>(d, gen, prod);
             slots = sms * occ;
             cache[key] = slots;
         }
@@ -851,7 +851,8 @@ int check_opts(const tsylv_opts& o, int d) {
         (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < -1 ||
         o.schedule < 0 || o.schedule > 1 || o.partition < 0 || o.partition > 1 || o.resid_update < 0 ||
         o.resid_update > 1 || o.fuse_step < 0 || o.fuse_step > 3 || o.timing < 0 || o.timing > 1 ||
-        o.use_graph < 0 || o.use_graph > 1 || o.wait_ms < 1 || o.wait_ms > 600000)
+        o.use_graph < 0 || o.use_graph > 1 || o.wait_ms < 1 || o.wait_ms > 600000 || o.fp64_update < 0 ||
+        o.fp64_update > 2)
         return -1;
     if (o.nmin < -1) return -1;
     for (int mu = 0; mu < kMaxD; mu++)
@@ -863,6 +864,14 @@ int check_opts(const tsylv_opts& o, int d) {
     // measured slower than separate launches
     if (o.fuse_step == 1) return TSYLV_EUNSUPPORTED;
     return 0;
+}
+
+// Block-update arithmetic of a TSYLV_FP64 solve (opts->fp64_update): FMA by
+// default; DMMA on request, built for d = 2, 3 in the Laplace and d-term forms
+// on the persistent schedule (-1: asked for where it is not built).
+int fp64_prod(const tsylv_opts& o, int d, bool persistent) {
+    if (o.fp64_update != 2) return kProdNative;
+    return (d == 2 || d == 3) && persistent ? kProdDMMA : -1;
 }
 
 int shape_of_nmin(int nmin) { return nmin == 0 ? 0 : nmin > 0 ? kShapeFixed + nmin : -1; }
@@ -946,6 +955,7 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     if ((o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) && o.schedule != 0)
         return TSYLV_EUNSUPPORTED;
     if (gen && d > 4) return TSYLV_EUNSUPPORTED;
+    if (o.precision == TSYLV_FP64 && fp64_prod(o, d, o.schedule == 0) < 0) return TSYLV_EUNSUPPORTED;
     const int shape = shape_of_opts(o, d);
     if (shape >= 0) return solve_body(d, n, A, C, B, X, work, work_bytes, o, shape, info, stream, gen, transposed);
     return solve_tuned(d, n, A, C, B, X, work, work_bytes, o, info, stream, gen, transposed);
@@ -970,7 +980,7 @@ int solve_tuned(int d, const int64_t* n, const double* const* A, const double* c
     int dev = 0;
     cudaGetDevice(&dev);
     std::vector<long long> key = {dev, d, gen ? 1 : 0, transposed ? 1 : 0, o.precision, o.schedule, o.partition,
-                                  o.residual, o.fuse_step, o.resid_update};
+                                  o.residual, o.fuse_step, o.resid_update, o.fp64_update};
     for (int mu = 0; mu < d; mu++) key.push_back(n[mu]);
     int shape = -1;
     {
@@ -1027,6 +1037,10 @@ int solve_body(int d, const int64_t* n, const double* const* A, const double* co
     c.flip = transposed;
     c.df = o.residual == TSYLV_RESID_DF64;
     c.prod = o.precision == TSYLV_TF32_REFINED ? kProdTF32 : o.precision == TSYLV_BF16_REFINED ? kProdBF16 : kProdNative;
+    if (!refined) {
+        c.prod = fp64_prod(o, d, o.schedule == 0);
+        if (c.prod < 0) return TSYLV_EUNSUPPORTED;
+    }
     c.timeout_ns = static_cast<long long>(o.wait_ms) * 1000000LL;
     for (int mu = 0; mu < d; mu++) {
         c.n[mu] = n[mu];
@@ -1258,7 +1272,7 @@ int solver_solve_tt(int d, const int64_t* n, const double* const* A, const doubl
     if (d < 2 || d > 4) return TSYLV_EUNSUPPORTED;
     if (work_bytes < solver_tt_workspace_bytes(d, n, o)) return -8;
     if (int st = check_opts(o, d)) return st < 0 ? -9 : st;
-    if (o.precision != TSYLV_FP64 || o.schedule != 0 || o.nmin < 0) return TSYLV_EUNSUPPORTED;
+    if (o.precision != TSYLV_FP64 || o.schedule != 0 || o.nmin < 0 || o.fp64_update == 2) return TSYLV_EUNSUPPORTED;
     const int shape = shape_of_opts(o, d);
     Call c;
     c.d = d;
@@ -1372,7 +1386,7 @@ int solver_solve_z(int d, const int64_t* n, const double* const* A, const double
     if (d > 4) return TSYLV_EUNSUPPORTED;
     if (work_bytes < solver_z_workspace_bytes(d, n, gen, o)) return -(7 + sh);
     if (int st = check_opts(o, d)) return st < 0 ? -(8 + sh) : st;
-    if (o.precision != TSYLV_FP64 || o.schedule != 0 || o.nmin < 0) return TSYLV_EUNSUPPORTED;
+    if (o.precision != TSYLV_FP64 || o.schedule != 0 || o.nmin < 0 || o.fp64_update == 2) return TSYLV_EUNSUPPORTED;
     const int shape = shape_of_opts(o, d);
     Call c;
     c.d = d;

@@ -49,7 +49,7 @@ enum : int { kErrSingular = 1, kErrNonfinite = 2, kErrTimeout = 4, kErrBounds = 
 enum : int { kFormLaplace = 0, kFormDTerm = 1, kFormTwoTerm = 2 };
 
 // Arithmetic used for the block products of a wavefront.
-enum ProductKind : int { kProdNative = 0, kProdTF32 = 1, kProdBF16 = 2 };
+enum ProductKind : int { kProdNative = 0, kProdTF32 = 1, kProdBF16 = 2, kProdDMMA = 3 };
 
 // Parameter block of one wavefront launch (passed by value).
 struct WaveArgs {

@@ -92,8 +92,13 @@ struct WaveCfg {
 
 // acc[q] += (S x_MU M)[e_q] for the thread's elements e_q = tid + q*kThreads:
 //   y(.., i, ..) = sum_k M(i, k) S(.., k, ..),  M a TE x TE column-major tile.
+// Padding is skipped: k runs over the source block's extent ks in mode MU
+// (the tile beyond it is zero), and element slots q whose whole warp holds
+// only padded elements of the target block (bit q of `live` clear) are not
+// computed (their sums stay zero, as the products of zero padding would be).
 template <typename T, int D, int MU, int EPT>
-__device__ __forceinline__ void prod_acc(T (&acc)[EPT], const T* __restrict__ M, const T* __restrict__ S) {
+__device__ __forceinline__ void prod_acc(T (&acc)[EPT], const T* __restrict__ M, const T* __restrict__ S, int ks,
+                                         unsigned live) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int st = ipow(TE, MU);
@@ -101,19 +106,25 @@ __device__ __forceinline__ void prod_acc(T (&acc)[EPT], const T* __restrict__ M,
     for (int q = 0; q < EPT; q++) {
         const int e = threadIdx.x + q * kThreads;
         if ((TD % kThreads) != 0 && e >= TD) continue;
+        if (!((live >> q) & 1u)) continue;  // uniform over the warp
         const int i = row_of<TE, st>(e);
         const int base = e - i * st;
         T s = acc[q];
+        if (ks == TE) {
 #pragma unroll
-        for (int k = 0; k < TE; k++) s = dev::fmadd(M[i + TE * k], S[base + k * st], s);
+            for (int k = 0; k < TE; k++) s = dev::fmadd(M[i + TE * k], S[base + k * st], s);
+        } else {
+            for (int k = 0; k < ks; k++) s = dev::fmadd(M[i + TE * k], S[base + k * st], s);
+        }
         acc[q] = s;
     }
 }
 
-// acc[q] += (S1 x_MU M1 + S2 x_MU M2)[e_q]
+// acc[q] += (S1 x_MU M1 + S2 x_MU M2)[e_q], padding skipped as above
 template <typename T, int D, int MU, int EPT>
 __device__ __forceinline__ void prod_acc2(T (&acc)[EPT], const T* __restrict__ M1, const T* __restrict__ S1,
-                                          const T* __restrict__ M2, const T* __restrict__ S2) {
+                                          const T* __restrict__ M2, const T* __restrict__ S2, int ks,
+                                          unsigned live) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int st = ipow(TE, MU);
@@ -121,13 +132,21 @@ __device__ __forceinline__ void prod_acc2(T (&acc)[EPT], const T* __restrict__ M
     for (int q = 0; q < EPT; q++) {
         const int e = threadIdx.x + q * kThreads;
         if ((TD % kThreads) != 0 && e >= TD) continue;
+        if (!((live >> q) & 1u)) continue;
         const int i = row_of<TE, st>(e);
         const int base = e - i * st;
         T s = acc[q];
+        if (ks == TE) {
 #pragma unroll
-        for (int k = 0; k < TE; k++) {
-            s = dev::fmadd(M1[i + TE * k], S1[base + k * st], s);
-            s = dev::fmadd(M2[i + TE * k], S2[base + k * st], s);
+            for (int k = 0; k < TE; k++) {
+                s = dev::fmadd(M1[i + TE * k], S1[base + k * st], s);
+                s = dev::fmadd(M2[i + TE * k], S2[base + k * st], s);
+            }
+        } else {
+            for (int k = 0; k < ks; k++) {
+                s = dev::fmadd(M1[i + TE * k], S1[base + k * st], s);
+                s = dev::fmadd(M2[i + TE * k], S2[base + k * st], s);
+            }
         }
         acc[q] = s;
     }
@@ -137,7 +156,7 @@ __device__ __forceinline__ void prod_acc2(T (&acc)[EPT], const T* __restrict__ M
 template <typename T, int D, int FM, int L>
 struct JobCompute {
     template <int NACC, int EPT>
-    __device__ __forceinline__ static void run(T (&acc)[NACC][EPT], const T* stage) {
+    __device__ __forceinline__ static void run(T (&acc)[NACC][EPT], const T* stage, int ks, unsigned live) {
         constexpr int TE = tile_extent(D);
         constexpr int TD = ipow(TE, D);
         constexpr int TC = TE * TE;
@@ -150,26 +169,26 @@ struct JobCompute {
             constexpr int MU = D - 1 - L;            // modes d-1, ..., 0
             if constexpr (MU >= 1) {
                 // L^Q_mu += Q_{mu+1} x A_mu  (Q_d = X)
-                prod_acc<T, D, MU, EPT>(acc[L], M1, S1);
+                prod_acc<T, D, MU, EPT>(acc[L], M1, S1, ks, live);
             } else {
                 // L_0 += Q_1 x C + X x A_1
-                prod_acc2<T, D, 0, EPT>(acc[NACC - 1], M1, S2, M2, S1);
+                prod_acc2<T, D, 0, EPT>(acc[NACC - 1], M1, S2, M2, S1, ks, live);
             }
         } else if constexpr (!C::GEN) {
-            prod_acc<T, D, L, EPT>(acc[0], M1, S1);  // Laplace: level L = mode L
+            prod_acc<T, D, L, EPT>(acc[0], M1, S1, ks, live);  // Laplace: level L = mode L
         } else {
             constexpr int MU = D - 1 - L;            // modes d-1, ..., 0
             if constexpr (L == 0) {
                 // L^P_{d-1} += X x C,  L^G_{d-1} += X x A
-                prod_acc<T, D, MU, EPT>(acc[0], M1, S1);
-                prod_acc<T, D, MU, EPT>(acc[1], M2, S1);
+                prod_acc<T, D, MU, EPT>(acc[0], M1, S1, ks, live);
+                prod_acc<T, D, MU, EPT>(acc[1], M2, S1, ks, live);
             } else if constexpr (MU >= 1) {
                 // L^P_mu += P_{mu+1} x C,  L^G_mu += G_{mu+1} x C + P_{mu+1} x A
-                prod_acc<T, D, MU, EPT>(acc[2 * L], M1, S1);
-                prod_acc2<T, D, MU, EPT>(acc[2 * L + 1], M1, S2, M2, S1);
+                prod_acc<T, D, MU, EPT>(acc[2 * L], M1, S1, ks, live);
+                prod_acc2<T, D, MU, EPT>(acc[2 * L + 1], M1, S2, M2, S1, ks, live);
             } else {
                 // L_0 += G_1 x C_0 + P_1 x A_0
-                prod_acc2<T, D, 0, EPT>(acc[NACC - 1], M1, S2, M2, S1);
+                prod_acc2<T, D, 0, EPT>(acc[NACC - 1], M1, S2, M2, S1, ks, live);
             }
         }
     }
@@ -177,12 +196,12 @@ struct JobCompute {
 
 template <typename T, int D, int FM, int L = 0>
 __device__ __forceinline__ void dispatch_job(int level, T (&acc)[WaveCfg<T, D, FM>::NACC][WaveCfg<T, D, FM>::EPT],
-                                             const T* stage) {
+                                             const T* stage, int ks, unsigned live) {
     if constexpr (L < D) {
         if (level == L)
-            JobCompute<T, D, FM, L>::run(acc, stage);
+            JobCompute<T, D, FM, L>::run(acc, stage, ks, live);
         else
-            dispatch_job<T, D, FM, L + 1>(level, acc, stage);
+            dispatch_job<T, D, FM, L + 1>(level, acc, stage, ks, live);
     }
 }
 
@@ -820,8 +839,10 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     constexpr int TE = C::TE, TD = C::TD, TC = C::TC, EPT = C::EPT, NACC = C::NACC;
     constexpr bool GEN = C::GEN, TT = C::TT, CHAIN = C::CHAIN;
     constexpr bool TCU = PK != kProdNative;  // tensor-core updates
-    static_assert(!TCU || sizeof(T) == 4, "tensor-core block updates serve the FP32 solve");
+    static_assert(!TCU || (PK == kProdDMMA ? sizeof(T) == 8 && !IsComplex<T>::value : sizeof(T) == 4),
+                  "TF32 / BF16 tensor-core block updates serve the FP32 solve, DMMA the FP64 solve");
     using Q = MmaCfg<D, TCU ? PK : kProdTF32>;
+    using QF = typename Q::F;
     constexpr int NS = GEN ? NACC : D;        // accumulator slots of the fragments
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* sbase = reinterpret_cast<T*>(smem_raw);
@@ -964,7 +985,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     for (int s = 0; s < NACC; s++)
 #pragma unroll
         for (int q = 0; q < EPT; q++) acc[s][q] = T(0);
-    float cfr[TCU ? NS : 1][TCU ? Q::UPW : 1][4];
+    QF cfr[TCU ? NS : 1][TCU ? Q::UPW : 1][Q::NF];
     if constexpr (TCU) {
 #pragma unroll
         for (int s = 0; s < NS; s++)
@@ -1116,6 +1137,13 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             Rd[e] = T(1) / diag;
         }
     }
+    // element slots of the block updates whose whole warp holds padding only
+    unsigned live = 0;
+#pragma unroll
+    for (int q = 0; q < EPT; q++)
+        if (__ballot_sync(0xffffffffu, okq[q])) live |= 1u << q;
+    // the tensor-core variant's output tiles that hold padding only
+    const unsigned tlive = TCU ? mma_tile_live<D, TCU ? PK : kProdTF32>(bs) : 0u;
     int nsum = 0;
 #pragma unroll
     for (int mu = 0; mu < D; mu++) nsum += ng[mu];
@@ -1194,10 +1222,13 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         }
         int L, Jp;
         job(j0 + jj, L, Jp);
+        // padding skipped where the FP64 pipes bound the updates (FP64,
+        // complex); the latency-bound FP32 updates run full tiles
+        const int ks = sizeof(T) >= 8 ? a.bsize[CHAIN ? D - 1 - L : L][Jp] : TE;
         if constexpr (TCU)
-            mma_dispatch<D, GEN, PK, NS>(L, cfr, reinterpret_cast<const float*>(stage + stg * C::STAGE));
+            mma_dispatch<D, GEN, PK, NS>(L, cfr, reinterpret_cast<const QF*>(stage + stg * C::STAGE), ks, tlive);
         else
-            dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE);
+            dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE, ks, sizeof(T) >= 8 ? live : ~0u);
         // every thread is done reading the stage (the barrier orders those
         // reads before the copies that refill it, as for a consumer-release
         // mbarrier arrival)
@@ -1216,7 +1247,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     for (int q = 0; q < NST; q++) uses[q] += static_cast<uint32_t>((njob - q + NST - 1) / NST);
     if constexpr (TCU) {
         // fragments -> element order (shared memory) -> the thread's own elements
-        mma_store<D, GEN, PK, NS>(cfr, reinterpret_cast<float*>(red));
+        mma_store<D, GEN, PK, NS>(cfr, reinterpret_cast<QF*>(red));
 #pragma unroll
         for (int s = 0; s < NACC; s++)
 #pragma unroll

@@ -91,9 +91,9 @@ def test_option_validation_without_gpu(lib):
 
     for kw in ({"fuse_step": 4}, {"fuse_step": -1}, {"schedule": 2}, {"partition": 2}, {"resid_update": 2},
                {"precision": 9}, {"tol": 0.0}, {"split": -1}, {"max_refine": -1}, {"residual": 7},
-               {"wait_ms": 0}, {"wait_ms": 600001}, {"nmin": -2}):
+               {"wait_ms": 0}, {"wait_ms": 600001}, {"nmin": -2}, {"fp64_update": 3}, {"fp64_update": -1}):
         assert st(**kw) == -8, kw
-    for kw in ({"host_io": 1}, {"fuse_step": 1}, {"nmin": 17}, {"nmin": 1},
+    for kw in ({"host_io": 1}, {"fuse_step": 1}, {"nmin": 17}, {"nmin": 1}, {"fp64_update": 2, "schedule": 1},
                {"precision": _lib.TSYLV_TF32_REFINED, "schedule": 1},
                {"precision": _lib.TSYLV_BF16_REFINED, "schedule": 1}):
         assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
@@ -298,3 +298,5 @@ def test_complex_validation_without_gpu(lib):
             _lib.TSYLV_EUNSUPPORTED, kw
     bad = _lib.default_opts(wait_ms=0)
     assert z(3, n, fake, P(16), P(16), P(256), 1 << 30, ctypes.byref(bad), None, None) == -8
+    dm = _lib.default_opts(fp64_update=2)
+    assert z(3, n, fake, P(16), P(16), P(256), 1 << 30, ctypes.byref(dm), None, None) == _lib.TSYLV_EUNSUPPORTED
