@@ -25,6 +25,10 @@
 namespace tsylv {
 
 enum ApplyKind : int { kApplyLaplace = 0, kApplyFirst = 1, kApplyMiddle = 2, kApplyFinal = 3 };
+// arithmetic of an apply: 0 FP64, 1 DF64, 2 FP32
+// 3: DF64 arithmetic on FP32 sources (the source's low word is zero: the
+// first refinement step's iterate s D with s a power of two)
+enum ApplyMode : int { kModeF64 = 0, kModeDF = 1, kModeF32 = 2, kModeDFh = 3 };
 
 struct ApplyArgs {
     int nb[kMaxD];

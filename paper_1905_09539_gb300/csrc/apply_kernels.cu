@@ -116,6 +116,7 @@ cudaError_t launch_apply_batched(int d, int mode, const ApplyArgs* eqs, const in
         if (mode == kModeF64) return launch_apply_batched_t<DD, kModeF64>(eqs, jobs, njobs, s);   \
         if (mode == kModeDF) return launch_apply_batched_t<DD, kModeDF>(eqs, jobs, njobs, s);     \
         if (mode == kModeF32) return launch_apply_batched_t<DD, kModeF32>(eqs, jobs, njobs, s);   \
+        if (mode == kModeDFh) return launch_apply_batched_t<DD, kModeDFh>(eqs, jobs, njobs, s);   \
     }
     TSYLV_APPLY_B(1)
     TSYLV_APPLY_B(2)
@@ -131,7 +132,8 @@ cudaError_t prepare_apply_batched() {
 #define TSYLV_PREP_B(DD)                                                                              \
     if (e == cudaSuccess) e = prepare_apply_batched_t<DD, kModeF64>();                                \
     if (e == cudaSuccess) e = prepare_apply_batched_t<DD, kModeDF>();                                 \
-    if (e == cudaSuccess) e = prepare_apply_batched_t<DD, kModeF32>();
+    if (e == cudaSuccess) e = prepare_apply_batched_t<DD, kModeF32>();                                \
+    if (e == cudaSuccess) e = prepare_apply_batched_t<DD, kModeDFh>();
     TSYLV_PREP_B(1)
     TSYLV_PREP_B(2)
     TSYLV_PREP_B(3)

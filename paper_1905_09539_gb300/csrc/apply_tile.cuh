@@ -38,11 +38,6 @@ __device__ __forceinline__ double df_to_double(float h, float l) { return static
 namespace tsylv {
 namespace apply_detail {
 
-// arithmetic of an apply: 0 FP64, 1 DF64, 2 FP32
-// 3: DF64 arithmetic on FP32 sources (the source's low word is zero: the
-// first refinement step's iterate s D with s a power of two)
-enum : int { kModeF64 = 0, kModeDF = 1, kModeF32 = 2, kModeDFh = 3 };
-
 template <int D, int M>
 struct ApplyCfg {
     static constexpr int TE = tile_extent(D);

@@ -659,7 +659,8 @@ struct RefExtra {
     size_t Bt = 0, Xt = 0, Rt = 0, set[2][2] = {}, part = 0, xpart = 0, nrm = 0, nA = 0;
     size_t tab = 0, tab_bytes = 0;  // geo64, geoX, args[2][4][count], ajobs, tile_eq, tile_off, norm tables
     size_t o_geo64 = 0, o_geoX = 0, o_args = 0, o_ajobs = 0, o_teq = 0, o_toff = 0, o_noff = 0, o_nn = 0, o_nup = 0;
-    size_t coef = 0;                 // FP64 coefficient tiles
+    size_t coef = 0, coef_bytes = 0;  // FP64 coefficient tiles
+    size_t cfh = 0, cfl = 0;          // their float-pair split (the first step's DF64 residual)
     size_t total = 0;
 };
 
@@ -684,7 +685,10 @@ RefExtra make_ref_extra(size_t start, int count, int d, bool gen, long long tile
     E.xpart = take(tiles * 8);
     E.nrm = take(static_cast<size_t>(count) * 4 * 8);
     E.nA = take(static_cast<size_t>(nmats) * 8);
-    E.coef = take(static_cast<size_t>(ctiles) * tc * 8 * (g ? 2 : 1) + static_cast<size_t>(count) * d * 2 * 256);
+    E.coef_bytes = static_cast<size_t>(ctiles) * tc * 8 * (g ? 2 : 1) + static_cast<size_t>(count) * d * 2 * 256;
+    E.coef = take(E.coef_bytes);
+    E.cfh = take(E.coef_bytes / 2);
+    E.cfl = take(E.coef_bytes / 2);
     size_t t = 0;
     auto tt = [&](size_t bytes) {
         const size_t at = t;
@@ -693,7 +697,7 @@ RefExtra make_ref_extra(size_t start, int count, int d, bool gen, long long tile
     };
     E.o_geo64 = tt(count * sizeof(BatchGeom));
     E.o_geoX = tt(count * sizeof(BatchGeom));
-    E.o_args = tt(static_cast<size_t>(2) * kMaxD * count * sizeof(ApplyArgs));
+    E.o_args = tt(static_cast<size_t>(3) * kMaxD * count * sizeof(ApplyArgs));
     E.o_ajobs = tt(tiles * sizeof(int2));
     E.o_teq = tt(tiles * sizeof(int));
     E.o_toff = tt((count + 1) * sizeof(long long));
@@ -777,7 +781,8 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
     std::vector<unsigned char> xt(E.tab_bytes, 0);
     BatchGeom* g64 = reinterpret_cast<BatchGeom*>(xt.data() + E.o_geo64);
     BatchGeom* gX = reinterpret_cast<BatchGeom*>(xt.data() + E.o_geoX);
-    ApplyArgs* args = reinterpret_cast<ApplyArgs*>(xt.data() + E.o_args);  // [mode 0 full, 1 update][level][eq]
+    // [mode 0 full FP64, 1 FP32 update, 2 first step in DF64 on the FP32 correction][level][eq]
+    ApplyArgs* args = reinterpret_cast<ApplyArgs*>(xt.data() + E.o_args);
     int2* ajobs = reinterpret_cast<int2*>(xt.data() + E.o_ajobs);
     int* teq = reinterpret_cast<int*>(xt.data() + E.o_teq);
     long long* toff = reinterpret_cast<long long*>(xt.data() + E.o_toff);
@@ -829,8 +834,14 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
         BatchGeom x = a;
         x.X = Xt + t0 * td;
         gX[e] = x;
-        // residual applies: [0] full FP64 R = B - A(X), [1] FP32 update R -= s A(D)
-        for (int mode = 0; mode < 2; mode++) {
+        // residual applies: [0] full FP64 R = B - A(X), [1] FP32 update R -= s A(D),
+        // [2] the first step (X = s D exactly): R = B - s A(D) in DF64 on the
+        // FP32 correction D, the coefficients as float pairs, the d-term
+        // form's intermediates as float-pair planes of the FP64 sets
+        auto cf = [&](const void* p64, size_t region) -> const void* {
+            return base + region + static_cast<size_t>(static_cast<const char*>(p64) - (base + E.coef)) / 2;
+        };
+        for (int mode = 0; mode < 3; mode++) {
             const int levels = g ? dd : 1;
             int cur = 0;
             for (int lv = 0; lv < levels; lv++) {
@@ -838,11 +849,18 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
                 for (int mu = 0; mu < dd; mu++) {
                     r.nb[mu] = q.nb[mu];
                     r.tstride[mu] = q.tstride[mu];
-                    r.A[mu] = mode == 0 ? a.At[mu] : w32[e].At[mu];
-                    r.C[mu] = g ? (mode == 0 ? a.Ct[mu] : w32[e].Ct[mu]) : nullptr;
+                    if (mode == 2) {
+                        r.A[mu] = cf(a.At[mu], E.cfh);
+                        r.Al[mu] = cf(a.At[mu], E.cfl);
+                        r.C[mu] = g ? cf(a.Ct[mu], E.cfh) : nullptr;
+                        r.Cl[mu] = g ? cf(a.Ct[mu], E.cfl) : nullptr;
+                    } else {
+                        r.A[mu] = mode == 0 ? a.At[mu] : w32[e].At[mu];
+                        r.C[mu] = g ? (mode == 0 ? a.Ct[mu] : w32[e].Ct[mu]) : nullptr;
+                    }
                 }
                 r.ntiles = q.ntiles;
-                r.B = mode == 0 ? Bt + t0 * td : Rt + t0 * td;
+                r.B = mode == 1 ? Rt + t0 * td : Bt + t0 * td;
                 r.R = Rt + t0 * td;
                 r.scale = mode == 0 ? nullptr : nrm + 4 * e;
                 r.part = part + 2 * t0;
@@ -852,6 +870,13 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
                 auto setp = [&](int kk, int j) -> void* {
                     return base + E.set[kk][j] + static_cast<size_t>(t0) * td * 8;
                 };
+                // float-pair planes of set kk, j: the high words, then the low words
+                auto seth = [&](int kk, int j) -> void* {
+                    return base + E.set[kk][j] + static_cast<size_t>(t0) * td * 4;
+                };
+                auto setl = [&](int kk, int j) -> void* {
+                    return base + E.set[kk][j] + static_cast<size_t>(T) * td * 4 + static_cast<size_t>(t0) * td * 4;
+                };
                 if (!g) {
                     r.kind = kApplyLaplace;
                     r.s1 = xs;
@@ -859,17 +884,35 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
                     r.kind = kApplyFirst;
                     r.mode = dd - 1;
                     r.s1 = xs;
-                    r.o1 = setp(0, 0);
-                    r.o2 = setp(0, 1);
+                    if (mode == 2) {
+                        r.o1 = seth(0, 0);
+                        r.o1l = setl(0, 0);
+                        r.o2 = seth(0, 1);
+                        r.o2l = setl(0, 1);
+                    } else {
+                        r.o1 = setp(0, 0);
+                        r.o2 = setp(0, 1);
+                    }
                     cur = 0;
                 } else {
                     const int l = dd - 1 - lv;  // mode of this level
                     r.kind = l == 0 ? kApplyFinal : kApplyMiddle;
                     r.mode = l;
-                    r.s1 = setp(cur, 0);
-                    r.s2 = setp(cur, 1);
-                    r.o1 = setp(1 - cur, 0);
-                    r.o2 = setp(1 - cur, 1);
+                    if (mode == 2) {
+                        r.s1 = seth(cur, 0);
+                        r.s1l = setl(cur, 0);
+                        r.s2 = seth(cur, 1);
+                        r.s2l = setl(cur, 1);
+                        r.o1 = seth(1 - cur, 0);
+                        r.o1l = setl(1 - cur, 0);
+                        r.o2 = seth(1 - cur, 1);
+                        r.o2l = setl(1 - cur, 1);
+                    } else {
+                        r.s1 = setp(cur, 0);
+                        r.s2 = setp(cur, 1);
+                        r.o1 = setp(1 - cur, 0);
+                        r.o2 = setp(1 - cur, 1);
+                    }
                     cur = 1 - cur;
                 }
                 args[(static_cast<size_t>(mode) * kMaxD + lv) * count + e] = r;
@@ -922,6 +965,8 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
         TRYB(cudaMemcpyAsync(dt, t_pin_tab.ptr + L.tab_bytes, E.tab_bytes, cudaMemcpyHostToDevice, s));
         TRYB(launch_batch_pack<float>(dgeo32, djobs, 0, dcjobs, ncj, nullptr, A_pool, C_pool, s));
         TRYB(launch_batch_pack<double>(dgeo64, djobs, njobs, dcjobs, ncj, B_pool, A_pool, C_pool, s));
+        TRYB(launch_split(reinterpret_cast<const double*>(base + E.coef), reinterpret_cast<float*>(base + E.cfh),
+                          reinterpret_cast<float*>(base + E.cfl), static_cast<long long>(E.coef_bytes / 8), s));
         TRYB(cudaMemsetAsync(Xt, 0, static_cast<size_t>(T) * td * 8, s));
         TRYB(cudaMemcpyAsync(Rt, Bt, static_cast<size_t>(T) * td * 8, cudaMemcpyDeviceToDevice, s));
         TRYB(launch_tile_stats(Rt, part, T, td, s));
@@ -931,7 +976,7 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
         TRYB(cudaMemcpyAsync(hn, nrm, static_cast<size_t>(count) * 4 * 8, cudaMemcpyDeviceToHost, s));
         return cudaMemcpyAsync(hA, nA, static_cast<size_t>(nm) * 8, cudaMemcpyDeviceToHost, s);
     };
-    auto iterate = [&](bool update, cudaStream_t s) -> cudaError_t {
+    auto iterate = [&](bool update, bool first, cudaStream_t s) -> cudaError_t {
         TRYB(launch_bscale(Rt, X32, dteq, nrm, T * td, td, s));
         TRYB(cudaMemsetAsync(ctl, 0, 8 * sizeof(int) + static_cast<size_t>(count) * sizeof(int), s));
         TRYB(cudaMemsetAsync(base + L.flags, 0, static_cast<size_t>(T) * sizeof(int), s));
@@ -946,10 +991,12 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
         TRYB(launch_batched<float>(dd, gen, ba, grid, s));
         TRYB(launch_bupdate(Xt, X32, dteq, nrm, xpart, T, td, s));
         const int levels = g ? dd : 1;
-        const int mode = update ? 1 : 0;
-        for (int lv = 0; lv < levels; lv++)
-            TRYB(launch_apply_batched(dd, update ? 2 : 0, dargs + (static_cast<size_t>(mode) * kMaxD + lv) * count,
-                                      dajobs, static_cast<int>(T), s));
+        const int mode = update ? 1 : first ? 2 : 0;
+        for (int lv = 0; lv < levels; lv++) {
+            const int am = update ? kModeF32 : !first ? kModeF64 : lv == 0 ? kModeDFh : kModeDF;
+            TRYB(launch_apply_batched(dd, am, dargs + (static_cast<size_t>(mode) * kMaxD + lv) * count, dajobs,
+                                      static_cast<int>(T), s));
+        }
         TRYB(launch_breduce(part, xpart, dtoff, count, nrm, s));
         return cudaMemcpyAsync(hn, nrm, static_cast<size_t>(count) * 4 * 8, cudaMemcpyDeviceToHost, s);
     };
@@ -990,8 +1037,9 @@ int solver_batched_refined(int count, const int* d, const int64_t* n_packed, con
     bool update = false;
     for (int it = 0; it < std::max(1, o.max_refine); it++) {
         if (o.resid_update == 0 && it > 0 && prev <= 1e-5) update = true;
-        if (int st = run_graph(*plan, key(update ? 2 : 1), ug, stream,
-                               [&](cudaStream_t s) { return iterate(update, s); }, "batched refinement: step"))
+        const bool first = it == 0;
+        if (int st = run_graph(*plan, key(update ? 2 : first ? 4 : 1), ug, stream,
+                               [&](cudaStream_t s) { return iterate(update, first, s); }, "batched refinement: step"))
             return st;
         if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "batched refinement: synchronize");
         iters = it + 1;

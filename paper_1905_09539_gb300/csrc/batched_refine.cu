@@ -16,12 +16,15 @@ inline int grid_for(long long total) {
     return static_cast<int>(b);
 }
 
-// r32 = r / s_e, s_e the power of two at or above max|r_e| (nrm[4 e + 1])
+// r32 = r / s_e, s_e the power of two at or above max|r_e| (nrm[4 e + 1]):
+// one CTA per block at a time, the exact reciprocal of s_e taken once per block
 __global__ void k_bscale(const double* __restrict__ r, float* __restrict__ r32, const int* __restrict__ tile_eq,
-                         const double* __restrict__ nrm, long long n, int td) {
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        r32[i] = static_cast<float>(r[i] * (1.0 / dev::step_scale(nrm[4 * tile_eq[i / td] + 1])));
+                         const double* __restrict__ nrm, long long ntiles, int td) {
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const double inv = 1.0 / dev::step_scale(nrm[4 * tile_eq[t] + 1]);  // a power of two: exact
+        const double* rt = r + t * td;
+        float* ot = r32 + t * td;
+        for (int e = threadIdx.x; e < td; e += blockDim.x) ot[e] = static_cast<float>(rt[e] * inv);
     }
 }
 
@@ -88,10 +91,64 @@ __global__ void k_breduce(const double* __restrict__ part, const double* __restr
     }
 }
 
-// ||M||_2 estimates of many n x n column-major matrices (one CTA each): 30
-// steps of power iteration on M^T M in FP32 over the structurally nonzero
-// part (upper triangle, plus the first subdiagonal when upper == 0).  The
-// estimates only scale the stopping test.
+// ||M||_2 estimates of many n x n column-major matrices: 30 steps of power
+// iteration on M^T M in FP32 over the structurally nonzero part (upper
+// triangle, plus the first subdiagonal when upper == 0).  The estimates only
+// scale the stopping test.
+//   k_bnorm2_warp: n <= kNormWarpN, one warp per matrix, the matrix held in
+//   shared memory as floats (the batch's small equations);
+//   k_bnorm2: any n, one CTA per matrix, reading the matrix from memory.
+constexpr int kNormWarpN = 48;  // four warps' matrices within 48 KB of shared memory
+constexpr int kNormWarps = 4;
+
+__device__ __forceinline__ int norm_j0(int i, int up) { return up ? i : (i > 0 ? i - 1 : 0); }
+
+__global__ void __launch_bounds__(32 * kNormWarps) k_bnorm2_warp(const double* __restrict__ pool,
+                                                                 const long long* __restrict__ off,
+                                                                 const long long* __restrict__ nmat,
+                                                                 const int* __restrict__ upper, int count,
+                                                                 int nmax, double* __restrict__ out) {
+    extern __shared__ float shw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float* Ms = shw + static_cast<size_t>(wid) * (nmax * nmax + 2 * nmax);
+    float* v = Ms + nmax * nmax;
+    float* w = v + nmax;
+    for (int mat = blockIdx.x * kNormWarps + wid; mat < count; mat += gridDim.x * kNormWarps) {
+        const double* M = pool + off[mat];
+        const int n = static_cast<int>(nmat[mat]);
+        const int up = upper[mat];
+        for (int k = lane; k < n * n; k += 32) Ms[k] = static_cast<float>(M[k]);
+        for (int i = lane; i < n; i += 32) v[i] = 1.0f + 0.01f * (i % 7);
+        __syncwarp();
+        float lam = 0.f;
+        for (int it = 0; it < 30; it++) {
+            for (int i = lane; i < n; i += 32) {  // w = M v
+                float acc = 0.f;
+                for (int j = norm_j0(i, up); j < n; j++) acc = fmaf(Ms[i + n * j], v[j], acc);
+                w[i] = acc;
+            }
+            __syncwarp();
+            float part = 0.f;
+            for (int j = lane; j < n; j += 32) {  // v = M^T w
+                float acc = 0.f;
+                const int iend = up ? j : (j + 1 < n ? j + 1 : n - 1);
+                for (int i = 0; i <= iend; i++) acc = fmaf(Ms[i + n * j], w[i], acc);
+                v[j] = acc;
+                part += acc * acc;
+            }
+            for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            const float nv = sqrtf(part);
+            lam = nv;
+            const float inv = nv > 0.f ? 1.0f / nv : 0.f;
+            __syncwarp();
+            for (int j = lane; j < n; j += 32) v[j] *= inv;
+            __syncwarp();
+        }
+        if (lane == 0) out[mat] = sqrt(static_cast<double>(lam));
+        __syncwarp();
+    }
+}
+
 __global__ void k_bnorm2(const double* __restrict__ pool, const long long* __restrict__ off,
                          const long long* __restrict__ nmat, const int* __restrict__ upper, int count,
                          double* __restrict__ out) {
@@ -109,8 +166,7 @@ __global__ void k_bnorm2(const double* __restrict__ pool, const long long* __res
         for (int it = 0; it < 30; it++) {
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 float s = 0.f;
-                const int j0 = up ? i : (i > 0 ? i - 1 : 0);
-                for (int j = j0; j < n; j++) s = fmaf(static_cast<float>(M[i + static_cast<long long>(n) * j]), v[j], s);
+                for (int j = norm_j0(i, up); j < n; j++) s = fmaf(static_cast<float>(M[i + static_cast<long long>(n) * j]), v[j], s);
                 w[i] = s;
             }
             __syncthreads();
@@ -146,7 +202,9 @@ __global__ void k_bnorm2(const double* __restrict__ pool, const long long* __res
 
 cudaError_t launch_bscale(const double* r, float* r32, const int* tile_eq, const double* nrm, long long n, int td,
                           cudaStream_t s) {
-    k_bscale<<<grid_for(n), 256, 0, s>>>(r, r32, tile_eq, nrm, n, td);
+    const long long ntiles = n / td;
+    const int g = static_cast<int>(ntiles < 152LL * 16 ? (ntiles > 0 ? ntiles : 1) : 152LL * 16);
+    k_bscale<<<g, 128, 0, s>>>(r, r32, tile_eq, nrm, ntiles, td);
     return cudaGetLastError();
 }
 
@@ -166,8 +224,16 @@ cudaError_t launch_breduce(const double* part, const double* xpart, const long l
 
 cudaError_t launch_bnorm2(const double* pool, const long long* off, const long long* nmat, const int* upper, int count,
                           long long nmax, double* out, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (nmax <= kNormWarpN) {
+        const int nm = static_cast<int>(nmax);
+        const size_t sm = static_cast<size_t>(kNormWarps) * (nm * nm + 2 * nm) * sizeof(float);
+        const int g = (count + kNormWarps - 1) / kNormWarps;
+        k_bnorm2_warp<<<g, 32 * kNormWarps, sm, s>>>(pool, off, nmat, upper, count, nm, out);
+        return cudaGetLastError();
+    }
     const int g = count < 152 * 8 ? count : 152 * 8;
-    k_bnorm2<<<g > 0 ? g : 1, 256, 2 * nmax * sizeof(float), s>>>(pool, off, nmat, upper, count, out);
+    k_bnorm2<<<g, 256, 2 * nmax * sizeof(float), s>>>(pool, off, nmat, upper, count, out);
     return cudaGetLastError();
 }
 

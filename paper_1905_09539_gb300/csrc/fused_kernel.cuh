@@ -13,7 +13,7 @@ namespace tsylv {
 template <int D>
 struct FusedCfg {
     using CW = WaveCfg<float, D, false>;
-    using CA = apply_detail::ApplyCfg<D, apply_detail::kModeDF>;
+    using CA = apply_detail::ApplyCfg<D, kModeDF>;
     static constexpr size_t body = CW::smem > CA::smem ? CW::smem : CA::smem;
     static constexpr size_t oBarW = (body + 15) / 16 * 16;
     static constexpr size_t oBarA = oBarW + 8 * CW::NST;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) k_refine2(const Refine2Args f) {
             __syncthreads();
             if (threadIdx.x == 0) dev::publish(const_cast<int*>((kind == 0 ? w1 : w2).ready) + t, 1, nullptr);
         } else if (kind == 1) {
-            if (alive) apply_detail::apply_tile<D, apply_detail::kModeDFh>(f.r1, t, smem_raw, barA, usesA);
+            if (alive) apply_detail::apply_tile<D, kModeDFh>(f.r1, t, smem_raw, barA, usesA);
             __syncthreads();
             // right-hand side of the second solve: R1 / s (exact scaling)
             const double* R = f.r1.R + t * TD;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kThreads) k_refine2(const Refine2Args f) {
             __syncthreads();
             if (threadIdx.x == 0) dev::publish(f.r1done + t, 1, nullptr);
         } else {
-            if (alive) apply_detail::apply_tile<D, apply_detail::kModeF32>(f.r2, t, smem_raw, barA, usesA);
+            if (alive) apply_detail::apply_tile<D, kModeF32>(f.r2, t, smem_raw, barA, usesA);
             __syncthreads();
         }
     }

@@ -1062,14 +1062,16 @@ int solve_body(int d, const int64_t* n, const double* const* A, const double* co
     c.persistent = o.schedule == 0;
     if (c.persistent) c.flow_grid = flow_grid(refined ? 4 : 8, d, c.gen, c.plan->ntiles, c.prod);
     // pipelined first two steps: always (2), or by default (0) when the solve is
-    // latency-bound, i.e. its largest wavefront has fewer blocks than a
-    // persistent launch has resident CTAs (measured: faster there, slower on
-    // wavefronts that fill the GPU)
+    // latency-bound, i.e. its largest wavefront has fewer than 5 blocks per SM
+    // (measured: faster there, slower on wavefronts that fill the GPU)
     bool want_pipe = o.fuse_step == 2;
     if (o.fuse_step == 0 && refined && c.plan->n_rjobs > 0) {
         int wmax = 0;
         for (int w : c.plan->wave_cnt) wmax = std::max(wmax, w);
-        want_pipe = wmax < flow_grid(4, d, false, 1LL << 40, c.prod);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        want_pipe = wmax < 5 * sms;
     }
     c.pipe = refined && c.persistent && !c.gen && c.df && want_pipe && d >= 2 && c.plan->n_rjobs > 0 &&
              o.max_refine >= 2;

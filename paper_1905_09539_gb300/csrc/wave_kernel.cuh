@@ -38,16 +38,18 @@ struct WaveCfg {
     static constexpr int NL = CHAIN ? D - 1 : 0;  // stored levels l = 1..d-1
     static constexpr int STAGE = 2 * TD + 2 * TC;
     // stages of the bulk-copy ring: the FP64 updates are bound by the FP64
-    // pipes, the FP32 ones by the copy latency (4 stages measured a little
-    // faster than 6 for the FP32 Laplace form)
-    static constexpr int NST = sizeof(T) >= 8 ? 2 : 4;
+    // pipes; the FP32 solves of d = 3 measured faster with 2 stages and more
+    // resident CTAs than with 4 (other orders keep 4)
+    static constexpr int NST = (sizeof(T) >= 8 || D == 3) ? 2 : 4;
     // resident CTAs per SM the persistent kernel is compiled for (register
     // budget): FP64 Laplace d = 3 6 (its shared memory allows 6, registers
-    // alone would give 5), FP64 generalized 3 (shared-memory bound), FP32 5 / 4
+    // alone would give 5), FP64 generalized 3 (shared-memory bound); FP32
+    // d = 3 8 (Laplace) / 5 (generalized), other orders 5 / 4
     static constexpr int MINB = D == 5 ? 3  // d = 5: 1024-entry blocks, shared memory allows 3 CTAs/SM
                                 : sizeof(T) == 16 ? 3  // complex FP64: 16-byte entries
                                 : sizeof(T) == 8 ? (CHAIN ? (D == 3 ? 3 : 4) : (D == 3 ? 6 : 4))
-                                                 : (CHAIN ? 4 : 5);
+                                : D == 3 ? (CHAIN ? 5 : 8)
+                                         : (CHAIN ? 4 : 5);
     // The coupled-group inverses depend only on the diagonal blocks: they are
     // computed when the block starts, off the critical path, in a region of
     // their own (INV_EARLY), except for the FP64 Laplace form, whose shared
