@@ -15,6 +15,7 @@ struct NormArgs {
 
 cudaError_t launch_tile_stats(const double* x, double* part, long long nt, int td, cudaStream_t s);
 cudaError_t launch_split(const double* x, float* h, float* l, long long n, cudaStream_t s);
+cudaError_t prepare_norm2();  // shared-memory limit of the norm estimate (before any capture)
 cudaError_t launch_scale_to_f32(const double* r, float* r32, const double* nrm, long long n, cudaStream_t s);
 cudaError_t launch_update_x(double* x, const float* d32, const double* nrm, float* xh, float* xl, double* xpart,
                             long long n, int td, cudaStream_t s);

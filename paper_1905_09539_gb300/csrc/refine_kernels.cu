@@ -107,6 +107,15 @@ __global__ void k_reduce(const double* __restrict__ part, const double* __restri
 // ||M||_2 estimate of an n x n column-major matrix (structural zeros below
 // the first subdiagonal ignored): 30 steps of power iteration on M^T M in
 // FP32, one CTA per matrix.  The estimate only scales the stopping test.
+// When it fits (n <= kNormSmemN) the matrix is first staged in shared memory
+// as floats, packed by columns (upper triangle, entry (i, j), i <= j, at
+// j (j + 1) / 2 + i) plus the first subdiagonal, so that the iterations read
+// no global memory; larger matrices are read from global memory.
+constexpr int kNormSmemN = 320;
+constexpr size_t norm_smem_bytes(int n) {
+    return (static_cast<size_t>(n) * (n + 1) / 2 + 3 * static_cast<size_t>(n)) * sizeof(float);
+}
+
 __global__ void k_norm2(NormArgs a, double* __restrict__ out) {
     const int mat = blockIdx.x;
     const double* M = a.M[mat];
@@ -115,23 +124,45 @@ __global__ void k_norm2(NormArgs a, double* __restrict__ out) {
     extern __shared__ float shf[];
     float* v = shf;          // n
     float* w = shf + n;      // n
+    const bool staged = n <= kNormSmemN;
+    float* sub = shf + 2 * n;  // n: M(j + 1, j)
+    float* P = shf + 3 * n;    // packed upper triangle
     __shared__ float red[32];
+    if (staged) {
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {  // coalesced, independent loads
+            const int i = idx % n, j = idx / n;
+            if (i <= j) P[static_cast<size_t>(j) * (j + 1) / 2 + i] = static_cast<float>(M[idx]);
+        }
+        for (int j = threadIdx.x; j < n; j += blockDim.x)
+            sub[j] = (!upper && j + 1 < n) ? static_cast<float>(M[j + 1 + static_cast<long long>(n) * j]) : 0.f;
+    }
     for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.0f + 0.01f * (i % 7);
     __syncthreads();
     float lam = 0.f;
     for (int it = 0; it < 30; it++) {
         for (int i = threadIdx.x; i < n; i += blockDim.x) {  // w = M v
             float s = 0.f;
-            const int j0 = upper ? i : (i > 0 ? i - 1 : 0);
-            for (int j = j0; j < n; j++) s = fmaf(static_cast<float>(M[i + static_cast<long long>(n) * j]), v[j], s);
+            if (staged) {
+                if (i > 0) s = sub[i - 1] * v[i - 1];
+                for (int j = i; j < n; j++) s = fmaf(P[static_cast<size_t>(j) * (j + 1) / 2 + i], v[j], s);
+            } else {
+                const int j0 = upper ? i : (i > 0 ? i - 1 : 0);
+                for (int j = j0; j < n; j++) s = fmaf(static_cast<float>(M[i + static_cast<long long>(n) * j]), v[j], s);
+            }
             w[i] = s;
         }
         __syncthreads();
         float part = 0.f;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {  // v = M^T w
             float s = 0.f;
-            const int iend = upper ? j : (j + 1 < n ? j + 1 : n - 1);
-            for (int i = 0; i <= iend; i++) s = fmaf(static_cast<float>(M[i + static_cast<long long>(n) * j]), w[i], s);
+            if (staged) {
+                const float* col = P + static_cast<size_t>(j) * (j + 1) / 2;
+                for (int i = 0; i <= j; i++) s = fmaf(col[i], w[i], s);
+                if (j + 1 < n) s = fmaf(sub[j], w[j + 1], s);
+            } else {
+                const int iend = upper ? j : (j + 1 < n ? j + 1 : n - 1);
+                for (int i = 0; i <= iend; i++) s = fmaf(static_cast<float>(M[i + static_cast<long long>(n) * j]), w[i], s);
+            }
             v[j] = s;
             part += s * s;
         }
@@ -213,8 +244,14 @@ cudaError_t launch_reduce(const double* part, const double* xpart, long long nt,
 }
 
 cudaError_t launch_norm2(const NormArgs& a, int count, int nmax, double* out, cudaStream_t s) {
-    k_norm2<<<count, 256, 2 * nmax * sizeof(float), s>>>(a, out);
+    const size_t sm = nmax <= kNormSmemN ? norm_smem_bytes(nmax) : 2 * static_cast<size_t>(nmax) * sizeof(float);
+    k_norm2<<<count, 256, sm, s>>>(a, out);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_norm2() {
+    return cudaFuncSetAttribute(k_norm2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(norm_smem_bytes(kNormSmemN)));
 }
 
 }  // namespace tsylv

@@ -764,6 +764,7 @@ int prepare_kernels() {
         if (e == cudaSuccess) e = prepare_batched_tt();
         if (e == cudaSuccess) e = prepare_batched_z();
         if (e == cudaSuccess) e = prepare_refine2();
+        if (e == cudaSuccess) e = prepare_norm2();
         if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
         prepared[dev] = true;
     }
