@@ -243,6 +243,48 @@ int gtsylv_solve_transposed(int d, const int64_t* n, const double* const* A,
                             size_t work_bytes, const tsylv_opts* opts, tsylv_info* info,
                             cudaStream_t stream);
 
+/* Solve plans: repeated FP64 solves of Eq. (2.2) or of the d-term form (forward
+ * or transposed) with the same mode sizes, the same coefficient pointers and
+ * the same 2x2 block structure of the A_mu, queued without host
+ * synchronisation.  tsylv_solve synchronises its stream twice per call (it
+ * reads the 2x2 structure back to plan the block partition, and reads the
+ * status word); a plan reads the structure once, at creation, and an
+ * execution only enqueues work, so a caller can queue solves back to back and
+ * overlap them with its own copies and kernels.
+ *
+ * tsylv_plan_create: d, n, A, C (NULL: the Laplace form), transposed (0 / 1),
+ *   work / work_bytes (the workspace of tsylv_workspace_bytes(d, n, C != NULL,
+ *   opts); it only has to be valid during the call and during executions),
+ *   opts (TSYLV_FP64 only; nmin >= 0 or leaf bounds -- no autotuning; no event
+ *   timing; fp64_update as for tsylv_solve).  Reads the structure (one
+ *   synchronisation of `stream`), builds the partition and schedule, and keeps
+ *   a copy of the structure on the device (one byte per subdiagonal entry,
+ *   allocated here).  Returns 0 and sets *plan, -i for a bad i-th argument
+ *   (-4: A violates the quasi-triangular structure), TSYLV_EUNSUPPORTED or
+ *   TSYLV_ECUDA.
+ * tsylv_plan_execute: enqueues one whole solve on `stream` -- coefficient
+ *   tiles packed from the plan's A_mu (C_mu) pointers, whose VALUES may change
+ *   between executions, right-hand side packed from B, the persistent solve,
+ *   the unpack into X -- and returns without waiting.  If status is not NULL
+ *   (a device int), the execution writes its TSYLV status code there when the
+ *   stream reaches it: 0, 1 singular, 2 non-finite, 5 wait timed out, 4 device
+ *   self-check, -3 the A_mu no longer have the plan's 2x2 structure (checked
+ *   on the device at every execution; the solution is then meaningless).  The
+ *   return value only reports the enqueue: 0, -1 null plan, -2 null B, -3 null
+ *   X, -4 work not 256-byte aligned, -5 work_bytes too small,
+ *   TSYLV_EUNSUPPORTED on another device than the plan's, TSYLV_ECUDA.
+ *   Executions sharing a workspace must be ordered (one stream, or events):
+ *   the workspace holds the block tensors of the solve in flight.  The first
+ *   execution for a given (B, X, work) builds a CUDA graph (host work only).
+ * tsylv_plan_destroy: frees the plan (after the last execution has finished:
+ *   it synchronises the device). */
+typedef struct tsylv_plan_s* tsylv_plan;
+int tsylv_plan_create(tsylv_plan* plan, int d, const int64_t* n, const double* const* A, const double* const* C,
+                      int transposed, void* work, size_t work_bytes, const tsylv_opts* opts, cudaStream_t stream);
+int tsylv_plan_execute(tsylv_plan plan, const double* B, double* X, void* work, size_t work_bytes, int* status,
+                       cudaStream_t stream);
+void tsylv_plan_destroy(tsylv_plan plan);
+
 /* The complex-triangular variant (Sec. 2.4: the paper's experiments reduce
  * every coefficient to complex Schur form, which is upper triangular): the
  * Laplace form Eq. (2.2) (ztsylv_solve) or the d-term generalized form

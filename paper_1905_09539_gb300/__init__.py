@@ -23,7 +23,7 @@ __all__ = ["tsylv_solve", "gtsylv_solve", "gsylvten_solve", "ztsylv_solve", "tsy
            "tsylv_residual", "tsylv_backward", "tsylv_solve_batched", "BatchPools", "solve", "fortran", "TsylvError",
            "Opts", "Info", "default_opts", "TSYLV_FP64", "TSYLV_FP32_REFINED", "TSYLV_TF32_REFINED",
            "TSYLV_BF16_REFINED", "TSYLV_RESID_DF64", "TSYLV_RESID_FP64", "workspace", "solve_general",
-           "reduce_coefficients", "transform", "selftest_wait_timeout", "empty_fortran"]
+           "reduce_coefficients", "transform", "selftest_wait_timeout", "empty_fortran", "SolvePlan"]
 
 
 class TsylvError(RuntimeError):
@@ -206,6 +206,63 @@ def ztsylv_solve(A, B, C=None, X=None, *, opts=None, check=True, stream=None, in
     if check and st != 0:
         raise TsylvError(st, "ztsylv_solve")
     return X, st
+
+
+class SolvePlan:
+    """Repeated FP64 solves with fixed coefficients (tsylv_plan_*): the 2x2
+    structure of the A_mu is read once here; solve() only enqueues work on
+    the stream (no host synchronisation) and returns X and a device int32
+    tensor that receives the execution's status code.  The coefficient
+    tensors must stay alive (and keep their 2x2 structure) while the plan is
+    used; their values may change between executions."""
+
+    def __init__(self, A, C=None, *, transposed=False, opts=None, stream=None, **kw):
+        lib = load()
+        _check_cuda(*A, *(C or []))
+        self._o = _opts(opts, kw)
+        self._A, pa = _mats(A)
+        self._C, pc = (None, None) if C is None else _mats(C)
+        self.d = len(A)
+        self.shape = tuple(int(a.shape[0]) for a in self._A)
+        self.device = self._A[0].device
+        n = _dims(self.shape)
+        nbytes = lib.tsylv_workspace_bytes(self.d, n, 1 if C is not None else 0, ctypes.byref(self._o))
+        if nbytes == 0:
+            raise ValueError("SolvePlan: invalid or unsupported shape %s" % (self.shape,))
+        self._work = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        st = lib.tsylv_plan_create(ctypes.byref(h), self.d, n, pa, pc, 1 if transposed else 0,
+                                   self._work.data_ptr(), self._work.numel(), ctypes.byref(self._o), _stream(stream))
+        if st != 0:
+            raise TsylvError(st, "tsylv_plan_create")
+        self._h = h
+
+    def solve(self, B, X=None, status=None, *, stream=None):
+        """Enqueue one solve of B (column-major float64, the plan's shape)."""
+        lib = load()
+        B = fortran(B)
+        if tuple(B.shape) != self.shape:
+            raise ValueError("B must have the plan's shape %s" % (self.shape,))
+        if X is None:
+            X = empty_fortran(B.shape, B.device)
+        if status is None:
+            status = torch.zeros(1, dtype=torch.int32, device=B.device)
+        st = lib.tsylv_plan_execute(self._h, B.data_ptr(), X.data_ptr(), self._work.data_ptr(), self._work.numel(),
+                                    status.data_ptr(), _stream(stream))
+        if st != 0:
+            raise TsylvError(st, "tsylv_plan_execute")
+        return X, status
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().tsylv_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tsylv_solve_transposed(A, G, L=None, *, opts=None, check=True, stream=None, info=None, **kw):

@@ -51,7 +51,8 @@ EXPORTS = [
     "tsylv_backward", "tsylv_batched_workspace_bytes", "tsylv_solve_batched", "tsylv_last_error",
     "tsylv_solve_noalloc", "tsylv_residual_workspace_bytes", "tsylv_selftest_wait_timeout",
     "tsylv_transform", "tsylv_transform_workspace_bytes", "gsylvten_solve", "gsylvten_workspace_bytes",
-    "ztsylv_solve", "zgtsylv_solve", "ztsylv_workspace_bytes",
+    "ztsylv_solve", "zgtsylv_solve", "ztsylv_workspace_bytes", "tsylv_plan_create", "tsylv_plan_execute",
+    "tsylv_plan_destroy",
 ]
 
 _lib = None
@@ -112,6 +113,12 @@ def load(path=LIB_PATH):
     lib.ztsylv_solve.restype = I
     lib.zgtsylv_solve.argtypes = [I, I64P, P, P, P, P, P, S, OP, IP, P]
     lib.zgtsylv_solve.restype = I
+    lib.tsylv_plan_create.argtypes = [ctypes.POINTER(P), I, I64P, P, P, I, P, S, OP, P]
+    lib.tsylv_plan_create.restype = I
+    lib.tsylv_plan_execute.argtypes = [P, P, P, P, S, P, P]
+    lib.tsylv_plan_execute.restype = I
+    lib.tsylv_plan_destroy.argtypes = [P]
+    lib.tsylv_plan_destroy.restype = None
     for f in ("tsylv_solve", "gtsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
               "tsylv_residual", "tsylv_backward", "tsylv_solve_batched"):
         getattr(lib, f).restype = I

@@ -90,6 +90,24 @@ extern "C" int gtsylv_solve_transposed(int d, const int64_t* n, const double* co
     return solver_solve(d, n, A, C, G, L, work, work_bytes, opts, info, stream, true, true);
 }
 
+extern "C" int tsylv_plan_create(tsylv_plan* plan, int d, const int64_t* n, const double* const* A,
+                                 const double* const* C, int transposed, void* work, size_t work_bytes,
+                                 const tsylv_opts* opts, cudaStream_t stream) {
+    if (!plan) return -1;
+    if (transposed != 0 && transposed != 1) return -6;
+    void* h = nullptr;
+    const int st = plan_create(&h, d, n, A, C, transposed != 0, work, work_bytes, opts, stream);
+    *plan = static_cast<tsylv_plan>(h);
+    return st;
+}
+
+extern "C" int tsylv_plan_execute(tsylv_plan plan, const double* B, double* X, void* work, size_t work_bytes,
+                                  int* status, cudaStream_t stream) {
+    return plan_execute(plan, B, X, work, work_bytes, status, stream);
+}
+
+extern "C" void tsylv_plan_destroy(tsylv_plan plan) { plan_destroy(plan); }
+
 extern "C" size_t ztsylv_workspace_bytes(int d, const int64_t* n, int generalized, const tsylv_opts* opts) {
     tsylv_opts o;
     if (opts) o = *opts; else tsylv_opts_default(&o);

@@ -15,6 +15,49 @@ int batched_occupancy_t();
 
 namespace {
 
+// Column-major offset, in its equation's tensor, of in-block element e of a
+// block with extents sz and first indices st (mode sizes n), the order D
+// fixed at compile time (the tile extent a constant: no integer division);
+// false for padding.
+template <int D>
+__device__ __forceinline__ bool tile_elem(int e, const int (&sz)[kMaxD], const long long (&st)[kMaxD],
+                                          const long long* n, long long& off) {
+    constexpr int TE = tile_extent(D);
+    off = 0;
+    long long gst = 1;
+    bool valid = true;
+#pragma unroll
+    for (int mu = 0; mu < D; mu++) {
+        const int i = e % TE;
+        e /= TE;
+        valid &= i < sz[mu];
+        off += (st[mu] + i) * gst;
+        gst *= n[mu];
+    }
+    return valid;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void pack_tile(T* __restrict__ dst, const double* __restrict__ B, const BatchGeom& g,
+                                          const int (&sz)[kMaxD], const long long (&st)[kMaxD]) {
+    constexpr int TD = ipow(tile_extent(D), D);
+    for (int e = threadIdx.x; e < TD; e += blockDim.x) {
+        long long off;
+        const bool v = tile_elem<D>(e, sz, st, g.n, off);
+        dst[e] = v ? static_cast<T>(B[g.xoff + off]) : T(0);
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void unpack_tile(const T* __restrict__ src, double* __restrict__ X, const BatchGeom& g,
+                                            const int (&sz)[kMaxD], const long long (&st)[kMaxD]) {
+    constexpr int TD = ipow(tile_extent(D), D);
+    for (int e = threadIdx.x; e < TD; e += blockDim.x) {
+        long long off;
+        if (tile_elem<D>(e, sz, st, g.n, off)) X[g.xoff + off] = static_cast<double>(src[e]);
+    }
+}
+
 // CTA b < njobs: block tensor tile of job b (B -> tile, zero padding);
 // CTA njobs + c: coefficient tile c (A, and C for the generalized form;
 // entries that the structure makes zero are written as zero unread).
@@ -27,26 +70,20 @@ __global__ void k_batch_pack(const BatchGeom* __restrict__ geo, const BatchJob* 
             const BatchJob jb = jobs[b];
             const BatchGeom& g = geo[jb.eq];
             const int d = g.d, te = tile_extent(d), td = ipow(te, d);
-            int I[kMaxD], sz[kMaxD];
-            long long st[kMaxD];
+            int sz[kMaxD] = {};
+            long long st[kMaxD] = {};
             for (int mu = 0; mu < d; mu++) {
-                I[mu] = static_cast<int>((jb.tile / g.tstride[mu]) % g.nb[mu]);
-                sz[mu] = g.size[mu][I[mu]];
-                st[mu] = g.start[mu][I[mu]];
+                const int I = static_cast<int>((jb.tile / g.tstride[mu]) % g.nb[mu]);
+                sz[mu] = g.size[mu][I];
+                st[mu] = g.start[mu][I];
             }
             T* dst = static_cast<T*>(g.X) + static_cast<long long>(jb.tile) * td;
-            for (int e = threadIdx.x; e < td; e += blockDim.x) {
-                int rem = e;
-                long long off = 0, gst = 1;
-                bool valid = true;
-                for (int mu = 0; mu < d; mu++) {
-                    const int i = rem % te;
-                    rem /= te;
-                    if (i >= sz[mu]) valid = false;
-                    off += (st[mu] + i) * gst;
-                    gst *= g.n[mu];
-                }
-                dst[e] = valid ? static_cast<T>(B[g.xoff + off]) : T(0);
+            switch (d) {
+                case 1: pack_tile<T, 1>(dst, B, g, sz, st); break;
+                case 2: pack_tile<T, 2>(dst, B, g, sz, st); break;
+                case 3: pack_tile<T, 3>(dst, B, g, sz, st); break;
+                case 4: pack_tile<T, 4>(dst, B, g, sz, st); break;
+                default: pack_tile<T, kMaxD>(dst, B, g, sz, st); break;
             }
         } else {
             const BatchCoefJob cj = cjobs[b - njobs];
@@ -82,26 +119,20 @@ __global__ void k_batch_unpack(const BatchGeom* __restrict__ geo, const BatchJob
         const BatchJob jb = jobs[b];
         const BatchGeom& g = geo[jb.eq];
         const int d = g.d, te = tile_extent(d), td = ipow(te, d);
-        int sz[kMaxD];
-        long long st[kMaxD];
+        int sz[kMaxD] = {};
+        long long st[kMaxD] = {};
         for (int mu = 0; mu < d; mu++) {
             const int I = static_cast<int>((jb.tile / g.tstride[mu]) % g.nb[mu]);
             sz[mu] = g.size[mu][I];
             st[mu] = g.start[mu][I];
         }
         const T* src = static_cast<const T*>(g.X) + static_cast<long long>(jb.tile) * td;
-        for (int e = threadIdx.x; e < td; e += blockDim.x) {
-            int rem = e;
-            long long off = 0, gst = 1;
-            bool valid = true;
-            for (int mu = 0; mu < d; mu++) {
-                const int i = rem % te;
-                rem /= te;
-                if (i >= sz[mu]) valid = false;
-                off += (st[mu] + i) * gst;
-                gst *= g.n[mu];
-            }
-            if (valid) X[g.xoff + off] = static_cast<double>(src[e]);
+        switch (d) {
+            case 1: unpack_tile<T, 1>(src, X, g, sz, st); break;
+            case 2: unpack_tile<T, 2>(src, X, g, sz, st); break;
+            case 3: unpack_tile<T, 3>(src, X, g, sz, st); break;
+            case 4: unpack_tile<T, 4>(src, X, g, sz, st); break;
+            default: unpack_tile<T, kMaxD>(src, X, g, sz, st); break;
         }
     }
 }

@@ -109,6 +109,31 @@ __global__ void k_gather_subdiag(const SubdiagArgs a, double* out) {
     }
 }
 
+__global__ void k_check_subdiag(const SubdiagArgs a, const uint8_t* __restrict__ pat, int* err) {
+    long long base = 0;
+    bool bad = false;
+    for (int mu = 0; mu < a.d; mu++) {
+        const long long m = a.n[mu];
+        for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i + 1 < m;
+             i += static_cast<long long>(gridDim.x) * blockDim.x)
+            if ((a.A[mu][(i + 1) + m * i] != 0.0) != (pat[base + i] != 0)) bad = true;
+        base += m > 0 ? m - 1 : 0;
+    }
+    if (bad) atomicOr(err, kErrStructure);
+}
+
+// the order of map_err on the host: device self-check, structure, timeout,
+// singular, non-finite
+__global__ void k_status_word(const int* __restrict__ err, int* __restrict__ status) {
+    const int e = *err;
+    *status = (e & kErrBounds)      ? TSYLV_ECUDA
+              : (e & kErrStructure) ? -3
+              : (e & kErrTimeout)   ? TSYLV_ETIMEOUT
+              : (e & kErrSingular)  ? TSYLV_ESINGULAR
+              : (e & kErrNonfinite) ? TSYLV_ENONFINITE
+                                    : TSYLV_OK;
+}
+
 inline int grid_for(long long total) {
     long long b = (total + 255) / 256;
     if (b > 152LL * 32) b = 152LL * 32;
@@ -151,6 +176,25 @@ cudaError_t launch_gather_subdiag(int d, const long long* n, const double* const
         if (n[mu] > mx) mx = n[mu];
     }
     k_gather_subdiag<<<grid_for(mx), 256, 0, s>>>(a, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_subdiag(int d, const long long* n, const double* const* A, const uint8_t* pat, int* err,
+                                 cudaStream_t s) {
+    SubdiagArgs a{};
+    a.d = d;
+    long long mx = 1;
+    for (int mu = 0; mu < d; mu++) {
+        a.n[mu] = n[mu];
+        a.A[mu] = A[mu];
+        if (n[mu] > mx) mx = n[mu];
+    }
+    k_check_subdiag<<<grid_for(mx), 256, 0, s>>>(a, pat, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_status_word(const int* err, int* status, cudaStream_t s) {
+    k_status_word<<<1, 1, 0, s>>>(err, status);
     return cudaGetLastError();
 }
 

@@ -164,6 +164,8 @@ struct Call {
     double* X = nullptr;
     const double* Xin = nullptr;  // tsylv_residual: the X to evaluate
     double* Rout = nullptr;       // tsylv_residual: output R
+    const uint8_t* pat = nullptr;  // plan execution: the plan's subdiagonal pattern (device)
+    int* status_out = nullptr;     // plan execution: device int for the status code
     char* base = nullptr;
     std::shared_ptr<Plan> plan;
     Layout L;
@@ -278,6 +280,31 @@ cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
     TRY(mark(c, 2, s));
     TRY(launch_unpack_tensor<double>(g, Xt, c.X, s));
     return mark(c, 3, s);
+}
+
+// A plan execution: the FP64 solve, preceded by the check of the
+// coefficients' 2x2 structure against the plan's and followed by the status
+// code written to the caller's device int.
+cudaError_t enqueue_plan_fp64(const Call& c, cudaStream_t s) {
+    const Plan& p = *c.plan;
+    char* base = c.base;
+    int* err = reinterpret_cast<int*>(base + c.L.err);
+    TRY(mark(c, 0, s));
+    TRY(cudaMemsetAsync(err, 0, 64, s));
+    TRY(launch_check_subdiag(p.d, c.n, c.A, c.pat, err, s));
+    GeomArgs g = geom_of(p, c.L, base, c.flip);
+    TRY(cudaMemcpyAsync(base + c.L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int mu = 0; mu < p.d; mu++) {
+        TRY(launch_pack_coef<double>(g, mu, c.A[mu], reinterpret_cast<double*>(base + c.L.At[mu]), false, s));
+        if (p.gen)
+            TRY(launch_pack_coef<double>(g, mu, c.C[mu], reinterpret_cast<double*>(base + c.L.Ct[mu]), true, s));
+    }
+    double* Xt = reinterpret_cast<double*>(base + c.L.X);
+    TRY(launch_pack_tensor<double>(g, c.B, Xt, 1.0, s));
+    TRY(enqueue_waves<double>(c, c.L, s));
+    TRY(launch_unpack_tensor<double>(g, Xt, c.X, s));
+    if (c.status_out) TRY(launch_status_word(err, c.status_out, s));
+    return cudaSuccess;
 }
 
 // The paper's two-term form Eq. (3.1), FP64: A_mu tiles of every mode (the
@@ -813,6 +840,7 @@ std::vector<const void*> make_key(const Call& c, int tag) {
     key.push_back(c.X);
     key.push_back(c.Xin);
     key.push_back(c.Rout);
+    key.push_back(c.status_out);
     key.push_back(c.base);
     key.push_back(reinterpret_cast<const void*>(static_cast<uintptr_t>(tag)));
     key.push_back(reinterpret_cast<const void*>(static_cast<uintptr_t>(c.timeout_ns)));
@@ -1681,6 +1709,134 @@ int solver_backward(int d, const int64_t* n, const double* const* A, const doubl
         info->launches = si.launches + launches;
     }
     return st;
+}
+
+// ------------------------------------------------------------------ plans
+
+struct SolvePlan {
+    int d = 0;
+    long long n[kMaxD] = {};
+    const double* A[kMaxD] = {};
+    const double* C[kMaxD] = {};
+    bool gen = false, flip = false;
+    int prod = kProdNative;
+    int flow_grid = 0;
+    bool use_graph = true;
+    long long timeout_ns = kTimeoutNs;
+    std::shared_ptr<Plan> plan;
+    Layout L;
+    int dev = 0;
+    uint8_t* pat = nullptr;  // device: A_mu(i + 1, i) != 0, modes back to back (unflipped)
+};
+
+int plan_create(void** out, int d, const int64_t* n, const double* const* A, const double* const* C, bool flip,
+                void* work, size_t work_bytes, const tsylv_opts* opts, cudaStream_t stream) {
+    if (!out) return -1;
+    *out = nullptr;
+    tsylv_opts o;
+    if (opts) o = *opts; else tsylv_opts_default(&o);
+    const bool gen = C != nullptr;
+    if (d < 1 || d > kMaxD) return -2;
+    if (!shape_ok(d, n)) return -3;
+    if (!A) return -4;
+    for (int mu = 0; mu < d; mu++)
+        if (!A[mu]) return -4;
+    if (gen)
+        for (int mu = 0; mu < d; mu++)
+            if (!C[mu]) return -5;
+    if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -7;
+    if (work_bytes < solver_workspace_bytes(d, n, gen, o, flip)) return -8;
+    if (int st = check_opts(o, d)) return st < 0 ? -9 : st;
+    if (o.precision != TSYLV_FP64 || o.nmin < 0 || o.timing || (gen && d > 4)) return TSYLV_EUNSUPPORTED;
+    const int prod = fp64_prod(o, d, o.schedule == 0);
+    if (prod < 0) return TSYLV_EUNSUPPORTED;
+    (void)cudaGetLastError();
+    auto sp = std::make_unique<SolvePlan>();
+    sp->d = d;
+    sp->gen = gen && d >= 2;
+    sp->flip = flip;
+    sp->prod = prod;
+    sp->use_graph = o.use_graph != 0;
+    sp->timeout_ns = static_cast<long long>(o.wait_ms) * 1000000LL;
+    for (int mu = 0; mu < d; mu++) {
+        sp->n[mu] = n[mu];
+        sp->A[mu] = A[mu];
+        sp->C[mu] = gen ? C[mu] : nullptr;
+    }
+    std::vector<uint8_t> sub;
+    if (int st = read_structure(d, sp->n, sp->A, static_cast<char*>(work), flip, stream, sub))
+        return st == -3 ? -4 : st;
+    sp->plan = get_plan(d, sp->n, sp->gen, 8, o.split, &sub, o.partition, shape_of_opts(o, d));
+    if (!sp->plan) return cuda_fail_msg("plan: pinned host allocation");
+    if (int st = prepare_kernels()) return st;
+    if (o.schedule == 0) sp->flow_grid = flow_grid(8, d, sp->gen, sp->plan->ntiles, prod);
+    sp->L = make_layout(d, sp->n, sp->plan->nb, sp->gen, 8, sp->plan->tab.size());
+    if (sp->L.total > work_bytes) return -8;
+    // the unflipped pattern, as the device check reads it
+    size_t nsub = 0;
+    for (int mu = 0; mu < d; mu++) nsub += static_cast<size_t>(n[mu] - 1);
+    std::vector<uint8_t> raw(nsub + 1, 0);
+    size_t off = 0;
+    for (int mu = 0; mu < d; mu++) {
+        const long long m = n[mu];
+        for (long long i = 0; i + 1 < m; i++) raw[off + static_cast<size_t>(flip ? m - 2 - i : i)] = sub[off + i];
+        off += static_cast<size_t>(m - 1);
+    }
+    cudaError_t e;
+    if ((e = cudaGetDevice(&sp->dev)) != cudaSuccess) return cuda_fail(e, "plan: cudaGetDevice");
+    if ((e = cudaMalloc(&sp->pat, raw.size())) != cudaSuccess) return cuda_fail(e, "plan: cudaMalloc");
+    if ((e = cudaMemcpy(sp->pat, raw.data(), raw.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cudaFree(sp->pat);
+        return cuda_fail(e, "plan: structure upload");
+    }
+    *out = sp.release();
+    return 0;
+}
+
+int plan_execute(void* handle, const double* B, double* X, void* work, size_t work_bytes, int* status,
+                 cudaStream_t stream) {
+    if (!handle) return -1;
+    SolvePlan& sp = *static_cast<SolvePlan*>(handle);
+    if (!B) return -2;
+    if (!X) return -3;
+    if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -4;
+    if (work_bytes < sp.L.total) return -5;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != sp.dev) return TSYLV_EUNSUPPORTED;
+    (void)cudaGetLastError();
+    Call c;
+    c.d = sp.d;
+    c.gen = sp.gen;
+    c.flip = sp.flip;
+    c.prod = sp.prod;
+    c.timeout_ns = sp.timeout_ns;
+    for (int mu = 0; mu < sp.d; mu++) {
+        c.n[mu] = sp.n[mu];
+        c.A[mu] = sp.A[mu];
+        c.C[mu] = sp.C[mu];
+    }
+    c.B = B;
+    c.X = X;
+    c.base = static_cast<char*>(work);
+    c.plan = sp.plan;
+    c.L = sp.L;
+    c.persistent = sp.flow_grid > 0;
+    c.flow_grid = sp.flow_grid;
+    c.pat = sp.pat;
+    c.status_out = status;
+    const int tag = (sp.flip ? 1 : 0) | (c.persistent ? 256 : 0) | (c.prod << 14) | (1 << 20);
+    return run_enqueue(*sp.plan, make_key(c, tag), sp.use_graph, stream, enqueue_plan_fp64, c);
+}
+
+void plan_destroy(void* handle) {
+    if (!handle) return;
+    SolvePlan* sp = static_cast<SolvePlan*>(handle);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != sp->dev) cudaSetDevice(sp->dev);
+    if (sp->pat) cudaFree(sp->pat);  // synchronises the device: no execution still reads the pattern
+    if (cur != sp->dev) cudaSetDevice(cur);
+    delete sp;
 }
 
 }  // namespace tsylv

@@ -30,6 +30,13 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
 
 cudaStream_t capture_stream();
 
+// Solve plans (tsylv_plan_*): opaque handles of repeated FP64 solves.
+int plan_create(void** out, int d, const int64_t* n, const double* const* A, const double* const* C, bool flip,
+                void* work, size_t work_bytes, const tsylv_opts* opts, cudaStream_t stream);
+int plan_execute(void* handle, const double* B, double* X, void* work, size_t work_bytes, int* status,
+                 cudaStream_t stream);
+void plan_destroy(void* handle);
+
 size_t solver_tt_workspace_bytes(int d, const int64_t* n, const tsylv_opts& o);
 size_t solver_z_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opts& o);
 int solver_solve_z(int d, const int64_t* n, const double* const* A, const double* const* C, const double* B,

@@ -42,7 +42,8 @@ int cuda_fail(cudaError_t e, const char* where);
 int cuda_fail_msg(const char* where);
 
 // Device-side error bits (OR-ed into the workspace status word).
-enum : int { kErrSingular = 1, kErrNonfinite = 2, kErrTimeout = 4, kErrBounds = 8 };
+enum : int { kErrSingular = 1, kErrNonfinite = 2, kErrTimeout = 4, kErrBounds = 8,
+             kErrStructure = 16 /* a plan's coefficients no longer have its 2x2 structure */ };
 
 // Forms of the equation (the block kernels' form parameter): Eq. (2.2), the
 // d-term generalized form, and the paper's two-term form Eq. (3.1).
@@ -117,5 +118,12 @@ cudaError_t launch_pack_coef_z(const GeomArgs& g, int mu, const zd* M, zd* tiles
 // out[i] = sub-diagonal entries of every A_mu (concatenated, n_mu - 1 each).
 cudaError_t launch_gather_subdiag(int d, const long long* n, const double* const* A, double* out,
                                   cudaStream_t s);
+// Sets kErrStructure in *err unless the nonzero pattern of the first
+// subdiagonal of every A_mu (modes back to back, entry i of mode mu: A(i+1, i))
+// equals pat (one byte per entry).
+cudaError_t launch_check_subdiag(int d, const long long* n, const double* const* A, const uint8_t* pat, int* err,
+                                 cudaStream_t s);
+// *status = the TSYLV status code of the device error word *err.
+cudaError_t launch_status_word(const int* err, int* status, cudaStream_t s);
 
 }  // namespace tsylv

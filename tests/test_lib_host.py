@@ -300,3 +300,36 @@ def test_complex_validation_without_gpu(lib):
     assert z(3, n, fake, P(16), P(16), P(256), 1 << 30, ctypes.byref(bad), None, None) == -8
     dm = _lib.default_opts(fp64_update=2)
     assert z(3, n, fake, P(16), P(16), P(256), 1 << 30, ctypes.byref(dm), None, None) == _lib.TSYLV_EUNSUPPORTED
+
+
+def test_plan_validation_without_gpu(lib):
+    """tsylv_plan_create / tsylv_plan_execute: bad arguments give -i and the
+    requests a plan does not serve give TSYLV_EUNSUPPORTED, all before any
+    CUDA call; destroying a null plan is a no-op."""
+    from paper_1905_09539_gb300 import _lib
+    P = ctypes.c_void_p
+    n = (ctypes.c_int64 * 3)(8, 8, 8)
+    fake = (P * 3)(16, 16, 16)
+    o = _lib.default_opts()
+    wb = lib.tsylv_workspace_bytes(3, n, 0, ctypes.byref(o))
+    h = P()
+    cr = lambda *a: lib.tsylv_plan_create(*a)
+    assert cr(None, 3, n, fake, None, 0, P(256), wb, ctypes.byref(o), None) == -1
+    assert cr(ctypes.byref(h), 0, n, fake, None, 0, P(256), wb, ctypes.byref(o), None) == -2
+    bad = (ctypes.c_int64 * 3)(8, 0, 8)
+    assert cr(ctypes.byref(h), 3, bad, fake, None, 0, P(256), wb, ctypes.byref(o), None) == -3
+    assert cr(ctypes.byref(h), 3, n, None, None, 0, P(256), wb, ctypes.byref(o), None) == -4
+    holes = (P * 3)(16, None, 16)
+    assert cr(ctypes.byref(h), 3, n, fake, holes, 0, P(256), wb, ctypes.byref(o), None) == -5
+    assert cr(ctypes.byref(h), 3, n, fake, None, 2, P(256), wb, ctypes.byref(o), None) == -6
+    assert cr(ctypes.byref(h), 3, n, fake, None, 0, P(257), wb, ctypes.byref(o), None) == -7
+    assert cr(ctypes.byref(h), 3, n, fake, None, 0, P(256), 16, ctypes.byref(o), None) == -8
+    badopt = _lib.default_opts(wait_ms=0)
+    assert cr(ctypes.byref(h), 3, n, fake, None, 0, P(256), wb, ctypes.byref(badopt), None) == -9
+    for kw in ({"precision": _lib.TSYLV_FP32_REFINED}, {"nmin": -1}, {"timing": 1}, {"fp64_update": 2, "schedule": 1}):
+        ok = _lib.default_opts(**kw)
+        assert cr(ctypes.byref(h), 3, n, fake, None, 0, P(256), 1 << 30, ctypes.byref(ok), None) == \
+            _lib.TSYLV_EUNSUPPORTED, kw
+    assert not h.value
+    assert lib.tsylv_plan_execute(None, P(16), P(16), P(256), wb, None, None) == -1
+    lib.tsylv_plan_destroy(None)
