@@ -595,6 +595,8 @@ def run_ours(args, ws, rank, local):
         return torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=dev)
 
     jobs = []  # (inputs [(host, device)], run(), outputs() -> [device tensors], host outputs)
+    plans, plan_inputs = {}, {}
+    plan_status = {}
     for name, gen, prec in SOLVE_PARTS:
         pr = probs[gen]
         dA = [dev_like(a) for a in pr["A"]]
@@ -606,11 +608,17 @@ def run_ours(args, ws, rank, local):
             ins += [(pinned_like(c), d) for c, d in zip(pr["C"], dC)]
 
         def run(gen=gen, prec=prec, dA=dA, dC=dC, dB=dB, dXo=dXo, name=name):
-            if gen:
+            if name in plans:
+                # FP64: the solve plan of these coefficient buffers (created
+                # once, outside the timed region): no host synchronisation
+                plans[name].solve(dB, X=dXo, status=plan_status[name])
+            elif gen:
                 ts.gtsylv_solve(dA, dC, dB, X=dXo, info=infos[name], precision=PREC[prec])
             else:
                 ts.tsylv_solve(dA, dB, X=dXo, info=infos[name], precision=PREC[prec])
             return [dXo]
+        if prec == 0:
+            plan_inputs[name] = (dA, dC)
         jobs.append((ins, run, [pinned_like(dXo)]))
     for prec in (0, 1):
         tag = "adjoint_fp64" if prec == 0 else "adjoint_fp32r"
@@ -675,8 +683,16 @@ def run_ours(args, ws, rank, local):
                     h.copy_(d, non_blocking=True)
                 ev_out[k].record(cs)
 
-    # one untimed pass (first=True) so that the graphs for the new buffers exist
+    # one untimed pass (first=True) so that the graphs for the new buffers exist;
+    # then the FP64 parts' solve plans on the copied-in coefficients (the plan
+    # reads their 2x2 structure once; every execution re-packs the values and
+    # checks the structure on the device), and a second untimed pass for their graphs
     e2e_step(True)
+    torch.cuda.synchronize(dev)
+    for name, (pA, pC) in plan_inputs.items():
+        plans[name] = ts.SolvePlan(pA, pC)
+        plan_status[name] = torch.full((1,), -99, dtype=torch.int32, device=dev)
+    e2e_step(False)
     torch.cuda.synchronize(dev)
     barrier(ws)
     torch.cuda.synchronize(dev)
@@ -690,6 +706,11 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize(dev)
     barrier(ws)
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws, dev)
+    for name, st in plan_status.items():
+        if int(st.item()) != 0:
+            raise RuntimeError("end-to-end leg: plan execution of %s returned status %d" % (name, int(st.item())))
+    for pl in plans.values():
+        pl.close()
 
     # ---- the other configurations, measured beside the step (not part of
     # `value`; after the end-to-end leg, whose captured schedules a larger
@@ -934,7 +955,10 @@ def run_ours(args, ws, rank, local):
         "other_configs": other,
         "roofline": roofline,
         "e2e": {"value": units / (e2e_ms * 1e-3), "unit": "unknowns/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "note": "FP64 256^3 parts through solve plans (tsylv_plan_execute; each plan created once "
+                        "before the timed region on the device coefficient buffers, which every step "
+                        "refills from the host); refined, adjoint and batch parts through their solve calls"},
         "gpu_launches": launches,
         "clocks": clocks,
     }
