@@ -459,6 +459,16 @@ def run_ours(args, ws, rank, local):
                 name = "%s_%s" % (PNAME[prec], "generalized" if gen else "laplace")
                 infos[name] = _lib.Info()
                 table[name] = (lambda gen=gen, prec=prec, name=name: solve(name, gen, prec))
+        if args.only.startswith("complex_"):
+            # the complex-triangular variant at the bench's size (FP64)
+            zgen = args.only == "complex_dterm"
+            zq = synthetic.complex_problem(args.seed + rank, shape, generalized=zgen)
+            zt = lambda a: torch.from_numpy(np.ascontiguousarray(np.asarray(a).T)).to(dev).T
+            zA = [zt(a) for a in zq["A"]]
+            zC = [zt(c) for c in zq["C"]] if zgen else None
+            zB = torch.from_numpy(np.ascontiguousarray(zq["B"].transpose(2, 1, 0))).to(dev).permute(2, 1, 0)
+            zX = ts.empty_fortran(shape, dev, torch.complex128)
+            table[args.only] = lambda: ts.ztsylv_solve(zA, zB, zC, X=zX)
         fn = table[args.only]
         for _ in range(args.warmup):
             fn()
@@ -991,8 +1001,8 @@ def main():
                     help="skip the measurements of the d = 4 and batched FP32-refined configurations")
     ap.add_argument("--fp64-peak", action="store_true", help="build and run the FP64 throughput probe")
     ap.add_argument("--only", default=None,
-                    help="profiling aid: run just this part of the step (e.g. fp64_generalized) for the warm-up "
-                         "and timed steps, print its time and exit")
+                    help="profiling aid: run just this part of the step (e.g. fp64_generalized; also "
+                         "complex_laplace, complex_dterm) for the warm-up and timed steps, print its time and exit")
     args = ap.parse_args()
     if args.fp64_peak:
         run_fp64_peak()
