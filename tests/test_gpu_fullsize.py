@@ -8,8 +8,11 @@ where A(X)(u) is contracted directly from the definition (Eq. (2.2), and the
 d-term form) with numpy in FP64 for each sampled multi-index u (corners
 included: u = 0 carries the whole dependency cone).  An FP64 solve is
 backward stable to a small multiple of n * eps, so r(u) <= 1e-11; the refined
-solve stops at a normwise residual of 1e-12, so r(u) <= 1e-10.  The 64^3
-workload is also compared element by element with the oracle.
+solve stops at a normwise residual of 1e-12, so r(u) <= 1e-10.  At 256^3 the
+trailing 24^3 box (which solves the trailing sub-problem by itself, the
+coefficients being upper quasi-triangular) is also compared element by element
+with the oracle's solve of that sub-problem.  The 64^3 workload is compared
+element by element with the oracle in full.
 """
 import numpy as np
 import pytest
@@ -85,6 +88,30 @@ def _check_residual(X, p, tol, count=16, seed=0):
     return worst
 
 
+def _trailing_cut(A, size):
+    """First index k >= n - size of the trailing box that splits no 2x2 block (A(k, k-1) = 0)."""
+    n = A.shape[0]
+    k = n - size
+    while k > 1 and A[k, k - 1] != 0.0:
+        k -= 1
+    return k
+
+
+def _check_trailing_box(X, p, size, tol):
+    """With upper quasi-triangular coefficients, the trailing box X[k:, k:, ...]
+    (k not inside a 2x2 block) solves the trailing sub-problem on its own: the
+    oracle solves that small problem and the GPU's entries are compared with
+    it element by element."""
+    ks = [_trailing_cut(a, size) for a in p["A"]]
+    sub = tuple(slice(k, None) for k in ks)
+    As = [np.asfortranarray(a[k:, k:]) for a, k in zip(p["A"], ks)]
+    Cs = None if p["C"] is None else [np.asfortranarray(c[k:, k:]) for c, k in zip(p["C"], ks)]
+    Xo = oracle.solve_recursive(As, np.asfortranarray(p["B"][sub]), Cs, nmin=4)
+    err = rel_err(np.asfortranarray(X[sub]), Xo)
+    assert err <= tol, err
+    assert float(np.max(np.abs(X[sub] - Xo)) / np.max(np.abs(Xo))) <= tol
+
+
 def _solve(lib, p, prec):
     A = [to_dev(a) for a in p["A"]]
     B = to_dev(p["B"])
@@ -116,6 +143,7 @@ def test_config_256cubed(lib, gen, precision):
     prec = lib.TSYLV_FP64 if precision == "fp64" else lib.TSYLV_FP32_REFINED
     X = _solve(lib, p, prec)
     _check_residual(X, p, 1e-11 if precision == "fp64" else 1e-10)
+    _check_trailing_box(X, p, 24, 1e-11 if precision == "fp64" else 1e-10)
 
 
 @pytest.mark.gpu

@@ -325,3 +325,27 @@ def test_structure_rejected():
     A[2, 1] = 1.0                 # two adjacent subdiagonal entries: not quasi-triangular
     with pytest.raises(oracle.OracleError):
         oracle.solve_backsub([A], np.ones(5))
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_trailing_box_is_decoupled(gen):
+    """With upper quasi-triangular coefficients and a cut k that splits no 2x2
+    block, the trailing box X[k:, k:, k:] solves the trailing sub-problem by
+    itself (the fact the full-size GPU tests use to check outputs element by
+    element): the C oracle on the whole problem against the dense solve of the
+    trailing one."""
+    shape = (14, 12, 11)
+    p = _prob(shape, gen, seed=17, force=[[3], [5], [2]])
+    X = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+    ks = []
+    for a in p["A"]:
+        k = a.shape[0] - 6
+        while a[k, k - 1] != 0.0:
+            k -= 1
+        ks.append(k)
+    sub = tuple(slice(k, None) for k in ks)
+    As = [a[k:, k:] for a, k in zip(p["A"], ks)]
+    Cs = None if p["C"] is None else [c[k:, k:] for c, k in zip(p["C"], ks)]
+    M = operator(As, Cs)
+    Xs = unvec(np.linalg.solve(M, vec(p["B"][sub])), tuple(a.shape[0] for a in As))
+    assert np.linalg.norm(X[sub] - Xs) / np.linalg.norm(Xs) <= 1e-13
