@@ -1216,25 +1216,29 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     bool dead = false;
     for (int jj = 0; jj < njob && !dead; jj++) {
         const int stg = jj % NST;
-        const bool ok = dev::mbar_wait(&bar[stg], (uses[stg] + static_cast<uint32_t>(jj / NST)) & 1u, a.timeout_ns);
+        // uniform over the warp (the tensor-core variants issue warp-wide mma)
+        const bool ok = __all_sync(0xffffffffu, dev::mbar_wait(&bar[stg], (uses[stg] + static_cast<uint32_t>(jj / NST)) & 1u,
+                                                               a.timeout_ns));
+        if (ok) {  // a warp whose wait ran out skips the job; the block is abandoned below
+            int L, Jp;
+            job(j0 + jj, L, Jp);
+            // padding skipped where the FP64 pipes bound the updates (FP64,
+            // complex); the latency-bound FP32 updates run full tiles
+            const int ks = sizeof(T) >= 8 ? a.bsize[CHAIN ? D - 1 - L : L][Jp] : TE;
+            if constexpr (TCU)
+                mma_dispatch<D, GEN, PK, NS>(L, cfr, reinterpret_cast<const QF*>(stage + stg * C::STAGE), ks, tlive);
+            else
+                dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE, ks, sizeof(T) >= 8 ? live : ~0u);
+        }
+        // one barrier per job: every thread is done reading the stage (it
+        // orders those reads before the copies that refill it, as for a
+        // consumer-release mbarrier arrival), and the outcome of the waits
+        // becomes uniform over the CTA
         if (__syncthreads_or(!ok)) {
             dead = true;
             if (tid == 0) atomicOr(a.err, kErrTimeout);
             break;
         }
-        int L, Jp;
-        job(j0 + jj, L, Jp);
-        // padding skipped where the FP64 pipes bound the updates (FP64,
-        // complex); the latency-bound FP32 updates run full tiles
-        const int ks = sizeof(T) >= 8 ? a.bsize[CHAIN ? D - 1 - L : L][Jp] : TE;
-        if constexpr (TCU)
-            mma_dispatch<D, GEN, PK, NS>(L, cfr, reinterpret_cast<const QF*>(stage + stg * C::STAGE), ks, tlive);
-        else
-            dispatch_job<T, D, GENF>(L, acc, stage + stg * C::STAGE, ks, sizeof(T) >= 8 ? live : ~0u);
-        // every thread is done reading the stage (the barrier orders those
-        // reads before the copies that refill it, as for a consumer-release
-        // mbarrier arrival)
-        __syncthreads();
         if (tid == 0 && jj + NST < njob) issue(j0 + jj + NST, stg);
     }
     if (dead) {  // uniform over the CTA
