@@ -427,8 +427,9 @@ int tsylv_solve_batched(int count, const int* d, const int64_t* n_packed, const 
  * every call.  Arguments and status codes as tsylv_solve, with opts the 6th
  * argument: its fields are checked as tsylv_solve checks them (-6 for a field
  * out of range, TSYLV_EUNSUPPORTED for host_io or an nmin outside 0, 2..TE);
- * opts->precision must be TSYLV_FP64 (else -6), opts->timing 0 and
- * opts->nmin not -1 (no autotuning runs; else TSYLV_EUNSUPPORTED).  The schedule is always one launch per anti-diagonal
+ * opts->precision must be TSYLV_FP64 (else -6), opts->timing 0,
+ * opts->nmin not -1 (no autotuning runs) and opts->fp64_update not 2 (its
+ * block updates are FP64 FMA); else TSYLV_EUNSUPPORTED.  The schedule is always one launch per anti-diagonal
  * wavefront (opts->schedule is not used). */
 int tsylv_solve_noalloc(int d, const int64_t* n, const double* const* A, const double* B, double* X,
                         const tsylv_opts* opts, tsylv_info* info, cudaStream_t stream);
