@@ -388,8 +388,9 @@ def run_ours(args, ws, rank, local):
     ts.load()
     shape = (args.n, args.n, args.n)
     N = float(np.prod(shape))
-    PREC = {0: _lib.TSYLV_FP64, 1: _lib.TSYLV_FP32_REFINED, 2: _lib.TSYLV_TF32_REFINED, 3: _lib.TSYLV_BF16_REFINED}
-    PNAME = {0: "fp64", 1: "fp32r", 2: "tf32r", 3: "bf16r"}
+    PREC = {0: _lib.TSYLV_FP64, 1: _lib.TSYLV_FP32_REFINED, 2: _lib.TSYLV_TF32_REFINED, 3: _lib.TSYLV_BF16_REFINED,
+            4: _lib.TSYLV_DF64}
+    PNAME = {0: "fp64", 1: "fp32r", 2: "tf32r", 3: "bf16r", 4: "df64"}
 
     def to_dev(a):
         a = np.asfortranarray(a)
@@ -452,7 +453,7 @@ def run_ours(args, ws, rank, local):
     if args.only:
         table = {name: (lambda name=name, gen=gen, prec=prec: solve(name, gen, prec)) for name, gen, prec in SOLVE_PARTS}
         table.update({"adjoint_fp64": lambda: adjoint(0), "adjoint_fp32r": lambda: adjoint(1), "batched_fp64": batched})
-        for prec in (2, 3):
+        for prec in (2, 3, 4):
             for gen in (False, True):
                 pr = probs[gen]
                 pr["X"][prec] = ts.empty_fortran(shape, dev)

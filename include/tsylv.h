@@ -96,8 +96,17 @@ enum tsylv_precision {
                                 step more than TSYLV_FP32_REFINED.  Persistent
                                 schedule only (opts->schedule = 1 returns
                                 TSYLV_EUNSUPPORTED)                                */
-    TSYLV_BF16_REFINED = 3   /* as TSYLV_TF32_REFINED with BF16 operands (about
+    TSYLV_BF16_REFINED = 3,  /* as TSYLV_TF32_REFINED with BF16 operands (about
                                 two steps more than TSYLV_FP32_REFINED)          */
+    TSYLV_DF64 = 4           /* one solve in double-float arithmetic on the FP32
+                                pipes: every value a pair of floats (about 48
+                                significant bits; exact products by FMA, two-sum
+                                accumulation), the same partition, schedule and
+                                back-substitution as TSYLV_FP64.  No residual is
+                                evaluated (info->resid = -1; tsylv_residual
+                                measures it).  tsylv_solve / gtsylv_solve and the
+                                transposed solves, d = 1..4, persistent schedule;
+                                elsewhere TSYLV_EUNSUPPORTED                      */
 };
 
 enum tsylv_residual_kind {

@@ -17,12 +17,12 @@ import torch
 
 from . import _lib
 from ._lib import (TSYLV_BF16_REFINED, TSYLV_FP32_REFINED, TSYLV_FP64, TSYLV_RESID_DF64, TSYLV_RESID_FP64,
-                   TSYLV_TF32_REFINED, Info, Opts, default_opts, load, status_string)
+                   TSYLV_TF32_REFINED, TSYLV_DF64, Info, Opts, default_opts, load, status_string)
 
 __all__ = ["tsylv_solve", "gtsylv_solve", "gsylvten_solve", "ztsylv_solve", "tsylv_solve_transposed", "gtsylv_solve_transposed",
            "tsylv_residual", "tsylv_backward", "tsylv_solve_batched", "BatchPools", "solve", "fortran", "TsylvError",
            "Opts", "Info", "default_opts", "TSYLV_FP64", "TSYLV_FP32_REFINED", "TSYLV_TF32_REFINED",
-           "TSYLV_BF16_REFINED", "TSYLV_RESID_DF64", "TSYLV_RESID_FP64", "workspace", "solve_general",
+           "TSYLV_BF16_REFINED", "TSYLV_DF64", "TSYLV_RESID_DF64", "TSYLV_RESID_FP64", "workspace", "solve_general",
            "reduce_coefficients", "transform", "selftest_wait_timeout", "empty_fortran", "SolvePlan"]
 
 

@@ -18,6 +18,7 @@ TSYLV_FP64 = 0
 TSYLV_FP32_REFINED = 1
 TSYLV_TF32_REFINED = 2
 TSYLV_BF16_REFINED = 3
+TSYLV_DF64 = 4
 
 TSYLV_RESID_DF64 = 0
 TSYLV_RESID_FP64 = 1

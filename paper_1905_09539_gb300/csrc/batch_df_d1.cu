@@ -1,0 +1,10 @@
+// Persistent batched kernel instantiations: the double-float solve (TSYLV_DF64), d = 1.
+#include "batched_kernel.cuh"
+
+namespace tsylv {
+
+template cudaError_t launch_batched_t<dfl, 1, kFormLaplace>(const BatchArgs&, int, cudaStream_t);
+template cudaError_t prepare_batched_t<dfl, 1, kFormLaplace>();
+template int batched_occupancy_t<dfl, 1, kFormLaplace>();
+
+}  // namespace tsylv

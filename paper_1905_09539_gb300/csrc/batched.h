@@ -74,6 +74,10 @@ cudaError_t prepare_batched_tt();
 cudaError_t launch_batched_z(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s);
 int batched_occupancy_z(int d, bool gen);
 cudaError_t prepare_batched_z();
+// The double-float solve (TSYLV_DF64), d = 1..4, Laplace and d-term forms.
+cudaError_t launch_batched_df(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s);
+int batched_occupancy_df(int d, bool gen);
+cudaError_t prepare_batched_df();
 // *dst = a, by one thread (a captured launch keeps `a` by value).
 cudaError_t launch_store_args(const WaveArgs& a, WaveArgs* dst, cudaStream_t s);
 // Resident CTAs per SM of the persistent kernel.

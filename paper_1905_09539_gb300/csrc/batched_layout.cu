@@ -305,6 +305,46 @@ cudaError_t prepare_batched_z() {
     return prepare_batched_t<zd, 4, kFormDTerm>();
 }
 
+// The double-float solve (TSYLV_DF64): d = 1..4, Laplace and d-term forms.
+cudaError_t launch_batched_df(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s) {
+    switch (d * 2 + (gen ? 1 : 0)) {
+        case 2:
+        case 3: return launch_batched_t<dfl, 1, kFormLaplace>(a, grid, s);
+        case 4: return launch_batched_t<dfl, 2, kFormLaplace>(a, grid, s);
+        case 5: return launch_batched_t<dfl, 2, kFormDTerm>(a, grid, s);
+        case 6: return launch_batched_t<dfl, 3, kFormLaplace>(a, grid, s);
+        case 7: return launch_batched_t<dfl, 3, kFormDTerm>(a, grid, s);
+        case 8: return launch_batched_t<dfl, 4, kFormLaplace>(a, grid, s);
+        case 9: return launch_batched_t<dfl, 4, kFormDTerm>(a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int batched_occupancy_df(int d, bool gen) {
+    switch (d * 2 + (gen ? 1 : 0)) {
+        case 2:
+        case 3: return batched_occupancy_t<dfl, 1, kFormLaplace>();
+        case 4: return batched_occupancy_t<dfl, 2, kFormLaplace>();
+        case 5: return batched_occupancy_t<dfl, 2, kFormDTerm>();
+        case 6: return batched_occupancy_t<dfl, 3, kFormLaplace>();
+        case 7: return batched_occupancy_t<dfl, 3, kFormDTerm>();
+        case 8: return batched_occupancy_t<dfl, 4, kFormLaplace>();
+        case 9: return batched_occupancy_t<dfl, 4, kFormDTerm>();
+        default: return 1;
+    }
+}
+
+cudaError_t prepare_batched_df() {
+    cudaError_t e;
+    if ((e = prepare_batched_t<dfl, 1, kFormLaplace>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<dfl, 2, kFormLaplace>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<dfl, 2, kFormDTerm>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<dfl, 3, kFormLaplace>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<dfl, 3, kFormDTerm>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<dfl, 4, kFormLaplace>()) != cudaSuccess) return e;
+    return prepare_batched_t<dfl, 4, kFormDTerm>();
+}
+
 cudaError_t launch_batched_tt(int d, const BatchArgs& a, int grid, cudaStream_t s) {
     switch (d) {
         case 2: return launch_batched_t<double, 2, kFormTwoTerm>(a, grid, s);

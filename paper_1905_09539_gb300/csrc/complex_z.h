@@ -42,6 +42,13 @@ __device__ __forceinline__ bool operator!=(zd a, zd b) { return !(a == b); }
 // factor sqrt(2) of the modulus)
 __device__ __forceinline__ double fabs(zd a) { return ::fabs(a.re) + ::fabs(a.im); }
 __device__ __forceinline__ bool isfinite(zd a) { return ::isfinite(a.re) && ::isfinite(a.im); }
+// the real types' own (exact matches inside this namespace, ahead of the
+// element types' overloads, which a double or float would otherwise reach by
+// conversion)
+__device__ __forceinline__ double fabs(double a) { return ::fabs(a); }
+__device__ __forceinline__ float fabs(float a) { return ::fabsf(a); }
+__device__ __forceinline__ bool isfinite(double a) { return ::isfinite(a); }
+__device__ __forceinline__ bool isfinite(float a) { return ::isfinite(a); }
 #endif
 
 template <typename T>

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "complex_z.h"
+#include "double_float.h"
 
 namespace tsylv {
 namespace dev {
@@ -161,7 +162,7 @@ __device__ __forceinline__ bool wait_at_least(const int* p, int need, int* abort
 // Scale of a refinement step: the power of two at or above max|R| (1 when R
 // is zero or not finite), so that R / s and s * D are exact.
 __device__ __forceinline__ double step_scale(double mx) {
-    if (!(mx > 0) || !isfinite(mx)) return 1.0;
+    if (!(mx > 0) || !::isfinite(mx)) return 1.0;
     int ex = 0;
     (void)frexp(mx, &ex);  // mx = f 2^ex, 1/2 <= f < 1
     return ldexp(1.0, ex);
@@ -197,6 +198,44 @@ __device__ __forceinline__ zd add_rn(zd a, zd b) { return zd(__dadd_rn(a.re, b.r
 __device__ __forceinline__ zd ld_dsmem(const zd* local, uint32_t rank) {
     return zd(ld_dsmem(&local->re, rank), ld_dsmem(&local->im, rank));
 }
+
+// Double-float: epsilon of the pair arithmetic (2^-44, a bound on the
+// relative error of one operation); the block products accumulate with a
+// multiply-add that leaves its pair unnormalised (the high words summed by
+// two_sum, every error and low-word product gathered in the low word), and
+// `settle` normalises an accumulator once its products are summed.
+template <>
+struct Eps<dfl> { static constexpr float v = 5.684341886080802e-14f; };
+template <>
+__device__ __forceinline__ dfl fmadd<dfl>(dfl a, dfl b, dfl c) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);  // exact: a.h b.h = p + e
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    float s, t;
+    dfl_detail::two_sum(c.h, p, s, t);
+    return dfl(s, __fadd_rn(t, __fadd_rn(c.l, e)));
+}
+__device__ __forceinline__ dfl add_rn(dfl a, dfl b) { return a + b; }
+__device__ __forceinline__ dfl ld_dsmem(const dfl* local, uint32_t rank) {
+    return dfl(ld_dsmem(&local->h, rank), ld_dsmem(&local->l, rank));
+}
+template <typename T>
+__device__ __forceinline__ T settle(T x) { return x; }
+
+// warp broadcast of a value of the element type
+template <typename T>
+__device__ __forceinline__ T shfl(unsigned mask, T v, int src) { return __shfl_sync(mask, v, src); }
+template <>
+__device__ __forceinline__ dfl shfl<dfl>(unsigned mask, dfl v, int src) {
+    return dfl(__shfl_sync(mask, v.h, src), __shfl_sync(mask, v.l, src));
+}
+template <>
+__device__ __forceinline__ zd shfl<zd>(unsigned mask, zd v, int src) {
+    return zd(__shfl_sync(mask, v.re, src), __shfl_sync(mask, v.im, src));
+}
+template <>
+__device__ __forceinline__ dfl settle<dfl>(dfl x) { return dfl_detail::fast_two_sum(x.h, x.l); }
 
 }  // namespace dev
 }  // namespace tsylv

@@ -226,5 +226,8 @@ template cudaError_t launch_unpack_tensor<double>(const GeomArgs&, const double*
 template cudaError_t launch_unpack_tensor<float>(const GeomArgs&, const float*, double*, cudaStream_t);
 template cudaError_t launch_pack_coef<double>(const GeomArgs&, int, const double*, double*, bool, cudaStream_t);
 template cudaError_t launch_pack_coef<float>(const GeomArgs&, int, const double*, float*, bool, cudaStream_t);
+template cudaError_t launch_pack_tensor<dfl>(const GeomArgs&, const double*, dfl*, double, cudaStream_t);
+template cudaError_t launch_unpack_tensor<dfl>(const GeomArgs&, const dfl*, double*, cudaStream_t);
+template cudaError_t launch_pack_coef<dfl>(const GeomArgs&, int, const double*, dfl*, bool, cudaStream_t);
 
 }  // namespace tsylv

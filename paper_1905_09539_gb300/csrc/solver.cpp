@@ -243,11 +243,13 @@ cudaError_t enqueue_waves(const Call& c, const Layout& L, cudaStream_t s) {
         if (p.tt) return launch_batched_tt(p.d, ba, c.flow_grid, s);
         if constexpr (std::is_same<T, zd>::value)
             return launch_batched_z(p.d, p.gen, ba, c.flow_grid, s);
+        else if constexpr (std::is_same<T, dfl>::value)
+            return launch_batched_df(p.d, p.gen, ba, c.flow_grid, s);
         else
             return launch_batched<T>(p.d, p.gen, ba, c.flow_grid, s, c.prod);
     }
-    if constexpr (std::is_same<T, zd>::value) {
-        return cudaErrorInvalidValue;  // the complex solve runs the persistent schedule only
+    if constexpr (std::is_same<T, zd>::value || std::is_same<T, dfl>::value) {
+        return cudaErrorInvalidValue;  // the complex and double-float solves run the persistent schedule only
     } else {
         for (size_t w = 0; w < p.wave_off.size(); w++) {
             wa.tiles = tab + p.t_wave + p.wave_off[w];
@@ -261,7 +263,11 @@ cudaError_t enqueue_waves(const Call& c, const Layout& L, cudaStream_t s) {
 
 // ---------------------------------------------------------------- FP64 solve
 
-cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
+// The FP64 solve (T = double) and the double-float solve (T = dfl: every
+// coefficient and right-hand-side entry split into a pair of floats, the
+// solution summed back into doubles): 8-byte entries, the same layout.
+template <typename T>
+cudaError_t enqueue_fp64_t(const Call& c, cudaStream_t s) {
     const Plan& p = *c.plan;
     const Layout& L = c.L;
     char* base = c.base;
@@ -270,17 +276,19 @@ cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) {
     TRY(cudaMemsetAsync(base + L.err, 0, 64, s));
     TRY(cudaMemcpyAsync(base + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     for (int mu = 0; mu < p.d; mu++) {
-        TRY(launch_pack_coef<double>(g, mu, c.A[mu], reinterpret_cast<double*>(base + L.At[mu]), false, s));
-        if (p.gen) TRY(launch_pack_coef<double>(g, mu, c.C[mu], reinterpret_cast<double*>(base + L.Ct[mu]), true, s));
+        TRY(launch_pack_coef<T>(g, mu, c.A[mu], reinterpret_cast<T*>(base + L.At[mu]), false, s));
+        if (p.gen) TRY(launch_pack_coef<T>(g, mu, c.C[mu], reinterpret_cast<T*>(base + L.Ct[mu]), true, s));
     }
-    double* Xt = reinterpret_cast<double*>(base + L.X);
-    TRY(launch_pack_tensor<double>(g, c.B, Xt, 1.0, s));
+    T* Xt = reinterpret_cast<T*>(base + L.X);
+    TRY(launch_pack_tensor<T>(g, c.B, Xt, 1.0, s));
     TRY(mark(c, 1, s));
-    TRY(enqueue_waves<double>(c, L, s));
+    TRY(enqueue_waves<T>(c, L, s));
     TRY(mark(c, 2, s));
-    TRY(launch_unpack_tensor<double>(g, Xt, c.X, s));
+    TRY(launch_unpack_tensor<T>(g, Xt, c.X, s));
     return mark(c, 3, s);
 }
+
+cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) { return enqueue_fp64_t<double>(c, s); }
 
 // A plan execution: the FP64 solve, preceded by the check of the
 // coefficients' 2x2 structure against the plan's and followed by the status
@@ -790,6 +798,7 @@ int prepare_kernels() {
         if (e == cudaSuccess) e = prepare_batched<float>();
         if (e == cudaSuccess) e = prepare_batched_tt();
         if (e == cudaSuccess) e = prepare_batched_z();
+        if (e == cudaSuccess) e = prepare_batched_df();
         if (e == cudaSuccess) e = prepare_refine2();
         if (e == cudaSuccess) e = prepare_norm2();
         if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
@@ -876,7 +885,7 @@ int solve_read_structure(int d, const long long* n, const double* const* A, char
 }
 
 int check_opts(const tsylv_opts& o, int d) {
-    if (o.precision < TSYLV_FP64 || o.precision > TSYLV_BF16_REFINED || o.max_refine < 0 || !(o.tol > 0) ||
+    if (o.precision < TSYLV_FP64 || o.precision > TSYLV_DF64 || o.max_refine < 0 || !(o.tol > 0) ||
         (o.residual != TSYLV_RESID_DF64 && o.residual != TSYLV_RESID_FP64) || o.split < 0 || o.nmin < -1 ||
         o.schedule < 0 || o.schedule > 1 || o.partition < 0 || o.partition > 1 || o.resid_update < 0 ||
         o.resid_update > 1 || o.fuse_step < 0 || o.fuse_step > 3 || o.timing < 0 || o.timing > 1 ||
@@ -926,8 +935,9 @@ size_t solver_workspace_bytes(int d, const int64_t* n, bool gen, const tsylv_opt
         nb[mu] = max_blocks(static_cast<int>(n[mu]), shape_min_cut(d, mu, shape));
     }
     const bool g = gen && d >= 2;
-    size_t total = o.precision == TSYLV_FP64 ? make_layout(d, nn, nb, g, 8, tab_ints_bound(d, nn, nb)).total
-                                             : make_ref_layout(d, nn, nb, g, tab_ints_bound(d, nn, nb)).total;
+    const bool one_solve = o.precision == TSYLV_FP64 || o.precision == TSYLV_DF64;
+    size_t total = one_solve ? make_layout(d, nn, nb, g, 8, tab_ints_bound(d, nn, nb)).total
+                             : make_ref_layout(d, nn, nb, g, tab_ints_bound(d, nn, nb)).total;
     if (o.host_io) {
         size_t N = 1, coef = 0;
         for (int mu = 0; mu < d; mu++) {
@@ -983,6 +993,8 @@ int solver_solve(int d, const int64_t* n, const double* const* A, const double* 
     // generalized form is built for d <= 4
     if ((o.precision == TSYLV_TF32_REFINED || o.precision == TSYLV_BF16_REFINED) && o.schedule != 0)
         return TSYLV_EUNSUPPORTED;
+    // the double-float solve: persistent schedule, d <= 4, FMA-style pair arithmetic
+    if (o.precision == TSYLV_DF64 && (o.schedule != 0 || d > 4 || o.fp64_update == 2)) return TSYLV_EUNSUPPORTED;
     if (gen && d > 4) return TSYLV_EUNSUPPORTED;
     if (o.precision == TSYLV_FP64 && fp64_prod(o, d, o.schedule == 0) < 0) return TSYLV_EUNSUPPORTED;
     const int shape = shape_of_opts(o, d);
@@ -1059,14 +1071,15 @@ int solve_body(int d, const int64_t* n, const double* const* A, const double* co
                void* work, size_t work_bytes, const tsylv_opts& o, int shape, tsylv_info* info, cudaStream_t stream,
                bool gen, bool transposed) {
     const int sh = gen ? 1 : 0;
-    const bool refined = o.precision != TSYLV_FP64;
+    const bool df64 = o.precision == TSYLV_DF64;
+    const bool refined = o.precision != TSYLV_FP64 && !df64;
     Call c;
     c.d = d;
     c.gen = gen && d >= 2;
     c.flip = transposed;
     c.df = o.residual == TSYLV_RESID_DF64;
     c.prod = o.precision == TSYLV_TF32_REFINED ? kProdTF32 : o.precision == TSYLV_BF16_REFINED ? kProdBF16 : kProdNative;
-    if (!refined) {
+    if (!refined && !df64) {
         c.prod = fp64_prod(o, d, o.schedule == 0);
         if (c.prod < 0) return TSYLV_EUNSUPPORTED;
     }
@@ -1089,7 +1102,17 @@ int solve_body(int d, const int64_t* n, const double* const* A, const double* co
     c.timing = o.timing != 0;
     if (int st = ensure_events(c)) return st;
     c.persistent = o.schedule == 0;
-    if (c.persistent) c.flow_grid = flow_grid(refined ? 4 : 8, d, c.gen, c.plan->ntiles, c.prod);
+    if (c.persistent) {
+        if (df64) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+            const long long slots = static_cast<long long>(sms) * batched_occupancy_df(d, c.gen);
+            c.flow_grid = static_cast<int>(c.plan->ntiles < slots ? c.plan->ntiles : slots);
+        } else {
+            c.flow_grid = flow_grid(refined ? 4 : 8, d, c.gen, c.plan->ntiles, c.prod);
+        }
+    }
     // pipelined first two steps: always (2), or by default (0) when the solve is
     // latency-bound, i.e. its largest wavefront has fewer than 5 blocks per SM
     // (measured: faster there, slower on wavefronts that fill the GPU)
@@ -1106,12 +1129,13 @@ int solve_body(int d, const int64_t* n, const double* const* A, const double* co
              o.max_refine >= 2;
     if (c.pipe) c.pipe_grid = pipe_grid(d, 4 * c.plan->ntiles, c.prod);
     const int tagbase = (transposed ? 1 : 0) | (c.timing ? 2 : 0) | (c.df ? 4 : 0) | (c.persistent ? 256 : 0) |
-                        (c.prod << 14);
+                        (c.prod << 14) | (df64 ? 1 << 18 : 0);
 
     if (!refined) {
         c.L = make_layout(d, c.n, c.plan->nb, c.gen, 8, c.plan->tab.size());
         if (c.L.total > work_bytes) return -(7 + sh);
-        int st = run_enqueue(*c.plan, make_key(c, tagbase), o.use_graph != 0, stream, enqueue_fp64, c);
+        int st = run_enqueue(*c.plan, make_key(c, tagbase), o.use_graph != 0, stream,
+                             df64 ? enqueue_fp64_t<dfl> : enqueue_fp64_t<double>, c);
         if (st) return st;
         int herr = 0;
         if (cudaError_t e = cudaMemcpyAsync(&herr, c.base + c.L.err, sizeof(int), cudaMemcpyDeviceToHost, stream);

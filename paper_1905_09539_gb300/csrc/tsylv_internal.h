@@ -8,6 +8,7 @@
 
 #include "../../include/tsylv.h"
 #include "complex_z.h"
+#include "double_float.h"
 
 namespace tsylv {
 

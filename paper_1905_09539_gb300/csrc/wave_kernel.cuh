@@ -47,6 +47,7 @@ struct WaveCfg {
     // d = 3 8 (Laplace) / 5 (generalized), other orders 5 / 4
     static constexpr int MINB = D == 5 ? 3  // d = 5: 1024-entry blocks, shared memory allows 3 CTAs/SM
                                 : sizeof(T) == 16 ? 3  // complex FP64: 16-byte entries
+                                : IsDoubleFloat<T>::value ? (CHAIN ? 3 : 4)  // double-float: pair arithmetic
                                 : sizeof(T) == 8 ? (CHAIN ? (D == 3 ? 3 : 4) : (D == 3 ? 6 : 4))
                                 : D == 3 ? (CHAIN ? 5 : 8)
                                          : (CHAIN ? 4 : 5);
@@ -98,12 +99,49 @@ struct WaveCfg {
 // (the tile beyond it is zero), and element slots q whose whole warp holds
 // only padded elements of the target block (bit q of `live` clear) are not
 // computed (their sums stay zero, as the products of zero padding would be).
+// Double-float: one multiply-add is a dozen FP32 instructions, so the k loop
+// stays rolled (the fully unrolled products of every level overflow the
+// instruction cache) and runs outside the element slots, whose independent
+// accumulators then interleave.
+template <typename T, int D, int MU, int EPT, int NPROD>
+__device__ __forceinline__ void prod_acc_rolled(T (&acc)[EPT], const T* __restrict__ M1, const T* __restrict__ S1,
+                                                const T* __restrict__ M2, const T* __restrict__ S2, int ks,
+                                                unsigned live) {
+    constexpr int TE = tile_extent(D);
+    constexpr int TD = ipow(TE, D);
+    constexpr int st = ipow(TE, MU);
+    int iq[EPT], bq[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; q++) {
+        const int e = threadIdx.x + q * kThreads;
+        iq[q] = row_of<TE, st>(e);
+        bq[q] = e - iq[q] * st;
+    }
+#pragma unroll 1
+    for (int k = 0; k < ks; k++) {
+#pragma unroll
+        for (int q = 0; q < EPT; q++) {
+            const int e = threadIdx.x + q * kThreads;
+            if ((TD % kThreads) != 0 && e >= TD) continue;
+            if (!((live >> q) & 1u)) continue;  // uniform over the warp
+            acc[q] = dev::fmadd(M1[iq[q] + TE * k], S1[bq[q] + k * st], acc[q]);
+            if constexpr (NPROD == 2) acc[q] = dev::fmadd(M2[iq[q] + TE * k], S2[bq[q] + k * st], acc[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < EPT; q++) acc[q] = dev::settle(acc[q]);
+}
+
 template <typename T, int D, int MU, int EPT>
 __device__ __forceinline__ void prod_acc(T (&acc)[EPT], const T* __restrict__ M, const T* __restrict__ S, int ks,
                                          unsigned live) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int st = ipow(TE, MU);
+    if constexpr (IsDoubleFloat<T>::value) {
+        prod_acc_rolled<T, D, MU, EPT, 1>(acc, M, S, M, S, ks, live);
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < EPT; q++) {
         const int e = threadIdx.x + q * kThreads;
@@ -118,7 +156,7 @@ __device__ __forceinline__ void prod_acc(T (&acc)[EPT], const T* __restrict__ M,
         } else {
             for (int k = 0; k < ks; k++) s = dev::fmadd(M[i + TE * k], S[base + k * st], s);
         }
-        acc[q] = s;
+        acc[q] = dev::settle(s);
     }
 }
 
@@ -130,6 +168,10 @@ __device__ __forceinline__ void prod_acc2(T (&acc)[EPT], const T* __restrict__ M
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int st = ipow(TE, MU);
+    if constexpr (IsDoubleFloat<T>::value) {
+        prod_acc_rolled<T, D, MU, EPT, 2>(acc, M1, S1, M2, S2, ks, live);
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < EPT; q++) {
         const int e = threadIdx.x + q * kThreads;
@@ -150,7 +192,7 @@ __device__ __forceinline__ void prod_acc2(T (&acc)[EPT], const T* __restrict__ M
                 s = dev::fmadd(M2[i + TE * k], S2[base + k * st], s);
             }
         }
-        acc[q] = s;
+        acc[q] = dev::settle(s);
     }
 }
 
@@ -366,7 +408,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int src = member_with(mask, m, l, k);
-                const T pp = __shfl_sync(full, P0[l + 1], src);
+                const T pp = dev::shfl(full, P0[l + 1], src);
                 if (k == 0 || two) p = dev::fmadd(Em(l, u[l], two ? a[l] + k : u[l]), pp, p);
             }
             P0[l] = p;
@@ -377,7 +419,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int src = member_with(mask, m, 0, k);
-                const T pp = __shfl_sync(full, P0[1], src);
+                const T pp = dev::shfl(full, P0[1], src);
                 if (k == 0 || two) of = dev::fmadd(Em(0, u[0], two ? a[0] + k : u[0]), pp, of);
             }
         }
@@ -421,8 +463,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int src = member_with(mask, m, l, k);
-                const T pp = __shfl_sync(full, P0[l + 1], src);
-                const T gg = __shfl_sync(full, G0[l + 1], src);
+                const T pp = dev::shfl(full, P0[l + 1], src);
+                const T gg = dev::shfl(full, G0[l + 1], src);
                 if (k == 0 || two) {
                     const int kk = two ? a[l] + k : u[l];
                     p = dev::fmadd(Em(l, u[l], kk), pp, p);
@@ -438,8 +480,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int src = member_with(mask, m, 0, k);
-                const T pp = __shfl_sync(full, P0[1], src);
-                const T gg = __shfl_sync(full, G0[1], src);
+                const T pp = dev::shfl(full, P0[1], src);
+                const T gg = dev::shfl(full, G0[1], src);
                 if (k == 0 || two) {
                     const int kk = two ? a[0] + k : u[0];
                     of = dev::fmadd(Em(0, u[0], kk), gg, dev::fmadd(Dm(0, u[0], kk), pp, of));
@@ -474,25 +516,26 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
         // precomputed inverse: x_m = sum_k Minv(m, k) r_k
 #pragma unroll
         for (int k = 0; k < S; k++) {
-            const T rk = __shfl_sync(full, r, k);
+            const T rk = dev::shfl(full, r, k);
             if (act) x = dev::fmadd(minv[m * S + k], rk, x);
         }
     } else {
-    // scale for the pivot test: 16 eps max |M|
-    T big = 0;
+    // scale for the pivot test: 16 eps max |M| (magnitudes in the real type of T)
+    using R = typename RealOf<T>::type;
+    R big = 0;
 #pragma unroll
     for (int k = 0; k < S; k++) big = fmax(big, fabs(row[k]));
 #pragma unroll
     for (int w = 16; w >= 1; w >>= 1) big = fmax(big, __shfl_xor_sync(full, big, w));
-    const T tiny = T(16) * dev::Eps<T>::v * big;
+    const R tiny = R(16) * dev::Eps<T>::v * big;
     // forward elimination
 #pragma unroll
     for (int c = 0; c < S; c++) {
-        T val = (lane >= c && act) ? fabs(row[c]) : T(-1);
+        R val = (lane >= c && act) ? fabs(row[c]) : R(-1);
         int idx = lane;
 #pragma unroll
         for (int w = 16; w >= 1; w >>= 1) {
-            const T ov = __shfl_xor_sync(full, val, w);
+            const R ov = __shfl_xor_sync(full, val, w);
             const int oi = __shfl_xor_sync(full, idx, w);
             if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
         }
@@ -500,13 +543,13 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
         if (pv != c) {
             const int src = lane == c ? pv : (lane == pv ? c : lane);
 #pragma unroll
-            for (int k = 0; k < S; k++) row[k] = __shfl_sync(full, row[k], src);
-            r = __shfl_sync(full, r, src);
+            for (int k = 0; k < S; k++) row[k] = dev::shfl(full, row[k], src);
+            r = dev::shfl(full, r, src);
         }
         T prow[S];
 #pragma unroll
-        for (int k = 0; k < S; k++) prow[k] = __shfl_sync(full, row[k], c);
-        const T pr = __shfl_sync(full, r, c);
+        for (int k = 0; k < S; k++) prow[k] = dev::shfl(full, row[k], c);
+        const T pr = dev::shfl(full, r, c);
         if (!(fabs(prow[c]) > tiny)) status |= kErrSingular;
         if (act && lane > c) {
             const T f = row[c] / prow[c];
@@ -519,7 +562,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
     for (int c = S - 1; c >= 0; c--) {
         const T xc_local = r / row[c];
-        const T xc = __shfl_sync(full, xc_local, c);
+        const T xc = dev::shfl(full, xc_local, c);
         if (lane == c) x = xc;
         if (act && lane < c) r = dev::fmadd(-row[c], xc, r);
     }
@@ -537,7 +580,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
             T p = 0;
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const T xv = __shfl_sync(full, x, member_with(mask, m, mu, k));
+                const T xv = dev::shfl(full, x, member_with(mask, m, mu, k));
                 if (k == 0 || two) p = dev::fmadd(Em(mu, u[mu], two ? a[mu] + k : u[mu]), xv, p);
             }
             pc[mu] = p;
@@ -548,7 +591,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
             T p = 0;
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const T pp = __shfl_sync(full, pc[l + 1], member_with(mask, m, l, k));
+                const T pp = dev::shfl(full, pc[l + 1], member_with(mask, m, l, k));
                 if (k == 0 || two) p = dev::fmadd(Em(l, u[l], two ? a[l] + k : u[l]), pp, p);
             }
             pc[l] = p;
@@ -567,7 +610,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
             T p = 0, q = 0;
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const T xv = __shfl_sync(full, x, member_with(mask, m, mu, k));
+                const T xv = dev::shfl(full, x, member_with(mask, m, mu, k));
                 if (k == 0 || two) {
                     const int kk = two ? a[mu] + k : u[mu];
                     p = dev::fmadd(Em(mu, u[mu], kk), xv, p);
@@ -584,8 +627,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int src = member_with(mask, m, l, k);
-                const T pp = __shfl_sync(full, pc[l + 1], src);
-                const T gg = __shfl_sync(full, gc[l + 1], src);
+                const T pp = dev::shfl(full, pc[l + 1], src);
+                const T gg = dev::shfl(full, gc[l + 1], src);
                 if (k == 0 || two) {
                     const int kk = two ? a[l] + k : u[l];
                     p = dev::fmadd(Em(l, u[l], kk), pp, p);
@@ -766,7 +809,8 @@ __device__ __forceinline__ T group_entry(const TileSmem<T, D, FM>& sm, const int
 template <typename T, int D, int GEN, int S>
 __device__ int group_inverse_s(const TileSmem<T, D, GEN>& sm, const int (&a)[D], int mask, T* out) {
     T W[S][2 * S];
-    T big = 0;
+    using R = typename RealOf<T>::type;
+    R big = 0;
 #pragma unroll
     for (int m = 0; m < S; m++)
 #pragma unroll
@@ -775,7 +819,7 @@ __device__ int group_inverse_s(const TileSmem<T, D, GEN>& sm, const int (&a)[D],
             W[m][S + k] = m == k ? T(1) : T(0);
             big = fmax(big, fabs(W[m][k]));
         }
-    const T tiny = T(16) * dev::Eps<T>::v * big;
+    const R tiny = R(16) * dev::Eps<T>::v * big;
     int status = 0;
 #pragma unroll
     for (int c = 0; c < S; c++) {

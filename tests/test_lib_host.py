@@ -95,8 +95,10 @@ def test_option_validation_without_gpu(lib):
         assert st(**kw) == -8, kw
     for kw in ({"host_io": 1}, {"fuse_step": 1}, {"nmin": 17}, {"nmin": 1}, {"fp64_update": 2, "schedule": 1},
                {"precision": _lib.TSYLV_TF32_REFINED, "schedule": 1},
-               {"precision": _lib.TSYLV_BF16_REFINED, "schedule": 1}):
+               {"precision": _lib.TSYLV_BF16_REFINED, "schedule": 1}, {"precision": _lib.TSYLV_DF64, "schedule": 1},
+               {"precision": _lib.TSYLV_DF64, "fp64_update": 2}):
         assert st(**kw) == _lib.TSYLV_EUNSUPPORTED, kw
+    assert st(precision=5) == -8
 
 
 def test_noalloc_option_validation_without_gpu(lib):
