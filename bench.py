@@ -903,6 +903,22 @@ def run_ours(args, ws, rank, local):
             "note": "gsylvten_solve, Eq. (3.1): X x_1 A_1 + X x_1 C x_2 A_2 x_3 A_3 = B; residual by the DMMA "
                     "mode-product kernel"}
         del qA, qC, qX, T1, T2, Rq
+        # the double-float solve at 256^3 (pairs of floats on the FP32 pipes),
+        # both forms, against the FP64 solve of the step; FP64 residual of the result
+        for dgen in (False, True):
+            pr = probs[dgen]
+            pr["X"][4] = ts.empty_fortran(shape, dev)
+            nm = "df64_" + ("generalized" if dgen else "laplace")
+            infos[nm] = _lib.Info()
+            fd = lambda: solve(nm, dgen, 4)
+            fd()
+            td = event_ms(fd, 3)
+            _, rho_d, _ = ts.tsylv_residual(pr["A"], pr["B"], pr["X"][4], pr["C"], residual=_lib.TSYLV_RESID_FP64)
+            fp = parts["fp64_generalized" if dgen else "fp64_laplace"]["ms"]
+            other["df64_256_" + ("generalized" if dgen else "laplace")] = {
+                "ms": td, "unknowns_per_s": N / (td * 1e-3), "rel_residual_fp64": rho_d, "vs_fp64": fp / td,
+                "note": "precision TSYLV_DF64: one solve in double-float arithmetic (float pairs) on the FP32 pipes"}
+            del pr["X"][4]
         # the complex-triangular variant at 256^3 (coefficients in complex
         # Schur form, as in the paper's experiments), both forms; the residual
         # is a check computed by torch mode products, outside the timed calls
