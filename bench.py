@@ -757,7 +757,7 @@ def run_ours(args, ws, rank, local):
             qA = [to_dev(a) for a in q["A"]]
             qC = [to_dev(c) for c in q["C"]]
             qB = to_dev(q["B"])
-            res = precision_sweep(qA, qC, qB, shp, (0, 1, 2, 3))
+            res = precision_sweep(qA, qC, qB, shp, (0, 1, 2, 3, 4))
             res["mixed_vs_fp64"] = res["fp64"]["ms"] / res["fp32r"]["ms"]
             other["d4_generalized_" + "x".join(str(v) for v in shp)] = res
             del qA, qC, qB
