@@ -264,8 +264,8 @@ int gtsylv_solve_transposed(int d, const int64_t* n, const double* const* A,
  * tsylv_plan_create: d, n, A, C (NULL: the Laplace form), transposed (0 / 1),
  *   work / work_bytes (the workspace of tsylv_workspace_bytes(d, n, C != NULL,
  *   opts); it only has to be valid during the call and during executions),
- *   opts (TSYLV_FP64 only; nmin >= 0 or leaf bounds -- no autotuning; no event
- *   timing; fp64_update as for tsylv_solve).  Reads the structure (one
+ *   opts (TSYLV_FP64 or TSYLV_DF64; nmin >= 0 or leaf bounds -- no
+ *   autotuning; no event timing; fp64_update as for tsylv_solve).  Reads the structure (one
  *   synchronisation of `stream`), builds the partition and schedule, and keeps
  *   a copy of the structure on the device (one byte per subdiagonal entry,
  *   allocated here).  Returns 0 and sets *plan, -i for a bad i-th argument

@@ -293,7 +293,8 @@ cudaError_t enqueue_fp64(const Call& c, cudaStream_t s) { return enqueue_fp64_t<
 // A plan execution: the FP64 solve, preceded by the check of the
 // coefficients' 2x2 structure against the plan's and followed by the status
 // code written to the caller's device int.
-cudaError_t enqueue_plan_fp64(const Call& c, cudaStream_t s) {
+template <typename T>
+cudaError_t enqueue_plan_t(const Call& c, cudaStream_t s) {
     const Plan& p = *c.plan;
     char* base = c.base;
     int* err = reinterpret_cast<int*>(base + c.L.err);
@@ -303,14 +304,13 @@ cudaError_t enqueue_plan_fp64(const Call& c, cudaStream_t s) {
     GeomArgs g = geom_of(p, c.L, base, c.flip);
     TRY(cudaMemcpyAsync(base + c.L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     for (int mu = 0; mu < p.d; mu++) {
-        TRY(launch_pack_coef<double>(g, mu, c.A[mu], reinterpret_cast<double*>(base + c.L.At[mu]), false, s));
-        if (p.gen)
-            TRY(launch_pack_coef<double>(g, mu, c.C[mu], reinterpret_cast<double*>(base + c.L.Ct[mu]), true, s));
+        TRY(launch_pack_coef<T>(g, mu, c.A[mu], reinterpret_cast<T*>(base + c.L.At[mu]), false, s));
+        if (p.gen) TRY(launch_pack_coef<T>(g, mu, c.C[mu], reinterpret_cast<T*>(base + c.L.Ct[mu]), true, s));
     }
-    double* Xt = reinterpret_cast<double*>(base + c.L.X);
-    TRY(launch_pack_tensor<double>(g, c.B, Xt, 1.0, s));
-    TRY(enqueue_waves<double>(c, c.L, s));
-    TRY(launch_unpack_tensor<double>(g, Xt, c.X, s));
+    T* Xt = reinterpret_cast<T*>(base + c.L.X);
+    TRY(launch_pack_tensor<T>(g, c.B, Xt, 1.0, s));
+    TRY(enqueue_waves<T>(c, c.L, s));
+    TRY(launch_unpack_tensor<T>(g, Xt, c.X, s));
     if (c.status_out) TRY(launch_status_word(err, c.status_out, s));
     return cudaSuccess;
 }
@@ -1746,6 +1746,7 @@ struct SolvePlan {
     int prod = kProdNative;
     int flow_grid = 0;
     bool use_graph = true;
+    bool df64 = false;  // the double-float solve (TSYLV_DF64)
     long long timeout_ns = kTimeoutNs;
     std::shared_ptr<Plan> plan;
     Layout L;
@@ -1771,8 +1772,10 @@ int plan_create(void** out, int d, const int64_t* n, const double* const* A, con
     if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -7;
     if (work_bytes < solver_workspace_bytes(d, n, gen, o, flip)) return -8;
     if (int st = check_opts(o, d)) return st < 0 ? -9 : st;
-    if (o.precision != TSYLV_FP64 || o.nmin < 0 || o.timing || (gen && d > 4)) return TSYLV_EUNSUPPORTED;
-    const int prod = fp64_prod(o, d, o.schedule == 0);
+    const bool df64 = o.precision == TSYLV_DF64;
+    if ((o.precision != TSYLV_FP64 && !df64) || o.nmin < 0 || o.timing || (gen && d > 4)) return TSYLV_EUNSUPPORTED;
+    if (df64 && (o.schedule != 0 || d > 4 || o.fp64_update == 2)) return TSYLV_EUNSUPPORTED;
+    const int prod = df64 ? kProdNative : fp64_prod(o, d, o.schedule == 0);
     if (prod < 0) return TSYLV_EUNSUPPORTED;
     (void)cudaGetLastError();
     auto sp = std::make_unique<SolvePlan>();
@@ -1780,6 +1783,7 @@ int plan_create(void** out, int d, const int64_t* n, const double* const* A, con
     sp->gen = gen && d >= 2;
     sp->flip = flip;
     sp->prod = prod;
+    sp->df64 = df64;
     sp->use_graph = o.use_graph != 0;
     sp->timeout_ns = static_cast<long long>(o.wait_ms) * 1000000LL;
     for (int mu = 0; mu < d; mu++) {
@@ -1793,7 +1797,17 @@ int plan_create(void** out, int d, const int64_t* n, const double* const* A, con
     sp->plan = get_plan(d, sp->n, sp->gen, 8, o.split, &sub, o.partition, shape_of_opts(o, d));
     if (!sp->plan) return cuda_fail_msg("plan: pinned host allocation");
     if (int st = prepare_kernels()) return st;
-    if (o.schedule == 0) sp->flow_grid = flow_grid(8, d, sp->gen, sp->plan->ntiles, prod);
+    if (o.schedule == 0) {
+        if (df64) {
+            int dv = 0, sms = 0;
+            cudaGetDevice(&dv);
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dv) != cudaSuccess || sms < 1) sms = 1;
+            const long long slots = static_cast<long long>(sms) * batched_occupancy_df(d, sp->gen);
+            sp->flow_grid = static_cast<int>(sp->plan->ntiles < slots ? sp->plan->ntiles : slots);
+        } else {
+            sp->flow_grid = flow_grid(8, d, sp->gen, sp->plan->ntiles, prod);
+        }
+    }
     sp->L = make_layout(d, sp->n, sp->plan->nb, sp->gen, 8, sp->plan->tab.size());
     if (sp->L.total > work_bytes) return -8;
     // the unflipped pattern, as the device check reads it
@@ -1848,8 +1862,9 @@ int plan_execute(void* handle, const double* B, double* X, void* work, size_t wo
     c.flow_grid = sp.flow_grid;
     c.pat = sp.pat;
     c.status_out = status;
-    const int tag = (sp.flip ? 1 : 0) | (c.persistent ? 256 : 0) | (c.prod << 14) | (1 << 20);
-    return run_enqueue(*sp.plan, make_key(c, tag), sp.use_graph, stream, enqueue_plan_fp64, c);
+    const int tag = (sp.flip ? 1 : 0) | (c.persistent ? 256 : 0) | (c.prod << 14) | (sp.df64 ? 1 << 18 : 0) | (1 << 20);
+    return run_enqueue(*sp.plan, make_key(c, tag), sp.use_graph, stream,
+                       sp.df64 ? enqueue_plan_t<dfl> : enqueue_plan_t<double>, c);
 }
 
 void plan_destroy(void* handle) {

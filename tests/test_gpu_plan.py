@@ -146,7 +146,7 @@ def test_plan_transposed(lib, gen):
     assert rel_err(to_host(L), Lo) <= TOL
 
 
-@pytest.mark.parametrize("kw", [{"schedule": 1}, {"fp64_update": 2}, {"nmin": 6}])
+@pytest.mark.parametrize("kw", [{"schedule": 1}, {"fp64_update": 2}, {"nmin": 6}, {"precision": 4}])
 def test_plan_options(lib, kw):
     shape = (33, 29, 25)
     p = synthetic.problem(47, shape, generalized=True)

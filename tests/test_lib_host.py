@@ -328,7 +328,8 @@ def test_plan_validation_without_gpu(lib):
     assert cr(ctypes.byref(h), 3, n, fake, None, 0, P(256), 16, ctypes.byref(o), None) == -8
     badopt = _lib.default_opts(wait_ms=0)
     assert cr(ctypes.byref(h), 3, n, fake, None, 0, P(256), wb, ctypes.byref(badopt), None) == -9
-    for kw in ({"precision": _lib.TSYLV_FP32_REFINED}, {"nmin": -1}, {"timing": 1}, {"fp64_update": 2, "schedule": 1}):
+    for kw in ({"precision": _lib.TSYLV_FP32_REFINED}, {"nmin": -1}, {"timing": 1}, {"fp64_update": 2, "schedule": 1},
+               {"precision": _lib.TSYLV_DF64, "schedule": 1}):
         ok = _lib.default_opts(**kw)
         assert cr(ctypes.byref(h), 3, n, fake, None, 0, P(256), 1 << 30, ctypes.byref(ok), None) == \
             _lib.TSYLV_EUNSUPPORTED, kw
