@@ -965,6 +965,15 @@ def run_ours(args, ws, rank, local):
             "ms": tr, "unknowns_per_s": units_rank["batched"] / (tr * 1e-3), "iterations": ir.iterations,
             "mixed_vs_fp64": parts["batched_fp64"]["ms"] / tr,
             "rel_diff_vs_fp64": float(torch.linalg.vector_norm(pools.X - X64) / torch.linalg.vector_norm(X64))}
+        idf = _lib.Info()
+        fdf = lambda: pools.solve(info=idf, precision=_lib.TSYLV_DF64)
+        fdf()
+        tdf = event_ms(fdf, max(3, args.steps))
+        other["batched_df64"] = {
+            "ms": tdf, "unknowns_per_s": units_rank["batched"] / (tdf * 1e-3),
+            "vs_fp64": parts["batched_fp64"]["ms"] / tdf,
+            "rel_diff_vs_fp64": float(torch.linalg.vector_norm(pools.X - X64) / torch.linalg.vector_norm(X64)),
+            "note": "precision TSYLV_DF64: the double-float solve of every equation in one persistent launch"}
         pools.solve(info=infos["batched_fp64"])  # leave the FP64 solutions in place
         del X64
 

@@ -104,9 +104,10 @@ enum tsylv_precision {
                                 accumulation), the same partition, schedule and
                                 back-substitution as TSYLV_FP64.  No residual is
                                 evaluated (info->resid = -1; tsylv_residual
-                                measures it).  tsylv_solve / gtsylv_solve and the
-                                transposed solves, d = 1..4, persistent schedule;
-                                elsewhere TSYLV_EUNSUPPORTED                      */
+                                measures it).  tsylv_solve / gtsylv_solve, the
+                                transposed solves, solve plans and
+                                tsylv_solve_batched, d = 1..4, persistent
+                                schedule; elsewhere TSYLV_EUNSUPPORTED            */
 };
 
 enum tsylv_residual_kind {
@@ -397,9 +398,10 @@ size_t tsylv_batched_workspace_bytes(int count, const int* d, const int64_t* n_p
  *               B_pool
  *   work        device workspace of tsylv_batched_workspace_bytes bytes,
  *               256-byte aligned, caller-owned
- * Precision: TSYLV_FP64, or TSYLV_FP32_REFINED when every equation of the
- * batch has the same order d (FP32 solves of all equations in one persistent
- * launch, FP64 residuals and corrections per equation, each equation refined to
+ * Precision: TSYLV_FP64; TSYLV_DF64 (the double-float solve, every order
+ * d <= 4); or TSYLV_FP32_REFINED when every equation of the batch has the same
+ * order d (FP32 solves of all equations in one persistent launch, FP64
+ * residuals and corrections per equation, each equation refined to
  * opts->tol); other values return TSYLV_EUNSUPPORTED.
  * Launch parameters: on the first call for a given set of shapes and 2x2
  * structures a built-in autotuner times the job-queue orders (longest

@@ -250,8 +250,10 @@ double eq_flops(const EqPlan& q, bool gen) {
 }
 
 std::shared_ptr<BatchPlan> get_batch_plan(int count, const int* d, const int64_t* n_packed, bool gen, int elem,
-                                          const std::vector<uint8_t>& sub, int partition, int shape) {
-    std::vector<long long> key = {count, gen ? 1 : 0, elem, partition, shape};
+                                          const std::vector<uint8_t>& sub, int partition, int shape,
+                                          int variant = 0) {
+    // variant 1: the double-float batch (same layout as FP64; own tuning and graphs)
+    std::vector<long long> key = {count, gen ? 1 : 0, elem, partition, shape, variant};
     size_t k = 0;
     for (int e = 0; e < count; e++) {
         key.push_back(d[e]);
@@ -441,16 +443,17 @@ struct Pinned {
 // by their synchronisation at the end).
 thread_local Pinned t_pin_tab, t_pin_small;
 
-int occupancy_cached(int d, bool gen, int elem = 8) {
+int occupancy_cached(int d, bool gen, int elem = 8, bool df64 = false) {
     static std::mutex m;
     static std::map<int, int> cache;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int key = (dev * 16 + d * 2 + (gen ? 1 : 0)) * 2 + (elem == 4 ? 1 : 0);
+    const int key = ((dev * 16 + d * 2 + (gen ? 1 : 0)) * 2 + (elem == 4 ? 1 : 0)) * 2 + (df64 ? 1 : 0);
     std::lock_guard<std::mutex> lk(m);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    const int o = elem == 4 ? batched_occupancy<float>(d, gen) : batched_occupancy<double>(d, gen);
+    const int o = elem == 4 ? batched_occupancy<float>(d, gen)
+                            : df64 ? batched_occupancy_df(d, gen) : batched_occupancy<double>(d, gen);
     cache[key] = o;
     return o;
 }
@@ -495,6 +498,7 @@ struct BatchCall {
     int* herr = nullptr;   // pinned host copy of the per-equation status words
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the persistent launches (autotuner)
     bool unpack = true;    // false for the autotuner's timing runs: X may alias B
+    bool df64 = false;     // the double-float solve (pairs of floats in the block tensors)
 };
 
 cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
@@ -509,8 +513,10 @@ cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
     const BatchJob* jobs = reinterpret_cast<const BatchJob*>(tab + c.L.o_jobs);
     const BatchCoefJob* cjobs = reinterpret_cast<const BatchCoefJob*>(tab + c.L.o_cjobs);
     const int njobs = static_cast<int>(p.jobs[0].size());
-    if ((e = launch_batch_pack<double>(geo, jobs, njobs, cjobs, static_cast<int>(p.cjobs.size()), c.B, c.A,
-                                       p.gen ? c.C : nullptr, s)) != cudaSuccess)
+    if ((e = c.df64 ? launch_batch_pack<dfl>(geo, jobs, njobs, cjobs, static_cast<int>(p.cjobs.size()), c.B, c.A,
+                                             p.gen ? c.C : nullptr, s)
+                    : launch_batch_pack<double>(geo, jobs, njobs, cjobs, static_cast<int>(p.cjobs.size()), c.B, c.A,
+                                                p.gen ? c.C : nullptr, s)) != cudaSuccess)
         return e;
     if (c.ev0 && (e = cudaEventRecord(c.ev0, s)) != cudaSuccess) return e;
     for (size_t g = 0; g < p.dlist.size(); g++) {
@@ -526,10 +532,14 @@ cudaError_t enqueue_batch(const BatchCall& c, cudaStream_t s) {
         int grid = c.grid_per_sm[dd] * sm_count();
         if (grid > a.njobs) grid = a.njobs;
         if (grid < 1) grid = 1;
-        if ((e = launch_batched<double>(dd, p.gen, a, grid, s)) != cudaSuccess) return e;
+        if ((e = c.df64 ? launch_batched_df(dd, p.gen, a, grid, s) : launch_batched<double>(dd, p.gen, a, grid, s)) !=
+            cudaSuccess)
+            return e;
     }
     if (c.ev1 && (e = cudaEventRecord(c.ev1, s)) != cudaSuccess) return e;
-    if (c.unpack && (e = launch_batch_unpack<double>(geo, jobs, njobs, c.X, s)) != cudaSuccess) return e;
+    if (c.unpack && (e = c.df64 ? launch_batch_unpack<dfl>(geo, jobs, njobs, c.X, s)
+                                : launch_batch_unpack<double>(geo, jobs, njobs, c.X, s)) != cudaSuccess)
+        return e;
     return cudaMemcpyAsync(c.herr, ctl + 8 + p.count, sizeof(int) * p.count, cudaMemcpyDeviceToHost, s);
 }
 
@@ -1095,7 +1105,7 @@ size_t solver_batched_workspace_bytes(int count, const int* d, const int64_t* n_
     if (!shapes_ok(count, d, n_packed)) return 0;
     if (o.precision == TSYLV_FP32_REFINED)
         return uniform_order(count, d) ? refined_workspace_bytes(count, d, n_packed, gen, refined_shape(o)) : 0;
-    if (o.precision != TSYLV_FP64) return 0;
+    if (o.precision != TSYLV_FP64 && o.precision != TSYLV_DF64) return 0;
     const Bounds b = batch_bounds(count, d, n_packed, gen, 8, fp64_shape(o));
     const BatchLayout L = make_batch_layout(count, d, n_packed, gen, 8, b.jobs, b.cjobs, b.pints, b.data);
     return L.total;
@@ -1117,8 +1127,13 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     if (!B_pool) return -8;
     if (!X_pool) return -9;
     if (!work || (reinterpret_cast<uintptr_t>(work) & 255)) return -10;
-    if (o.precision != TSYLV_FP64 && o.precision != TSYLV_FP32_REFINED) return TSYLV_EUNSUPPORTED;
+    if (o.precision != TSYLV_FP64 && o.precision != TSYLV_FP32_REFINED && o.precision != TSYLV_DF64)
+        return TSYLV_EUNSUPPORTED;
     const bool refined = o.precision == TSYLV_FP32_REFINED;
+    const bool df64 = o.precision == TSYLV_DF64;
+    if (df64)  // the double-float kernels are built for d <= 4
+        for (int e = 0; e < count; e++)
+            if (d[e] > 4) return TSYLV_EUNSUPPORTED;
     if (refined && !uniform_order(count, d)) return TSYLV_EUNSUPPORTED;
     if (gen)  // the generalized form is built for d <= 4
         for (int e = 0; e < count; e++)
@@ -1161,11 +1176,12 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
     const int fixed_shape = fixed_shape_of(o);
     const int part_rule = o.partition == 1 ? 1 : 0;
     std::shared_ptr<BatchPlan> plan0 =
-        get_batch_plan(count, d, n_packed, gen, 8, sub, part_rule, fixed_shape >= 0 ? fixed_shape : 0);
+        get_batch_plan(count, d, n_packed, gen, 8, sub, part_rule, fixed_shape >= 0 ? fixed_shape : 0, df64 ? 1 : 0);
     if (!plan0) return cuda_fail_msg("batched: plan");
     if (plan0->data_bytes > bd.data) return cuda_fail_msg("batched: workspace bound");
     if (int st = prepare_batched_once()) return st;
     BatchCall c;
+    c.df64 = df64;
     c.plan = plan0.get();
     c.L = L;
     c.base = base;
@@ -1179,7 +1195,7 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
 
     auto set_grid = [&](int per_sm) {
         for (int dd : plan0->dlist) {
-            const int occ = occupancy_cached(dd, gen);
+            const int occ = occupancy_cached(dd, gen, 8, df64);
             c.grid_per_sm[dd] = std::max(1, std::min(per_sm, occ));
         }
     };
@@ -1196,7 +1212,7 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
         per_sm = o.split;
     } else if (policy < 0) {
         int occ = 1;
-        for (int dd : plan0->dlist) occ = std::max(occ, occupancy_cached(dd, gen));
+        for (int dd : plan0->dlist) occ = std::max(occ, occupancy_cached(dd, gen, 8, df64));
         std::vector<int> grids = {occ};
         if (occ >= 2) grids.push_back((occ + 1) / 2);
         if (occ >= 3) grids.push_back(1);
@@ -1218,7 +1234,7 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
         for (int sc : shapes) {
             std::shared_ptr<BatchPlan> ps =
                 sc == (fixed_shape >= 0 ? fixed_shape : 0) ? plan0 : get_batch_plan(count, d, n_packed, gen, 8, sub,
-                                                                                     part_rule, sc);
+                                                                                     part_rule, sc, df64 ? 1 : 0);
             if (!ps || ps->data_bytes > bd.data) continue;
             c.plan = ps.get();
             c.L = plan_layout(*ps, d, n_packed, 8);
@@ -1269,7 +1285,7 @@ int solver_batched(int count, const int* d, const int64_t* n_packed, const int64
         plan0->tuned_grid = per_sm = bg;
     }
     if (shape != (fixed_shape >= 0 ? fixed_shape : 0)) {
-        plan = get_batch_plan(count, d, n_packed, gen, 8, sub, part_rule, shape);
+        plan = get_batch_plan(count, d, n_packed, gen, 8, sub, part_rule, shape, df64 ? 1 : 0);
         if (!plan) return cuda_fail_msg("batched: plan");
         if (plan->data_bytes > bd.data) return cuda_fail_msg("batched: workspace bound");
     }

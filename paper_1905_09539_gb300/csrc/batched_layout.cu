@@ -416,5 +416,8 @@ template cudaError_t launch_batch_pack<double>(const BatchGeom*, const BatchJob*
 template cudaError_t launch_batch_unpack<double>(const BatchGeom*, const BatchJob*, int, double*, cudaStream_t);
 template cudaError_t launch_batch_pack<float>(const BatchGeom*, const BatchJob*, int, const BatchCoefJob*, int,
                                               const double*, const double*, const double*, cudaStream_t);
+template cudaError_t launch_batch_pack<dfl>(const BatchGeom*, const BatchJob*, int, const BatchCoefJob*, int,
+                                            const double*, const double*, const double*, cudaStream_t);
+template cudaError_t launch_batch_unpack<dfl>(const BatchGeom*, const BatchJob*, int, double*, cudaStream_t);
 
 }  // namespace tsylv

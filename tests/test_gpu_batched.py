@@ -230,3 +230,36 @@ def test_batch_with_d5_equations(lib):
     assert all(s == 0 for s in st)
     for p, X in zip(ps, Xs):
         assert rel_err(to_host(X), oracle.solve_recursive(p["A"], p["B"], None, nmin=4)) <= 1e-11
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_batch_df64(lib, gen):
+    """The double-float batch: every equation against the oracle (1e-11, the
+    FP64 parity tolerance) and against its own double-float single solve;
+    mixed orders d = 1..4, 2x2 blocks across split points."""
+    shapes = [(37,), (5, 70), (16, 16), (9, 8, 7), (24, 17, 13), (9, 7, 5, 6), (1, 20, 9), (30, 22, 18)]
+    if gen:
+        shapes = [s for s in shapes if len(s) >= 2]
+    ps = [synthetic.problem([14, i], s, generalized=gen, force_blocks=[[n // 2 - 1] if n >= 4 else [] for n in s])
+          for i, s in enumerate(shapes)]
+    prs = _problems(ps, gen)
+    Xs, st = lib.tsylv_solve_batched(prs, generalized=gen, precision=lib.TSYLV_DF64)
+    assert all(s == 0 for s in st)
+    for p, pr, X in zip(ps, prs, Xs):
+        Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+        assert rel_err(to_host(X), Xo) <= 1e-11
+        if gen:
+            Xs1 = lib.gtsylv_solve(pr[0], pr[2], pr[1], precision=lib.TSYLV_DF64)[0]
+        else:
+            Xs1 = lib.tsylv_solve(pr[0], pr[1], precision=lib.TSYLV_DF64)[0]
+        assert rel_err(to_host(X), to_host(Xs1)) <= 1e-12
+
+
+def test_batch_df64_workload_512(lib):
+    ps = synthetic.batch(0, count=512)
+    prs = _problems(ps, False)
+    X64, st64 = lib.tsylv_solve_batched(prs)
+    Xdf, stdf = lib.tsylv_solve_batched(prs, precision=lib.TSYLV_DF64)
+    assert all(s == 0 for s in st64) and all(s == 0 for s in stdf)
+    worst = max(rel_err(to_host(a), to_host(b)) for a, b in zip(Xdf, X64))
+    assert worst <= 1e-12, worst
