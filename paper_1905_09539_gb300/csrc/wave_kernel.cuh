@@ -47,7 +47,10 @@ struct WaveCfg {
     // d = 3 8 (Laplace) / 5 (generalized), other orders 5 / 4
     static constexpr int MINB = D == 5 ? 3  // d = 5: 1024-entry blocks, shared memory allows 3 CTAs/SM
                                 : sizeof(T) == 16 ? 3  // complex FP64: 16-byte entries
-                                : IsDoubleFloat<T>::value ? (CHAIN ? 3 : 4)  // double-float: pair arithmetic
+                                // double-float: the Laplace form measured fastest at 5 (10.6 ms at
+                                // 256^3 against 11.5 at 4 and 10.8 at 6); the d-term form is
+                                // shared-memory bound at 3
+                                : IsDoubleFloat<T>::value ? (CHAIN ? 3 : 5)
                                 : sizeof(T) == 8 ? (CHAIN ? (D == 3 ? 3 : 4) : (D == 3 ? 6 : 4))
                                 : D == 3 ? (CHAIN ? 5 : 8)
                                          : (CHAIN ? 4 : 5);
