@@ -902,6 +902,16 @@ def run_ours(args, ws, rank, local):
             "rel_residual_fp64": float(torch.linalg.vector_norm(Rq) / (opn * torch.linalg.vector_norm(qX))),
             "note": "gsylvten_solve, Eq. (3.1): X x_1 A_1 + X x_1 C x_2 A_2 x_3 A_3 = B; residual by the DMMA "
                     "mode-product kernel"}
+        fqd = lambda: ts.gsylvten_solve(qA, qC, qB, X=qX, precision=_lib.TSYLV_DF64)
+        fqd()
+        tqd = event_ms(fqd, 3)
+        T1 = transform(qX, [qA[0], None, None])
+        T2 = transform(qX, [qC] + qA[1:])
+        Rq = qB - T1 - T2
+        other["two_term_256_df64"] = {
+            "ms": tqd, "unknowns_per_s": N / (tqd * 1e-3), "vs_fp64": tq / tqd,
+            "rel_residual_fp64": float(torch.linalg.vector_norm(Rq) / (opn * torch.linalg.vector_norm(qX))),
+            "note": "gsylvten_solve with precision TSYLV_DF64 (double-float arithmetic on the FP32 pipes)"}
         del qA, qC, qX, T1, T2, Rq
         # the double-float solve at 256^3 (pairs of floats on the FP32 pipes),
         # both forms, against the FP64 solve of the step; FP64 residual of the result

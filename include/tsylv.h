@@ -105,9 +105,10 @@ enum tsylv_precision {
                                 back-substitution as TSYLV_FP64.  No residual is
                                 evaluated (info->resid = -1; tsylv_residual
                                 measures it).  tsylv_solve / gtsylv_solve, the
-                                transposed solves, solve plans and
-                                tsylv_solve_batched, d = 1..4, persistent
-                                schedule; elsewhere TSYLV_EUNSUPPORTED            */
+                                transposed solves, solve plans,
+                                tsylv_solve_batched (d = 1..4) and gsylvten_solve
+                                (d = 2..4), persistent schedule; elsewhere
+                                TSYLV_EUNSUPPORTED                                 */
 };
 
 enum tsylv_residual_kind {
@@ -332,8 +333,9 @@ int zgtsylv_solve(int d, const int64_t* n, const double* const* A, const double*
  *   A      host array of d device pointers: A_1 .. A_d, n_mu x n_mu
  *   C      device pointer: the n_1 x n_1 upper triangular C
  *   B, X   as tsylv_solve (X may equal B); work of gsylvten_workspace_bytes
- * Options: FP64 only (other precisions, opts->schedule = 1 and autotuning
- * nmin = -1 return TSYLV_EUNSUPPORTED); nmin >= 2, leaf, split, partition,
+ * Options: precision TSYLV_FP64 or TSYLV_DF64 (other precisions,
+ * opts->schedule = 1, fp64_update = 2 and autotuning nmin = -1 return
+ * TSYLV_EUNSUPPORTED); nmin >= 2, leaf, split, partition,
  * use_graph, timing, wait_ms as for tsylv_solve.  Arguments: 1 d, 2 n, 3 A,
  * 4 C, 5 B, 6 X, 7 work, 8 work_bytes, 9 opts; statuses as tsylv_solve. */
 size_t gsylvten_workspace_bytes(int d, const int64_t* n, const tsylv_opts* opts);

@@ -78,6 +78,10 @@ cudaError_t prepare_batched_z();
 cudaError_t launch_batched_df(int d, bool gen, const BatchArgs& a, int grid, cudaStream_t s);
 int batched_occupancy_df(int d, bool gen);
 cudaError_t prepare_batched_df();
+// The two-term form Eq. (3.1) in double-float arithmetic, d = 2..4.
+cudaError_t launch_batched_tt_df(int d, const BatchArgs& a, int grid, cudaStream_t s);
+int batched_occupancy_tt_df(int d);
+cudaError_t prepare_batched_tt_df();
 // *dst = a, by one thread (a captured launch keeps `a` by value).
 cudaError_t launch_store_args(const WaveArgs& a, WaveArgs* dst, cudaStream_t s);
 // Resident CTAs per SM of the persistent kernel.

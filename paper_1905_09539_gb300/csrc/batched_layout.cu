@@ -345,6 +345,31 @@ cudaError_t prepare_batched_df() {
     return prepare_batched_t<dfl, 4, kFormDTerm>();
 }
 
+cudaError_t launch_batched_tt_df(int d, const BatchArgs& a, int grid, cudaStream_t s) {
+    switch (d) {
+        case 2: return launch_batched_t<dfl, 2, kFormTwoTerm>(a, grid, s);
+        case 3: return launch_batched_t<dfl, 3, kFormTwoTerm>(a, grid, s);
+        case 4: return launch_batched_t<dfl, 4, kFormTwoTerm>(a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int batched_occupancy_tt_df(int d) {
+    switch (d) {
+        case 2: return batched_occupancy_t<dfl, 2, kFormTwoTerm>();
+        case 3: return batched_occupancy_t<dfl, 3, kFormTwoTerm>();
+        case 4: return batched_occupancy_t<dfl, 4, kFormTwoTerm>();
+        default: return 1;
+    }
+}
+
+cudaError_t prepare_batched_tt_df() {
+    cudaError_t e;
+    if ((e = prepare_batched_t<dfl, 2, kFormTwoTerm>()) != cudaSuccess) return e;
+    if ((e = prepare_batched_t<dfl, 3, kFormTwoTerm>()) != cudaSuccess) return e;
+    return prepare_batched_t<dfl, 4, kFormTwoTerm>();
+}
+
 cudaError_t launch_batched_tt(int d, const BatchArgs& a, int grid, cudaStream_t s) {
     switch (d) {
         case 2: return launch_batched_t<double, 2, kFormTwoTerm>(a, grid, s);

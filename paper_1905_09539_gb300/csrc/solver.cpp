@@ -240,7 +240,10 @@ cudaError_t enqueue_waves(const Call& c, const Layout& L, cudaStream_t s) {
         ba.done = nullptr;
         ba.abort = ctl + 1;
         ba.timeout_ns = c.timeout_ns;
-        if (p.tt) return launch_batched_tt(p.d, ba, c.flow_grid, s);
+        if (p.tt) {
+            if constexpr (std::is_same<T, dfl>::value) return launch_batched_tt_df(p.d, ba, c.flow_grid, s);
+            else return launch_batched_tt(p.d, ba, c.flow_grid, s);
+        }
         if constexpr (std::is_same<T, zd>::value)
             return launch_batched_z(p.d, p.gen, ba, c.flow_grid, s);
         else if constexpr (std::is_same<T, dfl>::value)
@@ -318,7 +321,8 @@ cudaError_t enqueue_plan_t(const Call& c, cudaStream_t s) {
 // The paper's two-term form Eq. (3.1), FP64: A_mu tiles of every mode (the
 // A_1 term and the chain factors A_2 .. A_d), C tiles of mode 1, the
 // persistent solve (the two-term form of the block kernel).
-cudaError_t enqueue_tt(const Call& c, cudaStream_t s) {
+template <typename T>
+cudaError_t enqueue_tt_t(const Call& c, cudaStream_t s) {
     const Plan& p = *c.plan;
     const Layout& L = c.L;
     char* base = c.base;
@@ -327,14 +331,14 @@ cudaError_t enqueue_tt(const Call& c, cudaStream_t s) {
     TRY(cudaMemsetAsync(base + L.err, 0, 64, s));
     TRY(cudaMemcpyAsync(base + L.tab, p.h_tab, p.tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     for (int mu = 0; mu < p.d; mu++)
-        TRY(launch_pack_coef<double>(g, mu, c.A[mu], reinterpret_cast<double*>(base + L.At[mu]), false, s));
-    TRY(launch_pack_coef<double>(g, 0, c.C[0], reinterpret_cast<double*>(base + L.Ct[0]), true, s));
-    double* Xt = reinterpret_cast<double*>(base + L.X);
-    TRY(launch_pack_tensor<double>(g, c.B, Xt, 1.0, s));
+        TRY(launch_pack_coef<T>(g, mu, c.A[mu], reinterpret_cast<T*>(base + L.At[mu]), false, s));
+    TRY(launch_pack_coef<T>(g, 0, c.C[0], reinterpret_cast<T*>(base + L.Ct[0]), true, s));
+    T* Xt = reinterpret_cast<T*>(base + L.X);
+    TRY(launch_pack_tensor<T>(g, c.B, Xt, 1.0, s));
     TRY(mark(c, 1, s));
-    TRY(enqueue_waves<double>(c, L, s));
+    TRY(enqueue_waves<T>(c, L, s));
     TRY(mark(c, 2, s));
-    TRY(launch_unpack_tensor<double>(g, Xt, c.X, s));
+    TRY(launch_unpack_tensor<T>(g, Xt, c.X, s));
     return mark(c, 3, s);
 }
 
@@ -799,6 +803,7 @@ int prepare_kernels() {
         if (e == cudaSuccess) e = prepare_batched_tt();
         if (e == cudaSuccess) e = prepare_batched_z();
         if (e == cudaSuccess) e = prepare_batched_df();
+        if (e == cudaSuccess) e = prepare_batched_tt_df();
         if (e == cudaSuccess) e = prepare_refine2();
         if (e == cudaSuccess) e = prepare_norm2();
         if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
@@ -1327,7 +1332,9 @@ int solver_solve_tt(int d, const int64_t* n, const double* const* A, const doubl
     if (d < 2 || d > 4) return TSYLV_EUNSUPPORTED;
     if (work_bytes < solver_tt_workspace_bytes(d, n, o)) return -8;
     if (int st = check_opts(o, d)) return st < 0 ? -9 : st;
-    if (o.precision != TSYLV_FP64 || o.schedule != 0 || o.nmin < 0 || o.fp64_update == 2) return TSYLV_EUNSUPPORTED;
+    const bool df64 = o.precision == TSYLV_DF64;
+    if ((o.precision != TSYLV_FP64 && !df64) || o.schedule != 0 || o.nmin < 0 || o.fp64_update == 2)
+        return TSYLV_EUNSUPPORTED;
     const int shape = shape_of_opts(o, d);
     Call c;
     c.d = d;
@@ -1359,22 +1366,25 @@ int solver_solve_tt(int d, const int64_t* n, const double* const* A, const doubl
         int slots = 0;
         {
             std::lock_guard<std::mutex> lk(m);
-            auto it = occ.find(dev * 8 + d);
+            const int key = (dev * 8 + d) * 2 + (df64 ? 1 : 0);
+            auto it = occ.find(key);
             if (it != occ.end()) {
                 slots = it->second;
             } else {
                 int sms = 0;
                 if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
-                slots = sms * batched_occupancy_tt(d);
-                occ[dev * 8 + d] = slots;
+                slots = sms * (df64 ? batched_occupancy_tt_df(d) : batched_occupancy_tt(d));
+                occ[key] = slots;
             }
         }
         c.flow_grid = static_cast<int>(c.plan->ntiles < slots ? c.plan->ntiles : slots);
     }
     c.L = make_layout(d, c.n, c.plan->nb, false, 8, c.plan->tab.size(), true);
     if (c.L.total > work_bytes) return -8;
-    const int tag = 8192 * 4 | (c.timing ? 2 : 0);
-    if (int st = run_enqueue(*c.plan, make_key(c, tag), o.use_graph != 0, stream, enqueue_tt, c)) return st;
+    const int tag = 8192 * 4 | (c.timing ? 2 : 0) | (df64 ? 1 << 18 : 0);
+    if (int st = run_enqueue(*c.plan, make_key(c, tag), o.use_graph != 0, stream,
+                             df64 ? enqueue_tt_t<dfl> : enqueue_tt_t<double>, c))
+        return st;
     int herr = 0;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(&herr, c.base + c.L.err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)

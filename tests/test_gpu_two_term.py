@@ -120,3 +120,25 @@ def test_two_term_repeat_and_in_place(lib):
     Bd = to_dev(B)
     X3, st = lib.gsylvten_solve(Ad, Cd, Bd, X=Bd)
     assert st == 0 and X3.data_ptr() == Bd.data_ptr() and torch.equal(X3, X1)
+
+
+@pytest.mark.parametrize("d,shape", [(2, (33, 17)), (3, (24, 20, 16)), (3, (37, 30, 23)), (4, (13, 11, 10, 9))])
+def test_two_term_df64(lib, d, shape):
+    """The two-term form in double-float arithmetic (precision TSYLV_DF64),
+    2x2 blocks across the split points, against the oracle at the FP64
+    tolerance."""
+    A, C, B = _problem(47, shape, _force(shape, _te(d)))
+    Xo = two_term.solve_recursive(A, C, B, nmin=4)
+    X, st, _ = _solve(lib, A, C, B, precision=lib.TSYLV_DF64)
+    assert st == 0, lib.status_string(st)
+    Xg = to_host(X)
+    assert rel_err(Xg, Xo) <= TOL and max_rel(Xg, Xo) <= TOL
+
+
+def test_two_term_df64_deep_queue(lib):
+    shape = (96, 80, 72)
+    A, C, B = _problem(45, shape, [[7, 31, 55], [15, 39], [23, 47]])
+    Xo = two_term.solve_recursive(A, C, B, nmin=8)
+    X, st, _ = _solve(lib, A, C, B, precision=lib.TSYLV_DF64)
+    assert st == 0
+    assert rel_err(to_host(X), Xo) <= TOL
