@@ -765,26 +765,26 @@ def run_ours(args, ws, rank, local):
             pr = probs[gen]
             other["tensorcore_256_" + ("generalized" if gen else "laplace")] = precision_sweep(
                 pr["A"], pr["C"], pr["B"], shape, (2, 3))
-        tag = "adjoint_tf32r"
-        infos[tag + "_fwd"] = _lib.Info()
-        infos[tag + "_bwd"] = _lib.Info()
-        Xt = ts.empty_fortran(ADJ_SHAPE, dev)
+        for tag, prc in (("adjoint_tf32r", 2), ("adjoint_df64", 4)):
+            infos[tag + "_fwd"] = _lib.Info()
+            infos[tag + "_bwd"] = _lib.Info()
+            Xt = ts.empty_fortran(ADJ_SHAPE, dev)
 
-        def adjoint_tc():
-            ts.tsylv_solve(adj["A"], adj["B"], X=Xt, info=infos[tag + "_fwd"], precision=PREC[2])
-            adj["out"][2] = ts.tsylv_backward(adj["A"], Xt, Xt - adj["Xs"], want_dB=True, want_dA=True,
-                                              info=infos[tag + "_bwd"], precision=PREC[2])
-        adjoint_tc()
-        tm = event_ms(adjoint_tc, max(3, args.steps))
-        dB, dA, _ = adj["out"][2]
-        dB0, dA0, _ = adj["out"][0]
-        other[tag] = {"ms": tm, "unknowns_per_s": 2 * Na / (tm * 1e-3),
-                      "iterations_fwd_bwd": [infos[tag + "_fwd"].iterations, infos[tag + "_bwd"].iterations],
-                      "vs_fp64": parts["adjoint_fp64"]["ms"] / tm,
-                      "rel_diff_vs_fp64": {
-                          "dB": float(torch.linalg.vector_norm(dB - dB0) / torch.linalg.vector_norm(dB0)),
-                          "dA": max(float(torch.linalg.matrix_norm(a - b) / torch.linalg.matrix_norm(b))
-                                    for a, b in zip(dA, dA0))}}
+            def adjoint_tc(tag=tag, prc=prc, Xt=Xt):
+                ts.tsylv_solve(adj["A"], adj["B"], X=Xt, info=infos[tag + "_fwd"], precision=PREC[prc])
+                adj["out"][prc] = ts.tsylv_backward(adj["A"], Xt, Xt - adj["Xs"], want_dB=True, want_dA=True,
+                                                    info=infos[tag + "_bwd"], precision=PREC[prc])
+            adjoint_tc()
+            tm = event_ms(adjoint_tc, max(3, args.steps))
+            dB, dA, _ = adj["out"][prc]
+            dB0, dA0, _ = adj["out"][0]
+            other[tag] = {"ms": tm, "unknowns_per_s": 2 * Na / (tm * 1e-3),
+                          "iterations_fwd_bwd": [infos[tag + "_fwd"].iterations, infos[tag + "_bwd"].iterations],
+                          "vs_fp64": parts["adjoint_fp64"]["ms"] / tm,
+                          "rel_diff_vs_fp64": {
+                              "dB": float(torch.linalg.vector_norm(dB - dB0) / torch.linalg.vector_norm(dB0)),
+                              "dA": max(float(torch.linalg.matrix_norm(a - b) / torch.linalg.matrix_norm(b))
+                                        for a, b in zip(dA, dA0))}}
         del Xt
         # general (dense) coefficients, Alg. 1: host Schur reduction, GPU
         # change-of-basis transforms (dense FP64 mode products) and the FP64

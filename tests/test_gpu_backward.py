@@ -43,7 +43,7 @@ def _force(shape):
 
 
 @pytest.mark.parametrize("gen,shape", CASES)
-@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32r", "df64"])
 def test_backward_vs_oracle(lib, gen, shape, precision):
     p = synthetic.problem(21, shape, generalized=gen, force_blocks=_force(shape))
     A, C, B, Xs = p["A"], p["C"], p["B"], p["Xstar"]
@@ -51,7 +51,8 @@ def test_backward_vs_oracle(lib, gen, shape, precision):
     dX = X - Xs
     Lam = oracle.solve_backsub(A, dX, C, transpose=True)
     dAo, dCo = oracle.grad(A, X, Lam, C)
-    prec = {"fp64": lib.TSYLV_FP64, "fp32r": lib.TSYLV_FP32_REFINED, "tf32r": lib.TSYLV_TF32_REFINED}[precision]
+    prec = {"fp64": lib.TSYLV_FP64, "fp32r": lib.TSYLV_FP32_REFINED, "tf32r": lib.TSYLV_TF32_REFINED,
+            "df64": lib.TSYLV_DF64}[precision]
     dB, dA, dC = lib.tsylv_backward([to_dev(a) for a in A], to_dev(X), to_dev(dX),
                                     [to_dev(c) for c in C] if gen else None, precision=prec)
     torch.cuda.synchronize()
@@ -212,7 +213,7 @@ def _config_oracle(p):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("precision", ["fp64", "fp32r", "tf32r"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32r", "tf32r", "df64"])
 def test_differentiation_config(lib, precision):
     """d = 3, n = (200, 160, 120), Laplace form, L = 0.5 ||X - X*||^2: the
     gradient against the oracle's FP64 gradient, and (FP64) central finite
@@ -221,7 +222,8 @@ def test_differentiation_config(lib, precision):
     p = synthetic.problem(0, shape)
     A, B, Xs = p["A"], p["B"], p["Xstar"]
     X, Lam, dAo = _config_oracle(p)
-    prec = {"fp64": lib.TSYLV_FP64, "fp32r": lib.TSYLV_FP32_REFINED, "tf32r": lib.TSYLV_TF32_REFINED}[precision]
+    prec = {"fp64": lib.TSYLV_FP64, "fp32r": lib.TSYLV_FP32_REFINED, "tf32r": lib.TSYLV_TF32_REFINED,
+            "df64": lib.TSYLV_DF64}[precision]
     Ad = [to_dev(a).requires_grad_(True) for a in A]
     Bd = to_dev(B).requires_grad_(True)
     Xd = lib.solve(Ad, Bd, precision=prec)
