@@ -128,3 +128,33 @@ def test_df64_singular(lib):
     A = [to_dev(a) for a in p["A"]]
     _, st = lib.tsylv_solve(A, to_dev(p["B"]), precision=lib.TSYLV_DF64, check=False)
     assert st == 1
+
+
+@pytest.mark.parametrize("kw", [{"nmin": -1}, {"leaf": (6, 5, 8)}, {"nmin": 4}])
+def test_df64_tile_shapes(lib, kw):
+    """Other leaf bounds (fixed, per mode, or autotuned) in double-float arithmetic."""
+    shape = (29, 22, 18)
+    p = synthetic.problem(9, shape, generalized=True, force_blocks=_force(shape, 8))
+    Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+    assert rel_err(to_host(_solve(lib, p, **kw)), Xo) <= TOL
+
+
+def test_df64_plan_and_in_place(lib):
+    """A double-float solve plan (two right-hand sides queued) and an in-place call."""
+    shape = (30, 21, 17)
+    p = synthetic.problem(10, shape, generalized=True)
+    A = [to_dev(a) for a in p["A"]]
+    C = [to_dev(c) for c in p["C"]]
+    plan = lib.SolvePlan(A, C, precision=lib.TSYLV_DF64)
+    B2 = np.asfortranarray(2.0 * p["B"])
+    outs = [plan.solve(to_dev(p["B"])), plan.solve(to_dev(B2))]
+    torch.cuda.synchronize()
+    Xo = oracle.solve_recursive(p["A"], p["B"], p["C"], nmin=4)
+    for scale, (X, status) in zip((1.0, 2.0), outs):
+        assert int(status.item()) == 0
+        assert rel_err(to_host(X), scale * Xo) <= TOL
+    plan.close()
+    B = to_dev(p["B"])
+    X, st = lib.gtsylv_solve(A, C, B, X=B, precision=lib.TSYLV_DF64)
+    assert st == 0
+    assert rel_err(to_host(X), Xo) <= TOL
