@@ -223,16 +223,19 @@ __device__ __forceinline__ dfl ld_dsmem(const dfl* local, uint32_t rank) {
 template <typename T>
 __device__ __forceinline__ T settle(T x) { return x; }
 
-// warp broadcast of a value of the element type
+// warp broadcast of a value of the element type (within segments of `width`
+// lanes when width < 32: src is then the lane within the segment)
 template <typename T>
-__device__ __forceinline__ T shfl(unsigned mask, T v, int src) { return __shfl_sync(mask, v, src); }
-template <>
-__device__ __forceinline__ dfl shfl<dfl>(unsigned mask, dfl v, int src) {
-    return dfl(__shfl_sync(mask, v.h, src), __shfl_sync(mask, v.l, src));
+__device__ __forceinline__ T shfl(unsigned mask, T v, int src, int width = 32) {
+    return __shfl_sync(mask, v, src, width);
 }
 template <>
-__device__ __forceinline__ zd shfl<zd>(unsigned mask, zd v, int src) {
-    return zd(__shfl_sync(mask, v.re, src), __shfl_sync(mask, v.im, src));
+__device__ __forceinline__ dfl shfl<dfl>(unsigned mask, dfl v, int src, int width) {
+    return dfl(__shfl_sync(mask, v.h, src, width), __shfl_sync(mask, v.l, src, width));
+}
+template <>
+__device__ __forceinline__ zd shfl<zd>(unsigned mask, zd v, int src, int width) {
+    return zd(__shfl_sync(mask, v.re, src, width), __shfl_sync(mask, v.im, src, width));
 }
 template <>
 __device__ __forceinline__ dfl settle<dfl>(dfl x) { return dfl_detail::fast_two_sum(x.h, x.l); }

@@ -84,7 +84,8 @@ struct WaveCfg {
     static constexpr int oEnd = INV_EARLY ? oMinv + MINV : oE + (CHAIN ? D * TC : 0);
     static constexpr size_t oBar = ((oEnd * sizeof(T)) + 15) / 16 * 16;
     static constexpr size_t oMeta = oBar + ((8 * NST + 15) / 16) * 16;
-    // meta: gs, gl, gidx [D][TE]; ng, bs [D]; flag [4]; coupled-group lists
+    // meta: gs, gl, gidx [D][TE]; ng, bs [D]; flag [4]; coupled-group lists;
+    // element lists
     static constexpr int MAXSTEP = D * TE;
     static constexpr size_t oJob =
         oMeta + (3 * D * TE + 3 * D + 4 + 3 * MAXSTEP + 1 + 2 * (TD / 2 + 1) + 3 * MAXSTEP + 1 + TD) * sizeof(int);
@@ -379,7 +380,8 @@ __device__ __forceinline__ int member_with(int mask, int m, int mu, int k) {
 }
 
 template <typename T, int D, int FM, int S>
-__device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D], int mask, const T* minv) {
+__device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int* list, const int* moff, int count,
+                                const T* Minv) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int TC = TE * TE;
@@ -387,8 +389,21 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
     constexpr bool GEN = C::GEN;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const bool act = lane < S;
-    const int m = act ? lane : 0;
+    const int g = lane / S, m = lane % S;
+    const bool act = g < count;
+    // the lane's group: first element, 2x2 modes, precomputed inverse (if any)
+    int a[D], mask = 0;
+    {
+        int rem = list[act ? g : 0] & 0xfff;
+#pragma unroll
+        for (int mu = 0; mu < D; mu++) {
+            a[mu] = rem % TE;
+            rem /= TE;
+            if (sm.gl[mu * TE + sm.gidx[mu * TE + a[mu]]] == 2) mask |= 1 << mu;
+        }
+    }
+    const int mo = moff[act ? g : 0];
+    const T* minv = act && mo >= 0 ? Minv + mo : nullptr;
     int u[D], o = 0;
 #pragma unroll
     for (int mu = 0; mu < D; mu++) {
@@ -411,7 +426,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int src = member_with(mask, m, l, k);
-                const T pp = dev::shfl(full, P0[l + 1], src);
+                const T pp = dev::shfl(full, P0[l + 1], src, S);
                 if (k == 0 || two) p = dev::fmadd(Em(l, u[l], two ? a[l] + k : u[l]), pp, p);
             }
             P0[l] = p;
@@ -422,7 +437,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int src = member_with(mask, m, 0, k);
-                const T pp = dev::shfl(full, P0[1], src);
+                const T pp = dev::shfl(full, P0[1], src, S);
                 if (k == 0 || two) of = dev::fmadd(Em(0, u[0], two ? a[0] + k : u[0]), pp, of);
             }
         }
@@ -466,8 +481,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int src = member_with(mask, m, l, k);
-                const T pp = dev::shfl(full, P0[l + 1], src);
-                const T gg = dev::shfl(full, G0[l + 1], src);
+                const T pp = dev::shfl(full, P0[l + 1], src, S);
+                const T gg = dev::shfl(full, G0[l + 1], src, S);
                 if (k == 0 || two) {
                     const int kk = two ? a[l] + k : u[l];
                     p = dev::fmadd(Em(l, u[l], kk), pp, p);
@@ -483,8 +498,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int src = member_with(mask, m, 0, k);
-                const T pp = dev::shfl(full, P0[1], src);
-                const T gg = dev::shfl(full, G0[1], src);
+                const T pp = dev::shfl(full, P0[1], src, S);
+                const T gg = dev::shfl(full, G0[1], src, S);
                 if (k == 0 || two) {
                     const int kk = two ? a[0] + k : u[0];
                     of = dev::fmadd(Em(0, u[0], kk), gg, dev::fmadd(Dm(0, u[0], kk), pp, of));
@@ -508,67 +523,76 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
             row[k] = e;
         }
     }
-    if (!act) {
-        r = 0;
+    // lanes of a group that is not eliminated here (it has an inverse, or the
+    // segment has no group) carry an identity row, which the elimination
+    // leaves as it is
+    const bool ge = act && minv == nullptr;
+    if (!act) r = 0;
+    if (!ge) {
 #pragma unroll
-        for (int k = 0; k < S; k++) row[k] = 0;
+        for (int k = 0; k < S; k++) row[k] = k == m ? T(1) : T(0);
     }
     int status = 0;
     T x = 0;
-    if (minv != nullptr) {
+    if (__any_sync(full, minv != nullptr)) {
         // precomputed inverse: x_m = sum_k Minv(m, k) r_k
 #pragma unroll
         for (int k = 0; k < S; k++) {
-            const T rk = dev::shfl(full, r, k);
-            if (act) x = dev::fmadd(minv[m * S + k], rk, x);
-        }
-    } else {
-    // scale for the pivot test: 16 eps max |M| (magnitudes in the real type of T)
-    using R = typename RealOf<T>::type;
-    R big = 0;
-#pragma unroll
-    for (int k = 0; k < S; k++) big = fmax(big, fabs(row[k]));
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) big = fmax(big, __shfl_xor_sync(full, big, w));
-    const R tiny = R(16) * dev::Eps<T>::v * big;
-    // forward elimination
-#pragma unroll
-    for (int c = 0; c < S; c++) {
-        R val = (lane >= c && act) ? fabs(row[c]) : R(-1);
-        int idx = lane;
-#pragma unroll
-        for (int w = 16; w >= 1; w >>= 1) {
-            const R ov = __shfl_xor_sync(full, val, w);
-            const int oi = __shfl_xor_sync(full, idx, w);
-            if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
-        }
-        const int pv = idx;  // identical on every lane
-        if (pv != c) {
-            const int src = lane == c ? pv : (lane == pv ? c : lane);
-#pragma unroll
-            for (int k = 0; k < S; k++) row[k] = dev::shfl(full, row[k], src);
-            r = dev::shfl(full, r, src);
-        }
-        T prow[S];
-#pragma unroll
-        for (int k = 0; k < S; k++) prow[k] = dev::shfl(full, row[k], c);
-        const T pr = dev::shfl(full, r, c);
-        if (!(fabs(prow[c]) > tiny)) status |= kErrSingular;
-        if (act && lane > c) {
-            const T f = row[c] / prow[c];
-#pragma unroll
-            for (int k = c + 1; k < S; k++) row[k] = dev::fmadd(-f, prow[k], row[k]);
-            r = dev::fmadd(-f, pr, r);
+            const T rk = dev::shfl(full, r, k, S);
+            if (minv != nullptr) x = dev::fmadd(minv[m * S + k], rk, x);
         }
     }
-    // back substitution; lane m ends with x_m
+    if (__any_sync(full, ge)) {
+        // scale for the pivot test: 16 eps max |M| over the group (magnitudes
+        // in the real type of T)
+        using R = typename RealOf<T>::type;
+        R big = 0;
 #pragma unroll
-    for (int c = S - 1; c >= 0; c--) {
-        const T xc_local = r / row[c];
-        const T xc = dev::shfl(full, xc_local, c);
-        if (lane == c) x = xc;
-        if (act && lane < c) r = dev::fmadd(-row[c], xc, r);
-    }
+        for (int k = 0; k < S; k++) big = fmax(big, fabs(row[k]));
+#pragma unroll
+        for (int w = S / 2; w >= 1; w >>= 1) big = fmax(big, __shfl_xor_sync(full, big, w, S));
+        const R tiny = R(16) * dev::Eps<T>::v * big;
+        // forward elimination; the reciprocal of each pivot stays with the
+        // pivot's lane for the back substitution
+        T dinv = T(1);
+#pragma unroll
+        for (int c = 0; c < S; c++) {
+            R val = m >= c ? fabs(row[c]) : R(-1);
+            int idx = m;
+#pragma unroll
+            for (int w = S / 2; w >= 1; w >>= 1) {
+                const R ov = __shfl_xor_sync(full, val, w, S);
+                const int oi = __shfl_xor_sync(full, idx, w, S);
+                if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+            }
+            const int pv = idx;  // identical on the lanes of a segment
+            if (__any_sync(full, pv != c)) {
+                const int src = m == c ? pv : (m == pv ? c : m);
+#pragma unroll
+                for (int k = 0; k < S; k++) row[k] = dev::shfl(full, row[k], src, S);
+                r = dev::shfl(full, r, src, S);
+            }
+            // the pivot row is broadcast one entry at a time
+            const T pc = dev::shfl(full, row[c], c, S);
+            if (ge && !(fabs(pc) > tiny)) status |= kErrSingular;
+            const T rinv = T(1) / pc;
+            if (m == c) dinv = rinv;
+            const T f = row[c] * rinv;
+#pragma unroll
+            for (int k = c + 1; k < S; k++) {
+                const T pk = dev::shfl(full, row[k], c, S);
+                if (m > c) row[k] = dev::fmadd(-f, pk, row[k]);
+            }
+            const T pr = dev::shfl(full, r, c, S);
+            if (m > c) r = dev::fmadd(-f, pr, r);
+        }
+        // back substitution; lane m ends with x_m
+#pragma unroll
+        for (int c = S - 1; c >= 0; c--) {
+            const T xc = dev::shfl(full, r * dinv, c, S);
+            if (ge && m == c) x = xc;
+            if (m < c) r = dev::fmadd(-row[c], xc, r);
+        }
     }
     if (act) {
         if (!isfinite(x)) status |= kErrNonfinite;
@@ -583,7 +607,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
             T p = 0;
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const T xv = dev::shfl(full, x, member_with(mask, m, mu, k));
+                const T xv = dev::shfl(full, x, member_with(mask, m, mu, k), S);
                 if (k == 0 || two) p = dev::fmadd(Em(mu, u[mu], two ? a[mu] + k : u[mu]), xv, p);
             }
             pc[mu] = p;
@@ -594,7 +618,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
             T p = 0;
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const T pp = dev::shfl(full, pc[l + 1], member_with(mask, m, l, k));
+                const T pp = dev::shfl(full, pc[l + 1], member_with(mask, m, l, k), S);
                 if (k == 0 || two) p = dev::fmadd(Em(l, u[l], two ? a[l] + k : u[l]), pp, p);
             }
             pc[l] = p;
@@ -613,7 +637,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
             T p = 0, q = 0;
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const T xv = dev::shfl(full, x, member_with(mask, m, mu, k));
+                const T xv = dev::shfl(full, x, member_with(mask, m, mu, k), S);
                 if (k == 0 || two) {
                     const int kk = two ? a[mu] + k : u[mu];
                     p = dev::fmadd(Em(mu, u[mu], kk), xv, p);
@@ -630,8 +654,8 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int src = member_with(mask, m, l, k);
-                const T pp = dev::shfl(full, pc[l + 1], src);
-                const T gg = dev::shfl(full, gc[l + 1], src);
+                const T pp = dev::shfl(full, pc[l + 1], src, S);
+                const T gg = dev::shfl(full, gc[l + 1], src, S);
                 if (k == 0 || two) {
                     const int kk = two ? a[l] + k : u[l];
                     p = dev::fmadd(Em(l, u[l], kk), pp, p);
@@ -652,24 +676,18 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int (&a)[D],
     return status;
 }
 
-// Warp-uniform entry: the group whose first member is the in-block element e.
+// Warp-uniform entry: `count` (<= 32 >> cls) groups with cls coupled modes,
+// listed at `list` (first in-block element of each) with their inverse
+// offsets at `moff` (-1: none).
 template <typename T, int D, int FM>
-__device__ int warp_group(const TileSmem<T, D, FM>& sm, int e, const T* minv) {
-    constexpr int TE = tile_extent(D);
-    int a[D], mask = 0, rem = e;
-#pragma unroll
-    for (int mu = 0; mu < D; mu++) {
-        a[mu] = rem % TE;
-        rem /= TE;
-        const int gi = sm.gidx[mu * TE + a[mu]];
-        if (sm.gl[mu * TE + gi] == 2) mask |= 1 << mu;
-    }
-    switch (__popc(mask)) {
-        case 1: return warp_group_solve<T, D, FM, 2>(sm, a, mask, minv);
-        case 2: return warp_group_solve<T, D, FM, 4>(sm, a, mask, minv);
-        case 3: if constexpr (D >= 3) return warp_group_solve<T, D, FM, 8>(sm, a, mask, nullptr); else return 0;
-        case 4: if constexpr (D >= 4) return warp_group_solve<T, D, FM, 16>(sm, a, mask, nullptr); else return 0;
-        case 5: if constexpr (D >= 5) return warp_group_solve<T, D, FM, 32>(sm, a, mask, nullptr); else return 0;
+__device__ int warp_group(const TileSmem<T, D, FM>& sm, int cls, const int* list, const int* moff, int count,
+                          const T* Minv) {
+    switch (cls) {
+        case 1: return warp_group_solve<T, D, FM, 2>(sm, list, moff, count, Minv);
+        case 2: return warp_group_solve<T, D, FM, 4>(sm, list, moff, count, Minv);
+        case 3: if constexpr (D >= 3) return warp_group_solve<T, D, FM, 8>(sm, list, moff, count, Minv); else return 0;
+        case 4: if constexpr (D >= 4) return warp_group_solve<T, D, FM, 16>(sm, list, moff, count, Minv); else return 0;
+        case 5: if constexpr (D >= 5) return warp_group_solve<T, D, FM, 32>(sm, list, moff, count, Minv); else return 0;
         default: return 0;
     }
 }
@@ -1097,7 +1115,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     int* cg_cnt = gidx + D * TE;        // coupled groups per anti-diagonal
     int* cg_off = cg_cnt + C::MAXSTEP;  // their offsets in cg_list
     int* cg_fill = cg_off + C::MAXSTEP + 1;
-    int* cg_list = cg_fill + C::MAXSTEP;
+    int* cg_list = cg_fill + C::MAXSTEP;  // class << 12 | first element (in-block elements < 4096)
     int* cg_moff = cg_list + (TD / 2 + 1);  // offset of each group's inverse (-1: none)
     int* act_cnt = cg_moff + (TD / 2 + 1);  // elements per anti-diagonal
     int* act_off = act_cnt + C::MAXSTEP;
@@ -1228,23 +1246,28 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     if (tid == 0) {
         // canonical order within every anti-diagonal (the fill order above
         // depends on the atomics), so that which groups get an inverse within
-        // the budget, and hence the rounding, is the same in every run
+        // the budget, and hence the rounding, is the same in every run: by
+        // class (number of coupled modes), then by first element, so that
+        // the groups of one class that a warp solves together are adjacent
+        auto cls_of = [&](int e) {
+            int rem = e, mask = 0;
+            for (int mu = 0; mu < D; mu++) {
+                const int ai = rem % TE;
+                rem /= TE;
+                if (gl[mu * TE + gidx[mu * TE + ai]] == 2) mask |= 1 << mu;
+            }
+            return __popc(mask);
+        };
         for (int st = 0; st < C::MAXSTEP; st++)
-            for (int i = cg_off[st] + 1; i < cg_off[st + 1]; i++) {
-                const int v = cg_list[i];
+            for (int i = cg_off[st]; i < cg_off[st + 1]; i++) {
+                const int v = (cls_of(cg_list[i]) << 12) | cg_list[i];
                 int k = i - 1;
                 for (; k >= cg_off[st] && cg_list[k] > v; k--) cg_list[k + 1] = cg_list[k];
                 cg_list[k + 1] = v;
             }
         int run = 0;
         for (int i = 0; i < ncg; i++) {
-            int rem = cg_list[i], mask = 0;
-            for (int mu = 0; mu < D; mu++) {
-                const int ai = rem % TE;
-                rem /= TE;
-                if (gl[mu * TE + gidx[mu * TE + ai]] == 2) mask |= 1 << mu;
-            }
-            const int S = 1 << __popc(mask);
+            const int S = 1 << (cg_list[i] >> 12);
             if (S <= 4 && run + S * S <= C::MINV) {
                 cg_moff[i] = run;
                 run += S * S;
@@ -1258,7 +1281,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
         const TileSmem<T, D, GENF> smi{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
         for (int i = tid; i < ncg; i += kThreads)
             if constexpr (!C::CPLX)
-                if (cg_moff[i] >= 0) status |= group_inverse<T, D, GENF>(smi, cg_list[i], Minv + cg_moff[i]);
+                if (cg_moff[i] >= 0) status |= group_inverse<T, D, GENF>(smi, cg_list[i] & 0xfff, Minv + cg_moff[i]);
     }
     bool dead = false;
     for (int jj = 0; jj < njob && !dead; jj++) {
@@ -1472,7 +1495,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
     TileSmem<T, D, GENF> sm{Ds, Es, Rs, Rd, Xs, Pin, Gin, Lin, gs, gl, ng, bs, gidx};
     if constexpr (!C::INV_EARLY && !C::CPLX)
         for (int i = tid; i < ncg; i += kThreads)
-            if (cg_moff[i] >= 0) status |= group_inverse<T, D, GENF>(sm, cg_list[i], Minv + cg_moff[i]);
+            if (cg_moff[i] >= 0) status |= group_inverse<T, D, GENF>(sm, cg_list[i] & 0xfff, Minv + cg_moff[i]);
     __syncthreads();
     // all warps take part (a one-warp variant with warp barriers between the
     // anti-diagonals measured slower for FP32 too: the line sums of one step
@@ -1508,10 +1531,35 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             if (cn > 0) {
                 if constexpr (SOLO) __syncwarp(); else __syncthreads();
                 const int warp = SOLO ? 0 : tid >> 5, nw = SOLO ? 1 : kThreads >> 5;
-                if constexpr (!C::CPLX)  // no coupled groups with complex triangular coefficients
-                    for (int k = warp; k < cn; k += nw)
-                        status |= warp_group<T, D, GENF>(sm, cg_list[c0 + k],
-                                                        cg_moff[c0 + k] >= 0 ? Minv + cg_moff[c0 + k] : nullptr);
+                if constexpr (!C::CPLX) {  // no coupled groups with complex triangular coefficients
+                    // groups of each class in this anti-diagonal (the list is
+                    // ordered by class), then the warp tasks: up to 32 >> c
+                    // groups of class c each
+                    int cc[D];
+#pragma unroll
+                    for (int c = 0; c < D; c++) cc[c] = 0;
+                    for (int i0 = 0; i0 < cn; i0 += 32) {
+                        const int i = i0 + (tid & 31);
+                        const int cls = i < cn ? cg_list[c0 + i] >> 12 : 0;
+#pragma unroll
+                        for (int c = 0; c < D; c++) cc[c] += __popc(__ballot_sync(0xffffffffu, cls == c + 1));
+                    }
+                    int ntask = 0;
+#pragma unroll
+                    for (int c = 1; c <= D; c++) ntask += (cc[c - 1] + (32 >> c) - 1) >> (5 - c);
+                    for (int tk = warp; tk < ntask; tk += nw) {
+                        int c = 1, first = 0, rest = tk;
+                        for (; c < D; c++) {
+                            const int nt = (cc[c - 1] + (32 >> c) - 1) >> (5 - c);
+                            if (rest < nt) break;
+                            rest -= nt;
+                            first += cc[c - 1];
+                        }
+                        first += rest << (5 - c);
+                        const int count = min(32 >> c, cc[c - 1] - (rest << (5 - c)));
+                        status |= warp_group<T, D, GENF>(sm, c, cg_list + c0 + first, cg_moff + c0 + first, count, Minv);
+                    }
+                }
             }
             if constexpr (SOLO) __syncwarp(); else __syncthreads();
         }
