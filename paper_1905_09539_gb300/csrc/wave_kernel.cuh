@@ -541,6 +541,7 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int* list, c
             const T rk = dev::shfl(full, r, k, S);
             if (minv != nullptr) x = dev::fmadd(minv[m * S + k], rk, x);
         }
+        x = dev::settle(x);
     }
     if (__any_sync(full, ge)) {
         // scale for the pivot test: 16 eps max |M| over the group (magnitudes
@@ -578,20 +579,23 @@ __device__ int warp_group_solve(const TileSmem<T, D, FM>& sm, const int* list, c
             const T rinv = T(1) / pc;
             if (m == c) dinv = rinv;
             const T f = row[c] * rinv;
+            // (double-float: the updated pairs are normalised, so that the
+            // pivot tests, which read the high word, see their value after
+            // the cancellation that elimination is made of)
 #pragma unroll
             for (int k = c + 1; k < S; k++) {
                 const T pk = dev::shfl(full, row[k], c, S);
-                if (m > c) row[k] = dev::fmadd(-f, pk, row[k]);
+                if (m > c) row[k] = dev::settle(dev::fmadd(-f, pk, row[k]));
             }
             const T pr = dev::shfl(full, r, c, S);
-            if (m > c) r = dev::fmadd(-f, pr, r);
+            if (m > c) r = dev::settle(dev::fmadd(-f, pr, r));
         }
         // back substitution; lane m ends with x_m
 #pragma unroll
         for (int c = S - 1; c >= 0; c--) {
             const T xc = dev::shfl(full, r * dinv, c, S);
             if (ge && m == c) x = xc;
-            if (m < c) r = dev::fmadd(-row[c], xc, r);
+            if (m < c) r = dev::settle(dev::fmadd(-row[c], xc, r));
         }
     }
     if (act) {
@@ -863,7 +867,7 @@ __device__ int group_inverse_s(const TileSmem<T, D, GEN>& sm, const int (&a)[D],
             if (q == c) continue;
             const T f = W[q][c];
 #pragma unroll
-            for (int k = 0; k < 2 * S; k++) W[q][k] = dev::fmadd(-f, W[c][k], W[q][k]);
+            for (int k = 0; k < 2 * S; k++) W[q][k] = dev::settle(dev::fmadd(-f, W[c][k], W[q][k]));
         }
     }
 #pragma unroll
