@@ -68,6 +68,12 @@ struct WaveCfg {
     // (complex triangular coefficients have no 2x2 blocks, hence no inverses)
     static constexpr bool CPLX = IsComplex<T>::value;
     static constexpr bool INV_EARLY = D >= 2 && !CPLX && !(sizeof(T) == 8 && !CHAIN);
+    // FP64: the base case's line sums run, warp by warp, over the terms some
+    // lane of the warp needs (a rolled range; measured 2% faster for the
+    // d-term form at 256^3, 2.6% slower for the double-float Laplace form,
+    // whose pair arithmetic issues from the FP32 pipes and wants the unrolled,
+    // per-lane form)
+    static constexpr bool WARP_TERMS = std::is_same<T, double>::value;
     static constexpr bool PIN_IN_RING = CHAIN && sizeof(T) == 8 && 2 * NL * TD <= NST * STAGE;
     static constexpr int UNION = (NST * STAGE > MINV || INV_EARLY) ? NST * STAGE : MINV;
     static constexpr int oStage = 0;
@@ -365,11 +371,15 @@ __device__ __forceinline__ int solve_single(const TileSmem<T, D, FM>& sm, int o,
     return isfinite(x) ? 0 : kErrNonfinite;
 }
 
-// Coupled group solved by one warp: lane m (< S) holds the equation row of
-// member m.  Members are ordered with the 2x2 modes of `mask` as binary
-// digits (member offset delta_mu(m) in {0, 1}).  Gaussian elimination with
-// partial pivoting runs across the lanes with warp shuffles; everything from
-// outside the group is already in the running line sums Lin.
+// Coupled groups of S members solved by one warp, 32 / S groups at a time:
+// the warp's lanes form segments of S lanes, lane m of segment g holds the
+// equation row of member m of group g.  Members are ordered with the 2x2
+// modes of the group's `mask` as binary digits (member offset delta_mu(m) in
+// {0, 1}).  Gaussian elimination with partial pivoting runs across the lanes
+// of each segment with shuffles of width S; everything from outside the group
+// is already in the running line sums Lin.  Packing the groups keeps the
+// lanes of the FP64 pipes busy (a warp instruction occupies them whatever
+// lanes are active).
 __device__ __forceinline__ int member_delta(int mask, int m, int mu) {
     return ((mask >> mu) & 1) ? ((m >> __popc(mask & ((1 << mu) - 1))) & 1) : 0;
 }
@@ -704,7 +714,7 @@ __device__ int warp_group(const TileSmem<T, D, FM>& sm, int cls, const int* list
 // interleaved chains, so the latency is that of a few multiply-adds.
 template <typename T, int D, int FM>
 __device__ __forceinline__ void pull_lines(const TileSmem<T, D, FM>& sm, int e, const int (&u)[D], const int (&k0s)[D],
-                                           T (&L)[WaveCfg<T, D, FM>::NACC]) {
+                                           T (&L)[WaveCfg<T, D, FM>::NACC], bool on) {
     constexpr int TE = tile_extent(D);
     constexpr int TD = ipow(TE, D);
     constexpr int TC = TE * TE;
@@ -720,16 +730,24 @@ __device__ __forceinline__ void pull_lines(const TileSmem<T, D, FM>& sm, int e, 
         T a0 = 0, a1 = 0, b0 = 0, b1 = 0, c0 = 0, c1 = 0;
         // FP32: all TE terms with the coefficients before k0 masked to zero
         // (positions beyond the block extent hold zeros), fully unrolled so
-        // that every load is in flight at once; FP64: only the terms needed
-        // (the FP64 pipe is the scarce resource there)
+        // that every load is in flight at once; wider types: only the terms
+        // needed (the FP64 pipe is the scarce resource there, and a warp
+        // instruction occupies it whatever lanes are active).  WARP_TERMS:
+        // the range starts at the warp's first needed term (`on` marks the
+        // lanes that hold an element; all 32 lanes call).
         constexpr bool FULL = sizeof(T) == 4;
+        constexpr bool WT = C::WARP_TERMS;
+        int wlo = 0;
+        if constexpr (WT) wlo = __reduce_min_sync(0xffffffffu, on ? k0 : TE);
 #pragma unroll
-        for (int k = 0; k < TE; k++) {
+        for (int kk = 0; kk < TE; kk++) {
+            const int k = WT ? wlo + kk : kk;
+            if (WT && k >= kb) break;  // uniform over the warp
             if (!FULL && (k < k0 || k >= kb)) continue;
             const bool in = !FULL || k >= k0;
             const int v = in ? e + (k - u[mu]) * st : e;
             const T dv = in ? sm.Ds[mu * TC + u[mu] + TE * k] : T(0);
-            const bool odd = k & 1;
+            const bool odd = kk & 1;
             if constexpr (C::TT) {
                 // chain factor (C in mode 1, A_mu elsewhere) on X (mode d) or
                 // on Q_{mu+1}; mode 1 also carries A_1 on X
@@ -1512,7 +1530,7 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
             // then the 1x1 groups are solved by their threads; members of coupled
             // groups publish their sums for the solving warp
             const int a0 = act_off[step], an = act_cnt[step];
-            for (int i = SOLO ? lane : tid; i < an; i += SOLO ? 32 : kThreads) {
+            auto line_step = [&](int i, bool on) {
                 const int code = act_list[a0 + i];
                 const int e = ElemCode<D>::elem(code);
                 int u[D], k0s[D], rem = e;
@@ -1523,13 +1541,21 @@ __device__ __forceinline__ bool wave_tile(const WaveArgs& a, const long long t, 
                     k0s[mu] = ElemCode<D>::k0(code, mu);
                 }
                 T L[NACC];
-                pull_lines<T, D, GENF>(sm, e, u, k0s, L);
+                pull_lines<T, D, GENF>(sm, e, u, k0s, L, on);
+                if (!on) return;
                 if (!ElemCode<D>::coupled(code)) {
                     status |= solve_single<T, D, GENF>(sm, e, u, L);
                 } else {
 #pragma unroll
                     for (int k = 0; k < NACC; k++) Lin[k * TD + e] = L[k];
                 }
+            };
+            if constexpr (C::WARP_TERMS) {
+                // whole warps take part (the line sums' term range is the warp's)
+                for (int i0 = SOLO ? 0 : (tid & ~31); i0 < an; i0 += SOLO ? 32 : kThreads)
+                    line_step(i0 + lane < an ? i0 + lane : i0, i0 + lane < an);
+            } else {
+                for (int i = SOLO ? lane : tid; i < an; i += SOLO ? 32 : kThreads) line_step(i, true);
             }
             const int c0 = cg_off[step], cn = cg_cnt[step];
             if (cn > 0) {
