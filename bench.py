@@ -38,8 +38,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.10
 # DRAM bytes (read + write) per launch of the dominant kernel (one FP64 solve of
 # the 256^3 generalized form) from an ncu capture of the current kernel:
-# 10.535 GB read + 0.846 GB written (the capture is summarised under profiles/)
-TRAFFIC_PER_LAUNCH_BYTES = 11.381e9
+# 10.531 GB read + 0.842 GB written (the capture is summarised under profiles/)
+TRAFFIC_PER_LAUNCH_BYTES = 11.373e9
 
 
 def bf16_peak_measured():
