@@ -91,6 +91,37 @@ def test_dense_assembled_solve(shape, gen):
 
 
 @pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("shape", [(8, 6), (6, 6, 6), (7, 5, 6), (4, 4, 4, 4)])
+def test_dense_solve_all_pairs(shape, gen):
+    """Every index of every mode in a 2x2 block (one 1x1 block left in odd
+    modes): nearly every unknown belongs to a coupled group of 2^d members,
+    the perfect-shuffled diagonal blocks of Sec. 2.3 at their densest."""
+    force = [list(range(0, n - 1, 2)) for n in shape]
+    p = _prob(shape, gen, seed=5, force=force)
+    A, C, B = p["A"], p["C"], p["B"]
+    Xd = unvec(np.linalg.solve(operator(A, C), vec(B)), shape)
+    for X in (oracle.solve_backsub(A, B, C),
+              oracle.solve_recursive(A, B, C, nmin=2),
+              oracle.solve_recursive(A, B, C, nmin=4)):
+        assert np.linalg.norm(X - Xd) / np.linalg.norm(Xd) <= 1e-13
+
+
+@pytest.mark.parametrize("shape", [(10, 8, 6), (9, 7)])
+def test_dense_solve_real_schur(shape):
+    """Coefficients that are real Schur forms of dense random matrices (the
+    reduction of Alg. 1): 2x2 blocks wherever LAPACK's standardised form puts
+    a complex pair, with unequal off-diagonal entries."""
+    rng = np.random.default_rng(7)
+    A = [np.asfortranarray(sla.schur(rng.standard_normal((n, n)) / np.sqrt(n) + 2.5 * np.eye(n),
+                                     output="real")[0]) for n in shape]
+    assert sum(int(np.count_nonzero(np.diag(a, -1))) for a in A) >= 2
+    B = np.asfortranarray(rng.standard_normal(shape))
+    Xd = unvec(np.linalg.solve(operator(A, None), vec(B)), shape)
+    for X in (oracle.solve_backsub(A, B, None), oracle.solve_recursive(A, B, None, nmin=2)):
+        assert np.linalg.norm(X - Xd) / np.linalg.norm(Xd) <= 1e-13
+
+
+@pytest.mark.parametrize("gen", [False, True])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_apply_matches_kron(shape, gen):
     p = _prob(shape, gen, seed=4)
